@@ -1,0 +1,102 @@
+"""Pins of the oracle's SCP loop (Sec. III-A) on the two workload models.
+
+* a nominal produced by an RK4 rollout has zero dynamics defect, so the
+  merit of the first nominal equals its cost, computed here from the
+  problem data;
+* the nominal carried to the next iteration is the candidate when it is
+  accepted and the old nominal otherwise (bookkeeping of the acceptance test);
+* converged solves reach the defect level the method is measured at
+  (max |RK4(x_i,u_i) - x_{i+1}|_inf <= 1e-5), satisfy the boundary
+  conditions of Eq. (1c) and the control sets exactly, and keep clear of the
+  obstacles / inside the thrust and glide-slope sets.
+"""
+import math
+
+import numpy as np
+
+import oracle
+import workloads as W
+
+
+def instance(prob, x, u, b):
+    xo, uo, N = prob.xoff[b], prob.uoff[b], int(prob.N[b])
+    return x[xo:xo + N + 1], u[uo:uo + N]
+
+
+def cost(prob, b, x, u):
+    """phi(x_N) + sum l(x_i, u_i) of Eq. (1a), from the problem data."""
+    N = int(prob.N[b])
+    ex = x - prob.xref[b]; eu = u - prob.uref[b]
+    c = 0.5 * np.sum(prob.Qd[b] * ex[:N] ** 2) + 0.5 * np.sum(prob.Rd[b] * eu ** 2)
+    c += 0.5 * np.sum(prob.QNd[b] * ex[N] ** 2) + prob.qN[b] @ x[N]
+    return c
+
+
+def max_defect(prob, b, x, u):
+    N = int(prob.N[b])
+    return max(np.abs(oracle.rk4(prob.model, prob.params[b], prob.dt[b], x[i], u[i]) - x[i + 1]).max()
+               for i in range(N))
+
+
+def test_rollout_nominal_has_zero_defect_and_merit_equals_cost():
+    prob = W.quad_path(1, seed=3, settings=dict(scp_iters=1, admm_iters=5))
+    N = int(prob.N[0])
+    u = prob.uguess.copy()
+    u[:, 1] += 0.05 * np.sin(np.arange(N))
+    x = np.zeros((N + 1, 12)); x[0] = prob.xinit[0]
+    for i in range(N):
+        x[i + 1] = oracle.rk4(1, prob.params[0], prob.dt[0], x[i], u[i])
+    _, _, _, log = oracle.scp_solve(prob, xguess=x, uguess=u, log=True)
+    assert max_defect(prob, 0, x, u) == 0.0
+    assert abs(log[0, 0, 2] - cost(prob, 0, x, u)) < 1e-9 * max(1.0, abs(cost(prob, 0, x, u)))
+
+
+def test_nominal_bookkeeping_follows_accept_flags():
+    prob = W.quad_path(1, seed=0)
+    _, _, st, log = oracle.scp_solve(prob, log=True)
+    K = int(prob.settings["scp_iters"])
+    for k in range(K - 1):
+        expect = log[0, k, 3] if log[0, k, 0] == 1 else log[0, k, 2]
+        assert abs(log[0, k + 1, 2] - expect) <= 1e-9 * max(1.0, abs(expect))
+    assert st[0, 8] == np.sum(log[0, :, 0])
+
+
+def test_quadrotor_converges_and_respects_sets():
+    # with rho = 10 the solves reach the defect level (rho = 1 needs far more iterations)
+    prob = W.quad_path(4, seed=0, settings=dict(rho_eq=10.0, rho_dyn=10.0, rho_geo=10.0, scp_iters=40,
+                                                stop=1, step_tol=1.0))
+    x, u, st, _ = oracle.scp_solve(prob)
+    for b in range(4):
+        xb, ub = instance(prob, x, u, b)
+        assert st[b, 0] <= 1e-5 and st[b, 10] == 0
+        assert abs(max_defect(prob, b, xb, ub) - st[b, 0]) < 1e-15
+        np.testing.assert_array_equal(xb[0], prob.xinit[b])                   # x_0 = x_init
+        np.testing.assert_array_equal(xb[-1][:6], prob.xtarget[b][:6])        # S x_N = x_target
+        assert ub.min() >= prob.ulo[b].min() and ub.max() <= prob.uhi[b].max()  # control box
+        for j in range(prob.nobs[b]):
+            dist = np.linalg.norm(xb[:, :3] - prob.obs_c[b, j], axis=1)
+            assert dist.min() >= prob.obs_r[b, j] - 1e-4
+
+
+def test_mars_converges_and_respects_sets():
+    prob = W.mars_batch(3, seed=1)
+    x, u, st, _ = oracle.scp_solve(prob)
+    tmin, tmax, tang = prob.sets[0, :3]
+    for b in range(3):
+        xb, ub = instance(prob, x, u, b)
+        assert st[b, 0] <= 1e-5 and st[b, 10] == 0
+        assert st[b, 7] < 150                                                 # stopped by the test
+        np.testing.assert_array_equal(xb[0], prob.xinit[b])
+        np.testing.assert_array_equal(xb[-1][:6], 0.0)
+        Tn = np.linalg.norm(ub, axis=1)
+        assert Tn.max() <= tmax + 1e-4 and Tn.min() >= tmin - 1e-4             # thrust annulus
+        horiz = np.hypot(xb[:, 1], xb[:, 2])
+        assert np.all(horiz <= tang * xb[:, 0] + 1e-4)                        # glide slope
+        assert xb[:, 6].min() >= prob.xlo[b, 6] and np.all(np.diff(xb[:, 6]) <= 1e-5)   # mass only falls
+
+
+def test_fixed_count_solve_runs_every_iteration():
+    prob = W.quad_path(1, seed=0)
+    _, _, st, log = oracle.scp_solve(prob, log=True)
+    assert st[0, 7] == prob.settings["scp_iters"]
+    assert np.all(np.isfinite(log[0, :, 2]))
