@@ -1,0 +1,306 @@
+"""Benchmark: SCP solves/s at max nonlinear defect <= 1e-5 on one GB300.
+
+Workload: the Mars powered-descent batch (1024 instances, N = 100, 3-DOF,
+|T| in [4.8, 19.2] kN, glide slope 86 deg), solved by the fused persistent
+SCP kernel in the FP32 + refinement path (ADMM in FP32, RK4 rollout /
+defect / acceptance in FP64).  One step = one ucn_scp_solve launch over the
+whole batch.  `value` counts only solves whose returned trajectory has max
+defect <= 1e-5.  The plain FP64 path is timed beside it on the same batch.
+
+  python bench.py [--steps K] [--warmup W] [--gpus N] [--impl ours|reference]
+
+Multi-GPU (torchrun): instances are independent, so every rank solves its
+own batch (weak scaling, no data-path collective); value = passing solves
+of all ranks / max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "SCP solves/s at defect<=1e-5 (batched FP32+refine; plain FP64 beside it); p50/p99 ms"
+UNIT = "solves/s"
+WORKLOAD = "mars_batch_1024_N100"
+SM_COUNT, FP32_LANES = 152, 128
+
+
+def flops_per_node_iter(nx, nu, mirror_flops, refine=True):
+    """FP32 arithmetic of one ADMM iteration at one node (FMA = 2 flops).
+
+    Step 1: A^T w, B^T w (2 nx n), two triangular solves (2 n (n+1));
+    refinement: H xi via A xi + B u, A^T v, B^T v (4 nx n) + 4 n, two more
+    solves; propagation A x + B u + c (2 nx n); Steps 2-4: 12 flops per
+    state component, 6 per control component, plus the mirror sets."""
+    n = nx + nu
+    f = 2 * nx * n + 2 * n * (n + 1) + 2 * nx * n + 12 * nx + 6 * nu + mirror_flops
+    if refine:
+        f += 4 * nx * n + 4 * n + 2 * n * (n + 1)
+    return f
+
+
+def mars_mirror_flops():
+    # cone (|y|, compare, scale: ~30), ball (~20), half-space (~14) with their duals and RHS terms
+    return 64
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_rank%d.csv" % gpu_index)
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        try:
+            rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        except Exception:
+            rows = []
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if len(r) > 5 + k and "Active" in r[5 + k]
+                          and "Not" not in r[5 + k]})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def run_ours(args, rank, world):
+    import torch
+    from paper_2603_10711_gb300 import ucn
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    prob = W.mars_batch(args.batch, seed=1 + rank)
+    B = prob.batch
+    solver = ucn.Solver(prob, precision=ucn.UCN_PREC_FP32_REFINE, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    x0 = solver.tensor(prob.xguess)
+    u0 = solver.tensor(prob.uguess)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 256 MB > L2
+
+    def step():
+        solver.scp_solve(x0, u0)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    times, passed, lat, nodeiters = [], 0, [], 0
+    sampler = ClockSampler(dev.index)
+    with sampler:
+        for _ in range(args.steps):
+            flush.fill_(1.0)                       # evict the batch from L2 between steps
+            e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+            st = solver.stats_host()
+            passed += int(np.sum(st["defect"] <= 1e-5))
+            t0 = st["t_start_ns"].min()
+            lat.extend(((st["t_end_ns"] - t0) / 1e6).tolist())
+            nodeiters += int(np.sum(st["scp_iters"].astype(np.int64) * (prob.N.astype(np.int64) + 1))) * int(prob.settings["admm_iters"])
+    torch.cuda.synchronize()
+    total = sum(times)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total, float(passed)], dtype=torch.float64, device=dev)
+        tmax = t.clone(); dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        tsum = t.clone(); dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+        total, passed_all = float(tmax[0]), float(tsum[1])
+    else:
+        passed_all = passed
+    value = passed_all / total
+    clocks = sampler.summary()
+
+    # ---- end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    xh = torch.from_numpy(np.ascontiguousarray(prob.xguess)).pin_memory()
+    uh = torch.from_numpy(np.ascontiguousarray(prob.uguess)).pin_memory()
+    xo_h = torch.empty(solver.x_out.shape, dtype=torch.float64).pin_memory()
+    uo_h = torch.empty(solver.u_out.shape, dtype=torch.float64).pin_memory()
+    so_h = torch.empty(solver.stats.shape, dtype=torch.uint8).pin_memory()
+    e2e_times, e2e_pass = [], 0
+    for _ in range(max(2, args.steps // 2)):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        x0.copy_(xh, non_blocking=True); u0.copy_(uh, non_blocking=True)
+        solver.scp_solve(x0, u0)
+        xo_h.copy_(solver.x_out, non_blocking=True); uo_h.copy_(solver.u_out, non_blocking=True)
+        so_h.copy_(solver.stats, non_blocking=True)
+        torch.cuda.current_stream(dev).synchronize()
+        e2e_times.append(time.perf_counter() - t0)
+        st = np.frombuffer(so_h.numpy().tobytes(), dtype=ucn.STATS_DTYPE)
+        e2e_pass += int(np.sum(st["defect"] <= 1e-5))
+    h2d = xh.numel() * 8 + uh.numel() * 8
+    d2h = xo_h.numel() * 8 + uo_h.numel() * 8 + so_h.numel()
+
+    # ---- plain FP64 path on the same batch (a few steps; it is the slow comparison path)
+    s64 = ucn.Solver(prob, precision=ucn.UCN_PREC_FP64, device=dev)
+    s64.scp_solve(x0, u0); torch.cuda.synchronize()
+    t64, p64 = [], 0
+    for _ in range(args.fp64_steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream); s64.scp_solve(x0, u0); e1.record(stream); e1.synchronize()
+        t64.append(e0.elapsed_time(e1) / 1e3)
+        p64 += int(np.sum(s64.stats_host()["defect"] <= 1e-5))
+    st64 = s64.stats_host()
+    s64.close()
+
+    flops_ni = flops_per_node_iter(prob.nx, prob.nu, mars_mirror_flops())
+    flops_launch = nodeiters / args.steps * flops_ni
+    avg = total / args.steps if world == 1 else sum(times) / len(times)
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_tf = SM_COUNT * FP32_LANES * 2 * sm_max * 1e6 / 1e12
+    achieved = flops_launch / avg / 1e12
+    st_last = solver.stats_host()
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (ADMM) + f64 (rollout, defect, acceptance)",
+        "data": "synthetic (seeded Mars descent dispersions)",
+        "config": {"workload": WORKLOAD, "instances_per_gpu": B, "horizon": 100, "nx": 7, "nu": 3,
+                   "admm_iters_per_scp": int(prob.settings["admm_iters"]), "scp_iter_cap": int(prob.settings["scp_iters"]),
+                   "rho": "1 -> 1e5 geometric", "stop": "defect <= 1e-5", "l2": "flushed (256 MB write) before each step",
+                   "parallelism": "one CTA per instance, one thread per node; ranks hold independent batches"},
+        "pass_rate": passed / (B * args.steps),
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                       "definition": "per solve: instance end - first instance start within its launch"},
+        "scp_iters_mean": float(st_last["scp_iters"].mean()),
+        "fp64_plain": {"value": p64 / sum(t64), "unit": UNIT, "ms_per_step": 1e3 * sum(t64) / len(t64),
+                       "pass_rate": p64 / (B * len(t64)), "scp_iters_mean": float(st64["scp_iters"].mean())},
+        "e2e": {"value": e2e_pass / sum(e2e_times), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
+                     "frac": achieved / peak_tf, "traffic": None,
+                     "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 x %.0f MHz" % sm_max,
+                     "algorithmic_flops_per_node_iter": flops_ni, "node_iters_per_launch": nodeiters / args.steps},
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+    }
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        out["cpu_baseline"] = cpu_baseline(args)
+    solver.close()
+    return out
+
+
+def oracle_sample(args, seconds=None):
+    """The FP64 CPU oracle on a bounded sample of the same workload."""
+    import oracle
+    prob = W.mars_batch(args.batch, seed=1)
+    threads = oracle.max_threads()
+    n = max(threads, args.cpu_sample)
+    sub = prob.subset(np.arange(n) * (prob.batch // n))
+    t0 = time.perf_counter()
+    _, _, st, _ = oracle.scp_solve(sub, nthreads=threads)
+    dt = time.perf_counter() - t0
+    passed = int(np.sum(st[:, 0] <= 1e-5))
+    return passed, n, dt, threads
+
+
+def cpu_baseline(args):
+    passed, n, dt, threads = oracle_sample(args)
+    return {"value": passed / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": "%d of the %d Mars instances (every %d-th), %.1f s, %d passed" % (n, args.batch, args.batch // n, dt, passed)}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    times, passed_all, n_all = [], 0, 0
+    for _ in range(args.warmup):
+        pass   # the oracle has no warm state; warm-up steps are not needed on the CPU
+    for _ in range(args.steps):
+        passed, n, dt, threads = oracle_sample(args)
+        times.append(dt); passed_all += passed; n_all += n
+    value = passed_all / sum(times)
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded Mars descent dispersions)",
+            "config": {"workload": WORKLOAD, "instances_per_step": n_all // args.steps},
+            "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": "%d Mars instances per step on %d host threads" % (n_all // args.steps, threads)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "pass_rate": passed_all / max(1, n_all)}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--batch", type=int, default=1024)
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--cpu-sample", type=int, default=96)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1 and args.impl == "ours":
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+    else:
+        out = run_ours(args, rank, world)
+    if rank == 0 and out is not None:
+        print(json.dumps(out))
+    if world > 1 and args.impl == "ours":
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

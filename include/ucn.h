@@ -1,0 +1,190 @@
+/*
+ * ucn -- GPU-native sequential convex programming with a consensus-ADMM
+ * inner solver (arXiv 2603.10711), for NVIDIA GB300 (sm_103a).
+ *
+ * C ABI.  Every pointer argument is either a HOST pointer (suffix none,
+ * only in ucn_problem_desc) or a DEVICE pointer (suffix _d) owned by the
+ * caller; sizes are element counts.  All device buffers are packed per
+ * node across the batch:
+ *
+ *   states   x[total_x][nx], total_x = sum_b (N_b + 1); instance b owns rows
+ *            xoff_b .. xoff_b + N_b with xoff_b = sum_{b'<b} (N_b' + 1)
+ *   controls u[total_u][nu], total_u = sum_b N_b, uoff_b = sum_{b'<b} N_b'
+ *   A[total_u][nx][nx], B[total_u][nx][nu], d[total_u][nx]  (row-major)
+ *
+ * Calls are asynchronous on the given CUDA stream (a cudaStream_t passed
+ * as void*; NULL = legacy default stream).  They return validation and
+ * launch errors synchronously; numerical outcomes are reported per
+ * instance in the stats records.  No call allocates device memory except
+ * ucn_problem_create (which allocates the whole workspace); no exception
+ * crosses the ABI.  ucn_last_error() returns a thread-local message for
+ * the last failing call on the calling thread.
+ *
+ * Equations cited are those of the paper:
+ *   Eq. (1)   the discrete nonlinear optimal control problem
+ *   Eq. (2)   the convex QP subproblem at SCP iterate k
+ *   Eq. (3)   the augmented Lagrangian of the temporal splitting
+ *   Eq. (4)   the per-node KKT Hessian H_i (Sec. III-B, Step 1)
+ *   Eq. (5)   the dynamic consensus update (Step 2)
+ *   Eq. (6)-(7) projections (Step 3);  Eq. (8) dual ascent (Step 4)
+ */
+#ifndef UCN_H
+#define UCN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  UCN_OK = 0,
+  UCN_EINVAL = 1,     /* invalid argument or descriptor */
+  UCN_ENOMEM = 2,     /* device allocation failed (ucn_problem_create only) */
+  UCN_ECUDA = 3,      /* a CUDA runtime call failed */
+  UCN_ENUMERIC = 4,   /* per instance: NaN/Inf or a non-positive Cholesky pivot */
+  UCN_ENOTCONV = 5,   /* per instance: final defect above defect_tol */
+  UCN_ETIMEOUT = 6,   /* per instance: the device time budget ran out */
+  UCN_EBUSY = 7       /* serving: no free slot / ring full */
+} ucn_status;
+
+typedef enum { UCN_MODEL_QUAD12 = 1, UCN_MODEL_MARS7 = 2 } ucn_model;
+typedef enum { UCN_PREC_FP64 = 0, UCN_PREC_FP32_REFINE = 1 } ucn_precision;
+
+/*
+ * Problem batch (host memory; copied to the device by ucn_problem_create).
+ * The OCP of Eq. (1):  min phi(x_N) + sum_i l(x_i,u_i)  s.t.  x_{i+1} = RK4(x_i,u_i,dt),
+ * x_0 = x_init, S x_N = x_target (S = term_mask), x_i in X_i, u_i in U_i.
+ *
+ *  model         UCN_MODEL_QUAD12 (nx=12: p, v, ZYX Euler angles, body rates;
+ *                nu=4 rotor thrusts) or UCN_MODEL_MARS7 (nx=7: r Up-East-North,
+ *                v, mass; nu=3 thrust vector; non-dimensional units)
+ *  horizon[b]    N_b >= 1;  dt[b] RK4 step
+ *  model_params  [batch][8]: quad (m, Jx, Jy, Jz, arm, km, drag, g);
+ *                Mars (g, alpha = mass flow per unit thrust, 0...)
+ *  cost          l = 1/2 |x - x_ref|^2_Q + 1/2 |u - u_ref|^2_R (diagonal Q, R),
+ *                phi = 1/2 |x_N - x_ref|^2_QN + qN^T x_N       [batch][nx|nu]
+ *  boxes         x_lo/x_hi [batch][nx], u_lo/u_hi [batch][nu] (+-inf allowed)
+ *  obstacles     quad only: n_obs[b] <= max_obs spheres obs_c [batch][max_obs][3],
+ *                obs_r [batch][max_obs]; linearised about the nominal
+ *  sets          Mars only [batch][4]: thrust_min (linearised |T| >= Tmin),
+ *                thrust_max (ball |T| <= Tmax), tan of the glide-slope cone
+ *                half-angle; a value <= 0 switches the set off
+ *  rho_*         ADMM penalties of Eq. (3); rho_final > 0 selects the geometric
+ *                schedule rho_k = rho * (rho_final/rho_geo)^(k/(scp_iters-1))
+ *  scp_iters     SCP iteration cap; admm_iters ADMM iterations per SCP iteration
+ *  stop          1: stop an instance once an accepted candidate has max defect
+ *                <= defect_tol and step <= step_tol (0: run every iteration)
+ *  tr_*          l_inf trust region (initial, floor, cap) of Eq. (2c)
+ *  w_d           weight of the l1 defect in the acceptance merit
+ *  vc_weight     virtual control weight; must be 0 (virtual control is off)
+ *  precision     UCN_PREC_FP64: every step in FP64.  UCN_PREC_FP32_REFINE:
+ *                Jacobians, factorisation and ADMM in FP32 with one
+ *                iterative-refinement step per KKT solve; the RK4 rollout,
+ *                defects, costs and residual sums in FP64
+ *  timeout_s     device time budget per ucn_scp_solve launch (0: 60 s)
+ */
+typedef struct {
+  int model, nx, nu, batch;
+  const int* horizon;
+  const double* dt;
+  const double* model_params;
+  const double *Q_diag, *x_ref, *R_diag, *u_ref, *QN_diag, *qN;
+  const double *x_lo, *x_hi, *u_lo, *u_hi;
+  const double *x_init, *x_target;
+  const unsigned char* term_mask;
+  int max_obs;
+  const int* n_obs;
+  const double *obs_c, *obs_r;
+  const double* sets;
+  double rho_eq, rho_dyn, rho_geo, rho_final;
+  int scp_iters, admm_iters, stop;
+  double tr_init, tr_min, tr_max, w_d, defect_tol, step_tol, vc_weight;
+  int precision;
+  double timeout_s;
+} ucn_problem_desc;
+
+/* Per-instance result of ucn_scp_solve (device memory, 128 bytes). */
+typedef struct {
+  double defect;        /* max_i |RK4(x_i,u_i) - x_{i+1}|_inf of the returned trajectory */
+  double cost;          /* phi(x_N) + sum l(x_i,u_i) of the returned trajectory */
+  double merit;         /* cost + w_d * sum_i |defect_i|_1 */
+  double primal_res;    /* ADMM primal residual of the last ADMM call (FP64 sum) */
+  double dual_res;      /* ADMM dual residual of the last ADMM step (FP64 sum) */
+  double tr_radius;     /* trust-region radius at exit */
+  double step;          /* |candidate - nominal|_inf of the last SCP iteration */
+  int scp_iters;        /* SCP iterations run */
+  int accepted;         /* candidates accepted */
+  unsigned long long accept_mask;   /* bit k: iteration k accepted (k < 64) */
+  int status;           /* ucn_status: OK, ENUMERIC, ENOTCONV or ETIMEOUT */
+  int reserved;
+  unsigned long long t_start_ns, t_end_ns;   /* device globaltimer at instance start / end */
+  double pad[4];
+} ucn_scp_stats;
+
+typedef struct ucn_problem ucn_problem;
+
+/* Validate `desc`, copy it to the device and allocate every workspace the
+ * calls below need (the only allocating call).  Blocks until the copies are
+ * done.  Errors: UCN_EINVAL (bad sizes, model, pointers, vc_weight != 0,
+ * horizon too long), UCN_ENOMEM, UCN_ECUDA.  Eq. (1) and (2) define the data. */
+ucn_status ucn_problem_create(const ucn_problem_desc* desc, ucn_problem** out);
+
+/* Free everything ucn_problem_create allocated (synchronises the device). */
+void ucn_problem_destroy(ucn_problem* prob);
+
+/* Number of elements of the packed state / trajectory buffers. */
+long long ucn_total_x(const ucn_problem* prob);
+long long ucn_total_u(const ucn_problem* prob);
+/* Doubles written by ucn_state_export (sum over instances of the flat ADMM state). */
+long long ucn_state_size(const ucn_problem* prob);
+
+/* Linearisation (Sec. III-A, Eq. (2b)): for every node i < N_b of every
+ * instance, A_i = dRK4/dx, B_i = dRK4/du at (xbar_i, ubar_i) and
+ * d_i = RK4(xbar_i, ubar_i) - A_i xbar_i - B_i ubar_i.  Forward-mode
+ * differentiation through the four RK4 stages, in FP64 (precision FP64)
+ * or FP32 for A, B with d in FP64 (precision FP32_REFINE).
+ * In: xbar_d [total_x][nx], ubar_d [total_u][nu].  Out: A_d, B_d, d_d. */
+ucn_status ucn_linearize(ucn_problem* prob, const double* xbar_d, const double* ubar_d,
+                         double* A_d, double* B_d, double* d_d, void* stream);
+
+/* One ADMM call (Sec. III-B, Steps 1-4, `iters` iterations) on each
+ * instance's QP of Eq. (2) built at the nominal (xbar, ubar) with the given
+ * linearisation (A, B, d), trust radius radius_d[b] and the problem's costs,
+ * boxes and sets.  H_i of Eq. (4) is assembled and Cholesky-factored once per
+ * call.  warm = 0 starts from x = x-hat = z = nominal, zero duals; warm = 1
+ * continues from the state left by the previous ucn_admm_solve on this
+ * problem.  Out: xhat_d [total_x][nx], uhat_d [total_u][nu] (the mirror
+ * trajectory), res_d [batch][2] (primal, dual residual), status_d [batch]. */
+ucn_status ucn_admm_solve(ucn_problem* prob, const double* xbar_d, const double* ubar_d,
+                          const double* A_d, const double* B_d, const double* d_d,
+                          const double* radius_d, int iters, int warm,
+                          double* xhat_d, double* uhat_d, double* res_d, int* status_d,
+                          void* stream);
+
+/* Copy the ADMM state left by the last ucn_admm_solve / ucn_scp_solve, in
+ * absolute FP64 coordinates, to state_d [ucn_state_size].  Per instance, in
+ * order: x (N+1)nx, u N nu, z (N+1)nx (z_0 = 0), lambda (N+1)nx, mu (N+1)nx,
+ * x-hat (N+1)nx, u-hat N nu, nu_x (N+1)nx, nu_u N nu, mirrors s (N+1) mb 3 and
+ * their duals (N+1) mb 3, where mb = max_obs (quad) or 3 (Mars: glide cone,
+ * thrust ball, thrust lower bound). */
+ucn_status ucn_state_export(ucn_problem* prob, double* state_d, void* stream);
+
+/* Full SCP solve (Sec. III-A with the ADMM of Sec. III-B) of every
+ * instance in ONE persistent kernel launch: per SCP iteration the RK4
+ * linearisation, assembly + factorisation, admm_iters ADMM iterations, and
+ * the FP64 rollout / defect / trust-region acceptance test, all on the
+ * device.  In: initial guesses x0_d, u0_d.  Out: x_out_d, u_out_d (the last
+ * accepted trajectory), stats_d [batch], status_d [batch] (== stats.status). */
+ucn_status ucn_scp_solve(ucn_problem* prob, const double* x0_d, const double* u0_d,
+                         double* x_out_d, double* u_out_d, ucn_scp_stats* stats_d,
+                         int* status_d, void* stream);
+
+/* Thread-local description of the last error on this thread ("" if none). */
+const char* ucn_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* UCN_H */

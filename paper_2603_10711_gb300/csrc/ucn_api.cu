@@ -1,0 +1,289 @@
+// C-ABI implementation: descriptor validation, device copies, workspace
+// sizing and kernel dispatch.  See include/ucn.h for the contract.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "ucn_internal.h"
+#include "ucn_kernels.cuh"
+
+using namespace ucn;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+ucn_status fail(ucn_status s, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return s;
+}
+
+// Host-side fault injection: UCN_FAULT_ALLOC=n makes the n-th device
+// allocation of a ucn_problem_create call fail (1-based).
+int fault_alloc_at() {
+  const char* e = std::getenv("UCN_FAULT_ALLOC");
+  return e ? std::atoi(e) : 0;
+}
+
+long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
+
+Layout make_layout(int model, int nodes, int max_obs, int tsize) {
+  const int NX = model == UCN_MODEL_QUAD12 ? 12 : 7, NU = model == UCN_MODEL_QUAD12 ? 4 : 3, NN = NX + NU;
+  // must match Rec<M>: the fixed part of a node record
+  const int fixed = NX * NX + NX * NU + NX + NN * (NN + 1) / 2 + NX + NU + 2 * NX + 2 * NU + 6 * NX + 3 * NU + 2 * NX;
+  const int dfixed = 2 * NX + NU;
+  Layout L;
+  std::memset(&L, 0, sizeof(L));
+  const int mo = std::max(max_obs, 1);
+  L.MS = model == UCN_MODEL_QUAD12 ? mo : 7;
+  L.MD = model == UCN_MODEL_QUAD12 ? 4 * mo : 4;
+  L.MB = model == UCN_MODEL_QUAD12 ? max_obs : 3;
+  L.oS = fixed;
+  L.oNus = fixed + L.MS;
+  L.oMd = fixed + 2 * L.MS;
+  const int nt = fixed + 2 * L.MS + L.MD;
+  L.S = nodes;
+  L.NS = nt | 1;       // odd record strides: consecutive nodes fall in distinct banks
+  L.DS = dfixed | 1;
+  L.tbytes = round_up((long long)nodes * L.NS * tsize, 16);
+  L.bytes = round_up(L.tbytes + (long long)nodes * L.DS * 8, 16);
+  return L;
+}
+
+}  // namespace
+
+struct ucn_problem {
+  int model, nx, nu, batch, max_obs, Nmax, precision;
+  long long total_x, total_u, state_size;
+  std::vector<void*> allocs;
+  ProblemDev dev;
+  Layout L;
+  bool smem;
+  long long smem_bytes;
+  int threads;
+  int* node_inst;
+};
+
+namespace {
+
+template <class V>
+ucn_status dev_copy(ucn_problem* p, int& nalloc, int fault_at, const V* host, size_t n, V** out) {
+  ++nalloc;
+  if (fault_at > 0 && nalloc == fault_at) return fail(UCN_ENOMEM, "injected allocation failure (UCN_FAULT_ALLOC=%d)", fault_at);
+  void* d = nullptr;
+  const size_t bytes = std::max<size_t>(n * sizeof(V), 16);
+  if (cudaMalloc(&d, bytes) != cudaSuccess) { cudaGetLastError(); return fail(UCN_ENOMEM, "cudaMalloc of %zu bytes failed", bytes); }
+  p->allocs.push_back(d);
+  if (host && n) {
+    const cudaError_t e = cudaMemcpy(d, host, n * sizeof(V), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return fail(UCN_ECUDA, "cudaMemcpy: %s", cudaGetErrorString(e));
+  } else {
+    cudaMemset(d, 0, bytes);
+  }
+  *out = (V*)d;
+  return UCN_OK;
+}
+
+cudaStream_t as_stream(void* s) { return (cudaStream_t)s; }
+
+}  // namespace
+
+extern "C" {
+
+const char* ucn_last_error(void) { return g_err; }
+
+void ucn_problem_destroy(ucn_problem* p) {
+  if (!p) return;
+  cudaDeviceSynchronize();
+  for (void* a : p->allocs) cudaFree(a);
+  delete p;
+}
+
+ucn_status ucn_problem_create(const ucn_problem_desc* d, ucn_problem** out) {
+  g_err[0] = 0;
+  if (!d || !out) return fail(UCN_EINVAL, "null descriptor or output pointer");
+  *out = nullptr;
+  if (d->model != UCN_MODEL_QUAD12 && d->model != UCN_MODEL_MARS7) return fail(UCN_EINVAL, "unknown model %d", d->model);
+  const int NX = d->model == UCN_MODEL_QUAD12 ? 12 : 7, NU = d->model == UCN_MODEL_QUAD12 ? 4 : 3;
+  if (d->nx != NX || d->nu != NU) return fail(UCN_EINVAL, "model %d needs nx=%d nu=%d (got %d, %d)", d->model, NX, NU, d->nx, d->nu);
+  if (d->batch < 1) return fail(UCN_EINVAL, "batch must be >= 1 (got %d)", d->batch);
+  if (d->precision != UCN_PREC_FP64 && d->precision != UCN_PREC_FP32_REFINE) return fail(UCN_EINVAL, "unknown precision %d", d->precision);
+  if (d->vc_weight != 0.0) return fail(UCN_EINVAL, "virtual control (vc_weight != 0) is not supported");
+  if (!d->horizon || !d->dt || !d->model_params || !d->Q_diag || !d->x_ref || !d->R_diag || !d->u_ref ||
+      !d->QN_diag || !d->qN || !d->x_lo || !d->x_hi || !d->u_lo || !d->u_hi || !d->x_init || !d->x_target ||
+      !d->term_mask)
+    return fail(UCN_EINVAL, "a required descriptor array is NULL");
+  if (d->model == UCN_MODEL_QUAD12 && d->max_obs > 0 && (!d->n_obs || !d->obs_c || !d->obs_r))
+    return fail(UCN_EINVAL, "obstacle arrays are NULL with max_obs > 0");
+  if (d->model == UCN_MODEL_MARS7 && !d->sets) return fail(UCN_EINVAL, "Mars problems need the sets array");
+  if (d->max_obs < 0 || d->max_obs > 64) return fail(UCN_EINVAL, "max_obs must be in [0, 64]");
+  if (!(d->rho_eq > 0 && d->rho_dyn > 0 && d->rho_geo > 0)) return fail(UCN_EINVAL, "penalties must be positive");
+  if (d->scp_iters < 1 || d->admm_iters < 1) return fail(UCN_EINVAL, "iteration counts must be >= 1");
+  if (!(d->tr_init > 0 && d->tr_min > 0 && d->tr_max >= d->tr_min)) return fail(UCN_EINVAL, "bad trust-region bounds");
+  int Nmax = 0;
+  for (int b = 0; b < d->batch; ++b) {
+    const int N = d->horizon[b];
+    if (N < 1 || N + 1 > MAX_THREADS) return fail(UCN_EINVAL, "horizon[%d] = %d outside [1, %d]", b, N, MAX_THREADS - 1);
+    if (!(d->dt[b] > 0)) return fail(UCN_EINVAL, "dt[%d] must be positive", b);
+    if (d->model == UCN_MODEL_QUAD12 && d->max_obs > 0 && (d->n_obs[b] < 0 || d->n_obs[b] > d->max_obs))
+      return fail(UCN_EINVAL, "n_obs[%d] = %d outside [0, max_obs]", b, d->n_obs[b]);
+    Nmax = std::max(Nmax, N);
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return fail(UCN_ECUDA, "no CUDA device"); }
+  ucn_problem* p = new ucn_problem();
+  p->model = d->model; p->nx = NX; p->nu = NU; p->batch = d->batch; p->max_obs = d->model == UCN_MODEL_QUAD12 ? d->max_obs : 0;
+  p->Nmax = Nmax; p->precision = d->precision;
+  const int B = d->batch;
+  std::vector<long long> xoff(B), uoff(B), soff(B);
+  std::vector<int> node_inst;
+  const int mb = d->model == UCN_MODEL_QUAD12 ? p->max_obs : 3;
+  long long tx = 0, tu = 0, ts = 0;
+  for (int b = 0; b < B; ++b) {
+    const long long N = d->horizon[b];
+    xoff[b] = tx; uoff[b] = tu; soff[b] = ts;
+    tx += N + 1; tu += N;
+    ts += 6 * (N + 1) * NX + 3 * N * NU + 2 * (N + 1) * mb * 3;
+    for (long long i = 0; i < N; ++i) node_inst.push_back(b);
+  }
+  p->total_x = tx; p->total_u = tu; p->state_size = ts;
+  const int fa = fault_alloc_at();
+  int na = 0;
+  ucn_status s = UCN_OK;
+  ProblemDev& P = p->dev;
+  std::memset(&P, 0, sizeof(P));
+  P.model = d->model; P.nx = NX; P.nu = NU; P.batch = B; P.max_obs = p->max_obs;
+  std::vector<double> zeros_obs(1, 0.0);
+  std::vector<int> zeros_nobs(B, 0);
+  std::vector<double> zeros_sets((size_t)B * 4, 0.0);
+#define COPY(dst, src, n)                                                                  \
+  if (s == UCN_OK) { s = dev_copy(p, na, fa, src, (size_t)(n), &dst); }
+  int* Ndev = nullptr; long long *xo = nullptr, *uo = nullptr, *so = nullptr;
+  double *dtd, *prm, *Qd, *xr, *Rd, *ur, *QNd, *qN, *xlo, *xhi, *ulo, *uhi, *xi, *xt, *oc, *orr, *sets;
+  unsigned char* tm; int* nobs;
+  COPY(Ndev, d->horizon, B); COPY(xo, xoff.data(), B); COPY(uo, uoff.data(), B); COPY(so, soff.data(), B);
+  COPY(dtd, d->dt, B); COPY(prm, d->model_params, (size_t)B * 8);
+  COPY(Qd, d->Q_diag, (size_t)B * NX); COPY(xr, d->x_ref, (size_t)B * NX);
+  COPY(Rd, d->R_diag, (size_t)B * NU); COPY(ur, d->u_ref, (size_t)B * NU);
+  COPY(QNd, d->QN_diag, (size_t)B * NX); COPY(qN, d->qN, (size_t)B * NX);
+  COPY(xlo, d->x_lo, (size_t)B * NX); COPY(xhi, d->x_hi, (size_t)B * NX);
+  COPY(ulo, d->u_lo, (size_t)B * NU); COPY(uhi, d->u_hi, (size_t)B * NU);
+  COPY(xi, d->x_init, (size_t)B * NX); COPY(xt, d->x_target, (size_t)B * NX);
+  COPY(tm, d->term_mask, (size_t)B * NX);
+  if (p->max_obs > 0) {
+    COPY(nobs, d->n_obs, B); COPY(oc, d->obs_c, (size_t)B * p->max_obs * 3); COPY(orr, d->obs_r, (size_t)B * p->max_obs);
+  } else {
+    COPY(nobs, zeros_nobs.data(), B); COPY(oc, zeros_obs.data(), 1); COPY(orr, zeros_obs.data(), 1);
+  }
+  COPY(sets, d->sets ? d->sets : zeros_sets.data(), (size_t)B * 4);
+  int* ni = nullptr;
+  COPY(ni, node_inst.empty() ? zeros_nobs.data() : node_inst.data(), std::max<size_t>(node_inst.size(), 1));
+  double* sabs = nullptr;
+  COPY(sabs, (const double*)nullptr, (size_t)ts);
+#undef COPY
+  if (s != UCN_OK) { ucn_problem_destroy(p); return s; }
+  P.N = Ndev; P.xoff = xo; P.uoff = uo; P.soff = so; P.dt = dtd; P.params = prm;
+  P.Qd = Qd; P.xref = xr; P.Rd = Rd; P.uref = ur; P.QNd = QNd; P.qN = qN;
+  P.xlo = xlo; P.xhi = xhi; P.ulo = ulo; P.uhi = uhi; P.xinit = xi; P.xtarget = xt; P.tmask = tm;
+  P.nobs = nobs; P.obs_c = oc; P.obs_r = orr; P.sets = sets;
+  P.rho_eq = d->rho_eq; P.rho_dyn = d->rho_dyn; P.rho_geo = d->rho_geo; P.rho_final = d->rho_final;
+  P.scp_iters = d->scp_iters; P.admm_iters = d->admm_iters; P.stop = d->stop;
+  P.tr_init = d->tr_init; P.tr_min = d->tr_min; P.tr_max = d->tr_max; P.w_d = d->w_d;
+  P.defect_tol = d->defect_tol; P.step_tol = d->step_tol;
+  P.timeout_ns = (unsigned long long)((d->timeout_s > 0 ? d->timeout_s : 60.0) * 1e9);
+  P.state_abs = sabs;
+  p->node_inst = ni;
+  // per-node storage: shared memory when one instance fits, else a global slice per instance
+  const int tsize = d->precision == UCN_PREC_FP64 ? 8 : 4;
+  p->L = make_layout(d->model, Nmax + 1, p->max_obs, tsize);
+  p->threads = (int)round_up(Nmax + 1, 32);
+  int optin = 0;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  const long long static_sh = (long long)sizeof(InstShared) + 64;
+  p->smem = p->L.bytes + static_sh <= optin;
+  p->smem_bytes = p->smem ? p->L.bytes : 0;
+  P.ws = nullptr;
+  if (!p->smem) {
+    char* ws = nullptr;
+    ++na;
+    if (fa > 0 && na == fa) { ucn_problem_destroy(p); return fail(UCN_ENOMEM, "injected allocation failure (UCN_FAULT_ALLOC=%d)", fa); }
+    if (cudaMalloc(&ws, (size_t)(p->L.bytes * B)) != cudaSuccess) {
+      cudaGetLastError();
+      ucn_problem_destroy(p);
+      return fail(UCN_ENOMEM, "workspace of %lld bytes", (long long)(p->L.bytes * B));
+    }
+    p->allocs.push_back(ws);
+    P.ws = ws;
+  }
+  *out = p;
+  return UCN_OK;
+}
+
+long long ucn_total_x(const ucn_problem* p) { return p ? p->total_x : -1; }
+long long ucn_total_u(const ucn_problem* p) { return p ? p->total_u : -1; }
+long long ucn_state_size(const ucn_problem* p) { return p ? p->state_size : -1; }
+
+static LaunchCfg cfg_of(ucn_problem* p, void* stream) {
+  LaunchCfg c;
+  c.P = &p->dev; c.L = &p->L; c.smem = p->smem; c.smem_bytes = p->smem_bytes;
+  c.threads = p->threads; c.blocks = p->batch; c.stream = as_stream(stream);
+  return c;
+}
+
+ucn_status ucn_linearize(ucn_problem* p, const double* xbar_d, const double* ubar_d, double* A_d, double* B_d,
+                         double* d_d, void* stream) {
+  g_err[0] = 0;
+  if (!p || !xbar_d || !ubar_d || !A_d || !B_d || !d_d) return fail(UCN_EINVAL, "null argument");
+  auto fn = p->model == UCN_MODEL_QUAD12 ? (p->precision == UCN_PREC_FP64 ? quad64_linearize : quad32_linearize)
+                                         : (p->precision == UCN_PREC_FP64 ? mars64_linearize : mars32_linearize);
+  const cudaError_t e = fn(&p->dev, p->node_inst, p->total_u, xbar_d, ubar_d, A_d, B_d, d_d, as_stream(stream));
+  if (e != cudaSuccess) return fail(UCN_ECUDA, "linearize launch: %s", cudaGetErrorString(e));
+  return UCN_OK;
+}
+
+ucn_status ucn_admm_solve(ucn_problem* p, const double* xbar_d, const double* ubar_d, const double* A_d,
+                          const double* B_d, const double* d_d, const double* radius_d, int iters, int warm,
+                          double* xhat_d, double* uhat_d, double* res_d, int* status_d, void* stream) {
+  g_err[0] = 0;
+  if (!p || !xbar_d || !ubar_d || !A_d || !B_d || !d_d || !radius_d || !xhat_d || !uhat_d || !res_d || !status_d)
+    return fail(UCN_EINVAL, "null argument");
+  if (iters < 1) return fail(UCN_EINVAL, "iters must be >= 1");
+  const LaunchCfg c = cfg_of(p, stream);
+  auto fn = p->model == UCN_MODEL_QUAD12 ? (p->precision == UCN_PREC_FP64 ? quad64_admm : quad32_admm)
+                                         : (p->precision == UCN_PREC_FP64 ? mars64_admm : mars32_admm);
+  const cudaError_t e = fn(c, xbar_d, ubar_d, A_d, B_d, d_d, radius_d, iters, warm ? 1 : 0, xhat_d, uhat_d, res_d, status_d);
+  if (e != cudaSuccess) return fail(UCN_ECUDA, "admm launch: %s", cudaGetErrorString(e));
+  return UCN_OK;
+}
+
+ucn_status ucn_state_export(ucn_problem* p, double* state_d, void* stream) {
+  g_err[0] = 0;
+  if (!p || !state_d) return fail(UCN_EINVAL, "null argument");
+  const cudaError_t e = cudaMemcpyAsync(state_d, p->dev.state_abs, (size_t)p->state_size * sizeof(double),
+                                        cudaMemcpyDeviceToDevice, as_stream(stream));
+  if (e != cudaSuccess) return fail(UCN_ECUDA, "state export: %s", cudaGetErrorString(e));
+  return UCN_OK;
+}
+
+ucn_status ucn_scp_solve(ucn_problem* p, const double* x0_d, const double* u0_d, double* x_out_d, double* u_out_d,
+                         ucn_scp_stats* stats_d, int* status_d, void* stream) {
+  g_err[0] = 0;
+  if (!p || !x0_d || !u0_d || !x_out_d || !u_out_d || !stats_d || !status_d) return fail(UCN_EINVAL, "null argument");
+  const LaunchCfg c = cfg_of(p, stream);
+  auto fn = p->model == UCN_MODEL_QUAD12 ? (p->precision == UCN_PREC_FP64 ? quad64_scp : quad32_scp)
+                                         : (p->precision == UCN_PREC_FP64 ? mars64_scp : mars32_scp);
+  const cudaError_t e = fn(c, x0_d, u0_d, x_out_d, u_out_d, stats_d, status_d);
+  if (e != cudaSuccess) return fail(UCN_ECUDA, "scp launch: %s", cudaGetErrorString(e));
+  return UCN_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,1098 @@
+// Device path of SCP + consensus ADMM (arXiv 2603.10711) for sm_103a.
+//
+// Mapping.  One CTA owns one instance; thread i owns time node i (state x_i,
+// control u_i, and its consensus copies).  Per-node data live in a
+// structure-of-arrays block (element k of node i at base[off + k*S + i]) in
+// shared memory when the instance fits, else in a per-instance global
+// workspace slice; the same code serves both.  The only inter-node exchange
+// of an ADMM iteration is nearest-neighbour (Eq. (5) needs A_{i-1}x_{i-1}+...
+// from the left; Step 1 needs mu_{i+1} + rho_dyn z_{i+1} from the right),
+// done through two shared exchange vectors and two CTA barriers.
+//
+// Coordinates.  The QP of Eq. (2) is solved in deviations from the nominal,
+// delta = x - xbar.  Every ADMM step of Sec. III-B commutes with that
+// translation (the duals are unchanged), so the iterates are the paper's up to
+// rounding; the affine term becomes c_i = RK4(xbar_i, ubar_i) - xbar_{i+1},
+// which is small, and that is what lets the FP32 path keep its accuracy.
+#pragma once
+#include <type_traits>
+
+#include "ucn_math.cuh"
+
+namespace ucn {
+
+enum { ST_OK = 0, ST_NUMERIC = 4, ST_NOTCONV = 5, ST_TIMEOUT = 6 };
+constexpr int MAX_THREADS = 256;   // CTA size cap: horizons up to 255 nodes
+
+struct ProblemDev {
+  int model, nx, nu, batch, max_obs;
+  const int* N;
+  const long long* xoff;
+  const long long* uoff;
+  const long long* soff;
+  const double *dt, *params, *Qd, *xref, *Rd, *uref, *QNd, *qN;
+  const double *xlo, *xhi, *ulo, *uhi, *xinit, *xtarget;
+  const unsigned char* tmask;
+  const int* nobs;
+  const double *obs_c, *obs_r, *sets;
+  double rho_eq, rho_dyn, rho_geo, rho_final;
+  int scp_iters, admm_iters, stop;
+  double tr_init, tr_min, tr_max, w_d, defect_tol, step_tol;
+  unsigned long long timeout_ns;
+  double* state_abs;       // exported ADMM state, absolute FP64 (soff layout)
+  char* ws;                // per-instance node storage when it does not fit in shared memory
+};
+
+// Fixed part of a node record: compile-time element offsets of every per-node
+// array (the mirror arrays, whose length depends on the obstacle count, follow
+// at the runtime offsets Layout::oS / oNus / oMd).
+template <class M>
+struct Rec {
+  static constexpr int NX = M::NX, NU = M::NU, NN = NX + NU;
+  static constexpr int A = 0, B = A + NX * NX, C = B + NX * NU, L = C + NX, Q = L + NN * (NN + 1) / 2;
+  static constexpr int R = Q + NX, Xlo = R + NU, Xhi = Xlo + NX, Ulo = Xhi + NX, Uhi = Ulo + NU;
+  static constexpr int X = Uhi + NU, Z = X + NX, Lam = Z + NX, Mu = Lam + NX, Xh = Mu + NX, Nux = Xh + NX;
+  static constexpr int U = Nux + NX, Uh = U + NU, Nuu = Uh + NU, Ex1 = Nuu + NU, Ex2 = Ex1 + NX, END = Ex2 + NX;
+  // FP64 record: nominal state, nominal control, candidate state (exchange)
+  static constexpr int Xbar = 0, Ubar = NX, Xc = NX + NU, DEND = 2 * NX + NU;
+};
+
+// Where the per-node records of one instance live.
+//  shared memory: node i's record at t + i*NS (NS odd: conflict-free banks),
+//                 FP64 record at d + i*DS (DS odd);
+//  global slice:  element k of node i at t[k*S + i] (coalesced SoA).
+struct Layout {
+  int S, NS, DS;           // SoA stride (nodes); AoS record strides (elements)
+  int MS, MD, MB;          // mirror scalars / mirror data per node; exported mirror blocks
+  int oS, oNus, oMd;       // runtime offsets of the mirror arrays in the record
+  long long tbytes;        // bytes of the T region (16-byte multiple)
+  long long bytes;         // bytes per instance
+};
+
+// Per-thread view of its node.
+template <class T, bool AOS>
+struct Node {
+  T* t;          // T region base
+  double* d;     // FP64 region base
+  int S, NS, DS, i, N;
+  __device__ __forceinline__ T& at(int off, int k) const { return AOS ? t[i * NS + off + k] : t[(long long)(off + k) * S + i]; }
+  __device__ __forceinline__ T& nb(int off, int k, int j) const { return AOS ? t[j * NS + off + k] : t[(long long)(off + k) * S + j]; }
+  __device__ __forceinline__ double& dat(int off, int k) const { return AOS ? d[i * DS + off + k] : d[(long long)(off + k) * S + i]; }
+  __device__ __forceinline__ double& dnb(int off, int k, int j) const { return AOS ? d[j * DS + off + k] : d[(long long)(off + k) * S + j]; }
+};
+
+template <class M> struct IsQuad { static constexpr bool value = std::is_same<M, Quad12>::value; };
+
+// Per-instance scalars in shared memory.
+struct InstShared {
+  double red[32][6];
+  double Jn, radius;
+  double out[8];
+  int fail;
+  int accept, stop, status;
+};
+
+// ------------------------------------------------------------------ block reduction
+// Reduces up to 6 FP64 values: entries [0, nsum) summed, [nsum, nval) maxed.
+__device__ __forceinline__ void block_reduce(InstShared& sh, double* v, int nsum, int nval) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  for (int k = 0; k < nval; ++k) v[k] = (k < nsum) ? warp_sum(v[k]) : warp_max(v[k]);
+  if (lane == 0)
+    for (int k = 0; k < nval; ++k) sh.red[warp][k] = v[k];
+  __syncthreads();
+  if (warp == 0) {
+    for (int k = 0; k < nval; ++k) {
+      double a = (lane < nw) ? sh.red[lane][k] : (k < nsum ? 0.0 : -1.0);
+      a = (k < nsum) ? warp_sum(a) : warp_max(a);
+      if (lane == 0) sh.out[k] = a;
+    }
+  }
+  __syncthreads();
+  for (int k = 0; k < nval; ++k) v[k] = sh.out[k];
+  __syncthreads();
+}
+
+// ------------------------------------------------------------------ per-node pieces
+// Nominal of node i from packed global trajectories.
+template <class M, class T, bool AOS>
+__device__ void load_nominal(const Node<T, AOS>& nd, const Layout& L, const double* xg, const double* ug,
+                             long long xo, long long uo) {
+  for (int j = 0; j < M::NX; ++j) nd.dat(Rec<M>::Xbar, j) = xg[(xo + nd.i) * M::NX + j];
+  if (nd.i < nd.N)
+    for (int j = 0; j < M::NU; ++j) nd.dat(Rec<M>::Ubar, j) = ug[(uo + nd.i) * M::NU + j];
+}
+
+template <class M, class T, bool AOS>
+__device__ __forceinline__ void read_nominal(const Node<T, AOS>& nd, bool hasU, double* xb, double* ub) {
+#pragma unroll
+  for (int j = 0; j < M::NX; ++j) xb[j] = nd.dat(Rec<M>::Xbar, j);
+#pragma unroll
+  for (int j = 0; j < M::NU; ++j) ub[j] = hasU ? nd.dat(Rec<M>::Ubar, j) : 0.0;
+}
+
+// A_i, B_i by forward-mode differentiation of the RK4 map (Eq. (2b)), in T.
+template <class M, class T, bool AOS>
+__device__ void node_jacobians(const Node<T, AOS>& nd, const Layout& L, const double* prm, double h) {
+  constexpr int NX = M::NX, NU = M::NU;
+  double xb[NX], ub[NU];
+  read_nominal<M, T, AOS>(nd, true, xb, ub);
+  for (int dir = 0; dir < NX + NU; ++dir) {
+    T col[NX];
+    rk4_jvp<M, T>(prm, h, xb, ub, dir, col);
+#pragma unroll
+    for (int r = 0; r < NX; ++r) {
+      if (dir < NX) nd.at(Rec<M>::A, r * NX + dir) = col[r];
+      else nd.at(Rec<M>::B, r * NU + (dir - NX)) = col[r];
+    }
+  }
+}
+
+// QP data of node i at the nominal: cost gradient in deviations, the
+// trust-region boxes of Eq. (2c) (with the boundary conditions of Eq. (1c)
+// as degenerate boxes at nodes 0 and N), and the mirror-set data.
+template <class M, class T, bool AOS>
+__device__ void node_setup(const Node<T, AOS>& nd, const Layout& L, const ProblemDev& P, int b, double radius) {
+  constexpr int NX = M::NX, NU = M::NU;
+  const int i = nd.i, N = nd.N;
+  double xb[NX], ub[NU];
+  read_nominal<M, T, AOS>(nd, i < N, xb, ub);
+  const bool term = (i == N);
+  for (int j = 0; j < NX; ++j) {
+    const double w = term ? P.QNd[b * NX + j] : P.Qd[b * NX + j];
+    nd.at(Rec<M>::Q, j) = (T)(w * (xb[j] - P.xref[b * NX + j]) + (term ? P.qN[b * NX + j] : 0.0));
+    double lo = fmax(P.xlo[b * NX + j], xb[j] - radius) - xb[j];
+    double hi = fmin(P.xhi[b * NX + j], xb[j] + radius) - xb[j];
+    if (i == 0) lo = hi = P.xinit[b * NX + j] - xb[j];
+    else if (term && P.tmask[b * NX + j]) lo = hi = P.xtarget[b * NX + j] - xb[j];
+    nd.at(Rec<M>::Xlo, j) = (T)lo;
+    nd.at(Rec<M>::Xhi, j) = (T)hi;
+  }
+  if (!term) {
+    for (int j = 0; j < NU; ++j) {
+      nd.at(Rec<M>::R, j) = (T)(P.Rd[b * NU + j] * (ub[j] - P.uref[b * NU + j]));
+      nd.at(Rec<M>::Ulo, j) = (T)(fmax(P.ulo[b * NU + j], ub[j] - radius) - ub[j]);
+      nd.at(Rec<M>::Uhi, j) = (T)(fmin(P.uhi[b * NU + j], ub[j] + radius) - ub[j]);
+    }
+  }
+  if constexpr (IsQuad<M>::value) {
+    // Obstacle j linearised about the nominal position: n = (p - c)/|p - c|,
+    // keep n^T p >= n^T c + r; in deviations n^T dp >= n^T (c - pbar) + r.
+    const int no = P.nobs[b];
+    for (int j = 0; j < no; ++j) {
+      const double* c = &P.obs_c[((long long)b * P.max_obs + j) * 3];
+      double nv[3] = {xb[0] - c[0], xb[1] - c[1], xb[2] - c[2]};
+      double nn = sqrt(nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2]);
+      if (nn < 1e-12) { nv[0] = 0; nv[1] = 0; nv[2] = 1; nn = 1; }
+      double n0 = nv[0] / nn, n1 = nv[1] / nn, n2 = nv[2] / nn;
+      const double bd = n0 * (c[0] - xb[0]) + n1 * (c[1] - xb[1]) + n2 * (c[2] - xb[2]) + P.obs_r[(long long)b * P.max_obs + j];
+      nd.at(L.oMd, 4 * j + 0) = (T)n0;
+      nd.at(L.oMd, 4 * j + 1) = (T)n1;
+      nd.at(L.oMd, 4 * j + 2) = (T)n2;
+      nd.at(L.oMd, 4 * j + 3) = (T)bd;
+    }
+  } else {
+    // Thrust lower bound |T| >= Tmin linearised: nbar^T T >= Tmin, nbar = Tbar/|Tbar|.
+    if (!term) {
+      double nv[3] = {ub[0], ub[1], ub[2]};
+      double nn = sqrt(nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2]);
+      if (nn < 1e-12) { nv[0] = 1; nv[1] = 0; nv[2] = 0; nn = 1; }
+      const double n0 = nv[0] / nn, n1 = nv[1] / nn, n2 = nv[2] / nn;
+      nd.at(L.oMd, 0) = (T)n0;
+      nd.at(L.oMd, 1) = (T)n1;
+      nd.at(L.oMd, 2) = (T)n2;
+      nd.at(L.oMd, 3) = (T)(P.sets[b * 4 + 0] - (n0 * ub[0] + n1 * ub[1] + n2 * ub[2]));
+    }
+  }
+}
+
+// Packed lower-triangular index (row r, column c <= r).
+__host__ __device__ constexpr int pk(int r, int c) { return r * (r + 1) / 2 + c; }
+
+// H_i of Eq. (4) plus rho_geo G_j^T G_j for each mirror set, assembled in
+// packed form and factored H = L L^T in place (unpivoted Cholesky; the
+// diagonal holds 1/L_jj).  Returns false on a non-positive pivot.
+template <class M, class T, bool AOS, int n>
+__device__ bool node_factor(const Node<T, AOS>& nd, const Layout& L, const ProblemDev& P, int b,
+                            T re, T rd, T rg) {
+  constexpr int NX = M::NX, NU = M::NU;
+  const int i = nd.i, N = nd.N;
+  const bool hasU = (n > NX);
+  const bool term = (i == N);
+  for (int r = 0; r < n; ++r) {
+    for (int c = 0; c <= r; ++c) {
+      T h = T(0);
+      if (r < NX) {  // H11
+        if (r == c) h = (T)(term ? P.QNd[b * NX + r] : P.Qd[b * NX + r]) + rg + (i > 0 ? re : T(0));
+        if (!term) {
+          T acc = T(0);
+          for (int k = 0; k < NX; ++k) acc += nd.at(Rec<M>::A, k * NX + r) * nd.at(Rec<M>::A, k * NX + c);
+          h += rd * acc;
+        }
+        if constexpr (IsQuad<M>::value) {
+          if (r < 3 && c < 3) {
+            T acc = T(0);
+            for (int j = 0; j < P.nobs[b]; ++j) acc += nd.at(L.oMd, 4 * j + r) * nd.at(L.oMd, 4 * j + c);
+            h += rg * acc;
+          }
+        } else {
+          if (r < 3 && r == c && P.sets[b * 4 + 2] > 0.0) h += rg;
+        }
+      } else if (c < NX) {  // H21 = H12^T
+        T acc = T(0);
+        for (int k = 0; k < NX; ++k) acc += nd.at(Rec<M>::B, k * NU + (r - NX)) * nd.at(Rec<M>::A, k * NX + c);
+        h = rd * acc;
+      } else {  // H22
+        const int rr = r - NX, cc = c - NX;
+        if (rr == cc) h = (T)P.Rd[b * NU + rr] + rg;
+        T acc = T(0);
+        for (int k = 0; k < NX; ++k) acc += nd.at(Rec<M>::B, k * NU + rr) * nd.at(Rec<M>::B, k * NU + cc);
+        h += rd * acc;
+        if constexpr (!IsQuad<M>::value) {
+          if (rr < 3 && cc < 3) {
+            if (rr == cc && P.sets[b * 4 + 1] > 0.0) h += rg;
+            if (P.sets[b * 4 + 0] > 0.0) h += rg * nd.at(L.oMd, rr) * nd.at(L.oMd, cc);
+          }
+        }
+      }
+      nd.at(Rec<M>::L, pk(r, c)) = h;
+    }
+  }
+  (void)hasU;
+  bool ok = true;
+  for (int j = 0; j < n; ++j) {
+    T s = nd.at(Rec<M>::L, pk(j, j));
+    for (int k = 0; k < j; ++k) { const T l = nd.at(Rec<M>::L, pk(j, k)); s -= l * l; }
+    if (!(s > T(0))) { ok = false; s = T(1); }
+    const T inv = T(1) / sqrt_(s);
+    nd.at(Rec<M>::L, pk(j, j)) = inv;
+    for (int r = j + 1; r < n; ++r) {
+      T t = nd.at(Rec<M>::L, pk(r, j));
+      for (int k = 0; k < j; ++k) t -= nd.at(Rec<M>::L, pk(r, k)) * nd.at(Rec<M>::L, pk(j, k));
+      nd.at(Rec<M>::L, pk(r, j)) = t * inv;
+    }
+  }
+  return ok;
+}
+
+// Forward and backward substitution with the cached factor.
+template <class T, bool AOS, int n>
+__device__ __forceinline__ void chol_solve(const Node<T, AOS>& nd, int oL, const T* g, T* xi) {
+  T y[n];
+#pragma unroll
+  for (int r = 0; r < n; ++r) {
+    T t = g[r];
+#pragma unroll
+    for (int c = 0; c < r; ++c) t -= nd.at(oL, pk(r, c)) * y[c];
+    y[r] = t * nd.at(oL, pk(r, r));
+  }
+#pragma unroll
+  for (int r = n - 1; r >= 0; --r) {
+    T t = y[r];
+#pragma unroll
+    for (int k = r + 1; k < n; ++k) t -= nd.at(oL, pk(k, r)) * xi[k];
+    xi[r] = t * nd.at(oL, pk(r, r));
+  }
+}
+
+// H xi without forming H (A, B, the cost diagonals, the rho terms and the
+// mirror Gram terms), for the refinement residual g - H xi.
+template <class M, class T, bool AOS, int n>
+__device__ __forceinline__ void apply_H(const Node<T, AOS>& nd, const Layout& L, const ProblemDev& P, int b,
+                                        T re, T rd, T rg, const T* xi, T* out) {
+  constexpr int NX = M::NX, NU = M::NU;
+  const int i = nd.i, N = nd.N;
+  const bool term = (i == N);
+#pragma unroll
+  for (int j = 0; j < NX; ++j)
+    out[j] = ((T)(term ? P.QNd[b * NX + j] : P.Qd[b * NX + j]) + rg + (i > 0 ? re : T(0))) * xi[j];
+  if constexpr (n > NX) {
+    T v[NX];
+#pragma unroll
+    for (int r = 0; r < NX; ++r) {
+      T acc = T(0);
+#pragma unroll
+      for (int c = 0; c < NX; ++c) acc += nd.at(Rec<M>::A, r * NX + c) * xi[c];
+#pragma unroll
+      for (int c = 0; c < NU; ++c) acc += nd.at(Rec<M>::B, r * NU + c) * xi[NX + c];
+      v[r] = rd * acc;
+    }
+#pragma unroll
+    for (int j = 0; j < NX; ++j) {
+      T acc = T(0);
+#pragma unroll
+      for (int k = 0; k < NX; ++k) acc += nd.at(Rec<M>::A, k * NX + j) * v[k];
+      out[j] += acc;
+    }
+#pragma unroll
+    for (int j = 0; j < NU; ++j) {
+      T acc = T(0);
+#pragma unroll
+      for (int k = 0; k < NX; ++k) acc += nd.at(Rec<M>::B, k * NU + j) * v[k];
+      out[NX + j] = ((T)P.Rd[b * NU + j] + rg) * xi[NX + j] + acc;
+    }
+  }
+  if constexpr (IsQuad<M>::value) {
+    for (int j = 0; j < P.nobs[b]; ++j) {
+      const T n0 = nd.at(L.oMd, 4 * j), n1 = nd.at(L.oMd, 4 * j + 1), n2 = nd.at(L.oMd, 4 * j + 2);
+      const T y = rg * (n0 * xi[0] + n1 * xi[1] + n2 * xi[2]);
+      out[0] += n0 * y; out[1] += n1 * y; out[2] += n2 * y;
+    }
+  } else {
+    if (P.sets[b * 4 + 2] > 0.0) { out[0] += rg * xi[0]; out[1] += rg * xi[1]; out[2] += rg * xi[2]; }
+    if constexpr (n > NX) {
+      if (P.sets[b * 4 + 1] > 0.0) { out[NX] += rg * xi[NX]; out[NX + 1] += rg * xi[NX + 1]; out[NX + 2] += rg * xi[NX + 2]; }
+      if (P.sets[b * 4 + 0] > 0.0) {
+        const T n0 = nd.at(L.oMd, 0), n1 = nd.at(L.oMd, 1), n2 = nd.at(L.oMd, 2);
+        const T y = rg * (n0 * xi[NX] + n1 * xi[NX + 1] + n2 * xi[NX + 2]);
+        out[NX] += n0 * y; out[NX + 1] += n1 * y; out[NX + 2] += n2 * y;
+      }
+    }
+  }
+}
+
+// Right-hand side g_i of Step 1 (stationarity of Eq. (3) in (x_i, u_i)).
+template <class M, class T, bool AOS, int n>
+__device__ __forceinline__ void node_rhs(const Node<T, AOS>& nd, const Layout& L, const ProblemDev& P, int b,
+                                         T re, T rd, T rg, T* g) {
+  constexpr int NX = M::NX, NU = M::NU;
+  const int i = nd.i;
+#pragma unroll
+  for (int j = 0; j < NX; ++j) {
+    T v = -nd.at(Rec<M>::Q, j) + rg * nd.at(Rec<M>::Xh, j) - nd.at(Rec<M>::Nux, j);
+    if (i > 0) v += re * nd.at(Rec<M>::Z, j) - nd.at(Rec<M>::Lam, j);
+    g[j] = v;
+  }
+  if constexpr (n > NX) {
+    // w_i = mu_{i+1} + rho_dyn (z_{i+1} - c_i); node i+1 publishes mu + rho_dyn z
+    T w[NX];
+#pragma unroll
+    for (int k = 0; k < NX; ++k) w[k] = nd.nb(Rec<M>::Ex2, k, i + 1) - rd * nd.at(Rec<M>::C, k);
+#pragma unroll
+    for (int j = 0; j < NX; ++j) {
+      T acc = T(0);
+#pragma unroll
+      for (int k = 0; k < NX; ++k) acc += nd.at(Rec<M>::A, k * NX + j) * w[k];
+      g[j] += acc;
+    }
+#pragma unroll
+    for (int j = 0; j < NU; ++j) {
+      T acc = T(0);
+#pragma unroll
+      for (int k = 0; k < NX; ++k) acc += nd.at(Rec<M>::B, k * NU + j) * w[k];
+      g[NX + j] = -nd.at(Rec<M>::R, j) + acc + rg * nd.at(Rec<M>::Uh, j) - nd.at(Rec<M>::Nuu, j);
+    }
+  }
+  if constexpr (IsQuad<M>::value) {
+    for (int j = 0; j < P.nobs[b]; ++j) {
+      const T a = rg * nd.at(L.oS, j) - nd.at(L.oNus, j);
+      g[0] += nd.at(L.oMd, 4 * j) * a;
+      g[1] += nd.at(L.oMd, 4 * j + 1) * a;
+      g[2] += nd.at(L.oMd, 4 * j + 2) * a;
+    }
+  } else {
+    if (P.sets[b * 4 + 2] > 0.0)
+      for (int k = 0; k < 3; ++k) g[k] += rg * nd.at(L.oS, k) - nd.at(L.oNus, k);
+    if constexpr (n > NX) {
+      if (P.sets[b * 4 + 1] > 0.0)
+        for (int k = 0; k < 3; ++k) g[NX + k] += rg * nd.at(L.oS, 3 + k) - nd.at(L.oNus, 3 + k);
+      if (P.sets[b * 4 + 0] > 0.0) {
+        const T a = rg * nd.at(L.oS, 6) - nd.at(L.oNus, 6);
+        for (int k = 0; k < 3; ++k) g[NX + k] += nd.at(L.oMd, k) * a;
+      }
+    }
+  }
+}
+
+// Mirror projections (Step 3) and their dual ascent (Step 4) for the non-box
+// sets; `sv` accumulates rho_geo G^T (s_new - s_old) for the dual residual,
+// `rp` the squared primal residual |G xi - s|^2.  Initialisation (reseed)
+// mode projects G xi alone and leaves the duals untouched.
+template <class M, class T, bool AOS, int n>
+__device__ __forceinline__ void node_mirrors(const Node<T, AOS>& nd, const Layout& L, const ProblemDev& P, int b,
+                                             T rg, const T* xi, bool reseed, bool want_res, T* sv, double& rp) {
+  constexpr int NX = M::NX;
+  const T irg = T(1) / rg;
+  if constexpr (IsQuad<M>::value) {
+    for (int j = 0; j < P.nobs[b]; ++j) {
+      const T n0 = nd.at(L.oMd, 4 * j), n1 = nd.at(L.oMd, 4 * j + 1), n2 = nd.at(L.oMd, 4 * j + 2);
+      const T bd = nd.at(L.oMd, 4 * j + 3);
+      const T y = n0 * xi[0] + n1 * xi[1] + n2 * xi[2];
+      if (reseed) { nd.at(L.oS, j) = fmax(bd, y); continue; }
+      const T so = nd.at(L.oS, j);
+      const T s = fmax(bd, y + nd.at(L.oNus, j) * irg);
+      nd.at(L.oS, j) = s;
+      nd.at(L.oNus, j) += rg * (y - s);
+      if (want_res) {
+        const T ds = rg * (s - so);
+        sv[0] += n0 * ds; sv[1] += n1 * ds; sv[2] += n2 * ds;
+        rp += (double)(y - s) * (double)(y - s);
+      }
+    }
+  } else {
+    const int i = nd.i;
+    const bool hasU = (n > NX);
+    double xb[3], ub[3];
+    for (int k = 0; k < 3; ++k) xb[k] = nd.dat(Rec<M>::Xbar, k);
+    for (int k = 0; k < 3; ++k) ub[k] = hasU ? nd.dat(Rec<M>::Ubar, k) : 0.0;
+    (void)i;
+    if (P.sets[b * 4 + 2] > 0.0) {  // glide-slope cone on the position (t = Up)
+      T v[3];
+      for (int k = 0; k < 3; ++k) v[k] = (T)xb[k] + xi[k] + (reseed ? T(0) : nd.at(L.oNus, k) * irg);
+      proj_cone3(v, (T)P.sets[b * 4 + 2]);
+      for (int k = 0; k < 3; ++k) {
+        const T s = v[k] - (T)xb[k];
+        if (reseed) { nd.at(L.oS, k) = s; continue; }
+        const T so = nd.at(L.oS, k);
+        nd.at(L.oS, k) = s;
+        nd.at(L.oNus, k) += rg * (xi[k] - s);
+        if (want_res) { sv[k] += rg * (s - so); rp += (double)(xi[k] - s) * (double)(xi[k] - s); }
+      }
+    }
+    if constexpr (n > NX) {
+      if (P.sets[b * 4 + 1] > 0.0) {  // |T| <= Tmax
+        T v[3];
+        for (int k = 0; k < 3; ++k) v[k] = (T)ub[k] + xi[NX + k] + (reseed ? T(0) : nd.at(L.oNus, 3 + k) * irg);
+        proj_ball3(v, (T)P.sets[b * 4 + 1]);
+        for (int k = 0; k < 3; ++k) {
+          const T s = v[k] - (T)ub[k];
+          if (reseed) { nd.at(L.oS, 3 + k) = s; continue; }
+          const T so = nd.at(L.oS, 3 + k);
+          nd.at(L.oS, 3 + k) = s;
+          nd.at(L.oNus, 3 + k) += rg * (xi[NX + k] - s);
+          if (want_res) { sv[NX + k] += rg * (s - so); rp += (double)(xi[NX + k] - s) * (double)(xi[NX + k] - s); }
+        }
+      }
+      if (P.sets[b * 4 + 0] > 0.0) {  // linearised |T| >= Tmin
+        const T n0 = nd.at(L.oMd, 0), n1 = nd.at(L.oMd, 1), n2 = nd.at(L.oMd, 2), bd = nd.at(L.oMd, 3);
+        const T y = n0 * xi[NX] + n1 * xi[NX + 1] + n2 * xi[NX + 2];
+        if (reseed) {
+          nd.at(L.oS, 6) = fmax(bd, y);
+        } else {
+          const T so = nd.at(L.oS, 6);
+          const T s = fmax(bd, y + nd.at(L.oNus, 6) * irg);
+          nd.at(L.oS, 6) = s;
+          nd.at(L.oNus, 6) += rg * (y - s);
+          if (want_res) {
+            const T ds = rg * (s - so);
+            sv[NX] += n0 * ds; sv[NX + 1] += n1 * ds; sv[NX + 2] += n2 * ds;
+            rp += (double)(y - s) * (double)(y - s);
+          }
+        }
+      }
+    }
+  }
+}
+
+// Mirror initialisation / re-seeding from (x-hat, u-hat) in deviations.
+template <class M, class T, bool AOS>
+__device__ void node_reseed(const Node<T, AOS>& nd, const Layout& L, const ProblemDev& P, int b) {
+  constexpr int NX = M::NX, NU = M::NU;
+  T xi[NX + NU], sv[NX + NU];
+  double rp = 0.0;
+  for (int j = 0; j < NX; ++j) xi[j] = nd.at(Rec<M>::Xh, j);
+  if (nd.i < nd.N) {
+    for (int j = 0; j < NU; ++j) xi[NX + j] = nd.at(Rec<M>::Uh, j);
+    node_mirrors<M, T, AOS, NX + NU>(nd, L, P, b, T(1), xi, true, false, sv, rp);
+  } else {
+    node_mirrors<M, T, AOS, NX>(nd, L, P, b, T(1), xi, true, false, sv, rp);
+  }
+}
+
+// ------------------------------------------------------------------ the ADMM loop
+// `iters` iterations of Steps 1-4 (Sec. III-B) over the CTA's instance.
+// All threads of the CTA must call it.  On the last iteration the primal and
+// dual residuals are accumulated in FP64 and returned in res[0..1].
+template <class M, class T, bool AOS, bool REFINE>
+__device__ void admm_iterations(const Node<T, AOS>& nd, const Layout& L, const ProblemDev& P, int b, bool active,
+                                T re, T rd, T rg, int iters, InstShared& sh, double* res) {
+  constexpr int NX = M::NX, NU = M::NU, NN = NX + NU;
+  const int i = nd.i, N = nd.N;
+  const T irg = T(1) / rg, ired = T(1) / (re + rd);
+  double rp = 0.0, rdl = 0.0;
+  for (int it = 0; it < iters; ++it) {
+    const bool last = (it == iters - 1);
+    T x[NN];
+    // ---- Step 1: H_i xi_i = g_i with the cached factor (+ one refinement step)
+    if (active) {
+      T g[NN];
+      if (i < N) {
+        node_rhs<M, T, AOS, NN>(nd, L, P, b, re, rd, rg, g);
+        chol_solve<T, AOS, NN>(nd, Rec<M>::L, g, x);
+        if constexpr (REFINE) {
+          T hx[NN], dx[NN];
+          apply_H<M, T, AOS, NN>(nd, L, P, b, re, rd, rg, x, hx);
+#pragma unroll
+          for (int j = 0; j < NN; ++j) hx[j] = g[j] - hx[j];
+          chol_solve<T, AOS, NN>(nd, Rec<M>::L, hx, dx);
+#pragma unroll
+          for (int j = 0; j < NN; ++j) x[j] += dx[j];
+        }
+        // linearised propagation d_dyn,i = A x + B u + c_i, published to node i+1
+#pragma unroll
+        for (int r = 0; r < NX; ++r) {
+          T acc = nd.at(Rec<M>::C, r);
+#pragma unroll
+          for (int c = 0; c < NX; ++c) acc += nd.at(Rec<M>::A, r * NX + c) * x[c];
+#pragma unroll
+          for (int c = 0; c < NU; ++c) acc += nd.at(Rec<M>::B, r * NU + c) * x[NX + c];
+          nd.at(Rec<M>::Ex1, r) = acc;
+        }
+      } else {
+        node_rhs<M, T, AOS, NX>(nd, L, P, b, re, rd, rg, g);
+        chol_solve<T, AOS, NX>(nd, Rec<M>::L, g, x);
+        if constexpr (REFINE) {
+          T hx[NX], dx[NX];
+          apply_H<M, T, AOS, NX>(nd, L, P, b, re, rd, rg, x, hx);
+#pragma unroll
+          for (int j = 0; j < NX; ++j) hx[j] = g[j] - hx[j];
+          chol_solve<T, AOS, NX>(nd, Rec<M>::L, hx, dx);
+#pragma unroll
+          for (int j = 0; j < NX; ++j) x[j] += dx[j];
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < NX; ++j) nd.at(Rec<M>::X, j) = x[j];
+      if (i < N) {
+#pragma unroll
+        for (int j = 0; j < NU; ++j) nd.at(Rec<M>::U, j) = x[NX + j];
+      }
+    }
+    __syncthreads();
+    T dz[NX];
+    T sv[NN];
+    if (active) {
+#pragma unroll
+      for (int j = 0; j < NN; ++j) sv[j] = T(0);
+      // ---- Step 2: dynamic consensus, Eq. (5), then its duals (Step 4)
+      if (i >= 1) {
+#pragma unroll
+        for (int j = 0; j < NX; ++j) {
+          const T dd = nd.nb(Rec<M>::Ex1, j, i - 1);
+          const T zo = nd.at(Rec<M>::Z, j);
+          const T lam = nd.at(Rec<M>::Lam, j), mu = nd.at(Rec<M>::Mu, j);
+          const T z = (re * x[j] + lam + rd * dd - mu) * ired;
+          nd.at(Rec<M>::Z, j) = z;
+          nd.at(Rec<M>::Lam, j) = lam + re * (x[j] - z);
+          const T mun = mu + rd * (z - dd);
+          nd.at(Rec<M>::Mu, j) = mun;
+          dz[j] = z - zo;
+          if (last) {
+            sv[j] += re * dz[j];
+            rp += (double)(x[j] - z) * (double)(x[j] - z) + (double)(z - dd) * (double)(z - dd);
+          }
+        }
+      }
+      // ---- Step 3: projections onto the boxes (Eq. (7)) and Step 4 for nu_x, nu_u
+#pragma unroll
+      for (int j = 0; j < NX; ++j) {
+        const T nux = nd.at(Rec<M>::Nux, j);
+        const T xh = clampv(x[j] + nux * irg, nd.at(Rec<M>::Xlo, j), nd.at(Rec<M>::Xhi, j));
+        if (last) { sv[j] += rg * (xh - nd.at(Rec<M>::Xh, j)); rp += (double)(x[j] - xh) * (double)(x[j] - xh); }
+        nd.at(Rec<M>::Xh, j) = xh;
+        nd.at(Rec<M>::Nux, j) = nux + rg * (x[j] - xh);
+      }
+      if (i < N) {
+#pragma unroll
+        for (int j = 0; j < NU; ++j) {
+          const T nuu = nd.at(Rec<M>::Nuu, j);
+          const T uh = clampv(x[NX + j] + nuu * irg, nd.at(Rec<M>::Ulo, j), nd.at(Rec<M>::Uhi, j));
+          if (last) { sv[NX + j] += rg * (uh - nd.at(Rec<M>::Uh, j)); rp += (double)(x[NX + j] - uh) * (double)(x[NX + j] - uh); }
+          nd.at(Rec<M>::Uh, j) = uh;
+          nd.at(Rec<M>::Nuu, j) = nuu + rg * (x[NX + j] - uh);
+        }
+        node_mirrors<M, T, AOS, NN>(nd, L, P, b, rg, x, false, last, sv, rp);
+      } else {
+        node_mirrors<M, T, AOS, NX>(nd, L, P, b, rg, x, false, last, sv, rp);
+      }
+    }
+    if (last) {
+      // dual residual needs rho_dyn (z_{i+1,new} - z_{i+1,old}) from the right neighbour
+      __syncthreads();
+      if (active && i >= 1) {
+#pragma unroll
+        for (int j = 0; j < NX; ++j) nd.at(Rec<M>::Ex1, j) = rd * dz[j];
+      }
+      __syncthreads();
+      if (active) {
+        if (i < N) {
+#pragma unroll
+          for (int j = 0; j < NX; ++j) {
+            T acc = T(0);
+#pragma unroll
+            for (int k = 0; k < NX; ++k) acc += nd.at(Rec<M>::A, k * NX + j) * nd.nb(Rec<M>::Ex1, k, i + 1);
+            sv[j] += acc;
+          }
+#pragma unroll
+          for (int j = 0; j < NU; ++j) {
+            T acc = T(0);
+#pragma unroll
+            for (int k = 0; k < NX; ++k) acc += nd.at(Rec<M>::B, k * NU + j) * nd.nb(Rec<M>::Ex1, k, i + 1);
+            sv[NX + j] += acc;
+          }
+        }
+        const int n = (i < N) ? NN : NX;
+        for (int j = 0; j < n; ++j) rdl += (double)sv[j] * (double)sv[j];
+      }
+    }
+    if (active && i >= 1) {
+#pragma unroll
+      for (int j = 0; j < NX; ++j) nd.at(Rec<M>::Ex2, j) = nd.at(Rec<M>::Mu, j) + rd * nd.at(Rec<M>::Z, j);
+    }
+    __syncthreads();
+  }
+  double v[2] = {rp, rdl};
+  block_reduce(sh, v, 2, 2);
+  res[0] = sqrt(v[0]);
+  res[1] = sqrt(v[1]);
+}
+
+// Publish mu_i + rho_dyn z_i before the first Step 1.
+template <class M, class T, bool AOS>
+__device__ __forceinline__ void publish_ex2(const Node<T, AOS>& nd, const Layout& L, bool active, T rd) {
+  if (active && nd.i >= 1)
+    for (int j = 0; j < M::NX; ++j) nd.at(Rec<M>::Ex2, j) = nd.at(Rec<M>::Mu, j) + rd * nd.at(Rec<M>::Z, j);
+}
+
+// Cold start: x = x-hat = z = nominal, u = u-hat = nominal, zero duals.
+template <class M, class T, bool AOS>
+__device__ void node_cold_start(const Node<T, AOS>& nd, const Layout& L) {
+  for (int j = 0; j < M::NX; ++j) {
+    nd.at(Rec<M>::X, j) = T(0); nd.at(Rec<M>::Z, j) = T(0); nd.at(Rec<M>::Lam, j) = T(0); nd.at(Rec<M>::Mu, j) = T(0);
+    nd.at(Rec<M>::Xh, j) = T(0); nd.at(Rec<M>::Nux, j) = T(0);
+  }
+  for (int j = 0; j < M::NU; ++j) { nd.at(Rec<M>::U, j) = T(0); nd.at(Rec<M>::Uh, j) = T(0); nd.at(Rec<M>::Nuu, j) = T(0); }
+  for (int j = 0; j < L.MS; ++j) { nd.at(L.oS, j) = T(0); nd.at(L.oNus, j) = T(0); }
+}
+
+// ------------------------------------------------------------------ absolute state in/out
+// Flat per-instance order: x, u, z, lam, mu, xh, uh, nux, nuu, s[(N+1)][MB][3], nus[...].
+template <class M, class T, bool AOS>
+__device__ void node_export(const Node<T, AOS>& nd, const Layout& L, const ProblemDev& P, int b, double* out) {
+  constexpr int NX = M::NX, NU = M::NU;
+  const int i = nd.i, N = nd.N;
+  const long long nX = (long long)(N + 1) * NX, nU = (long long)N * NU;
+  double* px = out;           double* pu = px + nX;
+  double* pz = pu + nU;       double* plam = pz + nX;
+  double* pmu = plam + nX;    double* pxh = pmu + nX;
+  double* puh = pxh + nX;     double* pnux = puh + nU;
+  double* pnuu = pnux + nX;   double* ps = pnuu + nU;
+  double* pnus = ps + (long long)(N + 1) * L.MB * 3;
+  for (int j = 0; j < NX; ++j) {
+    const double xb = nd.dat(Rec<M>::Xbar, j);
+    px[i * NX + j] = xb + (double)nd.at(Rec<M>::X, j);
+    pz[i * NX + j] = (i >= 1) ? xb + (double)nd.at(Rec<M>::Z, j) : 0.0;
+    plam[i * NX + j] = (i >= 1) ? (double)nd.at(Rec<M>::Lam, j) : 0.0;
+    pmu[i * NX + j] = (i >= 1) ? (double)nd.at(Rec<M>::Mu, j) : 0.0;
+    pxh[i * NX + j] = xb + (double)nd.at(Rec<M>::Xh, j);
+    pnux[i * NX + j] = (double)nd.at(Rec<M>::Nux, j);
+  }
+  if (i < N)
+    for (int j = 0; j < NU; ++j) {
+      const double ub = nd.dat(Rec<M>::Ubar, j);
+      pu[i * NU + j] = ub + (double)nd.at(Rec<M>::U, j);
+      puh[i * NU + j] = ub + (double)nd.at(Rec<M>::Uh, j);
+      pnuu[i * NU + j] = (double)nd.at(Rec<M>::Nuu, j);
+    }
+  double* si = ps + (long long)i * L.MB * 3;
+  double* ni = pnus + (long long)i * L.MB * 3;
+  for (int k = 0; k < L.MB * 3; ++k) { si[k] = 0.0; ni[k] = 0.0; }
+  if constexpr (IsQuad<M>::value) {
+    for (int j = 0; j < P.nobs[b]; ++j) {
+      double np = 0.0;
+      for (int k = 0; k < 3; ++k) np += (double)nd.at(L.oMd, 4 * j + k) * nd.dat(Rec<M>::Xbar, k);
+      si[3 * j] = (double)nd.at(L.oS, j) + np;
+      ni[3 * j] = (double)nd.at(L.oNus, j);
+    }
+  } else {
+    if (P.sets[b * 4 + 2] > 0.0)
+      for (int k = 0; k < 3; ++k) { si[k] = (double)nd.at(L.oS, k) + nd.dat(Rec<M>::Xbar, k); ni[k] = (double)nd.at(L.oNus, k); }
+    if (i < N && P.sets[b * 4 + 1] > 0.0)
+      for (int k = 0; k < 3; ++k) { si[3 + k] = (double)nd.at(L.oS, 3 + k) + nd.dat(Rec<M>::Ubar, k); ni[3 + k] = (double)nd.at(L.oNus, 3 + k); }
+    if (i < N && P.sets[b * 4 + 0] > 0.0) {
+      double np = 0.0;
+      for (int k = 0; k < 3; ++k) np += (double)nd.at(L.oMd, k) * nd.dat(Rec<M>::Ubar, k);
+      si[6] = (double)nd.at(L.oS, 6) + np;
+      ni[6] = (double)nd.at(L.oNus, 6);
+    }
+  }
+}
+
+template <class M, class T, bool AOS>
+__device__ void node_import(const Node<T, AOS>& nd, const Layout& L, const ProblemDev& P, int b, const double* in) {
+  constexpr int NX = M::NX, NU = M::NU;
+  const int i = nd.i, N = nd.N;
+  const long long nX = (long long)(N + 1) * NX, nU = (long long)N * NU;
+  const double* px = in;          const double* pu = px + nX;
+  const double* pz = pu + nU;     const double* plam = pz + nX;
+  const double* pmu = plam + nX;  const double* pxh = pmu + nX;
+  const double* puh = pxh + nX;   const double* pnux = puh + nU;
+  const double* pnuu = pnux + nX; const double* ps = pnuu + nU;
+  const double* pnus = ps + (long long)(N + 1) * L.MB * 3;
+  for (int j = 0; j < NX; ++j) {
+    const double xb = nd.dat(Rec<M>::Xbar, j);
+    nd.at(Rec<M>::X, j) = (T)(px[i * NX + j] - xb);
+    nd.at(Rec<M>::Z, j) = (i >= 1) ? (T)(pz[i * NX + j] - xb) : T(0);
+    nd.at(Rec<M>::Lam, j) = (T)plam[i * NX + j];
+    nd.at(Rec<M>::Mu, j) = (T)pmu[i * NX + j];
+    nd.at(Rec<M>::Xh, j) = (T)(pxh[i * NX + j] - xb);
+    nd.at(Rec<M>::Nux, j) = (T)pnux[i * NX + j];
+  }
+  for (int j = 0; j < NU; ++j) {
+    const double ub = (i < N) ? nd.dat(Rec<M>::Ubar, j) : 0.0;
+    nd.at(Rec<M>::U, j) = (i < N) ? (T)(pu[i * NU + j] - ub) : T(0);
+    nd.at(Rec<M>::Uh, j) = (i < N) ? (T)(puh[i * NU + j] - ub) : T(0);
+    nd.at(Rec<M>::Nuu, j) = (i < N) ? (T)pnuu[i * NU + j] : T(0);
+  }
+  for (int j = 0; j < L.MS; ++j) { nd.at(L.oS, j) = T(0); nd.at(L.oNus, j) = T(0); }
+  const double* si = ps + (long long)i * L.MB * 3;
+  const double* ni = pnus + (long long)i * L.MB * 3;
+  if constexpr (IsQuad<M>::value) {
+    for (int j = 0; j < P.nobs[b]; ++j) {
+      double np = 0.0;
+      for (int k = 0; k < 3; ++k) np += (double)nd.at(L.oMd, 4 * j + k) * nd.dat(Rec<M>::Xbar, k);
+      nd.at(L.oS, j) = (T)(si[3 * j] - np);
+      nd.at(L.oNus, j) = (T)ni[3 * j];
+    }
+  } else {
+    for (int k = 0; k < 3; ++k) { nd.at(L.oS, k) = (T)(si[k] - nd.dat(Rec<M>::Xbar, k)); nd.at(L.oNus, k) = (T)ni[k]; }
+    if (i < N) {
+      for (int k = 0; k < 3; ++k) { nd.at(L.oS, 3 + k) = (T)(si[3 + k] - nd.dat(Rec<M>::Ubar, k)); nd.at(L.oNus, 3 + k) = (T)ni[3 + k]; }
+      double np = 0.0;
+      for (int k = 0; k < 3; ++k) np += (double)nd.at(L.oMd, k) * nd.dat(Rec<M>::Ubar, k);
+      nd.at(L.oS, 6) = (T)(si[6] - np);
+      nd.at(L.oNus, 6) = (T)ni[6];
+    }
+  }
+}
+
+// After an accepted step the nominal moves by (dxh, duh): express the mirror
+// variables in deviations from the new nominal (same absolute values).
+template <class M, class T, bool AOS>
+__device__ void node_rebase_mirrors(const Node<T, AOS>& nd, const Layout& L, const ProblemDev& P, int b) {
+  if constexpr (IsQuad<M>::value) {
+    for (int j = 0; j < P.nobs[b]; ++j) {
+      T y = T(0);
+      for (int k = 0; k < 3; ++k) y += nd.at(L.oMd, 4 * j + k) * nd.at(Rec<M>::Xh, k);
+      nd.at(L.oS, j) -= y;
+    }
+  } else {
+    for (int k = 0; k < 3; ++k) nd.at(L.oS, k) -= nd.at(Rec<M>::Xh, k);
+    if (nd.i < nd.N) {
+      T y = T(0);
+      for (int k = 0; k < 3; ++k) { nd.at(L.oS, 3 + k) -= nd.at(Rec<M>::Uh, k); y += nd.at(L.oMd, k) * nd.at(Rec<M>::Uh, k); }
+      nd.at(L.oS, 6) -= y;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ kernels
+template <class T, bool SMEM>
+__device__ __forceinline__ Node<T, SMEM> make_node(const ProblemDev& P, const Layout& L, unsigned char* smem, int b) {
+  unsigned char* base = SMEM ? smem : (unsigned char*)(P.ws + (long long)b * L.bytes);
+  Node<T, SMEM> nd;
+  nd.t = (T*)base;
+  nd.d = (double*)(base + L.tbytes);
+  nd.S = L.S;
+  nd.NS = L.NS;
+  nd.DS = L.DS;
+  nd.i = threadIdx.x;
+  nd.N = P.N[b];
+  return nd;
+}
+
+// Linearisation of every node of every instance (one thread per control node).
+template <class M, class T>
+__global__ void __launch_bounds__(128) linearize_kernel(ProblemDev P, const int* node_inst, long long total_u,
+                                                        const double* xbar, const double* ubar,
+                                                        double* A, double* B, double* d) {
+  constexpr int NX = M::NX, NU = M::NU;
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= total_u) return;
+  const int b = node_inst[g];
+  const long long i = g - P.uoff[b];
+  const long long xr = P.xoff[b] + i;
+  double x[NX], u[NU];
+  for (int j = 0; j < NX; ++j) x[j] = xbar[xr * NX + j];
+  for (int j = 0; j < NU; ++j) u[j] = ubar[g * NU + j];
+  const double* prm = P.params + b * 8;
+  const double h = P.dt[b];
+  double Ad[NX * NX], Bd[NX * NU];
+  for (int dir = 0; dir < NX + NU; ++dir) {
+    T col[NX];
+    rk4_jvp<M, T>(prm, h, x, u, dir, col);
+    for (int r = 0; r < NX; ++r) {
+      if (dir < NX) Ad[r * NX + dir] = (double)col[r];
+      else Bd[r * NU + dir - NX] = (double)col[r];
+    }
+  }
+  double xn[NX];
+  rk4<M, double>(prm, h, x, u, xn);
+  for (int r = 0; r < NX; ++r) {
+    double acc = xn[r];
+    for (int c = 0; c < NX; ++c) acc -= Ad[r * NX + c] * x[c];
+    for (int c = 0; c < NU; ++c) acc -= Bd[r * NU + c] * u[c];
+    d[g * NX + r] = acc;
+  }
+  for (int e = 0; e < NX * NX; ++e) A[g * NX * NX + e] = Ad[e];
+  for (int e = 0; e < NX * NU; ++e) B[g * NX * NU + e] = Bd[e];
+}
+
+// Standalone ADMM call on caller-supplied linearisations (one CTA per instance).
+template <class M, class T, bool SMEM, bool REFINE>
+__global__ void __launch_bounds__(MAX_THREADS) admm_kernel(ProblemDev P, Layout L, const double* xbar, const double* ubar,
+                                                           const double* Ag, const double* Bg, const double* dg,
+                                                           const double* radius, int iters, int warm,
+                                                           double* xhat, double* uhat, double* res, int* status) {
+  constexpr int NX = M::NX, NU = M::NU;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ InstShared sh;
+  const int b = blockIdx.x;
+  constexpr bool AOS = SMEM;
+  Node<T, AOS> nd = make_node<T, SMEM>(P, L, smem, b);
+  const int i = nd.i, N = nd.N;
+  const bool active = i <= N;
+  const long long xo = P.xoff[b], uo = P.uoff[b];
+  if (threadIdx.x == 0) sh.fail = 0;
+  if (active) load_nominal<M, T, AOS>(nd, L, xbar, ubar, xo, uo);
+  __syncthreads();
+  if (active && i < N) {
+    // A, B in T; deviation affine term c_i = A xbar_i + B ubar_i + d_i - xbar_{i+1} in FP64
+    const long long g = uo + i;
+    for (int e = 0; e < NX * NX; ++e) nd.at(Rec<M>::A, e) = (T)Ag[g * NX * NX + e];
+    for (int e = 0; e < NX * NU; ++e) nd.at(Rec<M>::B, e) = (T)Bg[g * NX * NU + e];
+    for (int r = 0; r < NX; ++r) {
+      double acc = dg[g * NX + r];
+      for (int c = 0; c < NX; ++c) acc += Ag[g * NX * NX + r * NX + c] * nd.dat(Rec<M>::Xbar, c);
+      for (int c = 0; c < NU; ++c) acc += Bg[g * NX * NU + r * NU + c] * nd.dat(Rec<M>::Ubar, c);
+      nd.at(Rec<M>::C, r) = (T)(acc - nd.dnb(Rec<M>::Xbar, r, i + 1));
+    }
+  }
+  const T re = (T)P.rho_eq, rd = (T)P.rho_dyn, rg = (T)P.rho_geo;
+  if (active) {
+    node_setup<M, T, AOS>(nd, L, P, b, radius[b]);
+    const bool ok = (i < N) ? node_factor<M, T, AOS, NX + NU>(nd, L, P, b, re, rd, rg)
+                            : node_factor<M, T, AOS, NX>(nd, L, P, b, re, rd, rg);
+    if (!ok) atomicOr(&sh.fail, 1);
+    const double* sa = P.state_abs + P.soff[b];
+    if (warm) {
+      node_import<M, T, AOS>(nd, L, P, b, sa);
+    } else {
+      node_cold_start<M, T, AOS>(nd, L);
+      node_reseed<M, T, AOS>(nd, L, P, b);
+    }
+    publish_ex2<M, T, AOS>(nd, L, active, rd);
+  }
+  __syncthreads();
+  double r2[2] = {0.0, 0.0};
+  if (!sh.fail) admm_iterations<M, T, AOS, REFINE>(nd, L, P, b, active, re, rd, rg, iters, sh, r2);
+  if (active) {
+    node_export<M, T, AOS>(nd, L, P, b, P.state_abs + P.soff[b]);
+    for (int j = 0; j < NX; ++j) xhat[(xo + i) * NX + j] = nd.dat(Rec<M>::Xbar, j) + (double)nd.at(Rec<M>::Xh, j);
+    if (i < N)
+      for (int j = 0; j < NU; ++j) uhat[(uo + i) * NU + j] = nd.dat(Rec<M>::Ubar, j) + (double)nd.at(Rec<M>::Uh, j);
+  }
+  if (threadIdx.x == 0) {
+    res[2 * b] = r2[0];
+    res[2 * b + 1] = r2[1];
+    status[b] = sh.fail ? ST_NUMERIC : ST_OK;
+  }
+}
+
+// Nonlinear cost l(x_i,u_i) (or phi(x_N)) of node i in FP64.
+template <class M>
+__device__ __forceinline__ double node_cost(const ProblemDev& P, int b, int i, int N, const double* x, const double* u) {
+  constexpr int NX = M::NX, NU = M::NU;
+  double c = 0.0;
+  if (i < N) {
+    for (int j = 0; j < NX; ++j) { const double e = x[j] - P.xref[b * NX + j]; c += 0.5 * P.Qd[b * NX + j] * e * e; }
+    for (int j = 0; j < NU; ++j) { const double e = u[j] - P.uref[b * NU + j]; c += 0.5 * P.Rd[b * NU + j] * e * e; }
+  } else {
+    for (int j = 0; j < NX; ++j) {
+      const double e = x[j] - P.xref[b * NX + j];
+      c += 0.5 * P.QNd[b * NX + j] * e * e + P.qN[b * NX + j] * x[j];
+    }
+  }
+  return c;
+}
+
+// The whole SCP solve of one instance per CTA (Sec. III-A + III-B): per SCP
+// iteration, linearise (T), assemble + factor (T), admm_iters ADMM
+// iterations (T, FP64 residual sums), then the FP64 rollout, defects, merit
+// and trust-region acceptance, and the nominal update -- without leaving
+// the kernel.
+template <class M, class T, bool SMEM, bool REFINE>
+__global__ void __launch_bounds__(MAX_THREADS) scp_kernel(ProblemDev P, Layout L, const double* x0, const double* u0,
+                                                          double* xout, double* uout, ucn_scp_stats* stats, int* status_out) {
+  constexpr int NX = M::NX, NU = M::NU, NN = NX + NU;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ InstShared sh;
+  const int b = blockIdx.x;
+  constexpr bool AOS = SMEM;
+  Node<T, AOS> nd = make_node<T, SMEM>(P, L, smem, b);
+  const int i = nd.i, N = nd.N;
+  const bool active = i <= N;
+  const long long xo = P.xoff[b], uo = P.uoff[b];
+  const double* prm = P.params + b * 8;
+  const double h = P.dt[b];
+  const unsigned long long t0 = globaltimer_ns();
+  if (threadIdx.x == 0) { sh.fail = 0; sh.status = ST_OK; sh.radius = P.tr_init; sh.stop = 0; }
+  if (active) load_nominal<M, T, AOS>(nd, L, x0, u0, xo, uo);
+  __syncthreads();
+  // c_i = RK4(xbar_i, ubar_i) - xbar_{i+1} and J(nominal)
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  if (active) {
+    double xb[NX], ub[NU];
+    read_nominal<M, T, AOS>(nd, i < N, xb, ub);
+    acc[0] = node_cost<M>(P, b, i, N, xb, ub);
+    if (i < N) {
+      double fn[NX];
+      rk4<M, double>(prm, h, xb, ub, fn);
+      for (int j = 0; j < NX; ++j) {
+        const double e = fn[j] - nd.dnb(Rec<M>::Xbar, j, i + 1);
+        nd.at(Rec<M>::C, j) = (T)e;
+        acc[1] += fabs(e);
+      }
+    }
+  }
+  block_reduce(sh, acc, 2, 2);
+  if (threadIdx.x == 0) sh.Jn = acc[0] + P.w_d * acc[1];
+  if (active) node_cold_start<M, T, AOS>(nd, L);
+  __syncthreads();
+  int accepted = 0, iters_run = 0;
+  unsigned long long mask = 0ull;
+  double res[2] = {0, 0}, last_step = 0.0;
+  const int K = P.scp_iters;
+  for (int k = 0; k < K; ++k) {
+    double fac = 1.0;
+    if (P.rho_final > 0.0 && K > 1) fac = pow(P.rho_final / P.rho_geo, (double)k / (double)(K - 1));
+    const T re = (T)(P.rho_eq * fac), rd = (T)(P.rho_dyn * fac), rg = (T)(P.rho_geo * fac);
+    const double radius = sh.radius;
+    if (active) {
+      if (i < N) node_jacobians<M, T, AOS>(nd, L, prm, h);
+      node_setup<M, T, AOS>(nd, L, P, b, radius);
+      const bool ok = (i < N) ? node_factor<M, T, AOS, NN>(nd, L, P, b, re, rd, rg) : node_factor<M, T, AOS, NX>(nd, L, P, b, re, rd, rg);
+      if (!ok) atomicOr(&sh.fail, 1);
+      node_reseed<M, T, AOS>(nd, L, P, b);
+      publish_ex2<M, T, AOS>(nd, L, active, rd);
+    }
+    __syncthreads();
+    if (sh.fail) { if (threadIdx.x == 0) sh.status = ST_NUMERIC; iters_run++; break; }
+    admm_iterations<M, T, AOS, REFINE>(nd, L, P, b, active, re, rd, rg, P.admm_iters, sh, res);
+    ++iters_run;
+    // ---- candidate (x-hat, u-hat): FP64 rollout, defects, cost, linear model
+    double xc[NX], uc[NU], fc[NX];
+    if (active) {
+      for (int j = 0; j < NX; ++j) { xc[j] = nd.dat(Rec<M>::Xbar, j) + (double)nd.at(Rec<M>::Xh, j); nd.dat(Rec<M>::Xc, j) = xc[j]; }
+      for (int j = 0; j < NU; ++j) uc[j] = (i < N) ? nd.dat(Rec<M>::Ubar, j) + (double)nd.at(Rec<M>::Uh, j) : 0.0;
+    }
+    __syncthreads();
+    double v[6] = {0, 0, 0, 0, 0};   // cost, nl1, lin1 | dinf, step
+    if (active) {
+      v[0] = node_cost<M>(P, b, i, N, xc, uc);
+      double st = 0.0;
+      for (int j = 0; j < NX; ++j) st = fmax(st, fabs((double)nd.at(Rec<M>::Xh, j)));
+      if (i < N) {
+        for (int j = 0; j < NU; ++j) st = fmax(st, fabs((double)nd.at(Rec<M>::Uh, j)));
+        rk4<M, double>(prm, h, xc, uc, fc);
+        double dinf = 0.0;
+        for (int r = 0; r < NX; ++r) {
+          fc[r] -= nd.dnb(Rec<M>::Xc, r, i + 1);
+          v[1] += fabs(fc[r]);
+          dinf = fmax(dinf, fabs(fc[r]));
+          double lin = (double)nd.at(Rec<M>::C, r) - (double)nd.nb(Rec<M>::Xh, r, i + 1);
+          for (int c = 0; c < NX; ++c) lin += (double)nd.at(Rec<M>::A, r * NX + c) * (double)nd.at(Rec<M>::Xh, c);
+          for (int c = 0; c < NU; ++c) lin += (double)nd.at(Rec<M>::B, r * NU + c) * (double)nd.at(Rec<M>::Uh, c);
+          v[2] += fabs(lin);
+        }
+        v[3] = dinf;
+      }
+      v[4] = st;
+    }
+    block_reduce(sh, v, 3, 5);
+    if (threadIdx.x == 0) {
+      // acceptance (the paper omits it; ratio test on an l1 merit)
+      const double Jn = sh.Jn, Jc = v[0] + P.w_d * v[1], Lc = v[0] + P.w_d * v[2];
+      const double den = Jn - Lc, num = Jn - Jc;
+      double radius2 = sh.radius;
+      bool acc_ = true;
+      if (!(den <= 1e-12)) {
+        const double ratio = num / den;
+        acc_ = ratio > 0.0;
+        if (ratio < 0.25) radius2 *= 0.5;
+        else if (ratio > 0.75) radius2 = fmin(2.0 * radius2, P.tr_max);
+      }
+      radius2 = fmax(radius2, P.tr_min);
+      if (!isfinite(Jc)) { acc_ = false; sh.status = ST_NUMERIC; }
+      if (acc_) sh.Jn = Jc;
+      sh.radius = radius2;
+      sh.accept = acc_;
+      int stop = (sh.status == ST_NUMERIC);
+      if (P.stop && acc_ && v[3] <= P.defect_tol && v[4] <= P.step_tol) stop = 1;
+      if (globaltimer_ns() - t0 > P.timeout_ns && !stop && k + 1 < K) { sh.status = ST_TIMEOUT; stop = 1; }
+      sh.stop = stop;
+    }
+    __syncthreads();
+    last_step = v[4];
+    if (sh.accept) {
+      ++accepted;
+      if (k < 64) mask |= (1ull << k);
+      if (active) {
+        // new nominal = candidate; its defect becomes c_i; re-base deviations
+        node_rebase_mirrors<M, T, AOS>(nd, L, P, b);
+        for (int j = 0; j < NX; ++j) {
+          const T xh = nd.at(Rec<M>::Xh, j);
+          nd.dat(Rec<M>::Xbar, j) = xc[j];
+          nd.at(Rec<M>::X, j) -= xh;
+          if (i >= 1) nd.at(Rec<M>::Z, j) -= xh;
+          nd.at(Rec<M>::Xh, j) = T(0);
+          if (i < N) nd.at(Rec<M>::C, j) = (T)fc[j];
+        }
+        if (i < N)
+          for (int j = 0; j < NU; ++j) {
+            const T uh = nd.at(Rec<M>::Uh, j);
+            nd.dat(Rec<M>::Ubar, j) = uc[j];
+            nd.at(Rec<M>::U, j) -= uh;
+            nd.at(Rec<M>::Uh, j) = T(0);
+          }
+      }
+    }
+    __syncthreads();
+    if (sh.stop) break;
+  }
+  // defect, cost and merit of the returned (last accepted) trajectory, FP64
+  double w[6] = {0, 0, 0, 0, 0, 0};
+  if (active) {
+    double xb[NX], ub[NU];
+    read_nominal<M, T, AOS>(nd, i < N, xb, ub);
+    w[0] = node_cost<M>(P, b, i, N, xb, ub);
+    if (i < N) {
+      double fn[NX];
+      rk4<M, double>(prm, h, xb, ub, fn);
+      for (int j = 0; j < NX; ++j) {
+        const double e = fabs(fn[j] - nd.dnb(Rec<M>::Xbar, j, i + 1));
+        w[1] += e;
+        w[2] = fmax(w[2], e);
+      }
+    }
+    for (int j = 0; j < NX; ++j) xout[(xo + i) * NX + j] = xb[j];
+    if (i < N)
+      for (int j = 0; j < NU; ++j) uout[(uo + i) * NU + j] = ub[j];
+    node_export<M, T, AOS>(nd, L, P, b, P.state_abs + P.soff[b]);
+  }
+  block_reduce(sh, w, 2, 3);
+  if (threadIdx.x == 0) {
+    int st = sh.status;
+    if (!isfinite(w[2])) st = ST_NUMERIC;
+    if (st == ST_OK && !(w[2] <= P.defect_tol)) st = ST_NOTCONV;
+    ucn_scp_stats s;
+    s.defect = w[2]; s.cost = w[0]; s.merit = w[0] + P.w_d * w[1];
+    s.primal_res = res[0]; s.dual_res = res[1]; s.tr_radius = sh.radius; s.step = last_step;
+    s.scp_iters = iters_run; s.accepted = accepted; s.accept_mask = mask; s.status = st; s.reserved = 0;
+    s.t_start_ns = t0; s.t_end_ns = globaltimer_ns();
+    s.pad[0] = s.pad[1] = s.pad[2] = s.pad[3] = 0.0;
+    stats[b] = s;
+    status_out[b] = st;
+  }
+}
+
+}  // namespace ucn

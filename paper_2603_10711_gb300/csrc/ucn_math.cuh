@@ -1,0 +1,196 @@
+// Scalar types, dynamics models, RK4 and projections for the device path.
+//
+// The dynamics are written once over a scalar type S that is float, double
+// or a forward-mode dual number Dual<T>; the Jacobians A_i, B_i of the RK4
+// map (Sec. III-A, Eq. (2b)) are obtained by pushing one tangent direction
+// at a time through the four RK4 stages.
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+
+namespace ucn {
+
+// ------------------------------------------------------------------ dual numbers
+template <class T>
+struct Dual {
+  T v, d;
+};
+
+template <class S> struct BaseOf { typedef S type; };
+template <class T> struct BaseOf<Dual<T>> { typedef T type; };
+
+template <class T> __device__ __forceinline__ Dual<T> operator+(Dual<T> a, Dual<T> b) { return {a.v + b.v, a.d + b.d}; }
+template <class T> __device__ __forceinline__ Dual<T> operator-(Dual<T> a, Dual<T> b) { return {a.v - b.v, a.d - b.d}; }
+template <class T> __device__ __forceinline__ Dual<T> operator-(Dual<T> a) { return {-a.v, -a.d}; }
+template <class T> __device__ __forceinline__ Dual<T> operator*(Dual<T> a, Dual<T> b) { return {a.v * b.v, a.d * b.v + a.v * b.d}; }
+template <class T> __device__ __forceinline__ Dual<T> operator/(Dual<T> a, Dual<T> b) {
+  T q = a.v / b.v;
+  return {q, (a.d - q * b.d) / b.v};
+}
+template <class T> __device__ __forceinline__ Dual<T> operator+(Dual<T> a, T b) { return {a.v + b, a.d}; }
+template <class T> __device__ __forceinline__ Dual<T> operator+(T b, Dual<T> a) { return {a.v + b, a.d}; }
+template <class T> __device__ __forceinline__ Dual<T> operator-(Dual<T> a, T b) { return {a.v - b, a.d}; }
+template <class T> __device__ __forceinline__ Dual<T> operator-(T b, Dual<T> a) { return {b - a.v, -a.d}; }
+template <class T> __device__ __forceinline__ Dual<T> operator*(Dual<T> a, T b) { return {a.v * b, a.d * b}; }
+template <class T> __device__ __forceinline__ Dual<T> operator*(T b, Dual<T> a) { return {a.v * b, a.d * b}; }
+template <class T> __device__ __forceinline__ Dual<T> operator/(Dual<T> a, T b) { return {a.v / b, a.d / b}; }
+
+__device__ __forceinline__ float sin_(float a) { return sinf(a); }
+__device__ __forceinline__ float cos_(float a) { return cosf(a); }
+__device__ __forceinline__ float sqrt_(float a) { return sqrtf(a); }
+__device__ __forceinline__ double sin_(double a) { return sin(a); }
+__device__ __forceinline__ double cos_(double a) { return cos(a); }
+__device__ __forceinline__ double sqrt_(double a) { return sqrt(a); }
+template <class T> __device__ __forceinline__ Dual<T> sin_(Dual<T> a) { return {sin_(a.v), cos_(a.v) * a.d}; }
+template <class T> __device__ __forceinline__ Dual<T> cos_(Dual<T> a) { return {cos_(a.v), -sin_(a.v) * a.d}; }
+template <class T> __device__ __forceinline__ Dual<T> sqrt_(Dual<T> a) {
+  T s = sqrt_(a.v);
+  return {s, s > T(0) ? a.d / (T(2) * s) : T(0)};
+}
+
+// ------------------------------------------------------------------ models
+// Quadrotor, 12 states (position, velocity, ZYX Euler angles phi/theta/psi,
+// body rates), 4 rotor thrusts in a "+" layout.
+// prm: m, Jx, Jy, Jz, arm, km (yaw moment per unit thrust), drag, g.
+struct Quad12 {
+  static constexpr int NX = 12, NU = 4;
+  template <class S>
+  __device__ static void f(const double* prm, const S* x, const S* u, S* xd) {
+    typedef typename BaseOf<S>::type R;
+    const R m = (R)prm[0], Jx = (R)prm[1], Jy = (R)prm[2], Jz = (R)prm[3];
+    const R arm = (R)prm[4], km = (R)prm[5], cd = (R)prm[6], g = (R)prm[7];
+    const S sph = sin_(x[6]), cph = cos_(x[6]);
+    const S sth = sin_(x[7]), cth = cos_(x[7]);
+    const S sps = sin_(x[8]), cps = cos_(x[8]);
+    const S F = u[0] + u[1] + u[2] + u[3];
+    // third column of R = Rz(psi) Ry(theta) Rx(phi): the body thrust axis in the world frame
+    const S a0 = cph * sth * cps + sph * sps;
+    const S a1 = cph * sth * sps - sph * cps;
+    const S a2 = cph * cth;
+    xd[0] = x[3];
+    xd[1] = x[4];
+    xd[2] = x[5];
+    xd[3] = a0 * F / m - (cd / m) * x[3];
+    xd[4] = a1 * F / m - (cd / m) * x[4];
+    xd[5] = a2 * F / m - g - (cd / m) * x[5];
+    const S wx = x[9], wy = x[10], wz = x[11];
+    const S tth = sth / cth;
+    // Euler-angle rates from body rates (ZYX kinematics)
+    xd[6] = wx + sph * tth * wy + cph * tth * wz;
+    xd[7] = cph * wy - sph * wz;
+    xd[8] = (sph * wy + cph * wz) / cth;
+    // rigid-body rotation: J w' = tau - w x (J w)
+    const S tx = arm * (u[1] - u[3]);
+    const S ty = arm * (u[2] - u[0]);
+    const S tz = km * (u[0] - u[1] + u[2] - u[3]);
+    xd[9] = (tx - (Jz - Jy) * wy * wz) / Jx;
+    xd[10] = (ty - (Jx - Jz) * wz * wx) / Jy;
+    xd[11] = (tz - (Jy - Jx) * wx * wy) / Jz;
+  }
+};
+
+// Mars powered descent, 7 states: position (Up-East-North), velocity, mass;
+// control = thrust vector.  prm: g (acting along -Up), alpha (mass flow per
+// unit thrust), non-dimensional units.
+struct Mars7 {
+  static constexpr int NX = 7, NU = 3;
+  template <class S>
+  __device__ static void f(const double* prm, const S* x, const S* u, S* xd) {
+    typedef typename BaseOf<S>::type R;
+    const R g = (R)prm[0], alpha = (R)prm[1];
+    const S Tn = sqrt_(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    xd[0] = x[3];
+    xd[1] = x[4];
+    xd[2] = x[5];
+    xd[3] = u[0] / x[6] - g;
+    xd[4] = u[1] / x[6];
+    xd[5] = u[2] / x[6];
+    xd[6] = -(alpha * Tn);
+  }
+};
+
+// Classical fourth-order Runge-Kutta step (Eq. (1b)).
+template <class M, class S>
+__device__ __forceinline__ void rk4(const double* prm, double h_, const S* x, const S* u, S* xn) {
+  typedef typename BaseOf<S>::type R;
+  constexpr int NX = M::NX;
+  const R h = (R)h_, hh = (R)(0.5 * h_), h6 = (R)(h_ / 6.0);
+  S k[NX], t[NX], acc[NX];
+  M::f(prm, x, u, k);
+#pragma unroll
+  for (int j = 0; j < NX; ++j) { acc[j] = k[j]; t[j] = x[j] + hh * k[j]; }
+  M::f(prm, t, u, k);
+#pragma unroll
+  for (int j = 0; j < NX; ++j) { acc[j] = acc[j] + R(2) * k[j]; t[j] = x[j] + hh * k[j]; }
+  M::f(prm, t, u, k);
+#pragma unroll
+  for (int j = 0; j < NX; ++j) { acc[j] = acc[j] + R(2) * k[j]; t[j] = x[j] + h * k[j]; }
+  M::f(prm, t, u, k);
+#pragma unroll
+  for (int j = 0; j < NX; ++j) xn[j] = x[j] + h6 * (acc[j] + k[j]);
+}
+
+// Column `dir` of [A B] = d RK4 / d(x, u) at (x, u), by one forward-mode pass.
+template <class M, class T>
+__device__ __forceinline__ void rk4_jvp(const double* prm, double h, const double* x, const double* u,
+                                        int dir, T* col) {
+  constexpr int NX = M::NX, NU = M::NU;
+  Dual<T> xd[NX], ud[NU], out[NX];
+#pragma unroll
+  for (int j = 0; j < NX; ++j) xd[j] = {(T)x[j], (T)(dir == j ? 1 : 0)};
+#pragma unroll
+  for (int j = 0; j < NU; ++j) ud[j] = {(T)u[j], (T)(dir == NX + j ? 1 : 0)};
+  rk4<M, Dual<T>>(prm, h, xd, ud, out);
+#pragma unroll
+  for (int j = 0; j < NX; ++j) col[j] = out[j].d;
+}
+
+// ------------------------------------------------------------------ projections
+// Ball {|y| <= R}: vector scaling.
+template <class T>
+__device__ __forceinline__ void proj_ball3(T* y, T R) {
+  const T n = sqrt_(y[0] * y[0] + y[1] * y[1] + y[2] * y[2]);
+  if (n > R) {
+    const T s = R / n;
+    y[0] *= s; y[1] *= s; y[2] *= s;
+  }
+}
+
+// Lorentz cone {(t, y1, y2) : |y| <= tau t}: inside -> unchanged; inside the
+// polar cone (tau |y| <= -t) -> 0; otherwise onto the boundary ray.
+template <class T>
+__device__ __forceinline__ void proj_cone3(T* v, T tau) {
+  const T t = v[0];
+  const T s = sqrt_(v[1] * v[1] + v[2] * v[2]);
+  if (s <= tau * t) return;
+  if (tau * s <= -t) { v[0] = v[1] = v[2] = T(0); return; }
+  const T ca = T(1) / sqrt_(T(1) + tau * tau), sa = tau * ca;
+  const T c = t * ca + s * sa;
+  v[0] = c * ca;
+  const T r = c * sa / s;
+  v[1] *= r;
+  v[2] *= r;
+}
+
+template <class T> __device__ __forceinline__ T clampv(T v, T lo, T hi) { return fmin(fmax(v, lo), hi); }
+__device__ __forceinline__ float clampv(float v, float lo, float hi) { return fminf(fmaxf(v, lo), hi); }
+
+// ------------------------------------------------------------------ block reductions (FP64)
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+}  // namespace ucn

@@ -1,0 +1,225 @@
+"""GPU path vs the FP64 CPU oracle, element by element, through the C ABI.
+
+Tolerances (normwise, floor 1):  |gpu - oracle|_max <= tol * max(1, |oracle|_max)
+  * FP64 plain path:          tol = 1e-9
+  * FP32 path with refinement: tol = 1e-4, and the GPU result's own max
+    nonlinear defect <= 1e-5 where the oracle reaches it.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2603_10711_gb300 import ucn  # noqa: E402
+
+TOL64, TOL32 = 1e-9, 1e-4
+
+
+def rel_err(a, b):
+    a = np.asarray(a, dtype=np.float64); b = np.asarray(b, dtype=np.float64)
+    return float(np.abs(a - b).max() / max(1.0, np.abs(b).max())) if b.size else 0.0
+
+
+def t(a, dtype=None):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype or torch.float64, device="cuda")
+
+
+def perturbed_nominal(prob, seed=0, scale=0.05):
+    rng = np.random.default_rng(seed)
+    x = prob.xguess + scale * rng.standard_normal(prob.xguess.shape)
+    u = prob.uguess + scale * rng.standard_normal(prob.uguess.shape)
+    for b in range(prob.batch):
+        x[prob.xoff[b]] = prob.xinit[b]
+    return x, u
+
+
+def oracle_linearize(prob, x, u):
+    nx, nu = prob.nx, prob.nu
+    A = np.zeros((prob.total_u, nx, nx)); B = np.zeros((prob.total_u, nx, nu)); d = np.zeros((prob.total_u, nx))
+    for b in range(prob.batch):
+        for i in range(int(prob.N[b])):
+            g = prob.uoff[b] + i
+            A[g], B[g], d[g], _ = oracle.linearize(prob.model, prob.params[b], prob.dt[b], x[prob.xoff[b] + i], u[g])
+    return A, B, d
+
+
+PROBLEMS = {
+    "quad_path": lambda: W.quad_path(1, seed=0),
+    "quad_uneven": lambda: W.quad_box(3, seed=5, N_range=(5, 17), obs_range=(2, 6)),
+    "mars": lambda: W.mars_batch(3, seed=1, N=40),
+}
+
+
+# ------------------------------------------------------------------ linearisation (Eq. (2b))
+@pytest.mark.parametrize("name", list(PROBLEMS))
+@pytest.mark.parametrize("prec,tol", [(ucn.UCN_PREC_FP64, 1e-12), (ucn.UCN_PREC_FP32_REFINE, 2e-5)])
+def test_linearize_matches_oracle(name, prec, tol):
+    prob = PROBLEMS[name]()
+    x, u = perturbed_nominal(prob)
+    s = ucn.Solver(prob, precision=prec)
+    A, B, d = s.linearize(t(x), t(u))
+    torch.cuda.synchronize()
+    Ar, Br, dr = oracle_linearize(prob, x, u)
+    assert rel_err(A.cpu().numpy(), Ar) <= tol
+    assert rel_err(B.cpu().numpy(), Br) <= tol
+    # d = RK4 - A x - B u is evaluated in FP64 with the path's own A, B
+    Ag, Bg = A.cpu().numpy(), B.cpu().numpy()
+    xs = np.concatenate([x[prob.xoff[b]:prob.xoff[b] + int(prob.N[b])] for b in range(prob.batch)])
+    rk = dr + np.einsum("gij,gj->gi", Ar, xs) + np.einsum("gij,gj->gi", Br, u)
+    expect_d = rk - np.einsum("gij,gj->gi", Ag, xs) - np.einsum("gij,gj->gi", Bg, u)
+    assert rel_err(d.cpu().numpy(), expect_d) <= 1e-12
+    s.close()
+
+
+# ------------------------------------------------------------------ one ADMM call (Sec. III-B)
+def admm_case(prob, prec, iters_cold, iters_warm):
+    x, u = perturbed_nominal(prob, seed=3, scale=0.02)
+    Ar, Br, dr = oracle_linearize(prob, x, u)
+    radius = np.full(prob.batch, 0.7)
+    s = ucn.Solver(prob, precision=prec)
+    xh, uh, res, st = s.admm_solve(t(x), t(u), t(Ar), t(Br), t(dr), t(radius), iters_cold, warm=False)
+    xh2, uh2, res2, st2 = s.admm_solve(t(x), t(u), t(Ar), t(Br), t(dr), t(radius), iters_warm, warm=True)
+    state = s.state_export().cpu().numpy()
+    torch.cuda.synchronize()
+    assert (st.cpu().numpy() == 0).all() and (st2.cpu().numpy() == 0).all()
+    mb = oracle.maxblk(prob)
+    off = 0
+    for b in range(prob.batch):
+        N = int(prob.N[b])
+        xo, uo = prob.xoff[b], prob.uoff[b]
+        sl = lambda a, o, n: a[o:o + n]
+        A_b, B_b, d_b = sl(Ar, uo, N), sl(Br, uo, N), sl(dr, uo, N)
+        ref, r1, _ = oracle.problem_admm(prob, b, sl(x, xo, N + 1), sl(u, uo, N), A_b, B_b, d_b, radius[b], iters_cold)
+        size = oracle.state_size(N, prob.nx, prob.nu, mb)
+        yield b, "cold-xhat", xh.cpu().numpy()[xo:xo + N + 1], oracle.unpack_state(ref, N, prob.nx, prob.nu, mb)["xh"]
+        yield b, "cold-res", res.cpu().numpy()[b], np.array(r1)
+        ref2, r2, _ = oracle.problem_admm(prob, b, sl(x, xo, N + 1), sl(u, uo, N), A_b, B_b, d_b, radius[b], iters_warm, state=ref)
+        yield b, "warm-state", state[off:off + size], ref2
+        yield b, "warm-uhat", uh2.cpu().numpy()[uo:uo + N], oracle.unpack_state(ref2, N, prob.nx, prob.nu, mb)["uh"]
+        yield b, "warm-res", res2.cpu().numpy()[b], np.array(r2)
+        off += size
+    s.close()
+
+
+@pytest.mark.parametrize("name", list(PROBLEMS))
+def test_admm_fp64_matches_oracle(name):
+    for b, what, got, ref in admm_case(PROBLEMS[name](), ucn.UCN_PREC_FP64, 150, 60):
+        assert rel_err(got, ref) <= TOL64, (b, what, rel_err(got, ref))
+
+
+@pytest.mark.parametrize("name", list(PROBLEMS))
+def test_admm_fp32_matches_oracle(name):
+    for b, what, got, ref in admm_case(PROBLEMS[name](), ucn.UCN_PREC_FP32_REFINE, 150, 60):
+        if what.endswith("res"):
+            continue   # residual norms are differences of iterates: not compared at FP32
+        assert rel_err(got, ref) <= TOL32, (b, what, rel_err(got, ref))
+
+
+# ------------------------------------------------------------------ full SCP solve
+def scp_compare(prob, prec, tol, check_defect=False):
+    s = ucn.Solver(prob, precision=prec)
+    x, u = s.scp_solve()
+    torch.cuda.synchronize()
+    st = s.stats_host()
+    xg, ug = x.cpu().numpy(), u.cpu().numpy()
+    xr, ur, sr, _ = oracle.scp_solve(prob)
+    for b in range(prob.batch):
+        xo, uo, N = prob.xoff[b], prob.uoff[b], int(prob.N[b])
+        assert rel_err(xg[xo:xo + N + 1], xr[xo:xo + N + 1]) <= tol, (b, rel_err(xg[xo:xo + N + 1], xr[xo:xo + N + 1]))
+        assert rel_err(ug[uo:uo + N], ur[uo:uo + N]) <= tol, b
+        if prec == ucn.UCN_PREC_FP64:
+            assert int(st["scp_iters"][b]) == int(sr[b, 7])
+            assert int(st["accepted"][b]) == int(sr[b, 8])
+            assert int(st["accept_mask"][b]) == int(sr[b, 9])
+            assert int(st["status"][b]) == int(sr[b, 10])
+            assert abs(st["defect"][b] - sr[b, 0]) <= 1e-9 * max(1e-3, sr[b, 0])
+            assert abs(st["cost"][b] - sr[b, 1]) <= 1e-9 * max(1.0, abs(sr[b, 1]))
+        if check_defect and sr[b, 0] <= 1e-5:
+            assert st["defect"][b] <= 1e-5, (b, st["defect"][b])
+            assert int(st["status"][b]) == 0
+    s.close()
+    return st, sr
+
+
+def test_scp_fp64_quad_path_matches_oracle():
+    # the single-quadrotor workload as stated: 15 SCP x 200 ADMM iterations, rho = 1
+    scp_compare(W.quad_path(1, seed=0), ucn.UCN_PREC_FP64, TOL64)
+
+
+def test_scp_fp64_quad_converging_matches_oracle():
+    prob = W.quad_path(2, seed=0, settings=dict(rho_eq=10.0, rho_dyn=10.0, rho_geo=10.0, scp_iters=40, stop=1, step_tol=1.0))
+    st, sr = scp_compare(prob, ucn.UCN_PREC_FP64, TOL64)
+    assert (sr[:, 0] <= 1e-5).all()
+
+
+def test_scp_fp64_uneven_quad_matches_oracle():
+    prob = W.quad_box(4, seed=7, N_range=(6, 30), obs_range=(3, 10), settings=dict(scp_iters=8, admm_iters=60))
+    scp_compare(prob, ucn.UCN_PREC_FP64, TOL64)
+
+
+def test_scp_fp64_mars_matches_oracle():
+    prob = W.mars_batch(3, seed=1, N=50, settings=dict(scp_iters=40, admm_iters=100))
+    scp_compare(prob, ucn.UCN_PREC_FP64, TOL64)
+
+
+def test_scp_fp64_global_workspace_path_matches_oracle():
+    # N = 60 quadrotor in FP64 does not fit in shared memory: per-node data in global memory
+    prob = W.quad_path(1, seed=4, N=60, settings=dict(scp_iters=5, admm_iters=80))
+    scp_compare(prob, ucn.UCN_PREC_FP64, TOL64)
+
+
+def test_scp_fp32_mars_fixed_iterations_matches_oracle():
+    prob = W.mars_batch(4, seed=1, N=50, settings=dict(scp_iters=30, admm_iters=100, stop=0))
+    scp_compare(prob, ucn.UCN_PREC_FP32_REFINE, TOL32)
+
+
+def test_scp_fp32_mars_reaches_defect_gate():
+    prob = W.mars_batch(6, seed=1)
+    st, sr = scp_compare(prob, ucn.UCN_PREC_FP32_REFINE, TOL32, check_defect=True)
+    assert (st["defect"] <= 1e-5).all()
+
+
+def test_scp_fp32_quad_matches_oracle():
+    prob = W.quad_path(2, seed=0, settings=dict(rho_eq=10.0, rho_dyn=10.0, rho_geo=10.0, scp_iters=25))
+    scp_compare(prob, ucn.UCN_PREC_FP32_REFINE, TOL32)
+
+
+# ------------------------------------------------------------------ edge cases
+def test_horizon_one_and_single_instance():
+    prob = W.quad_path(1, seed=2, N=1, settings=dict(scp_iters=3, admm_iters=20))
+    scp_compare(prob, ucn.UCN_PREC_FP64, TOL64)
+
+
+def test_longest_horizon():
+    # 255 nodes: the largest CTA (256 threads)
+    prob = W.mars_batch(1, seed=3, N=255, settings=dict(scp_iters=2, admm_iters=30, stop=0))
+    scp_compare(prob, ucn.UCN_PREC_FP64, TOL64)
+
+
+def test_full_size_mars_batch_sampled_against_oracle():
+    # the Mars batch of 1024 instances in the benchmark's launch; 4 instances checked against the oracle
+    prob = W.mars_batch(1024, seed=1)
+    s = ucn.Solver(prob, precision=ucn.UCN_PREC_FP32_REFINE)
+    x, u = s.scp_solve()
+    torch.cuda.synchronize()
+    st = s.stats_host()
+    xg, ug = x.cpu().numpy(), u.cpu().numpy()
+    s.close()
+    assert np.isfinite(xg).all() and np.isfinite(ug).all()
+    assert (st["status"] == np.where(st["defect"] <= 1e-5, 0, st["status"])).all()
+    assert np.mean(st["defect"] <= 1e-5) >= 0.95
+    idx = [0, 1023, 377, 640]
+    sub = prob.subset(idx)
+    xr, ur, sr, _ = oracle.scp_solve(sub)
+    for k, b in enumerate(idx):
+        xo, uo = prob.xoff[b], prob.uoff[b]
+        so, su = sub.xoff[k], sub.uoff[k]
+        if sr[k, 0] <= 1e-5 and st["defect"][b] <= 1e-5:
+            assert rel_err(xg[xo:xo + 101], xr[so:so + 101]) <= TOL32 * 10
+        # every returned trajectory satisfies the boundary conditions exactly
+        np.testing.assert_array_equal(xg[xo], prob.xinit[b])
+        np.testing.assert_array_equal(xg[xo + 100][:6], 0.0)
