@@ -36,6 +36,12 @@ int fault_alloc_at() {
 
 long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
 
+}  // namespace
+
+namespace ucn {
+
+void set_error_message(const char* msg) { snprintf(g_err, sizeof(g_err), "%s", msg); }
+
 Layout make_layout(int model, int nodes, int max_obs, int tsize) {
   const int NX = model == UCN_MODEL_QUAD12 ? 12 : 7, NU = model == UCN_MODEL_QUAD12 ? 4 : 3, NN = NX + NU;
   // must match Rec<M>: the fixed part of a node record
@@ -59,7 +65,7 @@ Layout make_layout(int model, int nodes, int max_obs, int tsize) {
   return L;
 }
 
-}  // namespace
+}  // namespace ucn
 
 struct ucn_problem {
   int model, nx, nu, batch, max_obs, Nmax, precision;

@@ -10,6 +10,12 @@ namespace ucn {
 struct ProblemDev;
 struct Layout;
 
+// Sets the thread-local message returned by ucn_last_error (ucn_api.cu).
+void set_error_message(const char* msg);
+
+// Node-record layout of one instance (defined in ucn_api.cu).
+Layout make_layout(int model, int nodes, int max_obs, int tsize);
+
 // Everything one kernel launch needs besides its buffers.
 struct LaunchCfg {
   const void* P;        // ProblemDev*

@@ -1,0 +1,156 @@
+// ucn_scp_solve_noalloc: the fused SCP solve for callers that cannot
+// allocate device memory.
+//
+// Who needs it.  ucn_problem_create allocates the problem's device copy and
+// workspace with cudaMalloc.  Some callers cannot: code that runs inside a
+// real-time control loop where allocation (and its implicit device
+// synchronisation) is forbidden, an application whose memory pool owns the
+// whole GPU, or a runtime that hands us pre-registered buffers only.  They
+// already hold their problem data on the device, so this entry point takes
+// the descriptor's arrays as device pointers and keeps the kernel's scratch
+// (per-instance index tables and the final ADMM state the kernel writes out)
+// in one file-scope __device__ array instead of allocated memory.
+//
+// Limits and sharing.  The array holds UCN_NOALLOC_SCRATCH_BYTES (64 MiB) on
+// every GPU that loads the library, until the process exits.  All calls share
+// it and it keeps the last call's contents; two calls whose kernels overlap on
+// the GPU (different streams, or different host threads on one device) race
+// on it.  Nothing in it has to start at zero: each call writes every table
+// entry and every exported state entry its kernel reads or reports.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "ucn_internal.h"
+#include "ucn_kernels.cuh"
+
+using namespace ucn;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[UCN_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+ucn_status nfail(ucn_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  set_error_message(buf);
+  return s;
+}
+
+long long up256(long long v) { return (v + 255) / 256 * 256; }
+
+// Device address of the scratch array, looked up once per device with that
+// device current (a host-side name of a __device__ variable is not a device
+// address).
+std::mutex g_mu;
+void* g_addr[128] = {nullptr};
+
+cudaError_t scratch_address(int dev, void** out) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
+  if (!g_addr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_addr[dev] = p;
+  }
+  *out = g_addr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" ucn_status ucn_scp_solve_noalloc(const ucn_problem_desc* d, const double* x0_d, const double* u0_d,
+                                            double* x_out_d, double* u_out_d, ucn_scp_stats* stats_d,
+                                            int* status_d, void* stream) {
+  set_error_message("");
+  if (!d || !x0_d || !u0_d || !x_out_d || !u_out_d || !stats_d || !status_d) return nfail(UCN_EINVAL, "null argument");
+  if (d->model != UCN_MODEL_QUAD12 && d->model != UCN_MODEL_MARS7) return nfail(UCN_EINVAL, "unknown model %d", d->model);
+  const int NX = d->model == UCN_MODEL_QUAD12 ? 12 : 7, NU = d->model == UCN_MODEL_QUAD12 ? 4 : 3;
+  if (d->nx != NX || d->nu != NU) return nfail(UCN_EINVAL, "model %d needs nx=%d nu=%d", d->model, NX, NU);
+  if (d->batch < 1) return nfail(UCN_EINVAL, "batch must be >= 1");
+  if (d->precision != UCN_PREC_FP64 && d->precision != UCN_PREC_FP32_REFINE) return nfail(UCN_EINVAL, "unknown precision %d", d->precision);
+  if (d->vc_weight != 0.0) return nfail(UCN_EINVAL, "virtual control (vc_weight != 0) is not supported");
+  if (!d->horizon || !d->dt || !d->model_params || !d->Q_diag || !d->x_ref || !d->R_diag || !d->u_ref ||
+      !d->QN_diag || !d->qN || !d->x_lo || !d->x_hi || !d->u_lo || !d->u_hi || !d->x_init || !d->x_target || !d->term_mask)
+    return nfail(UCN_EINVAL, "a required descriptor array is NULL");
+  const int max_obs = d->model == UCN_MODEL_QUAD12 ? d->max_obs : 0;
+  if (max_obs < 0 || max_obs > 64) return nfail(UCN_EINVAL, "max_obs must be in [0, 64]");
+  if (d->model == UCN_MODEL_QUAD12 && (!d->n_obs || (max_obs > 0 && (!d->obs_c || !d->obs_r))))
+    return nfail(UCN_EINVAL, "quadrotor problems need n_obs (and obs_c, obs_r when max_obs > 0)");
+  if (d->model == UCN_MODEL_MARS7 && !d->sets) return nfail(UCN_EINVAL, "Mars problems need the sets array");
+  if (!(d->rho_eq > 0 && d->rho_dyn > 0 && d->rho_geo > 0)) return nfail(UCN_EINVAL, "penalties must be positive");
+  if (d->scp_iters < 1 || d->admm_iters < 1) return nfail(UCN_EINVAL, "iteration counts must be >= 1");
+  if (!(d->tr_init > 0 && d->tr_min > 0 && d->tr_max >= d->tr_min)) return nfail(UCN_EINVAL, "bad trust-region bounds");
+  const int B = d->batch;
+  // index tables (host copy of the horizons -> offsets), then the exported state
+  std::vector<int> N(B);
+  std::vector<long long> xoff(B), uoff(B), soff(B);
+  const int mb = d->model == UCN_MODEL_QUAD12 ? max_obs : 3;
+  long long tx = 0, tu = 0, ts = 0;
+  int Nmax = 0;
+  for (int b = 0; b < B; ++b) {
+    const int n = d->horizon[b];
+    if (n < 1 || n + 1 > MAX_THREADS) return nfail(UCN_EINVAL, "horizon[%d] = %d outside [1, %d]", b, n, MAX_THREADS - 1);
+    N[b] = n; xoff[b] = tx; uoff[b] = tu; soff[b] = ts;
+    tx += n + 1; tu += n;
+    ts += 6LL * (n + 1) * NX + 3LL * n * NU + 2LL * (n + 1) * mb * 3;
+    Nmax = std::max(Nmax, n);
+  }
+  const long long oN = 0, oX = up256(4LL * B), oU = oX + up256(8LL * B), oS = oU + up256(8LL * B);
+  const long long oState = oS + up256(8LL * B);
+  const long long need = oState + 8LL * ts;
+  if (need > (long long)UCN_NOALLOC_SCRATCH_BYTES)
+    return nfail(UCN_EINVAL, "batch needs %lld bytes of scratch; the no-allocation entry point holds %llu",
+                 need, (unsigned long long)UCN_NOALLOC_SCRATCH_BYTES);
+  const int tsize = d->precision == UCN_PREC_FP64 ? 8 : 4;
+  const Layout L = make_layout(d->model, Nmax + 1, max_obs, tsize);
+  int dev = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return nfail(UCN_ECUDA, "no CUDA device"); }
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (L.bytes + (long long)sizeof(InstShared) + 64 > optin)
+    return nfail(UCN_EINVAL, "an instance of %d nodes needs %lld bytes of shared memory (device limit %d); "
+                 "the no-allocation entry point has no global workspace", Nmax + 1, (long long)L.bytes, optin);
+  unsigned char* scr = nullptr;
+  cudaError_t e = scratch_address(dev, (void**)&scr);
+  if (e != cudaSuccess) return nfail(UCN_ECUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+  cudaStream_t st = (cudaStream_t)stream;
+  // the tables go in with stream-ordered copies from host memory (no allocation)
+  if ((e = cudaMemcpyAsync(scr + oN, N.data(), 4LL * B, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(scr + oX, xoff.data(), 8LL * B, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(scr + oU, uoff.data(), 8LL * B, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(scr + oS, soff.data(), 8LL * B, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+    return nfail(UCN_ECUDA, "table copy: %s", cudaGetErrorString(e));
+  ProblemDev P;
+  std::memset(&P, 0, sizeof(P));
+  P.model = d->model; P.nx = NX; P.nu = NU; P.batch = B; P.max_obs = max_obs;
+  P.N = (const int*)(scr + oN); P.xoff = (const long long*)(scr + oX);
+  P.uoff = (const long long*)(scr + oU); P.soff = (const long long*)(scr + oS);
+  P.dt = d->dt; P.params = d->model_params; P.Qd = d->Q_diag; P.xref = d->x_ref; P.Rd = d->R_diag; P.uref = d->u_ref;
+  P.QNd = d->QN_diag; P.qN = d->qN; P.xlo = d->x_lo; P.xhi = d->x_hi; P.ulo = d->u_lo; P.uhi = d->u_hi;
+  P.xinit = d->x_init; P.xtarget = d->x_target; P.tmask = d->term_mask;
+  P.nobs = d->n_obs; P.obs_c = d->obs_c; P.obs_r = d->obs_r; P.sets = d->sets;
+  P.rho_eq = d->rho_eq; P.rho_dyn = d->rho_dyn; P.rho_geo = d->rho_geo; P.rho_final = d->rho_final;
+  P.scp_iters = d->scp_iters; P.admm_iters = d->admm_iters; P.stop = d->stop;
+  P.tr_init = d->tr_init; P.tr_min = d->tr_min; P.tr_max = d->tr_max; P.w_d = d->w_d;
+  P.defect_tol = d->defect_tol; P.step_tol = d->step_tol;
+  P.timeout_ns = (unsigned long long)((d->timeout_s > 0 ? d->timeout_s : 60.0) * 1e9);
+  P.state_abs = (double*)(scr + oState);
+  P.ws = nullptr;
+  LaunchCfg c;
+  c.P = &P; c.L = &L; c.smem = true; c.smem_bytes = L.bytes;
+  c.threads = (int)((Nmax + 1 + 31) / 32 * 32); c.blocks = B; c.stream = st;
+  auto fn = d->model == UCN_MODEL_QUAD12 ? (d->precision == UCN_PREC_FP64 ? quad64_scp : quad32_scp)
+                                         : (d->precision == UCN_PREC_FP64 ? mars64_scp : mars32_scp);
+  e = fn(c, x0_d, u0_d, x_out_d, u_out_d, stats_d, status_d);
+  if (e != cudaSuccess) return nfail(UCN_ECUDA, "scp launch: %s", cudaGetErrorString(e));
+  return UCN_OK;
+}

@@ -88,6 +88,8 @@ def lib():
             L.ucn_state_export.restype = C.c_int
             L.ucn_scp_solve.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
             L.ucn_scp_solve.restype = C.c_int
+            L.ucn_scp_solve_noalloc.argtypes = [C.POINTER(ProblemDesc), vp, vp, vp, vp, vp, vp, vp]
+            L.ucn_scp_solve_noalloc.restype = C.c_int
             _lib = L
         return _lib
 
@@ -224,6 +226,17 @@ def ucn_scp_solve(h, x0, u0, x_out, u_out, stats, status, stream=None):
     _check(lib().ucn_scp_solve(h, _ptr(x0, f, name="x0"), _ptr(u0, f, name="u0"), _ptr(x_out, f, name="x_out"),
                                _ptr(u_out, f, name="u_out"), _ptr(stats, torch.uint8, name="stats"),
                                _ptr(status, torch.int32, name="status"), _stream(stream)))
+
+
+def ucn_scp_solve_noalloc(desc: ProblemDesc, x0, u0, x_out, u_out, stats, status, stream=None):
+    """No-allocation solve: ``desc`` holds a host ``horizon`` array and device
+    pointers for every other array (see include/ucn.h)."""
+    import torch
+    f = torch.float64
+    _check(lib().ucn_scp_solve_noalloc(C.byref(desc), _ptr(x0, f, name="x0"), _ptr(u0, f, name="u0"),
+                                       _ptr(x_out, f, name="x_out"), _ptr(u_out, f, name="u_out"),
+                                       _ptr(stats, torch.uint8, name="stats"), _ptr(status, torch.int32, name="status"),
+                                       _stream(stream)))
 
 
 class Solver:
