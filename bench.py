@@ -110,13 +110,41 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def make_problem(args, rank=0):
+    over = {}
+    if args.scp_iters:
+        over = dict(scp_iters=args.scp_iters, stop=0)
+    return W.mars_batch(args.batch, seed=1 + rank, settings=over)
+
+
+def run_kernel_only(args):
+    """Only the FP32 fused kernel on the chosen batch (for profiler captures)."""
+    import torch
+    from paper_2603_10711_gb300 import ucn
+    prob = make_problem(args)
+    solver = ucn.Solver(prob, precision=ucn.UCN_PREC_FP64 if args.fp64 else ucn.UCN_PREC_FP32_REFINE)
+    x0, u0 = solver.tensor(prob.xguess), solver.tensor(prob.uguess)
+    for _ in range(args.warmup):
+        solver.scp_solve(x0, u0)
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(args.steps):
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(); solver.scp_solve(x0, u0); e1.record(); e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    st = solver.stats_host()
+    solver.close()
+    return {"mode": "kernel", "batch": prob.batch, "ms": times, "scp_iters_mean": float(st["scp_iters"].mean()),
+            "pass_rate": float(np.mean(st["defect"] <= 1e-5))}
+
+
 def run_ours(args, rank, world):
     import torch
     from paper_2603_10711_gb300 import ucn
 
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
-    prob = W.mars_batch(args.batch, seed=1 + rank)
+    prob = make_problem(args, rank)
     B = prob.batch
     solver = ucn.Solver(prob, precision=ucn.UCN_PREC_FP32_REFINE, device=dev)
     stream = torch.cuda.current_stream(dev)
@@ -285,13 +313,19 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--cpu-sample", type=int, default=96)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", default="full", choices=["full", "kernel"],
+                    help="kernel: time only the fused kernel (profiler captures)")
+    ap.add_argument("--scp-iters", type=int, default=0, help="fixed SCP iteration count (0: the workload's cap + stop test)")
+    ap.add_argument("--fp64", action="store_true", help="kernel mode: the FP64 plain path")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if world > 1 and args.impl == "ours":
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    if args.impl == "reference":
+    if args.mode == "kernel":
+        out = run_kernel_only(args)
+    elif args.impl == "reference":
         out = run_reference(args, rank, world)
     else:
         out = run_ours(args, rank, world)

@@ -43,15 +43,14 @@ namespace ucn {
 void set_error_message(const char* msg) { snprintf(g_err, sizeof(g_err), "%s", msg); }
 
 Layout make_layout(int model, int nodes, int max_obs, int tsize) {
-  const int NX = model == UCN_MODEL_QUAD12 ? 12 : 7, NU = model == UCN_MODEL_QUAD12 ? 4 : 3, NN = NX + NU;
-  // must match Rec<M>: the fixed part of a node record
-  const int fixed = NX * NX + NX * NU + NX + NN * (NN + 1) / 2 + NX + NU + 2 * NX + 2 * NU + 6 * NX + 3 * NU + 2 * NX;
-  const int dfixed = 2 * NX + NU;
+  const bool quad = model == UCN_MODEL_QUAD12;
+  const int fixed = quad ? Rec<Quad12>::END : Rec<Mars7>::END;     // fixed part of a node record
+  const int dfixed = quad ? Rec<Quad12>::DEND : Rec<Mars7>::DEND;
   Layout L;
   std::memset(&L, 0, sizeof(L));
   const int mo = std::max(max_obs, 1);
   L.MS = model == UCN_MODEL_QUAD12 ? mo : 7;
-  L.MD = model == UCN_MODEL_QUAD12 ? 4 * mo : 4;
+  L.MD = model == UCN_MODEL_QUAD12 ? 4 * mo : 10;   // Mars: nbar, bound, nominal position, nominal thrust
   L.MB = model == UCN_MODEL_QUAD12 ? max_obs : 3;
   L.oS = fixed;
   L.oNus = fixed + L.MS;

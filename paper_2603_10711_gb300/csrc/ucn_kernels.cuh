@@ -49,8 +49,8 @@ struct ProblemDev {
 template <class M>
 struct Rec {
   static constexpr int NX = M::NX, NU = M::NU, NN = NX + NU;
-  static constexpr int A = 0, B = A + NX * NX, C = B + NX * NU, L = C + NX, Q = L + NN * (NN + 1) / 2;
-  static constexpr int R = Q + NX, Xlo = R + NU, Xhi = Xlo + NX, Ulo = Xhi + NX, Uhi = Ulo + NU;
+  static constexpr int A = 0, B = A + NX * NX, C = B + NX * NU, Hi = C + NX;
+  static constexpr int Xlo = Hi + NN * (NN + 1) / 2, Xhi = Xlo + NX, Ulo = Xhi + NX, Uhi = Ulo + NU;
   static constexpr int X = Uhi + NU, Z = X + NX, Lam = Z + NX, Mu = Lam + NX, Xh = Mu + NX, Nux = Xh + NX;
   static constexpr int U = Nux + NX, Uh = U + NU, Nuu = Uh + NU, Ex1 = Nuu + NU, Ex2 = Ex1 + NX, END = Ex2 + NX;
   // FP64 record: nominal state, nominal control, candidate state (exchange)
@@ -82,6 +82,38 @@ struct Node {
 };
 
 template <class M> struct IsQuad { static constexpr bool value = std::is_same<M, Quad12>::value; };
+
+// Per-node constants of one SCP iteration, held in registers across the ADMM
+// loop: the cost gradient (q_i, r_i) in deviations and the diagonal of H_i
+// without its A/B and mirror Gram terms.
+template <class M, class T>
+struct NodeConst {
+  T q[M::NX + M::NU];
+  T hd[M::NX + M::NU];
+};
+
+// Per-instance constants read once per kernel into registers, so that the
+// ADMM loop touches no global memory and no FP64 arithmetic.
+template <class T>
+struct Inst {
+  int nobs;                 // quadrotor: obstacles of this instance
+  bool cone, ball, half;    // Mars: glide-slope cone, thrust ball, thrust lower bound
+  T tau, tmax, ca, sa;      // cone tan(half-angle) and its cos/sin; thrust ball radius
+};
+
+template <class M, class T>
+__device__ __forceinline__ Inst<T> make_inst(const ProblemDev& P, int b) {
+  Inst<T> I;
+  I.nobs = IsQuad<M>::value ? P.nobs[b] : 0;
+  const double tmin = IsQuad<M>::value ? 0.0 : P.sets[b * 4 + 0];
+  const double tmax = IsQuad<M>::value ? 0.0 : P.sets[b * 4 + 1];
+  const double tau = IsQuad<M>::value ? 0.0 : P.sets[b * 4 + 2];
+  I.half = tmin > 0.0; I.ball = tmax > 0.0; I.cone = tau > 0.0;
+  I.tau = (T)tau; I.tmax = (T)tmax;
+  const double ca = 1.0 / sqrt(1.0 + tau * tau);
+  I.ca = (T)ca; I.sa = (T)(tau * ca);
+  return I;
+}
 
 // Per-instance scalars in shared memory.
 struct InstShared {
@@ -151,7 +183,8 @@ __device__ void node_jacobians(const Node<T, AOS>& nd, const Layout& L, const do
 // trust-region boxes of Eq. (2c) (with the boundary conditions of Eq. (1c)
 // as degenerate boxes at nodes 0 and N), and the mirror-set data.
 template <class M, class T, bool AOS>
-__device__ void node_setup(const Node<T, AOS>& nd, const Layout& L, const ProblemDev& P, int b, double radius) {
+__device__ void node_setup(const Node<T, AOS>& nd, const Layout& L, const ProblemDev& P, int b, double radius,
+                           T re, T rg, NodeConst<M, T>& K) {
   constexpr int NX = M::NX, NU = M::NU;
   const int i = nd.i, N = nd.N;
   double xb[NX], ub[NU];
@@ -159,7 +192,8 @@ __device__ void node_setup(const Node<T, AOS>& nd, const Layout& L, const Proble
   const bool term = (i == N);
   for (int j = 0; j < NX; ++j) {
     const double w = term ? P.QNd[b * NX + j] : P.Qd[b * NX + j];
-    nd.at(Rec<M>::Q, j) = (T)(w * (xb[j] - P.xref[b * NX + j]) + (term ? P.qN[b * NX + j] : 0.0));
+    K.q[j] = (T)(w * (xb[j] - P.xref[b * NX + j]) + (term ? P.qN[b * NX + j] : 0.0));
+    K.hd[j] = (T)w + rg + (i > 0 ? re : T(0));
     double lo = fmax(P.xlo[b * NX + j], xb[j] - radius) - xb[j];
     double hi = fmin(P.xhi[b * NX + j], xb[j] + radius) - xb[j];
     if (i == 0) lo = hi = P.xinit[b * NX + j] - xb[j];
@@ -167,9 +201,11 @@ __device__ void node_setup(const Node<T, AOS>& nd, const Layout& L, const Proble
     nd.at(Rec<M>::Xlo, j) = (T)lo;
     nd.at(Rec<M>::Xhi, j) = (T)hi;
   }
+  for (int j = 0; j < NU; ++j) { K.q[NX + j] = T(0); K.hd[NX + j] = T(1); }
   if (!term) {
     for (int j = 0; j < NU; ++j) {
-      nd.at(Rec<M>::R, j) = (T)(P.Rd[b * NU + j] * (ub[j] - P.uref[b * NU + j]));
+      K.q[NX + j] = (T)(P.Rd[b * NU + j] * (ub[j] - P.uref[b * NU + j]));
+      K.hd[NX + j] = (T)P.Rd[b * NU + j] + rg;
       nd.at(Rec<M>::Ulo, j) = (T)(fmax(P.ulo[b * NU + j], ub[j] - radius) - ub[j]);
       nd.at(Rec<M>::Uhi, j) = (T)(fmin(P.uhi[b * NU + j], ub[j] + radius) - ub[j]);
     }
@@ -191,6 +227,9 @@ __device__ void node_setup(const Node<T, AOS>& nd, const Layout& L, const Proble
       nd.at(L.oMd, 4 * j + 3) = (T)bd;
     }
   } else {
+    // nominal position / thrust in T, the offsets of the cone and ball projections
+    for (int k = 0; k < 3; ++k) nd.at(L.oMd, 4 + k) = (T)xb[k];
+    for (int k = 0; k < 3; ++k) nd.at(L.oMd, 7 + k) = (T)ub[k];
     // Thrust lower bound |T| >= Tmin linearised: nbar^T T >= Tmin, nbar = Tbar/|Tbar|.
     if (!term) {
       double nv[3] = {ub[0], ub[1], ub[2]};
@@ -212,8 +251,8 @@ __host__ __device__ constexpr int pk(int r, int c) { return r * (r + 1) / 2 + c;
 // packed form and factored H = L L^T in place (unpivoted Cholesky; the
 // diagonal holds 1/L_jj).  Returns false on a non-positive pivot.
 template <class M, class T, bool AOS, int n>
-__device__ bool node_factor(const Node<T, AOS>& nd, const Layout& L, const ProblemDev& P, int b,
-                            T re, T rd, T rg) {
+__device__ bool node_factor(const Node<T, AOS>& nd, const Layout& L, const Inst<T>& I, const NodeConst<M, T>& K,
+                            T rd, T rg) {
   constexpr int NX = M::NX, NU = M::NU;
   const int i = nd.i, N = nd.N;
   const bool hasU = (n > NX);
@@ -222,7 +261,7 @@ __device__ bool node_factor(const Node<T, AOS>& nd, const Layout& L, const Probl
     for (int c = 0; c <= r; ++c) {
       T h = T(0);
       if (r < NX) {  // H11
-        if (r == c) h = (T)(term ? P.QNd[b * NX + r] : P.Qd[b * NX + r]) + rg + (i > 0 ? re : T(0));
+        if (r == c) h = K.hd[r];
         if (!term) {
           T acc = T(0);
           for (int k = 0; k < NX; ++k) acc += nd.at(Rec<M>::A, k * NX + r) * nd.at(Rec<M>::A, k * NX + c);
@@ -231,11 +270,11 @@ __device__ bool node_factor(const Node<T, AOS>& nd, const Layout& L, const Probl
         if constexpr (IsQuad<M>::value) {
           if (r < 3 && c < 3) {
             T acc = T(0);
-            for (int j = 0; j < P.nobs[b]; ++j) acc += nd.at(L.oMd, 4 * j + r) * nd.at(L.oMd, 4 * j + c);
+            for (int j = 0; j < I.nobs; ++j) acc += nd.at(L.oMd, 4 * j + r) * nd.at(L.oMd, 4 * j + c);
             h += rg * acc;
           }
         } else {
-          if (r < 3 && r == c && P.sets[b * 4 + 2] > 0.0) h += rg;
+          if (r < 3 && r == c && I.cone) h += rg;
         }
       } else if (c < NX) {  // H21 = H12^T
         T acc = T(0);
@@ -243,68 +282,81 @@ __device__ bool node_factor(const Node<T, AOS>& nd, const Layout& L, const Probl
         h = rd * acc;
       } else {  // H22
         const int rr = r - NX, cc = c - NX;
-        if (rr == cc) h = (T)P.Rd[b * NU + rr] + rg;
+        if (rr == cc) h = K.hd[r];
         T acc = T(0);
         for (int k = 0; k < NX; ++k) acc += nd.at(Rec<M>::B, k * NU + rr) * nd.at(Rec<M>::B, k * NU + cc);
         h += rd * acc;
         if constexpr (!IsQuad<M>::value) {
           if (rr < 3 && cc < 3) {
-            if (rr == cc && P.sets[b * 4 + 1] > 0.0) h += rg;
-            if (P.sets[b * 4 + 0] > 0.0) h += rg * nd.at(L.oMd, rr) * nd.at(L.oMd, cc);
+            if (rr == cc && I.ball) h += rg;
+            if (I.half) h += rg * nd.at(L.oMd, rr) * nd.at(L.oMd, cc);
           }
         }
       }
-      nd.at(Rec<M>::L, pk(r, c)) = h;
+      nd.at(Rec<M>::Hi, pk(r, c)) = h;
     }
   }
   (void)hasU;
   bool ok = true;
   for (int j = 0; j < n; ++j) {
-    T s = nd.at(Rec<M>::L, pk(j, j));
-    for (int k = 0; k < j; ++k) { const T l = nd.at(Rec<M>::L, pk(j, k)); s -= l * l; }
+    T s = nd.at(Rec<M>::Hi, pk(j, j));
+    for (int k = 0; k < j; ++k) { const T l = nd.at(Rec<M>::Hi, pk(j, k)); s -= l * l; }
     if (!(s > T(0))) { ok = false; s = T(1); }
     const T inv = T(1) / sqrt_(s);
-    nd.at(Rec<M>::L, pk(j, j)) = inv;
+    nd.at(Rec<M>::Hi, pk(j, j)) = inv;
     for (int r = j + 1; r < n; ++r) {
-      T t = nd.at(Rec<M>::L, pk(r, j));
-      for (int k = 0; k < j; ++k) t -= nd.at(Rec<M>::L, pk(r, k)) * nd.at(Rec<M>::L, pk(j, k));
-      nd.at(Rec<M>::L, pk(r, j)) = t * inv;
+      T t = nd.at(Rec<M>::Hi, pk(r, j));
+      for (int k = 0; k < j; ++k) t -= nd.at(Rec<M>::Hi, pk(r, k)) * nd.at(Rec<M>::Hi, pk(j, k));
+      nd.at(Rec<M>::Hi, pk(r, j)) = t * inv;
     }
+  }
+  // In place: L -> L^-1 (column by column; the diagonal already holds 1/L_jj),
+  // then L^-1 -> H^-1 = L^-T L^-1 (row by row, lower triangle).  The ADMM
+  // loop then solves H xi = g by one symmetric mat-vec: the same solve as the
+  // forward/back substitution, with independent dot products instead of a
+  // chain of n dependent steps.
+  for (int j = 0; j < n; ++j) {
+    T col[n];
+    col[j] = nd.at(Rec<M>::Hi, pk(j, j));
+    for (int r = j + 1; r < n; ++r) {
+      T t = T(0);
+      for (int k = j; k < r; ++k) t += nd.at(Rec<M>::Hi, pk(r, k)) * (k == j ? col[j] : col[k]);
+      col[r] = -t * nd.at(Rec<M>::Hi, pk(r, r));
+    }
+    for (int r = j + 1; r < n; ++r) nd.at(Rec<M>::Hi, pk(r, j)) = col[r];
+  }
+  for (int r = 0; r < n; ++r) {
+    T row[n];
+    for (int c = 0; c <= r; ++c) {
+      T t = T(0);
+      for (int k = r; k < n; ++k) t += nd.at(Rec<M>::Hi, pk(k, r)) * nd.at(Rec<M>::Hi, pk(k, c));
+      row[c] = t;
+    }
+    for (int c = 0; c <= r; ++c) nd.at(Rec<M>::Hi, pk(r, c)) = row[c];
   }
   return ok;
 }
 
-// Forward and backward substitution with the cached factor.
+// xi = H^-1 g with the cached packed inverse (lower triangle of a symmetric matrix).
 template <class T, bool AOS, int n>
-__device__ __forceinline__ void chol_solve(const Node<T, AOS>& nd, int oL, const T* g, T* xi) {
-  T y[n];
+__device__ __forceinline__ void sym_solve(const Node<T, AOS>& nd, int oH, const T* g, T* xi) {
 #pragma unroll
   for (int r = 0; r < n; ++r) {
-    T t = g[r];
+    T t = T(0);
 #pragma unroll
-    for (int c = 0; c < r; ++c) t -= nd.at(oL, pk(r, c)) * y[c];
-    y[r] = t * nd.at(oL, pk(r, r));
-  }
-#pragma unroll
-  for (int r = n - 1; r >= 0; --r) {
-    T t = y[r];
-#pragma unroll
-    for (int k = r + 1; k < n; ++k) t -= nd.at(oL, pk(k, r)) * xi[k];
-    xi[r] = t * nd.at(oL, pk(r, r));
+    for (int c = 0; c < n; ++c) t += nd.at(oH, r >= c ? pk(r, c) : pk(c, r)) * g[c];
+    xi[r] = t;
   }
 }
 
 // H xi without forming H (A, B, the cost diagonals, the rho terms and the
 // mirror Gram terms), for the refinement residual g - H xi.
 template <class M, class T, bool AOS, int n>
-__device__ __forceinline__ void apply_H(const Node<T, AOS>& nd, const Layout& L, const ProblemDev& P, int b,
-                                        T re, T rd, T rg, const T* xi, T* out) {
+__device__ __forceinline__ void apply_H(const Node<T, AOS>& nd, const Layout& L, const Inst<T>& I,
+                                        const NodeConst<M, T>& K, T rd, T rg, const T* xi, T* out) {
   constexpr int NX = M::NX, NU = M::NU;
-  const int i = nd.i, N = nd.N;
-  const bool term = (i == N);
 #pragma unroll
-  for (int j = 0; j < NX; ++j)
-    out[j] = ((T)(term ? P.QNd[b * NX + j] : P.Qd[b * NX + j]) + rg + (i > 0 ? re : T(0))) * xi[j];
+  for (int j = 0; j < NX; ++j) out[j] = K.hd[j] * xi[j];
   if constexpr (n > NX) {
     T v[NX];
 #pragma unroll
@@ -328,20 +380,20 @@ __device__ __forceinline__ void apply_H(const Node<T, AOS>& nd, const Layout& L,
       T acc = T(0);
 #pragma unroll
       for (int k = 0; k < NX; ++k) acc += nd.at(Rec<M>::B, k * NU + j) * v[k];
-      out[NX + j] = ((T)P.Rd[b * NU + j] + rg) * xi[NX + j] + acc;
+      out[NX + j] = K.hd[NX + j] * xi[NX + j] + acc;
     }
   }
   if constexpr (IsQuad<M>::value) {
-    for (int j = 0; j < P.nobs[b]; ++j) {
+    for (int j = 0; j < I.nobs; ++j) {
       const T n0 = nd.at(L.oMd, 4 * j), n1 = nd.at(L.oMd, 4 * j + 1), n2 = nd.at(L.oMd, 4 * j + 2);
       const T y = rg * (n0 * xi[0] + n1 * xi[1] + n2 * xi[2]);
       out[0] += n0 * y; out[1] += n1 * y; out[2] += n2 * y;
     }
   } else {
-    if (P.sets[b * 4 + 2] > 0.0) { out[0] += rg * xi[0]; out[1] += rg * xi[1]; out[2] += rg * xi[2]; }
+    if (I.cone) { out[0] += rg * xi[0]; out[1] += rg * xi[1]; out[2] += rg * xi[2]; }
     if constexpr (n > NX) {
-      if (P.sets[b * 4 + 1] > 0.0) { out[NX] += rg * xi[NX]; out[NX + 1] += rg * xi[NX + 1]; out[NX + 2] += rg * xi[NX + 2]; }
-      if (P.sets[b * 4 + 0] > 0.0) {
+      if (I.ball) { out[NX] += rg * xi[NX]; out[NX + 1] += rg * xi[NX + 1]; out[NX + 2] += rg * xi[NX + 2]; }
+      if (I.half) {
         const T n0 = nd.at(L.oMd, 0), n1 = nd.at(L.oMd, 1), n2 = nd.at(L.oMd, 2);
         const T y = rg * (n0 * xi[NX] + n1 * xi[NX + 1] + n2 * xi[NX + 2]);
         out[NX] += n0 * y; out[NX + 1] += n1 * y; out[NX + 2] += n2 * y;
@@ -352,13 +404,13 @@ __device__ __forceinline__ void apply_H(const Node<T, AOS>& nd, const Layout& L,
 
 // Right-hand side g_i of Step 1 (stationarity of Eq. (3) in (x_i, u_i)).
 template <class M, class T, bool AOS, int n>
-__device__ __forceinline__ void node_rhs(const Node<T, AOS>& nd, const Layout& L, const ProblemDev& P, int b,
-                                         T re, T rd, T rg, T* g) {
+__device__ __forceinline__ void node_rhs(const Node<T, AOS>& nd, const Layout& L, const Inst<T>& I,
+                                         const NodeConst<M, T>& K, T re, T rd, T rg, T* g) {
   constexpr int NX = M::NX, NU = M::NU;
   const int i = nd.i;
 #pragma unroll
   for (int j = 0; j < NX; ++j) {
-    T v = -nd.at(Rec<M>::Q, j) + rg * nd.at(Rec<M>::Xh, j) - nd.at(Rec<M>::Nux, j);
+    T v = -K.q[j] + rg * nd.at(Rec<M>::Xh, j) - nd.at(Rec<M>::Nux, j);
     if (i > 0) v += re * nd.at(Rec<M>::Z, j) - nd.at(Rec<M>::Lam, j);
     g[j] = v;
   }
@@ -379,23 +431,23 @@ __device__ __forceinline__ void node_rhs(const Node<T, AOS>& nd, const Layout& L
       T acc = T(0);
 #pragma unroll
       for (int k = 0; k < NX; ++k) acc += nd.at(Rec<M>::B, k * NU + j) * w[k];
-      g[NX + j] = -nd.at(Rec<M>::R, j) + acc + rg * nd.at(Rec<M>::Uh, j) - nd.at(Rec<M>::Nuu, j);
+      g[NX + j] = -K.q[NX + j] + acc + rg * nd.at(Rec<M>::Uh, j) - nd.at(Rec<M>::Nuu, j);
     }
   }
   if constexpr (IsQuad<M>::value) {
-    for (int j = 0; j < P.nobs[b]; ++j) {
+    for (int j = 0; j < I.nobs; ++j) {
       const T a = rg * nd.at(L.oS, j) - nd.at(L.oNus, j);
       g[0] += nd.at(L.oMd, 4 * j) * a;
       g[1] += nd.at(L.oMd, 4 * j + 1) * a;
       g[2] += nd.at(L.oMd, 4 * j + 2) * a;
     }
   } else {
-    if (P.sets[b * 4 + 2] > 0.0)
+    if (I.cone)
       for (int k = 0; k < 3; ++k) g[k] += rg * nd.at(L.oS, k) - nd.at(L.oNus, k);
     if constexpr (n > NX) {
-      if (P.sets[b * 4 + 1] > 0.0)
+      if (I.ball)
         for (int k = 0; k < 3; ++k) g[NX + k] += rg * nd.at(L.oS, 3 + k) - nd.at(L.oNus, 3 + k);
-      if (P.sets[b * 4 + 0] > 0.0) {
+      if (I.half) {
         const T a = rg * nd.at(L.oS, 6) - nd.at(L.oNus, 6);
         for (int k = 0; k < 3; ++k) g[NX + k] += nd.at(L.oMd, k) * a;
       }
@@ -408,12 +460,12 @@ __device__ __forceinline__ void node_rhs(const Node<T, AOS>& nd, const Layout& L
 // `rp` the squared primal residual |G xi - s|^2.  Initialisation (reseed)
 // mode projects G xi alone and leaves the duals untouched.
 template <class M, class T, bool AOS, int n>
-__device__ __forceinline__ void node_mirrors(const Node<T, AOS>& nd, const Layout& L, const ProblemDev& P, int b,
+__device__ __forceinline__ void node_mirrors(const Node<T, AOS>& nd, const Layout& L, const Inst<T>& I,
                                              T rg, const T* xi, bool reseed, bool want_res, T* sv, double& rp) {
   constexpr int NX = M::NX;
   const T irg = T(1) / rg;
   if constexpr (IsQuad<M>::value) {
-    for (int j = 0; j < P.nobs[b]; ++j) {
+    for (int j = 0; j < I.nobs; ++j) {
       const T n0 = nd.at(L.oMd, 4 * j), n1 = nd.at(L.oMd, 4 * j + 1), n2 = nd.at(L.oMd, 4 * j + 2);
       const T bd = nd.at(L.oMd, 4 * j + 3);
       const T y = n0 * xi[0] + n1 * xi[1] + n2 * xi[2];
@@ -429,18 +481,15 @@ __device__ __forceinline__ void node_mirrors(const Node<T, AOS>& nd, const Layou
       }
     }
   } else {
-    const int i = nd.i;
-    const bool hasU = (n > NX);
-    double xb[3], ub[3];
-    for (int k = 0; k < 3; ++k) xb[k] = nd.dat(Rec<M>::Xbar, k);
-    for (int k = 0; k < 3; ++k) ub[k] = hasU ? nd.dat(Rec<M>::Ubar, k) : 0.0;
-    (void)i;
-    if (P.sets[b * 4 + 2] > 0.0) {  // glide-slope cone on the position (t = Up)
+    T xb[3], ub[3];
+    for (int k = 0; k < 3; ++k) xb[k] = nd.at(L.oMd, 4 + k);
+    for (int k = 0; k < 3; ++k) ub[k] = (n > NX) ? nd.at(L.oMd, 7 + k) : T(0);
+    if (I.cone) {  // glide-slope cone on the position (t = Up)
       T v[3];
-      for (int k = 0; k < 3; ++k) v[k] = (T)xb[k] + xi[k] + (reseed ? T(0) : nd.at(L.oNus, k) * irg);
-      proj_cone3(v, (T)P.sets[b * 4 + 2]);
+      for (int k = 0; k < 3; ++k) v[k] = xb[k] + xi[k] + (reseed ? T(0) : nd.at(L.oNus, k) * irg);
+      proj_cone3c(v, I.tau, I.ca, I.sa);
       for (int k = 0; k < 3; ++k) {
-        const T s = v[k] - (T)xb[k];
+        const T s = v[k] - xb[k];
         if (reseed) { nd.at(L.oS, k) = s; continue; }
         const T so = nd.at(L.oS, k);
         nd.at(L.oS, k) = s;
@@ -449,12 +498,12 @@ __device__ __forceinline__ void node_mirrors(const Node<T, AOS>& nd, const Layou
       }
     }
     if constexpr (n > NX) {
-      if (P.sets[b * 4 + 1] > 0.0) {  // |T| <= Tmax
+      if (I.ball) {  // |T| <= Tmax
         T v[3];
-        for (int k = 0; k < 3; ++k) v[k] = (T)ub[k] + xi[NX + k] + (reseed ? T(0) : nd.at(L.oNus, 3 + k) * irg);
-        proj_ball3(v, (T)P.sets[b * 4 + 1]);
+        for (int k = 0; k < 3; ++k) v[k] = ub[k] + xi[NX + k] + (reseed ? T(0) : nd.at(L.oNus, 3 + k) * irg);
+        proj_ball3(v, I.tmax);
         for (int k = 0; k < 3; ++k) {
-          const T s = v[k] - (T)ub[k];
+          const T s = v[k] - ub[k];
           if (reseed) { nd.at(L.oS, 3 + k) = s; continue; }
           const T so = nd.at(L.oS, 3 + k);
           nd.at(L.oS, 3 + k) = s;
@@ -462,7 +511,7 @@ __device__ __forceinline__ void node_mirrors(const Node<T, AOS>& nd, const Layou
           if (want_res) { sv[NX + k] += rg * (s - so); rp += (double)(xi[NX + k] - s) * (double)(xi[NX + k] - s); }
         }
       }
-      if (P.sets[b * 4 + 0] > 0.0) {  // linearised |T| >= Tmin
+      if (I.half) {  // linearised |T| >= Tmin
         const T n0 = nd.at(L.oMd, 0), n1 = nd.at(L.oMd, 1), n2 = nd.at(L.oMd, 2), bd = nd.at(L.oMd, 3);
         const T y = n0 * xi[NX] + n1 * xi[NX + 1] + n2 * xi[NX + 2];
         if (reseed) {
@@ -485,16 +534,16 @@ __device__ __forceinline__ void node_mirrors(const Node<T, AOS>& nd, const Layou
 
 // Mirror initialisation / re-seeding from (x-hat, u-hat) in deviations.
 template <class M, class T, bool AOS>
-__device__ void node_reseed(const Node<T, AOS>& nd, const Layout& L, const ProblemDev& P, int b) {
+__device__ void node_reseed(const Node<T, AOS>& nd, const Layout& L, const Inst<T>& I) {
   constexpr int NX = M::NX, NU = M::NU;
   T xi[NX + NU], sv[NX + NU];
   double rp = 0.0;
   for (int j = 0; j < NX; ++j) xi[j] = nd.at(Rec<M>::Xh, j);
   if (nd.i < nd.N) {
     for (int j = 0; j < NU; ++j) xi[NX + j] = nd.at(Rec<M>::Uh, j);
-    node_mirrors<M, T, AOS, NX + NU>(nd, L, P, b, T(1), xi, true, false, sv, rp);
+    node_mirrors<M, T, AOS, NX + NU>(nd, L, I, T(1), xi, true, false, sv, rp);
   } else {
-    node_mirrors<M, T, AOS, NX>(nd, L, P, b, T(1), xi, true, false, sv, rp);
+    node_mirrors<M, T, AOS, NX>(nd, L, I, T(1), xi, true, false, sv, rp);
   }
 }
 
@@ -503,8 +552,9 @@ __device__ void node_reseed(const Node<T, AOS>& nd, const Layout& L, const Probl
 // All threads of the CTA must call it.  On the last iteration the primal and
 // dual residuals are accumulated in FP64 and returned in res[0..1].
 template <class M, class T, bool AOS, bool REFINE>
-__device__ void admm_iterations(const Node<T, AOS>& nd, const Layout& L, const ProblemDev& P, int b, bool active,
-                                T re, T rd, T rg, int iters, InstShared& sh, double* res) {
+__device__ void admm_iterations(const Node<T, AOS>& nd, const Layout& L, const Inst<T>& I,
+                                const NodeConst<M, T>& K, bool active, T re, T rd, T rg, int iters,
+                                InstShared& sh, double* res) {
   constexpr int NX = M::NX, NU = M::NU, NN = NX + NU;
   const int i = nd.i, N = nd.N;
   const T irg = T(1) / rg, ired = T(1) / (re + rd);
@@ -516,14 +566,14 @@ __device__ void admm_iterations(const Node<T, AOS>& nd, const Layout& L, const P
     if (active) {
       T g[NN];
       if (i < N) {
-        node_rhs<M, T, AOS, NN>(nd, L, P, b, re, rd, rg, g);
-        chol_solve<T, AOS, NN>(nd, Rec<M>::L, g, x);
+        node_rhs<M, T, AOS, NN>(nd, L, I, K, re, rd, rg, g);
+        sym_solve<T, AOS, NN>(nd, Rec<M>::Hi, g, x);
         if constexpr (REFINE) {
           T hx[NN], dx[NN];
-          apply_H<M, T, AOS, NN>(nd, L, P, b, re, rd, rg, x, hx);
+          apply_H<M, T, AOS, NN>(nd, L, I, K, rd, rg, x, hx);
 #pragma unroll
           for (int j = 0; j < NN; ++j) hx[j] = g[j] - hx[j];
-          chol_solve<T, AOS, NN>(nd, Rec<M>::L, hx, dx);
+          sym_solve<T, AOS, NN>(nd, Rec<M>::Hi, hx, dx);
 #pragma unroll
           for (int j = 0; j < NN; ++j) x[j] += dx[j];
         }
@@ -538,14 +588,14 @@ __device__ void admm_iterations(const Node<T, AOS>& nd, const Layout& L, const P
           nd.at(Rec<M>::Ex1, r) = acc;
         }
       } else {
-        node_rhs<M, T, AOS, NX>(nd, L, P, b, re, rd, rg, g);
-        chol_solve<T, AOS, NX>(nd, Rec<M>::L, g, x);
+        node_rhs<M, T, AOS, NX>(nd, L, I, K, re, rd, rg, g);
+        sym_solve<T, AOS, NX>(nd, Rec<M>::Hi, g, x);
         if constexpr (REFINE) {
           T hx[NX], dx[NX];
-          apply_H<M, T, AOS, NX>(nd, L, P, b, re, rd, rg, x, hx);
+          apply_H<M, T, AOS, NX>(nd, L, I, K, rd, rg, x, hx);
 #pragma unroll
           for (int j = 0; j < NX; ++j) hx[j] = g[j] - hx[j];
-          chol_solve<T, AOS, NX>(nd, Rec<M>::L, hx, dx);
+          sym_solve<T, AOS, NX>(nd, Rec<M>::Hi, hx, dx);
 #pragma unroll
           for (int j = 0; j < NX; ++j) x[j] += dx[j];
         }
@@ -600,9 +650,9 @@ __device__ void admm_iterations(const Node<T, AOS>& nd, const Layout& L, const P
           nd.at(Rec<M>::Uh, j) = uh;
           nd.at(Rec<M>::Nuu, j) = nuu + rg * (x[NX + j] - uh);
         }
-        node_mirrors<M, T, AOS, NN>(nd, L, P, b, rg, x, false, last, sv, rp);
+        node_mirrors<M, T, AOS, NN>(nd, L, I, rg, x, false, last, sv, rp);
       } else {
-        node_mirrors<M, T, AOS, NX>(nd, L, P, b, rg, x, false, last, sv, rp);
+        node_mirrors<M, T, AOS, NX>(nd, L, I, rg, x, false, last, sv, rp);
       }
     }
     if (last) {
@@ -868,23 +918,25 @@ __global__ void __launch_bounds__(MAX_THREADS) admm_kernel(ProblemDev P, Layout 
     }
   }
   const T re = (T)P.rho_eq, rd = (T)P.rho_dyn, rg = (T)P.rho_geo;
+  const Inst<T> I = make_inst<M, T>(P, b);
+  NodeConst<M, T> K;
   if (active) {
-    node_setup<M, T, AOS>(nd, L, P, b, radius[b]);
-    const bool ok = (i < N) ? node_factor<M, T, AOS, NX + NU>(nd, L, P, b, re, rd, rg)
-                            : node_factor<M, T, AOS, NX>(nd, L, P, b, re, rd, rg);
+    node_setup<M, T, AOS>(nd, L, P, b, radius[b], re, rg, K);
+    const bool ok = (i < N) ? node_factor<M, T, AOS, NX + NU>(nd, L, I, K, rd, rg)
+                            : node_factor<M, T, AOS, NX>(nd, L, I, K, rd, rg);
     if (!ok) atomicOr(&sh.fail, 1);
     const double* sa = P.state_abs + P.soff[b];
     if (warm) {
       node_import<M, T, AOS>(nd, L, P, b, sa);
     } else {
       node_cold_start<M, T, AOS>(nd, L);
-      node_reseed<M, T, AOS>(nd, L, P, b);
+      node_reseed<M, T, AOS>(nd, L, I);
     }
     publish_ex2<M, T, AOS>(nd, L, active, rd);
   }
   __syncthreads();
   double r2[2] = {0.0, 0.0};
-  if (!sh.fail) admm_iterations<M, T, AOS, REFINE>(nd, L, P, b, active, re, rd, rg, iters, sh, r2);
+  if (!sh.fail) admm_iterations<M, T, AOS, REFINE>(nd, L, I, K, active, re, rd, rg, iters, sh, r2);
   if (active) {
     node_export<M, T, AOS>(nd, L, P, b, P.state_abs + P.soff[b]);
     for (int j = 0; j < NX; ++j) xhat[(xo + i) * NX + j] = nd.dat(Rec<M>::Xbar, j) + (double)nd.at(Rec<M>::Xh, j);
@@ -935,6 +987,8 @@ __global__ void __launch_bounds__(MAX_THREADS) scp_kernel(ProblemDev P, Layout L
   const double* prm = P.params + b * 8;
   const double h = P.dt[b];
   const unsigned long long t0 = globaltimer_ns();
+  const Inst<T> I = make_inst<M, T>(P, b);
+  NodeConst<M, T> K;
   if (threadIdx.x == 0) { sh.fail = 0; sh.status = ST_OK; sh.radius = P.tr_init; sh.stop = 0; }
   if (active) load_nominal<M, T, AOS>(nd, L, x0, u0, xo, uo);
   __syncthreads();
@@ -961,23 +1015,23 @@ __global__ void __launch_bounds__(MAX_THREADS) scp_kernel(ProblemDev P, Layout L
   int accepted = 0, iters_run = 0;
   unsigned long long mask = 0ull;
   double res[2] = {0, 0}, last_step = 0.0;
-  const int K = P.scp_iters;
-  for (int k = 0; k < K; ++k) {
+  const int Kscp = P.scp_iters;
+  for (int k = 0; k < Kscp; ++k) {
     double fac = 1.0;
-    if (P.rho_final > 0.0 && K > 1) fac = pow(P.rho_final / P.rho_geo, (double)k / (double)(K - 1));
+    if (P.rho_final > 0.0 && Kscp > 1) fac = pow(P.rho_final / P.rho_geo, (double)k / (double)(Kscp - 1));
     const T re = (T)(P.rho_eq * fac), rd = (T)(P.rho_dyn * fac), rg = (T)(P.rho_geo * fac);
     const double radius = sh.radius;
     if (active) {
       if (i < N) node_jacobians<M, T, AOS>(nd, L, prm, h);
-      node_setup<M, T, AOS>(nd, L, P, b, radius);
-      const bool ok = (i < N) ? node_factor<M, T, AOS, NN>(nd, L, P, b, re, rd, rg) : node_factor<M, T, AOS, NX>(nd, L, P, b, re, rd, rg);
+      node_setup<M, T, AOS>(nd, L, P, b, radius, re, rg, K);
+      const bool ok = (i < N) ? node_factor<M, T, AOS, NN>(nd, L, I, K, rd, rg) : node_factor<M, T, AOS, NX>(nd, L, I, K, rd, rg);
       if (!ok) atomicOr(&sh.fail, 1);
-      node_reseed<M, T, AOS>(nd, L, P, b);
+      node_reseed<M, T, AOS>(nd, L, I);
       publish_ex2<M, T, AOS>(nd, L, active, rd);
     }
     __syncthreads();
     if (sh.fail) { if (threadIdx.x == 0) sh.status = ST_NUMERIC; iters_run++; break; }
-    admm_iterations<M, T, AOS, REFINE>(nd, L, P, b, active, re, rd, rg, P.admm_iters, sh, res);
+    admm_iterations<M, T, AOS, REFINE>(nd, L, I, K, active, re, rd, rg, P.admm_iters, sh, res);
     ++iters_run;
     // ---- candidate (x-hat, u-hat): FP64 rollout, defects, cost, linear model
     double xc[NX], uc[NU], fc[NX];
@@ -1028,7 +1082,7 @@ __global__ void __launch_bounds__(MAX_THREADS) scp_kernel(ProblemDev P, Layout L
       sh.accept = acc_;
       int stop = (sh.status == ST_NUMERIC);
       if (P.stop && acc_ && v[3] <= P.defect_tol && v[4] <= P.step_tol) stop = 1;
-      if (globaltimer_ns() - t0 > P.timeout_ns && !stop && k + 1 < K) { sh.status = ST_TIMEOUT; stop = 1; }
+      if (globaltimer_ns() - t0 > P.timeout_ns && !stop && k + 1 < Kscp) { sh.status = ST_TIMEOUT; stop = 1; }
       sh.stop = stop;
     }
     __syncthreads();

@@ -172,6 +172,20 @@ __device__ __forceinline__ void proj_cone3(T* v, T tau) {
   v[2] *= r;
 }
 
+// The same cone projection with cos / sin of the half-angle precomputed.
+template <class T>
+__device__ __forceinline__ void proj_cone3c(T* v, T tau, T ca, T sa) {
+  const T t = v[0];
+  const T s = sqrt_(v[1] * v[1] + v[2] * v[2]);
+  if (s <= tau * t) return;
+  if (tau * s <= -t) { v[0] = v[1] = v[2] = T(0); return; }
+  const T c = t * ca + s * sa;
+  v[0] = c * ca;
+  const T r = c * sa / s;
+  v[1] *= r;
+  v[2] *= r;
+}
+
 template <class T> __device__ __forceinline__ T clampv(T v, T lo, T hi) { return fmin(fmax(v, lo), hi); }
 __device__ __forceinline__ float clampv(float v, float lo, float hi) { return fminf(fmaxf(v, lo), hi); }
 
