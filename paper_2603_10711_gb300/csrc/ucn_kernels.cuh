@@ -99,6 +99,8 @@ struct Inst {
   int nobs;                 // quadrotor: obstacles of this instance
   bool cone, ball, half;    // Mars: glide-slope cone, thrust ball, thrust lower bound
   T tau, tmax, ca, sa;      // cone tan(half-angle) and its cos/sin; thrust ball radius
+  bool run_cost, term_quad; // nonzero running weights / terminal quadratic weights
+  T prm[8];                 // model constants in T (Jacobian passes)
 };
 
 template <class M, class T>
@@ -112,13 +114,18 @@ __device__ __forceinline__ Inst<T> make_inst(const ProblemDev& P, int b) {
   I.tau = (T)tau; I.tmax = (T)tmax;
   const double ca = 1.0 / sqrt(1.0 + tau * tau);
   I.ca = (T)ca; I.sa = (T)(tau * ca);
+  bool rc = false, tq = false;
+  for (int j = 0; j < M::NX; ++j) { rc = rc || P.Qd[b * M::NX + j] != 0.0; tq = tq || P.QNd[b * M::NX + j] != 0.0; }
+  for (int j = 0; j < M::NU; ++j) rc = rc || P.Rd[b * M::NU + j] != 0.0;
+  I.run_cost = rc; I.term_quad = tq;
+  for (int k = 0; k < 8; ++k) I.prm[k] = (T)P.params[b * 8 + k];
   return I;
 }
 
 // Per-instance scalars in shared memory.
 struct InstShared {
   double red[32][6];
-  double Jn, radius;
+  double Jn, radius, fac;
   double out[8];
   int fail;
   int accept, stop, status;
@@ -164,13 +171,18 @@ __device__ __forceinline__ void read_nominal(const Node<T, AOS>& nd, bool hasU, 
 
 // A_i, B_i by forward-mode differentiation of the RK4 map (Eq. (2b)), in T.
 template <class M, class T, bool AOS>
-__device__ void node_jacobians(const Node<T, AOS>& nd, const Layout& L, const double* prm, double h) {
+__device__ void node_jacobians(const Node<T, AOS>& nd, const Layout& L, const T* prm, double h) {
   constexpr int NX = M::NX, NU = M::NU;
   double xb[NX], ub[NU];
   read_nominal<M, T, AOS>(nd, true, xb, ub);
+  T xt[NX], ut[NU];
+#pragma unroll
+  for (int j = 0; j < NX; ++j) xt[j] = (T)xb[j];
+#pragma unroll
+  for (int j = 0; j < NU; ++j) ut[j] = (T)ub[j];
   for (int dir = 0; dir < NX + NU; ++dir) {
     T col[NX];
-    rk4_jvp<M, T>(prm, h, xb, ub, dir, col);
+    rk4_jvp<M, T>(prm, h, xt, ut, dir, col);
 #pragma unroll
     for (int r = 0; r < NX; ++r) {
       if (dir < NX) nd.at(Rec<M>::A, r * NX + dir) = col[r];
@@ -216,11 +228,13 @@ __device__ void node_setup(const Node<T, AOS>& nd, const Layout& L, const Proble
     const int no = P.nobs[b];
     for (int j = 0; j < no; ++j) {
       const double* c = &P.obs_c[((long long)b * P.max_obs + j) * 3];
-      double nv[3] = {xb[0] - c[0], xb[1] - c[1], xb[2] - c[2]};
-      double nn = sqrt(nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2]);
-      if (nn < 1e-12) { nv[0] = 0; nv[1] = 0; nv[2] = 1; nn = 1; }
-      double n0 = nv[0] / nn, n1 = nv[1] / nn, n2 = nv[2] / nn;
-      const double bd = n0 * (c[0] - xb[0]) + n1 * (c[1] - xb[1]) + n2 * (c[2] - xb[2]) + P.obs_r[(long long)b * P.max_obs + j];
+      const T dp[3] = {(T)(xb[0] - c[0]), (T)(xb[1] - c[1]), (T)(xb[2] - c[2])};
+      T nv[3] = {dp[0], dp[1], dp[2]};
+      T nn = sqrt_(nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2]);
+      if (nn < T(1e-12)) { nv[0] = 0; nv[1] = 0; nv[2] = 1; nn = 1; }
+      const T inn = T(1) / nn;
+      const T n0 = nv[0] * inn, n1 = nv[1] * inn, n2 = nv[2] * inn;
+      const T bd = -(n0 * dp[0] + n1 * dp[1] + n2 * dp[2]) + (T)P.obs_r[(long long)b * P.max_obs + j];
       nd.at(L.oMd, 4 * j + 0) = (T)n0;
       nd.at(L.oMd, 4 * j + 1) = (T)n1;
       nd.at(L.oMd, 4 * j + 2) = (T)n2;
@@ -232,14 +246,16 @@ __device__ void node_setup(const Node<T, AOS>& nd, const Layout& L, const Proble
     for (int k = 0; k < 3; ++k) nd.at(L.oMd, 7 + k) = (T)ub[k];
     // Thrust lower bound |T| >= Tmin linearised: nbar^T T >= Tmin, nbar = Tbar/|Tbar|.
     if (!term) {
-      double nv[3] = {ub[0], ub[1], ub[2]};
-      double nn = sqrt(nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2]);
-      if (nn < 1e-12) { nv[0] = 1; nv[1] = 0; nv[2] = 0; nn = 1; }
-      const double n0 = nv[0] / nn, n1 = nv[1] / nn, n2 = nv[2] / nn;
-      nd.at(L.oMd, 0) = (T)n0;
-      nd.at(L.oMd, 1) = (T)n1;
-      nd.at(L.oMd, 2) = (T)n2;
-      nd.at(L.oMd, 3) = (T)(P.sets[b * 4 + 0] - (n0 * ub[0] + n1 * ub[1] + n2 * ub[2]));
+      const T ut[3] = {(T)ub[0], (T)ub[1], (T)ub[2]};
+      T nv[3] = {ut[0], ut[1], ut[2]};
+      T nn = sqrt_(nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2]);
+      if (nn < T(1e-12)) { nv[0] = 1; nv[1] = 0; nv[2] = 0; nn = 1; }
+      const T inn = T(1) / nn;
+      const T n0 = nv[0] * inn, n1 = nv[1] * inn, n2 = nv[2] * inn;
+      nd.at(L.oMd, 0) = n0;
+      nd.at(L.oMd, 1) = n1;
+      nd.at(L.oMd, 2) = n2;
+      nd.at(L.oMd, 3) = (T)P.sets[b * 4 + 0] - (n0 * ut[0] + n1 * ut[1] + n2 * ut[2]);
     }
   }
 }
@@ -469,9 +485,9 @@ __device__ __forceinline__ void node_mirrors(const Node<T, AOS>& nd, const Layou
       const T n0 = nd.at(L.oMd, 4 * j), n1 = nd.at(L.oMd, 4 * j + 1), n2 = nd.at(L.oMd, 4 * j + 2);
       const T bd = nd.at(L.oMd, 4 * j + 3);
       const T y = n0 * xi[0] + n1 * xi[1] + n2 * xi[2];
-      if (reseed) { nd.at(L.oS, j) = fmax(bd, y); continue; }
+      if (reseed) { nd.at(L.oS, j) = maxv(bd, y); continue; }
       const T so = nd.at(L.oS, j);
-      const T s = fmax(bd, y + nd.at(L.oNus, j) * irg);
+      const T s = maxv(bd, y + nd.at(L.oNus, j) * irg);
       nd.at(L.oS, j) = s;
       nd.at(L.oNus, j) += rg * (y - s);
       if (want_res) {
@@ -515,10 +531,10 @@ __device__ __forceinline__ void node_mirrors(const Node<T, AOS>& nd, const Layou
         const T n0 = nd.at(L.oMd, 0), n1 = nd.at(L.oMd, 1), n2 = nd.at(L.oMd, 2), bd = nd.at(L.oMd, 3);
         const T y = n0 * xi[NX] + n1 * xi[NX + 1] + n2 * xi[NX + 2];
         if (reseed) {
-          nd.at(L.oS, 6) = fmax(bd, y);
+          nd.at(L.oS, 6) = maxv(bd, y);
         } else {
           const T so = nd.at(L.oS, 6);
-          const T s = fmax(bd, y + nd.at(L.oNus, 6) * irg);
+          const T s = maxv(bd, y + nd.at(L.oNus, 6) * irg);
           nd.at(L.oS, 6) = s;
           nd.at(L.oNus, 6) += rg * (y - s);
           if (want_res) {
@@ -548,19 +564,18 @@ __device__ void node_reseed(const Node<T, AOS>& nd, const Layout& L, const Inst<
 }
 
 // ------------------------------------------------------------------ the ADMM loop
-// `iters` iterations of Steps 1-4 (Sec. III-B) over the CTA's instance.
-// All threads of the CTA must call it.  On the last iteration the primal and
-// dual residuals are accumulated in FP64 and returned in res[0..1].
-template <class M, class T, bool AOS, bool REFINE>
-__device__ void admm_iterations(const Node<T, AOS>& nd, const Layout& L, const Inst<T>& I,
-                                const NodeConst<M, T>& K, bool active, T re, T rd, T rg, int iters,
-                                InstShared& sh, double* res) {
+// One iteration of Steps 1-4 (Sec. III-B) over the CTA's instance; all
+// threads of the CTA call it.  The LAST instance also accumulates the primal
+// and dual residuals in FP64 (a separate instantiation, so that the hot loop
+// carries no FP64 instruction, not even a predicated-off one).
+template <class M, class T, bool AOS, bool REFINE, bool LAST>
+__device__ __forceinline__ void admm_iteration(const Node<T, AOS>& nd, const Layout& L, const Inst<T>& I,
+                                               const NodeConst<M, T>& K, bool active, T re, T rd, T rg,
+                                               T irg, T ired, double& rp, double& rdl) {
   constexpr int NX = M::NX, NU = M::NU, NN = NX + NU;
   const int i = nd.i, N = nd.N;
-  const T irg = T(1) / rg, ired = T(1) / (re + rd);
-  double rp = 0.0, rdl = 0.0;
-  for (int it = 0; it < iters; ++it) {
-    const bool last = (it == iters - 1);
+  constexpr bool last = LAST;
+  {
     T x[NN];
     // ---- Step 1: H_i xi_i = g_i with the cached factor (+ one refinement step)
     if (active) {
@@ -655,7 +670,7 @@ __device__ void admm_iterations(const Node<T, AOS>& nd, const Layout& L, const I
         node_mirrors<M, T, AOS, NX>(nd, L, I, rg, x, false, last, sv, rp);
       }
     }
-    if (last) {
+    if constexpr (LAST) {
       // dual residual needs rho_dyn (z_{i+1,new} - z_{i+1,old}) from the right neighbour
       __syncthreads();
       if (active && i >= 1) {
@@ -690,6 +705,19 @@ __device__ void admm_iterations(const Node<T, AOS>& nd, const Layout& L, const I
     }
     __syncthreads();
   }
+}
+
+// `iters` iterations of Steps 1-4; the primal and dual residuals of the last
+// one (FP64 sums) are returned in res[0..1].
+template <class M, class T, bool AOS, bool REFINE>
+__device__ void admm_iterations(const Node<T, AOS>& nd, const Layout& L, const Inst<T>& I,
+                                const NodeConst<M, T>& K, bool active, T re, T rd, T rg, int iters,
+                                InstShared& sh, double* res) {
+  const T irg = T(1) / rg, ired = T(1) / (re + rd);
+  double rp = 0.0, rdl = 0.0;
+  for (int it = 0; it + 1 < iters; ++it)
+    admm_iteration<M, T, AOS, REFINE, false>(nd, L, I, K, active, re, rd, rg, irg, ired, rp, rdl);
+  admm_iteration<M, T, AOS, REFINE, true>(nd, L, I, K, active, re, rd, rg, irg, ired, rp, rdl);
   double v[2] = {rp, rdl};
   block_reduce(sh, v, 2, 2);
   res[0] = sqrt(v[0]);
@@ -951,10 +979,16 @@ __global__ void __launch_bounds__(MAX_THREADS) admm_kernel(ProblemDev P, Layout 
 }
 
 // Nonlinear cost l(x_i,u_i) (or phi(x_N)) of node i in FP64.
-template <class M>
-__device__ __forceinline__ double node_cost(const ProblemDev& P, int b, int i, int N, const double* x, const double* u) {
+template <class M, class T>
+__device__ __forceinline__ double node_cost(const ProblemDev& P, const Inst<T>& I, int b, int i, int N,
+                                            const double* x, const double* u) {
   constexpr int NX = M::NX, NU = M::NU;
   double c = 0.0;
+  if (i == N && !I.term_quad) {
+    for (int j = 0; j < NX; ++j) c += P.qN[b * NX + j] * x[j];
+    return c;
+  }
+  if (i < N && !I.run_cost) return 0.0;
   if (i < N) {
     for (int j = 0; j < NX; ++j) { const double e = x[j] - P.xref[b * NX + j]; c += 0.5 * P.Qd[b * NX + j] * e * e; }
     for (int j = 0; j < NU; ++j) { const double e = u[j] - P.uref[b * NU + j]; c += 0.5 * P.Rd[b * NU + j] * e * e; }
@@ -997,7 +1031,7 @@ __global__ void __launch_bounds__(MAX_THREADS) scp_kernel(ProblemDev P, Layout L
   if (active) {
     double xb[NX], ub[NU];
     read_nominal<M, T, AOS>(nd, i < N, xb, ub);
-    acc[0] = node_cost<M>(P, b, i, N, xb, ub);
+    acc[0] = node_cost<M, T>(P, I, b, i, N, xb, ub);
     if (i < N) {
       double fn[NX];
       rk4<M, double>(prm, h, xb, ub, fn);
@@ -1017,12 +1051,17 @@ __global__ void __launch_bounds__(MAX_THREADS) scp_kernel(ProblemDev P, Layout L
   double res[2] = {0, 0}, last_step = 0.0;
   const int Kscp = P.scp_iters;
   for (int k = 0; k < Kscp; ++k) {
-    double fac = 1.0;
-    if (P.rho_final > 0.0 && Kscp > 1) fac = pow(P.rho_final / P.rho_geo, (double)k / (double)(Kscp - 1));
+    if (threadIdx.x == 0) {
+      double f = 1.0;
+      if (P.rho_final > 0.0 && Kscp > 1) f = pow(P.rho_final / P.rho_geo, (double)k / (double)(Kscp - 1));
+      sh.fac = f;
+    }
+    __syncthreads();
+    const double fac = sh.fac;
     const T re = (T)(P.rho_eq * fac), rd = (T)(P.rho_dyn * fac), rg = (T)(P.rho_geo * fac);
     const double radius = sh.radius;
     if (active) {
-      if (i < N) node_jacobians<M, T, AOS>(nd, L, prm, h);
+      if (i < N) node_jacobians<M, T, AOS>(nd, L, I.prm, h);
       node_setup<M, T, AOS>(nd, L, P, b, radius, re, rg, K);
       const bool ok = (i < N) ? node_factor<M, T, AOS, NN>(nd, L, I, K, rd, rg) : node_factor<M, T, AOS, NX>(nd, L, I, K, rd, rg);
       if (!ok) atomicOr(&sh.fail, 1);
@@ -1042,25 +1081,27 @@ __global__ void __launch_bounds__(MAX_THREADS) scp_kernel(ProblemDev P, Layout L
     __syncthreads();
     double v[6] = {0, 0, 0, 0, 0};   // cost, nl1, lin1 | dinf, step
     if (active) {
-      v[0] = node_cost<M>(P, b, i, N, xc, uc);
-      double st = 0.0;
-      for (int j = 0; j < NX; ++j) st = fmax(st, fabs((double)nd.at(Rec<M>::Xh, j)));
+      v[0] = node_cost<M, T>(P, I, b, i, N, xc, uc);
+      T st = T(0);
+      for (int j = 0; j < NX; ++j) st = maxv(st, absv(nd.at(Rec<M>::Xh, j)));
       if (i < N) {
-        for (int j = 0; j < NU; ++j) st = fmax(st, fabs((double)nd.at(Rec<M>::Uh, j)));
+        for (int j = 0; j < NU; ++j) st = maxv(st, absv(nd.at(Rec<M>::Uh, j)));
         rk4<M, double>(prm, h, xc, uc, fc);
         double dinf = 0.0;
+        T lin1 = T(0);
         for (int r = 0; r < NX; ++r) {
           fc[r] -= nd.dnb(Rec<M>::Xc, r, i + 1);
           v[1] += fabs(fc[r]);
           dinf = fmax(dinf, fabs(fc[r]));
-          double lin = (double)nd.at(Rec<M>::C, r) - (double)nd.nb(Rec<M>::Xh, r, i + 1);
-          for (int c = 0; c < NX; ++c) lin += (double)nd.at(Rec<M>::A, r * NX + c) * (double)nd.at(Rec<M>::Xh, c);
-          for (int c = 0; c < NU; ++c) lin += (double)nd.at(Rec<M>::B, r * NU + c) * (double)nd.at(Rec<M>::Uh, c);
-          v[2] += fabs(lin);
+          T lin = nd.at(Rec<M>::C, r) - nd.nb(Rec<M>::Xh, r, i + 1);
+          for (int c = 0; c < NX; ++c) lin += nd.at(Rec<M>::A, r * NX + c) * nd.at(Rec<M>::Xh, c);
+          for (int c = 0; c < NU; ++c) lin += nd.at(Rec<M>::B, r * NU + c) * nd.at(Rec<M>::Uh, c);
+          lin1 += absv(lin);
         }
+        v[2] = (double)lin1;
         v[3] = dinf;
       }
-      v[4] = st;
+      v[4] = (double)st;
     }
     block_reduce(sh, v, 3, 5);
     if (threadIdx.x == 0) {
@@ -1118,7 +1159,7 @@ __global__ void __launch_bounds__(MAX_THREADS) scp_kernel(ProblemDev P, Layout L
   if (active) {
     double xb[NX], ub[NU];
     read_nominal<M, T, AOS>(nd, i < N, xb, ub);
-    w[0] = node_cost<M>(P, b, i, N, xb, ub);
+    w[0] = node_cost<M, T>(P, I, b, i, N, xb, ub);
     if (i < N) {
       double fn[NX];
       rk4<M, double>(prm, h, xb, ub, fn);

@@ -34,6 +34,10 @@ template <class T> __device__ __forceinline__ Dual<T> operator-(T b, Dual<T> a) 
 template <class T> __device__ __forceinline__ Dual<T> operator*(Dual<T> a, T b) { return {a.v * b, a.d * b}; }
 template <class T> __device__ __forceinline__ Dual<T> operator*(T b, Dual<T> a) { return {a.v * b, a.d * b}; }
 template <class T> __device__ __forceinline__ Dual<T> operator/(Dual<T> a, T b) { return {a.v / b, a.d / b}; }
+template <class T> __device__ __forceinline__ Dual<T> operator/(T a, Dual<T> b) {
+  T q = a / b.v;
+  return {q, -q * b.d / b.v};
+}
 
 __device__ __forceinline__ float sin_(float a) { return sinf(a); }
 __device__ __forceinline__ float cos_(float a) { return cosf(a); }
@@ -54,8 +58,8 @@ template <class T> __device__ __forceinline__ Dual<T> sqrt_(Dual<T> a) {
 // prm: m, Jx, Jy, Jz, arm, km (yaw moment per unit thrust), drag, g.
 struct Quad12 {
   static constexpr int NX = 12, NU = 4;
-  template <class S>
-  __device__ static void f(const double* prm, const S* x, const S* u, S* xd) {
+  template <class S, class P>
+  __device__ static void f(const P* prm, const S* x, const S* u, S* xd) {
     typedef typename BaseOf<S>::type R;
     const R m = (R)prm[0], Jx = (R)prm[1], Jy = (R)prm[2], Jz = (R)prm[3];
     const R arm = (R)prm[4], km = (R)prm[5], cd = (R)prm[6], g = (R)prm[7];
@@ -94,24 +98,25 @@ struct Quad12 {
 // unit thrust), non-dimensional units.
 struct Mars7 {
   static constexpr int NX = 7, NU = 3;
-  template <class S>
-  __device__ static void f(const double* prm, const S* x, const S* u, S* xd) {
+  template <class S, class P>
+  __device__ static void f(const P* prm, const S* x, const S* u, S* xd) {
     typedef typename BaseOf<S>::type R;
     const R g = (R)prm[0], alpha = (R)prm[1];
     const S Tn = sqrt_(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    const S im = R(1) / x[6];   // one division per evaluation (GB300's FP64 divide is costly)
     xd[0] = x[3];
     xd[1] = x[4];
     xd[2] = x[5];
-    xd[3] = u[0] / x[6] - g;
-    xd[4] = u[1] / x[6];
-    xd[5] = u[2] / x[6];
+    xd[3] = u[0] * im - g;
+    xd[4] = u[1] * im;
+    xd[5] = u[2] * im;
     xd[6] = -(alpha * Tn);
   }
 };
 
 // Classical fourth-order Runge-Kutta step (Eq. (1b)).
-template <class M, class S>
-__device__ __forceinline__ void rk4(const double* prm, double h_, const S* x, const S* u, S* xn) {
+template <class M, class S, class P>
+__device__ __forceinline__ void rk4(const P* prm, double h_, const S* x, const S* u, S* xn) {
   typedef typename BaseOf<S>::type R;
   constexpr int NX = M::NX;
   const R h = (R)h_, hh = (R)(0.5 * h_), h6 = (R)(h_ / 6.0);
@@ -131,16 +136,15 @@ __device__ __forceinline__ void rk4(const double* prm, double h_, const S* x, co
 }
 
 // Column `dir` of [A B] = d RK4 / d(x, u) at (x, u), by one forward-mode pass.
-template <class M, class T>
-__device__ __forceinline__ void rk4_jvp(const double* prm, double h, const double* x, const double* u,
-                                        int dir, T* col) {
+template <class M, class T, class X, class P>
+__device__ __forceinline__ void rk4_jvp(const P* prm, double h, const X* x, const X* u, int dir, T* col) {
   constexpr int NX = M::NX, NU = M::NU;
   Dual<T> xd[NX], ud[NU], out[NX];
 #pragma unroll
   for (int j = 0; j < NX; ++j) xd[j] = {(T)x[j], (T)(dir == j ? 1 : 0)};
 #pragma unroll
   for (int j = 0; j < NU; ++j) ud[j] = {(T)u[j], (T)(dir == NX + j ? 1 : 0)};
-  rk4<M, Dual<T>>(prm, h, xd, ud, out);
+  rk4<M, Dual<T>, P>(prm, h, xd, ud, out);
 #pragma unroll
   for (int j = 0; j < NX; ++j) col[j] = out[j].d;
 }
@@ -187,6 +191,11 @@ __device__ __forceinline__ void proj_cone3c(T* v, T tau, T ca, T sa) {
 }
 
 template <class T> __device__ __forceinline__ T clampv(T v, T lo, T hi) { return fmin(fmax(v, lo), hi); }
+// max / |.| in the type of the arguments (never promoted to FP64 for floats)
+__device__ __forceinline__ float maxv(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double maxv(double a, double b) { return fmax(a, b); }
+__device__ __forceinline__ float absv(float a) { return fabsf(a); }
+__device__ __forceinline__ double absv(double a) { return fabs(a); }
 __device__ __forceinline__ float clampv(float v, float lo, float hi) { return fminf(fmaxf(v, lo), hi); }
 
 // ------------------------------------------------------------------ block reductions (FP64)
