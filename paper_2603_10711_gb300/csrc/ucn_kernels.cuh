@@ -83,6 +83,37 @@ struct Node {
 
 template <class M> struct IsQuad { static constexpr bool value = std::is_same<M, Quad12>::value; };
 
+// Storage of a node's matrices A_i, B_i and the packed H_i^-1.  Small models
+// keep them in registers (every index below is a compile-time constant after
+// unrolling), which takes ~60% of the shared-memory traffic out of the ADMM
+// iteration; larger ones keep them in the node record.
+template <class M, class T, bool AOS>
+struct SmemMats {
+  Node<T, AOS> nd;
+  __device__ __forceinline__ T& A(int k) const { return nd.at(Rec<M>::A, k); }
+  __device__ __forceinline__ T& B(int k) const { return nd.at(Rec<M>::B, k); }
+  __device__ __forceinline__ T& H(int k) const { return nd.at(Rec<M>::Hi, k); }
+};
+template <class M, class T>
+struct RegMats {
+  static constexpr int NN = M::NX + M::NU;
+  mutable T a[M::NX * M::NX], b[M::NX * M::NU], h[NN * (NN + 1) / 2];
+  __device__ __forceinline__ T& A(int k) const { return a[k]; }
+  __device__ __forceinline__ T& B(int k) const { return b[k]; }
+  __device__ __forceinline__ T& H(int k) const { return h[k]; }
+};
+template <class M> struct SmallModel {
+  static constexpr int NN = M::NX + M::NU;
+  static constexpr bool value = M::NX * M::NX + M::NX * M::NU + NN * (NN + 1) / 2 <= 128;
+};
+template <class M, class T, bool AOS>
+using MatsFor = typename std::conditional<AOS && SmallModel<M>::value, RegMats<M, T>, SmemMats<M, T, AOS>>::type;
+
+template <class M, class T, bool AOS>
+__device__ __forceinline__ void init_mats(SmemMats<M, T, AOS>& m, const Node<T, AOS>& nd) { m.nd = nd; }
+template <class M, class T, bool AOS>
+__device__ __forceinline__ void init_mats(RegMats<M, T>& m, const Node<T, AOS>& nd) {}
+
 // Per-node constants of one SCP iteration, held in registers across the ADMM
 // loop: the cost gradient (q_i, r_i) in deviations and the diagonal of H_i
 // without its A/B and mirror Gram terms.
@@ -170,8 +201,8 @@ __device__ __forceinline__ void read_nominal(const Node<T, AOS>& nd, bool hasU, 
 }
 
 // A_i, B_i by forward-mode differentiation of the RK4 map (Eq. (2b)), in T.
-template <class M, class T, bool AOS>
-__device__ void node_jacobians(const Node<T, AOS>& nd, const Layout& L, const T* prm, double h) {
+template <class M, class T, bool AOS, class MS>
+__device__ __forceinline__ void node_jacobians(const Node<T, AOS>& nd, const MS& MT, const T* prm, double h) {
   constexpr int NX = M::NX, NU = M::NU;
   double xb[NX], ub[NU];
   read_nominal<M, T, AOS>(nd, true, xb, ub);
@@ -180,13 +211,14 @@ __device__ void node_jacobians(const Node<T, AOS>& nd, const Layout& L, const T*
   for (int j = 0; j < NX; ++j) xt[j] = (T)xb[j];
 #pragma unroll
   for (int j = 0; j < NU; ++j) ut[j] = (T)ub[j];
+#pragma unroll
   for (int dir = 0; dir < NX + NU; ++dir) {
     T col[NX];
     rk4_jvp<M, T>(prm, h, xt, ut, dir, col);
 #pragma unroll
     for (int r = 0; r < NX; ++r) {
-      if (dir < NX) nd.at(Rec<M>::A, r * NX + dir) = col[r];
-      else nd.at(Rec<M>::B, r * NU + (dir - NX)) = col[r];
+      if (dir < NX) MT.A(r * NX + dir) = col[r];
+      else MT.B(r * NU + (dir - NX)) = col[r];
     }
   }
 }
@@ -265,65 +297,77 @@ __host__ __device__ constexpr int pk(int r, int c) { return r * (r + 1) / 2 + c;
 
 // H_i of Eq. (4) plus rho_geo G_j^T G_j for each mirror set, assembled in
 // packed form and factored H = L L^T in place (unpivoted Cholesky; the
-// diagonal holds 1/L_jj).  Returns false on a non-positive pivot.
-template <class M, class T, bool AOS, int n>
-__device__ bool node_factor(const Node<T, AOS>& nd, const Layout& L, const Inst<T>& I, const NodeConst<M, T>& K,
-                            T rd, T rg) {
+// diagonal holds 1/L_jj).  Returns false on a non-positive pivot.  Node N,
+// which has no control, is factored at the same size with an identity
+// control block and no coupling, so its state block is H_N exactly.
+template <class M, class T, bool AOS, int n, class MS>
+__device__ __forceinline__ bool node_factor(const Node<T, AOS>& nd, const MS& MT, const Layout& L, const Inst<T>& I,
+                                            const NodeConst<M, T>& K, T rd, T rg) {
   constexpr int NX = M::NX, NU = M::NU;
   const int i = nd.i, N = nd.N;
   const bool hasU = (n > NX);
   const bool term = (i == N);
+  #pragma unroll
   for (int r = 0; r < n; ++r) {
+    #pragma unroll
     for (int c = 0; c <= r; ++c) {
       T h = T(0);
       if (r < NX) {  // H11
         if (r == c) h = K.hd[r];
         if (!term) {
           T acc = T(0);
-          for (int k = 0; k < NX; ++k) acc += nd.at(Rec<M>::A, k * NX + r) * nd.at(Rec<M>::A, k * NX + c);
+          #pragma unroll
+          for (int k = 0; k < NX; ++k) acc += MT.A(k * NX + r) * MT.A(k * NX + c);
           h += rd * acc;
         }
         if constexpr (IsQuad<M>::value) {
           if (r < 3 && c < 3) {
             T acc = T(0);
+            #pragma unroll
             for (int j = 0; j < I.nobs; ++j) acc += nd.at(L.oMd, 4 * j + r) * nd.at(L.oMd, 4 * j + c);
             h += rg * acc;
           }
         } else {
           if (r < 3 && r == c && I.cone) h += rg;
         }
-      } else if (c < NX) {  // H21 = H12^T
+      } else if (c < NX) {  // H21 = H12^T (zero at node N: no control there)
         T acc = T(0);
-        for (int k = 0; k < NX; ++k) acc += nd.at(Rec<M>::B, k * NU + (r - NX)) * nd.at(Rec<M>::A, k * NX + c);
-        h = rd * acc;
-      } else {  // H22
+        #pragma unroll
+        for (int k = 0; k < NX; ++k) acc += MT.B(k * NU + (r - NX)) * MT.A(k * NX + c);
+        h = term ? T(0) : rd * acc;
+      } else {  // H22 (identity at node N, decoupled from the state block)
         const int rr = r - NX, cc = c - NX;
         if (rr == cc) h = K.hd[r];
         T acc = T(0);
-        for (int k = 0; k < NX; ++k) acc += nd.at(Rec<M>::B, k * NU + rr) * nd.at(Rec<M>::B, k * NU + cc);
-        h += rd * acc;
+        #pragma unroll
+        for (int k = 0; k < NX; ++k) acc += MT.B(k * NU + rr) * MT.B(k * NU + cc);
+        if (!term) h += rd * acc;
         if constexpr (!IsQuad<M>::value) {
-          if (rr < 3 && cc < 3) {
+          if (rr < 3 && cc < 3 && !term) {
             if (rr == cc && I.ball) h += rg;
             if (I.half) h += rg * nd.at(L.oMd, rr) * nd.at(L.oMd, cc);
           }
         }
       }
-      nd.at(Rec<M>::Hi, pk(r, c)) = h;
+      MT.H(pk(r, c)) = h;
     }
   }
   (void)hasU;
   bool ok = true;
+  #pragma unroll
   for (int j = 0; j < n; ++j) {
-    T s = nd.at(Rec<M>::Hi, pk(j, j));
-    for (int k = 0; k < j; ++k) { const T l = nd.at(Rec<M>::Hi, pk(j, k)); s -= l * l; }
+    T s = MT.H(pk(j, j));
+    #pragma unroll
+    for (int k = 0; k < j; ++k) { const T l = MT.H(pk(j, k)); s -= l * l; }
     if (!(s > T(0))) { ok = false; s = T(1); }
     const T inv = T(1) / sqrt_(s);
-    nd.at(Rec<M>::Hi, pk(j, j)) = inv;
+    MT.H(pk(j, j)) = inv;
+    #pragma unroll
     for (int r = j + 1; r < n; ++r) {
-      T t = nd.at(Rec<M>::Hi, pk(r, j));
-      for (int k = 0; k < j; ++k) t -= nd.at(Rec<M>::Hi, pk(r, k)) * nd.at(Rec<M>::Hi, pk(j, k));
-      nd.at(Rec<M>::Hi, pk(r, j)) = t * inv;
+      T t = MT.H(pk(r, j));
+      #pragma unroll
+      for (int k = 0; k < j; ++k) t -= MT.H(pk(r, k)) * MT.H(pk(j, k));
+      MT.H(pk(r, j)) = t * inv;
     }
   }
   // In place: L -> L^-1 (column by column; the diagonal already holds 1/L_jj),
@@ -331,44 +375,52 @@ __device__ bool node_factor(const Node<T, AOS>& nd, const Layout& L, const Inst<
   // loop then solves H xi = g by one symmetric mat-vec: the same solve as the
   // forward/back substitution, with independent dot products instead of a
   // chain of n dependent steps.
+  #pragma unroll
   for (int j = 0; j < n; ++j) {
     T col[n];
-    col[j] = nd.at(Rec<M>::Hi, pk(j, j));
+    col[j] = MT.H(pk(j, j));
+    #pragma unroll
     for (int r = j + 1; r < n; ++r) {
       T t = T(0);
-      for (int k = j; k < r; ++k) t += nd.at(Rec<M>::Hi, pk(r, k)) * (k == j ? col[j] : col[k]);
-      col[r] = -t * nd.at(Rec<M>::Hi, pk(r, r));
+      #pragma unroll
+      for (int k = j; k < r; ++k) t += MT.H(pk(r, k)) * (k == j ? col[j] : col[k]);
+      col[r] = -t * MT.H(pk(r, r));
     }
-    for (int r = j + 1; r < n; ++r) nd.at(Rec<M>::Hi, pk(r, j)) = col[r];
+    #pragma unroll
+    for (int r = j + 1; r < n; ++r) MT.H(pk(r, j)) = col[r];
   }
+  #pragma unroll
   for (int r = 0; r < n; ++r) {
     T row[n];
+    #pragma unroll
     for (int c = 0; c <= r; ++c) {
       T t = T(0);
-      for (int k = r; k < n; ++k) t += nd.at(Rec<M>::Hi, pk(k, r)) * nd.at(Rec<M>::Hi, pk(k, c));
+      #pragma unroll
+      for (int k = r; k < n; ++k) t += MT.H(pk(k, r)) * MT.H(pk(k, c));
       row[c] = t;
     }
-    for (int c = 0; c <= r; ++c) nd.at(Rec<M>::Hi, pk(r, c)) = row[c];
+    #pragma unroll
+    for (int c = 0; c <= r; ++c) MT.H(pk(r, c)) = row[c];
   }
   return ok;
 }
 
 // xi = H^-1 g with the cached packed inverse (lower triangle of a symmetric matrix).
-template <class T, bool AOS, int n>
-__device__ __forceinline__ void sym_solve(const Node<T, AOS>& nd, int oH, const T* g, T* xi) {
+template <class T, int n, class MS>
+__device__ __forceinline__ void sym_solve(const MS& MT, const T* g, T* xi) {
 #pragma unroll
   for (int r = 0; r < n; ++r) {
     T t = T(0);
 #pragma unroll
-    for (int c = 0; c < n; ++c) t += nd.at(oH, r >= c ? pk(r, c) : pk(c, r)) * g[c];
+    for (int c = 0; c < n; ++c) t += MT.H(r >= c ? pk(r, c) : pk(c, r)) * g[c];
     xi[r] = t;
   }
 }
 
 // H xi without forming H (A, B, the cost diagonals, the rho terms and the
 // mirror Gram terms), for the refinement residual g - H xi.
-template <class M, class T, bool AOS, int n>
-__device__ __forceinline__ void apply_H(const Node<T, AOS>& nd, const Layout& L, const Inst<T>& I,
+template <class M, class T, bool AOS, int n, class MS>
+__device__ __forceinline__ void apply_H(const Node<T, AOS>& nd, const MS& MT, const Layout& L, const Inst<T>& I,
                                         const NodeConst<M, T>& K, T rd, T rg, const T* xi, T* out) {
   constexpr int NX = M::NX, NU = M::NU;
 #pragma unroll
@@ -379,23 +431,23 @@ __device__ __forceinline__ void apply_H(const Node<T, AOS>& nd, const Layout& L,
     for (int r = 0; r < NX; ++r) {
       T acc = T(0);
 #pragma unroll
-      for (int c = 0; c < NX; ++c) acc += nd.at(Rec<M>::A, r * NX + c) * xi[c];
+      for (int c = 0; c < NX; ++c) acc += MT.A(r * NX + c) * xi[c];
 #pragma unroll
-      for (int c = 0; c < NU; ++c) acc += nd.at(Rec<M>::B, r * NU + c) * xi[NX + c];
+      for (int c = 0; c < NU; ++c) acc += MT.B(r * NU + c) * xi[NX + c];
       v[r] = rd * acc;
     }
 #pragma unroll
     for (int j = 0; j < NX; ++j) {
       T acc = T(0);
 #pragma unroll
-      for (int k = 0; k < NX; ++k) acc += nd.at(Rec<M>::A, k * NX + j) * v[k];
+      for (int k = 0; k < NX; ++k) acc += MT.A(k * NX + j) * v[k];
       out[j] += acc;
     }
 #pragma unroll
     for (int j = 0; j < NU; ++j) {
       T acc = T(0);
 #pragma unroll
-      for (int k = 0; k < NX; ++k) acc += nd.at(Rec<M>::B, k * NU + j) * v[k];
+      for (int k = 0; k < NX; ++k) acc += MT.B(k * NU + j) * v[k];
       out[NX + j] = K.hd[NX + j] * xi[NX + j] + acc;
     }
   }
@@ -419,8 +471,8 @@ __device__ __forceinline__ void apply_H(const Node<T, AOS>& nd, const Layout& L,
 }
 
 // Right-hand side g_i of Step 1 (stationarity of Eq. (3) in (x_i, u_i)).
-template <class M, class T, bool AOS, int n>
-__device__ __forceinline__ void node_rhs(const Node<T, AOS>& nd, const Layout& L, const Inst<T>& I,
+template <class M, class T, bool AOS, int n, class MS>
+__device__ __forceinline__ void node_rhs(const Node<T, AOS>& nd, const MS& MT, const Layout& L, const Inst<T>& I,
                                          const NodeConst<M, T>& K, T re, T rd, T rg, T* g) {
   constexpr int NX = M::NX, NU = M::NU;
   const int i = nd.i;
@@ -439,14 +491,14 @@ __device__ __forceinline__ void node_rhs(const Node<T, AOS>& nd, const Layout& L
     for (int j = 0; j < NX; ++j) {
       T acc = T(0);
 #pragma unroll
-      for (int k = 0; k < NX; ++k) acc += nd.at(Rec<M>::A, k * NX + j) * w[k];
+      for (int k = 0; k < NX; ++k) acc += MT.A(k * NX + j) * w[k];
       g[j] += acc;
     }
 #pragma unroll
     for (int j = 0; j < NU; ++j) {
       T acc = T(0);
 #pragma unroll
-      for (int k = 0; k < NX; ++k) acc += nd.at(Rec<M>::B, k * NU + j) * w[k];
+      for (int k = 0; k < NX; ++k) acc += MT.B(k * NU + j) * w[k];
       g[NX + j] = -K.q[NX + j] + acc + rg * nd.at(Rec<M>::Uh, j) - nd.at(Rec<M>::Nuu, j);
     }
   }
@@ -568,8 +620,8 @@ __device__ void node_reseed(const Node<T, AOS>& nd, const Layout& L, const Inst<
 // threads of the CTA call it.  The LAST instance also accumulates the primal
 // and dual residuals in FP64 (a separate instantiation, so that the hot loop
 // carries no FP64 instruction, not even a predicated-off one).
-template <class M, class T, bool AOS, bool REFINE, bool LAST>
-__device__ __forceinline__ void admm_iteration(const Node<T, AOS>& nd, const Layout& L, const Inst<T>& I,
+template <class M, class T, bool AOS, bool REFINE, bool LAST, class MS>
+__device__ __forceinline__ void admm_iteration(const Node<T, AOS>& nd, const MS& MT, const Layout& L, const Inst<T>& I,
                                                const NodeConst<M, T>& K, bool active, T re, T rd, T rg,
                                                T irg, T ired, double& rp, double& rdl) {
   constexpr int NX = M::NX, NU = M::NU, NN = NX + NU;
@@ -581,14 +633,14 @@ __device__ __forceinline__ void admm_iteration(const Node<T, AOS>& nd, const Lay
     if (active) {
       T g[NN];
       if (i < N) {
-        node_rhs<M, T, AOS, NN>(nd, L, I, K, re, rd, rg, g);
-        sym_solve<T, AOS, NN>(nd, Rec<M>::Hi, g, x);
+        node_rhs<M, T, AOS, NN>(nd, MT, L, I, K, re, rd, rg, g);
+        sym_solve<T, NN>(MT, g, x);
         if constexpr (REFINE) {
           T hx[NN], dx[NN];
-          apply_H<M, T, AOS, NN>(nd, L, I, K, rd, rg, x, hx);
+          apply_H<M, T, AOS, NN>(nd, MT, L, I, K, rd, rg, x, hx);
 #pragma unroll
           for (int j = 0; j < NN; ++j) hx[j] = g[j] - hx[j];
-          sym_solve<T, AOS, NN>(nd, Rec<M>::Hi, hx, dx);
+          sym_solve<T, NN>(MT, hx, dx);
 #pragma unroll
           for (int j = 0; j < NN; ++j) x[j] += dx[j];
         }
@@ -597,20 +649,20 @@ __device__ __forceinline__ void admm_iteration(const Node<T, AOS>& nd, const Lay
         for (int r = 0; r < NX; ++r) {
           T acc = nd.at(Rec<M>::C, r);
 #pragma unroll
-          for (int c = 0; c < NX; ++c) acc += nd.at(Rec<M>::A, r * NX + c) * x[c];
+          for (int c = 0; c < NX; ++c) acc += MT.A(r * NX + c) * x[c];
 #pragma unroll
-          for (int c = 0; c < NU; ++c) acc += nd.at(Rec<M>::B, r * NU + c) * x[NX + c];
+          for (int c = 0; c < NU; ++c) acc += MT.B(r * NU + c) * x[NX + c];
           nd.at(Rec<M>::Ex1, r) = acc;
         }
       } else {
-        node_rhs<M, T, AOS, NX>(nd, L, I, K, re, rd, rg, g);
-        sym_solve<T, AOS, NX>(nd, Rec<M>::Hi, g, x);
+        node_rhs<M, T, AOS, NX>(nd, MT, L, I, K, re, rd, rg, g);
+        sym_solve<T, NX>(MT, g, x);
         if constexpr (REFINE) {
           T hx[NX], dx[NX];
-          apply_H<M, T, AOS, NX>(nd, L, I, K, rd, rg, x, hx);
+          apply_H<M, T, AOS, NX>(nd, MT, L, I, K, rd, rg, x, hx);
 #pragma unroll
           for (int j = 0; j < NX; ++j) hx[j] = g[j] - hx[j];
-          sym_solve<T, AOS, NX>(nd, Rec<M>::Hi, hx, dx);
+          sym_solve<T, NX>(MT, hx, dx);
 #pragma unroll
           for (int j = 0; j < NX; ++j) x[j] += dx[j];
         }
@@ -684,19 +736,20 @@ __device__ __forceinline__ void admm_iteration(const Node<T, AOS>& nd, const Lay
           for (int j = 0; j < NX; ++j) {
             T acc = T(0);
 #pragma unroll
-            for (int k = 0; k < NX; ++k) acc += nd.at(Rec<M>::A, k * NX + j) * nd.nb(Rec<M>::Ex1, k, i + 1);
+            for (int k = 0; k < NX; ++k) acc += MT.A(k * NX + j) * nd.nb(Rec<M>::Ex1, k, i + 1);
             sv[j] += acc;
           }
 #pragma unroll
           for (int j = 0; j < NU; ++j) {
             T acc = T(0);
 #pragma unroll
-            for (int k = 0; k < NX; ++k) acc += nd.at(Rec<M>::B, k * NU + j) * nd.nb(Rec<M>::Ex1, k, i + 1);
+            for (int k = 0; k < NX; ++k) acc += MT.B(k * NU + j) * nd.nb(Rec<M>::Ex1, k, i + 1);
             sv[NX + j] += acc;
           }
         }
-        const int n = (i < N) ? NN : NX;
-        for (int j = 0; j < n; ++j) rdl += (double)sv[j] * (double)sv[j];
+#pragma unroll
+        for (int j = 0; j < NN; ++j)
+          if (j < NX || i < N) rdl += (double)sv[j] * (double)sv[j];
       }
     }
     if (active && i >= 1) {
@@ -709,15 +762,15 @@ __device__ __forceinline__ void admm_iteration(const Node<T, AOS>& nd, const Lay
 
 // `iters` iterations of Steps 1-4; the primal and dual residuals of the last
 // one (FP64 sums) are returned in res[0..1].
-template <class M, class T, bool AOS, bool REFINE>
-__device__ void admm_iterations(const Node<T, AOS>& nd, const Layout& L, const Inst<T>& I,
+template <class M, class T, bool AOS, bool REFINE, class MS>
+__device__ __forceinline__ void admm_iterations(const Node<T, AOS>& nd, const MS& MT, const Layout& L, const Inst<T>& I,
                                 const NodeConst<M, T>& K, bool active, T re, T rd, T rg, int iters,
                                 InstShared& sh, double* res) {
   const T irg = T(1) / rg, ired = T(1) / (re + rd);
   double rp = 0.0, rdl = 0.0;
   for (int it = 0; it + 1 < iters; ++it)
-    admm_iteration<M, T, AOS, REFINE, false>(nd, L, I, K, active, re, rd, rg, irg, ired, rp, rdl);
-  admm_iteration<M, T, AOS, REFINE, true>(nd, L, I, K, active, re, rd, rg, irg, ired, rp, rdl);
+    admm_iteration<M, T, AOS, REFINE, false>(nd, MT, L, I, K, active, re, rd, rg, irg, ired, rp, rdl);
+  admm_iteration<M, T, AOS, REFINE, true>(nd, MT, L, I, K, active, re, rd, rg, irg, ired, rp, rdl);
   double v[2] = {rp, rdl};
   block_reduce(sh, v, 2, 2);
   res[0] = sqrt(v[0]);
@@ -927,6 +980,8 @@ __global__ void __launch_bounds__(MAX_THREADS) admm_kernel(ProblemDev P, Layout 
   const int b = blockIdx.x;
   constexpr bool AOS = SMEM;
   Node<T, AOS> nd = make_node<T, SMEM>(P, L, smem, b);
+  MatsFor<M, T, AOS> MT;
+  init_mats<M, T, AOS>(MT, nd);
   const int i = nd.i, N = nd.N;
   const bool active = i <= N;
   const long long xo = P.xoff[b], uo = P.uoff[b];
@@ -936,8 +991,10 @@ __global__ void __launch_bounds__(MAX_THREADS) admm_kernel(ProblemDev P, Layout 
   if (active && i < N) {
     // A, B in T; deviation affine term c_i = A xbar_i + B ubar_i + d_i - xbar_{i+1} in FP64
     const long long g = uo + i;
-    for (int e = 0; e < NX * NX; ++e) nd.at(Rec<M>::A, e) = (T)Ag[g * NX * NX + e];
-    for (int e = 0; e < NX * NU; ++e) nd.at(Rec<M>::B, e) = (T)Bg[g * NX * NU + e];
+#pragma unroll
+    for (int e = 0; e < NX * NX; ++e) MT.A(e) = (T)Ag[g * NX * NX + e];
+#pragma unroll
+    for (int e = 0; e < NX * NU; ++e) MT.B(e) = (T)Bg[g * NX * NU + e];
     for (int r = 0; r < NX; ++r) {
       double acc = dg[g * NX + r];
       for (int c = 0; c < NX; ++c) acc += Ag[g * NX * NX + r * NX + c] * nd.dat(Rec<M>::Xbar, c);
@@ -950,8 +1007,7 @@ __global__ void __launch_bounds__(MAX_THREADS) admm_kernel(ProblemDev P, Layout 
   NodeConst<M, T> K;
   if (active) {
     node_setup<M, T, AOS>(nd, L, P, b, radius[b], re, rg, K);
-    const bool ok = (i < N) ? node_factor<M, T, AOS, NX + NU>(nd, L, I, K, rd, rg)
-                            : node_factor<M, T, AOS, NX>(nd, L, I, K, rd, rg);
+    const bool ok = node_factor<M, T, AOS, NX + NU>(nd, MT, L, I, K, rd, rg);
     if (!ok) atomicOr(&sh.fail, 1);
     const double* sa = P.state_abs + P.soff[b];
     if (warm) {
@@ -964,7 +1020,7 @@ __global__ void __launch_bounds__(MAX_THREADS) admm_kernel(ProblemDev P, Layout 
   }
   __syncthreads();
   double r2[2] = {0.0, 0.0};
-  if (!sh.fail) admm_iterations<M, T, AOS, REFINE>(nd, L, I, K, active, re, rd, rg, iters, sh, r2);
+  if (!sh.fail) admm_iterations<M, T, AOS, REFINE>(nd, MT, L, I, K, active, re, rd, rg, iters, sh, r2);
   if (active) {
     node_export<M, T, AOS>(nd, L, P, b, P.state_abs + P.soff[b]);
     for (int j = 0; j < NX; ++j) xhat[(xo + i) * NX + j] = nd.dat(Rec<M>::Xbar, j) + (double)nd.at(Rec<M>::Xh, j);
@@ -1015,6 +1071,8 @@ __global__ void __launch_bounds__(MAX_THREADS) scp_kernel(ProblemDev P, Layout L
   const int b = blockIdx.x;
   constexpr bool AOS = SMEM;
   Node<T, AOS> nd = make_node<T, SMEM>(P, L, smem, b);
+  MatsFor<M, T, AOS> MT;
+  init_mats<M, T, AOS>(MT, nd);
   const int i = nd.i, N = nd.N;
   const bool active = i <= N;
   const long long xo = P.xoff[b], uo = P.uoff[b];
@@ -1061,16 +1119,16 @@ __global__ void __launch_bounds__(MAX_THREADS) scp_kernel(ProblemDev P, Layout L
     const T re = (T)(P.rho_eq * fac), rd = (T)(P.rho_dyn * fac), rg = (T)(P.rho_geo * fac);
     const double radius = sh.radius;
     if (active) {
-      if (i < N) node_jacobians<M, T, AOS>(nd, L, I.prm, h);
+      if (i < N) node_jacobians<M, T, AOS>(nd, MT, I.prm, h);
       node_setup<M, T, AOS>(nd, L, P, b, radius, re, rg, K);
-      const bool ok = (i < N) ? node_factor<M, T, AOS, NN>(nd, L, I, K, rd, rg) : node_factor<M, T, AOS, NX>(nd, L, I, K, rd, rg);
+      const bool ok = node_factor<M, T, AOS, NN>(nd, MT, L, I, K, rd, rg);
       if (!ok) atomicOr(&sh.fail, 1);
       node_reseed<M, T, AOS>(nd, L, I);
       publish_ex2<M, T, AOS>(nd, L, active, rd);
     }
     __syncthreads();
     if (sh.fail) { if (threadIdx.x == 0) sh.status = ST_NUMERIC; iters_run++; break; }
-    admm_iterations<M, T, AOS, REFINE>(nd, L, I, K, active, re, rd, rg, P.admm_iters, sh, res);
+    admm_iterations<M, T, AOS, REFINE>(nd, MT, L, I, K, active, re, rd, rg, P.admm_iters, sh, res);
     ++iters_run;
     // ---- candidate (x-hat, u-hat): FP64 rollout, defects, cost, linear model
     double xc[NX], uc[NU], fc[NX];
@@ -1089,13 +1147,16 @@ __global__ void __launch_bounds__(MAX_THREADS) scp_kernel(ProblemDev P, Layout L
         rk4<M, double>(prm, h, xc, uc, fc);
         double dinf = 0.0;
         T lin1 = T(0);
+#pragma unroll
         for (int r = 0; r < NX; ++r) {
           fc[r] -= nd.dnb(Rec<M>::Xc, r, i + 1);
           v[1] += fabs(fc[r]);
           dinf = fmax(dinf, fabs(fc[r]));
           T lin = nd.at(Rec<M>::C, r) - nd.nb(Rec<M>::Xh, r, i + 1);
-          for (int c = 0; c < NX; ++c) lin += nd.at(Rec<M>::A, r * NX + c) * nd.at(Rec<M>::Xh, c);
-          for (int c = 0; c < NU; ++c) lin += nd.at(Rec<M>::B, r * NU + c) * nd.at(Rec<M>::Uh, c);
+#pragma unroll
+          for (int c = 0; c < NX; ++c) lin += MT.A(r * NX + c) * nd.at(Rec<M>::Xh, c);
+#pragma unroll
+          for (int c = 0; c < NU; ++c) lin += MT.B(r * NU + c) * nd.at(Rec<M>::Uh, c);
           lin1 += absv(lin);
         }
         v[2] = (double)lin1;
