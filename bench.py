@@ -55,6 +55,26 @@ def mars_mirror_flops():
     return 64
 
 
+def kernel_sources_sha256():
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2603_10711_gb300", "csrc", "*"))):
+        h.update(os.path.basename(p).encode())
+        h.update(open(p, "rb").read())
+    return h.hexdigest()
+
+
+def recorded_traffic():
+    """DRAM bytes per launch of the fused kernel from the committed ncu capture,
+    or None when the kernel sources changed since that capture."""
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "scp_kernel_traffic.json")))
+    except Exception:
+        return None
+    return rec["traffic_bytes_per_launch"] if rec.get("csrc_sha256") == kernel_sources_sha256() else None
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -108,6 +128,26 @@ class ClockSampler:
                           and "Not" not in r[5 + k]})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": reasons, "samples": len(rows)}
+
+
+def reduce_over_ranks(total_time, passed, device):
+    """Whole-job figures of a weak-scaling run: the slowest rank's time and the
+    passed solves of all ranks (a control-path reduction; the solves share no data)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(total_time), float(passed)], dtype=torch.float64, device=device)
+    tmax = t.clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    tsum = t.clone()
+    dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+    return float(tmax[0]), float(tsum[1])
+
+
+def shard_bounds(batch, rank, world):
+    """Contiguous instance range [lo, hi) of `rank` when one batch is split over ranks."""
+    per, extra = divmod(batch, world)
+    lo = rank * per + min(rank, extra)
+    return lo, lo + per + (1 if rank < extra else 0)
 
 
 def make_problem(args, rank=0):
@@ -180,11 +220,7 @@ def run_ours(args, rank, world):
     torch.cuda.synchronize()
     total = sum(times)
     if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total, float(passed)], dtype=torch.float64, device=dev)
-        tmax = t.clone(); dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        tsum = t.clone(); dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
-        total, passed_all = float(tmax[0]), float(tsum[1])
+        total, passed_all = reduce_over_ranks(total, passed, dev)
     else:
         passed_all = passed
     value = passed_all / total
@@ -250,7 +286,8 @@ def run_ours(args, rank, world):
                        "pass_rate": p64 / (B * len(t64)), "scp_iters_mean": float(st64["scp_iters"].mean())},
         "e2e": {"value": e2e_pass / sum(e2e_times), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
-                     "frac": achieved / peak_tf, "traffic": None,
+                     "frac": achieved / peak_tf, "traffic": recorded_traffic(),
+                     "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
                      "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 x %.0f MHz" % sm_max,
                      "algorithmic_flops_per_node_iter": flops_ni, "node_iters_per_launch": nodeiters / args.steps},
         "gpu_launches": args.steps,
