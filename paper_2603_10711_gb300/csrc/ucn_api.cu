@@ -42,20 +42,27 @@ namespace ucn {
 
 void set_error_message(const char* msg) { snprintf(g_err, sizeof(g_err), "%s", msg); }
 
-Layout make_layout(int model, int nodes, int max_obs, int tsize) {
+Layout make_layout(int model, int nodes, int max_obs, int tsize, bool reg_mats) {
   const bool quad = model == UCN_MODEL_QUAD12;
+  const int NX = quad ? 12 : 7, NU = quad ? 4 : 3, NN = NX + NU;
   const int fixed = quad ? Rec<Quad12>::END : Rec<Mars7>::END;     // fixed part of a node record
   const int dfixed = quad ? Rec<Quad12>::DEND : Rec<Mars7>::DEND;
   Layout L;
   std::memset(&L, 0, sizeof(L));
   const int mo = std::max(max_obs, 1);
-  L.MS = model == UCN_MODEL_QUAD12 ? mo : 7;
-  L.MD = model == UCN_MODEL_QUAD12 ? 4 * mo : 10;   // Mars: nbar, bound, nominal position, nominal thrust
-  L.MB = model == UCN_MODEL_QUAD12 ? max_obs : 3;
+  L.MS = quad ? mo : 7;
+  L.MD = quad ? 4 * mo : 10;   // Mars: nbar, bound, nominal position, nominal thrust
+  L.MB = quad ? max_obs : 3;
   L.oS = fixed;
   L.oNus = fixed + L.MS;
   L.oMd = fixed + 2 * L.MS;
-  const int nt = fixed + 2 * L.MS + L.MD;
+  int nt = fixed + 2 * L.MS + L.MD;
+  if (reg_mats) {
+    L.oA = L.oB = L.oH = -1;
+  } else {
+    L.oA = nt; L.oB = L.oA + NX * NX; L.oH = L.oB + NX * NU;
+    nt = L.oH + NN * (NN + 1) / 2;
+  }
   L.S = nodes;
   L.NS = nt | 1;       // odd record strides: consecutive nodes fall in distinct banks
   L.DS = dfixed | 1;
@@ -207,14 +214,17 @@ ucn_status ucn_problem_create(const ucn_problem_desc* d, ucn_problem** out) {
   P.timeout_ns = (unsigned long long)((d->timeout_s > 0 ? d->timeout_s : 60.0) * 1e9);
   P.state_abs = sabs;
   p->node_inst = ni;
-  // per-node storage: shared memory when one instance fits, else a global slice per instance
+  // per-node storage: shared memory when one instance fits (small models then keep
+  // their matrices in registers), else a structure-of-arrays slice of global memory
   const int tsize = d->precision == UCN_PREC_FP64 ? 8 : 4;
-  p->L = make_layout(d->model, Nmax + 1, p->max_obs, tsize);
-  p->threads = (int)round_up(Nmax + 1, 32);
+  const bool small = d->model == UCN_MODEL_MARS7;   // SmallModel<Mars7>
   int optin = 0;
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   const long long static_sh = (long long)sizeof(InstShared) + 64;
+  p->L = make_layout(d->model, Nmax + 1, p->max_obs, tsize, small);
   p->smem = p->L.bytes + static_sh <= optin;
+  if (!p->smem) p->L = make_layout(d->model, Nmax + 1, p->max_obs, tsize, false);
+  p->threads = (int)round_up(Nmax + 1, 32);
   p->smem_bytes = p->smem ? p->L.bytes : 0;
   P.ws = nullptr;
   if (!p->smem) {

@@ -14,7 +14,7 @@ struct Layout;
 void set_error_message(const char* msg);
 
 // Node-record layout of one instance (defined in ucn_api.cu).
-Layout make_layout(int model, int nodes, int max_obs, int tsize);
+Layout make_layout(int model, int nodes, int max_obs, int tsize, bool reg_mats);
 
 // Everything one kernel launch needs besides its buffers.
 struct LaunchCfg {

@@ -44,13 +44,14 @@ struct ProblemDev {
 };
 
 // Fixed part of a node record: compile-time element offsets of every per-node
-// array (the mirror arrays, whose length depends on the obstacle count, follow
-// at the runtime offsets Layout::oS / oNus / oMd).
+// array.  The mirror arrays (whose length depends on the obstacle count) follow
+// at the runtime offsets Layout::oS / oNus / oMd, then the matrices A, B, H^-1
+// at Layout::oA / oB / oH -- absent from the record when they live in registers.
 template <class M>
 struct Rec {
   static constexpr int NX = M::NX, NU = M::NU, NN = NX + NU;
-  static constexpr int A = 0, B = A + NX * NX, C = B + NX * NU, Hi = C + NX;
-  static constexpr int Xlo = Hi + NN * (NN + 1) / 2, Xhi = Xlo + NX, Ulo = Xhi + NX, Uhi = Ulo + NU;
+  static constexpr int C = 0;
+  static constexpr int Xlo = C + NX, Xhi = Xlo + NX, Ulo = Xhi + NX, Uhi = Ulo + NU;
   static constexpr int X = Uhi + NU, Z = X + NX, Lam = Z + NX, Mu = Lam + NX, Xh = Mu + NX, Nux = Xh + NX;
   static constexpr int U = Nux + NX, Uh = U + NU, Nuu = Uh + NU, Ex1 = Nuu + NU, Ex2 = Ex1 + NX, END = Ex2 + NX;
   // FP64 record: nominal state, nominal control, candidate state (exchange)
@@ -65,6 +66,7 @@ struct Layout {
   int S, NS, DS;           // SoA stride (nodes); AoS record strides (elements)
   int MS, MD, MB;          // mirror scalars / mirror data per node; exported mirror blocks
   int oS, oNus, oMd;       // runtime offsets of the mirror arrays in the record
+  int oA, oB, oH;          // matrices in the record (-1 when register-resident)
   long long tbytes;        // bytes of the T region (16-byte multiple)
   long long bytes;         // bytes per instance
 };
@@ -90,9 +92,10 @@ template <class M> struct IsQuad { static constexpr bool value = std::is_same<M,
 template <class M, class T, bool AOS>
 struct SmemMats {
   Node<T, AOS> nd;
-  __device__ __forceinline__ T& A(int k) const { return nd.at(Rec<M>::A, k); }
-  __device__ __forceinline__ T& B(int k) const { return nd.at(Rec<M>::B, k); }
-  __device__ __forceinline__ T& H(int k) const { return nd.at(Rec<M>::Hi, k); }
+  int oA, oB, oH;
+  __device__ __forceinline__ T& A(int k) const { return nd.at(oA, k); }
+  __device__ __forceinline__ T& B(int k) const { return nd.at(oB, k); }
+  __device__ __forceinline__ T& H(int k) const { return nd.at(oH, k); }
 };
 template <class M, class T>
 struct RegMats {
@@ -110,9 +113,11 @@ template <class M, class T, bool AOS>
 using MatsFor = typename std::conditional<AOS && SmallModel<M>::value, RegMats<M, T>, SmemMats<M, T, AOS>>::type;
 
 template <class M, class T, bool AOS>
-__device__ __forceinline__ void init_mats(SmemMats<M, T, AOS>& m, const Node<T, AOS>& nd) { m.nd = nd; }
+__device__ __forceinline__ void init_mats(SmemMats<M, T, AOS>& m, const Node<T, AOS>& nd, const Layout& L) {
+  m.nd = nd; m.oA = L.oA; m.oB = L.oB; m.oH = L.oH;
+}
 template <class M, class T, bool AOS>
-__device__ __forceinline__ void init_mats(RegMats<M, T>& m, const Node<T, AOS>& nd) {}
+__device__ __forceinline__ void init_mats(RegMats<M, T>& m, const Node<T, AOS>& nd, const Layout& L) {}
 
 // Per-node constants of one SCP iteration, held in registers across the ADMM
 // loop: the cost gradient (q_i, r_i) in deviations and the diagonal of H_i
@@ -981,7 +986,7 @@ __global__ void __launch_bounds__(MAX_THREADS) admm_kernel(ProblemDev P, Layout 
   constexpr bool AOS = SMEM;
   Node<T, AOS> nd = make_node<T, SMEM>(P, L, smem, b);
   MatsFor<M, T, AOS> MT;
-  init_mats<M, T, AOS>(MT, nd);
+  init_mats<M, T, AOS>(MT, nd, L);
   const int i = nd.i, N = nd.N;
   const bool active = i <= N;
   const long long xo = P.xoff[b], uo = P.uoff[b];
@@ -1072,7 +1077,7 @@ __global__ void __launch_bounds__(MAX_THREADS) scp_kernel(ProblemDev P, Layout L
   constexpr bool AOS = SMEM;
   Node<T, AOS> nd = make_node<T, SMEM>(P, L, smem, b);
   MatsFor<M, T, AOS> MT;
-  init_mats<M, T, AOS>(MT, nd);
+  init_mats<M, T, AOS>(MT, nd, L);
   const int i = nd.i, N = nd.N;
   const bool active = i <= N;
   const long long xo = P.xoff[b], uo = P.uoff[b];

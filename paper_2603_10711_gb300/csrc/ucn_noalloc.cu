@@ -112,7 +112,7 @@ extern "C" ucn_status ucn_scp_solve_noalloc(const ucn_problem_desc* d, const dou
     return nfail(UCN_EINVAL, "batch needs %lld bytes of scratch; the no-allocation entry point holds %llu",
                  need, (unsigned long long)UCN_NOALLOC_SCRATCH_BYTES);
   const int tsize = d->precision == UCN_PREC_FP64 ? 8 : 4;
-  const Layout L = make_layout(d->model, Nmax + 1, max_obs, tsize);
+  const Layout L = make_layout(d->model, Nmax + 1, max_obs, tsize, d->model == UCN_MODEL_MARS7);
   int dev = 0, optin = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return nfail(UCN_ECUDA, "no CUDA device"); }
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
