@@ -154,6 +154,8 @@ def make_problem(args, rank=0):
     over = {}
     if args.scp_iters:
         over = dict(scp_iters=args.scp_iters, stop=0)
+    if getattr(args, "workload", "mars") == "quad_box":
+        return W.quad_box(args.batch, seed=2 + rank, settings=over)
     return W.mars_batch(args.batch, seed=1 + rank, settings=over)
 
 
@@ -354,6 +356,8 @@ def main():
                     help="kernel: time only the fused kernel (profiler captures)")
     ap.add_argument("--scp-iters", type=int, default=0, help="fixed SCP iteration count (0: the workload's cap + stop test)")
     ap.add_argument("--fp64", action="store_true", help="kernel mode: the FP64 plain path")
+    ap.add_argument("--workload", default="mars", choices=["mars", "quad_box"],
+                    help="kernel mode: mars (1024-instance Mars batch) or quad_box (uneven quadrotor batch)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -134,6 +134,13 @@ ucn_status ucn_problem_create(const ucn_problem_desc* desc, ucn_problem** out);
 /* Free everything ucn_problem_create allocated (synchronises the device). */
 void ucn_problem_destroy(ucn_problem* prob);
 
+/* Order in which the fused solve takes the instances (host array, a permutation
+ * of 0..batch-1; NULL = instance order).  The default, set by
+ * ucn_problem_create, is largest estimated work first, so that the long solves
+ * of an uneven batch start in the first wave.  Results do not depend on it.
+ * Synchronous (copies the permutation).  Errors: UCN_EINVAL, UCN_ECUDA. */
+ucn_status ucn_problem_set_order(ucn_problem* prob, const int* order);
+
 /* Number of elements of the packed state / trajectory buffers. */
 long long ucn_total_x(const ucn_problem* prob);
 long long ucn_total_u(const ucn_problem* prob);

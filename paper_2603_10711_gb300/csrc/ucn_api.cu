@@ -83,6 +83,7 @@ struct ucn_problem {
   long long smem_bytes;
   int threads;
   int* node_inst;
+  int* order_d;
 };
 
 namespace {
@@ -199,6 +200,19 @@ ucn_status ucn_problem_create(const ucn_problem_desc* d, ucn_problem** out) {
   COPY(sets, d->sets ? d->sets : zeros_sets.data(), (size_t)B * 4);
   int* ni = nullptr;
   COPY(ni, node_inst.empty() ? zeros_nobs.data() : node_inst.data(), std::max<size_t>(node_inst.size(), 1));
+  // default CTA order of the fused solve: largest estimated work first
+  // (nodes x (1 + obstacles / 8)), ties by index -- a longest-processing-time
+  // schedule for uneven batches; results do not depend on it
+  std::vector<int> order(B);
+  for (int b = 0; b < B; ++b) order[b] = b;
+  {
+    std::vector<double> w(B);
+    for (int b = 0; b < B; ++b)
+      w[b] = (d->horizon[b] + 1.0) * (1.0 + ((d->model == UCN_MODEL_QUAD12 && d->max_obs > 0) ? d->n_obs[b] / 8.0 : 0.0));
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return w[x] > w[y]; });
+  }
+  int* ord = nullptr;
+  COPY(ord, order.data(), B);
   double* sabs = nullptr;
   COPY(sabs, (const double*)nullptr, (size_t)ts);
 #undef COPY
@@ -213,7 +227,9 @@ ucn_status ucn_problem_create(const ucn_problem_desc* d, ucn_problem** out) {
   P.defect_tol = d->defect_tol; P.step_tol = d->step_tol;
   P.timeout_ns = (unsigned long long)((d->timeout_s > 0 ? d->timeout_s : 60.0) * 1e9);
   P.state_abs = sabs;
+  P.order = ord;
   p->node_inst = ni;
+  p->order_d = ord;
   // per-node storage: shared memory when one instance fits (small models then keep
   // their matrices in registers), else a structure-of-arrays slice of global memory
   const int tsize = d->precision == UCN_PREC_FP64 ? 8 : 4;
@@ -240,6 +256,25 @@ ucn_status ucn_problem_create(const ucn_problem_desc* d, ucn_problem** out) {
     P.ws = ws;
   }
   *out = p;
+  return UCN_OK;
+}
+
+ucn_status ucn_problem_set_order(ucn_problem* p, const int* order) {
+  g_err[0] = 0;
+  if (!p) return fail(UCN_EINVAL, "null problem");
+  std::vector<int> o(p->batch);
+  if (order) {
+    std::vector<char> seen(p->batch, 0);
+    for (int b = 0; b < p->batch; ++b) {
+      if (order[b] < 0 || order[b] >= p->batch || seen[order[b]]) return fail(UCN_EINVAL, "order is not a permutation of 0..batch-1");
+      seen[order[b]] = 1;
+      o[b] = order[b];
+    }
+  } else {
+    for (int b = 0; b < p->batch; ++b) o[b] = b;
+  }
+  const cudaError_t e = cudaMemcpy(p->order_d, o.data(), sizeof(int) * p->batch, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return fail(UCN_ECUDA, "order copy: %s", cudaGetErrorString(e));
   return UCN_OK;
 }
 

@@ -41,6 +41,7 @@ struct ProblemDev {
   unsigned long long timeout_ns;
   double* state_abs;       // exported ADMM state, absolute FP64 (soff layout)
   char* ws;                // per-instance node storage when it does not fit in shared memory
+  const int* order;        // CTA -> instance map of the fused solve (NULL: identity)
 };
 
 // Fixed part of a node record: compile-time element offsets of every per-node
@@ -1073,7 +1074,9 @@ __global__ void __launch_bounds__(MAX_THREADS) scp_kernel(ProblemDev P, Layout L
   constexpr int NX = M::NX, NU = M::NU, NN = NX + NU;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ InstShared sh;
-  const int b = blockIdx.x;
+  // instances are taken in the order given (largest first by default), so that
+  // the long solves of an uneven batch start in the first wave
+  const int b = P.order ? P.order[blockIdx.x] : (int)blockIdx.x;
   constexpr bool AOS = SMEM;
   Node<T, AOS> nd = make_node<T, SMEM>(P, L, smem, b);
   MatsFor<M, T, AOS> MT;

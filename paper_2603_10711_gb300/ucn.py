@@ -80,6 +80,8 @@ def lib():
             for f in ("ucn_total_x", "ucn_total_u", "ucn_state_size"):
                 getattr(L, f).argtypes = [vp]
                 getattr(L, f).restype = C.c_longlong
+            L.ucn_problem_set_order.argtypes = [vp, _ip]
+            L.ucn_problem_set_order.restype = C.c_int
             L.ucn_linearize.argtypes = [vp, vp, vp, vp, vp, vp, vp]
             L.ucn_linearize.restype = C.c_int
             L.ucn_admm_solve.argtypes = [vp, vp, vp, vp, vp, vp, vp, C.c_int, C.c_int, vp, vp, vp, vp, vp]
@@ -186,6 +188,15 @@ def ucn_problem_create(desc: ProblemDesc):
 
 def ucn_problem_destroy(h):
     lib().ucn_problem_destroy(h)
+
+
+def ucn_problem_set_order(h, order=None):
+    """CTA -> instance order of the fused solve (None: instance order)."""
+    if order is None:
+        _check(lib().ucn_problem_set_order(h, None))
+    else:
+        o = np.ascontiguousarray(order, dtype=np.int32)
+        _check(lib().ucn_problem_set_order(h, o.ctypes.data_as(_ip)))
 
 
 def ucn_total_x(h):

@@ -1,0 +1,78 @@
+"""Uneven-horizon batching on the GPU: instance order, size classes on
+concurrent streams, CUDA-graph replay and the autotuner give the same
+solves as one plain launch, and those match the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2603_10711_gb300 import batching, ucn  # noqa: E402
+
+
+def rel_err(a, b):
+    return float(np.abs(a - b).max() / max(1.0, np.abs(b).max()))
+
+
+def uneven(B=10, prec_settings=None):
+    return W.quad_box(B, seed=9, N_range=(6, 45), obs_range=(2, 8),
+                      settings=dict(scp_iters=6, admm_iters=60, stop=0) if prec_settings is None else prec_settings)
+
+
+def test_instance_order_does_not_change_results():
+    prob = uneven()
+    s = ucn.Solver(prob, precision=ucn.UCN_PREC_FP64)
+    s.scp_solve(); torch.cuda.synchronize()
+    x1 = s.x_out.cpu().numpy().copy(); st1 = s.stats_host().copy()
+    ucn.ucn_problem_set_order(s.handle, None)           # instance order
+    s.scp_solve(); torch.cuda.synchronize()
+    np.testing.assert_array_equal(s.x_out.cpu().numpy(), x1)
+    rev = np.arange(prob.batch)[::-1].copy()
+    ucn.ucn_problem_set_order(s.handle, rev)
+    s.scp_solve(); torch.cuda.synchronize()
+    np.testing.assert_array_equal(s.x_out.cpu().numpy(), x1)
+    np.testing.assert_array_equal(s.stats_host()["scp_iters"], st1["scp_iters"])
+    with pytest.raises(ucn.UcnError):
+        ucn.ucn_problem_set_order(s.handle, np.zeros(prob.batch, np.int32))
+    s.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(ucn.UCN_PREC_FP64, 1e-9), (ucn.UCN_PREC_FP32_REFINE, 1e-4)])
+def test_size_classes_match_single_launch_and_oracle(prec, tol):
+    prob = uneven()
+    cs = batching.ClassedSolver(prob, splits=[16, 32], precision=prec)
+    assert len(cs.classes) >= 2
+    cs.solve(); torch.cuda.synchronize()
+    xc, uc = cs.trajectories()
+    cs.close()
+    xr, ur, sr, _ = oracle.scp_solve(prob)
+    assert rel_err(xc, xr) <= tol and rel_err(uc, ur) <= tol
+
+
+def test_graph_replay_matches_direct_launch():
+    prob = uneven(prec_settings=dict(scp_iters=4, admm_iters=40, stop=0))
+    cs = batching.ClassedSolver(prob, splits=[32], precision=ucn.UCN_PREC_FP32_REFINE)
+    cs.solve(); torch.cuda.synchronize()
+    x_direct, _ = cs.trajectories()
+    for s in cs.solvers:
+        s.x_out.zero_()
+    cs.capture()
+    for s in cs.solvers:
+        s.x_out.zero_()
+    cs.solve(); torch.cuda.synchronize()
+    x_graph, _ = cs.trajectories()
+    np.testing.assert_array_equal(x_graph, x_direct)
+    cs.close()
+
+
+def test_autotune_picks_a_candidate_and_caches(tmp_path):
+    prob = W.quad_box(64, seed=4, N_range=(20, 90), obs_range=(3, 10))
+    path = str(tmp_path / "tune.json")
+    splits, timings = batching.autotune(prob, sample=64, scp_iters=1, cache_path=path)
+    assert [list(map(int, s)) for s in [splits]][0] in [c for c in batching.candidate_splits(prob)]
+    assert len(timings) == len(batching.candidate_splits(prob))
+    again, _ = batching.autotune(prob, sample=64, scp_iters=1, cache_path=path)
+    assert again == splits

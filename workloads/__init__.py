@@ -232,7 +232,8 @@ def quad_box(B=4096, seed=2, N_range=(40, 120), obs_range=(10, 30), dt=0.05,
 
     N_b ~ U{40..120}; 10..30 spheres per instance with radius ~ U[0.2,0.8] m
     and centres uniform in the box; start and goal uniform in the box and at
-    least 0.2 m clear of every sphere (redrawn otherwise).
+    least 0.2 m clear of every sphere (redrawn otherwise).  Settings: rho = 10,
+    200 ADMM iterations per SCP iteration, cap 40, stop at defect <= 1e-5.
     """
     lo = np.array([0.0, 0.0, 0.0]); hi = np.array([10.0, 10.0, 3.0])
     Ns = (N_range[0] + np.floor(uniform(seed, 10, np.arange(B)) * (N_range[1] - N_range[0] + 1))).astype(np.int32)
@@ -253,7 +254,9 @@ def quad_box(B=4096, seed=2, N_range=(40, 120), obs_range=(10, 30), dt=0.05,
                 if nobs[b] == 0 or d.min() > 0.2:
                     break
             arr[b] = p
-    return _quad_common(B, Ns, dt, start, goal, obs_c, obs_r, nobs, settings or {})
+    st = dict(rho_eq=10.0, rho_dyn=10.0, rho_geo=10.0, scp_iters=40, admm_iters=200, stop=1, step_tol=1.0)
+    st.update(settings or {})
+    return _quad_common(B, Ns, dt, start, goal, obs_c, obs_r, nobs, st)
 
 
 # ---------------------------------------------------------------- Mars 3-DOF
