@@ -263,6 +263,8 @@ def run_ours(args, rank, world):
     st64 = s64.stats_host()
     s64.close()
 
+    serving_out = run_serving(args) if (args.serving_requests > 0 and world == 1) else None
+
     flops_ni = flops_per_node_iter(prob.nx, prob.nu, mars_mirror_flops())
     flops_launch = nodeiters / args.steps * flops_ni
     avg = total / args.steps if world == 1 else sum(times) / len(times)
@@ -295,10 +297,39 @@ def run_ours(args, rank, world):
         "gpu_launches": args.steps,
         "clocks": clocks,
     }
+    if serving_out is not None:
+        out["serving"] = serving_out
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         out["cpu_baseline"] = cpu_baseline(args)
     solver.close()
     return out
+
+
+def run_serving(args):
+    """Continuous batching of a mixed Poisson request stream (70% quadrotor,
+    30% Mars descent) in FP32, and the same stream's head solved one request at a
+    time in FP64 (the plain per-request path)."""
+    from paper_2603_10711_gb300 import serving, ucn
+    stream = W.serving_stream(args.serving_requests, rate=args.serving_rate, seed=4)
+    qs, ms = W.quad_box(1).settings, W.mars_batch(1).settings
+
+    def servers(prec, slots):
+        return {1: serving.Server(1, prec, max_slots=slots, max_horizon=120, max_obs=30, lanes=4, settings=qs),
+                2: serving.Server(2, prec, max_slots=slots, max_horizon=200, lanes=4, settings=ms)}
+
+    sv = servers(ucn.UCN_PREC_FP32_REFINE, 512)
+    serving.run_stream(stream[:32], sv)                # warm-up
+    fp32 = serving.run_stream(stream, sv)
+    for s in sv.values():
+        s.close()
+    sv = servers(ucn.UCN_PREC_FP64, 4)
+    n64 = min(len(stream), args.serving_fp64_requests)
+    fp64 = serving.run_stream([(0.0, p) for _, p in stream[:n64]], sv, max_inflight=1)
+    for s in sv.values():
+        s.close()
+    return {"arrival_rate_per_s": args.serving_rate, "requests": len(stream), "mix": "70% quad N 30-120 / 30% Mars N 50-200",
+            "fp32_continuous": fp32, "fp64_per_request": dict(fp64, requests=n64),
+            "latency": "arrival -> result collected (host clock)"}
 
 
 def oracle_sample(args, seconds=None):
@@ -352,6 +383,9 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--cpu-sample", type=int, default=96)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=2000, help="requests of the serving stream (0: skip)")
+    ap.add_argument("--serving-rate", type=float, default=2000.0, help="Poisson arrival rate of the serving stream")
+    ap.add_argument("--serving-fp64-requests", type=int, default=16)
     ap.add_argument("--mode", default="full", choices=["full", "kernel"],
                     help="kernel: time only the fused kernel (profiler captures)")
     ap.add_argument("--scp-iters", type=int, default=0, help="fixed SCP iteration count (0: the workload's cap + stop test)")

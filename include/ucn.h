@@ -217,6 +217,72 @@ ucn_status ucn_scp_solve_noalloc(const ucn_problem_desc* desc, const double* x0_
                                  double* x_out_d, double* u_out_d, ucn_scp_stats* stats_d,
                                  int* status_d, void* stream);
 
+/* ---------------------------------------------------------------- serving
+ * Continuous batching of solves over a preallocated slot pool (not in the
+ * paper; the serving layer around the method).  ucn_serve_create allocates
+ * everything for `max_slots` instances of up to `max_horizon` nodes of one
+ * model and precision, plus `lanes` CUDA streams and a ring of `kept`
+ * finished trajectories (0: 2 * max_slots) for warm starts.  A request is
+ * admitted into a free slot while the sum of admitted footprints stays within
+ * hbm_budget_bytes (0: no budget beyond the slots); each pump launches the
+ * fused SCP kernel (one CTA per instance) over the slots admitted since the
+ * last pump on the next free lane, while earlier launches keep running; a
+ * non-blocking poll returns a finished result and frees its slot.  Every slot
+ * has the same CTA size and layout, so a result does not depend on what it was
+ * batched with.  Solver settings have the meaning they have in ucn_problem_desc. */
+typedef struct {
+  int model, precision, max_slots, max_horizon, max_obs, lanes, kept;
+  double hbm_budget_bytes;
+  double rho_eq, rho_dyn, rho_geo, rho_final;
+  int scp_iters, admm_iters, stop;
+  double tr_init, tr_min, tr_max, w_d, defect_tol, step_tol, timeout_s;
+} ucn_serve_config;
+
+/* One solve request (host memory, copied at submit).  Arrays as one instance
+ * of ucn_problem_desc (model_params [8], sets [4], obs_c [n_obs][3]).  The
+ * initial guess is x_guess [(horizon+1)][nx], u_guess [horizon][nu]; if either
+ * is NULL the guess is the kept trajectory of the finished request
+ * `warm_ticket` (same horizon), copied on the device. */
+typedef struct {
+  int horizon, n_obs;
+  double dt;
+  const double* model_params;
+  const double *Q_diag, *x_ref, *R_diag, *u_ref, *QN_diag, *qN;
+  const double *x_lo, *x_hi, *u_lo, *u_hi, *x_init, *x_target;
+  const unsigned char* term_mask;
+  const double *obs_c, *obs_r, *sets;
+  const double *x_guess, *u_guess;
+  unsigned long long warm_ticket;
+} ucn_request;
+
+/* A finished request.  x, u: caller host buffers ((horizon+1)*nx, horizon*nu
+ * doubles) filled by ucn_serve_poll when not NULL. */
+typedef struct {
+  ucn_scp_stats stats;
+  double *x, *u;
+  unsigned long long ticket;
+  int horizon, reserved;
+} ucn_result;
+
+typedef struct ucn_server ucn_server;
+
+/* Allocates the server.  Errors: UCN_EINVAL, UCN_ENOMEM, UCN_ECUDA. */
+ucn_status ucn_serve_create(const ucn_serve_config* cfg, ucn_server** out);
+/* Synchronises the device and frees everything. */
+void ucn_serve_destroy(ucn_server* srv);
+/* Admits a request into a free slot: UCN_OK and a ticket; UCN_EBUSY when no
+ * slot is free or its footprint exceeds the HBM budget; UCN_EINVAL. */
+ucn_status ucn_serve_submit(ucn_server* srv, const ucn_request* req, unsigned long long* ticket);
+/* Launches every admitted slot on a free lane (stream); *launched = their
+ * count (0 when nothing was admitted).  UCN_EBUSY when every lane is busy. */
+ucn_status ucn_serve_pump(ucn_server* srv, int* launched);
+/* Non-blocking: UCN_OK and the result (the slot is freed and the trajectory
+ * kept for warm starts), UCN_EBUSY while the request is queued or running,
+ * UCN_EINVAL for an unknown ticket, UCN_ECUDA if its launch failed. */
+ucn_status ucn_serve_poll(ucn_server* srv, unsigned long long ticket, ucn_result* res);
+/* Free slots right now (-1 for a NULL server). */
+int ucn_serve_free_slots(ucn_server* srv);
+
 /* Thread-local description of the last error on this thread ("" if none). */
 const char* ucn_last_error(void);
 

@@ -1,0 +1,196 @@
+"""Serving: continuous batching of SCP solves (binding of the ucn_serve_* ABI
+and a host scheduling loop for request streams).
+
+Requests are admitted into the server's slots as they arrive (while slots and
+the HBM budget allow), every pump launches the admitted ones on a free lane
+(stream) while earlier launches are still running, and finished results are
+collected by non-blocking polls.  Latency is arrival -> result collected.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import time
+from collections import deque
+
+import numpy as np
+
+from . import ucn
+
+_dp = C.POINTER(C.c_double)
+_up = C.POINTER(C.c_ubyte)
+
+
+class ServeConfig(C.Structure):
+    _fields_ = [("model", C.c_int), ("precision", C.c_int), ("max_slots", C.c_int), ("max_horizon", C.c_int),
+                ("max_obs", C.c_int), ("lanes", C.c_int), ("kept", C.c_int), ("hbm_budget_bytes", C.c_double),
+                ("rho_eq", C.c_double), ("rho_dyn", C.c_double), ("rho_geo", C.c_double), ("rho_final", C.c_double),
+                ("scp_iters", C.c_int), ("admm_iters", C.c_int), ("stop", C.c_int),
+                ("tr_init", C.c_double), ("tr_min", C.c_double), ("tr_max", C.c_double), ("w_d", C.c_double),
+                ("defect_tol", C.c_double), ("step_tol", C.c_double), ("timeout_s", C.c_double)]
+
+
+class Request(C.Structure):
+    _fields_ = [("horizon", C.c_int), ("n_obs", C.c_int), ("dt", C.c_double), ("model_params", _dp),
+                ("Q_diag", _dp), ("x_ref", _dp), ("R_diag", _dp), ("u_ref", _dp), ("QN_diag", _dp), ("qN", _dp),
+                ("x_lo", _dp), ("x_hi", _dp), ("u_lo", _dp), ("u_hi", _dp), ("x_init", _dp), ("x_target", _dp),
+                ("term_mask", _up), ("obs_c", _dp), ("obs_r", _dp), ("sets", _dp),
+                ("x_guess", _dp), ("u_guess", _dp), ("warm_ticket", C.c_ulonglong)]
+
+
+class Result(C.Structure):
+    _fields_ = [("stats", C.c_ubyte * 128), ("x", _dp), ("u", _dp), ("ticket", C.c_ulonglong),
+                ("horizon", C.c_int), ("reserved", C.c_int)]
+
+
+def _setup(L):
+    if getattr(L, "_serve_ready", False):
+        return L
+    vp = C.c_void_p
+    L.ucn_serve_create.argtypes = [C.POINTER(ServeConfig), C.POINTER(vp)]
+    L.ucn_serve_create.restype = C.c_int
+    L.ucn_serve_destroy.argtypes = [vp]
+    L.ucn_serve_destroy.restype = None
+    L.ucn_serve_submit.argtypes = [vp, C.POINTER(Request), C.POINTER(C.c_ulonglong)]
+    L.ucn_serve_submit.restype = C.c_int
+    L.ucn_serve_pump.argtypes = [vp, C.POINTER(C.c_int)]
+    L.ucn_serve_pump.restype = C.c_int
+    L.ucn_serve_poll.argtypes = [vp, C.c_ulonglong, C.POINTER(Result)]
+    L.ucn_serve_poll.restype = C.c_int
+    L.ucn_serve_free_slots.argtypes = [vp]
+    L.ucn_serve_free_slots.restype = C.c_int
+    L._serve_ready = True
+    return L
+
+
+class Server:
+    """One model / precision slot pool (ucn_serve_create)."""
+
+    def __init__(self, model, precision, max_slots, max_horizon, max_obs=0, lanes=4, settings=None,
+                 hbm_budget_bytes=0.0, kept=0, timeout_s=0.0):
+        self.L = _setup(ucn.lib())
+        s = settings or {}
+        c = ServeConfig()
+        c.model, c.precision, c.max_slots, c.max_horizon = model, precision, max_slots, max_horizon
+        c.max_obs, c.lanes, c.kept, c.hbm_budget_bytes = max_obs, lanes, kept, float(hbm_budget_bytes)
+        c.rho_eq, c.rho_dyn, c.rho_geo = float(s["rho_eq"]), float(s["rho_dyn"]), float(s["rho_geo"])
+        c.rho_final = float(s.get("rho_final", 0.0))
+        c.scp_iters, c.admm_iters, c.stop = int(s["scp_iters"]), int(s["admm_iters"]), int(s.get("stop", 0))
+        c.tr_init, c.tr_min, c.tr_max, c.w_d = float(s["tr_init"]), float(s["tr_min"]), float(s["tr_max"]), float(s["w_d"])
+        c.defect_tol, c.step_tol, c.timeout_s = float(s["defect_tol"]), float(s["step_tol"]), float(timeout_s)
+        self.model, self.nx, self.nu = model, (12 if model == 1 else 7), (4 if model == 1 else 3)
+        self.h = C.c_void_p()
+        rc = self.L.ucn_serve_create(C.byref(c), C.byref(self.h))
+        if rc != ucn.UCN_OK:
+            raise ucn.UcnError(rc, ucn.ucn_last_error())
+
+    def close(self):
+        if self.h is not None and self.h.value:
+            self.L.ucn_serve_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, prob, b=0, x_guess=None, u_guess=None, warm_ticket=0):
+        """Returns (status, ticket).  Without a guess: warm start from `warm_ticket`
+        if given, else the problem's own initial guess."""
+        keep = []
+
+        def d(a):
+            a = np.ascontiguousarray(a, dtype=np.float64)
+            keep.append(a)
+            return a.ctypes.data_as(_dp)
+
+        N = int(prob.N[b])
+        r = Request()
+        r.horizon, r.dt = N, float(prob.dt[b])
+        r.n_obs = int(prob.nobs[b]) if prob.model == 1 else 0
+        r.model_params = d(prob.params[b])
+        r.Q_diag, r.x_ref, r.R_diag, r.u_ref = d(prob.Qd[b]), d(prob.xref[b]), d(prob.Rd[b]), d(prob.uref[b])
+        r.QN_diag, r.qN = d(prob.QNd[b]), d(prob.qN[b])
+        r.x_lo, r.x_hi, r.u_lo, r.u_hi = d(prob.xlo[b]), d(prob.xhi[b]), d(prob.ulo[b]), d(prob.uhi[b])
+        r.x_init, r.x_target = d(prob.xinit[b]), d(prob.xtarget[b])
+        tm = np.ascontiguousarray(prob.tmask[b], dtype=np.uint8); keep.append(tm)
+        r.term_mask = tm.ctypes.data_as(_up)
+        if r.n_obs > 0:
+            r.obs_c, r.obs_r = d(prob.obs_c[b, :r.n_obs]), d(prob.obs_r[b, :r.n_obs])
+        r.sets = d(prob.sets[b])
+        if warm_ticket:
+            r.warm_ticket = int(warm_ticket)
+        else:
+            xo, uo = prob.xoff[b], prob.uoff[b]
+            xg = prob.xguess[xo:xo + N + 1] if x_guess is None else x_guess
+            ug = prob.uguess[uo:uo + N] if u_guess is None else u_guess
+            r.x_guess, r.u_guess = d(xg), d(ug)
+        t = C.c_ulonglong(0)
+        rc = self.L.ucn_serve_submit(self.h, C.byref(r), C.byref(t))
+        if rc not in (ucn.UCN_OK, ucn.UCN_EBUSY):
+            raise ucn.UcnError(rc, ucn.ucn_last_error())
+        return rc, int(t.value)
+
+    def pump(self):
+        n = C.c_int(0)
+        rc = self.L.ucn_serve_pump(self.h, C.byref(n))
+        if rc not in (ucn.UCN_OK, ucn.UCN_EBUSY):
+            raise ucn.UcnError(rc, ucn.ucn_last_error())
+        return rc, int(n.value)
+
+    def poll(self, ticket, horizon=None, trajectories=True):
+        """(status, result dict or None); status UCN_EBUSY while not finished."""
+        res = Result()
+        x = u = None
+        if trajectories and horizon is not None:
+            x = np.zeros((horizon + 1, self.nx)); u = np.zeros((horizon, self.nu))
+            res.x, res.u = x.ctypes.data_as(_dp), u.ctypes.data_as(_dp)
+        rc = self.L.ucn_serve_poll(self.h, C.c_ulonglong(ticket), C.byref(res))
+        if rc == ucn.UCN_EBUSY:
+            return rc, None
+        if rc != ucn.UCN_OK:
+            raise ucn.UcnError(rc, ucn.ucn_last_error())
+        st = np.frombuffer(bytes(res.stats), dtype=ucn.STATS_DTYPE)[0]
+        return rc, {"ticket": int(res.ticket), "horizon": int(res.horizon), "stats": st, "x": x, "u": u}
+
+    def free_slots(self):
+        return int(self.L.ucn_serve_free_slots(self.h))
+
+
+def run_stream(stream, servers, max_inflight=None, time_scale=1.0):
+    """Replay a request stream [(arrival_s, Problem)] against `servers`
+    (dict model -> Server) in real time.  max_inflight=1 gives the one-at-a-time
+    (per-request) path.  Returns latencies and throughput."""
+    pending = deque(sorted(stream, key=lambda r: r[0]))
+    waiting = deque()
+    inflight = {}
+    lat, defects = [], []
+    n = len(pending)
+    t0 = time.perf_counter()
+    while len(lat) < n:
+        now = (time.perf_counter() - t0) / time_scale
+        while pending and pending[0][0] <= now:
+            waiting.append(pending.popleft())
+        while waiting and (max_inflight is None or len(inflight) < max_inflight):
+            arr, p = waiting[0]
+            srv = servers[p.model]
+            rc, ticket = srv.submit(p)
+            if rc == ucn.UCN_EBUSY:
+                break
+            waiting.popleft()
+            inflight[(p.model, ticket)] = (arr, int(p.N[0]))
+        for srv in servers.values():
+            srv.pump()
+        for key in list(inflight):
+            model, ticket = key
+            rc, res = servers[model].poll(ticket, trajectories=False)
+            if rc == ucn.UCN_OK:
+                arr, N = inflight.pop(key)
+                lat.append((time.perf_counter() - t0) / time_scale - arr)
+                defects.append(float(res["stats"]["defect"]))
+    elapsed = time.perf_counter() - t0
+    lat = np.array(lat)
+    d = np.array(defects)
+    return {"completed": n, "elapsed_s": elapsed, "solves_per_s": float(np.sum(d <= 1e-5)) / elapsed,
+            "requests_per_s": n / elapsed, "pass_rate": float(np.mean(d <= 1e-5)),
+            "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99))}

@@ -364,3 +364,30 @@ def double_integrator(seed=0, N=3, nx=2, nu=1, dt=0.1):
     q = draw((N + 1, nx)); r = draw((N, nu))
     x0 = draw((nx,))
     return dict(A=A, B=Bm, d=d, Q=Q, R=R, M=M, q=q, r=r, x0=x0, N=N, nx=nx, nu=nu)
+
+
+# ---------------------------------------------------------------- serving stream
+def serving_stream(n: int, rate: float, seed: int = 4, quad_share: float = 0.7):
+    """A Poisson request stream mixing quadrotor and Mars-descent solves.
+
+    Arrival gaps ~ Exp(rate) (inverse transform of the counter generator).
+    70% quadrotor (N ~ U{30..120}, 5..30 obstacles in the 10 x 10 x 3 m box)
+    and 30% Mars descent (N ~ U{50..200}, t_f = 60 s), each a one-instance
+    Problem with its workload's solver settings.  Returns a list of
+    (arrival_time_s, Problem)."""
+    u_gap = uniform(seed, 41, np.arange(n))
+    t = np.cumsum(-np.log1p(-u_gap) / rate)
+    kind = uniform(seed, 42, np.arange(n)) < quad_share
+    u_n = uniform(seed, 43, np.arange(n))
+    u_o = uniform(seed, 44, np.arange(n))
+    out = []
+    for k in range(n):
+        if kind[k]:
+            N = 30 + int(u_n[k] * 91)
+            no = 5 + int(u_o[k] * 26)
+            p = quad_box(1, seed=1000 + k, N_range=(N, N), obs_range=(no, no))
+        else:
+            N = 50 + int(u_n[k] * 151)
+            p = mars_batch(1, seed=5000 + k, N=N)
+        out.append((float(t[k]), p))
+    return out
