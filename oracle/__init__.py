@@ -61,6 +61,7 @@ class OrcProblem(C.Structure):
         ("scp_iters", C.c_int), ("admm_iters", C.c_int), ("stop", C.c_int),
         ("tr_init", C.c_double), ("tr_min", C.c_double), ("tr_max", C.c_double), ("w_d", C.c_double),
         ("defect_tol", C.c_double), ("step_tol", C.c_double), ("vc_weight", C.c_double),
+        ("group", C.c_int),
     ]
 
 
@@ -210,6 +211,7 @@ class _Pinned:
         o.tr_init, o.tr_min, o.tr_max = float(s["tr_init"]), float(s["tr_min"]), float(s["tr_max"])
         o.w_d, o.defect_tol, o.step_tol = float(s["w_d"]), float(s["defect_tol"]), float(s["step_tol"])
         o.vc_weight = float(s.get("vc_weight", 0.0))
+        o.group = int(s.get("group", 1))
         self.c = o
 
 

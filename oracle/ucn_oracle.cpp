@@ -468,20 +468,33 @@ void reseed_mirrors(const QP& qp, State& st) {
 
 struct AdmmStats { double primal = 0, dual = 0; int ok = 1; };
 
-// `iters` ADMM iterations (Sec. III-B, Steps 1-4) on the QP, in place.
-AdmmStats admm_run(const QP& qp, State& st, int iters) {
-  AdmmStats out;
+// Work space of one ADMM call: the cached factors (H_i is constant within an
+// SCP iteration) and what the last iteration's residuals need.
+struct AdmmWork {
+  std::vector<std::vector<double>> L;
+  std::vector<double> dd, zold, xhold, uhold, sold;
+};
+
+bool admm_prepare(const QP& qp, AdmmWork& wk) {
+  const int N = qp.N, nx = qp.nx, nu = qp.nu, n1 = nx + nu;
+  wk.L.assign(N + 1, std::vector<double>());
+  for (int i = 0; i <= N; ++i) {
+    wk.L[i] = build_H(qp, i);
+    if (!cholesky(wk.L[i], (i < N) ? n1 : nx)) return false;
+  }
+  wk.dd.assign(N * nx, 0.0);
+  return true;
+}
+
+// First part of one ADMM iteration: Step 1, the linearised propagation,
+// Step 2 and Step 3.
+void admm_first_part(const QP& qp, State& st, AdmmWork& wk, bool last) {
   const int N = qp.N, nx = qp.nx, nu = qp.nu, n1 = nx + nu, mb = qp.maxblk;
   const double re = qp.rho_eq, rd = qp.rho_dyn, rg = qp.rho_geo;
-  // The factor is cached for the whole call (H_i is constant within an SCP iteration).
-  std::vector<std::vector<double>> L(N + 1);
-  for (int i = 0; i <= N; ++i) {
-    L[i] = build_H(qp, i);
-    if (!cholesky(L[i], (i < N) ? n1 : nx)) { out.ok = 0; return out; }
-  }
-  std::vector<double> dd(N * nx), zold, xhold, uhold, sold;
+  const std::vector<std::vector<double>>& L = wk.L;
+  std::vector<double>& dd = wk.dd;
   double g[32], xi[32], y[3], w[16];
-  for (int it = 0; it < iters; ++it) {
+  (void)re;
     // ---- Step 1: per-node KKT solve H_i xi_i = g_i
     for (int i = 0; i <= N; ++i) {
       const QPNode& nd = qp.node[i];
@@ -530,8 +543,7 @@ AdmmStats admm_run(const QP& qp, State& st, int iters) {
         dd[i * nx + r] = acc;
       }
     }
-    const bool last = (it == iters - 1);
-    if (last) { zold = st.z; xhold = st.xh; uhold = st.uh; sold = st.s; }
+    if (last) { wk.zold = st.z; wk.xhold = st.xh; wk.uhold = st.uh; wk.sold = st.s; }
     // ---- Step 2: dynamic consensus, Eq. (5)
     for (int i = 1; i <= N; ++i)
       for (int j = 0; j < nx; ++j)
@@ -559,6 +571,14 @@ AdmmStats admm_run(const QP& qp, State& st, int iters) {
         proj_block(B.kind, dim, B.p0, t, &st.s[(i * mb + b) * 3]);
       }
     }
+}
+
+// Second part: Step 4 (dual ascent) and, on the last iteration, the residuals.
+void admm_second_part(const QP& qp, State& st, AdmmWork& wk, bool last, AdmmStats& out) {
+  const int N = qp.N, nx = qp.nx, nu = qp.nu, n1 = nx + nu, mb = qp.maxblk;
+  const double re = qp.rho_eq, rd = qp.rho_dyn, rg = qp.rho_geo;
+  std::vector<double>& dd = wk.dd;
+  double xi[32], y[3], w[16];
     // ---- Step 4: dual ascent, Eq. (8) and its analogues
     for (int i = 1; i <= N; ++i)
       for (int j = 0; j < nx; ++j) {
@@ -607,15 +627,15 @@ AdmmStats admm_run(const QP& qp, State& st, int iters) {
         double sv[32];
         for (int c = 0; c < n; ++c) sv[c] = 0.0;
         for (int j = 0; j < nx; ++j) {
-          sv[j] += rg * (st.xh[i * nx + j] - xhold[i * nx + j]);
-          if (i > 0) sv[j] += re * (st.z[i * nx + j] - zold[i * nx + j]);
+          sv[j] += rg * (st.xh[i * nx + j] - wk.xhold[i * nx + j]);
+          if (i > 0) sv[j] += re * (st.z[i * nx + j] - wk.zold[i * nx + j]);
         }
         if (i < N) {
-          for (int k = 0; k < nx; ++k) w[k] = rd * (st.z[(i + 1) * nx + k] - zold[(i + 1) * nx + k]);
+          for (int k = 0; k < nx; ++k) w[k] = rd * (st.z[(i + 1) * nx + k] - wk.zold[(i + 1) * nx + k]);
           for (int j = 0; j < nx; ++j) for (int k = 0; k < nx; ++k) sv[j] += nd.A[k * nx + j] * w[k];
           for (int j = 0; j < nu; ++j) {
             for (int k = 0; k < nx; ++k) sv[nx + j] += nd.B[k * nu + j] * w[k];
-            sv[nx + j] += rg * (st.uh[i * nu + j] - uhold[i * nu + j]);
+            sv[nx + j] += rg * (st.uh[i * nu + j] - wk.uhold[i * nu + j]);
           }
         }
         for (int b = 0; b < mb; ++b) {
@@ -623,13 +643,24 @@ AdmmStats admm_run(const QP& qp, State& st, int iters) {
           if (B.kind == BLK_NONE) continue;
           for (int c = 0; c < n; ++c)
             for (int k = 0; k < blk_dim(B.kind); ++k)
-              sv[c] += rg * B.G[k * n + c] * (st.s[(i * mb + b) * 3 + k] - sold[(i * mb + b) * 3 + k]);
+              sv[c] += rg * B.G[k * n + c] * (st.s[(i * mb + b) * 3 + k] - wk.sold[(i * mb + b) * 3 + k]);
         }
         for (int c = 0; c < n; ++c) rdl += sv[c] * sv[c];
       }
       out.primal = std::sqrt(rp);
       out.dual = std::sqrt(rdl);
     }
+}
+
+// `iters` ADMM iterations (Sec. III-B, Steps 1-4) on the QP, in place.
+AdmmStats admm_run(const QP& qp, State& st, int iters) {
+  AdmmStats out;
+  AdmmWork wk;
+  if (!admm_prepare(qp, wk)) { out.ok = 0; return out; }
+  for (int it = 0; it < iters; ++it) {
+    const bool last = (it == iters - 1);
+    admm_first_part(qp, st, wk, last);
+    admm_second_part(qp, st, wk, last, out);
   }
   return out;
 }
@@ -656,6 +687,7 @@ struct OrcProblem {
   double rho_eq, rho_dyn, rho_geo, rho_final;
   int scp_iters, admm_iters, stop;
   double tr_init, tr_min, tr_max, w_d, defect_tol, step_tol, vc_weight;
+  int group;              // scenarios per group (1: independent instances)
 };
 
 }  // extern "C"
@@ -1008,6 +1040,152 @@ void scp_instance(const OrcProblem& P, int b, const double* xg, const double* ug
   S[5] = radius; S[6] = last_step; S[7] = iters_run; S[8] = accepted; S[9] = mask; S[10] = status;
 }
 
+// Non-anticipativity of the robust MPC (Sec. IV-A): after Step 3 the first
+// control mirror of every scenario becomes the projection of the scenarios'
+// Step-3 arguments u_0 + nu_u,0 / rho_geo onto {u_0^(1) = ... = u_0^(K)}
+// intersected with every scenario's box -- the clamped average.
+void consensus_u0(const std::vector<QP>& qps, std::vector<State>& sts) {
+  const int K = (int)qps.size(), nu = qps[0].nu;
+  const double rg = qps[0].rho_geo;
+  for (int j = 0; j < nu; ++j) {
+    double sum = 0.0, lo = -INFINITY, hi = INFINITY;
+    for (int k = 0; k < K; ++k) {
+      sum += sts[k].u[j] + sts[k].nuu[j] / rg;
+      lo = std::max(lo, qps[k].node[0].ulo[j]);
+      hi = std::min(hi, qps[k].node[0].uhi[j]);
+    }
+    const double v = std::min(std::max(sum / K, lo), hi);
+    for (int k = 0; k < K; ++k) sts[k].uh[j] = v;
+  }
+}
+
+// SCP of one group of K scenarios (instances b0 .. b0+K-1) sharing the first
+// control.  The scenarios' ADMM iterations run in lockstep with the consensus
+// step between Step 3 and Step 4; the acceptance test is taken on the group
+// (sums of merit and model over the scenarios, one trust radius, one
+// decision), so accepted nominals keep a common first control.
+void scp_group(const OrcProblem& P, int b0, int K, const double* xg_all, const double* ug_all,
+               double* xout_all, double* uout_all, double* stat, double* log) {
+  const int nx = P.nx, nu = P.nu;
+  std::vector<std::vector<double>> xbar(K), ubar(K), A(K), B(K), d(K), fnom(K);
+  std::vector<QP> qps(K);
+  std::vector<State> sts(K);
+  std::vector<AdmmWork> wks(K);
+  std::vector<AdmmStats> ass(K);
+  for (int k = 0; k < K; ++k) {
+    const int b = b0 + k, N = P.N[b];
+    xbar[k].assign(xg_all + P.xoff[b] * nx, xg_all + (P.xoff[b] + N + 1) * nx);
+    ubar[k].assign(ug_all + P.uoff[b] * nu, ug_all + (P.uoff[b] + N) * nu);
+    A[k].resize(N * nx * nx); B[k].resize(N * nx * nu); d[k].resize(N * nx); fnom[k].resize(N * nx);
+  }
+  double radius = P.tr_init, mask = 0.0, last_step = 0.0;
+  int status = ST_OK, accepted = 0, iters_run = 0;
+  const int Kscp = P.scp_iters;
+  std::vector<double> fc(nx);
+  for (int it_scp = 0; it_scp < Kscp; ++it_scp) {
+    double fac = 1.0;
+    if (P.rho_final > 0.0 && Kscp > 1) fac = std::pow(P.rho_final / P.rho_geo, (double)it_scp / (Kscp - 1));
+    const double re = P.rho_eq * fac, rd = P.rho_dyn * fac, rg = P.rho_geo * fac;
+    bool ok = true;
+    for (int k = 0; k < K; ++k) {
+      const int b = b0 + k, N = P.N[b];
+      const double* prm = P.params + b * 8;
+      for (int i = 0; i < N; ++i)
+        orc_linearize(P.model, prm, P.dt[b], &xbar[k][i * nx], &ubar[k][i * nu], &A[k][i * nx * nx],
+                      &B[k][i * nx * nu], &d[k][i * nx], &fnom[k][i * nx]);
+      build_qp(P, b, xbar[k].data(), ubar[k].data(), A[k].data(), B[k].data(), d[k].data(), radius, re, rd, rg, qps[k]);
+      if (it_scp == 0) init_state(qps[k], xbar[k].data(), ubar[k].data(), sts[k]);
+      else reseed_mirrors(qps[k], sts[k]);
+      ok = admm_prepare(qps[k], wks[k]) && ok;
+    }
+    ++iters_run;
+    if (!ok) { status = ST_NUMERIC; break; }
+    for (int it = 0; it < P.admm_iters; ++it) {
+      const bool last = (it == P.admm_iters - 1);
+      for (int k = 0; k < K; ++k) admm_first_part(qps[k], sts[k], wks[k], last);
+      consensus_u0(qps, sts);
+      for (int k = 0; k < K; ++k) admm_second_part(qps[k], sts[k], wks[k], last, ass[k]);
+    }
+    double Jn = 0.0, Jc = 0.0, Lc = 0.0, dmax = 0.0, step = 0.0;
+    std::vector<double> dmax_k(K, 0.0);
+    for (int k = 0; k < K; ++k) {
+      const int b = b0 + k, N = P.N[b];
+      const double* prm = P.params + b * 8;
+      const std::vector<double>& xc = sts[k].xh;
+      const std::vector<double>& uc = sts[k].uh;
+      double nl_nom = 0.0, nl_c = 0.0, lin_c = 0.0;
+      for (int i = 0; i < N; ++i) {
+        rk4<double>(P.model, prm, P.dt[b], &xc[i * nx], &uc[i * nu], fc.data());
+        for (int j = 0; j < nx; ++j) {
+          nl_nom += std::fabs(fnom[k][i * nx + j] - xbar[k][(i + 1) * nx + j]);
+          const double e = fc[j] - xc[(i + 1) * nx + j];
+          nl_c += std::fabs(e);
+          dmax_k[k] = std::max(dmax_k[k], std::fabs(e));
+          double lin = d[k][i * nx + j];
+          for (int c = 0; c < nx; ++c) lin += A[k][(i * nx + j) * nx + c] * xc[i * nx + c];
+          for (int c = 0; c < nu; ++c) lin += B[k][(i * nx + j) * nu + c] * uc[i * nu + c];
+          lin_c += std::fabs(lin - xc[(i + 1) * nx + j]);
+        }
+      }
+      for (size_t e = 0; e < xc.size(); ++e) step = std::max(step, std::fabs(xc[e] - xbar[k][e]));
+      for (size_t e = 0; e < uc.size(); ++e) step = std::max(step, std::fabs(uc[e] - ubar[k][e]));
+      const double cn = traj_cost(P, b, xbar[k].data(), ubar[k].data());
+      const double cc = traj_cost(P, b, xc.data(), uc.data());
+      Jn += cn + P.w_d * nl_nom; Jc += cc + P.w_d * nl_c; Lc += cc + P.w_d * lin_c;
+      dmax = std::max(dmax, dmax_k[k]);
+    }
+    const double den = Jn - Lc, num = Jn - Jc;
+    bool accept;
+    double ratio = NAN;
+    if (den <= 1e-12) {
+      accept = true;
+    } else {
+      ratio = num / den;
+      accept = ratio > 0.0;
+      if (ratio < 0.25) radius *= 0.5;
+      else if (ratio > 0.75) radius = std::min(2.0 * radius, P.tr_max);
+    }
+    radius = std::max(radius, P.tr_min);
+    if (!std::isfinite(Jc)) { accept = false; status = ST_NUMERIC; }
+    if (accept) {
+      for (int k = 0; k < K; ++k) { xbar[k] = sts[k].xh; ubar[k] = sts[k].uh; }
+      ++accepted;
+      mask += std::ldexp(1.0, it_scp);
+    }
+    last_step = step;
+    if (log)
+      for (int k = 0; k < K; ++k) {
+        double* L = &log[((size_t)(b0 + k) * Kscp + it_scp) * NLOG];
+        L[0] = accept; L[1] = ratio; L[2] = Jn; L[3] = Jc; L[4] = Lc; L[5] = dmax; L[6] = radius; L[7] = step;
+      }
+    if (status == ST_NUMERIC) break;
+    if (P.stop && accept && dmax <= P.defect_tol && step <= P.step_tol) break;
+  }
+  for (int k = 0; k < K; ++k) {
+    const int b = b0 + k, N = P.N[b];
+    const double* prm = P.params + b * 8;
+    double dm = 0.0, nl = 0.0;
+    for (int i = 0; i < N; ++i) {
+      rk4<double>(P.model, prm, P.dt[b], &xbar[k][i * nx], &ubar[k][i * nu], fc.data());
+      for (int j = 0; j < nx; ++j) {
+        const double e = std::fabs(fc[j] - xbar[k][(i + 1) * nx + j]);
+        dm = std::max(dm, e);
+        nl += e;
+      }
+    }
+    int st = status;
+    if (!std::isfinite(dm)) st = ST_NUMERIC;
+    if (st == ST_OK && !(dm <= P.defect_tol)) st = ST_NOTCONV;
+    std::copy(xbar[k].begin(), xbar[k].end(), xout_all + P.xoff[b] * nx);
+    std::copy(ubar[k].begin(), ubar[k].end(), uout_all + P.uoff[b] * nu);
+    const double c = traj_cost(P, b, xbar[k].data(), ubar[k].data());
+    double* S = &stat[(size_t)b * NSTAT];
+    for (int j = 0; j < NSTAT; ++j) S[j] = 0.0;
+    S[0] = dm; S[1] = c; S[2] = c + P.w_d * nl; S[3] = ass[k].primal; S[4] = ass[k].dual;
+    S[5] = radius; S[6] = last_step; S[7] = iters_run; S[8] = accepted; S[9] = mask; S[10] = st;
+  }
+}
+
 // Solve every instance; xout/uout packed like the guesses.  nthreads <= 0: OpenMP default.
 int orc_scp_solve(const OrcProblem* P, const double* xg, const double* ug, double* xout, double* uout,
                   double* stat, double* log, int nthreads) {
@@ -1016,6 +1194,10 @@ int orc_scp_solve(const OrcProblem* P, const double* xg, const double* ug, doubl
 #pragma omp parallel for schedule(dynamic, 1)
 #endif
   for (int b = 0; b < P->batch; ++b) {
+    if (P->group > 1) {
+      if (b % P->group == 0) scp_group(*P, b, P->group, xg, ug, xout, uout, stat, log);
+      continue;
+    }
     const long long xo = P->xoff[b], uo = P->uoff[b];
     scp_instance(*P, b, xg + xo * P->nx, ug + uo * P->nu, xout + xo * P->nx, uout + uo * P->nu, stat, log);
   }

@@ -391,3 +391,31 @@ def serving_stream(n: int, rate: float, seed: int = 4, quad_share: float = 0.7):
             p = mars_batch(1, seed=5000 + k, N=N)
         out.append((float(t[k]), p))
     return out
+
+
+# ---------------------------------------------------------------- scenario MPC
+def scenario_mpc(P=256, K=16, seed=3, N=40, n_obs=8, dt=0.05, settings=None) -> Problem:
+    """Scenario-based robust planning (the paper's robust MPC, Sec. IV-A):
+    P problems x K scenarios.  Each problem draws start, goal and `n_obs`
+    spheres in the 10 x 10 x 3 m box (like ``quad_box``); its K scenarios share
+    them and differ in mass ~ U[0.9, 1.1] kg and linear drag ~ U[0, 0.2].
+    Instances b = p*K + s; settings["group"] = K couples the scenarios of a
+    problem through their first control."""
+    base = quad_box(P, seed=seed, N_range=(N, N), obs_range=(n_obs, n_obs), dt=dt)
+    idx = np.repeat(np.arange(P), K)
+    prob = base.subset(idx)
+    mass = U(seed, 51, np.arange(P * K), 0.9, 1.1)
+    cd = U(seed, 52, np.arange(P * K), 0.0, 0.2)
+    prob.params[:, 0] = mass
+    prob.params[:, 6] = cd
+    hover = mass * QUAD_G / 4.0
+    prob.uref[:] = hover[:, None]
+    for b in range(P * K):
+        uo = prob.uoff[b]
+        prob.uguess[uo:uo + N] = hover[b]
+    st = dict(DEFAULT_SETTINGS)
+    st.update(dict(rho_eq=10.0, rho_dyn=10.0, rho_geo=10.0, scp_iters=40, admm_iters=200, stop=1, step_tol=1.0,
+                   group=K))
+    st.update(settings or {})
+    prob.settings = st
+    return prob
