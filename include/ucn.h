@@ -84,6 +84,17 @@ typedef enum { UCN_PREC_FP64 = 0, UCN_PREC_FP32_REFINE = 1 } ucn_precision;
  *                iterative-refinement step per KKT solve; the RK4 rollout,
  *                defects, costs and residual sums in FP64
  *  timeout_s     device time budget per ucn_scp_solve launch (0: 60 s)
+ *  group         scenarios per group for robust MPC (Sec. IV-A); 0 or 1:
+ *                independent instances.  With group = K in [2, 16] the
+ *                instances gK .. gK+K-1 are scenarios of one problem that share
+ *                the first control u_0: ucn_scp_solve runs each group's ADMM
+ *                iterations in lockstep, setting the first control copy of every
+ *                scenario to the average of their Step-3 arguments clamped to the
+ *                intersection of their boxes, and accepts, resizes the trust
+ *                region and stops per group (sums of the merits, maxima of
+ *                defect and step).  Requires the quadrotor model, batch % K == 0
+ *                and records that fit in shared memory; ucn_admm_solve and
+ *                ucn_problem_set_order reject grouped problems
  */
 typedef struct {
   int model, nx, nu, batch;
@@ -103,6 +114,7 @@ typedef struct {
   double tr_init, tr_min, tr_max, w_d, defect_tol, step_tol, vc_weight;
   int precision;
   double timeout_s;
+  int group;
 } ucn_problem_desc;
 
 /* Per-instance result of ucn_scp_solve (device memory, 128 bytes). */
@@ -187,6 +199,22 @@ ucn_status ucn_state_export(ucn_problem* prob, double* state_d, void* stream);
 ucn_status ucn_scp_solve(ucn_problem* prob, const double* x0_d, const double* u0_d,
                          double* x_out_d, double* u_out_d, ucn_scp_stats* stats_d,
                          int* status_d, void* stream);
+
+/* Receding-horizon step for MPC (Sec. IV-A: the controller applies the shared
+ * first control and warm-starts the next solve by shifting the scenario tube).
+ * From the solution (x_d, u_d) of ucn_scp_solve:
+ *   plant    each group's first instance (each instance when group <= 1) is
+ *            the plant: x_init <- RK4(x_init, u_0, dt) with its own model
+ *            parameters and first control, and every instance of the group
+ *            takes that state as its new x_init (the problem's device copy is
+ *            updated in place)
+ *   shift    xg_d, ug_d, packed like the guesses: xg_0 = the new x_init,
+ *            xg_i = x_{i+1} (0 < i < N), xg_N = x_N; ug_i = u_{i+1} (i < N-1),
+ *            ug_{N-1} = u_{N-1}
+ * Device pointers, asynchronous on `stream`; the outputs may not alias the
+ * inputs.  Errors: UCN_EINVAL (null or aliased pointer), UCN_ECUDA. */
+ucn_status ucn_mpc_shift(ucn_problem* prob, const double* x_d, const double* u_d, double* xg_d, double* ug_d,
+                         void* stream);
 
 /* Scratch held by ucn_scp_solve_noalloc on every GPU that loads the library. */
 #define UCN_NOALLOC_SCRATCH_BYTES (64ull << 20)

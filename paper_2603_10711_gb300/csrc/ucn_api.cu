@@ -84,6 +84,7 @@ struct ucn_problem {
   int threads;
   int* node_inst;
   int* order_d;
+  int group;
 };
 
 namespace {
@@ -107,6 +108,46 @@ ucn_status dev_copy(ucn_problem* p, int& nalloc, int fault_at, const V* host, si
 }
 
 cudaStream_t as_stream(void* s) { return (cudaStream_t)s; }
+
+}  // namespace
+
+namespace {
+
+// Receding-horizon step (Sec. IV-A): the plant -- the model of the group's
+// first instance -- takes the applied first control for one step from the
+// current initial state; every instance's next guess is its solution shifted
+// by one node (last node and control repeated) starting at the new state.
+template <class M>
+__global__ void mpc_shift_kernel(ProblemDev P, const double* x, const double* u, double* xg, double* ug) {
+  constexpr int NX = M::NX, NU = M::NU;
+  const int b = blockIdx.x, N = P.N[b];
+  const int lead = P.group > 1 ? b - b % P.group : b;
+  const long long xo = P.xoff[b], uo = P.uoff[b];
+  __shared__ double x0n[NX];
+  if (threadIdx.x == 0) {
+    double xi[NX], ui[NU];
+    for (int j = 0; j < NX; ++j) xi[j] = P.xinit[lead * NX + j];
+    for (int j = 0; j < NU; ++j) ui[j] = u[P.uoff[lead] * NU + j];
+    rk4<M, double>(P.params + lead * 8, P.dt[lead], xi, ui, x0n);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i <= N; i += blockDim.x) {
+    const long long src = xo + (i < N ? i + 1 : N);
+    for (int j = 0; j < NX; ++j) xg[(xo + i) * NX + j] = i == 0 ? x0n[j] : x[src * NX + j];
+    if (i < N) {
+      const long long su = uo + (i + 1 < N ? i + 1 : N - 1);
+      for (int j = 0; j < NU; ++j) ug[(uo + i) * NU + j] = u[su * NU + j];
+    }
+  }
+}
+
+// The problem's initial states <- node 0 of the shifted guesses.
+__global__ void mpc_set_init_kernel(ProblemDev P, double* xinit, const double* xg) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= P.batch * P.nx) return;
+  const int b = k / P.nx, j = k % P.nx;
+  xinit[k] = xg[P.xoff[b] * P.nx + j];
+}
 
 }  // namespace
 
@@ -142,6 +183,10 @@ ucn_status ucn_problem_create(const ucn_problem_desc* d, ucn_problem** out) {
   if (!(d->rho_eq > 0 && d->rho_dyn > 0 && d->rho_geo > 0)) return fail(UCN_EINVAL, "penalties must be positive");
   if (d->scp_iters < 1 || d->admm_iters < 1) return fail(UCN_EINVAL, "iteration counts must be >= 1");
   if (!(d->tr_init > 0 && d->tr_min > 0 && d->tr_max >= d->tr_min)) return fail(UCN_EINVAL, "bad trust-region bounds");
+  const int group = d->group > 1 ? d->group : 1;
+  if (d->group < 0 || group > 16) return fail(UCN_EINVAL, "group must be in [0, 16] (got %d)", d->group);
+  if (group > 1 && d->model != UCN_MODEL_QUAD12) return fail(UCN_EINVAL, "scenario groups need the quadrotor model");
+  if (group > 1 && d->batch % group) return fail(UCN_EINVAL, "batch %d is not a multiple of group %d", d->batch, group);
   int Nmax = 0;
   for (int b = 0; b < d->batch; ++b) {
     const int N = d->horizon[b];
@@ -155,7 +200,7 @@ ucn_status ucn_problem_create(const ucn_problem_desc* d, ucn_problem** out) {
   if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return fail(UCN_ECUDA, "no CUDA device"); }
   ucn_problem* p = new ucn_problem();
   p->model = d->model; p->nx = NX; p->nu = NU; p->batch = d->batch; p->max_obs = d->model == UCN_MODEL_QUAD12 ? d->max_obs : 0;
-  p->Nmax = Nmax; p->precision = d->precision;
+  p->Nmax = Nmax; p->precision = d->precision; p->group = group;
   const int B = d->batch;
   std::vector<long long> xoff(B), uoff(B), soff(B);
   std::vector<int> node_inst;
@@ -228,6 +273,7 @@ ucn_status ucn_problem_create(const ucn_problem_desc* d, ucn_problem** out) {
   P.timeout_ns = (unsigned long long)((d->timeout_s > 0 ? d->timeout_s : 60.0) * 1e9);
   P.state_abs = sabs;
   P.order = ord;
+  P.group = group;
   p->node_inst = ni;
   p->order_d = ord;
   // per-node storage: shared memory when one instance fits (small models then keep
@@ -236,12 +282,16 @@ ucn_status ucn_problem_create(const ucn_problem_desc* d, ucn_problem** out) {
   const bool small = d->model == UCN_MODEL_MARS7;   // SmallModel<Mars7>
   int optin = 0;
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  const long long static_sh = (long long)sizeof(InstShared) + 64;
+  const long long static_sh = (long long)sizeof(InstShared) + (group > 1 ? (long long)sizeof(GroupShared) : 0) + 64;
   p->L = make_layout(d->model, Nmax + 1, p->max_obs, tsize, small);
   p->smem = p->L.bytes + static_sh <= optin;
   if (!p->smem) p->L = make_layout(d->model, Nmax + 1, p->max_obs, tsize, false);
   p->threads = (int)round_up(Nmax + 1, 32);
   p->smem_bytes = p->smem ? p->L.bytes : 0;
+  if (group > 1 && !p->smem) {
+    ucn_problem_destroy(p);
+    return fail(UCN_EINVAL, "scenario groups need node records in shared memory (horizon or obstacle count too large)");
+  }
   P.ws = nullptr;
   if (!p->smem) {
     char* ws = nullptr;
@@ -262,6 +312,7 @@ ucn_status ucn_problem_create(const ucn_problem_desc* d, ucn_problem** out) {
 ucn_status ucn_problem_set_order(ucn_problem* p, const int* order) {
   g_err[0] = 0;
   if (!p) return fail(UCN_EINVAL, "null problem");
+  if (p->group > 1) return fail(UCN_EINVAL, "grouped problems run their clusters in instance order");
   std::vector<int> o(p->batch);
   if (order) {
     std::vector<char> seen(p->batch, 0);
@@ -285,7 +336,7 @@ long long ucn_state_size(const ucn_problem* p) { return p ? p->state_size : -1; 
 static LaunchCfg cfg_of(ucn_problem* p, void* stream) {
   LaunchCfg c;
   c.P = &p->dev; c.L = &p->L; c.smem = p->smem; c.smem_bytes = p->smem_bytes;
-  c.threads = p->threads; c.blocks = p->batch; c.stream = as_stream(stream);
+  c.threads = p->threads; c.blocks = p->batch; c.stream = as_stream(stream); c.group = p->group;
   return c;
 }
 
@@ -307,6 +358,7 @@ ucn_status ucn_admm_solve(ucn_problem* p, const double* xbar_d, const double* ub
   if (!p || !xbar_d || !ubar_d || !A_d || !B_d || !d_d || !radius_d || !xhat_d || !uhat_d || !res_d || !status_d)
     return fail(UCN_EINVAL, "null argument");
   if (iters < 1) return fail(UCN_EINVAL, "iters must be >= 1");
+  if (p->group > 1) return fail(UCN_EINVAL, "the scenario consensus runs inside ucn_scp_solve only");
   const LaunchCfg c = cfg_of(p, stream);
   auto fn = p->model == UCN_MODEL_QUAD12 ? (p->precision == UCN_PREC_FP64 ? quad64_admm : quad32_admm)
                                          : (p->precision == UCN_PREC_FP64 ? mars64_admm : mars32_admm);
@@ -329,10 +381,34 @@ ucn_status ucn_scp_solve(ucn_problem* p, const double* x0_d, const double* u0_d,
   g_err[0] = 0;
   if (!p || !x0_d || !u0_d || !x_out_d || !u_out_d || !stats_d || !status_d) return fail(UCN_EINVAL, "null argument");
   const LaunchCfg c = cfg_of(p, stream);
+  if (p->group > 1) {
+    const cudaError_t e = (p->precision == UCN_PREC_FP64 ? quad64_scp_group : quad32_scp_group)(
+        c, x0_d, u0_d, x_out_d, u_out_d, stats_d, status_d);
+    if (e == cudaErrorInvalidClusterSize)
+      return fail(UCN_EINVAL, "a cluster of %d CTAs (%d threads, %lld B shared memory each) does not fit on the device",
+                  p->group, p->threads, p->smem_bytes);
+    if (e != cudaSuccess) return fail(UCN_ECUDA, "scp group launch: %s", cudaGetErrorString(e));
+    return UCN_OK;
+  }
   auto fn = p->model == UCN_MODEL_QUAD12 ? (p->precision == UCN_PREC_FP64 ? quad64_scp : quad32_scp)
                                          : (p->precision == UCN_PREC_FP64 ? mars64_scp : mars32_scp);
   const cudaError_t e = fn(c, x0_d, u0_d, x_out_d, u_out_d, stats_d, status_d);
   if (e != cudaSuccess) return fail(UCN_ECUDA, "scp launch: %s", cudaGetErrorString(e));
+  return UCN_OK;
+}
+
+ucn_status ucn_mpc_shift(ucn_problem* p, const double* x_d, const double* u_d, double* xg_d, double* ug_d,
+                         void* stream) {
+  g_err[0] = 0;
+  if (!p || !x_d || !u_d || !xg_d || !ug_d) return fail(UCN_EINVAL, "null argument");
+  if ((const double*)xg_d == x_d || (const double*)ug_d == u_d) return fail(UCN_EINVAL, "the shifted guesses may not alias the solution");
+  const cudaStream_t st = as_stream(stream);
+  if (p->model == UCN_MODEL_QUAD12) mpc_shift_kernel<Quad12><<<p->batch, 64, 0, st>>>(p->dev, x_d, u_d, xg_d, ug_d);
+  else mpc_shift_kernel<Mars7><<<p->batch, 64, 0, st>>>(p->dev, x_d, u_d, xg_d, ug_d);
+  const int nx = p->nx;
+  mpc_set_init_kernel<<<(p->batch * nx + 127) / 128, 128, 0, st>>>(p->dev, const_cast<double*>(p->dev.xinit), xg_d);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(UCN_ECUDA, "mpc shift launch: %s", cudaGetErrorString(e));
   return UCN_OK;
 }
 

@@ -25,6 +25,7 @@ struct LaunchCfg {
   int threads;          // CTA size
   int blocks;           // one CTA per instance
   cudaStream_t stream;
+  int group;            // scenarios per thread-block cluster (scenario groups only)
 };
 
 // Launchers, one translation unit per (model, precision) so that the four
@@ -42,5 +43,11 @@ UCN_DECLARE_LAUNCHERS(quad64)
 UCN_DECLARE_LAUNCHERS(quad32)
 UCN_DECLARE_LAUNCHERS(mars64)
 UCN_DECLARE_LAUNCHERS(mars32)
+
+// Scenario groups (quadrotor only): thread-block clusters, one CTA per scenario.
+cudaError_t quad64_scp_group(const LaunchCfg& c, const double* x0, const double* u0, double* xo, double* uo,
+                             ucn_scp_stats* st, int* status);
+cudaError_t quad32_scp_group(const LaunchCfg& c, const double* x0, const double* u0, double* xo, double* uo,
+                             ucn_scp_stats* st, int* status);
 
 }  // namespace ucn

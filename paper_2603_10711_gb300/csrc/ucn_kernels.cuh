@@ -42,6 +42,7 @@ struct ProblemDev {
   double* state_abs;       // exported ADMM state, absolute FP64 (soff layout)
   char* ws;                // per-instance node storage when it does not fit in shared memory
   const int* order;        // CTA -> instance map of the fused solve (NULL: identity)
+  int group;               // scenarios per group (<= 1: independent instances)
 };
 
 // Fixed part of a node record: compile-time element offsets of every per-node
@@ -167,6 +168,26 @@ struct InstShared {
   int fail;
   int accept, stop, status;
 };
+
+// Exchange area of a scenario group (one thread-block cluster, one CTA per
+// scenario), read by the other CTAs through distributed shared memory.
+struct GroupShared {
+  double cons[2][12];   // per ADMM iteration (double-buffered): u_0 argument | lo | hi, absolute (nu <= 4)
+  double u0[4];         // the consensus u-hat_0 of the latest iteration, absolute
+  double acc[8];        // acceptance: merit of the nominal, of the candidate, of the model; defect; step; timeout
+  double flag;          // factorisation failure
+};
+
+// The exchange area exists in the shared memory of group kernels only.
+template <bool GROUP>
+__device__ __forceinline__ GroupShared* group_slot() {
+  if constexpr (GROUP) {
+    __shared__ GroupShared g;
+    return &g;
+  } else {
+    return nullptr;
+  }
+}
 
 // ------------------------------------------------------------------ block reduction
 // Reduces up to 6 FP64 values: entries [0, nsum) summed, [nsum, nval) maxed.
@@ -626,10 +647,17 @@ __device__ void node_reseed(const Node<T, AOS>& nd, const Layout& L, const Inst<
 // threads of the CTA call it.  The LAST instance also accumulates the primal
 // and dual residuals in FP64 (a separate instantiation, so that the hot loop
 // carries no FP64 instruction, not even a predicated-off one).
-template <class M, class T, bool AOS, bool REFINE, bool LAST, class MS>
+//
+// GROUP: the CTA is one scenario of a thread-block cluster whose scenarios
+// share the first control (Sec. IV-A).  After Step 3 the node-0 thread of every
+// CTA publishes its Step-3 argument u_0 + nu_u,0 / rho_geo and its box (both
+// absolute) in `cons`; after one cluster barrier each reads all of them and
+// sets u-hat_0 to the projection onto {equal u_0} intersected with every box,
+// i.e. the average clamped to the common box, before its Step 4.
+template <class M, class T, bool AOS, bool REFINE, bool LAST, bool GROUP, class MS>
 __device__ __forceinline__ void admm_iteration(const Node<T, AOS>& nd, const MS& MT, const Layout& L, const Inst<T>& I,
                                                const NodeConst<M, T>& K, bool active, T re, T rd, T rg,
-                                               T irg, T ired, double& rp, double& rdl) {
+                                               T irg, T ired, double& rp, double& rdl, GroupShared* G, int par) {
   constexpr int NX = M::NX, NU = M::NU, NN = NX + NU;
   const int i = nd.i, N = nd.N;
   constexpr bool last = LAST;
@@ -718,6 +746,15 @@ __device__ __forceinline__ void admm_iteration(const Node<T, AOS>& nd, const MS&
 #pragma unroll
         for (int j = 0; j < NU; ++j) {
           const T nuu = nd.at(Rec<M>::Nuu, j);
+          if constexpr (GROUP) {
+            if (i == 0) {
+              const double ub = nd.dat(Rec<M>::Ubar, j);
+              G->cons[par][j] = ub + (double)(x[NX + j] + nuu * irg);
+              G->cons[par][NU + j] = ub + (double)nd.at(Rec<M>::Ulo, j);
+              G->cons[par][2 * NU + j] = ub + (double)nd.at(Rec<M>::Uhi, j);
+              continue;
+            }
+          }
           const T uh = clampv(x[NX + j] + nuu * irg, nd.at(Rec<M>::Ulo, j), nd.at(Rec<M>::Uhi, j));
           if (last) { sv[NX + j] += rg * (uh - nd.at(Rec<M>::Uh, j)); rp += (double)(x[NX + j] - uh) * (double)(x[NX + j] - uh); }
           nd.at(Rec<M>::Uh, j) = uh;
@@ -726,6 +763,28 @@ __device__ __forceinline__ void admm_iteration(const Node<T, AOS>& nd, const MS&
         node_mirrors<M, T, AOS, NN>(nd, L, I, rg, x, false, last, sv, rp);
       } else {
         node_mirrors<M, T, AOS, NX>(nd, L, I, rg, x, false, last, sv, rp);
+      }
+    }
+    if constexpr (GROUP) {
+      cluster_sync();
+      if (active && i == 0 && i < N) {
+        const unsigned nk = cluster_size();
+#pragma unroll
+        for (int j = 0; j < NU; ++j) {
+          double sum = 0.0, lo = -INFINITY, hi = INFINITY;
+          for (unsigned r = 0; r < nk; ++r) {
+            sum += ld_cluster(&G->cons[par][j], r);
+            lo = fmax(lo, ld_cluster(&G->cons[par][NU + j], r));
+            hi = fmin(hi, ld_cluster(&G->cons[par][2 * NU + j], r));
+          }
+          const double v = fmin(fmax(sum / (double)nk, lo), hi);
+          G->u0[j] = v;
+          const T uh = (T)(v - nd.dat(Rec<M>::Ubar, j));
+          const T nuu = nd.at(Rec<M>::Nuu, j);
+          if (last) { sv[NX + j] += rg * (uh - nd.at(Rec<M>::Uh, j)); rp += (double)(x[NX + j] - uh) * (double)(x[NX + j] - uh); }
+          nd.at(Rec<M>::Uh, j) = uh;
+          nd.at(Rec<M>::Nuu, j) = nuu + rg * (x[NX + j] - uh);
+        }
       }
     }
     if constexpr (LAST) {
@@ -768,15 +827,16 @@ __device__ __forceinline__ void admm_iteration(const Node<T, AOS>& nd, const MS&
 
 // `iters` iterations of Steps 1-4; the primal and dual residuals of the last
 // one (FP64 sums) are returned in res[0..1].
-template <class M, class T, bool AOS, bool REFINE, class MS>
+template <class M, class T, bool AOS, bool REFINE, bool GROUP = false, class MS>
 __device__ __forceinline__ void admm_iterations(const Node<T, AOS>& nd, const MS& MT, const Layout& L, const Inst<T>& I,
                                 const NodeConst<M, T>& K, bool active, T re, T rd, T rg, int iters,
-                                InstShared& sh, double* res) {
+                                InstShared& sh, double* res, GroupShared* G = nullptr) {
   const T irg = T(1) / rg, ired = T(1) / (re + rd);
   double rp = 0.0, rdl = 0.0;
   for (int it = 0; it + 1 < iters; ++it)
-    admm_iteration<M, T, AOS, REFINE, false>(nd, MT, L, I, K, active, re, rd, rg, irg, ired, rp, rdl);
-  admm_iteration<M, T, AOS, REFINE, true>(nd, MT, L, I, K, active, re, rd, rg, irg, ired, rp, rdl);
+    admm_iteration<M, T, AOS, REFINE, false, GROUP>(nd, MT, L, I, K, active, re, rd, rg, irg, ired, rp, rdl, G, it & 1);
+  admm_iteration<M, T, AOS, REFINE, true, GROUP>(nd, MT, L, I, K, active, re, rd, rg, irg, ired, rp, rdl, G,
+                                                 (iters - 1) & 1);
   double v[2] = {rp, rdl};
   block_reduce(sh, v, 2, 2);
   res[0] = sqrt(v[0]);
@@ -1068,15 +1128,26 @@ __device__ __forceinline__ double node_cost(const ProblemDev& P, const Inst<T>& 
 // iterations (T, FP64 residual sums), then the FP64 rollout, defects, merit
 // and trust-region acceptance, and the nominal update -- without leaving
 // the kernel.
-template <class M, class T, bool SMEM, bool REFINE>
+//
+// GROUP: launched as thread-block clusters of P.group CTAs, CTA r of cluster c
+// solving scenario r of problem c (instance c * group + r).  The scenarios run
+// their ADMM iterations in lockstep with the first-control consensus and take
+// every decision as a group: a factorisation failure anywhere stops the group,
+// and acceptance, trust radius, stopping and the time budget are decided on the
+// group's sums (merits) and maxima (defect, step), so that accepted nominals
+// keep one first control.
+template <class M, class T, bool SMEM, bool REFINE, bool GROUP = false>
 __global__ void __launch_bounds__(MAX_THREADS) scp_kernel(ProblemDev P, Layout L, const double* x0, const double* u0,
                                                           double* xout, double* uout, ucn_scp_stats* stats, int* status_out) {
   constexpr int NX = M::NX, NU = M::NU, NN = NX + NU;
+  static_assert(!GROUP || NU <= 4, "GroupShared holds nu <= 4");
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ InstShared sh;
+  GroupShared* G = group_slot<GROUP>();
   // instances are taken in the order given (largest first by default), so that
-  // the long solves of an uneven batch start in the first wave
-  const int b = P.order ? P.order[blockIdx.x] : (int)blockIdx.x;
+  // the long solves of an uneven batch start in the first wave; a scenario group
+  // keeps its cluster's consecutive instances
+  const int b = (GROUP || !P.order) ? (int)blockIdx.x : P.order[blockIdx.x];
   constexpr bool AOS = SMEM;
   Node<T, AOS> nd = make_node<T, SMEM>(P, L, smem, b);
   MatsFor<M, T, AOS> MT;
@@ -1135,14 +1206,32 @@ __global__ void __launch_bounds__(MAX_THREADS) scp_kernel(ProblemDev P, Layout L
       publish_ex2<M, T, AOS>(nd, L, active, rd);
     }
     __syncthreads();
+    if constexpr (GROUP) {
+      // a failed factorisation in any scenario stops the whole group (this
+      // barrier is also the first one, so every CTA of the cluster has started
+      // before any distributed shared memory is read)
+      if (threadIdx.x == 0) G->flag = (double)sh.fail;
+      cluster_sync();
+      if (threadIdx.x == 0) {
+        double f = 0.0;
+        for (unsigned r = 0; r < cluster_size(); ++r) f = fmax(f, ld_cluster(&G->flag, r));
+        sh.fail = f != 0.0;
+      }
+      __syncthreads();
+    }
     if (sh.fail) { if (threadIdx.x == 0) sh.status = ST_NUMERIC; iters_run++; break; }
-    admm_iterations<M, T, AOS, REFINE>(nd, MT, L, I, K, active, re, rd, rg, P.admm_iters, sh, res);
+    admm_iterations<M, T, AOS, REFINE, GROUP>(nd, MT, L, I, K, active, re, rd, rg, P.admm_iters, sh, res, G);
     ++iters_run;
     // ---- candidate (x-hat, u-hat): FP64 rollout, defects, cost, linear model
     double xc[NX], uc[NU], fc[NX];
     if (active) {
       for (int j = 0; j < NX; ++j) { xc[j] = nd.dat(Rec<M>::Xbar, j) + (double)nd.at(Rec<M>::Xh, j); nd.dat(Rec<M>::Xc, j) = xc[j]; }
       for (int j = 0; j < NU; ++j) uc[j] = (i < N) ? nd.dat(Rec<M>::Ubar, j) + (double)nd.at(Rec<M>::Uh, j) : 0.0;
+      if constexpr (GROUP) {
+        // the shared first control exactly (bitwise equal across the group)
+        if (i == 0)
+          for (int j = 0; j < NU; ++j) uc[j] = G->u0[j];
+      }
     }
     __syncthreads();
     double v[6] = {0, 0, 0, 0, 0};   // cost, nl1, lin1 | dinf, step
@@ -1173,9 +1262,31 @@ __global__ void __launch_bounds__(MAX_THREADS) scp_kernel(ProblemDev P, Layout L
       v[4] = (double)st;
     }
     block_reduce(sh, v, 3, 5);
+    bool timed_out = false;
+    if (threadIdx.x == 0) timed_out = globaltimer_ns() - t0 > P.timeout_ns;
+    double Jn = sh.Jn, Jc = v[0] + P.w_d * v[1], Lc = v[0] + P.w_d * v[2];
+    const double Jc_own = Jc;
+    if constexpr (GROUP) {
+      if (threadIdx.x == 0) {
+        G->acc[0] = Jn; G->acc[1] = Jc; G->acc[2] = Lc; G->acc[3] = v[3]; G->acc[4] = v[4];
+        G->acc[5] = timed_out ? 1.0 : 0.0;
+      }
+      cluster_sync();
+      if (threadIdx.x == 0) {
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, m3 = 0.0, m4 = 0.0, to = 0.0;
+        for (unsigned r = 0; r < cluster_size(); ++r) {
+          s0 += ld_cluster(&G->acc[0], r);
+          s1 += ld_cluster(&G->acc[1], r);
+          s2 += ld_cluster(&G->acc[2], r);
+          m3 = fmax(m3, ld_cluster(&G->acc[3], r));
+          m4 = fmax(m4, ld_cluster(&G->acc[4], r));
+          to = fmax(to, ld_cluster(&G->acc[5], r));
+        }
+        Jn = s0; Jc = s1; Lc = s2; v[3] = m3; v[4] = m4; timed_out = to != 0.0;
+      }
+    }
     if (threadIdx.x == 0) {
       // acceptance (the paper omits it; ratio test on an l1 merit)
-      const double Jn = sh.Jn, Jc = v[0] + P.w_d * v[1], Lc = v[0] + P.w_d * v[2];
       const double den = Jn - Lc, num = Jn - Jc;
       double radius2 = sh.radius;
       bool acc_ = true;
@@ -1187,12 +1298,12 @@ __global__ void __launch_bounds__(MAX_THREADS) scp_kernel(ProblemDev P, Layout L
       }
       radius2 = fmax(radius2, P.tr_min);
       if (!isfinite(Jc)) { acc_ = false; sh.status = ST_NUMERIC; }
-      if (acc_) sh.Jn = Jc;
+      if (acc_) sh.Jn = Jc_own;
       sh.radius = radius2;
       sh.accept = acc_;
       int stop = (sh.status == ST_NUMERIC);
       if (P.stop && acc_ && v[3] <= P.defect_tol && v[4] <= P.step_tol) stop = 1;
-      if (globaltimer_ns() - t0 > P.timeout_ns && !stop && k + 1 < Kscp) { sh.status = ST_TIMEOUT; stop = 1; }
+      if (timed_out && !stop && k + 1 < Kscp) { sh.status = ST_TIMEOUT; stop = 1; }
       sh.stop = stop;
     }
     __syncthreads();
@@ -1257,6 +1368,8 @@ __global__ void __launch_bounds__(MAX_THREADS) scp_kernel(ProblemDev P, Layout L
     stats[b] = s;
     status_out[b] = st;
   }
+  // no CTA of a group may exit while another can still read its shared memory
+  if constexpr (GROUP) cluster_sync();
 }
 
 }  // namespace ucn

@@ -1,23 +1,81 @@
-// Launch wrappers, instantiated once per model by ucn_quad.cu / ucn_mars.cu.
+// Launch wrappers, instantiated per (model, precision) by the ucn_<model><bits>*.cu units.
 #pragma once
 #include "ucn_internal.h"
 #include "ucn_kernels.cuh"
 
 namespace ucn {
 
-template <class M, class T, bool R>
-cudaError_t launch_scp_t(const LaunchCfg& c, const double* x0, const double* u0, double* xo, double* uo,
+// One kernel variant per function, so that a translation unit can leave a
+// variant to another one (extern template) and the slow ones compile in parallel.
+template <class M, class T, bool SMEM, bool R>
+cudaError_t launch_scp_v(const LaunchCfg& c, const double* x0, const double* u0, double* xo, double* uo,
                          ucn_scp_stats* st, int* status) {
   const ProblemDev& P = *(const ProblemDev*)c.P;
   const Layout& L = *(const Layout*)c.L;
-  if (c.smem) {
-    auto k = scp_kernel<M, T, true, R>;
+  auto k = scp_kernel<M, T, SMEM, R>;
+  if (SMEM) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem_bytes);
     if (e != cudaSuccess) return e;
-    k<<<c.blocks, c.threads, c.smem_bytes, c.stream>>>(P, L, x0, u0, xo, uo, st, status);
-  } else {
-    scp_kernel<M, T, false, R><<<c.blocks, c.threads, 0, c.stream>>>(P, L, x0, u0, xo, uo, st, status);
   }
+  k<<<c.blocks, c.threads, SMEM ? c.smem_bytes : 0, c.stream>>>(P, L, x0, u0, xo, uo, st, status);
+  return cudaGetLastError();
+}
+
+template <class M, class T, bool R>
+cudaError_t launch_scp_t(const LaunchCfg& c, const double* x0, const double* u0, double* xo, double* uo,
+                         ucn_scp_stats* st, int* status) {
+  return c.smem ? launch_scp_v<M, T, true, R>(c, x0, u0, xo, uo, st, status)
+                : launch_scp_v<M, T, false, R>(c, x0, u0, xo, uo, st, status);
+}
+
+// Scenario groups: thread-block clusters of c.group CTAs (records in shared
+// memory only).  cudaErrorInvalidClusterSize when no such cluster fits on the
+// device (cluster size above 16, or too much shared memory per CTA).
+template <class M, class T, bool R>
+cudaError_t launch_scp_group_t(const LaunchCfg& c, const double* x0, const double* u0, double* xo, double* uo,
+                               ucn_scp_stats* st, int* status) {
+  const ProblemDev& P = *(const ProblemDev*)c.P;
+  const Layout& L = *(const Layout*)c.L;
+  if (!c.smem || c.group < 2 || c.group > 16 || c.blocks % c.group) return cudaErrorInvalidClusterSize;
+  auto k = scp_kernel<M, T, true, R, true>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem_bytes);
+  if (e != cudaSuccess) return e;
+  if (c.group > 8) {
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)c.blocks, 1, 1);
+  cfg.blockDim = dim3((unsigned)c.threads, 1, 1);
+  cfg.dynamicSmemBytes = (size_t)c.smem_bytes;
+  cfg.stream = c.stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = (unsigned)c.group;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int nclusters = 0;
+  e = cudaOccupancyMaxActiveClusters(&nclusters, k, &cfg);
+  if (e != cudaSuccess) return e;
+  if (nclusters < 1) return cudaErrorInvalidClusterSize;
+  return cudaLaunchKernelEx(&cfg, k, P, L, x0, u0, xo, uo, st, status);
+}
+
+template <class M, class T, bool SMEM, bool R>
+cudaError_t launch_admm_v(const LaunchCfg& c, const double* xbar, const double* ubar, const double* A,
+                          const double* B, const double* d, const double* radius, int iters, int warm,
+                          double* xhat, double* uhat, double* res, int* status) {
+  const ProblemDev& P = *(const ProblemDev*)c.P;
+  const Layout& L = *(const Layout*)c.L;
+  auto k = admm_kernel<M, T, SMEM, R>;
+  if (SMEM) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem_bytes);
+    if (e != cudaSuccess) return e;
+  }
+  k<<<c.blocks, c.threads, SMEM ? c.smem_bytes : 0, c.stream>>>(P, L, xbar, ubar, A, B, d, radius, iters, warm,
+                                                                xhat, uhat, res, status);
   return cudaGetLastError();
 }
 
@@ -25,19 +83,8 @@ template <class M, class T, bool R>
 cudaError_t launch_admm_t(const LaunchCfg& c, const double* xbar, const double* ubar, const double* A,
                           const double* B, const double* d, const double* radius, int iters, int warm,
                           double* xhat, double* uhat, double* res, int* status) {
-  const ProblemDev& P = *(const ProblemDev*)c.P;
-  const Layout& L = *(const Layout*)c.L;
-  if (c.smem) {
-    auto k = admm_kernel<M, T, true, R>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem_bytes);
-    if (e != cudaSuccess) return e;
-    k<<<c.blocks, c.threads, c.smem_bytes, c.stream>>>(P, L, xbar, ubar, A, B, d, radius, iters, warm, xhat, uhat,
-                                                      res, status);
-  } else {
-    admm_kernel<M, T, false, R><<<c.blocks, c.threads, 0, c.stream>>>(P, L, xbar, ubar, A, B, d, radius, iters, warm,
-                                                                      xhat, uhat, res, status);
-  }
-  return cudaGetLastError();
+  return c.smem ? launch_admm_v<M, T, true, R>(c, xbar, ubar, A, B, d, radius, iters, warm, xhat, uhat, res, status)
+                : launch_admm_v<M, T, false, R>(c, xbar, ubar, A, B, d, radius, iters, warm, xhat, uhat, res, status);
 }
 
 template <class M, class T>
@@ -71,3 +118,27 @@ cudaError_t launch_linearize_t(const void* Pv, const int* node_inst, long long t
     return launch_linearize_t<MODEL, T>(P, node_inst, total_u, xbar, ubar, A, B, d, stream);              \
   }                                                                                                        \
   }
+
+// Scenario-group solve, one translation unit per (model, precision).
+#define UCN_DEFINE_GROUP_LAUNCHER(NAME, MODEL, T, REFINE)                                                 \
+  namespace ucn {                                                                                          \
+  cudaError_t NAME##_scp_group(const LaunchCfg& c, const double* x0, const double* u0, double* xo,         \
+                               double* uo, ucn_scp_stats* st, int* status) {                               \
+    return launch_scp_group_t<MODEL, T, REFINE>(c, x0, u0, xo, uo, st, status);                           \
+  }                                                                                                        \
+  }
+
+// Explicit instantiation of one kernel variant (SMEM: records in shared memory)
+// in its own translation unit; the UCN_EXTERN_* forms keep it out of the others.
+#define UCN_SCP_V(MODEL, T, SMEM, REFINE)                                                                  \
+  cudaError_t ucn::launch_scp_v<ucn::MODEL, T, SMEM, REFINE>(const ucn::LaunchCfg&, const double*,       \
+                                                             const double*, double*, double*,            \
+                                                             ucn_scp_stats*, int*)
+#define UCN_ADMM_V(MODEL, T, SMEM, REFINE)                                                                 \
+  cudaError_t ucn::launch_admm_v<ucn::MODEL, T, SMEM, REFINE>(                                           \
+      const ucn::LaunchCfg&, const double*, const double*, const double*, const double*, const double*,  \
+      const double*, int, int, double*, double*, double*, int*)
+#define UCN_INSTANTIATE_SCP(MODEL, T, SMEM, REFINE) template UCN_SCP_V(MODEL, T, SMEM, REFINE);
+#define UCN_INSTANTIATE_ADMM(MODEL, T, SMEM, REFINE) template UCN_ADMM_V(MODEL, T, SMEM, REFINE);
+#define UCN_EXTERN_SCP(MODEL, T, SMEM, REFINE) extern template UCN_SCP_V(MODEL, T, SMEM, REFINE);
+#define UCN_EXTERN_ADMM(MODEL, T, SMEM, REFINE) extern template UCN_ADMM_V(MODEL, T, SMEM, REFINE);

@@ -79,6 +79,7 @@ extern "C" ucn_status ucn_scp_solve_noalloc(const ucn_problem_desc* d, const dou
   if (d->batch < 1) return nfail(UCN_EINVAL, "batch must be >= 1");
   if (d->precision != UCN_PREC_FP64 && d->precision != UCN_PREC_FP32_REFINE) return nfail(UCN_EINVAL, "unknown precision %d", d->precision);
   if (d->vc_weight != 0.0) return nfail(UCN_EINVAL, "virtual control (vc_weight != 0) is not supported");
+  if (d->group > 1) return nfail(UCN_EINVAL, "scenario groups run through ucn_scp_solve only");
   if (!d->horizon || !d->dt || !d->model_params || !d->Q_diag || !d->x_ref || !d->R_diag || !d->u_ref ||
       !d->QN_diag || !d->qN || !d->x_lo || !d->x_hi || !d->u_lo || !d->u_hi || !d->x_init || !d->x_target || !d->term_mask)
     return nfail(UCN_EINVAL, "a required descriptor array is NULL");
@@ -147,7 +148,7 @@ extern "C" ucn_status ucn_scp_solve_noalloc(const ucn_problem_desc* d, const dou
   P.ws = nullptr;
   LaunchCfg c;
   c.P = &P; c.L = &L; c.smem = true; c.smem_bytes = L.bytes;
-  c.threads = (int)((Nmax + 1 + 31) / 32 * 32); c.blocks = B; c.stream = st;
+  c.threads = (int)((Nmax + 1 + 31) / 32 * 32); c.blocks = B; c.stream = st; c.group = 1;
   auto fn = d->model == UCN_MODEL_QUAD12 ? (d->precision == UCN_PREC_FP64 ? quad64_scp : quad32_scp)
                                          : (d->precision == UCN_PREC_FP64 ? mars64_scp : mars32_scp);
   e = fn(c, x0_d, u0_d, x_out_d, u_out_d, stats_d, status_d);

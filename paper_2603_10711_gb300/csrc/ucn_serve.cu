@@ -320,7 +320,7 @@ ucn_status ucn_serve_pump(ucn_server* s, int* launched) {
   P.order = s->order_d[lane];
   LaunchCfg c;
   c.P = &P; c.L = &s->L; c.smem = s->smem; c.smem_bytes = s->smem_bytes;
-  c.threads = s->threads; c.blocks = (int)ready.size(); c.stream = st;
+  c.threads = s->threads; c.blocks = (int)ready.size(); c.stream = st; c.group = 1;
   const bool quad = s->cfg.model == UCN_MODEL_QUAD12, f64 = s->cfg.precision == UCN_PREC_FP64;
   auto fn = quad ? (f64 ? quad64_scp : quad32_scp) : (f64 ? mars64_scp : mars32_scp);
   cudaError_t e = fn(c, s->x0, s->u0, s->xo, s->uo, s->stats, s->status);

@@ -41,7 +41,7 @@ class ProblemDesc(C.Structure):
         ("scp_iters", C.c_int), ("admm_iters", C.c_int), ("stop", C.c_int),
         ("tr_init", C.c_double), ("tr_min", C.c_double), ("tr_max", C.c_double), ("w_d", C.c_double),
         ("defect_tol", C.c_double), ("step_tol", C.c_double), ("vc_weight", C.c_double),
-        ("precision", C.c_int), ("timeout_s", C.c_double),
+        ("precision", C.c_int), ("timeout_s", C.c_double), ("group", C.c_int),
     ]
 
 
@@ -90,6 +90,8 @@ def lib():
             L.ucn_state_export.restype = C.c_int
             L.ucn_scp_solve.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
             L.ucn_scp_solve.restype = C.c_int
+            L.ucn_mpc_shift.argtypes = [vp, vp, vp, vp, vp, vp]
+            L.ucn_mpc_shift.restype = C.c_int
             L.ucn_scp_solve_noalloc.argtypes = [C.POINTER(ProblemDesc), vp, vp, vp, vp, vp, vp, vp]
             L.ucn_scp_solve_noalloc.restype = C.c_int
             _lib = L
@@ -177,6 +179,7 @@ def make_desc(prob, precision=UCN_PREC_FP64, timeout_s=0.0, **overrides):
     d.vc_weight = float(s.get("vc_weight", 0.0))
     d.precision = int(precision)
     d.timeout_s = float(timeout_s)
+    d.group = int(s.get("group", 1))
     return d, k
 
 
@@ -239,6 +242,15 @@ def ucn_scp_solve(h, x0, u0, x_out, u_out, stats, status, stream=None):
                                _ptr(status, torch.int32, name="status"), _stream(stream)))
 
 
+def ucn_mpc_shift(h, x, u, xg, ug, stream=None):
+    """Apply the (shared) first control to the plant and shift the solution
+    into the next warm start; updates the problem's initial states."""
+    import torch
+    f = torch.float64
+    _check(lib().ucn_mpc_shift(h, _ptr(x, f, name="x"), _ptr(u, f, name="u"), _ptr(xg, f, name="xg"),
+                               _ptr(ug, f, name="ug"), _stream(stream)))
+
+
 def ucn_scp_solve_noalloc(desc: ProblemDesc, x0, u0, x_out, u_out, stats, status, stream=None):
     """No-allocation solve: ``desc`` holds a host ``horizon`` array and device
     pointers for every other array (see include/ucn.h)."""
@@ -291,6 +303,16 @@ class Solver:
         u0 = self.tensor(self.prob.uguess) if u0 is None else u0
         ucn_scp_solve(self.handle, x0, u0, self.x_out, self.u_out, self.stats, self.status, stream)
         return self.x_out, self.u_out
+
+    def mpc_shift(self, x=None, u=None, stream=None):
+        """Receding-horizon step from the last solution; returns the next
+        guesses (x, u) as new device tensors."""
+        import torch
+        x = self.x_out if x is None else x
+        u = self.u_out if u is None else u
+        xg, ug = torch.empty_like(x), torch.empty_like(u)
+        ucn_mpc_shift(self.handle, x, u, xg, ug, stream)
+        return xg, ug
 
     def stats_host(self):
         return np.frombuffer(self.stats.cpu().numpy().tobytes(), dtype=STATS_DTYPE)

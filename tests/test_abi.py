@@ -60,6 +60,9 @@ def create(ucn, prob, **over):
     (lambda d: setattr(d, "admm_iters", 0), "iteration"),
     (lambda d: setattr(d, "tr_min", -1.0), "trust"),
     (lambda d: setattr(d, "max_obs", 99), "max_obs"),
+    (lambda d: setattr(d, "group", 17), "group must be"),
+    (lambda d: setattr(d, "group", -1), "group must be"),
+    (lambda d: setattr(d, "group", 3), "not a multiple of group"),
 ])
 def test_create_rejects_bad_descriptors(ucn, mutate, needle):
     prob = W.quad_path(1, seed=0)
@@ -70,6 +73,15 @@ def test_create_rejects_bad_descriptors(ucn, mutate, needle):
     assert rc == ucn.UCN_EINVAL
     assert needle in ucn.ucn_last_error()
     assert not h.value
+
+
+def test_scenario_groups_need_the_quadrotor_model(ucn):
+    prob = W.mars_batch(4, seed=1, N=10)
+    desc, keep = create(ucn, prob, group=2)
+    h = C.c_void_p()
+    assert ucn.lib().ucn_problem_create(C.byref(desc), C.byref(h)) == ucn.UCN_EINVAL
+    assert "quadrotor" in ucn.ucn_last_error()
+    assert ucn.lib().ucn_scp_solve_noalloc(C.byref(desc), None, None, None, None, None, None, None) == ucn.UCN_EINVAL
 
 
 def test_create_rejects_bad_horizons(ucn):

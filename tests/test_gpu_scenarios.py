@@ -1,0 +1,191 @@
+"""Scenario groups (robust MPC, Sec. IV-A) on the GPU: thread-block clusters,
+one CTA per scenario, first-control consensus through distributed shared
+memory.  Checked element by element against the oracle's group solve, plus the
+properties the method fixes: one first control per group (bitwise), one
+decision per group, and a group of identical scenarios solving like one
+instance."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2603_10711_gb300 import ucn  # noqa: E402
+
+TOL64, TOL32 = 1e-9, 1e-4
+FIXED = dict(scp_iters=8, admm_iters=60, stop=0)
+
+
+def rel_err(a, b):
+    a = np.asarray(a, dtype=np.float64); b = np.asarray(b, dtype=np.float64)
+    return float(np.abs(a - b).max() / max(1.0, np.abs(b).max())) if b.size else 0.0
+
+
+def grouped(P, K, N=20, n_obs=4, seed=3, **settings):
+    st = dict(FIXED)
+    st.update(settings)
+    return W.scenario_mpc(P, K, seed=seed, N=N, n_obs=n_obs, settings=st)
+
+
+def solve(prob, prec, **kw):
+    s = ucn.Solver(prob, precision=prec, **kw)
+    x, u = s.scp_solve()
+    torch.cuda.synchronize()
+    out = x.cpu().numpy(), u.cpu().numpy(), s.stats_host()
+    s.close()
+    return out
+
+
+def check_group_invariants(prob, ug, st):
+    K = int(prob.settings["group"])
+    for p in range(prob.batch // K):
+        b0 = p * K
+        for k in range(1, K):
+            for f in ("scp_iters", "accepted", "accept_mask", "tr_radius", "step"):
+                assert st[f][b0 + k] == st[f][b0], (p, k, f)
+        if st["accepted"][b0] > 0:
+            for k in range(1, K):
+                np.testing.assert_array_equal(ug[prob.uoff[b0 + k]], ug[prob.uoff[b0]])
+
+
+def compare(prob, prec, tol):
+    xg, ug, st = solve(prob, prec)
+    xr, ur, sr, _ = oracle.scp_solve(prob)
+    for b in range(prob.batch):
+        xo, uo, N = prob.xoff[b], prob.uoff[b], int(prob.N[b])
+        assert rel_err(xg[xo:xo + N + 1], xr[xo:xo + N + 1]) <= tol, (b, rel_err(xg[xo:xo + N + 1], xr[xo:xo + N + 1]))
+        assert rel_err(ug[uo:uo + N], ur[uo:uo + N]) <= tol, b
+        if prec == ucn.UCN_PREC_FP64:
+            assert int(st["scp_iters"][b]) == int(sr[b, 7])
+            assert int(st["accepted"][b]) == int(sr[b, 8])
+            assert int(st["accept_mask"][b]) == int(sr[b, 9])
+            assert int(st["status"][b]) == int(sr[b, 10])
+            assert abs(st["cost"][b] - sr[b, 1]) <= 1e-9 * max(1.0, abs(sr[b, 1]))
+    check_group_invariants(prob, ug, st)
+    return xg, ug, st, sr
+
+
+@pytest.mark.parametrize("prec,tol", [(ucn.UCN_PREC_FP64, TOL64), (ucn.UCN_PREC_FP32_REFINE, TOL32)])
+def test_groups_match_the_oracle(prec, tol):
+    compare(grouped(3, 4), prec, tol)
+
+
+def test_groups_of_two_and_an_odd_size():
+    compare(grouped(2, 2, N=12, seed=5), ucn.UCN_PREC_FP64, TOL64)
+    compare(grouped(2, 3, N=9, n_obs=2, seed=6), ucn.UCN_PREC_FP64, TOL64)
+
+
+def test_converging_groups_match_the_oracle():
+    prob = grouped(2, 4, N=30, scp_iters=40, admm_iters=200, stop=1, step_tol=1.0)
+    xg, ug, st, sr = compare(prob, ucn.UCN_PREC_FP64, TOL64)
+    assert (sr[:, 0] <= 1e-5).all() and (st["defect"] <= 1e-5).all()
+
+
+def test_largest_group_with_benchmark_records():
+    # 16 scenarios per cluster (the non-portable maximum), N = 40 and 8 obstacles
+    prob = grouped(2, 16, N=40, n_obs=8, scp_iters=6, admm_iters=80)
+    compare(prob, ucn.UCN_PREC_FP32_REFINE, TOL32)
+
+
+def test_identical_scenarios_solve_like_one_instance():
+    base = W.quad_box(1, seed=11, N_range=(16, 16), obs_range=(3, 3), settings=dict(FIXED))
+    one = solve(base, ucn.UCN_PREC_FP64)
+    grp = base.subset(np.zeros(4, dtype=np.int64))
+    grp.settings = dict(base.settings, group=4)
+    xg, ug, st = solve(grp, ucn.UCN_PREC_FP64)
+    for k in range(4):
+        assert rel_err(xg[grp.xoff[k]:grp.xoff[k] + 17], one[0]) <= 1e-12
+        assert rel_err(ug[grp.uoff[k]:grp.uoff[k] + 16], one[1]) <= 1e-12
+        assert st["accept_mask"][k] == one[2]["accept_mask"][0]
+
+
+def test_time_budget_is_decided_per_group():
+    prob = grouped(2, 4, scp_iters=20)
+    xg, ug, st = solve(prob, ucn.UCN_PREC_FP32_REFINE, timeout_s=1e-9)
+    assert (st["status"] == ucn.UCN_ETIMEOUT).all()
+    assert (st["scp_iters"] == 1).all()
+    check_group_invariants(prob, ug, st)
+
+
+def test_grouped_problems_reject_the_separate_calls():
+    prob = grouped(1, 2, N=8)
+    s = ucn.Solver(prob, precision=ucn.UCN_PREC_FP64)
+    with pytest.raises(ucn.UcnError, match="instance order"):
+        ucn.ucn_problem_set_order(s.handle, [1, 0])
+    x = s.tensor(prob.xguess); u = s.tensor(prob.uguess)
+    A, B, d = s.linearize(x, u)
+    r = torch.full((prob.batch,), 1.0, dtype=torch.float64, device="cuda")
+    with pytest.raises(ucn.UcnError, match="inside ucn_scp_solve"):
+        s.admm_solve(x, u, A, B, d, r, 5)
+    s.close()
+
+
+def test_fp32_groups_reach_the_defect_gate():
+    prob = grouped(4, 8, N=30, n_obs=6, scp_iters=40, admm_iters=200, stop=1, step_tol=1.0)
+    xg, ug, st = solve(prob, ucn.UCN_PREC_FP32_REFINE)
+    check_group_invariants(prob, ug, st)
+    _, _, sr, _ = oracle.scp_solve(prob)
+    for b in range(prob.batch):
+        if sr[b, 0] <= 1e-5:
+            assert st["defect"][b] <= 1e-5, (b, st["defect"][b])
+
+
+# ------------------------------------------------------------------ receding horizon (Sec. IV-A)
+def test_mpc_shift_applies_the_shared_control_and_shifts():
+    K, N = 4, 20
+    prob = grouped(2, K, N=N, scp_iters=10, admm_iters=100, stop=1, step_tol=1.0)
+    s = ucn.Solver(prob, precision=ucn.UCN_PREC_FP64)
+    x, u = s.scp_solve()
+    torch.cuda.synchronize()
+    xs, us = x.cpu().numpy().copy(), u.cpu().numpy().copy()
+    xg_d, ug_d = s.mpc_shift()
+    torch.cuda.synchronize()
+    xg, ug = xg_d.cpu().numpy(), ug_d.cpu().numpy()
+    for b in range(prob.batch):
+        lead = b - b % K
+        xo, uo = prob.xoff[b], prob.uoff[b]
+        plant = oracle.rk4(prob.model, prob.params[lead], prob.dt[lead], prob.xinit[lead], us[prob.uoff[lead]])
+        assert rel_err(xg[xo], plant) <= 1e-13
+        np.testing.assert_array_equal(xg[xo + 1:xo + N], xs[xo + 2:xo + N + 1])
+        np.testing.assert_array_equal(xg[xo + N], xs[xo + N])
+        np.testing.assert_array_equal(ug[uo:uo + N - 1], us[uo + 1:uo + N])
+        np.testing.assert_array_equal(ug[uo + N - 1], us[uo + N - 1])
+    # the next solve starts from the new state, and matches the oracle warm-started the same way
+    x2, u2 = s.scp_solve(xg_d, ug_d)
+    torch.cuda.synchronize()
+    x2 = x2.cpu().numpy(); u2 = u2.cpu().numpy()
+    nxt = prob.subset(np.arange(prob.batch))
+    nxt.xinit = np.stack([xg[prob.xoff[b]] for b in range(prob.batch)])
+    xr, ur, sr, _ = oracle.scp_solve(nxt, xguess=xg, uguess=ug)
+    for b in range(prob.batch):
+        xo = prob.xoff[b]
+        np.testing.assert_array_equal(x2[xo], xg[xo])
+        assert rel_err(x2[xo:xo + N + 1], xr[xo:xo + N + 1]) <= TOL64
+    s.close()
+
+
+def test_receding_horizon_approaches_the_goal():
+    K, N, steps = 8, 40, 12
+    prob = grouped(4, K, N=N, n_obs=8, scp_iters=40, admm_iters=200, stop=1, step_tol=1.0)
+    s = ucn.Solver(prob, precision=ucn.UCN_PREC_FP32_REFINE)
+    goal = prob.xtarget[::K, :3]
+    d0 = np.linalg.norm(prob.xinit[::K, :3] - goal, axis=1)
+    xg, ug = s.tensor(prob.xguess), s.tensor(prob.uguess)
+    iters = []
+    for step in range(steps):
+        s.scp_solve(xg, ug)
+        xg, ug = s.mpc_shift()
+        torch.cuda.synchronize()
+        st = s.stats_host()
+        check_group_invariants(prob, s.u_out.cpu().numpy(), st)
+        iters.append(st["scp_iters"][::K].astype(float))
+        assert (st["defect"] <= 1e-4).mean() >= 0.75
+    x0 = xg.cpu().numpy()[prob.xoff[::K]]
+    d1 = np.linalg.norm(x0[:, :3] - goal, axis=1)
+    assert (d1 < d0).all()
+    # warm starts from the shifted tube converge in fewer SCP iterations than the cold start
+    assert np.mean(iters[1:]) < np.mean(iters[0])
+    s.close()

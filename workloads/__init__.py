@@ -400,7 +400,9 @@ def scenario_mpc(P=256, K=16, seed=3, N=40, n_obs=8, dt=0.05, settings=None) -> 
     spheres in the 10 x 10 x 3 m box (like ``quad_box``); its K scenarios share
     them and differ in mass ~ U[0.9, 1.1] kg and linear drag ~ U[0, 0.2].
     Instances b = p*K + s; settings["group"] = K couples the scenarios of a
-    problem through their first control."""
+    problem through their first control.  As in receding-horizon control the
+    goal is not a terminal equality (a 2 s horizon cannot always reach it):
+    the terminal cost weighs position and velocity by 10 instead."""
     base = quad_box(P, seed=seed, N_range=(N, N), obs_range=(n_obs, n_obs), dt=dt)
     idx = np.repeat(np.arange(P), K)
     prob = base.subset(idx)
@@ -408,6 +410,8 @@ def scenario_mpc(P=256, K=16, seed=3, N=40, n_obs=8, dt=0.05, settings=None) -> 
     cd = U(seed, 52, np.arange(P * K), 0.0, 0.2)
     prob.params[:, 0] = mass
     prob.params[:, 6] = cd
+    prob.tmask[:] = 0
+    prob.QNd[:, :6] = 10.0
     hover = mass * QUAD_G / 4.0
     prob.uref[:] = hover[:, None]
     for b in range(P * K):
