@@ -85,17 +85,25 @@ typedef enum { UCN_PREC_FP64 = 0, UCN_PREC_FP32_REFINE = 1 } ucn_precision;
  *                defects, costs and residual sums in FP64
  *  timeout_s     device time budget per ucn_scp_solve launch (0: 60 s)
  *  group         scenarios per group for robust MPC (Sec. IV-A); 0 or 1:
- *                independent instances.  With group = K in [2, 16] the
+ *                independent instances.  With group = K in [2, UCN_MAX_GROUP] the
  *                instances gK .. gK+K-1 are scenarios of one problem that share
  *                the first control u_0: ucn_scp_solve runs each group's ADMM
  *                iterations in lockstep, setting the first control copy of every
  *                scenario to the average of their Step-3 arguments clamped to the
  *                intersection of their boxes, and accepts, resizes the trust
  *                region and stops per group (sums of the merits, maxima of
- *                defect and step).  Requires the quadrotor model, batch % K == 0
- *                and records that fit in shared memory; ucn_admm_solve and
- *                ucn_problem_set_order reject grouped problems
+ *                defect and step).  A group is one thread-block cluster of K CTAs
+ *                when K <= 16, else K / c clusters of c CTAs (c the largest
+ *                divisor of K up to 16) that exchange partial sums through
+ *                global memory and must be resident together (ucn_scp_solve
+ *                returns UCN_EINVAL when they cannot be).  Requires the
+ *                quadrotor model, batch % K == 0 and records that fit in
+ *                shared memory; ucn_admm_solve and ucn_problem_set_order
+ *                reject grouped problems
  */
+/* Largest scenario group (ucn_problem_desc.group). */
+#define UCN_MAX_GROUP 1024
+
 typedef struct {
   int model, nx, nu, batch;
   const int* horizon;

@@ -84,7 +84,7 @@ struct ucn_problem {
   int threads;
   int* node_inst;
   int* order_d;
-  int group;
+  int group, gcsize;     // scenarios per group, CTAs per thread-block cluster
 };
 
 namespace {
@@ -184,7 +184,7 @@ ucn_status ucn_problem_create(const ucn_problem_desc* d, ucn_problem** out) {
   if (d->scp_iters < 1 || d->admm_iters < 1) return fail(UCN_EINVAL, "iteration counts must be >= 1");
   if (!(d->tr_init > 0 && d->tr_min > 0 && d->tr_max >= d->tr_min)) return fail(UCN_EINVAL, "bad trust-region bounds");
   const int group = d->group > 1 ? d->group : 1;
-  if (d->group < 0 || group > 16) return fail(UCN_EINVAL, "group must be in [0, 16] (got %d)", d->group);
+  if (d->group < 0 || group > UCN_MAX_GROUP) return fail(UCN_EINVAL, "group must be in [0, %d] (got %d)", UCN_MAX_GROUP, d->group);
   if (group > 1 && d->model != UCN_MODEL_QUAD12) return fail(UCN_EINVAL, "scenario groups need the quadrotor model");
   if (group > 1 && d->batch % group) return fail(UCN_EINVAL, "batch %d is not a multiple of group %d", d->batch, group);
   int Nmax = 0;
@@ -274,6 +274,14 @@ ucn_status ucn_problem_create(const ucn_problem_desc* d, ucn_problem** out) {
   P.state_abs = sabs;
   P.order = ord;
   P.group = group;
+  // a group is gclusters thread-block clusters of gcsize CTAs: the largest
+  // cluster size <= 16 that divides it
+  int gcsize = 1;
+  for (int c = std::min(group, 16); c >= 1; --c)
+    if (group % c == 0) { gcsize = c; break; }
+  p->gcsize = gcsize;
+  P.gclusters = group / gcsize;
+  P.gwait_ns = std::min<unsigned long long>(P.timeout_ns, 10ull * 1000000000ull);
   p->node_inst = ni;
   p->order_d = ord;
   // per-node storage: shared memory when one instance fits (small models then keep
@@ -291,6 +299,28 @@ ucn_status ucn_problem_create(const ucn_problem_desc* d, ucn_problem** out) {
   if (group > 1 && !p->smem) {
     ucn_problem_destroy(p);
     return fail(UCN_EINVAL, "scenario groups need node records in shared memory (horizon or obstacle count too large)");
+  }
+  if (P.gclusters > 1) {
+    // exchange slots and counters of the clusters of each group
+    const size_t nc = (size_t)(B / group) * P.gclusters;
+    const bool injected = fa > 0 && (na + 1 == fa || na + 2 == fa);
+    na += 2;
+    void* gx = nullptr;
+    void* gf = nullptr;
+    if (injected || cudaMalloc(&gx, nc * 2 * 16 * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      ucn_problem_destroy(p);
+      return fail(UCN_ENOMEM, "group exchange slots");
+    }
+    p->allocs.push_back(gx);
+    if (cudaMalloc(&gf, nc * sizeof(unsigned)) != cudaSuccess) {
+      cudaGetLastError();
+      ucn_problem_destroy(p);
+      return fail(UCN_ENOMEM, "group exchange counters");
+    }
+    p->allocs.push_back(gf);
+    P.gx = (double*)gx;
+    P.gflag = (unsigned*)gf;
   }
   P.ws = nullptr;
   if (!p->smem) {
@@ -336,7 +366,7 @@ long long ucn_state_size(const ucn_problem* p) { return p ? p->state_size : -1; 
 static LaunchCfg cfg_of(ucn_problem* p, void* stream) {
   LaunchCfg c;
   c.P = &p->dev; c.L = &p->L; c.smem = p->smem; c.smem_bytes = p->smem_bytes;
-  c.threads = p->threads; c.blocks = p->batch; c.stream = as_stream(stream); c.group = p->group;
+  c.threads = p->threads; c.blocks = p->batch; c.stream = as_stream(stream); c.group = p->gcsize;
   return c;
 }
 
@@ -382,11 +412,15 @@ ucn_status ucn_scp_solve(ucn_problem* p, const double* x0_d, const double* u0_d,
   if (!p || !x0_d || !u0_d || !x_out_d || !u_out_d || !stats_d || !status_d) return fail(UCN_EINVAL, "null argument");
   const LaunchCfg c = cfg_of(p, stream);
   if (p->group > 1) {
+    if (p->dev.gclusters > 1) {
+      const cudaError_t e = cudaMemsetAsync(p->dev.gflag, 0, sizeof(unsigned) * (p->batch / p->gcsize), c.stream);
+      if (e != cudaSuccess) return fail(UCN_ECUDA, "group counters: %s", cudaGetErrorString(e));
+    }
     const cudaError_t e = (p->precision == UCN_PREC_FP64 ? quad64_scp_group : quad32_scp_group)(
         c, x0_d, u0_d, x_out_d, u_out_d, stats_d, status_d);
     if (e == cudaErrorInvalidClusterSize)
-      return fail(UCN_EINVAL, "a cluster of %d CTAs (%d threads, %lld B shared memory each) does not fit on the device",
-                  p->group, p->threads, p->smem_bytes);
+      return fail(UCN_EINVAL, "%d clusters of %d CTAs (%d threads, %lld B shared memory each) cannot be resident together",
+                  p->dev.gclusters, p->gcsize, p->threads, p->smem_bytes);
     if (e != cudaSuccess) return fail(UCN_ECUDA, "scp group launch: %s", cudaGetErrorString(e));
     return UCN_OK;
   }

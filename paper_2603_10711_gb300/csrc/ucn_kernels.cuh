@@ -43,6 +43,10 @@ struct ProblemDev {
   char* ws;                // per-instance node storage when it does not fit in shared memory
   const int* order;        // CTA -> instance map of the fused solve (NULL: identity)
   int group;               // scenarios per group (<= 1: independent instances)
+  int gclusters;           // thread-block clusters per group (group = gclusters x cluster size)
+  double* gx;              // exchange slots between the clusters of a group [group][cluster][2][16]
+  unsigned* gflag;         // per [group][cluster]: last exchange published (+1); zeroed per launch
+  unsigned long long gwait_ns;   // bound on a wait for another cluster of the group
 };
 
 // Fixed part of a node record: compile-time element offsets of every per-node
@@ -169,14 +173,94 @@ struct InstShared {
   int accept, stop, status;
 };
 
-// Exchange area of a scenario group (one thread-block cluster, one CTA per
-// scenario), read by the other CTAs through distributed shared memory.
+// Exchange area of a scenario group (one CTA per scenario; the group is one
+// thread-block cluster, or several whose rank-0 CTAs meet in global memory),
+// read by the other CTAs of the cluster through distributed shared memory.
 struct GroupShared {
-  double cons[2][12];   // per ADMM iteration (double-buffered): u_0 argument | lo | hi, absolute (nu <= 4)
+  double mine[2][16];   // this CTA's contribution to the current exchange (double-buffered)
+  double bcast[17];     // rank 0's group result (+ [16]: an exchange gave up waiting)
   double u0[4];         // the consensus u-hat_0 of the latest iteration, absolute
-  double acc[8];        // acceptance: merit of the nominal, of the candidate, of the model; defect; step; timeout
-  double flag;          // factorisation failure
+  int gfail;            // sticky: a wait for another cluster of the group gave up
 };
+
+// Sequence state of the group exchanges, identical in every thread of the group.
+struct GroupX {
+  unsigned epoch;       // exchanges done
+  int g, c;             // group index, cluster index within the group
+};
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_gpu(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
+}
+
+// All-reduce over the scenario group of the NV values that thread 0 of every
+// CTA has put in G->mine[X.epoch & 1]: entries [0, ns) summed, the rest maxed,
+// in scenario order (cluster by cluster, rank by rank).  Every thread of every
+// CTA of the group calls it the same number of times; thread 0 receives the
+// result in out.  Several clusters: the rank-0 CTAs publish their partials in
+// global memory (release/acquire on per-cluster counters) and wait for the
+// others' with a time bound; a wait that gives up marks the group failed and
+// stops waiting for the rest of the launch (status ETIMEOUT), so the kernel
+// always ends.
+template <int NV>
+__device__ void group_allreduce(const ProblemDev& P, GroupShared* G, GroupX& X, int ns, double* out) {
+  const int par = X.epoch & 1;
+  cluster_sync();
+  const unsigned nk = cluster_size();
+  if (P.gclusters <= 1) {
+    if (threadIdx.x == 0) {
+      for (int j = 0; j < NV; ++j) out[j] = j < ns ? 0.0 : -INFINITY;
+      for (unsigned r = 0; r < nk; ++r)
+        for (int j = 0; j < NV; ++j) {
+          const double v = ld_cluster(&G->mine[par][j], r);
+          out[j] = j < ns ? out[j] + v : fmax(out[j], v);
+        }
+    }
+  } else {
+    if (threadIdx.x == 0 && cluster_rank() == 0) {
+      const int C = P.gclusters;
+      double pv[NV], tot[NV];
+      for (int j = 0; j < NV; ++j) { pv[j] = j < ns ? 0.0 : -INFINITY; tot[j] = pv[j]; }
+      for (unsigned r = 0; r < nk; ++r)
+        for (int j = 0; j < NV; ++j) {
+          const double v = ld_cluster(&G->mine[par][j], r);
+          pv[j] = j < ns ? pv[j] + v : fmax(pv[j], v);
+        }
+      double* slot = P.gx + (((long long)X.g * C + X.c) * 2 + par) * 16;
+      for (int j = 0; j < NV; ++j) slot[j] = pv[j];
+      st_release_gpu(&P.gflag[X.g * C + X.c], X.epoch + 1);
+      for (int c = 0; c < C; ++c) {
+        if (c != X.c && !G->gfail) {
+          const unsigned* f = &P.gflag[X.g * C + c];
+          const unsigned long long t0 = globaltimer_ns();
+          while (ld_acquire_gpu(f) < X.epoch + 1) {
+            if (globaltimer_ns() - t0 > P.gwait_ns) { G->gfail = 1; break; }
+            __nanosleep(64);
+          }
+        }
+        if (c != X.c && G->gfail) continue;
+        const double* src = P.gx + (((long long)X.g * C + c) * 2 + par) * 16;
+        for (int j = 0; j < NV; ++j) {
+          const double v = c == X.c ? pv[j] : __ldcg(src + j);
+          tot[j] = j < ns ? tot[j] + v : fmax(tot[j], v);
+        }
+      }
+      for (int j = 0; j < NV; ++j) G->bcast[j] = tot[j];
+      G->bcast[16] = G->gfail ? 1.0 : 0.0;
+    }
+    cluster_sync();
+    if (threadIdx.x == 0) {
+      for (int j = 0; j < NV; ++j) out[j] = ld_cluster(&G->bcast[j], 0);
+      if (ld_cluster(&G->bcast[16], 0) != 0.0) G->gfail = 1;
+    }
+  }
+  X.epoch++;
+}
 
 // The exchange area exists in the shared memory of group kernels only.
 template <bool GROUP>
@@ -657,7 +741,8 @@ __device__ void node_reseed(const Node<T, AOS>& nd, const Layout& L, const Inst<
 template <class M, class T, bool AOS, bool REFINE, bool LAST, bool GROUP, class MS>
 __device__ __forceinline__ void admm_iteration(const Node<T, AOS>& nd, const MS& MT, const Layout& L, const Inst<T>& I,
                                                const NodeConst<M, T>& K, bool active, T re, T rd, T rg,
-                                               T irg, T ired, double& rp, double& rdl, GroupShared* G, int par) {
+                                               T irg, T ired, double& rp, double& rdl, GroupShared* G,
+                                               GroupX& X, const ProblemDev& P) {
   constexpr int NX = M::NX, NU = M::NU, NN = NX + NU;
   const int i = nd.i, N = nd.N;
   constexpr bool last = LAST;
@@ -747,11 +832,12 @@ __device__ __forceinline__ void admm_iteration(const Node<T, AOS>& nd, const MS&
         for (int j = 0; j < NU; ++j) {
           const T nuu = nd.at(Rec<M>::Nuu, j);
           if constexpr (GROUP) {
-            if (i == 0) {
+            if (i == 0) {   // sum of arguments | max of lower bounds | max of -upper bounds
               const double ub = nd.dat(Rec<M>::Ubar, j);
-              G->cons[par][j] = ub + (double)(x[NX + j] + nuu * irg);
-              G->cons[par][NU + j] = ub + (double)nd.at(Rec<M>::Ulo, j);
-              G->cons[par][2 * NU + j] = ub + (double)nd.at(Rec<M>::Uhi, j);
+              double* m = G->mine[X.epoch & 1];
+              m[j] = ub + (double)(x[NX + j] + nuu * irg);
+              m[NU + j] = ub + (double)nd.at(Rec<M>::Ulo, j);
+              m[2 * NU + j] = -(ub + (double)nd.at(Rec<M>::Uhi, j));
               continue;
             }
           }
@@ -766,18 +852,12 @@ __device__ __forceinline__ void admm_iteration(const Node<T, AOS>& nd, const MS&
       }
     }
     if constexpr (GROUP) {
-      cluster_sync();
+      double tot[3 * NU];
+      group_allreduce<3 * NU>(P, G, X, NU, tot);
       if (active && i == 0 && i < N) {
-        const unsigned nk = cluster_size();
 #pragma unroll
         for (int j = 0; j < NU; ++j) {
-          double sum = 0.0, lo = -INFINITY, hi = INFINITY;
-          for (unsigned r = 0; r < nk; ++r) {
-            sum += ld_cluster(&G->cons[par][j], r);
-            lo = fmax(lo, ld_cluster(&G->cons[par][NU + j], r));
-            hi = fmin(hi, ld_cluster(&G->cons[par][2 * NU + j], r));
-          }
-          const double v = fmin(fmax(sum / (double)nk, lo), hi);
+          const double v = fmin(fmax(tot[j] / (double)P.group, tot[NU + j]), -tot[2 * NU + j]);
           G->u0[j] = v;
           const T uh = (T)(v - nd.dat(Rec<M>::Ubar, j));
           const T nuu = nd.at(Rec<M>::Nuu, j);
@@ -830,13 +910,12 @@ __device__ __forceinline__ void admm_iteration(const Node<T, AOS>& nd, const MS&
 template <class M, class T, bool AOS, bool REFINE, bool GROUP = false, class MS>
 __device__ __forceinline__ void admm_iterations(const Node<T, AOS>& nd, const MS& MT, const Layout& L, const Inst<T>& I,
                                 const NodeConst<M, T>& K, bool active, T re, T rd, T rg, int iters,
-                                InstShared& sh, double* res, GroupShared* G = nullptr) {
+                                InstShared& sh, double* res, GroupShared* G, GroupX& X, const ProblemDev& P) {
   const T irg = T(1) / rg, ired = T(1) / (re + rd);
   double rp = 0.0, rdl = 0.0;
   for (int it = 0; it + 1 < iters; ++it)
-    admm_iteration<M, T, AOS, REFINE, false, GROUP>(nd, MT, L, I, K, active, re, rd, rg, irg, ired, rp, rdl, G, it & 1);
-  admm_iteration<M, T, AOS, REFINE, true, GROUP>(nd, MT, L, I, K, active, re, rd, rg, irg, ired, rp, rdl, G,
-                                                 (iters - 1) & 1);
+    admm_iteration<M, T, AOS, REFINE, false, GROUP>(nd, MT, L, I, K, active, re, rd, rg, irg, ired, rp, rdl, G, X, P);
+  admm_iteration<M, T, AOS, REFINE, true, GROUP>(nd, MT, L, I, K, active, re, rd, rg, irg, ired, rp, rdl, G, X, P);
   double v[2] = {rp, rdl};
   block_reduce(sh, v, 2, 2);
   res[0] = sqrt(v[0]);
@@ -1086,7 +1165,8 @@ __global__ void __launch_bounds__(MAX_THREADS) admm_kernel(ProblemDev P, Layout 
   }
   __syncthreads();
   double r2[2] = {0.0, 0.0};
-  if (!sh.fail) admm_iterations<M, T, AOS, REFINE>(nd, MT, L, I, K, active, re, rd, rg, iters, sh, r2);
+  GroupX X{0u, 0, 0};
+  if (!sh.fail) admm_iterations<M, T, AOS, REFINE>(nd, MT, L, I, K, active, re, rd, rg, iters, sh, r2, nullptr, X, P);
   if (active) {
     node_export<M, T, AOS>(nd, L, P, b, P.state_abs + P.soff[b]);
     for (int j = 0; j < NX; ++j) xhat[(xo + i) * NX + j] = nd.dat(Rec<M>::Xbar, j) + (double)nd.at(Rec<M>::Xh, j);
@@ -1144,6 +1224,12 @@ __global__ void __launch_bounds__(MAX_THREADS) scp_kernel(ProblemDev P, Layout L
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ InstShared sh;
   GroupShared* G = group_slot<GROUP>();
+  GroupX X{0u, 0, 0};
+  if constexpr (GROUP) {
+    X.g = (int)blockIdx.x / P.group;
+    X.c = ((int)blockIdx.x % P.group) / (int)cluster_size();
+    if (threadIdx.x == 0) G->gfail = 0;
+  }
   // instances are taken in the order given (largest first by default), so that
   // the long solves of an uneven batch start in the first wave; a scenario group
   // keeps its cluster's consecutive instances
@@ -1210,17 +1296,14 @@ __global__ void __launch_bounds__(MAX_THREADS) scp_kernel(ProblemDev P, Layout L
       // a failed factorisation in any scenario stops the whole group (this
       // barrier is also the first one, so every CTA of the cluster has started
       // before any distributed shared memory is read)
-      if (threadIdx.x == 0) G->flag = (double)sh.fail;
-      cluster_sync();
-      if (threadIdx.x == 0) {
-        double f = 0.0;
-        for (unsigned r = 0; r < cluster_size(); ++r) f = fmax(f, ld_cluster(&G->flag, r));
-        sh.fail = f != 0.0;
-      }
+      if (threadIdx.x == 0) G->mine[X.epoch & 1][0] = (double)sh.fail;
+      double f[1];
+      group_allreduce<1>(P, G, X, 0, f);
+      if (threadIdx.x == 0) sh.fail = f[0] != 0.0;
       __syncthreads();
     }
     if (sh.fail) { if (threadIdx.x == 0) sh.status = ST_NUMERIC; iters_run++; break; }
-    admm_iterations<M, T, AOS, REFINE, GROUP>(nd, MT, L, I, K, active, re, rd, rg, P.admm_iters, sh, res, G);
+    admm_iterations<M, T, AOS, REFINE, GROUP>(nd, MT, L, I, K, active, re, rd, rg, P.admm_iters, sh, res, G, X, P);
     ++iters_run;
     // ---- candidate (x-hat, u-hat): FP64 rollout, defects, cost, linear model
     double xc[NX], uc[NU], fc[NX];
@@ -1268,21 +1351,13 @@ __global__ void __launch_bounds__(MAX_THREADS) scp_kernel(ProblemDev P, Layout L
     const double Jc_own = Jc;
     if constexpr (GROUP) {
       if (threadIdx.x == 0) {
-        G->acc[0] = Jn; G->acc[1] = Jc; G->acc[2] = Lc; G->acc[3] = v[3]; G->acc[4] = v[4];
-        G->acc[5] = timed_out ? 1.0 : 0.0;
+        double* m = G->mine[X.epoch & 1];
+        m[0] = Jn; m[1] = Jc; m[2] = Lc; m[3] = v[3]; m[4] = v[4]; m[5] = timed_out ? 1.0 : 0.0;
       }
-      cluster_sync();
+      double a[6];
+      group_allreduce<6>(P, G, X, 3, a);
       if (threadIdx.x == 0) {
-        double s0 = 0.0, s1 = 0.0, s2 = 0.0, m3 = 0.0, m4 = 0.0, to = 0.0;
-        for (unsigned r = 0; r < cluster_size(); ++r) {
-          s0 += ld_cluster(&G->acc[0], r);
-          s1 += ld_cluster(&G->acc[1], r);
-          s2 += ld_cluster(&G->acc[2], r);
-          m3 = fmax(m3, ld_cluster(&G->acc[3], r));
-          m4 = fmax(m4, ld_cluster(&G->acc[4], r));
-          to = fmax(to, ld_cluster(&G->acc[5], r));
-        }
-        Jn = s0; Jc = s1; Lc = s2; v[3] = m3; v[4] = m4; timed_out = to != 0.0;
+        Jn = a[0]; Jc = a[1]; Lc = a[2]; v[3] = a[3]; v[4] = a[4]; timed_out = a[5] != 0.0;
       }
     }
     if (threadIdx.x == 0) {
@@ -1357,6 +1432,9 @@ __global__ void __launch_bounds__(MAX_THREADS) scp_kernel(ProblemDev P, Layout L
   block_reduce(sh, w, 2, 3);
   if (threadIdx.x == 0) {
     int st = sh.status;
+    if constexpr (GROUP) {
+      if (G->gfail && st != ST_NUMERIC) st = ST_TIMEOUT;   // the group lost its consensus partner
+    }
     if (!isfinite(w[2])) st = ST_NUMERIC;
     if (st == ST_OK && !(w[2] <= P.defect_tol)) st = ST_NOTCONV;
     ucn_scp_stats s;

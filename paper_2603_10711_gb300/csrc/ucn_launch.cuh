@@ -29,14 +29,15 @@ cudaError_t launch_scp_t(const LaunchCfg& c, const double* x0, const double* u0,
 }
 
 // Scenario groups: thread-block clusters of c.group CTAs (records in shared
-// memory only).  cudaErrorInvalidClusterSize when no such cluster fits on the
-// device (cluster size above 16, or too much shared memory per CTA).
+// memory only), P.gclusters clusters per group.  cudaErrorInvalidClusterSize
+// when fewer than the clusters of one group can be resident together (cluster
+// size above 16, or too much shared memory per CTA).
 template <class M, class T, bool R>
 cudaError_t launch_scp_group_t(const LaunchCfg& c, const double* x0, const double* u0, double* xo, double* uo,
                                ucn_scp_stats* st, int* status) {
   const ProblemDev& P = *(const ProblemDev*)c.P;
   const Layout& L = *(const Layout*)c.L;
-  if (!c.smem || c.group < 2 || c.group > 16 || c.blocks % c.group) return cudaErrorInvalidClusterSize;
+  if (!c.smem || c.group < 1 || c.group > 16 || c.blocks % c.group) return cudaErrorInvalidClusterSize;
   auto k = scp_kernel<M, T, true, R, true>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem_bytes);
   if (e != cudaSuccess) return e;
@@ -59,7 +60,7 @@ cudaError_t launch_scp_group_t(const LaunchCfg& c, const double* x0, const doubl
   int nclusters = 0;
   e = cudaOccupancyMaxActiveClusters(&nclusters, k, &cfg);
   if (e != cudaSuccess) return e;
-  if (nclusters < 1) return cudaErrorInvalidClusterSize;
+  if (nclusters < (P.gclusters > 1 ? P.gclusters : 1)) return cudaErrorInvalidClusterSize;
   return cudaLaunchKernelEx(&cfg, k, P, L, x0, u0, xo, uo, st, status);
 }
 

@@ -60,7 +60,7 @@ def create(ucn, prob, **over):
     (lambda d: setattr(d, "admm_iters", 0), "iteration"),
     (lambda d: setattr(d, "tr_min", -1.0), "trust"),
     (lambda d: setattr(d, "max_obs", 99), "max_obs"),
-    (lambda d: setattr(d, "group", 17), "group must be"),
+    (lambda d: setattr(d, "group", 1025), "group must be"),
     (lambda d: setattr(d, "group", -1), "group must be"),
     (lambda d: setattr(d, "group", 3), "not a multiple of group"),
 ])

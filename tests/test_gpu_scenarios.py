@@ -90,6 +90,18 @@ def test_largest_group_with_benchmark_records():
     compare(prob, ucn.UCN_PREC_FP32_REFINE, TOL32)
 
 
+@pytest.mark.parametrize("K", [17, 24, 32, 64])
+def test_groups_of_several_clusters_match_the_oracle(K):
+    # K > 16: clusters of the largest divisor <= 16 (1, 12, 16, 16 CTAs) whose
+    # rank-0 CTAs combine partial sums through global memory
+    compare(grouped(2, K, N=16, n_obs=3, seed=7), ucn.UCN_PREC_FP64, TOL64)
+
+
+def test_sixty_four_scenarios_with_benchmark_records():
+    prob = grouped(3, 64, N=40, n_obs=8, scp_iters=4, admm_iters=60)
+    compare(prob, ucn.UCN_PREC_FP32_REFINE, TOL32)
+
+
 def test_identical_scenarios_solve_like_one_instance():
     base = W.quad_box(1, seed=11, N_range=(16, 16), obs_range=(3, 3), settings=dict(FIXED))
     one = solve(base, ucn.UCN_PREC_FP64)
