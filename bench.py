@@ -332,6 +332,62 @@ def run_serving(args):
             "latency": "arrival -> result collected (host clock)"}
 
 
+def run_scenarios(args):
+    """Scenario-based robust MPC (Sec. IV-A): P quadrotor problems x K scenarios
+    (mass, drag) sharing the first control, N = 40, 8 obstacles; a receding
+    horizon of S steps, each one grouped solve (thread-block clusters, FP32 +
+    refinement) and one shift that applies the shared control and warm-starts
+    the next solve.  The plain FP64 path runs the first (cold) step of the same
+    problems."""
+    import torch
+    from paper_2603_10711_gb300 import ucn
+    P, K, S = args.scenario_problems, args.scenario_count, args.scenario_steps
+    prob = W.scenario_mpc(P, K, seed=3, N=40, n_obs=8)
+    for prec in (ucn.UCN_PREC_FP32_REFINE, ucn.UCN_PREC_FP64):     # warm-up: module load, cluster set-up
+        w = ucn.Solver(W.scenario_mpc(2, K, seed=13, N=40, n_obs=8, settings=dict(scp_iters=2, admm_iters=20)),
+                       precision=prec)
+        w.scp_solve(); torch.cuda.synchronize(); w.close()
+    kc = max(c for c in range(1, min(K, 16) + 1) if K % c == 0)
+    goal = prob.xtarget[::K, :3]
+    d0 = np.linalg.norm(prob.xinit[::K, :3] - goal, axis=1)
+    s = ucn.Solver(prob, precision=ucn.UCN_PREC_FP32_REFINE)
+    x0, u0 = s.tensor(prob.xguess), s.tensor(prob.uguess)
+    xg, ug = x0, u0
+    stream = torch.cuda.current_stream()
+    step_ms, passed, iters = [], 0, []
+    for k in range(S):
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.scp_solve(xg, ug)
+        xg, ug = s.mpc_shift()
+        e1.record(stream); e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        st = s.stats_host()
+        passed += int(np.sum(st["defect"] <= 1e-5))
+        iters.append(float(st["scp_iters"].mean()))
+    d1 = np.linalg.norm(xg.cpu().numpy()[prob.xoff[::K], :3] - goal, axis=1)
+    s.close()
+    total = sum(step_ms) / 1e3
+    # plain FP64: the cold first step of the same problems
+    s64 = ucn.Solver(W.scenario_mpc(P, K, seed=3, N=40, n_obs=8), precision=ucn.UCN_PREC_FP64)
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream); s64.scp_solve(x0, u0); e1.record(stream); e1.synchronize()
+    t64 = e0.elapsed_time(e1) / 1e3
+    st64 = s64.stats_host()
+    s64.close()
+    return {"workload": "scenario_mpc_%dx%d_N40" % (P, K), "problems": P, "scenarios": K, "mpc_steps": S,
+            "groups": "%d CTAs per group: %d thread-block cluster(s) of %d" % (K, K // kc, kc),
+            "problem_steps_per_s": P * S / total, "scenario_solves_per_s": P * K * S / total,
+            "step_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
+                        "first_cold": step_ms[0]},
+            "pass_rate": passed / (P * K * S), "scp_iters_mean_per_step": iters,
+            "goal_distance_m": {"start_mean": float(d0.mean()), "end_mean": float(d1.mean())},
+            "fp64_plain_cold_step": {"ms": 1e3 * t64, "scenario_solves_per_s": P * K / t64,
+                                     "pass_rate": float(np.mean(st64["defect"] <= 1e-5)),
+                                     "scp_iters_mean": float(st64["scp_iters"].mean())},
+            "fp32_cold_step_ms": step_ms[0]}
+
+
 def oracle_sample(args, seconds=None):
     """The FP64 CPU oracle on a bounded sample of the same workload."""
     import oracle
@@ -386,7 +442,10 @@ def main():
     ap.add_argument("--serving-requests", type=int, default=2000, help="requests of the serving stream (0: skip)")
     ap.add_argument("--serving-rate", type=float, default=2000.0, help="Poisson arrival rate of the serving stream")
     ap.add_argument("--serving-fp64-requests", type=int, default=16)
-    ap.add_argument("--mode", default="full", choices=["full", "kernel"],
+    ap.add_argument("--scenario-problems", type=int, default=256)
+    ap.add_argument("--scenario-count", type=int, default=64, help="scenarios per problem (group size)")
+    ap.add_argument("--scenario-steps", type=int, default=3, help="receding-horizon steps (0: skip the section)")
+    ap.add_argument("--mode", default="full", choices=["full", "kernel", "scenario"],
                     help="kernel: time only the fused kernel (profiler captures)")
     ap.add_argument("--scp-iters", type=int, default=0, help="fixed SCP iteration count (0: the workload's cap + stop test)")
     ap.add_argument("--fp64", action="store_true", help="kernel mode: the FP64 plain path")
@@ -400,6 +459,8 @@ def main():
         dist.init_process_group("nccl")
     if args.mode == "kernel":
         out = run_kernel_only(args)
+    elif args.mode == "scenario":
+        out = run_scenarios(args)
     elif args.impl == "reference":
         out = run_reference(args, rank, world)
     else:
