@@ -161,6 +161,15 @@ void ucn_problem_destroy(ucn_problem* prob);
  * Synchronous (copies the permutation).  Errors: UCN_EINVAL, UCN_ECUDA. */
 ucn_status ucn_problem_set_order(ucn_problem* prob, const int* order);
 
+/* Threads per time node of ucn_scp_solve (a scheduling choice; results agree
+ * to rounding).  1: one thread per node.  4 (the default for quadrotor problems
+ * of at most 128 nodes): the node's 16 rows split over 4 lanes of a warp that
+ * exchange vectors by shuffles -- 4x the resident warps and a quarter of the
+ * per-thread dependent chain.  UCN_EINVAL for other values, or 4 on a Mars or
+ * longer problem.  ucn_problem_lanes returns the current choice (-1: NULL). */
+ucn_status ucn_problem_set_lanes(ucn_problem* prob, int lanes_per_node);
+int ucn_problem_lanes(const ucn_problem* prob);
+
 /* Number of elements of the packed state / trajectory buffers. */
 long long ucn_total_x(const ucn_problem* prob);
 long long ucn_total_u(const ucn_problem* prob);

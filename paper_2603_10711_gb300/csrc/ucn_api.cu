@@ -12,6 +12,7 @@
 
 #include "ucn_internal.h"
 #include "ucn_kernels.cuh"
+#include "ucn_lanes.cuh"
 
 using namespace ucn;
 
@@ -41,6 +42,10 @@ long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
 namespace ucn {
 
 void set_error_message(const char* msg) { snprintf(g_err, sizeof(g_err), "%s", msg); }
+
+int default_tpn(int model, int nodes) {
+  return (model == UCN_MODEL_QUAD12 && 4 * nodes <= LANES_MAX_THREADS) ? 4 : 1;
+}
 
 Layout make_layout(int model, int nodes, int max_obs, int tsize, bool reg_mats) {
   const bool quad = model == UCN_MODEL_QUAD12;
@@ -85,6 +90,7 @@ struct ucn_problem {
   int* node_inst;
   int* order_d;
   int group, gcsize;     // scenarios per group, CTAs per thread-block cluster
+  int tpn;               // threads per node of the fused solve
 };
 
 namespace {
@@ -201,6 +207,7 @@ ucn_status ucn_problem_create(const ucn_problem_desc* d, ucn_problem** out) {
   ucn_problem* p = new ucn_problem();
   p->model = d->model; p->nx = NX; p->nu = NU; p->batch = d->batch; p->max_obs = d->model == UCN_MODEL_QUAD12 ? d->max_obs : 0;
   p->Nmax = Nmax; p->precision = d->precision; p->group = group;
+  p->tpn = default_tpn(d->model, Nmax + 1);
   const int B = d->batch;
   std::vector<long long> xoff(B), uoff(B), soff(B);
   std::vector<int> node_inst;
@@ -359,6 +366,17 @@ ucn_status ucn_problem_set_order(ucn_problem* p, const int* order) {
   return UCN_OK;
 }
 
+ucn_status ucn_problem_set_lanes(ucn_problem* p, int lanes_per_node) {
+  g_err[0] = 0;
+  if (!p) return fail(UCN_EINVAL, "null problem");
+  if (lanes_per_node == 1) { p->tpn = 1; return UCN_OK; }
+  if (lanes_per_node == 4 && default_tpn(p->model, p->Nmax + 1) == 4) { p->tpn = 4; return UCN_OK; }
+  return fail(UCN_EINVAL, "%d threads per node: 1, or 4 for quadrotor problems of at most %d nodes", lanes_per_node,
+              LANES_MAX_THREADS / 4);
+}
+
+int ucn_problem_lanes(const ucn_problem* p) { return p ? p->tpn : -1; }
+
 long long ucn_total_x(const ucn_problem* p) { return p ? p->total_x : -1; }
 long long ucn_total_u(const ucn_problem* p) { return p ? p->total_u : -1; }
 long long ucn_state_size(const ucn_problem* p) { return p ? p->state_size : -1; }
@@ -367,6 +385,7 @@ static LaunchCfg cfg_of(ucn_problem* p, void* stream) {
   LaunchCfg c;
   c.P = &p->dev; c.L = &p->L; c.smem = p->smem; c.smem_bytes = p->smem_bytes;
   c.threads = p->threads; c.blocks = p->batch; c.stream = as_stream(stream); c.group = p->gcsize;
+  c.nodes = p->Nmax + 1; c.tpn = p->tpn;
   return c;
 }
 

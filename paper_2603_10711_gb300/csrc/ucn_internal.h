@@ -25,8 +25,13 @@ struct LaunchCfg {
   int threads;          // CTA size
   int blocks;           // one CTA per instance
   cudaStream_t stream;
-  int group;            // scenarios per thread-block cluster (scenario groups only)
+  int group;            // CTAs per thread-block cluster (scenario groups only)
+  int nodes;            // nodes of the longest instance (N_max + 1)
+  int tpn;              // threads per node of the fused solve: 1, or 4 (lane kernel, quadrotor)
 };
+
+// Threads per node the fused solve uses by default for a model and node count.
+int default_tpn(int model, int nodes);
 
 // Launchers, one translation unit per (model, precision) so that the four
 // compile in parallel.

@@ -1,0 +1,704 @@
+// Lane-parallel fused SCP kernel: TPN consecutive threads of a warp share one
+// time node.  Lane q owns the rows r of xi = (x_i, u_i) with r % TPN == q
+// (x rows q, q+TPN, ..., control rows NX+q, NX+q+TPN, ...), computes their
+// parts of Steps 1-4 (Sec. III-B), and the lanes of a node exchange whole
+// vectors with warp shuffles.  Compared with one thread per node this divides
+// the dependent chain of the per-node mat-vecs by TPN and multiplies the
+// resident warps by TPN -- the one-thread kernel of a 16-row node runs 1-2
+// warps per scheduler and is latency-bound.  The per-SCP-iteration work
+// (assembly and factorisation, the FP64 rollout, acceptance) stays on lane 0;
+// the Jacobian directions are split over the lanes.
+#pragma once
+#include "ucn_kernels.cuh"
+
+namespace ucn {
+
+constexpr int LANES_MAX_THREADS = 512;   // CTA size cap of the lane kernel
+constexpr unsigned WARP_ALL = 0xffffffffu;
+
+template <class M, int TPN>
+struct LaneRows {
+  static constexpr int NX = M::NX, NU = M::NU, NN = NX + NU;
+  static_assert(NX % TPN == 0 && NU % TPN == 0, "rows must split evenly over the lanes");
+  static constexpr int RX = NX / TPN, RU = NU / TPN, R = RX + RU;
+};
+
+// full[r] for every row r of a node from the lanes' own rows (shuffles inside
+// the TPN-lane segment; every thread of the warp must call it).
+template <class M, int TPN, class T>
+__device__ __forceinline__ void lanes_gather(const T* own, T* full) {
+  using LR = LaneRows<M, TPN>;
+#pragma unroll
+  for (int s = 0; s < TPN; ++s) {
+#pragma unroll
+    for (int m = 0; m < LR::RX; ++m) full[s + TPN * m] = __shfl_sync(WARP_ALL, own[m], s, TPN);
+#pragma unroll
+    for (int m = 0; m < LR::RU; ++m) full[LR::NX + s + TPN * m] = __shfl_sync(WARP_ALL, own[LR::RX + m], s, TPN);
+  }
+}
+
+// The x-rows only (NX entries).
+template <class M, int TPN, class T>
+__device__ __forceinline__ void lanes_gather_x(const T* own, T* full) {
+  using LR = LaneRows<M, TPN>;
+#pragma unroll
+  for (int s = 0; s < TPN; ++s)
+#pragma unroll
+    for (int m = 0; m < LR::RX; ++m) full[s + TPN * m] = __shfl_sync(WARP_ALL, own[m], s, TPN);
+}
+
+// Sum of v[0..n) over the TPN lanes of a node (butterfly).
+template <int TPN, int n, class T>
+__device__ __forceinline__ void lanes_allreduce(T* v) {
+#pragma unroll
+  for (int o = 1; o < TPN; o <<= 1)
+#pragma unroll
+    for (int k = 0; k < n; ++k) v[k] += __shfl_xor_sync(WARP_ALL, v[k], o, TPN);
+}
+
+// Row r of xi owned by lane q as its m-th row.
+template <class M, int TPN>
+__device__ __forceinline__ int own_row(int q, int m) {
+  using LR = LaneRows<M, TPN>;
+  return m < LR::RX ? q + TPN * m : LR::NX + q + TPN * (m - LR::RX);
+}
+
+// The lane's rows of the cached H^-1: registers for FP32 (loaded once per SCP
+// iteration), the packed record in shared memory for FP64.
+template <class M, class T, int TPN, bool REG>
+struct LaneH;
+template <class M, class T, int TPN>
+struct LaneH<M, T, TPN, true> {
+  static constexpr int NN = M::NX + M::NU, R = LaneRows<M, TPN>::R;
+  T h[R][NN];
+  template <class MS>
+  __device__ __forceinline__ void load(const MS& MT, int q, bool active) {
+#pragma unroll
+    for (int m = 0; m < R; ++m) {
+      const int r = own_row<M, TPN>(q, m);
+#pragma unroll
+      for (int c = 0; c < NN; ++c) h[m][c] = active ? MT.H(r >= c ? pk(r, c) : pk(c, r)) : T(0);
+    }
+  }
+  template <class MS>
+  __device__ __forceinline__ T get(const MS&, int, int m, int c) const { return h[m][c]; }
+};
+template <class M, class T, int TPN>
+struct LaneH<M, T, TPN, false> {
+  int rb[LaneRows<M, TPN>::R];   // packed offset of the start of each own row
+  template <class MS>
+  __device__ __forceinline__ void load(const MS&, int q, bool) {
+#pragma unroll
+    for (int m = 0; m < LaneRows<M, TPN>::R; ++m) { const int r = own_row<M, TPN>(q, m); rb[m] = r * (r + 1) / 2; }
+  }
+  template <class MS>
+  __device__ __forceinline__ T get(const MS& MT, int q, int m, int c) const {
+    const int r = own_row<M, TPN>(q, m);
+    return MT.H(r >= c ? rb[m] + c : pk(c, 0) + r);
+  }
+};
+
+// A_i, B_i (Eq. (2b)): the NN forward-mode directions split over the lanes.
+template <class M, class T, bool AOS, int TPN, class MS>
+__device__ __forceinline__ void lanes_jacobians(const Node<T, AOS>& nd, const MS& MT, const T* prm, double h, int q) {
+  constexpr int NX = M::NX, NU = M::NU;
+  double xb[NX], ub[NU];
+  read_nominal<M, T, AOS>(nd, true, xb, ub);
+  T xt[NX], ut[NU];
+#pragma unroll
+  for (int j = 0; j < NX; ++j) xt[j] = (T)xb[j];
+#pragma unroll
+  for (int j = 0; j < NU; ++j) ut[j] = (T)ub[j];
+  for (int dir = q; dir < NX + NU; dir += TPN) {
+    T col[NX];
+    rk4_jvp<M, T>(prm, h, xt, ut, dir, col);
+#pragma unroll
+    for (int r = 0; r < NX; ++r) {
+      if (dir < NX) MT.A(r * NX + dir) = col[r];
+      else MT.B(r * NU + (dir - NX)) = col[r];
+    }
+  }
+}
+
+// The lane's rows of the cost gradient (q_i, r_i) in deviations and of the
+// diagonal of H_i without its A/B and mirror Gram terms (the same numbers as
+// node_setup's NodeConst, for the own rows only).
+template <class M, class T, bool AOS, int TPN>
+__device__ __forceinline__ void lanes_consts(const Node<T, AOS>& nd, const ProblemDev& P, int b, int q, T re, T rg,
+                                             T* kq, T* khd) {
+  using LR = LaneRows<M, TPN>;
+  constexpr int NX = M::NX, NU = M::NU;
+  const int i = nd.i, N = nd.N;
+  const bool term = (i == N);
+#pragma unroll
+  for (int m = 0; m < LR::RX; ++m) {
+    const int j = q + TPN * m;
+    const double w = term ? P.QNd[b * NX + j] : P.Qd[b * NX + j];
+    kq[m] = (T)(w * (nd.dat(Rec<M>::Xbar, j) - P.xref[b * NX + j]) + (term ? P.qN[b * NX + j] : 0.0));
+    khd[m] = (T)w + rg + (i > 0 ? re : T(0));
+  }
+#pragma unroll
+  for (int m = 0; m < LR::RU; ++m) {
+    const int j = q + TPN * m;
+    if (term) {
+      kq[LR::RX + m] = T(0);
+      khd[LR::RX + m] = T(1);
+    } else {
+      kq[LR::RX + m] = (T)(P.Rd[b * NU + j] * (nd.dat(Rec<M>::Ubar, j) - P.uref[b * NU + j]));
+      khd[LR::RX + m] = (T)P.Rd[b * NU + j] + rg;
+    }
+  }
+}
+
+// One iteration of Steps 1-4 over the CTA's instance, lane-parallel.  Every
+// thread of the CTA calls it (inactive nodes with zero data: the shuffles
+// need whole warps).  Quadrotor mirror sets (linearised obstacles) only.
+template <class M, class T, bool AOS, bool REFINE, bool LAST, bool GROUP, int TPN, class MS, class HR>
+__device__ __forceinline__ void admm_iteration_lanes(const Node<T, AOS>& nd, const MS& MT, const HR& H, const Layout& L,
+                                                     const Inst<T>& I, const T* kq, const T* khd, bool active, int q,
+                                                     T re, T rd, T rg, T irg, T ired, double& rp, double& rdl,
+                                                     GroupShared* G, GroupX& X, const ProblemDev& P) {
+  static_assert(IsQuad<M>::value, "the lane kernel carries the quadrotor's mirror sets");
+  using LR = LaneRows<M, TPN>;
+  constexpr int NX = M::NX, NU = M::NU, NN = NX + NU, RX = LR::RX, RU = LR::RU, R = LR::R;
+  const int i = nd.i, N = nd.N;
+  const bool hasU = active && i < N;
+  T xo[R];      // own rows of xi
+  T xf[NN];     // all rows of xi (after the final gather)
+  // ---- Step 1: g_i (own rows), H_i xi = g_i by the cached inverse (+ one refinement)
+  {
+    T w[NX];
+#pragma unroll
+    for (int k = 0; k < NX; ++k) w[k] = hasU ? nd.nb(Rec<M>::Ex2, k, i + 1) - rd * nd.at(Rec<M>::C, k) : T(0);
+    T g[R];
+#pragma unroll
+    for (int m = 0; m < RX; ++m) {
+      const int j = q + TPN * m;
+      T v = T(0);
+      if (active) {
+        v = -kq[m] + rg * nd.at(Rec<M>::Xh, j) - nd.at(Rec<M>::Nux, j);
+        if (i > 0) v += re * nd.at(Rec<M>::Z, j) - nd.at(Rec<M>::Lam, j);
+        if (hasU) {
+          T acc = T(0);
+#pragma unroll
+          for (int k = 0; k < NX; ++k) acc += MT.A(k * NX + j) * w[k];
+          v += acc;
+        }
+        if (m == 0 && j < 3)
+          for (int o = 0; o < I.nobs; ++o) v += nd.at(L.oMd, 4 * o + j) * (rg * nd.at(L.oS, o) - nd.at(L.oNus, o));
+      }
+      g[m] = v;
+    }
+#pragma unroll
+    for (int m = 0; m < RU; ++m) {
+      const int j = q + TPN * m;
+      T v = T(0);
+      if (hasU) {
+        T acc = T(0);
+#pragma unroll
+        for (int k = 0; k < NX; ++k) acc += MT.B(k * NU + j) * w[k];
+        v = -kq[RX + m] + acc + rg * nd.at(Rec<M>::Uh, j) - nd.at(Rec<M>::Nuu, j);
+      }
+      g[RX + m] = v;
+    }
+    T gf[NN];
+    lanes_gather<M, TPN>(g, gf);
+#pragma unroll
+    for (int m = 0; m < R; ++m) {
+      T t = T(0);
+      if (active) {
+#pragma unroll
+        for (int c = 0; c < NN; ++c) t += H.get(MT, q, m, c) * gf[c];
+      }
+      xo[m] = t;
+    }
+    if constexpr (REFINE) {
+      // residual g - H xi with H applied from A, B, the diagonals and the mirror Gram terms
+      lanes_gather<M, TPN>(xo, xf);
+      T vo[RX];
+#pragma unroll
+      for (int m = 0; m < RX; ++m) {
+        const int k = q + TPN * m;
+        T acc = T(0);
+        if (hasU) {
+#pragma unroll
+          for (int c = 0; c < NX; ++c) acc += MT.A(k * NX + c) * xf[c];
+#pragma unroll
+          for (int c = 0; c < NU; ++c) acc += MT.B(k * NU + c) * xf[NX + c];
+        }
+        vo[m] = rd * acc;
+      }
+      T vf[NX];
+      lanes_gather_x<M, TPN>(vo, vf);
+      T res[R];
+#pragma unroll
+      for (int m = 0; m < RX; ++m) {
+        const int j = q + TPN * m;
+        T hx = khd[m] * xo[m];
+        if (hasU) {
+#pragma unroll
+          for (int k = 0; k < NX; ++k) hx += MT.A(k * NX + j) * vf[k];
+        }
+        if (active && m == 0 && j < 3)
+          for (int o = 0; o < I.nobs; ++o) {
+            const T n0 = nd.at(L.oMd, 4 * o), n1 = nd.at(L.oMd, 4 * o + 1), n2 = nd.at(L.oMd, 4 * o + 2);
+            hx += nd.at(L.oMd, 4 * o + j) * (rg * (n0 * xf[0] + n1 * xf[1] + n2 * xf[2]));
+          }
+        res[m] = g[m] - hx;
+      }
+#pragma unroll
+      for (int m = 0; m < RU; ++m) {
+        const int j = q + TPN * m;
+        T hx = khd[RX + m] * xo[RX + m];
+        if (hasU) {
+#pragma unroll
+          for (int k = 0; k < NX; ++k) hx += MT.B(k * NU + j) * vf[k];
+        }
+        res[RX + m] = g[RX + m] - hx;
+      }
+      T rf[NN];
+      lanes_gather<M, TPN>(res, rf);
+#pragma unroll
+      for (int m = 0; m < R; ++m) {
+        T t = T(0);
+        if (active) {
+#pragma unroll
+          for (int c = 0; c < NN; ++c) t += H.get(MT, q, m, c) * rf[c];
+        }
+        xo[m] += t;
+      }
+    }
+    lanes_gather<M, TPN>(xo, xf);
+    if (active) {
+      // linearised propagation d_dyn,i = A x + B u + c_i, published to node i+1
+      if (hasU) {
+#pragma unroll
+        for (int m = 0; m < RX; ++m) {
+          const int k = q + TPN * m;
+          T acc = nd.at(Rec<M>::C, k);
+#pragma unroll
+          for (int c = 0; c < NX; ++c) acc += MT.A(k * NX + c) * xf[c];
+#pragma unroll
+          for (int c = 0; c < NU; ++c) acc += MT.B(k * NU + c) * xf[NX + c];
+          nd.at(Rec<M>::Ex1, k) = acc;
+        }
+      }
+#pragma unroll
+      for (int m = 0; m < RX; ++m) nd.at(Rec<M>::X, q + TPN * m) = xo[m];
+      if (hasU) {
+#pragma unroll
+        for (int m = 0; m < RU; ++m) nd.at(Rec<M>::U, q + TPN * m) = xo[RX + m];
+      }
+    }
+  }
+  __syncthreads();
+  T dz[RX];
+  T sv[R];
+#pragma unroll
+  for (int m = 0; m < R; ++m) sv[m] = T(0);
+#pragma unroll
+  for (int m = 0; m < RX; ++m) dz[m] = T(0);
+  T msv[3] = {T(0), T(0), T(0)};
+  if (active) {
+    // ---- Step 2: dynamic consensus, Eq. (5), then its duals (Step 4)
+    if (i >= 1) {
+#pragma unroll
+      for (int m = 0; m < RX; ++m) {
+        const int j = q + TPN * m;
+        const T dd = nd.nb(Rec<M>::Ex1, j, i - 1);
+        const T zo = nd.at(Rec<M>::Z, j);
+        const T lam = nd.at(Rec<M>::Lam, j), mu = nd.at(Rec<M>::Mu, j);
+        const T z = (re * xo[m] + lam + rd * dd - mu) * ired;
+        nd.at(Rec<M>::Z, j) = z;
+        nd.at(Rec<M>::Lam, j) = lam + re * (xo[m] - z);
+        nd.at(Rec<M>::Mu, j) = mu + rd * (z - dd);
+        dz[m] = z - zo;
+        if (LAST) {
+          sv[m] += re * dz[m];
+          rp += (double)(xo[m] - z) * (double)(xo[m] - z) + (double)(z - dd) * (double)(z - dd);
+        }
+      }
+    }
+    // ---- Step 3: projections onto the boxes (Eq. (7)) and Step 4 for nu_x, nu_u
+#pragma unroll
+    for (int m = 0; m < RX; ++m) {
+      const int j = q + TPN * m;
+      const T nux = nd.at(Rec<M>::Nux, j);
+      const T xh = clampv(xo[m] + nux * irg, nd.at(Rec<M>::Xlo, j), nd.at(Rec<M>::Xhi, j));
+      if (LAST) { sv[m] += rg * (xh - nd.at(Rec<M>::Xh, j)); rp += (double)(xo[m] - xh) * (double)(xo[m] - xh); }
+      nd.at(Rec<M>::Xh, j) = xh;
+      nd.at(Rec<M>::Nux, j) = nux + rg * (xo[m] - xh);
+    }
+    if (i < N) {
+#pragma unroll
+      for (int m = 0; m < RU; ++m) {
+        const int j = q + TPN * m;
+        const T nuu = nd.at(Rec<M>::Nuu, j);
+        if constexpr (GROUP) {
+          if (i == 0) {   // sum of arguments | max of lower bounds | max of -upper bounds
+            const double ub = nd.dat(Rec<M>::Ubar, j);
+            double* mm = G->mine[X.epoch & 1];
+            mm[j] = ub + (double)(xo[RX + m] + nuu * irg);
+            mm[NU + j] = ub + (double)nd.at(Rec<M>::Ulo, j);
+            mm[2 * NU + j] = -(ub + (double)nd.at(Rec<M>::Uhi, j));
+            continue;
+          }
+        }
+        const T uh = clampv(xo[RX + m] + nuu * irg, nd.at(Rec<M>::Ulo, j), nd.at(Rec<M>::Uhi, j));
+        if (LAST) {
+          sv[RX + m] += rg * (uh - nd.at(Rec<M>::Uh, j));
+          rp += (double)(xo[RX + m] - uh) * (double)(xo[RX + m] - uh);
+        }
+        nd.at(Rec<M>::Uh, j) = uh;
+        nd.at(Rec<M>::Nuu, j) = nuu + rg * (xo[RX + m] - uh);
+      }
+    }
+    // linearised obstacles (mirror half-spaces on the position), split over the lanes
+    for (int o = q; o < I.nobs; o += TPN) {
+      const T n0 = nd.at(L.oMd, 4 * o), n1 = nd.at(L.oMd, 4 * o + 1), n2 = nd.at(L.oMd, 4 * o + 2);
+      const T bd = nd.at(L.oMd, 4 * o + 3);
+      const T y = n0 * xf[0] + n1 * xf[1] + n2 * xf[2];
+      const T so = nd.at(L.oS, o);
+      const T s = maxv(bd, y + nd.at(L.oNus, o) * irg);
+      nd.at(L.oS, o) = s;
+      nd.at(L.oNus, o) += rg * (y - s);
+      if (LAST) {
+        const T ds = rg * (s - so);
+        msv[0] += n0 * ds; msv[1] += n1 * ds; msv[2] += n2 * ds;
+        rp += (double)(y - s) * (double)(y - s);
+      }
+    }
+  }
+  if constexpr (GROUP) {
+    double tot[3 * NU];
+#pragma unroll
+    for (int j = 0; j < 3 * NU; ++j) tot[j] = 0.0;
+    group_allreduce<3 * NU>(P, G, X, NU, tot);
+#pragma unroll
+    for (int j = 0; j < 3 * NU; ++j) tot[j] = __shfl_sync(WARP_ALL, tot[j], 0, TPN);
+    if (active && i == 0 && i < N) {
+#pragma unroll
+      for (int m = 0; m < RU; ++m) {
+        const int j = q + TPN * m;
+        const double v = fmin(fmax(tot[j] / (double)P.group, tot[NU + j]), -tot[2 * NU + j]);
+        G->u0[j] = v;
+        const T uh = (T)(v - nd.dat(Rec<M>::Ubar, j));
+        const T nuu = nd.at(Rec<M>::Nuu, j);
+        if (LAST) {
+          sv[RX + m] += rg * (uh - nd.at(Rec<M>::Uh, j));
+          rp += (double)(xo[RX + m] - uh) * (double)(xo[RX + m] - uh);
+        }
+        nd.at(Rec<M>::Uh, j) = uh;
+        nd.at(Rec<M>::Nuu, j) = nuu + rg * (xo[RX + m] - uh);
+      }
+    }
+  }
+  if constexpr (LAST) {
+    // the obstacle terms of the dual residual belong to the position rows
+    lanes_allreduce<TPN, 3>(msv);
+    if (q < 3) sv[0] += msv[q == 0 ? 0 : (q == 1 ? 1 : 2)];
+    // dual residual needs rho_dyn (z_{i+1,new} - z_{i+1,old}) from the right neighbour
+    __syncthreads();
+    if (active && i >= 1) {
+#pragma unroll
+      for (int m = 0; m < RX; ++m) nd.at(Rec<M>::Ex1, q + TPN * m) = rd * dz[m];
+    }
+    __syncthreads();
+    if (hasU) {
+      T e[NX];
+#pragma unroll
+      for (int k = 0; k < NX; ++k) e[k] = nd.nb(Rec<M>::Ex1, k, i + 1);
+#pragma unroll
+      for (int m = 0; m < RX; ++m) {
+        const int j = q + TPN * m;
+        T acc = T(0);
+#pragma unroll
+        for (int k = 0; k < NX; ++k) acc += MT.A(k * NX + j) * e[k];
+        sv[m] += acc;
+      }
+#pragma unroll
+      for (int m = 0; m < RU; ++m) {
+        const int j = q + TPN * m;
+        T acc = T(0);
+#pragma unroll
+        for (int k = 0; k < NX; ++k) acc += MT.B(k * NU + j) * e[k];
+        sv[RX + m] += acc;
+      }
+    }
+    if (active) {
+#pragma unroll
+      for (int m = 0; m < R; ++m)
+        if (m < RX || i < N) rdl += (double)sv[m] * (double)sv[m];
+    }
+  }
+  if (active && i >= 1) {
+#pragma unroll
+    for (int m = 0; m < RX; ++m) {
+      const int j = q + TPN * m;
+      nd.at(Rec<M>::Ex2, j) = nd.at(Rec<M>::Mu, j) + rd * nd.at(Rec<M>::Z, j);
+    }
+  }
+  __syncthreads();
+}
+
+template <class M, class T, bool AOS, bool REFINE, bool GROUP, int TPN, class MS, class HR>
+__device__ __forceinline__ void admm_iterations_lanes(const Node<T, AOS>& nd, const MS& MT, const HR& H, const Layout& L,
+                                                      const Inst<T>& I, const T* kq, const T* khd, bool active, int q,
+                                                      T re, T rd, T rg, int iters, InstShared& sh, double* res,
+                                                      GroupShared* G, GroupX& X, const ProblemDev& P) {
+  const T irg = T(1) / rg, ired = T(1) / (re + rd);
+  double rp = 0.0, rdl = 0.0;
+  for (int it = 0; it + 1 < iters; ++it)
+    admm_iteration_lanes<M, T, AOS, REFINE, false, GROUP, TPN>(nd, MT, H, L, I, kq, khd, active, q, re, rd, rg, irg,
+                                                               ired, rp, rdl, G, X, P);
+  admm_iteration_lanes<M, T, AOS, REFINE, true, GROUP, TPN>(nd, MT, H, L, I, kq, khd, active, q, re, rd, rg, irg, ired,
+                                                            rp, rdl, G, X, P);
+  double v[2] = {rp, rdl};
+  block_reduce(sh, v, 2, 2);
+  res[0] = sqrt(v[0]);
+  res[1] = sqrt(v[1]);
+}
+
+// Node view of node `i` (the lane kernel maps TPN threads to a node).
+template <class T, bool SMEM>
+__device__ __forceinline__ Node<T, SMEM> make_node_at(const ProblemDev& P, const Layout& L, unsigned char* smem, int b,
+                                                      int i) {
+  Node<T, SMEM> nd = make_node<T, SMEM>(P, L, smem, b);
+  nd.i = i;
+  return nd;
+}
+
+// The fused SCP solve (as scp_kernel) with TPN lanes per node.
+template <class M, class T, bool SMEM, bool REFINE, bool GROUP, int TPN>
+__global__ void __launch_bounds__(LANES_MAX_THREADS) scp_kernel_lanes(ProblemDev P, Layout L, const double* x0,
+                                                                      const double* u0, double* xout, double* uout,
+                                                                      ucn_scp_stats* stats, int* status_out) {
+  using LR = LaneRows<M, TPN>;
+  constexpr int NX = M::NX, NU = M::NU, NN = NX + NU, R = LR::R;
+  static_assert(!GROUP || NU <= 4, "GroupShared holds nu <= 4");
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ InstShared sh;
+  GroupShared* G = group_slot<GROUP>();
+  GroupX X{0u, 0, 0};
+  if constexpr (GROUP) {
+    X.g = (int)blockIdx.x / P.group;
+    X.c = ((int)blockIdx.x % P.group) / (int)cluster_size();
+    if (threadIdx.x == 0) G->gfail = 0;
+  }
+  const int b = (GROUP || !P.order) ? (int)blockIdx.x : P.order[blockIdx.x];
+  constexpr bool AOS = SMEM;
+  const int q = (int)threadIdx.x % TPN;
+  Node<T, AOS> nd = make_node_at<T, SMEM>(P, L, smem, b, (int)threadIdx.x / TPN);
+  SmemMats<M, T, AOS> MT;
+  init_mats<M, T, AOS>(MT, nd, L);
+  LaneH<M, T, TPN, std::is_same<T, float>::value> H;
+  const int i = nd.i, N = nd.N;
+  const bool active = i <= N;
+  const bool lead = active && q == 0;
+  const long long xo = P.xoff[b], uo = P.uoff[b];
+  const double* prm = P.params + b * 8;
+  const double h = P.dt[b];
+  const unsigned long long t0 = globaltimer_ns();
+  const Inst<T> I = make_inst<M, T>(P, b);
+  NodeConst<M, T> K;
+  T kq[R], khd[R];
+#pragma unroll
+  for (int m = 0; m < R; ++m) { kq[m] = T(0); khd[m] = T(0); }
+  if (threadIdx.x == 0) { sh.fail = 0; sh.status = ST_OK; sh.radius = P.tr_init; sh.stop = 0; }
+  if (lead) load_nominal<M, T, AOS>(nd, L, x0, u0, xo, uo);
+  __syncthreads();
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  if (lead) {
+    double xb[NX], ub[NU];
+    read_nominal<M, T, AOS>(nd, i < N, xb, ub);
+    acc[0] = node_cost<M, T>(P, I, b, i, N, xb, ub);
+    if (i < N) {
+      double fn[NX];
+      rk4<M, double>(prm, h, xb, ub, fn);
+      for (int j = 0; j < NX; ++j) {
+        const double e = fn[j] - nd.dnb(Rec<M>::Xbar, j, i + 1);
+        nd.at(Rec<M>::C, j) = (T)e;
+        acc[1] += fabs(e);
+      }
+    }
+  }
+  block_reduce(sh, acc, 2, 2);
+  if (threadIdx.x == 0) sh.Jn = acc[0] + P.w_d * acc[1];
+  if (lead) node_cold_start<M, T, AOS>(nd, L);
+  __syncthreads();
+  int accepted = 0, iters_run = 0;
+  unsigned long long mask = 0ull;
+  double res[2] = {0, 0}, last_step = 0.0;
+  const int Kscp = P.scp_iters;
+  for (int k = 0; k < Kscp; ++k) {
+    if (threadIdx.x == 0) {
+      double f = 1.0;
+      if (P.rho_final > 0.0 && Kscp > 1) f = pow(P.rho_final / P.rho_geo, (double)k / (double)(Kscp - 1));
+      sh.fac = f;
+    }
+    __syncthreads();
+    const double fac = sh.fac;
+    const T re = (T)(P.rho_eq * fac), rd = (T)(P.rho_dyn * fac), rg = (T)(P.rho_geo * fac);
+    const double radius = sh.radius;
+    if (active && i < N) lanes_jacobians<M, T, AOS, TPN>(nd, MT, I.prm, h, q);
+    if (active) lanes_consts<M, T, AOS, TPN>(nd, P, b, q, re, rg, kq, khd);
+    __syncthreads();
+    if (lead) {
+      node_setup<M, T, AOS>(nd, L, P, b, radius, re, rg, K);
+      const bool ok = node_factor<M, T, AOS, NN>(nd, MT, L, I, K, rd, rg);
+      if (!ok) atomicOr(&sh.fail, 1);
+      node_reseed<M, T, AOS>(nd, L, I);
+      publish_ex2<M, T, AOS>(nd, L, true, rd);
+    }
+    __syncthreads();
+    H.load(MT, q, active);
+    if constexpr (GROUP) {
+      if (threadIdx.x == 0) G->mine[X.epoch & 1][0] = (double)sh.fail;
+      double f[1];
+      group_allreduce<1>(P, G, X, 0, f);
+      if (threadIdx.x == 0) sh.fail = f[0] != 0.0;
+      __syncthreads();
+    }
+    if (sh.fail) { if (threadIdx.x == 0) sh.status = ST_NUMERIC; iters_run++; break; }
+    admm_iterations_lanes<M, T, AOS, REFINE, GROUP, TPN>(nd, MT, H, L, I, kq, khd, active, q, re, rd, rg, P.admm_iters,
+                                                         sh, res, G, X, P);
+    ++iters_run;
+    // ---- candidate (x-hat, u-hat): FP64 rollout, defects, cost, linear model (lane 0)
+    double xc[NX], uc[NU], fc[NX];
+    if (lead) {
+      for (int j = 0; j < NX; ++j) { xc[j] = nd.dat(Rec<M>::Xbar, j) + (double)nd.at(Rec<M>::Xh, j); nd.dat(Rec<M>::Xc, j) = xc[j]; }
+      for (int j = 0; j < NU; ++j) uc[j] = (i < N) ? nd.dat(Rec<M>::Ubar, j) + (double)nd.at(Rec<M>::Uh, j) : 0.0;
+      if constexpr (GROUP) {
+        if (i == 0)
+          for (int j = 0; j < NU; ++j) uc[j] = G->u0[j];
+      }
+    }
+    __syncthreads();
+    double v[6] = {0, 0, 0, 0, 0};
+    if (lead) {
+      v[0] = node_cost<M, T>(P, I, b, i, N, xc, uc);
+      T st = T(0);
+      for (int j = 0; j < NX; ++j) st = maxv(st, absv(nd.at(Rec<M>::Xh, j)));
+      if (i < N) {
+        for (int j = 0; j < NU; ++j) st = maxv(st, absv(nd.at(Rec<M>::Uh, j)));
+        rk4<M, double>(prm, h, xc, uc, fc);
+        double dinf = 0.0;
+        T lin1 = T(0);
+        for (int r = 0; r < NX; ++r) {
+          fc[r] -= nd.dnb(Rec<M>::Xc, r, i + 1);
+          v[1] += fabs(fc[r]);
+          dinf = fmax(dinf, fabs(fc[r]));
+          T lin = nd.at(Rec<M>::C, r) - nd.nb(Rec<M>::Xh, r, i + 1);
+          for (int c = 0; c < NX; ++c) lin += MT.A(r * NX + c) * nd.at(Rec<M>::Xh, c);
+          for (int c = 0; c < NU; ++c) lin += MT.B(r * NU + c) * nd.at(Rec<M>::Uh, c);
+          lin1 += absv(lin);
+        }
+        v[2] = (double)lin1;
+        v[3] = dinf;
+      }
+      v[4] = (double)st;
+    }
+    block_reduce(sh, v, 3, 5);
+    bool timed_out = false;
+    if (threadIdx.x == 0) timed_out = globaltimer_ns() - t0 > P.timeout_ns;
+    double Jn = sh.Jn, Jc = v[0] + P.w_d * v[1], Lc = v[0] + P.w_d * v[2];
+    const double Jc_own = Jc;
+    if constexpr (GROUP) {
+      if (threadIdx.x == 0) {
+        double* m = G->mine[X.epoch & 1];
+        m[0] = Jn; m[1] = Jc; m[2] = Lc; m[3] = v[3]; m[4] = v[4]; m[5] = timed_out ? 1.0 : 0.0;
+      }
+      double a[6];
+      group_allreduce<6>(P, G, X, 3, a);
+      if (threadIdx.x == 0) {
+        Jn = a[0]; Jc = a[1]; Lc = a[2]; v[3] = a[3]; v[4] = a[4]; timed_out = a[5] != 0.0;
+      }
+    }
+    if (threadIdx.x == 0) {
+      // acceptance (the paper omits it; ratio test on an l1 merit)
+      const double den = Jn - Lc, num = Jn - Jc;
+      double radius2 = sh.radius;
+      bool acc_ = true;
+      if (!(den <= 1e-12)) {
+        const double ratio = num / den;
+        acc_ = ratio > 0.0;
+        if (ratio < 0.25) radius2 *= 0.5;
+        else if (ratio > 0.75) radius2 = fmin(2.0 * radius2, P.tr_max);
+      }
+      radius2 = fmax(radius2, P.tr_min);
+      if (!isfinite(Jc)) { acc_ = false; sh.status = ST_NUMERIC; }
+      if (acc_) sh.Jn = Jc_own;
+      sh.radius = radius2;
+      sh.accept = acc_;
+      int stop = (sh.status == ST_NUMERIC);
+      if (P.stop && acc_ && v[3] <= P.defect_tol && v[4] <= P.step_tol) stop = 1;
+      if (timed_out && !stop && k + 1 < Kscp) { sh.status = ST_TIMEOUT; stop = 1; }
+      sh.stop = stop;
+    }
+    __syncthreads();
+    last_step = v[4];
+    if (sh.accept) {
+      ++accepted;
+      if (k < 64) mask |= (1ull << k);
+      if (lead) {
+        node_rebase_mirrors<M, T, AOS>(nd, L, P, b);
+        for (int j = 0; j < NX; ++j) {
+          const T xh = nd.at(Rec<M>::Xh, j);
+          nd.dat(Rec<M>::Xbar, j) = xc[j];
+          nd.at(Rec<M>::X, j) -= xh;
+          if (i >= 1) nd.at(Rec<M>::Z, j) -= xh;
+          nd.at(Rec<M>::Xh, j) = T(0);
+          if (i < N) nd.at(Rec<M>::C, j) = (T)fc[j];
+        }
+        if (i < N)
+          for (int j = 0; j < NU; ++j) {
+            const T uh = nd.at(Rec<M>::Uh, j);
+            nd.dat(Rec<M>::Ubar, j) = uc[j];
+            nd.at(Rec<M>::U, j) -= uh;
+            nd.at(Rec<M>::Uh, j) = T(0);
+          }
+      }
+    }
+    __syncthreads();
+    if (sh.stop) break;
+  }
+  double w[6] = {0, 0, 0, 0, 0, 0};
+  if (lead) {
+    double xb[NX], ub[NU];
+    read_nominal<M, T, AOS>(nd, i < N, xb, ub);
+    w[0] = node_cost<M, T>(P, I, b, i, N, xb, ub);
+    if (i < N) {
+      double fn[NX];
+      rk4<M, double>(prm, h, xb, ub, fn);
+      for (int j = 0; j < NX; ++j) {
+        const double e = fabs(fn[j] - nd.dnb(Rec<M>::Xbar, j, i + 1));
+        w[1] += e;
+        w[2] = fmax(w[2], e);
+      }
+    }
+    for (int j = 0; j < NX; ++j) xout[(xo + i) * NX + j] = xb[j];
+    if (i < N)
+      for (int j = 0; j < NU; ++j) uout[(uo + i) * NU + j] = ub[j];
+    node_export<M, T, AOS>(nd, L, P, b, P.state_abs + P.soff[b]);
+  }
+  block_reduce(sh, w, 2, 3);
+  if (threadIdx.x == 0) {
+    int st = sh.status;
+    if constexpr (GROUP) {
+      if (G->gfail && st != ST_NUMERIC) st = ST_TIMEOUT;
+    }
+    if (!isfinite(w[2])) st = ST_NUMERIC;
+    if (st == ST_OK && !(w[2] <= P.defect_tol)) st = ST_NOTCONV;
+    ucn_scp_stats s;
+    s.defect = w[2]; s.cost = w[0]; s.merit = w[0] + P.w_d * w[1];
+    s.primal_res = res[0]; s.dual_res = res[1]; s.tr_radius = sh.radius; s.step = last_step;
+    s.scp_iters = iters_run; s.accepted = accepted; s.accept_mask = mask; s.status = st; s.reserved = 0;
+    s.t_start_ns = t0; s.t_end_ns = globaltimer_ns();
+    s.pad[0] = s.pad[1] = s.pad[2] = s.pad[3] = 0.0;
+    stats[b] = s;
+    status_out[b] = st;
+  }
+  if constexpr (GROUP) cluster_sync();
+}
+
+}  // namespace ucn

@@ -2,6 +2,7 @@
 #pragma once
 #include "ucn_internal.h"
 #include "ucn_kernels.cuh"
+#include "ucn_lanes.cuh"
 
 namespace ucn {
 
@@ -21,12 +22,40 @@ cudaError_t launch_scp_v(const LaunchCfg& c, const double* x0, const double* u0,
   return cudaGetLastError();
 }
 
+// The lane kernel (4 threads per node; quadrotor).
+template <class M, class T, bool SMEM, bool R>
+cudaError_t launch_scpl_v(const LaunchCfg& c, const double* x0, const double* u0, double* xo, double* uo,
+                          ucn_scp_stats* st, int* status) {
+  const ProblemDev& P = *(const ProblemDev*)c.P;
+  const Layout& L = *(const Layout*)c.L;
+  auto k = scp_kernel_lanes<M, T, SMEM, R, false, 4>;
+  if (SMEM) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem_bytes);
+    if (e != cudaSuccess) return e;
+  }
+  const int threads = (4 * c.nodes + 31) / 32 * 32;
+  if (threads > LANES_MAX_THREADS) return cudaErrorInvalidConfiguration;
+  k<<<c.blocks, threads, SMEM ? c.smem_bytes : 0, c.stream>>>(P, L, x0, u0, xo, uo, st, status);
+  return cudaGetLastError();
+}
+
 template <class M, class T, bool R>
 cudaError_t launch_scp_t(const LaunchCfg& c, const double* x0, const double* u0, double* xo, double* uo,
                          ucn_scp_stats* st, int* status) {
+  if constexpr (IsQuad<M>::value) {
+    if (c.tpn == 4)
+      return c.smem ? launch_scpl_v<M, T, true, R>(c, x0, u0, xo, uo, st, status)
+                    : launch_scpl_v<M, T, false, R>(c, x0, u0, xo, uo, st, status);
+  }
   return c.smem ? launch_scp_v<M, T, true, R>(c, x0, u0, xo, uo, st, status)
                 : launch_scp_v<M, T, false, R>(c, x0, u0, xo, uo, st, status);
 }
+
+// The group kernel of the lane layout (its own translation unit: defined there).
+template <class M, class T, bool R>
+using ScpKernelPtr = void (*)(ProblemDev, Layout, const double*, const double*, double*, double*, ucn_scp_stats*, int*);
+template <class M, class T, bool R>
+ScpKernelPtr<M, T, R> scp_group_lanes();
 
 // Scenario groups: thread-block clusters of c.group CTAs (records in shared
 // memory only), P.gclusters clusters per group.  cudaErrorInvalidClusterSize
@@ -38,7 +67,9 @@ cudaError_t launch_scp_group_t(const LaunchCfg& c, const double* x0, const doubl
   const ProblemDev& P = *(const ProblemDev*)c.P;
   const Layout& L = *(const Layout*)c.L;
   if (!c.smem || c.group < 1 || c.group > 16 || c.blocks % c.group) return cudaErrorInvalidClusterSize;
-  auto k = scp_kernel<M, T, true, R, true>;
+  auto k = c.tpn == 4 ? scp_group_lanes<M, T, R>() : scp_kernel<M, T, true, R, true>;
+  const int threads = c.tpn == 4 ? (4 * c.nodes + 31) / 32 * 32 : c.threads;
+  if (threads > LANES_MAX_THREADS) return cudaErrorInvalidConfiguration;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem_bytes);
   if (e != cudaSuccess) return e;
   if (c.group > 8) {
@@ -47,7 +78,7 @@ cudaError_t launch_scp_group_t(const LaunchCfg& c, const double* x0, const doubl
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)c.blocks, 1, 1);
-  cfg.blockDim = dim3((unsigned)c.threads, 1, 1);
+  cfg.blockDim = dim3((unsigned)threads, 1, 1);
   cfg.dynamicSmemBytes = (size_t)c.smem_bytes;
   cfg.stream = c.stream;
   cudaLaunchAttribute at[1];
@@ -143,3 +174,18 @@ cudaError_t launch_linearize_t(const void* Pv, const int* node_inst, long long t
 #define UCN_INSTANTIATE_ADMM(MODEL, T, SMEM, REFINE) template UCN_ADMM_V(MODEL, T, SMEM, REFINE);
 #define UCN_EXTERN_SCP(MODEL, T, SMEM, REFINE) extern template UCN_SCP_V(MODEL, T, SMEM, REFINE);
 #define UCN_EXTERN_ADMM(MODEL, T, SMEM, REFINE) extern template UCN_ADMM_V(MODEL, T, SMEM, REFINE);
+
+// Lane-kernel variants, each in its own translation unit.
+#define UCN_SCPL_V(MODEL, T, SMEM, REFINE)                                                                 \
+  cudaError_t ucn::launch_scpl_v<ucn::MODEL, T, SMEM, REFINE>(const ucn::LaunchCfg&, const double*,      \
+                                                              const double*, double*, double*,           \
+                                                              ucn_scp_stats*, int*)
+#define UCN_INSTANTIATE_SCPL(MODEL, T, SMEM, REFINE) template UCN_SCPL_V(MODEL, T, SMEM, REFINE);
+#define UCN_EXTERN_SCPL(MODEL, T, SMEM, REFINE) extern template UCN_SCPL_V(MODEL, T, SMEM, REFINE);
+#define UCN_DEFINE_GROUP_LANES(MODEL, T, REFINE)                                                           \
+  namespace ucn {                                                                                          \
+  template <>                                                                                              \
+  ScpKernelPtr<MODEL, T, REFINE> scp_group_lanes<MODEL, T, REFINE>() {                                     \
+    return scp_kernel_lanes<MODEL, T, true, REFINE, true, 4>;                                              \
+  }                                                                                                        \
+  }

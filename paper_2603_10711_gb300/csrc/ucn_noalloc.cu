@@ -149,6 +149,7 @@ extern "C" ucn_status ucn_scp_solve_noalloc(const ucn_problem_desc* d, const dou
   LaunchCfg c;
   c.P = &P; c.L = &L; c.smem = true; c.smem_bytes = L.bytes;
   c.threads = (int)((Nmax + 1 + 31) / 32 * 32); c.blocks = B; c.stream = st; c.group = 1;
+  c.nodes = Nmax + 1; c.tpn = default_tpn(d->model, Nmax + 1);
   auto fn = d->model == UCN_MODEL_QUAD12 ? (d->precision == UCN_PREC_FP64 ? quad64_scp : quad32_scp)
                                          : (d->precision == UCN_PREC_FP64 ? mars64_scp : mars32_scp);
   e = fn(c, x0_d, u0_d, x_out_d, u_out_d, stats_d, status_d);

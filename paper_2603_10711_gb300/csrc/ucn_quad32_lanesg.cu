@@ -1,0 +1,4 @@
+// Kernel instantiation: 12-state quadrotor, FP32 path with refinement, fused solve on the lane
+// layout (4 threads per node) with node records in global memory.
+#include "ucn_launch.cuh"
+UCN_INSTANTIATE_SCPL(Quad12, float, false, true)

@@ -1,0 +1,4 @@
+// Kernel instantiation: scenario groups of the 12-state quadrotor on the lane
+// layout (thread-block clusters, one CTA per scenario, 4 threads per node), FP32 path with refinement.
+#include "ucn_launch.cuh"
+UCN_DEFINE_GROUP_LANES(Quad12, float, true)

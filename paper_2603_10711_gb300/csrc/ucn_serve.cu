@@ -321,6 +321,7 @@ ucn_status ucn_serve_pump(ucn_server* s, int* launched) {
   LaunchCfg c;
   c.P = &P; c.L = &s->L; c.smem = s->smem; c.smem_bytes = s->smem_bytes;
   c.threads = s->threads; c.blocks = (int)ready.size(); c.stream = st; c.group = 1;
+  c.nodes = s->cfg.max_horizon + 1; c.tpn = default_tpn(s->cfg.model, s->cfg.max_horizon + 1);
   const bool quad = s->cfg.model == UCN_MODEL_QUAD12, f64 = s->cfg.precision == UCN_PREC_FP64;
   auto fn = quad ? (f64 ? quad64_scp : quad32_scp) : (f64 ? mars64_scp : mars32_scp);
   cudaError_t e = fn(c, s->x0, s->u0, s->xo, s->uo, s->stats, s->status);

@@ -82,6 +82,10 @@ def lib():
                 getattr(L, f).restype = C.c_longlong
             L.ucn_problem_set_order.argtypes = [vp, _ip]
             L.ucn_problem_set_order.restype = C.c_int
+            L.ucn_problem_set_lanes.argtypes = [vp, C.c_int]
+            L.ucn_problem_set_lanes.restype = C.c_int
+            L.ucn_problem_lanes.argtypes = [vp]
+            L.ucn_problem_lanes.restype = C.c_int
             L.ucn_linearize.argtypes = [vp, vp, vp, vp, vp, vp, vp]
             L.ucn_linearize.restype = C.c_int
             L.ucn_admm_solve.argtypes = [vp, vp, vp, vp, vp, vp, vp, C.c_int, C.c_int, vp, vp, vp, vp, vp]
@@ -191,6 +195,15 @@ def ucn_problem_create(desc: ProblemDesc):
 
 def ucn_problem_destroy(h):
     lib().ucn_problem_destroy(h)
+
+
+def ucn_problem_set_lanes(h, lanes_per_node):
+    """Threads per node of the fused solve (1, or 4 for quadrotor problems)."""
+    _check(lib().ucn_problem_set_lanes(h, int(lanes_per_node)))
+
+
+def ucn_problem_lanes(h):
+    return int(lib().ucn_problem_lanes(h))
 
 
 def ucn_problem_set_order(h, order=None):
