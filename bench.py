@@ -156,6 +156,8 @@ def make_problem(args, rank=0):
         over = dict(scp_iters=args.scp_iters, stop=0)
     if getattr(args, "workload", "mars") == "quad_box":
         return W.quad_box(args.batch, seed=2 + rank, settings=over)
+    if getattr(args, "workload", "mars") == "quad40":
+        return W.quad_box(args.batch, seed=2 + rank, N_range=(40, 40), obs_range=(8, 8), settings=over)
     return W.mars_batch(args.batch, seed=1 + rank, settings=over)
 
 
@@ -165,6 +167,8 @@ def run_kernel_only(args):
     from paper_2603_10711_gb300 import ucn
     prob = make_problem(args)
     solver = ucn.Solver(prob, precision=ucn.UCN_PREC_FP64 if args.fp64 else ucn.UCN_PREC_FP32_REFINE)
+    if args.lanes:
+        ucn.ucn_problem_set_lanes(solver.handle, args.lanes)
     x0, u0 = solver.tensor(prob.xguess), solver.tensor(prob.uguess)
     for _ in range(args.warmup):
         solver.scp_solve(x0, u0)
@@ -264,6 +268,7 @@ def run_ours(args, rank, world):
     s64.close()
 
     serving_out = run_serving(args) if (args.serving_requests > 0 and world == 1) else None
+    scenario_out = run_scenarios(args) if (args.scenario_steps > 0 and world == 1) else None
 
     flops_ni = flops_per_node_iter(prob.nx, prob.nu, mars_mirror_flops())
     flops_launch = nodeiters / args.steps * flops_ni
@@ -299,6 +304,8 @@ def run_ours(args, rank, world):
     }
     if serving_out is not None:
         out["serving"] = serving_out
+    if scenario_out is not None:
+        out["scenario_mpc"] = scenario_out
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         out["cpu_baseline"] = cpu_baseline(args)
     solver.close()
@@ -337,8 +344,8 @@ def run_scenarios(args):
     (mass, drag) sharing the first control, N = 40, 8 obstacles; a receding
     horizon of S steps, each one grouped solve (thread-block clusters, FP32 +
     refinement) and one shift that applies the shared control and warm-starts
-    the next solve.  The plain FP64 path runs the first (cold) step of the same
-    problems."""
+    the next solve.  The plain FP64 path runs the first (cold) step of the
+    first `--scenario-fp64-problems` problems."""
     import torch
     from paper_2603_10711_gb300 import ucn
     P, K, S = args.scenario_problems, args.scenario_count, args.scenario_steps
@@ -368,10 +375,12 @@ def run_scenarios(args):
     d1 = np.linalg.norm(xg.cpu().numpy()[prob.xoff[::K], :3] - goal, axis=1)
     s.close()
     total = sum(step_ms) / 1e3
-    # plain FP64: the cold first step of the same problems
-    s64 = ucn.Solver(W.scenario_mpc(P, K, seed=3, N=40, n_obs=8), precision=ucn.UCN_PREC_FP64)
+    # plain FP64: the cold first step of the first P64 problems
+    P64 = min(P, args.scenario_fp64_problems)
+    p64 = W.scenario_mpc(P, K, seed=3, N=40, n_obs=8).subset(np.arange(P64 * K))
+    s64 = ucn.Solver(p64, precision=ucn.UCN_PREC_FP64)
     e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream); s64.scp_solve(x0, u0); e1.record(stream); e1.synchronize()
+    e0.record(stream); s64.scp_solve(); e1.record(stream); e1.synchronize()
     t64 = e0.elapsed_time(e1) / 1e3
     st64 = s64.stats_host()
     s64.close()
@@ -382,7 +391,7 @@ def run_scenarios(args):
                         "first_cold": step_ms[0]},
             "pass_rate": passed / (P * K * S), "scp_iters_mean_per_step": iters,
             "goal_distance_m": {"start_mean": float(d0.mean()), "end_mean": float(d1.mean())},
-            "fp64_plain_cold_step": {"ms": 1e3 * t64, "scenario_solves_per_s": P * K / t64,
+            "fp64_plain_cold_step": {"problems": P64, "ms": 1e3 * t64, "scenario_solves_per_s": P64 * K / t64,
                                      "pass_rate": float(np.mean(st64["defect"] <= 1e-5)),
                                      "scp_iters_mean": float(st64["scp_iters"].mean())},
             "fp32_cold_step_ms": step_ms[0]}
@@ -445,12 +454,15 @@ def main():
     ap.add_argument("--scenario-problems", type=int, default=256)
     ap.add_argument("--scenario-count", type=int, default=64, help="scenarios per problem (group size)")
     ap.add_argument("--scenario-steps", type=int, default=3, help="receding-horizon steps (0: skip the section)")
+    ap.add_argument("--scenario-fp64-problems", type=int, default=64)
     ap.add_argument("--mode", default="full", choices=["full", "kernel", "scenario"],
                     help="kernel: time only the fused kernel (profiler captures)")
     ap.add_argument("--scp-iters", type=int, default=0, help="fixed SCP iteration count (0: the workload's cap + stop test)")
     ap.add_argument("--fp64", action="store_true", help="kernel mode: the FP64 plain path")
-    ap.add_argument("--workload", default="mars", choices=["mars", "quad_box"],
-                    help="kernel mode: mars (1024-instance Mars batch) or quad_box (uneven quadrotor batch)")
+    ap.add_argument("--workload", default="mars", choices=["mars", "quad_box", "quad40"],
+                    help="kernel mode: mars (1024-instance Mars batch), quad_box (uneven quadrotor batch) "
+                         "or quad40 (quadrotors with N = 40 and 8 obstacles)")
+    ap.add_argument("--lanes", type=int, default=0, help="kernel mode: threads per node (0: the library default)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

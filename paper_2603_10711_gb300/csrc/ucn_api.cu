@@ -69,7 +69,10 @@ Layout make_layout(int model, int nodes, int max_obs, int tsize, bool reg_mats) 
     nt = L.oH + NN * (NN + 1) / 2;
   }
   L.S = nodes;
-  L.NS = nt | 1;       // odd record strides: consecutive nodes fall in distinct banks
+  // Record stride: odd for one thread per node (consecutive nodes fall in
+  // distinct banks); 4 mod 32 for the lane kernel, whose warps read 8 nodes x
+  // 4 consecutive row elements -- 32 distinct banks.
+  L.NS = default_tpn(model, nodes) == 4 ? nt + ((4 - nt) % 32 + 32) % 32 : (nt | 1);
   L.DS = dfixed | 1;
   L.tbytes = round_up((long long)nodes * L.NS * tsize, 16);
   L.bytes = round_up(L.tbytes + (long long)nodes * L.DS * 8, 16);

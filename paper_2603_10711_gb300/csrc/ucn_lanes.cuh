@@ -6,8 +6,8 @@
 // the dependent chain of the per-node mat-vecs by TPN and multiplies the
 // resident warps by TPN -- the one-thread kernel of a 16-row node runs 1-2
 // warps per scheduler and is latency-bound.  The per-SCP-iteration work
-// (assembly and factorisation, the FP64 rollout, acceptance) stays on lane 0;
-// the Jacobian directions are split over the lanes.
+// (assembly and factorisation, the FP64 rollout, acceptance) maps one thread
+// to one node again; the Jacobian directions are split over the lanes.
 #pragma once
 #include "ucn_kernels.cuh"
 
@@ -494,7 +494,15 @@ __global__ void __launch_bounds__(LANES_MAX_THREADS) scp_kernel_lanes(ProblemDev
   LaneH<M, T, TPN, std::is_same<T, float>::value> H;
   const int i = nd.i, N = nd.N;
   const bool active = i <= N;
-  const bool lead = active && q == 0;
+  // The per-SCP-iteration work (nominal, assembly and factorisation, the FP64
+  // rollout and acceptance, the nominal update) maps one thread to one node, so
+  // that its warps run full -- the FP64 pipe charges a warp instruction whatever
+  // its active lanes.
+  Node<T, AOS> ndd = make_node<T, SMEM>(P, L, smem, b);
+  SmemMats<M, T, AOS> MTd;
+  init_mats<M, T, AOS>(MTd, ndd, L);
+  const int id = ndd.i;
+  const bool dact = id <= N;
   const long long xo = P.xoff[b], uo = P.uoff[b];
   const double* prm = P.params + b * 8;
   const double h = P.dt[b];
@@ -505,26 +513,26 @@ __global__ void __launch_bounds__(LANES_MAX_THREADS) scp_kernel_lanes(ProblemDev
 #pragma unroll
   for (int m = 0; m < R; ++m) { kq[m] = T(0); khd[m] = T(0); }
   if (threadIdx.x == 0) { sh.fail = 0; sh.status = ST_OK; sh.radius = P.tr_init; sh.stop = 0; }
-  if (lead) load_nominal<M, T, AOS>(nd, L, x0, u0, xo, uo);
+  if (dact) load_nominal<M, T, AOS>(ndd, L, x0, u0, xo, uo);
   __syncthreads();
   double acc[6] = {0, 0, 0, 0, 0, 0};
-  if (lead) {
+  if (dact) {
     double xb[NX], ub[NU];
-    read_nominal<M, T, AOS>(nd, i < N, xb, ub);
-    acc[0] = node_cost<M, T>(P, I, b, i, N, xb, ub);
-    if (i < N) {
+    read_nominal<M, T, AOS>(ndd, id < N, xb, ub);
+    acc[0] = node_cost<M, T>(P, I, b, id, N, xb, ub);
+    if (id < N) {
       double fn[NX];
       rk4<M, double>(prm, h, xb, ub, fn);
       for (int j = 0; j < NX; ++j) {
-        const double e = fn[j] - nd.dnb(Rec<M>::Xbar, j, i + 1);
-        nd.at(Rec<M>::C, j) = (T)e;
+        const double e = fn[j] - ndd.dnb(Rec<M>::Xbar, j, id + 1);
+        ndd.at(Rec<M>::C, j) = (T)e;
         acc[1] += fabs(e);
       }
     }
   }
   block_reduce(sh, acc, 2, 2);
   if (threadIdx.x == 0) sh.Jn = acc[0] + P.w_d * acc[1];
-  if (lead) node_cold_start<M, T, AOS>(nd, L);
+  if (dact) node_cold_start<M, T, AOS>(ndd, L);
   __syncthreads();
   int accepted = 0, iters_run = 0;
   unsigned long long mask = 0ull;
@@ -543,12 +551,12 @@ __global__ void __launch_bounds__(LANES_MAX_THREADS) scp_kernel_lanes(ProblemDev
     if (active && i < N) lanes_jacobians<M, T, AOS, TPN>(nd, MT, I.prm, h, q);
     if (active) lanes_consts<M, T, AOS, TPN>(nd, P, b, q, re, rg, kq, khd);
     __syncthreads();
-    if (lead) {
-      node_setup<M, T, AOS>(nd, L, P, b, radius, re, rg, K);
-      const bool ok = node_factor<M, T, AOS, NN>(nd, MT, L, I, K, rd, rg);
+    if (dact) {
+      node_setup<M, T, AOS>(ndd, L, P, b, radius, re, rg, K);
+      const bool ok = node_factor<M, T, AOS, NN>(ndd, MTd, L, I, K, rd, rg);
       if (!ok) atomicOr(&sh.fail, 1);
-      node_reseed<M, T, AOS>(nd, L, I);
-      publish_ex2<M, T, AOS>(nd, L, true, rd);
+      node_reseed<M, T, AOS>(ndd, L, I);
+      publish_ex2<M, T, AOS>(ndd, L, true, rd);
     }
     __syncthreads();
     H.load(MT, q, active);
@@ -565,32 +573,32 @@ __global__ void __launch_bounds__(LANES_MAX_THREADS) scp_kernel_lanes(ProblemDev
     ++iters_run;
     // ---- candidate (x-hat, u-hat): FP64 rollout, defects, cost, linear model (lane 0)
     double xc[NX], uc[NU], fc[NX];
-    if (lead) {
-      for (int j = 0; j < NX; ++j) { xc[j] = nd.dat(Rec<M>::Xbar, j) + (double)nd.at(Rec<M>::Xh, j); nd.dat(Rec<M>::Xc, j) = xc[j]; }
-      for (int j = 0; j < NU; ++j) uc[j] = (i < N) ? nd.dat(Rec<M>::Ubar, j) + (double)nd.at(Rec<M>::Uh, j) : 0.0;
+    if (dact) {
+      for (int j = 0; j < NX; ++j) { xc[j] = ndd.dat(Rec<M>::Xbar, j) + (double)ndd.at(Rec<M>::Xh, j); ndd.dat(Rec<M>::Xc, j) = xc[j]; }
+      for (int j = 0; j < NU; ++j) uc[j] = (id < N) ? ndd.dat(Rec<M>::Ubar, j) + (double)ndd.at(Rec<M>::Uh, j) : 0.0;
       if constexpr (GROUP) {
-        if (i == 0)
+        if (id == 0)
           for (int j = 0; j < NU; ++j) uc[j] = G->u0[j];
       }
     }
     __syncthreads();
     double v[6] = {0, 0, 0, 0, 0};
-    if (lead) {
-      v[0] = node_cost<M, T>(P, I, b, i, N, xc, uc);
+    if (dact) {
+      v[0] = node_cost<M, T>(P, I, b, id, N, xc, uc);
       T st = T(0);
-      for (int j = 0; j < NX; ++j) st = maxv(st, absv(nd.at(Rec<M>::Xh, j)));
-      if (i < N) {
-        for (int j = 0; j < NU; ++j) st = maxv(st, absv(nd.at(Rec<M>::Uh, j)));
+      for (int j = 0; j < NX; ++j) st = maxv(st, absv(ndd.at(Rec<M>::Xh, j)));
+      if (id < N) {
+        for (int j = 0; j < NU; ++j) st = maxv(st, absv(ndd.at(Rec<M>::Uh, j)));
         rk4<M, double>(prm, h, xc, uc, fc);
         double dinf = 0.0;
         T lin1 = T(0);
         for (int r = 0; r < NX; ++r) {
-          fc[r] -= nd.dnb(Rec<M>::Xc, r, i + 1);
+          fc[r] -= ndd.dnb(Rec<M>::Xc, r, id + 1);
           v[1] += fabs(fc[r]);
           dinf = fmax(dinf, fabs(fc[r]));
-          T lin = nd.at(Rec<M>::C, r) - nd.nb(Rec<M>::Xh, r, i + 1);
-          for (int c = 0; c < NX; ++c) lin += MT.A(r * NX + c) * nd.at(Rec<M>::Xh, c);
-          for (int c = 0; c < NU; ++c) lin += MT.B(r * NU + c) * nd.at(Rec<M>::Uh, c);
+          T lin = ndd.at(Rec<M>::C, r) - ndd.nb(Rec<M>::Xh, r, id + 1);
+          for (int c = 0; c < NX; ++c) lin += MTd.A(r * NX + c) * ndd.at(Rec<M>::Xh, c);
+          for (int c = 0; c < NU; ++c) lin += MTd.B(r * NU + c) * ndd.at(Rec<M>::Uh, c);
           lin1 += absv(lin);
         }
         v[2] = (double)lin1;
@@ -640,22 +648,22 @@ __global__ void __launch_bounds__(LANES_MAX_THREADS) scp_kernel_lanes(ProblemDev
     if (sh.accept) {
       ++accepted;
       if (k < 64) mask |= (1ull << k);
-      if (lead) {
-        node_rebase_mirrors<M, T, AOS>(nd, L, P, b);
+      if (dact) {
+        node_rebase_mirrors<M, T, AOS>(ndd, L, P, b);
         for (int j = 0; j < NX; ++j) {
-          const T xh = nd.at(Rec<M>::Xh, j);
-          nd.dat(Rec<M>::Xbar, j) = xc[j];
-          nd.at(Rec<M>::X, j) -= xh;
-          if (i >= 1) nd.at(Rec<M>::Z, j) -= xh;
-          nd.at(Rec<M>::Xh, j) = T(0);
-          if (i < N) nd.at(Rec<M>::C, j) = (T)fc[j];
+          const T xh = ndd.at(Rec<M>::Xh, j);
+          ndd.dat(Rec<M>::Xbar, j) = xc[j];
+          ndd.at(Rec<M>::X, j) -= xh;
+          if (id >= 1) ndd.at(Rec<M>::Z, j) -= xh;
+          ndd.at(Rec<M>::Xh, j) = T(0);
+          if (id < N) ndd.at(Rec<M>::C, j) = (T)fc[j];
         }
-        if (i < N)
+        if (id < N)
           for (int j = 0; j < NU; ++j) {
-            const T uh = nd.at(Rec<M>::Uh, j);
-            nd.dat(Rec<M>::Ubar, j) = uc[j];
-            nd.at(Rec<M>::U, j) -= uh;
-            nd.at(Rec<M>::Uh, j) = T(0);
+            const T uh = ndd.at(Rec<M>::Uh, j);
+            ndd.dat(Rec<M>::Ubar, j) = uc[j];
+            ndd.at(Rec<M>::U, j) -= uh;
+            ndd.at(Rec<M>::Uh, j) = T(0);
           }
       }
     }
@@ -663,23 +671,23 @@ __global__ void __launch_bounds__(LANES_MAX_THREADS) scp_kernel_lanes(ProblemDev
     if (sh.stop) break;
   }
   double w[6] = {0, 0, 0, 0, 0, 0};
-  if (lead) {
+  if (dact) {
     double xb[NX], ub[NU];
-    read_nominal<M, T, AOS>(nd, i < N, xb, ub);
-    w[0] = node_cost<M, T>(P, I, b, i, N, xb, ub);
-    if (i < N) {
+    read_nominal<M, T, AOS>(ndd, id < N, xb, ub);
+    w[0] = node_cost<M, T>(P, I, b, id, N, xb, ub);
+    if (id < N) {
       double fn[NX];
       rk4<M, double>(prm, h, xb, ub, fn);
       for (int j = 0; j < NX; ++j) {
-        const double e = fabs(fn[j] - nd.dnb(Rec<M>::Xbar, j, i + 1));
+        const double e = fabs(fn[j] - ndd.dnb(Rec<M>::Xbar, j, id + 1));
         w[1] += e;
         w[2] = fmax(w[2], e);
       }
     }
-    for (int j = 0; j < NX; ++j) xout[(xo + i) * NX + j] = xb[j];
-    if (i < N)
-      for (int j = 0; j < NU; ++j) uout[(uo + i) * NU + j] = ub[j];
-    node_export<M, T, AOS>(nd, L, P, b, P.state_abs + P.soff[b]);
+    for (int j = 0; j < NX; ++j) xout[(xo + id) * NX + j] = xb[j];
+    if (id < N)
+      for (int j = 0; j < NU; ++j) uout[(uo + id) * NU + j] = ub[j];
+    node_export<M, T, AOS>(ndd, L, P, b, P.state_abs + P.soff[b]);
   }
   block_reduce(sh, w, 2, 3);
   if (threadIdx.x == 0) {
