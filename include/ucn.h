@@ -92,11 +92,13 @@ typedef enum { UCN_PREC_FP64 = 0, UCN_PREC_FP32_REFINE = 1 } ucn_precision;
  *                scenario to the average of their Step-3 arguments clamped to the
  *                intersection of their boxes, and accepts, resizes the trust
  *                region and stops per group (sums of the merits, maxima of
- *                defect and step).  A group is one thread-block cluster of K CTAs
- *                when K <= 16, else K / c clusters of c CTAs (c the largest
- *                divisor of K up to 16) that exchange partial sums through
- *                global memory and must be resident together (ucn_scp_solve
- *                returns UCN_EINVAL when they cannot be).  Requires the
+ *                defect and step).  The scenarios exchange their contributions
+ *                through global memory (release/acquire counters, bounded
+ *                waits); a group is launched as one thread-block cluster of K
+ *                CTAs when K <= 16, else as K / c clusters of c CTAs (c the
+ *                largest divisor of K up to 16), which must be resident
+ *                together (ucn_scp_solve returns UCN_EINVAL when they cannot
+ *                be).  Requires the
  *                quadrotor model, batch % K == 0 and records that fit in
  *                shared memory; ucn_admm_solve and ucn_problem_set_order
  *                reject grouped problems

@@ -291,7 +291,9 @@ ucn_status ucn_problem_create(const ucn_problem_desc* d, ucn_problem** out) {
     if (group % c == 0) { gcsize = c; break; }
   p->gcsize = gcsize;
   P.gclusters = group / gcsize;
-  P.gwait_ns = std::min<unsigned long long>(P.timeout_ns, 10ull * 1000000000ull);
+  // bound on a wait for another scenario (the group runs in lockstep, so waits
+  // are short; the bound only guarantees that the kernel ends)
+  P.gwait_ns = 10ull * 1000000000ull;
   p->node_inst = ni;
   p->order_d = ord;
   // per-node storage: shared memory when one instance fits (small models then keep
@@ -310,9 +312,9 @@ ucn_status ucn_problem_create(const ucn_problem_desc* d, ucn_problem** out) {
     ucn_problem_destroy(p);
     return fail(UCN_EINVAL, "scenario groups need node records in shared memory (horizon or obstacle count too large)");
   }
-  if (P.gclusters > 1) {
-    // exchange slots and counters of the clusters of each group
-    const size_t nc = (size_t)(B / group) * P.gclusters;
+  if (group > 1) {
+    // exchange slots and counters of the scenarios
+    const size_t nc = (size_t)B;
     const bool injected = fa > 0 && (na + 1 == fa || na + 2 == fa);
     na += 2;
     void* gx = nullptr;
@@ -434,8 +436,8 @@ ucn_status ucn_scp_solve(ucn_problem* p, const double* x0_d, const double* u0_d,
   if (!p || !x0_d || !u0_d || !x_out_d || !u_out_d || !stats_d || !status_d) return fail(UCN_EINVAL, "null argument");
   const LaunchCfg c = cfg_of(p, stream);
   if (p->group > 1) {
-    if (p->dev.gclusters > 1) {
-      const cudaError_t e = cudaMemsetAsync(p->dev.gflag, 0, sizeof(unsigned) * (p->batch / p->gcsize), c.stream);
+    {
+      const cudaError_t e = cudaMemsetAsync(p->dev.gflag, 0, sizeof(unsigned) * p->batch, c.stream);
       if (e != cudaSuccess) return fail(UCN_ECUDA, "group counters: %s", cudaGetErrorString(e));
     }
     const cudaError_t e = (p->precision == UCN_PREC_FP64 ? quad64_scp_group : quad32_scp_group)(

@@ -44,9 +44,9 @@ struct ProblemDev {
   const int* order;        // CTA -> instance map of the fused solve (NULL: identity)
   int group;               // scenarios per group (<= 1: independent instances)
   int gclusters;           // thread-block clusters per group (group = gclusters x cluster size)
-  double* gx;              // exchange slots between the clusters of a group [group][cluster][2][16]
-  unsigned* gflag;         // per [group][cluster]: last exchange published (+1); zeroed per launch
-  unsigned long long gwait_ns;   // bound on a wait for another cluster of the group
+  double* gx;              // exchange slots of the scenarios [instance][2][16]
+  unsigned* gflag;         // per instance: last exchange published (+1); zeroed per launch
+  unsigned long long gwait_ns;   // bound on a wait for another scenario of the group
 };
 
 // Fixed part of a node record: compile-time element offsets of every per-node
@@ -173,20 +173,17 @@ struct InstShared {
   int accept, stop, status;
 };
 
-// Exchange area of a scenario group (one CTA per scenario; the group is one
-// thread-block cluster, or several whose rank-0 CTAs meet in global memory),
-// read by the other CTAs of the cluster through distributed shared memory.
+// Per-CTA state of a scenario group's exchanges (one CTA per scenario).
 struct GroupShared {
   double mine[2][16];   // this CTA's contribution to the current exchange (double-buffered)
-  double bcast[17];     // rank 0's group result (+ [16]: an exchange gave up waiting)
   double u0[4];         // the consensus u-hat_0 of the latest iteration, absolute
-  int gfail;            // sticky: a wait for another cluster of the group gave up
+  int gfail;            // sticky: a wait for another scenario of the group gave up
 };
 
 // Sequence state of the group exchanges, identical in every thread of the group.
 struct GroupX {
   unsigned epoch;       // exchanges done
-  int g, c;             // group index, cluster index within the group
+  int g, k;             // group index, scenario index within the group
 };
 
 __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
@@ -194,72 +191,123 @@ __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
+__device__ __forceinline__ unsigned ld_relaxed_gpu(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
 __device__ __forceinline__ void st_release_gpu(unsigned* p, unsigned v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
 }
 
-// All-reduce over the scenario group of the NV values that thread 0 of every
-// CTA has put in G->mine[X.epoch & 1]: entries [0, ns) summed, the rest maxed,
-// in scenario order (cluster by cluster, rank by rank).  Every thread of every
-// CTA of the group calls it the same number of times; thread 0 receives the
-// result in out.  Several clusters: the rank-0 CTAs publish their partials in
-// global memory (release/acquire on per-cluster counters) and wait for the
-// others' with a time bound; a wait that gives up marks the group failed and
-// stops waiting for the rest of the launch (status ETIMEOUT), so the kernel
-// always ends.
+// All-reduce over a scenario group of the NV values that warp 0 of every CTA
+// has put in G->mine[X.epoch & 1]: entries [0, ns) summed, the rest maxed.
+// Every thread of every CTA of the group calls it the same number of times;
+// thread 0 receives the result in out, and every CTA of the group the same
+// bits (the same operations on the same data).  Two forms, each the faster one
+// measured in its regime:
+//
+// One cluster per group (group <= 16): one cluster barrier, then lane r of
+// warp 0 loads rank r's values through distributed shared memory (all loads
+// in flight at once) and a butterfly over the warp combines them.
 template <int NV>
-__device__ void group_allreduce(const ProblemDev& P, GroupShared* G, GroupX& X, int ns, double* out) {
+__device__ void group_allreduce_cluster(GroupShared* G, GroupX& X, int ns, double* out) {
   const int par = X.epoch & 1;
   cluster_sync();
-  const unsigned nk = cluster_size();
-  if (P.gclusters <= 1) {
-    if (threadIdx.x == 0) {
-      for (int j = 0; j < NV; ++j) out[j] = j < ns ? 0.0 : -INFINITY;
-      for (unsigned r = 0; r < nk; ++r)
-        for (int j = 0; j < NV; ++j) {
-          const double v = ld_cluster(&G->mine[par][j], r);
-          out[j] = j < ns ? out[j] + v : fmax(out[j], v);
-        }
+  if (threadIdx.x < 32) {
+    const unsigned lane = threadIdx.x, nk = cluster_size();
+    double pv[NV];
+#pragma unroll
+    for (int j = 0; j < NV; ++j) pv[j] = j < ns ? 0.0 : -INFINITY;
+    if (lane < nk) {
+#pragma unroll
+      for (int j = 0; j < NV; ++j) pv[j] = ld_cluster(&G->mine[par][j], lane);
     }
-  } else {
-    if (threadIdx.x == 0 && cluster_rank() == 0) {
-      const int C = P.gclusters;
-      double pv[NV], tot[NV];
-      for (int j = 0; j < NV; ++j) { pv[j] = j < ns ? 0.0 : -INFINITY; tot[j] = pv[j]; }
-      for (unsigned r = 0; r < nk; ++r)
-        for (int j = 0; j < NV; ++j) {
-          const double v = ld_cluster(&G->mine[par][j], r);
-          pv[j] = j < ns ? pv[j] + v : fmax(pv[j], v);
-        }
-      double* slot = P.gx + (((long long)X.g * C + X.c) * 2 + par) * 16;
-      for (int j = 0; j < NV; ++j) slot[j] = pv[j];
-      st_release_gpu(&P.gflag[X.g * C + X.c], X.epoch + 1);
-      for (int c = 0; c < C; ++c) {
-        if (c != X.c && !G->gfail) {
-          const unsigned* f = &P.gflag[X.g * C + c];
-          const unsigned long long t0 = globaltimer_ns();
-          while (ld_acquire_gpu(f) < X.epoch + 1) {
-            if (globaltimer_ns() - t0 > P.gwait_ns) { G->gfail = 1; break; }
-            __nanosleep(64);
-          }
-        }
-        if (c != X.c && G->gfail) continue;
-        const double* src = P.gx + (((long long)X.g * C + c) * 2 + par) * 16;
-        for (int j = 0; j < NV; ++j) {
-          const double v = c == X.c ? pv[j] : __ldcg(src + j);
-          tot[j] = j < ns ? tot[j] + v : fmax(tot[j], v);
-        }
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1)
+#pragma unroll
+      for (int j = 0; j < NV; ++j) {
+        const double t = __shfl_xor_sync(0xffffffffu, pv[j], o);
+        pv[j] = j < ns ? pv[j] + t : fmax(pv[j], t);
       }
-      for (int j = 0; j < NV; ++j) G->bcast[j] = tot[j];
-      G->bcast[16] = G->gfail ? 1.0 : 0.0;
-    }
-    cluster_sync();
-    if (threadIdx.x == 0) {
-      for (int j = 0; j < NV; ++j) out[j] = ld_cluster(&G->bcast[j], 0);
-      if (ld_cluster(&G->bcast[16], 0) != 0.0) G->gfail = 1;
-    }
+    if (lane == 0)
+      for (int j = 0; j < NV; ++j) out[j] = pv[j];
   }
   X.epoch++;
+}
+
+// Several clusters per group: no barrier at all; lane 0 publishes the CTA's
+// values to its global slot and releases its counter; lane r then waits
+// (relaxed polling, then acquire; time-bounded) for scenario r's counter (r,
+// r+32, ...), loads that scenario's values, and a butterfly over the warp
+// combines them.  Slots are double-buffered by the exchange's parity: a
+// scenario can be at most one exchange ahead of another.  A wait that gives up
+// marks the group failed and stops waiting for the rest of the launch (status
+// ETIMEOUT), so the kernel always ends.
+template <int NV>
+__device__ void group_allreduce_flat(const ProblemDev& P, GroupShared* G, GroupX& X, int ns, double* out) {
+  static_assert(NV <= 16, "exchange slots hold 16 values");
+  const int par = X.epoch & 1;
+  if (threadIdx.x < 32) {
+    __syncwarp();
+    const int lane = threadIdx.x, K = P.group;
+    const long long base = (long long)X.g * K;
+    if (lane == 0) {
+      double* slot = P.gx + ((base + X.k) * 2 + par) * 16;
+      for (int j = 0; j < NV; ++j) slot[j] = G->mine[par][j];
+      st_release_gpu(&P.gflag[base + X.k], X.epoch + 1);
+    }
+    double pv[NV];
+#pragma unroll
+    for (int j = 0; j < NV; ++j) pv[j] = j < ns ? 0.0 : -INFINITY;
+    for (int r = lane; r < K; r += 32) {
+      const unsigned* f = &P.gflag[base + r];
+      bool ok = !G->gfail;
+      if (ok) {
+        // relaxed polling, one acquire once the counter is seen (an acquire per
+        // poll would also cost the SM its L1 lines); the clock is read every
+        // 256 polls
+        unsigned long long t0 = 0;
+        for (unsigned spins = 1; ld_relaxed_gpu(f) < X.epoch + 1; ++spins) {
+          if ((spins & 255u) == 0u) {
+            const unsigned long long now = globaltimer_ns();
+            if (t0 == 0) t0 = now;
+            else if (now - t0 > P.gwait_ns) { ok = false; G->gfail = 1; break; }
+          }
+        }
+        if (ok) (void)ld_acquire_gpu(f);
+      }
+      if (!ok) continue;
+      const double* src = P.gx + ((base + r) * 2 + par) * 16;
+      double v[NV];
+#pragma unroll
+      for (int j = 0; j < NV; ++j) v[j] = __ldcg(src + j);
+#pragma unroll
+      for (int j = 0; j < NV; ++j) pv[j] = j < ns ? pv[j] + v[j] : fmax(pv[j], v[j]);
+    }
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1)
+#pragma unroll
+      for (int j = 0; j < NV; ++j) {
+        const double t = __shfl_xor_sync(0xffffffffu, pv[j], o);
+        pv[j] = j < ns ? pv[j] + t : fmax(pv[j], t);
+      }
+    if (lane == 0)
+      for (int j = 0; j < NV; ++j) out[j] = pv[j];
+  }
+  X.epoch++;
+}
+
+template <int NV>
+__device__ __forceinline__ void group_allreduce(const ProblemDev& P, GroupShared* G, GroupX& X, int ns, double* out) {
+  if (P.gclusters <= 1) group_allreduce_cluster<NV>(G, X, ns, out);
+  else group_allreduce_flat<NV>(P, G, X, ns, out);
+}
+
+// The end of a group kernel: no CTA of a one-cluster group may exit while
+// another can still read its shared memory.
+__device__ __forceinline__ void group_finish(const ProblemDev& P) {
+  if (P.gclusters <= 1) cluster_sync();
 }
 
 // The exchange area exists in the shared memory of group kernels only.
@@ -732,12 +780,12 @@ __device__ void node_reseed(const Node<T, AOS>& nd, const Layout& L, const Inst<
 // and dual residuals in FP64 (a separate instantiation, so that the hot loop
 // carries no FP64 instruction, not even a predicated-off one).
 //
-// GROUP: the CTA is one scenario of a thread-block cluster whose scenarios
-// share the first control (Sec. IV-A).  After Step 3 the node-0 thread of every
-// CTA publishes its Step-3 argument u_0 + nu_u,0 / rho_geo and its box (both
-// absolute) in `cons`; after one cluster barrier each reads all of them and
-// sets u-hat_0 to the projection onto {equal u_0} intersected with every box,
-// i.e. the average clamped to the common box, before its Step 4.
+// GROUP: the CTA is one scenario of a group whose scenarios share the first
+// control (Sec. IV-A).  After Step 3 the node-0 thread of every CTA publishes
+// its Step-3 argument u_0 + nu_u,0 / rho_geo and its box (both absolute); the
+// group all-reduce combines them, and each CTA sets u-hat_0 to the projection
+// onto {equal u_0} intersected with every box, i.e. the average clamped to the
+// common box, before its Step 4.
 template <class M, class T, bool AOS, bool REFINE, bool LAST, bool GROUP, class MS>
 __device__ __forceinline__ void admm_iteration(const Node<T, AOS>& nd, const MS& MT, const Layout& L, const Inst<T>& I,
                                                const NodeConst<M, T>& K, bool active, T re, T rd, T rg,
@@ -1209,13 +1257,14 @@ __device__ __forceinline__ double node_cost(const ProblemDev& P, const Inst<T>& 
 // and trust-region acceptance, and the nominal update -- without leaving
 // the kernel.
 //
-// GROUP: launched as thread-block clusters of P.group CTAs, CTA r of cluster c
-// solving scenario r of problem c (instance c * group + r).  The scenarios run
-// their ADMM iterations in lockstep with the first-control consensus and take
-// every decision as a group: a factorisation failure anywhere stops the group,
-// and acceptance, trust radius, stopping and the time budget are decided on the
-// group's sums (merits) and maxima (defect, step), so that accepted nominals
-// keep one first control.
+// GROUP: CTA k of group g solves scenario k of problem g (instance g * group
+// + k); the group's CTAs are launched as thread-block clusters so that they are
+// resident together.  The scenarios run their ADMM iterations in lockstep with
+// the first-control consensus and take every decision as a group: a
+// factorisation failure anywhere stops the group, and acceptance, trust
+// radius, stopping and the time budget are decided on the group's sums
+// (merits) and maxima (defect, step), so that accepted nominals keep one first
+// control.
 template <class M, class T, bool SMEM, bool REFINE, bool GROUP = false>
 __global__ void __launch_bounds__(MAX_THREADS) scp_kernel(ProblemDev P, Layout L, const double* x0, const double* u0,
                                                           double* xout, double* uout, ucn_scp_stats* stats, int* status_out) {
@@ -1227,7 +1276,7 @@ __global__ void __launch_bounds__(MAX_THREADS) scp_kernel(ProblemDev P, Layout L
   GroupX X{0u, 0, 0};
   if constexpr (GROUP) {
     X.g = (int)blockIdx.x / P.group;
-    X.c = ((int)blockIdx.x % P.group) / (int)cluster_size();
+    X.k = (int)blockIdx.x % P.group;
     if (threadIdx.x == 0) G->gfail = 0;
   }
   // instances are taken in the order given (largest first by default), so that
@@ -1293,9 +1342,7 @@ __global__ void __launch_bounds__(MAX_THREADS) scp_kernel(ProblemDev P, Layout L
     }
     __syncthreads();
     if constexpr (GROUP) {
-      // a failed factorisation in any scenario stops the whole group (this
-      // barrier is also the first one, so every CTA of the cluster has started
-      // before any distributed shared memory is read)
+      // a failed factorisation in any scenario stops the whole group
       if (threadIdx.x == 0) G->mine[X.epoch & 1][0] = (double)sh.fail;
       double f[1];
       group_allreduce<1>(P, G, X, 0, f);
@@ -1446,8 +1493,7 @@ __global__ void __launch_bounds__(MAX_THREADS) scp_kernel(ProblemDev P, Layout L
     stats[b] = s;
     status_out[b] = st;
   }
-  // no CTA of a group may exit while another can still read its shared memory
-  if constexpr (GROUP) cluster_sync();
+  if constexpr (GROUP) group_finish(P);
 }
 
 }  // namespace ucn

@@ -482,7 +482,7 @@ __global__ void __launch_bounds__(LANES_MAX_THREADS) scp_kernel_lanes(ProblemDev
   GroupX X{0u, 0, 0};
   if constexpr (GROUP) {
     X.g = (int)blockIdx.x / P.group;
-    X.c = ((int)blockIdx.x % P.group) / (int)cluster_size();
+    X.k = (int)blockIdx.x % P.group;
     if (threadIdx.x == 0) G->gfail = 0;
   }
   const int b = (GROUP || !P.order) ? (int)blockIdx.x : P.order[blockIdx.x];
@@ -706,7 +706,7 @@ __global__ void __launch_bounds__(LANES_MAX_THREADS) scp_kernel_lanes(ProblemDev
     stats[b] = s;
     status_out[b] = st;
   }
-  if constexpr (GROUP) cluster_sync();
+  if constexpr (GROUP) group_finish(P);
 }
 
 }  // namespace ucn

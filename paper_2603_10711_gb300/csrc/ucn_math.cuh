@@ -211,23 +211,18 @@ __device__ __forceinline__ double warp_max(double v) {
 }
 
 // ------------------------------------------------------------------ thread-block clusters
-// Rank of this CTA in its cluster and the cluster size.
-__device__ __forceinline__ unsigned cluster_rank() {
-  unsigned r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
 __device__ __forceinline__ unsigned cluster_size() {
   unsigned r;
   asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
   return r;
 }
-// Split cluster barrier: arrive (release) ... wait (acquire).  Every thread of
-// every CTA of the cluster must execute the same sequence of arrive/wait.
-__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release;" ::: "memory"); }
-__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire;" ::: "memory"); }
-__device__ __forceinline__ void cluster_sync() { cluster_arrive(); cluster_wait(); }
-// Load a double from the shared memory of CTA `rank` of this cluster, at the
+// Cluster barrier (release on arrive, acquire on wait); every thread of every
+// CTA of the cluster executes the same sequence of them.
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release;" ::: "memory");
+  asm volatile("barrier.cluster.wait.acquire;" ::: "memory");
+}
+// A double from the shared memory of CTA `rank` of this cluster, at the
 // address that `local` has in this CTA (distributed shared memory).
 __device__ __forceinline__ double ld_cluster(const double* local, unsigned rank) {
   const unsigned a = (unsigned)__cvta_generic_to_shared(local);
