@@ -268,6 +268,7 @@ def run_ours(args, rank, world):
     s64.close()
 
     serving_out = run_serving(args) if (args.serving_requests > 0 and world == 1) else None
+    batching_out = run_batching(args) if (args.batching_batch > 0 and world == 1) else None
     scenario_out = run_scenarios(args) if (args.scenario_steps > 0 and world == 1) else None
 
     flops_ni = flops_per_node_iter(prob.nx, prob.nu, mars_mirror_flops())
@@ -306,6 +307,8 @@ def run_ours(args, rank, world):
         out["serving"] = serving_out
     if scenario_out is not None:
         out["scenario_mpc"] = scenario_out
+    if batching_out is not None:
+        out["batching"] = batching_out
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         out["cpu_baseline"] = cpu_baseline(args)
     solver.close()
@@ -337,6 +340,37 @@ def run_serving(args):
     return {"arrival_rate_per_s": args.serving_rate, "requests": len(stream), "mix": "70% quad N 30-120 / 30% Mars N 50-200",
             "fp32_continuous": fp32, "fp64_per_request": dict(fp64, requests=n64),
             "latency": "arrival -> result collected (host clock)"}
+
+
+def run_batching(args):
+    """Uneven-horizon batching: 4096 quadrotors, N ~ U{40..120}, 10-30 obstacles,
+    FP32 + refinement.  The autotuner picks the size-class split and threads per
+    node on a 608-instance sample; the batch is then solved as one plain launch
+    (library defaults) and as the tuned classes replayed from a CUDA graph."""
+    import torch
+    from paper_2603_10711_gb300 import batching
+    prob = W.quad_box(args.batching_batch, seed=2)
+    t0 = time.perf_counter()
+    cfg, timings = batching.autotune(prob, cache_path=None)
+    tune_s = time.perf_counter() - t0
+    out = {"workload": "quad_box_%d_N40-120_obs10-30" % prob.batch, "autotuned": cfg, "autotune_s": tune_s,
+           "candidates_ms": {k: 1e3 * v for k, v in timings.items()}}
+    for name, kw in (("default_single_launch", dict(splits=[])), ("tuned_graph", dict(splits=cfg["splits"], lanes=cfg["lanes"]))):
+        cs = batching.ClassedSolver(prob, **kw)
+        if name == "tuned_graph":
+            cs.capture()
+        cs.solve(); torch.cuda.synchronize()
+        ms = []
+        for _ in range(3):
+            e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(); cs.solve(); e1.record(); e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        st = cs.stats()
+        passed = int(np.sum(st["defect"] <= 1e-5))
+        out[name] = {"ms": min(ms), "solves_per_s": passed / (min(ms) / 1e3), "pass_rate": passed / prob.batch,
+                     "scp_iters_mean": float(st["scp_iters"].mean())}
+        cs.close()
+    return out
 
 
 def run_scenarios(args):
@@ -446,16 +480,17 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--batch", type=int, default=1024)
     ap.add_argument("--fp64-steps", type=int, default=2)
-    ap.add_argument("--cpu-sample", type=int, default=96)
+    ap.add_argument("--cpu-sample", type=int, default=384)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=2000, help="requests of the serving stream (0: skip)")
     ap.add_argument("--serving-rate", type=float, default=2000.0, help="Poisson arrival rate of the serving stream")
     ap.add_argument("--serving-fp64-requests", type=int, default=16)
+    ap.add_argument("--batching-batch", type=int, default=4096, help="uneven quadrotor batch (0: skip the section)")
     ap.add_argument("--scenario-problems", type=int, default=256)
     ap.add_argument("--scenario-count", type=int, default=64, help="scenarios per problem (group size)")
     ap.add_argument("--scenario-steps", type=int, default=3, help="receding-horizon steps (0: skip the section)")
     ap.add_argument("--scenario-fp64-problems", type=int, default=64)
-    ap.add_argument("--mode", default="full", choices=["full", "kernel", "scenario"],
+    ap.add_argument("--mode", default="full", choices=["full", "kernel", "scenario", "batching"],
                     help="kernel: time only the fused kernel (profiler captures)")
     ap.add_argument("--scp-iters", type=int, default=0, help="fixed SCP iteration count (0: the workload's cap + stop test)")
     ap.add_argument("--fp64", action="store_true", help="kernel mode: the FP64 plain path")
@@ -473,6 +508,8 @@ def main():
         out = run_kernel_only(args)
     elif args.mode == "scenario":
         out = run_scenarios(args)
+    elif args.mode == "batching":
+        out = run_batching(args)
     elif args.impl == "reference":
         out = run_reference(args, rank, world)
     else:

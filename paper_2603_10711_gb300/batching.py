@@ -28,7 +28,7 @@ import numpy as np
 from . import ucn
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "ucn_autotune.json")
+DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "ucn_autotune_v2.json")
 
 
 def class_indices(N: np.ndarray, splits: Sequence[int]) -> List[np.ndarray]:
@@ -45,7 +45,8 @@ def class_indices(N: np.ndarray, splits: Sequence[int]) -> List[np.ndarray]:
 class ClassedSolver:
     """The fused SCP solve of one batch, split into size classes."""
 
-    def __init__(self, prob, splits: Sequence[int] = (), precision=ucn.UCN_PREC_FP32_REFINE, device="cuda"):
+    def __init__(self, prob, splits: Sequence[int] = (), precision=ucn.UCN_PREC_FP32_REFINE, device="cuda",
+                 lanes: int = 0):
         import torch
         self.prob = prob
         self.splits = list(splits)
@@ -53,6 +54,13 @@ class ClassedSolver:
         self.classes = class_indices(np.asarray(prob.N), self.splits)
         self.subs = [prob.subset(idx) for idx in self.classes]
         self.solvers = [ucn.Solver(sp, precision=precision, device=device) for sp in self.subs]
+        if lanes:
+            # threads per node where the class allows it (4 needs a quadrotor class of <= 128 nodes)
+            for s in self.solvers:
+                try:
+                    ucn.ucn_problem_set_lanes(s.handle, lanes)
+                except ucn.UcnError:
+                    ucn.ucn_problem_set_lanes(s.handle, 1)
         self.x0 = [s.tensor(sp.xguess) for s, sp in zip(self.solvers, self.subs)]
         self.u0 = [s.tensor(sp.uguess) for s, sp in zip(self.solvers, self.subs)]
         self.streams = [torch.cuda.Stream(device=self.device) for _ in self.solvers]
@@ -132,13 +140,22 @@ def candidate_splits(prob) -> List[List[int]]:
     return cands
 
 
+def candidate_configs(prob) -> List[dict]:
+    """Every split, with one and with four threads per node (quadrotor) -- the
+    per-node parallelism the CTA size follows."""
+    lanes = (1, 4) if int(prob.model) == ucn.UCN_MODEL_QUAD12 else (1,)
+    return [{"splits": sp, "lanes": ln} for sp in candidate_splits(prob) for ln in lanes]
+
+
 def autotune(prob, precision=ucn.UCN_PREC_FP32_REFINE, sample: int = 608, scp_iters: int = 3,
              cache_path: Optional[str] = DEFAULT_CACHE, device="cuda", verbose=False):
-    """Pick the size-class split with the shortest solve of a sample of the batch.
+    """Pick the size-class split and threads per node with the shortest solve
+    of a sample of the batch.
 
-    Each candidate runs `scp_iters` fixed SCP iterations (the iteration count
-    only scales the time) on `sample` evenly spaced instances; the fastest
-    split is cached under the batch's signature.  Returns (splits, timings)."""
+    Each candidate of `candidate_configs` runs `scp_iters` fixed SCP iterations
+    (the iteration count only scales the time) on `sample` evenly spaced
+    instances; the fastest is cached under the batch's signature.  Returns
+    (config, timings), config = {"splits": [...], "lanes": n}."""
     import torch
     sig = signature(prob, precision)
     cache = {}
@@ -148,13 +165,13 @@ def autotune(prob, precision=ucn.UCN_PREC_FP32_REFINE, sample: int = 608, scp_it
         except Exception:
             cache = {}
     if sig in cache:
-        return cache[sig]["splits"], cache[sig]["timings"]
+        return cache[sig]["config"], cache[sig]["timings"]
     n = min(sample, prob.batch)
     sub = prob.subset(np.linspace(0, prob.batch - 1, n).astype(np.int64))
     sub.settings.update(dict(scp_iters=scp_iters, stop=0))
     timings = {}
-    for cand in candidate_splits(sub):
-        cs = ClassedSolver(sub, cand, precision=precision, device=device)
+    for cand in candidate_configs(sub):
+        cs = ClassedSolver(sub, cand["splits"], precision=precision, device=device, lanes=cand["lanes"])
         cs.launch()
         torch.cuda.synchronize(device)
         t0 = time.perf_counter()
@@ -163,10 +180,10 @@ def autotune(prob, precision=ucn.UCN_PREC_FP32_REFINE, sample: int = 608, scp_it
         timings[json.dumps(cand)] = time.perf_counter() - t0
         cs.close()
         if verbose:
-            print("split", cand, "%.2f ms" % (1e3 * timings[json.dumps(cand)]))
+            print("config", cand, "%.2f ms" % (1e3 * timings[json.dumps(cand)]))
     best = json.loads(min(timings, key=timings.get))
     if cache_path:
-        cache[sig] = {"splits": best, "timings": timings}
+        cache[sig] = {"config": best, "timings": timings}
         os.makedirs(os.path.dirname(cache_path), exist_ok=True)
         json.dump(cache, open(cache_path, "w"), indent=1)
     return best, timings

@@ -71,8 +71,43 @@ def test_graph_replay_matches_direct_launch():
 def test_autotune_picks_a_candidate_and_caches(tmp_path):
     prob = W.quad_box(64, seed=4, N_range=(20, 90), obs_range=(3, 10))
     path = str(tmp_path / "tune.json")
-    splits, timings = batching.autotune(prob, sample=64, scp_iters=1, cache_path=path)
-    assert [list(map(int, s)) for s in [splits]][0] in [c for c in batching.candidate_splits(prob)]
-    assert len(timings) == len(batching.candidate_splits(prob))
+    cfg, timings = batching.autotune(prob, sample=64, scp_iters=1, cache_path=path)
+    assert cfg in batching.candidate_configs(prob)
+    assert len(timings) == len(batching.candidate_configs(prob)) == 2 * len(batching.candidate_splits(prob))
     again, _ = batching.autotune(prob, sample=64, scp_iters=1, cache_path=path)
-    assert again == splits
+    assert again == cfg
+
+
+@pytest.mark.parametrize("prec,tol", [(ucn.UCN_PREC_FP64, 1e-9), (ucn.UCN_PREC_FP32_REFINE, 1e-4)])
+def test_threads_per_node_agree_with_each_other_and_the_oracle(prec, tol):
+    prob = uneven()
+    xs = {}
+    for lanes in (1, 4):
+        s = ucn.Solver(prob, precision=prec)
+        ucn.ucn_problem_set_lanes(s.handle, lanes)
+        assert ucn.ucn_problem_lanes(s.handle) == lanes
+        x, u = s.scp_solve(); torch.cuda.synchronize()
+        xs[lanes] = x.cpu().numpy().copy()
+        s.close()
+    xr, ur, sr, _ = oracle.scp_solve(prob)
+    for lanes in (1, 4):
+        assert rel_err(xs[lanes], xr) <= tol, lanes
+    if prec == ucn.UCN_PREC_FP64:
+        assert rel_err(xs[1], xs[4]) <= 1e-12
+
+
+def test_lane_layout_is_refused_where_it_does_not_apply():
+    mars = W.mars_batch(2, seed=1, N=20)
+    s = ucn.Solver(mars, precision=ucn.UCN_PREC_FP32_REFINE)
+    assert ucn.ucn_problem_lanes(s.handle) == 1
+    with pytest.raises(ucn.UcnError, match="threads per node"):
+        ucn.ucn_problem_set_lanes(s.handle, 4)
+    s.close()
+    long_quad = W.quad_box(1, seed=3, N_range=(130, 130), obs_range=(2, 2))
+    s = ucn.Solver(long_quad, precision=ucn.UCN_PREC_FP32_REFINE, scp_iters=2, admm_iters=10)
+    assert ucn.ucn_problem_lanes(s.handle) == 1
+    with pytest.raises(ucn.UcnError):
+        ucn.ucn_problem_set_lanes(s.handle, 4)
+    s.scp_solve(); torch.cuda.synchronize()
+    assert np.isfinite(s.stats_host()["cost"]).all()
+    s.close()
