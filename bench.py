@@ -154,6 +154,8 @@ def make_problem(args, rank=0):
     over = {}
     if args.scp_iters:
         over = dict(scp_iters=args.scp_iters, stop=0)
+    if getattr(args, "admm_iters", 0):
+        over["admm_iters"] = args.admm_iters
     if getattr(args, "workload", "mars") == "quad_box":
         return W.quad_box(args.batch, seed=2 + rank, settings=over)
     if getattr(args, "workload", "mars") == "quad40":
@@ -493,6 +495,7 @@ def main():
     ap.add_argument("--mode", default="full", choices=["full", "kernel", "scenario", "batching"],
                     help="kernel: time only the fused kernel (profiler captures)")
     ap.add_argument("--scp-iters", type=int, default=0, help="fixed SCP iteration count (0: the workload's cap + stop test)")
+    ap.add_argument("--admm-iters", type=int, default=0, help="kernel mode: ADMM iterations per SCP iteration (0: the workload's)")
     ap.add_argument("--fp64", action="store_true", help="kernel mode: the FP64 plain path")
     ap.add_argument("--workload", default="mars", choices=["mars", "quad_box", "quad40"],
                     help="kernel mode: mars (1024-instance Mars batch), quad_box (uneven quadrotor batch) "

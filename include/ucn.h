@@ -219,8 +219,9 @@ ucn_status ucn_scp_solve(ucn_problem* prob, const double* x0_d, const double* u0
                          double* x_out_d, double* u_out_d, ucn_scp_stats* stats_d,
                          int* status_d, void* stream);
 
-/* Receding-horizon step for MPC (Sec. IV-A: the controller applies the shared
- * first control and warm-starts the next solve by shifting the scenario tube).
+/* Receding-horizon step for MPC (Sec. IV-A: the common first control is
+ * executed after each solve and the next solve starts from the previous tube
+ * moved one step ahead).
  * From the solution (x_d, u_d) of ucn_scp_solve:
  *   plant    each group's first instance (each instance when group <= 1) is
  *            the plant: x_init <- RK4(x_init, u_0, dt) with its own model
