@@ -48,7 +48,7 @@
 
 namespace {
 
-enum { MODEL_QUAD12 = 1, MODEL_MARS7 = 2 };
+enum { MODEL_QUAD12 = 1, MODEL_MARS7 = 2, MODEL_QUAT13 = 3 };
 enum { BLK_NONE = -1, BLK_HALF = 0, BLK_BALL = 1, BLK_CONE = 2 };
 enum { ST_OK = 0, ST_NUMERIC = 4, ST_NOTCONV = 5 };
 
@@ -103,12 +103,46 @@ void mars_f(const double* prm, const S* x, const S* u, S* xd) {
   xd[6] = -alpha * Tn;
 }
 
-int model_nx(int model) { return model == MODEL_QUAD12 ? 12 : 7; }
-int model_nu(int model) { return model == MODEL_QUAD12 ? 4 : 3; }
+// Quadrotor, 13 states (Sec. IV-A1): r(3), v(3), unit quaternion q = (qw, qx,
+// qy, qz) body-to-world, omega(3) body rates; u = (T, tau_x, tau_y, tau_z) total
+// thrust along the body z axis and body torques.  params as quad_f (arm and km
+// unused).  Newton-Euler:
+//   r' = v
+//   v' = (T/m) R(q) e3 - g e3 - (cd/m) v,
+//        R(q) e3 = (2(qx qz + qw qy), 2(qy qz - qw qx), qw^2 - qx^2 - qy^2 + qz^2)
+//   q' = 1/2 q (x) (0, omega)          (Hamilton product)
+//   omega' = J^-1 (tau - omega x J omega)
+// The quaternion is integrated as four states (no renormalisation); R(q) e3 is
+// the quadratic form of the rotation, exact for unit q.
+template <class S>
+void quat_f(const double* prm, const S* x, const S* u, S* xd) {
+  const double m = prm[0], Jx = prm[1], Jy = prm[2], Jz = prm[3], cd = prm[6], g = prm[7];
+  const S qw = x[6], qx = x[7], qy = x[8], qz = x[9];
+  const S wx = x[10], wy = x[11], wz = x[12];
+  const S T = u[0];
+  const S a0 = 2.0 * (qx * qz + qw * qy);
+  const S a1 = 2.0 * (qy * qz - qw * qx);
+  const S a2 = qw * qw - qx * qx - qy * qy + qz * qz;
+  for (int k = 0; k < 3; ++k) xd[k] = x[3 + k];
+  xd[3] = a0 * T / m - (cd / m) * x[3];
+  xd[4] = a1 * T / m - (cd / m) * x[4];
+  xd[5] = a2 * T / m - g - (cd / m) * x[5];
+  xd[6] = 0.5 * (-qx * wx - qy * wy - qz * wz);
+  xd[7] = 0.5 * (qw * wx + qy * wz - qz * wy);
+  xd[8] = 0.5 * (qw * wy - qx * wz + qz * wx);
+  xd[9] = 0.5 * (qw * wz + qx * wy - qy * wx);
+  xd[10] = (u[1] - (Jz - Jy) * wy * wz) / Jx;
+  xd[11] = (u[2] - (Jx - Jz) * wz * wx) / Jy;
+  xd[12] = (u[3] - (Jy - Jx) * wx * wy) / Jz;
+}
+
+int model_nx(int model) { return model == MODEL_QUAD12 ? 12 : (model == MODEL_QUAT13 ? 13 : 7); }
+int model_nu(int model) { return model == MODEL_MARS7 ? 3 : 4; }
 
 template <class S>
 void f_eval(int model, const double* prm, const S* x, const S* u, S* xd) {
   if (model == MODEL_QUAD12) quad_f<S>(prm, x, u, xd);
+  else if (model == MODEL_QUAT13) quat_f<S>(prm, x, u, xd);
   else mars_f<S>(prm, x, u, xd);
 }
 
@@ -197,8 +231,48 @@ void mars_jac(const double* prm, const double* x, const double* u, double* fx, d
     for (int k = 0; k < 3; ++k) fu[6 * nu + k] = -alpha * u[k] / Tn;
 }
 
+void quat_jac(const double* prm, const double* x, const double* u, double* fx, double* fu) {
+  const int nx = 13, nu = 4;
+  const double m = prm[0], Jx = prm[1], Jy = prm[2], Jz = prm[3], cd = prm[6];
+  std::fill(fx, fx + nx * nx, 0.0);
+  std::fill(fu, fu + nx * nu, 0.0);
+  const double qw = x[6], qx = x[7], qy = x[8], qz = x[9];
+  const double wx = x[10], wy = x[11], wz = x[12];
+  const double T = u[0];
+  const double a[3] = {2.0 * (qx * qz + qw * qy), 2.0 * (qy * qz - qw * qx), qw * qw - qx * qx - qy * qy + qz * qz};
+  // d a_k / d (qw, qx, qy, qz)
+  const double da[3][4] = {{2.0 * qy, 2.0 * qz, 2.0 * qw, 2.0 * qx},
+                           {-2.0 * qx, -2.0 * qw, 2.0 * qz, 2.0 * qy},
+                           {2.0 * qw, -2.0 * qx, -2.0 * qy, 2.0 * qz}};
+  for (int k = 0; k < 3; ++k) fx[k * nx + 3 + k] = 1.0;              // r' = v
+  for (int k = 0; k < 3; ++k) {
+    fx[(3 + k) * nx + 3 + k] = -cd / m;
+    for (int j = 0; j < 4; ++j) fx[(3 + k) * nx + 6 + j] = da[k][j] * T / m;
+    fu[(3 + k) * nu + 0] = a[k] / m;
+  }
+  // q' = 1/2 Omega(omega) q: rows qw', qx', qy', qz' over (qw, qx, qy, qz)
+  const double Om[4][4] = {{0.0, -wx, -wy, -wz}, {wx, 0.0, wz, -wy}, {wy, -wz, 0.0, wx}, {wz, wy, -wx, 0.0}};
+  // ... and over (wx, wy, wz)
+  const double Qm[4][3] = {{-qx, -qy, -qz}, {qw, -qz, qy}, {qz, qw, -qx}, {-qy, qx, qw}};
+  for (int r = 0; r < 4; ++r) {
+    for (int c = 0; c < 4; ++c) fx[(6 + r) * nx + 6 + c] = 0.5 * Om[r][c];
+    for (int c = 0; c < 3; ++c) fx[(6 + r) * nx + 10 + c] = 0.5 * Qm[r][c];
+  }
+  // omega' = J^-1 (tau - omega x J omega)
+  fx[10 * nx + 11] = -(Jz - Jy) * wz / Jx;
+  fx[10 * nx + 12] = -(Jz - Jy) * wy / Jx;
+  fx[11 * nx + 10] = -(Jx - Jz) * wz / Jy;
+  fx[11 * nx + 12] = -(Jx - Jz) * wx / Jy;
+  fx[12 * nx + 10] = -(Jy - Jx) * wy / Jz;
+  fx[12 * nx + 11] = -(Jy - Jx) * wx / Jz;
+  fu[10 * nu + 1] = 1.0 / Jx;
+  fu[11 * nu + 2] = 1.0 / Jy;
+  fu[12 * nu + 3] = 1.0 / Jz;
+}
+
 void f_jac(int model, const double* prm, const double* x, const double* u, double* fx, double* fu) {
   if (model == MODEL_QUAD12) quad_jac(prm, x, u, fx, fu);
+  else if (model == MODEL_QUAT13) quat_jac(prm, x, u, fx, fu);
   else mars_jac(prm, x, u, fx, fu);
 }
 
@@ -694,7 +768,7 @@ struct OrcProblem {
 
 namespace {
 
-int problem_maxblk(const OrcProblem& P) { return P.model == MODEL_QUAD12 ? P.max_obs : 3; }
+int problem_maxblk(const OrcProblem& P) { return P.model == MODEL_MARS7 ? 3 : P.max_obs; }
 
 // Build the QP of Eq. (2) at nominal (xbar, ubar) for instance b: exact
 // quadratic cost expansion, trust-region l_inf box of radius `radius`
@@ -744,7 +818,7 @@ void build_qp(const OrcProblem& P, int b, const double* xbar, const double* ubar
     const int n = term ? nx : n1;
     nd.blk.assign(qp.maxblk, Block());
     for (Block& bl : nd.blk) bl.G.assign(3 * n, 0.0);
-    if (P.model == MODEL_QUAD12) {
+    if (P.model != MODEL_MARS7) {
       // Obstacle j, linearised about the nominal position:
       // n = (p - c)/|p - c|, keep n^T p >= n^T c + r (tie-break n = e_z).
       const double* p = &xbar[i * nx];

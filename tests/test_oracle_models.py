@@ -15,6 +15,7 @@ import workloads as W
 
 QUAD = W.MODEL_QUAD12
 MARS = W.MODEL_MARS7
+QUAT = W.MODEL_QUAT13
 
 
 def quad_params(m=1.0, J=(0.01, 0.01, 0.02), l=0.2, km=0.01, cd=0.0, g=9.81):
@@ -42,6 +43,22 @@ def R_zyx(phi, th, psi):
 
 def hat(w):
     return np.array([[0, -w[2], w[1]], [w[2], 0, -w[0]], [-w[1], w[0], 0]])
+
+
+def quat_mul(a, b):
+    """Hamilton product, scalar first."""
+    return np.array([a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3],
+                     a[0] * b[1] + a[1] * b[0] + a[2] * b[3] - a[3] * b[2],
+                     a[0] * b[2] - a[1] * b[3] + a[2] * b[0] + a[3] * b[1],
+                     a[0] * b[3] + a[1] * b[2] - a[2] * b[1] + a[3] * b[0]])
+
+
+def quat_from_euler(phi, th, psi):
+    """q of R = Rz(psi) Ry(theta) Rx(phi): q = qz (x) qy (x) qx."""
+    qx = np.array([math.cos(phi / 2), math.sin(phi / 2), 0, 0])
+    qy = np.array([math.cos(th / 2), 0, math.sin(th / 2), 0])
+    qz = np.array([math.cos(psi / 2), 0, 0, math.sin(psi / 2)])
+    return quat_mul(qz, quat_mul(qy, qx))
 
 
 # ------------------------------------------------------------------ quadrotor
@@ -149,13 +166,17 @@ def test_mars_free_fall():
     assert xt[6] == 1.0
 
 
-@pytest.mark.parametrize("model", [QUAD, MARS])
+@pytest.mark.parametrize("model", [QUAD, MARS, QUAT])
 def test_rk4_is_fourth_order(model):
     # one-step error against a converged fine rollout shrinks ~32x when h halves
     if model == QUAD:
         prm = quad_params(cd=0.1)
         x = np.array([0.1, 0.2, 0.3, 0.5, -0.4, 0.2, 0.3, -0.2, 0.4, 1.0, -2.0, 0.5])
         u = np.array([2.0, 3.0, 2.5, 1.5])
+    elif model == QUAT:
+        prm = quad_params(cd=0.1)
+        x = np.concatenate([[0.1, 0.2, 0.3, 0.5, -0.4, 0.2], quat_from_euler(0.3, -0.2, 0.4), [1.0, -2.0, 0.5]])
+        u = np.array([9.0, 0.05, -0.08, 0.02])
     else:
         prm = mars_params()
         x = np.array([2.0, 0.3, -0.1, -0.6, 0.1, 0.05, 1.0]); u = np.array([0.8, 0.2, -0.1])
@@ -173,6 +194,11 @@ def random_point(model, seed):
         x = rng.uniform(-1, 1, 12); x[6:9] *= 0.6
         u = rng.uniform(0.5, 4.0, 4)
         prm = quad_params(cd=0.15)
+    elif model == QUAT:
+        q = rng.normal(size=4); q /= np.linalg.norm(q)
+        x = np.concatenate([rng.uniform(-1, 1, 6), q, rng.uniform(-2, 2, 3)])
+        u = np.concatenate([rng.uniform(3, 15, 1), rng.uniform(-0.5, 0.5, 3)])
+        prm = quad_params(cd=0.15)
     else:
         x = np.concatenate([rng.uniform(0.5, 2, 3), rng.uniform(-0.5, 0.5, 3), [rng.uniform(0.8, 1.0)]])
         u = rng.uniform(-0.6, 0.9, 3)
@@ -180,7 +206,7 @@ def random_point(model, seed):
     return prm, x, u
 
 
-@pytest.mark.parametrize("model", [QUAD, MARS])
+@pytest.mark.parametrize("model", [QUAD, MARS, QUAT])
 @pytest.mark.parametrize("seed", range(5))
 def test_jacobians_match_complex_step(model, seed):
     prm, x, u = random_point(model, seed)
@@ -194,7 +220,7 @@ def test_jacobians_match_complex_step(model, seed):
     np.testing.assert_allclose(xn, oracle.rk4(model, prm, h, x, u), atol=0)
 
 
-@pytest.mark.parametrize("model", [QUAD, MARS])
+@pytest.mark.parametrize("model", [QUAD, MARS, QUAT])
 def test_jacobians_match_central_differences(model):
     prm, x, u = random_point(model, 11)
     h = 0.05
@@ -208,3 +234,71 @@ def test_jacobians_match_central_differences(model):
         col = (fp - fm) / (2 * eps)
         ref = A[:, j] if j < nx else B[:, j - nx]
         np.testing.assert_allclose(col, ref, atol=2e-8)
+
+
+# ------------------------------------------------------------------ 13-state quaternion quadrotor
+def test_quat_hover_is_equilibrium_at_any_yaw():
+    prm = quad_params()
+    for psi in (0.0, 0.7, -2.5):
+        x = np.concatenate([[1.0, -2.0, 3.0, 0, 0, 0], quat_from_euler(0, 0, psi), [0, 0, 0]])
+        u = np.array([9.81, 0.0, 0.0, 0.0])
+        np.testing.assert_allclose(oracle.f(QUAT, prm, x, u), 0.0, atol=1e-14)
+
+
+def test_quat_matches_the_euler_model_under_the_rotor_map():
+    # the 12-state Euler-angle model and the 13-state quaternion model describe the
+    # same rigid body: with q = q(eta), T = sum f_i and tau = the rotor torque map,
+    # accelerations agree, and q' is the chain rule of q(eta) along eta' = W omega
+    rng = np.random.default_rng(3)
+    prm = quad_params(cd=0.12)
+    l, km = prm[4], prm[5]
+    for _ in range(5):
+        eta = rng.uniform(-0.6, 0.6, 3)
+        p, v, w = rng.uniform(-1, 1, 3), rng.uniform(-1, 1, 3), rng.uniform(-2, 2, 3)
+        fr = rng.uniform(0.5, 4.0, 4)
+        x12 = np.concatenate([p, v, eta, w])
+        q = quat_from_euler(*eta)
+        x13 = np.concatenate([p, v, q, w])
+        u13 = np.array([fr.sum(), l * (fr[1] - fr[3]), l * (fr[2] - fr[0]), km * (fr[0] - fr[1] + fr[2] - fr[3])])
+        d12 = oracle.f(QUAD, prm, x12, fr)
+        d13 = oracle.f(QUAT, prm, x13, u13)
+        np.testing.assert_allclose(d13[0:6], d12[0:6], atol=1e-13)
+        np.testing.assert_allclose(d13[10:13], d12[9:12], atol=1e-12)
+        eps = 1e-6
+        dq = np.zeros(4)
+        for k in range(3):
+            e = np.zeros(3); e[k] = eps
+            dq += (quat_from_euler(*(eta + e)) - quat_from_euler(*(eta - e))) / (2 * eps) * d12[6 + k]
+        np.testing.assert_allclose(d13[6:10], dq, atol=1e-8)
+
+
+def test_quat_thrust_direction_is_the_body_z_axis():
+    prm = quad_params()
+    for eta in ((0.3, -0.2, 0.4), (-0.5, 0.1, 2.0)):
+        q = quat_from_euler(*eta)
+        x = np.concatenate([np.zeros(6), q, np.zeros(3)])
+        d = oracle.f(QUAT, prm, x, np.array([2.0, 0, 0, 0]))
+        np.testing.assert_allclose(d[3:6] + np.array([0, 0, 9.81]), 2.0 * R_zyx(*eta)[:, 2], atol=1e-14)
+
+
+def test_quat_kinematics_keep_the_norm_rate_zero():
+    rng = np.random.default_rng(5)
+    prm = quad_params()
+    for _ in range(10):
+        q = rng.normal(size=4) * rng.uniform(0.5, 2.0)
+        x = np.concatenate([np.zeros(6), q, rng.uniform(-3, 3, 3)])
+        d = oracle.f(QUAT, prm, x, np.array([5.0, 0.1, -0.2, 0.3]))
+        assert abs(q @ d[6:10]) < 1e-14 * max(1.0, q @ q)
+
+
+def test_quat_spin_about_a_principal_axis_matches_closed_form():
+    prm = quad_params()
+    wz = 1.3
+    x = np.concatenate([np.zeros(6), [1, 0, 0, 0], [0, 0, wz]])
+    u = np.array([9.81, 0, 0, 0])
+    t = 2.0
+    xt = rollout(QUAT, prm, 0.01, x, u, 200)
+    np.testing.assert_allclose(xt[6:10], [math.cos(wz * t / 2), 0, 0, math.sin(wz * t / 2)], atol=1e-9)
+    np.testing.assert_allclose(xt[10:13], [0, 0, wz], atol=1e-15)
+    # hover thrust holds the body still up to the RK4 drift of |q| (thrust scales with |q|^2)
+    np.testing.assert_allclose(xt[0:6], 0.0, atol=1e-8)

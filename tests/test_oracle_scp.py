@@ -95,6 +95,25 @@ def test_mars_converges_and_respects_sets():
         assert xb[:, 6].min() >= prob.xlo[b, 6] and np.all(np.diff(xb[:, 6]) <= 1e-5)   # mass only falls
 
 
+def test_quaternion_quadrotor_converges_and_respects_sets():
+    # the 13-state study task with a longer schedule (rho 10 -> 1e3 over 80 iterations)
+    prob = W.quat_study(3, rho0=10.0, rho_final=1e3, scp_iters=80, admm_iters=250,
+                        settings=dict(stop=1, step_tol=1.0))
+    x, u, st, _ = oracle.scp_solve(prob)
+    for b in range(3):
+        xb, ub = instance(prob, x, u, b)
+        assert st[b, 0] <= 1e-5 and st[b, 10] == 0
+        assert abs(max_defect(prob, b, xb, ub) - st[b, 0]) < 1e-15
+        np.testing.assert_array_equal(xb[0], prob.xinit[b])
+        np.testing.assert_array_equal(xb[-1][:6], prob.xtarget[b][:6])        # position, zero velocity
+        assert np.all(ub >= prob.ulo[b] - 1e-9) and np.all(ub <= prob.uhi[b] + 1e-9)
+        for j in range(prob.nobs[b]):
+            dist = np.linalg.norm(xb[:, :3] - prob.obs_c[b, j], axis=1)
+            assert dist.min() >= prob.obs_r[b, j] - 1e-3
+        # the quaternion stays a rotation to the accuracy the defect allows
+        assert np.abs(np.linalg.norm(xb[:, 6:10], axis=1) - 1.0).max() < 0.05
+
+
 def test_fixed_count_solve_runs_every_iteration():
     prob = W.quad_path(1, seed=0)
     _, _, st, log = oracle.scp_solve(prob, log=True)

@@ -35,6 +35,7 @@ import numpy as np
 
 MODEL_QUAD12 = 1
 MODEL_MARS7 = 2
+MODEL_QUAT13 = 3
 
 _M64 = np.uint64(0xFFFFFFFFFFFFFFFF)
 _GOLDEN = np.uint64(0x9E3779B97F4A7C15)
@@ -224,6 +225,62 @@ def quad_path(B=1, seed=0, N=50, dt=0.05, n_obs=5, settings=None) -> Problem:
             obs_c[b, j] = c; obs_r[b, j] = r
     return _quad_common(B, np.full(B, N), dt, start, goal, obs_c, obs_r, np.full(B, n_obs),
                         settings or {})
+
+
+QUAT_TMAX, QUAT_TAUMAX = 20.0, 5.0     # N, N m
+
+
+def quat_study(B=1, seed=5, N=50, tf=6.0, n_obs=3, rho0=1.0, rho_final=1e3, scp_iters=20, admm_iters=100,
+               settings=None) -> Problem:
+    """The paper's 13-state quadrotor parameter study (Sec. IV-A2): a 6 s flight
+    (N = 50) from hover at (-5, -5, 2) m to (5, 5, 2) m with the terminal
+    position and zero velocity enforced; three spheres of radius U[1.2, 1.5] m
+    on the direct path (centres at s = 1/4, 1/2, 3/4 of it, s jittered by
+    U[-0.05, 0.05], offset U[-0.6, 0.6] m across and U[-0.3, 0.3] m in height);
+    thrust in [0, 20] N, torques in [-5, 5] N m; m = 1 kg, g = 9.81, J as the
+    12-state model.  Cost Q = I about the goal state (identity attitude), R =
+    0.1 I about hover.  All three penalties start at rho0 and rise
+    geometrically to rho_final over the scp_iters SCP iterations (fixed count).
+    """
+    nx, nu = 13, 4
+    start = np.array([-5.0, -5.0, 2.0]); goal = np.array([5.0, 5.0, 2.0])
+    d = goal - start
+    across = np.array([-d[1], d[0], 0.0]) / np.linalg.norm(d[:2])
+    obs_c = np.zeros((B, n_obs, 3)); obs_r = np.zeros((B, n_obs))
+    for b in range(B):
+        for j in range(n_obs):
+            base = (b * 64 + j) * 8
+            sj = (j + 1) / (n_obs + 1) + U(seed, 60, base, -0.05, 0.05)
+            c = start + sj * d + U(seed, 61, base, -0.6, 0.6) * across + np.array([0.0, 0.0, U(seed, 62, base, -0.3, 0.3)])
+            obs_c[b, j] = c
+            obs_r[b, j] = U(seed, 63, base, 1.2, 1.5)
+    params = _quad_params(B)
+    hover = params[:, 0] * QUAD_G
+    xinit = np.zeros((B, nx)); xinit[:, 0:3] = start; xinit[:, 6] = 1.0
+    xtarget = np.zeros((B, nx)); xtarget[:, 0:3] = goal; xtarget[:, 6] = 1.0
+    tmask = np.zeros((B, nx), np.uint8); tmask[:, 0:6] = 1
+    uref = np.zeros((B, nu)); uref[:, 0] = hover
+    s_ = np.arange(N + 1)[:, None] / N
+    xs, us = [], []
+    for b in range(B):
+        xb = np.zeros((N + 1, nx)); xb[:, 0:3] = (1 - s_) * start + s_ * goal; xb[:, 6] = 1.0
+        xs.append(xb)
+        ub = np.zeros((N, nu)); ub[:, 0] = hover[b]
+        us.append(ub)
+    st = dict(DEFAULT_SETTINGS)
+    st.update(dict(rho_eq=rho0, rho_dyn=rho0, rho_geo=rho0, rho_final=rho_final, scp_iters=scp_iters,
+                   admm_iters=admm_iters, stop=0))
+    st.update(settings or {})
+    return Problem(
+        model=MODEL_QUAT13, nx=nx, nu=nu, N=np.full(B, N, np.int32), dt=np.full(B, tf / N),
+        params=params, Qd=np.ones((B, nx)), xref=xtarget.copy(), Rd=np.full((B, nu), 0.1), uref=uref,
+        QNd=np.ones((B, nx)), qN=np.zeros((B, nx)),
+        xlo=np.full((B, nx), -np.inf), xhi=np.full((B, nx), np.inf),
+        ulo=np.tile([0.0, -QUAT_TAUMAX, -QUAT_TAUMAX, -QUAT_TAUMAX], (B, 1)),
+        uhi=np.tile([QUAT_TMAX, QUAT_TAUMAX, QUAT_TAUMAX, QUAT_TAUMAX], (B, 1)),
+        xinit=xinit, xtarget=xtarget, tmask=tmask,
+        nobs=np.full(B, n_obs, np.int32), obs_c=obs_c, obs_r=obs_r, sets=np.zeros((B, 4)),
+        xguess=np.concatenate(xs), uguess=np.concatenate(us), settings=st)
 
 
 def quad_box(B=4096, seed=2, N_range=(40, 120), obs_range=(10, 30), dt=0.05,
