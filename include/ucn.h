@@ -49,7 +49,7 @@ typedef enum {
   UCN_EBUSY = 7       /* serving: no free slot / ring full */
 } ucn_status;
 
-typedef enum { UCN_MODEL_QUAD12 = 1, UCN_MODEL_MARS7 = 2 } ucn_model;
+typedef enum { UCN_MODEL_QUAD12 = 1, UCN_MODEL_MARS7 = 2, UCN_MODEL_QUAT13 = 3 } ucn_model;
 typedef enum { UCN_PREC_FP64 = 0, UCN_PREC_FP32_REFINE = 1 } ucn_precision;
 
 /*
@@ -58,15 +58,19 @@ typedef enum { UCN_PREC_FP64 = 0, UCN_PREC_FP32_REFINE = 1 } ucn_precision;
  * x_0 = x_init, S x_N = x_target (S = term_mask), x_i in X_i, u_i in U_i.
  *
  *  model         UCN_MODEL_QUAD12 (nx=12: p, v, ZYX Euler angles, body rates;
- *                nu=4 rotor thrusts) or UCN_MODEL_MARS7 (nx=7: r Up-East-North,
- *                v, mass; nu=3 thrust vector; non-dimensional units)
+ *                nu=4 rotor thrusts), UCN_MODEL_QUAT13 (nx=13: p, v, unit
+ *                quaternion body-to-world scalar first, body rates; nu=4 total
+ *                thrust along body z and body torques; Sec. IV-A1) or
+ *                UCN_MODEL_MARS7 (nx=7: r Up-East-North, v, mass; nu=3 thrust
+ *                vector; non-dimensional units)
  *  horizon[b]    N_b >= 1;  dt[b] RK4 step
- *  model_params  [batch][8]: quad (m, Jx, Jy, Jz, arm, km, drag, g);
- *                Mars (g, alpha = mass flow per unit thrust, 0...)
+ *  model_params  [batch][8]: quadrotors (m, Jx, Jy, Jz, arm, km, drag, g; arm
+ *                and km unused by QUAT13); Mars (g, alpha = mass flow per unit
+ *                thrust, 0...)
  *  cost          l = 1/2 |x - x_ref|^2_Q + 1/2 |u - u_ref|^2_R (diagonal Q, R),
  *                phi = 1/2 |x_N - x_ref|^2_QN + qN^T x_N       [batch][nx|nu]
  *  boxes         x_lo/x_hi [batch][nx], u_lo/u_hi [batch][nu] (+-inf allowed)
- *  obstacles     quad only: n_obs[b] <= max_obs spheres obs_c [batch][max_obs][3],
+ *  obstacles     quadrotors only: n_obs[b] <= max_obs spheres obs_c [batch][max_obs][3],
  *                obs_r [batch][max_obs]; linearised about the nominal
  *  sets          Mars only [batch][4]: thrust_min (linearised |T| >= Tmin),
  *                thrust_max (ball |T| <= Tmax), tan of the glide-slope cone

@@ -48,10 +48,12 @@ int default_tpn(int model, int nodes) {
 }
 
 Layout make_layout(int model, int nodes, int max_obs, int tsize, bool reg_mats) {
-  const bool quad = model == UCN_MODEL_QUAD12;
-  const int NX = quad ? 12 : 7, NU = quad ? 4 : 3, NN = NX + NU;
-  const int fixed = quad ? Rec<Quad12>::END : Rec<Mars7>::END;     // fixed part of a node record
-  const int dfixed = quad ? Rec<Quad12>::DEND : Rec<Mars7>::DEND;
+  const bool quad = model_obstacles(model);
+  const int NX = model_nx(model), NU = model_nu(model), NN = NX + NU;
+  const int fixed = model == UCN_MODEL_QUAD12 ? Rec<Quad12>::END                 // fixed part of a node record
+                    : (model == UCN_MODEL_QUAT13 ? Rec<Quat13>::END : Rec<Mars7>::END);
+  const int dfixed = model == UCN_MODEL_QUAD12 ? Rec<Quad12>::DEND
+                     : (model == UCN_MODEL_QUAT13 ? Rec<Quat13>::DEND : Rec<Mars7>::DEND);
   Layout L;
   std::memset(&L, 0, sizeof(L));
   const int mo = std::max(max_obs, 1);
@@ -175,8 +177,9 @@ ucn_status ucn_problem_create(const ucn_problem_desc* d, ucn_problem** out) {
   g_err[0] = 0;
   if (!d || !out) return fail(UCN_EINVAL, "null descriptor or output pointer");
   *out = nullptr;
-  if (d->model != UCN_MODEL_QUAD12 && d->model != UCN_MODEL_MARS7) return fail(UCN_EINVAL, "unknown model %d", d->model);
-  const int NX = d->model == UCN_MODEL_QUAD12 ? 12 : 7, NU = d->model == UCN_MODEL_QUAD12 ? 4 : 3;
+  if (!model_known(d->model)) return fail(UCN_EINVAL, "unknown model %d", d->model);
+  const int NX = model_nx(d->model), NU = model_nu(d->model);
+  const bool obst = model_obstacles(d->model);
   if (d->nx != NX || d->nu != NU) return fail(UCN_EINVAL, "model %d needs nx=%d nu=%d (got %d, %d)", d->model, NX, NU, d->nx, d->nu);
   if (d->batch < 1) return fail(UCN_EINVAL, "batch must be >= 1 (got %d)", d->batch);
   if (d->precision != UCN_PREC_FP64 && d->precision != UCN_PREC_FP32_REFINE) return fail(UCN_EINVAL, "unknown precision %d", d->precision);
@@ -185,7 +188,7 @@ ucn_status ucn_problem_create(const ucn_problem_desc* d, ucn_problem** out) {
       !d->QN_diag || !d->qN || !d->x_lo || !d->x_hi || !d->u_lo || !d->u_hi || !d->x_init || !d->x_target ||
       !d->term_mask)
     return fail(UCN_EINVAL, "a required descriptor array is NULL");
-  if (d->model == UCN_MODEL_QUAD12 && d->max_obs > 0 && (!d->n_obs || !d->obs_c || !d->obs_r))
+  if (obst && d->max_obs > 0 && (!d->n_obs || !d->obs_c || !d->obs_r))
     return fail(UCN_EINVAL, "obstacle arrays are NULL with max_obs > 0");
   if (d->model == UCN_MODEL_MARS7 && !d->sets) return fail(UCN_EINVAL, "Mars problems need the sets array");
   if (d->max_obs < 0 || d->max_obs > 64) return fail(UCN_EINVAL, "max_obs must be in [0, 64]");
@@ -201,20 +204,20 @@ ucn_status ucn_problem_create(const ucn_problem_desc* d, ucn_problem** out) {
     const int N = d->horizon[b];
     if (N < 1 || N + 1 > MAX_THREADS) return fail(UCN_EINVAL, "horizon[%d] = %d outside [1, %d]", b, N, MAX_THREADS - 1);
     if (!(d->dt[b] > 0)) return fail(UCN_EINVAL, "dt[%d] must be positive", b);
-    if (d->model == UCN_MODEL_QUAD12 && d->max_obs > 0 && (d->n_obs[b] < 0 || d->n_obs[b] > d->max_obs))
+    if (obst && d->max_obs > 0 && (d->n_obs[b] < 0 || d->n_obs[b] > d->max_obs))
       return fail(UCN_EINVAL, "n_obs[%d] = %d outside [0, max_obs]", b, d->n_obs[b]);
     Nmax = std::max(Nmax, N);
   }
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return fail(UCN_ECUDA, "no CUDA device"); }
   ucn_problem* p = new ucn_problem();
-  p->model = d->model; p->nx = NX; p->nu = NU; p->batch = d->batch; p->max_obs = d->model == UCN_MODEL_QUAD12 ? d->max_obs : 0;
+  p->model = d->model; p->nx = NX; p->nu = NU; p->batch = d->batch; p->max_obs = obst ? d->max_obs : 0;
   p->Nmax = Nmax; p->precision = d->precision; p->group = group;
   p->tpn = default_tpn(d->model, Nmax + 1);
   const int B = d->batch;
   std::vector<long long> xoff(B), uoff(B), soff(B);
   std::vector<int> node_inst;
-  const int mb = d->model == UCN_MODEL_QUAD12 ? p->max_obs : 3;
+  const int mb = obst ? p->max_obs : 3;
   long long tx = 0, tu = 0, ts = 0;
   for (int b = 0; b < B; ++b) {
     const long long N = d->horizon[b];
@@ -263,7 +266,7 @@ ucn_status ucn_problem_create(const ucn_problem_desc* d, ucn_problem** out) {
   {
     std::vector<double> w(B);
     for (int b = 0; b < B; ++b)
-      w[b] = (d->horizon[b] + 1.0) * (1.0 + ((d->model == UCN_MODEL_QUAD12 && d->max_obs > 0) ? d->n_obs[b] / 8.0 : 0.0));
+      w[b] = (d->horizon[b] + 1.0) * (1.0 + ((obst && d->max_obs > 0) ? d->n_obs[b] / 8.0 : 0.0));
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return w[x] > w[y]; });
   }
   int* ord = nullptr;
@@ -398,8 +401,7 @@ ucn_status ucn_linearize(ucn_problem* p, const double* xbar_d, const double* uba
                          double* d_d, void* stream) {
   g_err[0] = 0;
   if (!p || !xbar_d || !ubar_d || !A_d || !B_d || !d_d) return fail(UCN_EINVAL, "null argument");
-  auto fn = p->model == UCN_MODEL_QUAD12 ? (p->precision == UCN_PREC_FP64 ? quad64_linearize : quad32_linearize)
-                                         : (p->precision == UCN_PREC_FP64 ? mars64_linearize : mars32_linearize);
+  auto fn = launchers_for(p->model, p->precision).linearize;
   const cudaError_t e = fn(&p->dev, p->node_inst, p->total_u, xbar_d, ubar_d, A_d, B_d, d_d, as_stream(stream));
   if (e != cudaSuccess) return fail(UCN_ECUDA, "linearize launch: %s", cudaGetErrorString(e));
   return UCN_OK;
@@ -414,8 +416,7 @@ ucn_status ucn_admm_solve(ucn_problem* p, const double* xbar_d, const double* ub
   if (iters < 1) return fail(UCN_EINVAL, "iters must be >= 1");
   if (p->group > 1) return fail(UCN_EINVAL, "the scenario consensus runs inside ucn_scp_solve only");
   const LaunchCfg c = cfg_of(p, stream);
-  auto fn = p->model == UCN_MODEL_QUAD12 ? (p->precision == UCN_PREC_FP64 ? quad64_admm : quad32_admm)
-                                         : (p->precision == UCN_PREC_FP64 ? mars64_admm : mars32_admm);
+  auto fn = launchers_for(p->model, p->precision).admm;
   const cudaError_t e = fn(c, xbar_d, ubar_d, A_d, B_d, d_d, radius_d, iters, warm ? 1 : 0, xhat_d, uhat_d, res_d, status_d);
   if (e != cudaSuccess) return fail(UCN_ECUDA, "admm launch: %s", cudaGetErrorString(e));
   return UCN_OK;
@@ -448,8 +449,7 @@ ucn_status ucn_scp_solve(ucn_problem* p, const double* x0_d, const double* u0_d,
     if (e != cudaSuccess) return fail(UCN_ECUDA, "scp group launch: %s", cudaGetErrorString(e));
     return UCN_OK;
   }
-  auto fn = p->model == UCN_MODEL_QUAD12 ? (p->precision == UCN_PREC_FP64 ? quad64_scp : quad32_scp)
-                                         : (p->precision == UCN_PREC_FP64 ? mars64_scp : mars32_scp);
+  auto fn = launchers_for(p->model, p->precision).scp;
   const cudaError_t e = fn(c, x0_d, u0_d, x_out_d, u_out_d, stats_d, status_d);
   if (e != cudaSuccess) return fail(UCN_ECUDA, "scp launch: %s", cudaGetErrorString(e));
   return UCN_OK;
@@ -462,6 +462,7 @@ ucn_status ucn_mpc_shift(ucn_problem* p, const double* x_d, const double* u_d, d
   if ((const double*)xg_d == x_d || (const double*)ug_d == u_d) return fail(UCN_EINVAL, "the shifted guesses may not alias the solution");
   const cudaStream_t st = as_stream(stream);
   if (p->model == UCN_MODEL_QUAD12) mpc_shift_kernel<Quad12><<<p->batch, 64, 0, st>>>(p->dev, x_d, u_d, xg_d, ug_d);
+  else if (p->model == UCN_MODEL_QUAT13) mpc_shift_kernel<Quat13><<<p->batch, 64, 0, st>>>(p->dev, x_d, u_d, xg_d, ug_d);
   else mpc_shift_kernel<Mars7><<<p->batch, 64, 0, st>>>(p->dev, x_d, u_d, xg_d, ug_d);
   const int nx = p->nx;
   mpc_set_init_kernel<<<(p->batch * nx + 127) / 128, 128, 0, st>>>(p->dev, const_cast<double*>(p->dev.xinit), xg_d);

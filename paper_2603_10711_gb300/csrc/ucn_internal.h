@@ -48,6 +48,31 @@ UCN_DECLARE_LAUNCHERS(quad64)
 UCN_DECLARE_LAUNCHERS(quad32)
 UCN_DECLARE_LAUNCHERS(mars64)
 UCN_DECLARE_LAUNCHERS(mars32)
+UCN_DECLARE_LAUNCHERS(quat64)
+UCN_DECLARE_LAUNCHERS(quat32)
+
+// Model properties used by the host code.
+inline bool model_known(int m) { return m == UCN_MODEL_QUAD12 || m == UCN_MODEL_MARS7 || m == UCN_MODEL_QUAT13; }
+inline int model_nx(int m) { return m == UCN_MODEL_QUAD12 ? 12 : (m == UCN_MODEL_QUAT13 ? 13 : 7); }
+inline int model_nu(int m) { return m == UCN_MODEL_MARS7 ? 3 : 4; }
+inline bool model_obstacles(int m) { return m != UCN_MODEL_MARS7; }   // quadrotors: obstacle mirrors
+
+// The launchers of one model and precision.
+struct Launchers {
+  cudaError_t (*scp)(const LaunchCfg&, const double*, const double*, double*, double*, ucn_scp_stats*, int*);
+  cudaError_t (*admm)(const LaunchCfg&, const double*, const double*, const double*, const double*, const double*,
+                      const double*, int, int, double*, double*, double*, int*);
+  cudaError_t (*linearize)(const void*, const int*, long long, const double*, const double*, double*, double*,
+                           double*, cudaStream_t);
+};
+inline Launchers launchers_for(int model, int precision) {
+  const bool f64 = precision == UCN_PREC_FP64;
+  if (model == UCN_MODEL_QUAD12) return f64 ? Launchers{quad64_scp, quad64_admm, quad64_linearize}
+                                            : Launchers{quad32_scp, quad32_admm, quad32_linearize};
+  if (model == UCN_MODEL_QUAT13) return f64 ? Launchers{quat64_scp, quat64_admm, quat64_linearize}
+                                            : Launchers{quat32_scp, quat32_admm, quat32_linearize};
+  return f64 ? Launchers{mars64_scp, mars64_admm, mars64_linearize} : Launchers{mars32_scp, mars32_admm, mars32_linearize};
+}
 
 // Scenario groups (quadrotor only): thread-block clusters, one CTA per scenario.
 cudaError_t quad64_scp_group(const LaunchCfg& c, const double* x0, const double* u0, double* xo, double* uo,

@@ -89,7 +89,15 @@ struct Node {
   __device__ __forceinline__ double& dnb(int off, int k, int j) const { return AOS ? d[j * DS + off + k] : d[(long long)(off + k) * S + j]; }
 };
 
-template <class M> struct IsQuad { static constexpr bool value = std::is_same<M, Quad12>::value; };
+// Models whose mirror sets are the linearised obstacles (the quadrotors); the
+// others carry the Mars sets (thrust ball and lower bound, glide-slope cone).
+template <class M> struct IsQuad {
+  static constexpr bool value = std::is_same<M, Quad12>::value || std::is_same<M, Quat13>::value;
+};
+// Models the lane kernel serves (rows split evenly over 4 lanes).
+template <class M> struct LaneModel {
+  static constexpr bool value = IsQuad<M>::value && M::NX % 4 == 0 && M::NU % 4 == 0;
+};
 
 // Storage of a node's matrices A_i, B_i and the packed H_i^-1.  Small models
 // keep them in registers (every index below is a compile-time constant after

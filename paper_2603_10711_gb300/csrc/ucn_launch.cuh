@@ -42,7 +42,7 @@ cudaError_t launch_scpl_v(const LaunchCfg& c, const double* x0, const double* u0
 template <class M, class T, bool R>
 cudaError_t launch_scp_t(const LaunchCfg& c, const double* x0, const double* u0, double* xo, double* uo,
                          ucn_scp_stats* st, int* status) {
-  if constexpr (IsQuad<M>::value) {
+  if constexpr (LaneModel<M>::value) {
     if (c.tpn == 4)
       return c.smem ? launch_scpl_v<M, T, true, R>(c, x0, u0, xo, uo, st, status)
                     : launch_scpl_v<M, T, false, R>(c, x0, u0, xo, uo, st, status);

@@ -93,6 +93,40 @@ struct Quad12 {
   }
 };
 
+// Quadrotor, 13 states (position, velocity, quaternion body-to-world scalar
+// first, body rates); control = total thrust along the body z axis and three
+// body torques (Sec. IV-A1).  prm as Quad12 (arm and km unused).
+struct Quat13 {
+  static constexpr int NX = 13, NU = 4;
+  template <class S, class P>
+  __device__ static void f(const P* prm, const S* x, const S* u, S* xd) {
+    typedef typename BaseOf<S>::type R;
+    const R m = (R)prm[0], Jx = (R)prm[1], Jy = (R)prm[2], Jz = (R)prm[3];
+    const R cd = (R)prm[6], g = (R)prm[7];
+    const S qw = x[6], qx = x[7], qy = x[8], qz = x[9];
+    const S wx = x[10], wy = x[11], wz = x[12];
+    // body z axis in the world frame, R(q) e3 (quadratic form, exact for unit q)
+    const S a0 = R(2) * (qx * qz + qw * qy);
+    const S a1 = R(2) * (qy * qz - qw * qx);
+    const S a2 = qw * qw - qx * qx - qy * qy + qz * qz;
+    const S Tm = u[0] / m;
+    xd[0] = x[3];
+    xd[1] = x[4];
+    xd[2] = x[5];
+    xd[3] = a0 * Tm - (cd / m) * x[3];
+    xd[4] = a1 * Tm - (cd / m) * x[4];
+    xd[5] = a2 * Tm - g - (cd / m) * x[5];
+    // q' = q (x) (0, w) / 2
+    xd[6] = R(0.5) * (-(qx * wx) - qy * wy - qz * wz);
+    xd[7] = R(0.5) * (qw * wx + qy * wz - qz * wy);
+    xd[8] = R(0.5) * (qw * wy - qx * wz + qz * wx);
+    xd[9] = R(0.5) * (qw * wz + qx * wy - qy * wx);
+    xd[10] = (u[1] - (Jz - Jy) * wy * wz) / Jx;
+    xd[11] = (u[2] - (Jx - Jz) * wz * wx) / Jy;
+    xd[12] = (u[3] - (Jy - Jx) * wx * wy) / Jz;
+  }
+};
+
 // Mars powered descent, 7 states: position (Up-East-North), velocity, mass;
 // control = thrust vector.  prm: g (acting along -Up), alpha (mass flow per
 // unit thrust), non-dimensional units.

@@ -73,8 +73,9 @@ extern "C" ucn_status ucn_scp_solve_noalloc(const ucn_problem_desc* d, const dou
                                             int* status_d, void* stream) {
   set_error_message("");
   if (!d || !x0_d || !u0_d || !x_out_d || !u_out_d || !stats_d || !status_d) return nfail(UCN_EINVAL, "null argument");
-  if (d->model != UCN_MODEL_QUAD12 && d->model != UCN_MODEL_MARS7) return nfail(UCN_EINVAL, "unknown model %d", d->model);
-  const int NX = d->model == UCN_MODEL_QUAD12 ? 12 : 7, NU = d->model == UCN_MODEL_QUAD12 ? 4 : 3;
+  if (!model_known(d->model)) return nfail(UCN_EINVAL, "unknown model %d", d->model);
+  const int NX = model_nx(d->model), NU = model_nu(d->model);
+  const bool obst = model_obstacles(d->model);
   if (d->nx != NX || d->nu != NU) return nfail(UCN_EINVAL, "model %d needs nx=%d nu=%d", d->model, NX, NU);
   if (d->batch < 1) return nfail(UCN_EINVAL, "batch must be >= 1");
   if (d->precision != UCN_PREC_FP64 && d->precision != UCN_PREC_FP32_REFINE) return nfail(UCN_EINVAL, "unknown precision %d", d->precision);
@@ -83,9 +84,9 @@ extern "C" ucn_status ucn_scp_solve_noalloc(const ucn_problem_desc* d, const dou
   if (!d->horizon || !d->dt || !d->model_params || !d->Q_diag || !d->x_ref || !d->R_diag || !d->u_ref ||
       !d->QN_diag || !d->qN || !d->x_lo || !d->x_hi || !d->u_lo || !d->u_hi || !d->x_init || !d->x_target || !d->term_mask)
     return nfail(UCN_EINVAL, "a required descriptor array is NULL");
-  const int max_obs = d->model == UCN_MODEL_QUAD12 ? d->max_obs : 0;
+  const int max_obs = obst ? d->max_obs : 0;
   if (max_obs < 0 || max_obs > 64) return nfail(UCN_EINVAL, "max_obs must be in [0, 64]");
-  if (d->model == UCN_MODEL_QUAD12 && (!d->n_obs || (max_obs > 0 && (!d->obs_c || !d->obs_r))))
+  if (obst && (!d->n_obs || (max_obs > 0 && (!d->obs_c || !d->obs_r))))
     return nfail(UCN_EINVAL, "quadrotor problems need n_obs (and obs_c, obs_r when max_obs > 0)");
   if (d->model == UCN_MODEL_MARS7 && !d->sets) return nfail(UCN_EINVAL, "Mars problems need the sets array");
   if (!(d->rho_eq > 0 && d->rho_dyn > 0 && d->rho_geo > 0)) return nfail(UCN_EINVAL, "penalties must be positive");
@@ -95,7 +96,7 @@ extern "C" ucn_status ucn_scp_solve_noalloc(const ucn_problem_desc* d, const dou
   // index tables (host copy of the horizons -> offsets), then the exported state
   std::vector<int> N(B);
   std::vector<long long> xoff(B), uoff(B), soff(B);
-  const int mb = d->model == UCN_MODEL_QUAD12 ? max_obs : 3;
+  const int mb = obst ? max_obs : 3;
   long long tx = 0, tu = 0, ts = 0;
   int Nmax = 0;
   for (int b = 0; b < B; ++b) {
@@ -150,8 +151,7 @@ extern "C" ucn_status ucn_scp_solve_noalloc(const ucn_problem_desc* d, const dou
   c.P = &P; c.L = &L; c.smem = true; c.smem_bytes = L.bytes;
   c.threads = (int)((Nmax + 1 + 31) / 32 * 32); c.blocks = B; c.stream = st; c.group = 1;
   c.nodes = Nmax + 1; c.tpn = default_tpn(d->model, Nmax + 1);
-  auto fn = d->model == UCN_MODEL_QUAD12 ? (d->precision == UCN_PREC_FP64 ? quad64_scp : quad32_scp)
-                                         : (d->precision == UCN_PREC_FP64 ? mars64_scp : mars32_scp);
+  auto fn = launchers_for(d->model, d->precision).scp;
   e = fn(c, x0_d, u0_d, x_out_d, u_out_d, stats_d, status_d);
   if (e != cudaSuccess) return nfail(UCN_ECUDA, "scp launch: %s", cudaGetErrorString(e));
   return UCN_OK;

@@ -51,6 +51,7 @@ PROBLEMS = {
     "quad_path": lambda: W.quad_path(1, seed=0),
     "quad_uneven": lambda: W.quad_box(3, seed=5, N_range=(5, 17), obs_range=(2, 6)),
     "mars": lambda: W.mars_batch(3, seed=1, N=40),
+    "quat": lambda: W.quat_study(2, seed=5, N=30, tf=3.6),
 }
 
 
@@ -181,6 +182,21 @@ def test_scp_fp32_mars_reaches_defect_gate():
     prob = W.mars_batch(6, seed=1)
     st, sr = scp_compare(prob, ucn.UCN_PREC_FP32_REFINE, TOL32, check_defect=True)
     assert (st["defect"] <= 1e-5).all()
+
+
+def test_scp_fp64_quaternion_study_matches_oracle():
+    # the 13-state study task (N = 50, 3 spheres, rho 1 -> 1e3 over 20 SCP x 100 ADMM iterations);
+    # FP64 records of 17-row nodes exceed shared memory: global-memory workspace
+    scp_compare(W.quat_study(2, seed=5), ucn.UCN_PREC_FP64, TOL64)
+
+
+def test_scp_fp32_quaternion_study_matches_oracle():
+    scp_compare(W.quat_study(3, seed=6), ucn.UCN_PREC_FP32_REFINE, TOL32)
+
+
+def test_scp_fp32_quaternion_converges_to_the_defect_gate():
+    prob = W.quat_study(3, rho0=10.0, rho_final=1e3, scp_iters=80, admm_iters=250, settings=dict(stop=1, step_tol=1.0))
+    st, sr = scp_compare(prob, ucn.UCN_PREC_FP32_REFINE, 1e-3, check_defect=True)
 
 
 def test_scp_fp32_quad_matches_oracle():
