@@ -271,6 +271,7 @@ def run_ours(args, rank, world):
 
     serving_out = run_serving(args) if (args.serving_requests > 0 and world == 1) else None
     batching_out = run_batching(args) if (args.batching_batch > 0 and world == 1) else None
+    rho_out = run_rho_study(args) if (args.rho_study_batch > 0 and world == 1) else None
     scenario_out = run_scenarios(args) if (args.scenario_steps > 0 and world == 1) else None
 
     flops_ni = flops_per_node_iter(prob.nx, prob.nu, mars_mirror_flops())
@@ -311,6 +312,8 @@ def run_ours(args, rank, world):
         out["scenario_mpc"] = scenario_out
     if batching_out is not None:
         out["batching"] = batching_out
+    if rho_out is not None:
+        out["rho_study"] = rho_out
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         out["cpu_baseline"] = cpu_baseline(args)
     solver.close()
@@ -373,6 +376,30 @@ def run_batching(args):
                      "scp_iters_mean": float(st["scp_iters"].mean())}
         cs.close()
     return out
+
+
+def run_rho_study(args):
+    """The paper's penalty-schedule study (Sec. IV-A2) on the 13-state quaternion
+    quadrotor: all three penalties from 1 to rho_f geometrically over 20 SCP
+    iterations, rho_f in {1e3, 1e4, 1e5, 1e6}, 100 or 250 ADMM iterations per
+    SCP iteration; a batch of study tasks (obstacle placements drawn per
+    instance) solved in FP32 + refinement.  Reports the final defect and cost."""
+    import torch
+    from paper_2603_10711_gb300 import ucn
+    rows = []
+    for admm in (100, 250):
+        for rf in (1e3, 1e4, 1e5, 1e6):
+            prob = W.quat_study(args.rho_study_batch, seed=5, rho_final=rf, admm_iters=admm)
+            s = ucn.Solver(prob, precision=ucn.UCN_PREC_FP32_REFINE)
+            x0, u0 = s.tensor(prob.xguess), s.tensor(prob.uguess)
+            e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(); s.scp_solve(x0, u0); e1.record(); e1.synchronize()
+            st = s.stats_host()
+            s.close()
+            rows.append({"rho_final": rf, "admm_iters": admm, "defect_median": float(np.median(st["defect"])),
+                         "defect_max": float(st["defect"].max()), "cost_mean": float(st["cost"].mean()),
+                         "ms": e0.elapsed_time(e1)})
+    return {"workload": "quat_study_%d_N50" % args.rho_study_batch, "scp_iters": 20, "rho0": 1.0, "rows": rows}
 
 
 def run_scenarios(args):
@@ -488,11 +515,12 @@ def main():
     ap.add_argument("--serving-rate", type=float, default=2000.0, help="Poisson arrival rate of the serving stream")
     ap.add_argument("--serving-fp64-requests", type=int, default=16)
     ap.add_argument("--batching-batch", type=int, default=4096, help="uneven quadrotor batch (0: skip the section)")
+    ap.add_argument("--rho-study-batch", type=int, default=256, help="quaternion study tasks per setting (0: skip)")
     ap.add_argument("--scenario-problems", type=int, default=256)
     ap.add_argument("--scenario-count", type=int, default=64, help="scenarios per problem (group size)")
     ap.add_argument("--scenario-steps", type=int, default=3, help="receding-horizon steps (0: skip the section)")
     ap.add_argument("--scenario-fp64-problems", type=int, default=64)
-    ap.add_argument("--mode", default="full", choices=["full", "kernel", "scenario", "batching"],
+    ap.add_argument("--mode", default="full", choices=["full", "kernel", "scenario", "batching", "rho_study"],
                     help="kernel: time only the fused kernel (profiler captures)")
     ap.add_argument("--scp-iters", type=int, default=0, help="fixed SCP iteration count (0: the workload's cap + stop test)")
     ap.add_argument("--admm-iters", type=int, default=0, help="kernel mode: ADMM iterations per SCP iteration (0: the workload's)")
@@ -513,6 +541,8 @@ def main():
         out = run_scenarios(args)
     elif args.mode == "batching":
         out = run_batching(args)
+    elif args.mode == "rho_study":
+        out = run_rho_study(args)
     elif args.impl == "reference":
         out = run_reference(args, rank, world)
     else:
