@@ -50,6 +50,9 @@ typedef enum {
 } ucn_status;
 
 typedef enum { UCN_MODEL_QUAD12 = 1, UCN_MODEL_MARS7 = 2, UCN_MODEL_QUAT13 = 3 } ucn_model;
+
+/* Set parameters per instance in ucn_problem_desc.sets. */
+#define UCN_SET_PARAMS 8
 typedef enum { UCN_PREC_FP64 = 0, UCN_PREC_FP32_REFINE = 1 } ucn_precision;
 
 /*
@@ -72,7 +75,7 @@ typedef enum { UCN_PREC_FP64 = 0, UCN_PREC_FP32_REFINE = 1 } ucn_precision;
  *  boxes         x_lo/x_hi [batch][nx], u_lo/u_hi [batch][nu] (+-inf allowed)
  *  obstacles     quadrotors only: n_obs[b] <= max_obs spheres obs_c [batch][max_obs][3],
  *                obs_r [batch][max_obs]; linearised about the nominal
- *  sets          Mars only [batch][4]: thrust_min (linearised |T| >= Tmin),
+ *  sets          Mars only [batch][UCN_SET_PARAMS]: thrust_min (linearised |T| >= Tmin),
  *                thrust_max (ball |T| <= Tmax), tan of the glide-slope cone
  *                half-angle; a value <= 0 switches the set off
  *  rho_*         ADMM penalties of Eq. (3); rho_final > 0 selects the geometric
@@ -291,7 +294,7 @@ typedef struct {
 } ucn_serve_config;
 
 /* One solve request (host memory, copied at submit).  Arrays as one instance
- * of ucn_problem_desc (model_params [8], sets [4], obs_c [n_obs][3]).  The
+ * of ucn_problem_desc (model_params [8], sets [UCN_SET_PARAMS], obs_c [n_obs][3]).  The
  * initial guess is x_guess [(horizon+1)][nx], u_guess [horizon][nu]; if either
  * is NULL the guess is the kept trajectory of the finished request
  * `warm_ticket` (same horizon), copied on the device. */

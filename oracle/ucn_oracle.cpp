@@ -757,7 +757,7 @@ struct OrcProblem {
   const double* xlo; const double* xhi; const double* ulo; const double* uhi;
   const double* xinit; const double* xtarget; const unsigned char* tmask;
   int max_obs; const int* nobs; const double* obs_c; const double* obs_r;
-  const double* sets;     // [B][4]: thrust_min, thrust_max, tan(glide), unused
+  const double* sets;     // [B][8]: thrust_min, thrust_max, tan(glide), then model-specific
   double rho_eq, rho_dyn, rho_geo, rho_final;
   int scp_iters, admm_iters, stop;
   double tr_init, tr_min, tr_max, w_d, defect_tol, step_tol, vc_weight;
@@ -834,7 +834,7 @@ void build_qp(const OrcProblem& P, int b, const double* xbar, const double* ubar
         bl.p0 = bl.G[0] * c[0] + bl.G[1] * c[1] + bl.G[2] * c[2] + r;
       }
     } else {
-      const double* st = &P.sets[b * 4];
+      const double* st = &P.sets[b * 8];
       if (st[2] > 0.0) {  // glide-slope cone on the position (t = Up)
         Block& bl = nd.blk[0]; bl.kind = BLK_CONE; bl.p0 = st[2];
         for (int k = 0; k < 3; ++k) bl.G[k * n + k] = 1.0;

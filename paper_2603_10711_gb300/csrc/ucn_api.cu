@@ -235,7 +235,7 @@ ucn_status ucn_problem_create(const ucn_problem_desc* d, ucn_problem** out) {
   P.model = d->model; P.nx = NX; P.nu = NU; P.batch = B; P.max_obs = p->max_obs;
   std::vector<double> zeros_obs(1, 0.0);
   std::vector<int> zeros_nobs(B, 0);
-  std::vector<double> zeros_sets((size_t)B * 4, 0.0);
+  std::vector<double> zeros_sets((size_t)B * UCN_SET_PARAMS, 0.0);
 #define COPY(dst, src, n)                                                                  \
   if (s == UCN_OK) { s = dev_copy(p, na, fa, src, (size_t)(n), &dst); }
   int* Ndev = nullptr; long long *xo = nullptr, *uo = nullptr, *so = nullptr;
@@ -255,7 +255,7 @@ ucn_status ucn_problem_create(const ucn_problem_desc* d, ucn_problem** out) {
   } else {
     COPY(nobs, zeros_nobs.data(), B); COPY(oc, zeros_obs.data(), 1); COPY(orr, zeros_obs.data(), 1);
   }
-  COPY(sets, d->sets ? d->sets : zeros_sets.data(), (size_t)B * 4);
+  COPY(sets, d->sets ? d->sets : zeros_sets.data(), (size_t)B * UCN_SET_PARAMS);
   int* ni = nullptr;
   COPY(ni, node_inst.empty() ? zeros_nobs.data() : node_inst.data(), std::max<size_t>(node_inst.size(), 1));
   // default CTA order of the fused solve: largest estimated work first

@@ -157,9 +157,9 @@ template <class M, class T>
 __device__ __forceinline__ Inst<T> make_inst(const ProblemDev& P, int b) {
   Inst<T> I;
   I.nobs = IsQuad<M>::value ? P.nobs[b] : 0;
-  const double tmin = IsQuad<M>::value ? 0.0 : P.sets[b * 4 + 0];
-  const double tmax = IsQuad<M>::value ? 0.0 : P.sets[b * 4 + 1];
-  const double tau = IsQuad<M>::value ? 0.0 : P.sets[b * 4 + 2];
+  const double tmin = IsQuad<M>::value ? 0.0 : P.sets[b * UCN_SET_PARAMS + 0];
+  const double tmax = IsQuad<M>::value ? 0.0 : P.sets[b * UCN_SET_PARAMS + 1];
+  const double tau = IsQuad<M>::value ? 0.0 : P.sets[b * UCN_SET_PARAMS + 2];
   I.half = tmin > 0.0; I.ball = tmax > 0.0; I.cone = tau > 0.0;
   I.tau = (T)tau; I.tmax = (T)tmax;
   const double ca = 1.0 / sqrt(1.0 + tau * tau);
@@ -454,7 +454,7 @@ __device__ void node_setup(const Node<T, AOS>& nd, const Layout& L, const Proble
       nd.at(L.oMd, 0) = n0;
       nd.at(L.oMd, 1) = n1;
       nd.at(L.oMd, 2) = n2;
-      nd.at(L.oMd, 3) = (T)P.sets[b * 4 + 0] - (n0 * ut[0] + n1 * ut[1] + n2 * ut[2]);
+      nd.at(L.oMd, 3) = (T)P.sets[b * UCN_SET_PARAMS + 0] - (n0 * ut[0] + n1 * ut[1] + n2 * ut[2]);
     }
   }
 }
@@ -1036,11 +1036,11 @@ __device__ void node_export(const Node<T, AOS>& nd, const Layout& L, const Probl
       ni[3 * j] = (double)nd.at(L.oNus, j);
     }
   } else {
-    if (P.sets[b * 4 + 2] > 0.0)
+    if (P.sets[b * UCN_SET_PARAMS + 2] > 0.0)
       for (int k = 0; k < 3; ++k) { si[k] = (double)nd.at(L.oS, k) + nd.dat(Rec<M>::Xbar, k); ni[k] = (double)nd.at(L.oNus, k); }
-    if (i < N && P.sets[b * 4 + 1] > 0.0)
+    if (i < N && P.sets[b * UCN_SET_PARAMS + 1] > 0.0)
       for (int k = 0; k < 3; ++k) { si[3 + k] = (double)nd.at(L.oS, 3 + k) + nd.dat(Rec<M>::Ubar, k); ni[3 + k] = (double)nd.at(L.oNus, 3 + k); }
-    if (i < N && P.sets[b * 4 + 0] > 0.0) {
+    if (i < N && P.sets[b * UCN_SET_PARAMS + 0] > 0.0) {
       double np = 0.0;
       for (int k = 0; k < 3; ++k) np += (double)nd.at(L.oMd, k) * nd.dat(Rec<M>::Ubar, k);
       si[6] = (double)nd.at(L.oS, 6) + np;

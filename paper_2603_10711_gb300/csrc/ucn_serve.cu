@@ -168,14 +168,14 @@ ucn_status ucn_serve_create(const ucn_serve_config* c, ucn_server** out) {
   ok = ok && halloc(s, &s->hxlo, (size_t)S * NX) && halloc(s, &s->hxhi, (size_t)S * NX) && halloc(s, &s->hulo, (size_t)S * NU);
   ok = ok && halloc(s, &s->huhi, (size_t)S * NU) && halloc(s, &s->hxi, (size_t)S * NX) && halloc(s, &s->hxt, (size_t)S * NX);
   ok = ok && halloc(s, &s->htm, (size_t)S * NX) && halloc(s, &s->hoc, (size_t)S * MO * 3) && halloc(s, &s->hor, (size_t)S * MO);
-  ok = ok && halloc(s, &s->hsets, (size_t)S * 4) && halloc(s, &s->hxg, (size_t)S * Xn * NX) && halloc(s, &s->hug, (size_t)S * Un * NU);
+  ok = ok && halloc(s, &s->hsets, (size_t)S * UCN_SET_PARAMS) && halloc(s, &s->hxg, (size_t)S * Xn * NX) && halloc(s, &s->hug, (size_t)S * Un * NU);
   ok = ok && dalloc(s, &s->dN, S) && dalloc(s, &s->dnobs, S) && dalloc(s, &s->ddt, S) && dalloc(s, &s->dprm, (size_t)S * 8);
   ok = ok && dalloc(s, &s->dQd, (size_t)S * NX) && dalloc(s, &s->dxr, (size_t)S * NX) && dalloc(s, &s->dRd, (size_t)S * NU);
   ok = ok && dalloc(s, &s->dur, (size_t)S * NU) && dalloc(s, &s->dQNd, (size_t)S * NX) && dalloc(s, &s->dqN, (size_t)S * NX);
   ok = ok && dalloc(s, &s->dxlo, (size_t)S * NX) && dalloc(s, &s->dxhi, (size_t)S * NX) && dalloc(s, &s->dulo, (size_t)S * NU);
   ok = ok && dalloc(s, &s->duhi, (size_t)S * NU) && dalloc(s, &s->dxi, (size_t)S * NX) && dalloc(s, &s->dxt, (size_t)S * NX);
   ok = ok && dalloc(s, &s->dtm, (size_t)S * NX) && dalloc(s, &s->doc, (size_t)S * MO * 3) && dalloc(s, &s->dor, (size_t)S * MO);
-  ok = ok && dalloc(s, &s->dsets, (size_t)S * 4);
+  ok = ok && dalloc(s, &s->dsets, (size_t)S * UCN_SET_PARAMS);
   ok = ok && dalloc(s, &s->x0, (size_t)S * Xn * NX) && dalloc(s, &s->u0, (size_t)S * Un * NU);
   ok = ok && dalloc(s, &s->xo, (size_t)S * Xn * NX) && dalloc(s, &s->uo, (size_t)S * Un * NU);
   ok = ok && dalloc(s, &s->stats, (size_t)S) && dalloc(s, &s->status, (size_t)S);
@@ -261,8 +261,8 @@ ucn_status ucn_serve_submit(ucn_server* s, const ucn_request* r, unsigned long l
     std::memcpy(&s->hoc[(size_t)k * MO * 3], r->obs_c, (size_t)r->n_obs * 3 * 8);
     std::memcpy(&s->hor[(size_t)k * MO], r->obs_r, (size_t)r->n_obs * 8);
   }
-  if (r->sets) std::memcpy(&s->hsets[k * 4], r->sets, 4 * 8);
-  else std::memset(&s->hsets[k * 4], 0, 4 * 8);
+  if (r->sets) std::memcpy(&s->hsets[k * UCN_SET_PARAMS], r->sets, UCN_SET_PARAMS * 8);
+  else std::memset(&s->hsets[k * UCN_SET_PARAMS], 0, UCN_SET_PARAMS * 8);
   const long long Xn = s->Nmax + 1, Un = s->Nmax;
   if (ring < 0) {
     std::memcpy(&s->hxg[k * Xn * NX], r->x_guess, (size_t)(N + 1) * NX * 8);
@@ -302,7 +302,7 @@ ucn_status ucn_serve_pump(ucn_server* s, int* launched) {
   H2D(s->dQd, s->hQd, S * NX); H2D(s->dxr, s->hxr, S * NX); H2D(s->dRd, s->hRd, S * NU); H2D(s->dur, s->hur, S * NU);
   H2D(s->dQNd, s->hQNd, S * NX); H2D(s->dqN, s->hqN, S * NX); H2D(s->dxlo, s->hxlo, S * NX); H2D(s->dxhi, s->hxhi, S * NX);
   H2D(s->dulo, s->hulo, S * NU); H2D(s->duhi, s->huhi, S * NU); H2D(s->dxi, s->hxi, S * NX); H2D(s->dxt, s->hxt, S * NX);
-  H2D(s->dtm, s->htm, S * NX); H2D(s->doc, s->hoc, (size_t)S * MO * 3); H2D(s->dor, s->hor, (size_t)S * MO); H2D(s->dsets, s->hsets, S * 4);
+  H2D(s->dtm, s->htm, S * NX); H2D(s->doc, s->hoc, (size_t)S * MO * 3); H2D(s->dor, s->hor, (size_t)S * MO); H2D(s->dsets, s->hsets, S * UCN_SET_PARAMS);
   for (size_t j = 0; j < ready.size(); ++j) {
     const int k = ready[j], N = s->hN[k], ring = s->slot_warm_ring[k];
     if (ring >= 0) {

@@ -36,6 +36,7 @@ import numpy as np
 MODEL_QUAD12 = 1
 MODEL_MARS7 = 2
 MODEL_QUAT13 = 3
+SET_PARAMS = 8          # set parameters per instance (thrust bounds, cone tangents, ...)
 
 _M64 = np.uint64(0xFFFFFFFFFFFFFFFF)
 _GOLDEN = np.uint64(0x9E3779B97F4A7C15)
@@ -195,7 +196,7 @@ def _quad_common(B, N, dt, start, goal, obs_c, obs_r, nobs, settings, mass=None,
         xlo=np.full((B, nx), -np.inf), xhi=np.full((B, nx), np.inf),
         ulo=np.zeros((B, nu)), uhi=np.full((B, nu), QUAD_UMAX),
         xinit=xinit, xtarget=xtarget, tmask=tmask,
-        nobs=np.asarray(nobs, np.int32), obs_c=obs_c, obs_r=obs_r, sets=np.zeros((B, 4)),
+        nobs=np.asarray(nobs, np.int32), obs_c=obs_c, obs_r=obs_r, sets=np.zeros((B, SET_PARAMS)),
         xguess=np.concatenate(xs), uguess=np.concatenate(us), settings=st)
 
 
@@ -279,7 +280,7 @@ def quat_study(B=1, seed=5, N=50, tf=6.0, n_obs=3, rho0=1.0, rho_final=1e3, scp_
         ulo=np.tile([0.0, -QUAT_TAUMAX, -QUAT_TAUMAX, -QUAT_TAUMAX], (B, 1)),
         uhi=np.tile([QUAT_TMAX, QUAT_TAUMAX, QUAT_TAUMAX, QUAT_TAUMAX], (B, 1)),
         xinit=xinit, xtarget=xtarget, tmask=tmask,
-        nobs=np.full(B, n_obs, np.int32), obs_c=obs_c, obs_r=obs_r, sets=np.zeros((B, 4)),
+        nobs=np.full(B, n_obs, np.int32), obs_c=obs_c, obs_r=obs_r, sets=np.zeros((B, SET_PARAMS)),
         xguess=np.concatenate(xs), uguess=np.concatenate(us), settings=st)
 
 
@@ -353,7 +354,7 @@ def mars_batch(B=1024, seed=1, N=100, tf=60.0, settings=None) -> Problem:
     xtarget = np.zeros((B, nx))
     tmask = np.zeros((B, nx), np.uint8); tmask[:, 0:6] = 1
     tmin, tmax = MARS_TMIN / u["F"], MARS_TMAX / u["F"]
-    sets = np.zeros((B, 4)); sets[:, 0] = tmin; sets[:, 1] = tmax
+    sets = np.zeros((B, SET_PARAMS)); sets[:, 0] = tmin; sets[:, 1] = tmax
     sets[:, 2] = math.tan(math.radians(MARS_GLIDE_DEG))
     xlo = np.full((B, nx), -np.inf); xhi = np.full((B, nx), np.inf)
     xlo[:, 6] = MARS_DRY / u["M"]; xhi[:, 6] = m0
