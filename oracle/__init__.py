@@ -91,7 +91,7 @@ def _f64(a):
 
 
 def model_dims(model: int):
-    return {1: (12, 4), 2: (7, 3), 3: (13, 4)}[int(model)]
+    return {1: (12, 4), 2: (7, 3), 3: (13, 4), 4: (14, 3)}[int(model)]
 
 
 def f(model, params, x, u):
@@ -216,7 +216,7 @@ class _Pinned:
 
 
 def maxblk(prob):
-    return 3 if prob.model == 2 else prob.max_obs
+    return {2: 3, 4: 6}.get(int(prob.model), prob.max_obs)
 
 
 def problem_admm(prob, b, xbar, ubar, A, B, d, radius, iters, state=None):

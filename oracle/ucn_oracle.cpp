@@ -48,7 +48,7 @@
 
 namespace {
 
-enum { MODEL_QUAD12 = 1, MODEL_MARS7 = 2, MODEL_QUAT13 = 3 };
+enum { MODEL_QUAD12 = 1, MODEL_MARS7 = 2, MODEL_QUAT13 = 3, MODEL_MARS14 = 4 };
 enum { BLK_NONE = -1, BLK_HALF = 0, BLK_BALL = 1, BLK_CONE = 2 };
 enum { ST_OK = 0, ST_NUMERIC = 4, ST_NOTCONV = 5 };
 
@@ -136,13 +136,57 @@ void quat_f(const double* prm, const S* x, const S* u, S* xd) {
   xd[12] = (u[3] - (Jy - Jx) * wx * wy) / Jz;
 }
 
-int model_nx(int model) { return model == MODEL_QUAD12 ? 12 : (model == MODEL_QUAT13 ? 13 : 7); }
-int model_nu(int model) { return model == MODEL_MARS7 ? 3 : 4; }
+// Mars powered descent, 6-DOF, 14 states (Sec. IV-B1): mass m, position r
+// (Up-East-North), velocity v, quaternion q = (qw, qx, qy, qz) body-to-world
+// scalar first, body rates omega; u = thrust T in the body frame (body x is
+// the thrust axis).  params: alpha (mass flow per unit thrust), g (along -Up),
+// Jx, Jy, Jz (diagonal inertia), l (the thrust acts at -l e_x in the body).
+//   m' = -alpha |T|
+//   r' = v
+//   v' = C(q) T / m + (-g, 0, 0)
+//   q' = 1/2 q (x) (0, omega)
+//   omega' = J^-1 (r_T x T - omega x J omega),  r_T = (-l, 0, 0)
+// C(q) is the quadratic form of the rotation matrix (exact for unit q).
+template <class S>
+void quat_rot(const S* q, S C[3][3]) {
+  const S w = q[0], a = q[1], b = q[2], c = q[3];
+  C[0][0] = w * w + a * a - b * b - c * c; C[0][1] = 2.0 * (a * b - w * c); C[0][2] = 2.0 * (a * c + w * b);
+  C[1][0] = 2.0 * (a * b + w * c); C[1][1] = w * w - a * a + b * b - c * c; C[1][2] = 2.0 * (b * c - w * a);
+  C[2][0] = 2.0 * (a * c - w * b); C[2][1] = 2.0 * (b * c + w * a); C[2][2] = w * w - a * a - b * b + c * c;
+}
+
+template <class S>
+void mars6_f(const double* prm, const S* x, const S* u, S* xd) {
+  const double alpha = prm[0], g = prm[1], Jx = prm[2], Jy = prm[3], Jz = prm[4], l = prm[5];
+  const S m = x[0];
+  const S* q = &x[7];
+  const S wx = x[11], wy = x[12], wz = x[13];
+  S C[3][3];
+  quat_rot<S>(q, C);
+  const S Tn = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+  xd[0] = -alpha * Tn;
+  for (int k = 0; k < 3; ++k) xd[1 + k] = x[4 + k];
+  for (int k = 0; k < 3; ++k) xd[4 + k] = (C[k][0] * u[0] + C[k][1] * u[1] + C[k][2] * u[2]) / m;
+  xd[4] = xd[4] - g;
+  xd[7] = 0.5 * (-q[1] * wx - q[2] * wy - q[3] * wz);
+  xd[8] = 0.5 * (q[0] * wx + q[2] * wz - q[3] * wy);
+  xd[9] = 0.5 * (q[0] * wy - q[1] * wz + q[3] * wx);
+  xd[10] = 0.5 * (q[0] * wz + q[1] * wy - q[2] * wx);
+  xd[11] = (-(Jz - Jy) * wy * wz) / Jx;
+  xd[12] = (l * u[2] - (Jx - Jz) * wz * wx) / Jy;
+  xd[13] = (-l * u[1] - (Jy - Jx) * wx * wy) / Jz;
+}
+
+int model_nx(int model) {
+  return model == MODEL_QUAD12 ? 12 : (model == MODEL_QUAT13 ? 13 : (model == MODEL_MARS14 ? 14 : 7));
+}
+int model_nu(int model) { return (model == MODEL_MARS7 || model == MODEL_MARS14) ? 3 : 4; }
 
 template <class S>
 void f_eval(int model, const double* prm, const S* x, const S* u, S* xd) {
   if (model == MODEL_QUAD12) quad_f<S>(prm, x, u, xd);
   else if (model == MODEL_QUAT13) quat_f<S>(prm, x, u, xd);
+  else if (model == MODEL_MARS14) mars6_f<S>(prm, x, u, xd);
   else mars_f<S>(prm, x, u, xd);
 }
 
@@ -270,9 +314,55 @@ void quat_jac(const double* prm, const double* x, const double* u, double* fx, d
   fu[12 * nu + 3] = 1.0 / Jz;
 }
 
+void mars6_jac(const double* prm, const double* x, const double* u, double* fx, double* fu) {
+  const int nx = 14, nu = 3;
+  const double alpha = prm[0], Jx = prm[2], Jy = prm[3], Jz = prm[4], l = prm[5];
+  std::fill(fx, fx + nx * nx, 0.0);
+  std::fill(fu, fu + nx * nu, 0.0);
+  const double m = x[0];
+  const double qw = x[7], qa = x[8], qb = x[9], qc = x[10];
+  const double wx = x[11], wy = x[12], wz = x[13];
+  double C[3][3];
+  quat_rot<double>(&x[7], C);
+  // d C[k][j] / d (qw, qx, qy, qz)
+  const double dC[3][3][4] = {
+      {{2 * qw, 2 * qa, -2 * qb, -2 * qc}, {-2 * qc, 2 * qb, 2 * qa, -2 * qw}, {2 * qb, 2 * qc, 2 * qw, 2 * qa}},
+      {{2 * qc, 2 * qb, 2 * qa, 2 * qw}, {2 * qw, -2 * qa, 2 * qb, -2 * qc}, {-2 * qa, -2 * qw, 2 * qc, 2 * qb}},
+      {{-2 * qb, 2 * qc, -2 * qw, 2 * qa}, {2 * qa, 2 * qw, 2 * qc, 2 * qb}, {2 * qw, -2 * qa, -2 * qb, 2 * qc}}};
+  const double Tn = std::sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+  if (Tn > 0.0)
+    for (int j = 0; j < 3; ++j) fu[0 * nu + j] = -alpha * u[j] / Tn;
+  for (int k = 0; k < 3; ++k) fx[(1 + k) * nx + 4 + k] = 1.0;                 // r' = v
+  for (int k = 0; k < 3; ++k) {
+    const double CT = C[k][0] * u[0] + C[k][1] * u[1] + C[k][2] * u[2];
+    fx[(4 + k) * nx + 0] = -CT / (m * m);
+    for (int a = 0; a < 4; ++a) {
+      double acc = 0.0;
+      for (int j = 0; j < 3; ++j) acc += dC[k][j][a] * u[j];
+      fx[(4 + k) * nx + 7 + a] = acc / m;
+    }
+    for (int j = 0; j < 3; ++j) fu[(4 + k) * nu + j] = C[k][j] / m;
+  }
+  const double Om[4][4] = {{0.0, -wx, -wy, -wz}, {wx, 0.0, wz, -wy}, {wy, -wz, 0.0, wx}, {wz, wy, -wx, 0.0}};
+  const double Qm[4][3] = {{-qa, -qb, -qc}, {qw, -qc, qb}, {qc, qw, -qa}, {-qb, qa, qw}};
+  for (int r = 0; r < 4; ++r) {
+    for (int c = 0; c < 4; ++c) fx[(7 + r) * nx + 7 + c] = 0.5 * Om[r][c];
+    for (int c = 0; c < 3; ++c) fx[(7 + r) * nx + 11 + c] = 0.5 * Qm[r][c];
+  }
+  fx[11 * nx + 12] = -(Jz - Jy) * wz / Jx;
+  fx[11 * nx + 13] = -(Jz - Jy) * wy / Jx;
+  fx[12 * nx + 11] = -(Jx - Jz) * wz / Jy;
+  fx[12 * nx + 13] = -(Jx - Jz) * wx / Jy;
+  fx[13 * nx + 11] = -(Jy - Jx) * wy / Jz;
+  fx[13 * nx + 12] = -(Jy - Jx) * wx / Jz;
+  fu[12 * nu + 2] = l / Jy;
+  fu[13 * nu + 1] = -l / Jz;
+}
+
 void f_jac(int model, const double* prm, const double* x, const double* u, double* fx, double* fu) {
   if (model == MODEL_QUAD12) quad_jac(prm, x, u, fx, fu);
   else if (model == MODEL_QUAT13) quat_jac(prm, x, u, fx, fu);
+  else if (model == MODEL_MARS14) mars6_jac(prm, x, u, fx, fu);
   else mars_jac(prm, x, u, fx, fu);
 }
 
@@ -768,7 +858,9 @@ struct OrcProblem {
 
 namespace {
 
-int problem_maxblk(const OrcProblem& P) { return P.model == MODEL_MARS7 ? 3 : P.max_obs; }
+int problem_maxblk(const OrcProblem& P) {
+  return P.model == MODEL_MARS7 ? 3 : (P.model == MODEL_MARS14 ? 6 : P.max_obs);
+}
 
 // Build the QP of Eq. (2) at nominal (xbar, ubar) for instance b: exact
 // quadratic cost expansion, trust-region l_inf box of radius `radius`
@@ -818,7 +910,40 @@ void build_qp(const OrcProblem& P, int b, const double* xbar, const double* ubar
     const int n = term ? nx : n1;
     nd.blk.assign(qp.maxblk, Block());
     for (Block& bl : nd.blk) bl.G.assign(3 * n, 0.0);
-    if (P.model != MODEL_MARS7) {
+    if (P.model == MODEL_MARS14) {
+      const double* st = &P.sets[b * 8];
+      // [0] |T| >= T_min (linearised), [1] |T| <= T_max, [2] tan of the glide-slope
+      // half-angle from Up, [3] tan of the gimbal angle, [4] radius of (qy, qz)
+      // (sin of half the largest tilt), [5] largest body rate
+      if (st[2] > 0.0) {  // glide-slope cone on r (t = Up)
+        Block& bl = nd.blk[0]; bl.kind = BLK_CONE; bl.p0 = st[2];
+        for (int k = 0; k < 3; ++k) bl.G[k * n + 1 + k] = 1.0;
+      }
+      if (st[4] > 0.0) {  // tilt: |(qy, qz)| <= sin(theta_max / 2) (third row zero)
+        Block& bl = nd.blk[1]; bl.kind = BLK_BALL; bl.p0 = st[4];
+        bl.G[0 * n + 9] = 1.0; bl.G[1 * n + 10] = 1.0;
+      }
+      if (st[5] > 0.0) {  // |omega| <= omega_max
+        Block& bl = nd.blk[2]; bl.kind = BLK_BALL; bl.p0 = st[5];
+        for (int k = 0; k < 3; ++k) bl.G[k * n + 11 + k] = 1.0;
+      }
+      if (!term && st[1] > 0.0) {  // |T| <= T_max
+        Block& bl = nd.blk[3]; bl.kind = BLK_BALL; bl.p0 = st[1];
+        for (int k = 0; k < 3; ++k) bl.G[k * n + nx + k] = 1.0;
+      }
+      if (!term && st[0] > 0.0) {  // |T| >= T_min linearised at the nominal thrust
+        const double* ub = &ubar[i * nu];
+        double nv[3] = {ub[0], ub[1], ub[2]};
+        double nn = std::sqrt(nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2]);
+        if (nn < 1e-12) { nv[0] = 1; nv[1] = 0; nv[2] = 0; nn = 1; }
+        Block& bl = nd.blk[4]; bl.kind = BLK_HALF; bl.p0 = st[0];
+        for (int k = 0; k < 3; ++k) bl.G[nx + k] = nv[k] / nn;
+      }
+      if (!term && st[3] > 0.0) {  // gimbal: |(T_y, T_z)| <= tan(delta_max) T_x
+        Block& bl = nd.blk[5]; bl.kind = BLK_CONE; bl.p0 = st[3];
+        for (int k = 0; k < 3; ++k) bl.G[k * n + nx + k] = 1.0;
+      }
+    } else if (P.model != MODEL_MARS7) {
       // Obstacle j, linearised about the nominal position:
       // n = (p - c)/|p - c|, keep n^T p >= n^T c + r (tie-break n = e_z).
       const double* p = &xbar[i * nx];

@@ -16,6 +16,7 @@ import workloads as W
 QUAD = W.MODEL_QUAD12
 MARS = W.MODEL_MARS7
 QUAT = W.MODEL_QUAT13
+MARS6 = W.MODEL_MARS14
 
 
 def quad_params(m=1.0, J=(0.01, 0.01, 0.02), l=0.2, km=0.01, cd=0.0, g=9.81):
@@ -25,6 +26,10 @@ def quad_params(m=1.0, J=(0.01, 0.01, 0.02), l=0.2, km=0.01, cd=0.0, g=9.81):
 def mars_params():
     p = W.mars_batch(1)
     return p.params[0]
+
+
+def mars6_params():
+    return W.mars6_batch(1).params[0]
 
 
 def rollout(model, prm, h, x, u, steps):
@@ -199,6 +204,11 @@ def random_point(model, seed):
         x = np.concatenate([rng.uniform(-1, 1, 6), q, rng.uniform(-2, 2, 3)])
         u = np.concatenate([rng.uniform(3, 15, 1), rng.uniform(-0.5, 0.5, 3)])
         prm = quad_params(cd=0.15)
+    elif model == MARS6:
+        q = rng.normal(size=4); q /= np.linalg.norm(q)
+        x = np.concatenate([[rng.uniform(0.8, 2.0)], rng.uniform(-1, 2, 6), q, rng.uniform(-0.5, 0.5, 3)])
+        u = np.concatenate([rng.uniform(0.5, 2.5, 1), rng.uniform(-0.4, 0.4, 2)])
+        prm = mars6_params()
     else:
         x = np.concatenate([rng.uniform(0.5, 2, 3), rng.uniform(-0.5, 0.5, 3), [rng.uniform(0.8, 1.0)]])
         u = rng.uniform(-0.6, 0.9, 3)
@@ -206,7 +216,7 @@ def random_point(model, seed):
     return prm, x, u
 
 
-@pytest.mark.parametrize("model", [QUAD, MARS, QUAT])
+@pytest.mark.parametrize("model", [QUAD, MARS, QUAT, MARS6])
 @pytest.mark.parametrize("seed", range(5))
 def test_jacobians_match_complex_step(model, seed):
     prm, x, u = random_point(model, seed)
@@ -220,7 +230,7 @@ def test_jacobians_match_complex_step(model, seed):
     np.testing.assert_allclose(xn, oracle.rk4(model, prm, h, x, u), atol=0)
 
 
-@pytest.mark.parametrize("model", [QUAD, MARS, QUAT])
+@pytest.mark.parametrize("model", [QUAD, MARS, QUAT, MARS6])
 def test_jacobians_match_central_differences(model):
     prm, x, u = random_point(model, 11)
     h = 0.05
@@ -302,3 +312,56 @@ def test_quat_spin_about_a_principal_axis_matches_closed_form():
     np.testing.assert_allclose(xt[10:13], [0, 0, wz], atol=1e-15)
     # hover thrust holds the body still up to the RK4 drift of |q| (thrust scales with |q|^2)
     np.testing.assert_allclose(xt[0:6], 0.0, atol=1e-8)
+
+
+# ------------------------------------------------------------------ 14-state 6-DOF Mars
+def rot_from_quat(q):
+    from scipy.spatial.transform import Rotation
+    return Rotation.from_quat([q[1], q[2], q[3], q[0]]).as_matrix()     # scipy: scalar last
+
+
+def test_mars6_translation_and_mass_match_the_3dof_model_under_the_attitude():
+    # with the body thrust rotated to the world frame by an independent rotation
+    # matrix, (m, r, v) evolve exactly as the 3-DOF model's (r, v, m)
+    rng = np.random.default_rng(4)
+    p6, p3 = mars6_params(), mars_params().copy()
+    p3[0], p3[1] = p6[1], p6[0]                      # same g and alpha
+    for _ in range(5):
+        q = rng.normal(size=4); q /= np.linalg.norm(q)
+        m = rng.uniform(0.8, 2.0)
+        r, v, w = rng.uniform(-1, 2, 3), rng.uniform(-1, 1, 3), rng.uniform(-0.5, 0.5, 3)
+        TB = np.array([rng.uniform(0.5, 2.5), rng.uniform(-0.4, 0.4), rng.uniform(-0.4, 0.4)])
+        d6 = oracle.f(MARS6, p6, np.concatenate([[m], r, v, q, w]), TB)
+        d3 = oracle.f(MARS, p3, np.concatenate([r, v, [m]]), rot_from_quat(q) @ TB)
+        np.testing.assert_allclose(d6[1:7], d3[0:6], atol=1e-14)
+        np.testing.assert_allclose(d6[0], d3[6], atol=1e-15)
+
+
+def test_mars6_attitude_and_rate_dynamics():
+    rng = np.random.default_rng(8)
+    prm = mars6_params()
+    J = np.diag(prm[2:5]); l = prm[5]
+    for _ in range(5):
+        q = rng.normal(size=4); q /= np.linalg.norm(q)
+        w = rng.uniform(-0.5, 0.5, 3)
+        TB = rng.uniform(-1, 2, 3)
+        d = oracle.f(MARS6, prm, np.concatenate([[1.5], np.zeros(6), q, w]), TB)
+        np.testing.assert_allclose(d[7:11], 0.5 * quat_mul(q, np.concatenate([[0.0], w])), atol=1e-15)
+        wd = np.linalg.solve(J, np.cross([-l, 0, 0], TB) - np.cross(w, J @ w))
+        np.testing.assert_allclose(d[11:14], wd, atol=1e-13)
+
+
+def test_mars6_free_fall_and_upright_burn_closed_forms():
+    prm = mars6_params()
+    x = np.concatenate([[1.5, 2.0, 0.3, -0.2, -0.5, 0.1, 0.0], [1, 0, 0, 0], [0, 0, 0]])
+    xt = rollout(MARS6, prm, 0.1, x, np.zeros(3), 10)
+    np.testing.assert_allclose(xt[1:4], x[1:4] + x[4:7] + 0.5 * np.array([-prm[1], 0, 0]), atol=1e-13)
+    np.testing.assert_allclose(xt[[0] + list(range(7, 14))], x[[0] + list(range(7, 14))], atol=0)
+    # upright burn along the body (= world) x axis: the 3-DOF rocket equation
+    p3 = mars_params().copy(); p3[0], p3[1] = prm[1], prm[0]
+    T = np.array([2.2, 0, 0])
+    x3 = np.concatenate([x[1:7], [x[0]]])
+    a = rollout(MARS6, prm, 0.05, x, T, 20)
+    b = rollout(MARS, p3, 0.05, x3, T, 20)
+    np.testing.assert_allclose(a[1:7], b[0:6], atol=1e-14)
+    np.testing.assert_allclose(a[0], b[6], atol=1e-15)

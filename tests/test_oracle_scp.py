@@ -114,6 +114,25 @@ def test_quaternion_quadrotor_converges_and_respects_sets():
         assert np.abs(np.linalg.norm(xb[:, 6:10], axis=1) - 1.0).max() < 0.05
 
 
+def test_mars6_converges_and_respects_sets():
+    prob = W.mars6_batch(3, seed=7)
+    x, u, st, _ = oracle.scp_solve(prob)
+    tmin, tmax, tglide, tgimbal, rtilt, wmax = prob.sets[0, :6]
+    for b in range(3):
+        xb, ub = instance(prob, x, u, b)
+        assert st[b, 0] <= 1e-5 and st[b, 10] == 0
+        np.testing.assert_array_equal(xb[0], prob.xinit[b])
+        np.testing.assert_array_equal(xb[-1][1:7], prob.xtarget[b][1:7])          # touchdown
+        np.testing.assert_array_equal(xb[-1][9:11], 0.0)                          # upright
+        Tn = np.linalg.norm(ub, axis=1)
+        assert Tn.max() <= tmax + 1e-4 and Tn.min() >= tmin - 1e-4                 # thrust annulus
+        assert np.all(np.hypot(ub[:, 1], ub[:, 2]) <= tgimbal * ub[:, 0] + 1e-4)    # gimbal
+        assert np.all(np.hypot(xb[:, 2], xb[:, 3]) <= tglide * xb[:, 1] + 1e-4)     # glide slope
+        assert np.all(np.hypot(xb[:, 9], xb[:, 10]) <= rtilt + 1e-4)               # tilt
+        assert np.all(np.linalg.norm(xb[:, 11:14], axis=1) <= wmax + 1e-4)          # body rate
+        assert xb[:, 0].min() >= 0.75 and np.all(np.diff(xb[:, 0]) <= 1e-5)         # mass
+
+
 def test_fixed_count_solve_runs_every_iteration():
     prob = W.quad_path(1, seed=0)
     _, _, st, log = oracle.scp_solve(prob, log=True)

@@ -36,6 +36,7 @@ import numpy as np
 MODEL_QUAD12 = 1
 MODEL_MARS7 = 2
 MODEL_QUAT13 = 3
+MODEL_MARS14 = 4
 SET_PARAMS = 8          # set parameters per instance (thrust bounds, cone tangents, ...)
 
 _M64 = np.uint64(0xFFFFFFFFFFFFFFFF)
@@ -481,3 +482,66 @@ def scenario_mpc(P=256, K=16, seed=3, N=40, n_obs=8, dt=0.05, settings=None) -> 
     st.update(settings or {})
     prob.settings = st
     return prob
+
+
+# ---------------------------------------------------------------- Mars 6-DOF
+MARS6_ALPHA, MARS6_G = 0.1, 1.0                  # non-dimensional
+MARS6_J = (0.0168, 0.168, 0.168)                 # diagonal inertia (not given; proposed)
+MARS6_LEVER = 1.0                                # thrust applied at -l e_x in the body (proposed)
+
+
+def mars6_batch(B=1000, seed=7, N=30, tf=5.0, settings=None) -> Problem:
+    """The paper's 6-DOF Mars landing (Sec. IV-B1) as a Monte-Carlo batch
+    (Sec. IV-B2), non-dimensional units: state (m, r Up-East-North, v, q, omega),
+    control = body-frame thrust; m' = -0.1 |T|, g = 1 along -Up; mass in
+    [0.75, 2.0]; |T| in [0.5, 3.0]; gimbal <= 10 deg from the body x axis; glide
+    slope 10 deg above the horizon; tilt <= 20 deg from Up; |omega| <= 30 deg per
+    unit time; horizon 5.0 in N = 30 steps.  Nominal start m = 2, r = (2, 1, 0),
+    v = (-1, 0.2, 0), upright, at rest; every component perturbed by U[-0.05,
+    0.05] (mass downward only; quaternion renormalised); touchdown at r = 0 with
+    v = (-0.1, 0, 0) and the body upright (roll about the thrust axis free);
+    cost = -m_N (fuel).
+    """
+    nx, nu = 14, 3
+    x0n = np.array([2.0, 2.0, 1.0, 0.0, -1.0, 0.2, 0.0, 1.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0])
+    pert = np.stack([U(seed, 70 + k, np.arange(B), -0.05, 0.05) for k in range(nx)], axis=1)
+    pert[:, 0] = -np.abs(pert[:, 0])
+    xinit = x0n[None, :] + pert
+    xinit[:, 7:11] /= np.linalg.norm(xinit[:, 7:11], axis=1, keepdims=True)
+    xtarget = np.zeros((B, nx)); xtarget[:, 4] = -0.1; xtarget[:, 7] = 1.0
+    # touchdown: position, velocity and an upright body (qy = qz = 0); the roll
+    # about the thrust axis and the rates stay free (no torque acts about that axis)
+    tmask = np.zeros((B, nx), np.uint8); tmask[:, 1:7] = 1; tmask[:, 9:11] = 1
+    params = np.zeros((B, 8))
+    params[:, 0] = MARS6_ALPHA; params[:, 1] = MARS6_G; params[:, 2:5] = MARS6_J; params[:, 5] = MARS6_LEVER
+    sets = np.zeros((B, SET_PARAMS))
+    sets[:, 0] = 0.5; sets[:, 1] = 3.0
+    sets[:, 2] = math.tan(math.radians(90.0 - 10.0))       # glide slope: 10 deg above the horizon
+    sets[:, 3] = math.tan(math.radians(10.0))              # gimbal
+    sets[:, 4] = math.sin(math.radians(20.0) / 2)          # tilt: |(qy, qz)| <= sin(theta / 2)
+    sets[:, 5] = math.radians(30.0)                        # body rate
+    xlo = np.full((B, nx), -np.inf); xhi = np.full((B, nx), np.inf)
+    xlo[:, 0] = 0.75; xhi[:, 0] = 2.0
+    qN = np.zeros((B, nx)); qN[:, 0] = -1.0
+    s_ = np.arange(N + 1)[:, None] / N
+    xs, us = [], []
+    for b in range(B):
+        xb = (1 - s_) * xinit[b] + s_ * xtarget[b]
+        xb[:, 0] = xinit[b, 0]
+        xb[:, 7:11] = np.array([1.0, 0, 0, 0]); xb[0, 7:11] = xinit[b, 7:11]
+        xb[:, 11:14] = 0.0; xb[0, 11:14] = xinit[b, 11:14]
+        xs.append(xb)
+        ub = np.zeros((N, nu)); ub[:, 0] = xinit[b, 0] * MARS6_G
+        us.append(ub)
+    st = dict(DEFAULT_SETTINGS)
+    st.update(dict(rho_eq=1.0, rho_dyn=1.0, rho_geo=1.0, rho_final=1e5, scp_iters=150, admm_iters=100, stop=1,
+                   step_tol=1.0))
+    st.update(settings or {})
+    return Problem(
+        model=MODEL_MARS14, nx=nx, nu=nu, N=np.full(B, N, np.int32), dt=np.full(B, tf / N), params=params,
+        Qd=np.zeros((B, nx)), xref=np.zeros((B, nx)), Rd=np.zeros((B, nu)), uref=np.zeros((B, nu)),
+        QNd=np.zeros((B, nx)), qN=qN, xlo=xlo, xhi=xhi,
+        ulo=np.full((B, nu), -np.inf), uhi=np.full((B, nu), np.inf),
+        xinit=xinit, xtarget=xtarget, tmask=tmask,
+        nobs=np.zeros(B, np.int32), obs_c=np.zeros((B, 0, 3)), obs_r=np.zeros((B, 0)), sets=sets,
+        xguess=np.concatenate(xs), uguess=np.concatenate(us), settings=st)
