@@ -49,7 +49,7 @@ typedef enum {
   UCN_EBUSY = 7       /* serving: no free slot / ring full */
 } ucn_status;
 
-typedef enum { UCN_MODEL_QUAD12 = 1, UCN_MODEL_MARS7 = 2, UCN_MODEL_QUAT13 = 3 } ucn_model;
+typedef enum { UCN_MODEL_QUAD12 = 1, UCN_MODEL_MARS7 = 2, UCN_MODEL_QUAT13 = 3, UCN_MODEL_MARS14 = 4 } ucn_model;
 
 /* Set parameters per instance in ucn_problem_desc.sets. */
 #define UCN_SET_PARAMS 8

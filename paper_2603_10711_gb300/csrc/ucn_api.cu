@@ -51,15 +51,18 @@ Layout make_layout(int model, int nodes, int max_obs, int tsize, bool reg_mats) 
   const bool quad = model_obstacles(model);
   const int NX = model_nx(model), NU = model_nu(model), NN = NX + NU;
   const int fixed = model == UCN_MODEL_QUAD12 ? Rec<Quad12>::END                 // fixed part of a node record
-                    : (model == UCN_MODEL_QUAT13 ? Rec<Quat13>::END : Rec<Mars7>::END);
+                    : model == UCN_MODEL_QUAT13 ? Rec<Quat13>::END
+                    : model == UCN_MODEL_MARS14 ? Rec<Mars14>::END : Rec<Mars7>::END;
   const int dfixed = model == UCN_MODEL_QUAD12 ? Rec<Quad12>::DEND
-                     : (model == UCN_MODEL_QUAT13 ? Rec<Quat13>::DEND : Rec<Mars7>::DEND);
+                     : model == UCN_MODEL_QUAT13 ? Rec<Quat13>::DEND
+                     : model == UCN_MODEL_MARS14 ? Rec<Mars14>::DEND : Rec<Mars7>::DEND;
   Layout L;
   std::memset(&L, 0, sizeof(L));
   const int mo = std::max(max_obs, 1);
-  L.MS = quad ? mo : 7;
-  L.MD = quad ? 4 * mo : 10;   // Mars: nbar, bound, nominal position, nominal thrust
-  L.MB = quad ? max_obs : 3;
+  const bool m14 = model == UCN_MODEL_MARS14;
+  L.MS = quad ? mo : (m14 ? M14::MS : 7);
+  L.MD = quad ? 4 * mo : (m14 ? M14::MD : 10);   // Mars: nbar, bound, nominal position, thrust (+ qyz, rates)
+  L.MB = quad ? max_obs : (m14 ? 6 : 3);
   L.oS = fixed;
   L.oNus = fixed + L.MS;
   L.oMd = fixed + 2 * L.MS;
@@ -190,7 +193,7 @@ ucn_status ucn_problem_create(const ucn_problem_desc* d, ucn_problem** out) {
     return fail(UCN_EINVAL, "a required descriptor array is NULL");
   if (obst && d->max_obs > 0 && (!d->n_obs || !d->obs_c || !d->obs_r))
     return fail(UCN_EINVAL, "obstacle arrays are NULL with max_obs > 0");
-  if (d->model == UCN_MODEL_MARS7 && !d->sets) return fail(UCN_EINVAL, "Mars problems need the sets array");
+  if (!obst && !d->sets) return fail(UCN_EINVAL, "Mars problems need the sets array");
   if (d->max_obs < 0 || d->max_obs > 64) return fail(UCN_EINVAL, "max_obs must be in [0, 64]");
   if (!(d->rho_eq > 0 && d->rho_dyn > 0 && d->rho_geo > 0)) return fail(UCN_EINVAL, "penalties must be positive");
   if (d->scp_iters < 1 || d->admm_iters < 1) return fail(UCN_EINVAL, "iteration counts must be >= 1");
@@ -217,7 +220,7 @@ ucn_status ucn_problem_create(const ucn_problem_desc* d, ucn_problem** out) {
   const int B = d->batch;
   std::vector<long long> xoff(B), uoff(B), soff(B);
   std::vector<int> node_inst;
-  const int mb = obst ? p->max_obs : 3;
+  const int mb = obst ? p->max_obs : (d->model == UCN_MODEL_MARS14 ? 6 : 3);
   long long tx = 0, tu = 0, ts = 0;
   for (int b = 0; b < B; ++b) {
     const long long N = d->horizon[b];
@@ -302,7 +305,7 @@ ucn_status ucn_problem_create(const ucn_problem_desc* d, ucn_problem** out) {
   // per-node storage: shared memory when one instance fits (small models then keep
   // their matrices in registers), else a structure-of-arrays slice of global memory
   const int tsize = d->precision == UCN_PREC_FP64 ? 8 : 4;
-  const bool small = d->model == UCN_MODEL_MARS7;   // SmallModel<Mars7>
+  const bool small = d->model == UCN_MODEL_MARS7;   // SmallModel<Mars7> (registers hold A, B, H^-1)
   int optin = 0;
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   const long long static_sh = (long long)sizeof(InstShared) + (group > 1 ? (long long)sizeof(GroupShared) : 0) + 64;
@@ -463,6 +466,7 @@ ucn_status ucn_mpc_shift(ucn_problem* p, const double* x_d, const double* u_d, d
   const cudaStream_t st = as_stream(stream);
   if (p->model == UCN_MODEL_QUAD12) mpc_shift_kernel<Quad12><<<p->batch, 64, 0, st>>>(p->dev, x_d, u_d, xg_d, ug_d);
   else if (p->model == UCN_MODEL_QUAT13) mpc_shift_kernel<Quat13><<<p->batch, 64, 0, st>>>(p->dev, x_d, u_d, xg_d, ug_d);
+  else if (p->model == UCN_MODEL_MARS14) mpc_shift_kernel<Mars14><<<p->batch, 64, 0, st>>>(p->dev, x_d, u_d, xg_d, ug_d);
   else mpc_shift_kernel<Mars7><<<p->batch, 64, 0, st>>>(p->dev, x_d, u_d, xg_d, ug_d);
   const int nx = p->nx;
   mpc_set_init_kernel<<<(p->batch * nx + 127) / 128, 128, 0, st>>>(p->dev, const_cast<double*>(p->dev.xinit), xg_d);

@@ -50,12 +50,19 @@ UCN_DECLARE_LAUNCHERS(mars64)
 UCN_DECLARE_LAUNCHERS(mars32)
 UCN_DECLARE_LAUNCHERS(quat64)
 UCN_DECLARE_LAUNCHERS(quat32)
+UCN_DECLARE_LAUNCHERS(m6dof64)
+UCN_DECLARE_LAUNCHERS(m6dof32)
 
 // Model properties used by the host code.
-inline bool model_known(int m) { return m == UCN_MODEL_QUAD12 || m == UCN_MODEL_MARS7 || m == UCN_MODEL_QUAT13; }
-inline int model_nx(int m) { return m == UCN_MODEL_QUAD12 ? 12 : (m == UCN_MODEL_QUAT13 ? 13 : 7); }
-inline int model_nu(int m) { return m == UCN_MODEL_MARS7 ? 3 : 4; }
-inline bool model_obstacles(int m) { return m != UCN_MODEL_MARS7; }   // quadrotors: obstacle mirrors
+inline bool model_known(int m) {
+  return m == UCN_MODEL_QUAD12 || m == UCN_MODEL_MARS7 || m == UCN_MODEL_QUAT13 || m == UCN_MODEL_MARS14;
+}
+inline int model_nx(int m) {
+  return m == UCN_MODEL_QUAD12 ? 12 : m == UCN_MODEL_QUAT13 ? 13 : m == UCN_MODEL_MARS14 ? 14 : 7;
+}
+inline int model_nu(int m) { return (m == UCN_MODEL_MARS7 || m == UCN_MODEL_MARS14) ? 3 : 4; }
+// quadrotors: obstacle mirrors; Mars models: their thrust / attitude / glide-slope sets
+inline bool model_obstacles(int m) { return m == UCN_MODEL_QUAD12 || m == UCN_MODEL_QUAT13; }
 
 // The launchers of one model and precision.
 struct Launchers {
@@ -71,6 +78,8 @@ inline Launchers launchers_for(int model, int precision) {
                                             : Launchers{quad32_scp, quad32_admm, quad32_linearize};
   if (model == UCN_MODEL_QUAT13) return f64 ? Launchers{quat64_scp, quat64_admm, quat64_linearize}
                                             : Launchers{quat32_scp, quat32_admm, quat32_linearize};
+  if (model == UCN_MODEL_MARS14) return f64 ? Launchers{m6dof64_scp, m6dof64_admm, m6dof64_linearize}
+                                            : Launchers{m6dof32_scp, m6dof32_admm, m6dof32_linearize};
   return f64 ? Launchers{mars64_scp, mars64_admm, mars64_linearize} : Launchers{mars32_scp, mars32_admm, mars32_linearize};
 }
 

@@ -94,6 +94,14 @@ struct Node {
 template <class M> struct IsQuad {
   static constexpr bool value = std::is_same<M, Quad12>::value || std::is_same<M, Quat13>::value;
 };
+// The 6-DOF Mars model: its own sets (glide slope on r, tilt on (qy, qz), body
+// rate ball, thrust ball and lower bound, gimbal cone on the body thrust).
+template <class M> struct IsMars14 { static constexpr bool value = std::is_same<M, Mars14>::value; };
+// Mirror slots of the 6-DOF model in the record (scalars s and nu_s; data).
+struct M14 {
+  static constexpr int S_CONE = 0, S_BALL = 3, S_HALF = 6, S_TILT = 7, S_W = 9, S_GIM = 12, MS = 15;
+  static constexpr int D_N = 0, D_BD = 3, D_R = 4, D_U = 7, D_Q = 10, D_W = 12, MD = 15;
+};
 // Models the lane kernel serves (rows split evenly over 4 lanes).
 template <class M> struct LaneModel {
   static constexpr bool value = IsQuad<M>::value && M::NX % 4 == 0 && M::NU % 4 == 0;
@@ -149,6 +157,8 @@ struct Inst {
   int nobs;                 // quadrotor: obstacles of this instance
   bool cone, ball, half;    // Mars: glide-slope cone, thrust ball, thrust lower bound
   T tau, tmax, ca, sa;      // cone tan(half-angle) and its cos/sin; thrust ball radius
+  bool gim, tilt, wball;    // Mars 6-DOF: gimbal cone, tilt ball, body-rate ball
+  T tg, cg, sg, rtilt, wmax;
   bool run_cost, term_quad; // nonzero running weights / terminal quadratic weights
   T prm[8];                 // model constants in T (Jacobian passes)
 };
@@ -164,6 +174,12 @@ __device__ __forceinline__ Inst<T> make_inst(const ProblemDev& P, int b) {
   I.tau = (T)tau; I.tmax = (T)tmax;
   const double ca = 1.0 / sqrt(1.0 + tau * tau);
   I.ca = (T)ca; I.sa = (T)(tau * ca);
+  const double tg = IsMars14<M>::value ? P.sets[b * UCN_SET_PARAMS + 3] : 0.0;
+  const double rt = IsMars14<M>::value ? P.sets[b * UCN_SET_PARAMS + 4] : 0.0;
+  const double wm = IsMars14<M>::value ? P.sets[b * UCN_SET_PARAMS + 5] : 0.0;
+  I.gim = tg > 0.0; I.tilt = rt > 0.0; I.wball = wm > 0.0;
+  const double cg = 1.0 / sqrt(1.0 + tg * tg);
+  I.tg = (T)tg; I.cg = (T)cg; I.sg = (T)(tg * cg); I.rtilt = (T)rt; I.wmax = (T)wm;
   bool rc = false, tq = false;
   for (int j = 0; j < M::NX; ++j) { rc = rc || P.Qd[b * M::NX + j] != 0.0; tq = tq || P.QNd[b * M::NX + j] != 0.0; }
   for (int j = 0; j < M::NU; ++j) rc = rc || P.Rd[b * M::NU + j] != 0.0;
@@ -441,8 +457,13 @@ __device__ void node_setup(const Node<T, AOS>& nd, const Layout& L, const Proble
     }
   } else {
     // nominal position / thrust in T, the offsets of the cone and ball projections
-    for (int k = 0; k < 3; ++k) nd.at(L.oMd, 4 + k) = (T)xb[k];
+    constexpr int RC = IsMars14<M>::value ? 1 : 0;   // position's first state
+    for (int k = 0; k < 3; ++k) nd.at(L.oMd, 4 + k) = (T)xb[RC + k];
     for (int k = 0; k < 3; ++k) nd.at(L.oMd, 7 + k) = (T)ub[k];
+    if constexpr (IsMars14<M>::value) {   // nominal (qy, qz) and body rates
+      for (int k = 0; k < 2; ++k) nd.at(L.oMd, M14::D_Q + k) = (T)xb[9 + k];
+      for (int k = 0; k < 3; ++k) nd.at(L.oMd, M14::D_W + k) = (T)xb[11 + k];
+    }
     // Thrust lower bound |T| >= Tmin linearised: nbar^T T >= Tmin, nbar = Tbar/|Tbar|.
     if (!term) {
       const T ut[3] = {(T)ub[0], (T)ub[1], (T)ub[2]};
@@ -495,7 +516,12 @@ __device__ __forceinline__ bool node_factor(const Node<T, AOS>& nd, const MS& MT
             h += rg * acc;
           }
         } else {
-          if (r < 3 && r == c && I.cone) h += rg;
+          constexpr int RC = IsMars14<M>::value ? 1 : 0;
+          if (r >= RC && r < RC + 3 && r == c && I.cone) h += rg;
+          if constexpr (IsMars14<M>::value) {
+            if (r == c && I.tilt && (r == 9 || r == 10)) h += rg;
+            if (r == c && I.wball && r >= 11 && r <= 13) h += rg;
+          }
         }
       } else if (c < NX) {  // H21 = H12^T (zero at node N: no control there)
         T acc = T(0);
@@ -513,6 +539,9 @@ __device__ __forceinline__ bool node_factor(const Node<T, AOS>& nd, const MS& MT
           if (rr < 3 && cc < 3 && !term) {
             if (rr == cc && I.ball) h += rg;
             if (I.half) h += rg * nd.at(L.oMd, rr) * nd.at(L.oMd, cc);
+            if constexpr (IsMars14<M>::value) {
+              if (rr == cc && I.gim) h += rg;
+            }
           }
         }
       }
@@ -625,9 +654,17 @@ __device__ __forceinline__ void apply_H(const Node<T, AOS>& nd, const MS& MT, co
       out[0] += n0 * y; out[1] += n1 * y; out[2] += n2 * y;
     }
   } else {
-    if (I.cone) { out[0] += rg * xi[0]; out[1] += rg * xi[1]; out[2] += rg * xi[2]; }
+    constexpr int RC = IsMars14<M>::value ? 1 : 0;
+    if (I.cone) { out[RC] += rg * xi[RC]; out[RC + 1] += rg * xi[RC + 1]; out[RC + 2] += rg * xi[RC + 2]; }
+    if constexpr (IsMars14<M>::value) {
+      if (I.tilt) { out[9] += rg * xi[9]; out[10] += rg * xi[10]; }
+      if (I.wball) { out[11] += rg * xi[11]; out[12] += rg * xi[12]; out[13] += rg * xi[13]; }
+    }
     if constexpr (n > NX) {
       if (I.ball) { out[NX] += rg * xi[NX]; out[NX + 1] += rg * xi[NX + 1]; out[NX + 2] += rg * xi[NX + 2]; }
+      if constexpr (IsMars14<M>::value) {
+        if (I.gim) { out[NX] += rg * xi[NX]; out[NX + 1] += rg * xi[NX + 1]; out[NX + 2] += rg * xi[NX + 2]; }
+      }
       if (I.half) {
         const T n0 = nd.at(L.oMd, 0), n1 = nd.at(L.oMd, 1), n2 = nd.at(L.oMd, 2);
         const T y = rg * (n0 * xi[NX] + n1 * xi[NX + 1] + n2 * xi[NX + 2]);
@@ -677,9 +714,20 @@ __device__ __forceinline__ void node_rhs(const Node<T, AOS>& nd, const MS& MT, c
       g[2] += nd.at(L.oMd, 4 * j + 2) * a;
     }
   } else {
+    constexpr int RC = IsMars14<M>::value ? 1 : 0;
     if (I.cone)
-      for (int k = 0; k < 3; ++k) g[k] += rg * nd.at(L.oS, k) - nd.at(L.oNus, k);
+      for (int k = 0; k < 3; ++k) g[RC + k] += rg * nd.at(L.oS, k) - nd.at(L.oNus, k);
+    if constexpr (IsMars14<M>::value) {
+      if (I.tilt)
+        for (int k = 0; k < 2; ++k) g[9 + k] += rg * nd.at(L.oS, M14::S_TILT + k) - nd.at(L.oNus, M14::S_TILT + k);
+      if (I.wball)
+        for (int k = 0; k < 3; ++k) g[11 + k] += rg * nd.at(L.oS, M14::S_W + k) - nd.at(L.oNus, M14::S_W + k);
+    }
     if constexpr (n > NX) {
+      if constexpr (IsMars14<M>::value) {
+        if (I.gim)
+          for (int k = 0; k < 3; ++k) g[NX + k] += rg * nd.at(L.oS, M14::S_GIM + k) - nd.at(L.oNus, M14::S_GIM + k);
+      }
       if (I.ball)
         for (int k = 0; k < 3; ++k) g[NX + k] += rg * nd.at(L.oS, 3 + k) - nd.at(L.oNus, 3 + k);
       if (I.half) {
@@ -719,17 +767,64 @@ __device__ __forceinline__ void node_mirrors(const Node<T, AOS>& nd, const Layou
     T xb[3], ub[3];
     for (int k = 0; k < 3; ++k) xb[k] = nd.at(L.oMd, 4 + k);
     for (int k = 0; k < 3; ++k) ub[k] = (n > NX) ? nd.at(L.oMd, 7 + k) : T(0);
+    constexpr int RC = IsMars14<M>::value ? 1 : 0;   // position's first state
     if (I.cone) {  // glide-slope cone on the position (t = Up)
       T v[3];
-      for (int k = 0; k < 3; ++k) v[k] = xb[k] + xi[k] + (reseed ? T(0) : nd.at(L.oNus, k) * irg);
+      for (int k = 0; k < 3; ++k) v[k] = xb[k] + xi[RC + k] + (reseed ? T(0) : nd.at(L.oNus, k) * irg);
       proj_cone3c(v, I.tau, I.ca, I.sa);
       for (int k = 0; k < 3; ++k) {
         const T s = v[k] - xb[k];
         if (reseed) { nd.at(L.oS, k) = s; continue; }
         const T so = nd.at(L.oS, k);
         nd.at(L.oS, k) = s;
-        nd.at(L.oNus, k) += rg * (xi[k] - s);
-        if (want_res) { sv[k] += rg * (s - so); rp += (double)(xi[k] - s) * (double)(xi[k] - s); }
+        nd.at(L.oNus, k) += rg * (xi[RC + k] - s);
+        if (want_res) { sv[RC + k] += rg * (s - so); rp += (double)(xi[RC + k] - s) * (double)(xi[RC + k] - s); }
+      }
+    }
+    if constexpr (IsMars14<M>::value) {
+      if (I.tilt) {  // |(qy, qz)| <= sin(theta_max / 2)
+        T v[3];
+        for (int k = 0; k < 2; ++k)
+          v[k] = nd.at(L.oMd, M14::D_Q + k) + xi[9 + k] + (reseed ? T(0) : nd.at(L.oNus, M14::S_TILT + k) * irg);
+        v[2] = T(0);
+        proj_ball3(v, I.rtilt);
+        for (int k = 0; k < 2; ++k) {
+          const T s = v[k] - nd.at(L.oMd, M14::D_Q + k);
+          if (reseed) { nd.at(L.oS, M14::S_TILT + k) = s; continue; }
+          const T so = nd.at(L.oS, M14::S_TILT + k);
+          nd.at(L.oS, M14::S_TILT + k) = s;
+          nd.at(L.oNus, M14::S_TILT + k) += rg * (xi[9 + k] - s);
+          if (want_res) { sv[9 + k] += rg * (s - so); rp += (double)(xi[9 + k] - s) * (double)(xi[9 + k] - s); }
+        }
+      }
+      if (I.wball) {  // |omega| <= omega_max
+        T v[3];
+        for (int k = 0; k < 3; ++k)
+          v[k] = nd.at(L.oMd, M14::D_W + k) + xi[11 + k] + (reseed ? T(0) : nd.at(L.oNus, M14::S_W + k) * irg);
+        proj_ball3(v, I.wmax);
+        for (int k = 0; k < 3; ++k) {
+          const T s = v[k] - nd.at(L.oMd, M14::D_W + k);
+          if (reseed) { nd.at(L.oS, M14::S_W + k) = s; continue; }
+          const T so = nd.at(L.oS, M14::S_W + k);
+          nd.at(L.oS, M14::S_W + k) = s;
+          nd.at(L.oNus, M14::S_W + k) += rg * (xi[11 + k] - s);
+          if (want_res) { sv[11 + k] += rg * (s - so); rp += (double)(xi[11 + k] - s) * (double)(xi[11 + k] - s); }
+        }
+      }
+      if constexpr (n > NX) {
+        if (I.gim) {  // gimbal: |(T_y, T_z)| <= tan(delta_max) T_x (t = body x)
+          T v[3];
+          for (int k = 0; k < 3; ++k) v[k] = ub[k] + xi[NX + k] + (reseed ? T(0) : nd.at(L.oNus, M14::S_GIM + k) * irg);
+          proj_cone3c(v, I.tg, I.cg, I.sg);
+          for (int k = 0; k < 3; ++k) {
+            const T s = v[k] - ub[k];
+            if (reseed) { nd.at(L.oS, M14::S_GIM + k) = s; continue; }
+            const T so = nd.at(L.oS, M14::S_GIM + k);
+            nd.at(L.oS, M14::S_GIM + k) = s;
+            nd.at(L.oNus, M14::S_GIM + k) += rg * (xi[NX + k] - s);
+            if (want_res) { sv[NX + k] += rg * (s - so); rp += (double)(xi[NX + k] - s) * (double)(xi[NX + k] - s); }
+          }
+        }
       }
     }
     if constexpr (n > NX) {
@@ -1035,6 +1130,34 @@ __device__ void node_export(const Node<T, AOS>& nd, const Layout& L, const Probl
       si[3 * j] = (double)nd.at(L.oS, j) + np;
       ni[3 * j] = (double)nd.at(L.oNus, j);
     }
+  } else if constexpr (IsMars14<M>::value) {
+    // blocks as the problem's sets: glide cone, tilt, body rate, thrust ball, thrust lower bound, gimbal
+    const double* st = &P.sets[b * UCN_SET_PARAMS];
+    if (st[2] > 0.0)
+      for (int k = 0; k < 3; ++k) { si[k] = (double)nd.at(L.oS, k) + nd.dat(Rec<M>::Xbar, 1 + k); ni[k] = (double)nd.at(L.oNus, k); }
+    if (st[4] > 0.0)
+      for (int k = 0; k < 2; ++k) {
+        si[3 + k] = (double)nd.at(L.oS, M14::S_TILT + k) + nd.dat(Rec<M>::Xbar, 9 + k);
+        ni[3 + k] = (double)nd.at(L.oNus, M14::S_TILT + k);
+      }
+    if (st[5] > 0.0)
+      for (int k = 0; k < 3; ++k) {
+        si[6 + k] = (double)nd.at(L.oS, M14::S_W + k) + nd.dat(Rec<M>::Xbar, 11 + k);
+        ni[6 + k] = (double)nd.at(L.oNus, M14::S_W + k);
+      }
+    if (i < N && st[1] > 0.0)
+      for (int k = 0; k < 3; ++k) { si[9 + k] = (double)nd.at(L.oS, 3 + k) + nd.dat(Rec<M>::Ubar, k); ni[9 + k] = (double)nd.at(L.oNus, 3 + k); }
+    if (i < N && st[0] > 0.0) {
+      double np = 0.0;
+      for (int k = 0; k < 3; ++k) np += (double)nd.at(L.oMd, k) * nd.dat(Rec<M>::Ubar, k);
+      si[12] = (double)nd.at(L.oS, 6) + np;
+      ni[12] = (double)nd.at(L.oNus, 6);
+    }
+    if (i < N && st[3] > 0.0)
+      for (int k = 0; k < 3; ++k) {
+        si[15 + k] = (double)nd.at(L.oS, M14::S_GIM + k) + nd.dat(Rec<M>::Ubar, k);
+        ni[15 + k] = (double)nd.at(L.oNus, M14::S_GIM + k);
+      }
   } else {
     if (P.sets[b * UCN_SET_PARAMS + 2] > 0.0)
       for (int k = 0; k < 3; ++k) { si[k] = (double)nd.at(L.oS, k) + nd.dat(Rec<M>::Xbar, k); ni[k] = (double)nd.at(L.oNus, k); }
@@ -1085,6 +1208,28 @@ __device__ void node_import(const Node<T, AOS>& nd, const Layout& L, const Probl
       nd.at(L.oS, j) = (T)(si[3 * j] - np);
       nd.at(L.oNus, j) = (T)ni[3 * j];
     }
+  } else if constexpr (IsMars14<M>::value) {
+    // blocks as exported: glide cone, tilt, body rate, thrust ball, thrust lower bound, gimbal
+    for (int k = 0; k < 3; ++k) { nd.at(L.oS, k) = (T)(si[k] - nd.dat(Rec<M>::Xbar, 1 + k)); nd.at(L.oNus, k) = (T)ni[k]; }
+    for (int k = 0; k < 2; ++k) {
+      nd.at(L.oS, M14::S_TILT + k) = (T)(si[3 + k] - nd.dat(Rec<M>::Xbar, 9 + k));
+      nd.at(L.oNus, M14::S_TILT + k) = (T)ni[3 + k];
+    }
+    for (int k = 0; k < 3; ++k) {
+      nd.at(L.oS, M14::S_W + k) = (T)(si[6 + k] - nd.dat(Rec<M>::Xbar, 11 + k));
+      nd.at(L.oNus, M14::S_W + k) = (T)ni[6 + k];
+    }
+    if (i < N) {
+      for (int k = 0; k < 3; ++k) { nd.at(L.oS, 3 + k) = (T)(si[9 + k] - nd.dat(Rec<M>::Ubar, k)); nd.at(L.oNus, 3 + k) = (T)ni[9 + k]; }
+      double np = 0.0;
+      for (int k = 0; k < 3; ++k) np += (double)nd.at(L.oMd, k) * nd.dat(Rec<M>::Ubar, k);
+      nd.at(L.oS, 6) = (T)(si[12] - np);
+      nd.at(L.oNus, 6) = (T)ni[12];
+      for (int k = 0; k < 3; ++k) {
+        nd.at(L.oS, M14::S_GIM + k) = (T)(si[15 + k] - nd.dat(Rec<M>::Ubar, k));
+        nd.at(L.oNus, M14::S_GIM + k) = (T)ni[15 + k];
+      }
+    }
   } else {
     for (int k = 0; k < 3; ++k) { nd.at(L.oS, k) = (T)(si[k] - nd.dat(Rec<M>::Xbar, k)); nd.at(L.oNus, k) = (T)ni[k]; }
     if (i < N) {
@@ -1108,11 +1253,18 @@ __device__ void node_rebase_mirrors(const Node<T, AOS>& nd, const Layout& L, con
       nd.at(L.oS, j) -= y;
     }
   } else {
-    for (int k = 0; k < 3; ++k) nd.at(L.oS, k) -= nd.at(Rec<M>::Xh, k);
+    constexpr int RC = IsMars14<M>::value ? 1 : 0;
+    for (int k = 0; k < 3; ++k) nd.at(L.oS, k) -= nd.at(Rec<M>::Xh, RC + k);
+    if constexpr (IsMars14<M>::value) {
+      for (int k = 0; k < 2; ++k) nd.at(L.oS, M14::S_TILT + k) -= nd.at(Rec<M>::Xh, 9 + k);
+      for (int k = 0; k < 3; ++k) nd.at(L.oS, M14::S_W + k) -= nd.at(Rec<M>::Xh, 11 + k);
+    }
     if (nd.i < nd.N) {
       T y = T(0);
       for (int k = 0; k < 3; ++k) { nd.at(L.oS, 3 + k) -= nd.at(Rec<M>::Uh, k); y += nd.at(L.oMd, k) * nd.at(Rec<M>::Uh, k); }
       nd.at(L.oS, 6) -= y;
+      if constexpr (IsMars14<M>::value)
+        for (int k = 0; k < 3; ++k) nd.at(L.oS, M14::S_GIM + k) -= nd.at(Rec<M>::Uh, k);
     }
   }
 }

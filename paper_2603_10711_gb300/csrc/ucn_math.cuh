@@ -148,6 +148,43 @@ struct Mars7 {
   }
 };
 
+// Mars powered descent, 6-DOF, 14 states (Sec. IV-B1): mass, position
+// (Up-East-North), velocity, quaternion body-to-world scalar first, body rates;
+// control = thrust in the body frame (body x = thrust axis).  prm: alpha (mass
+// flow per unit thrust), g (along -Up), Jx, Jy, Jz, l (the thrust acts at
+// -l e_x in the body).  Non-dimensional units.
+struct Mars14 {
+  static constexpr int NX = 14, NU = 3;
+  template <class S, class P>
+  __device__ static void f(const P* prm, const S* x, const S* u, S* xd) {
+    typedef typename BaseOf<S>::type R;
+    const R alpha = (R)prm[0], g = (R)prm[1], Jx = (R)prm[2], Jy = (R)prm[3], Jz = (R)prm[4], l = (R)prm[5];
+    const S qw = x[7], qx = x[8], qy = x[9], qz = x[10];
+    const S wx = x[11], wy = x[12], wz = x[13];
+    const S Tn = sqrt_(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    const S im = R(1) / x[0];
+    // rotation body -> world (quadratic form), applied to the body thrust
+    const S c00 = qw * qw + qx * qx - qy * qy - qz * qz, c01 = R(2) * (qx * qy - qw * qz), c02 = R(2) * (qx * qz + qw * qy);
+    const S c10 = R(2) * (qx * qy + qw * qz), c11 = qw * qw - qx * qx + qy * qy - qz * qz, c12 = R(2) * (qy * qz - qw * qx);
+    const S c20 = R(2) * (qx * qz - qw * qy), c21 = R(2) * (qy * qz + qw * qx), c22 = qw * qw - qx * qx - qy * qy + qz * qz;
+    xd[0] = -(alpha * Tn);
+    xd[1] = x[4];
+    xd[2] = x[5];
+    xd[3] = x[6];
+    xd[4] = (c00 * u[0] + c01 * u[1] + c02 * u[2]) * im - g;
+    xd[5] = (c10 * u[0] + c11 * u[1] + c12 * u[2]) * im;
+    xd[6] = (c20 * u[0] + c21 * u[1] + c22 * u[2]) * im;
+    xd[7] = R(0.5) * (-(qx * wx) - qy * wy - qz * wz);
+    xd[8] = R(0.5) * (qw * wx + qy * wz - qz * wy);
+    xd[9] = R(0.5) * (qw * wy - qx * wz + qz * wx);
+    xd[10] = R(0.5) * (qw * wz + qx * wy - qy * wx);
+    // J w' = r_T x T - w x (J w), r_T = (-l, 0, 0): r_T x T = (0, l T_z, -l T_y)
+    xd[11] = (-((Jz - Jy) * wy * wz)) / Jx;
+    xd[12] = (l * u[2] - (Jx - Jz) * wz * wx) / Jy;
+    xd[13] = (-(l * u[1]) - (Jy - Jx) * wx * wy) / Jz;
+  }
+};
+
 // Classical fourth-order Runge-Kutta step (Eq. (1b)).
 template <class M, class S, class P>
 __device__ __forceinline__ void rk4(const P* prm, double h_, const S* x, const S* u, S* xn) {

@@ -88,7 +88,7 @@ extern "C" ucn_status ucn_scp_solve_noalloc(const ucn_problem_desc* d, const dou
   if (max_obs < 0 || max_obs > 64) return nfail(UCN_EINVAL, "max_obs must be in [0, 64]");
   if (obst && (!d->n_obs || (max_obs > 0 && (!d->obs_c || !d->obs_r))))
     return nfail(UCN_EINVAL, "quadrotor problems need n_obs (and obs_c, obs_r when max_obs > 0)");
-  if (d->model == UCN_MODEL_MARS7 && !d->sets) return nfail(UCN_EINVAL, "Mars problems need the sets array");
+  if (!obst && !d->sets) return nfail(UCN_EINVAL, "Mars problems need the sets array");
   if (!(d->rho_eq > 0 && d->rho_dyn > 0 && d->rho_geo > 0)) return nfail(UCN_EINVAL, "penalties must be positive");
   if (d->scp_iters < 1 || d->admm_iters < 1) return nfail(UCN_EINVAL, "iteration counts must be >= 1");
   if (!(d->tr_init > 0 && d->tr_min > 0 && d->tr_max >= d->tr_min)) return nfail(UCN_EINVAL, "bad trust-region bounds");
@@ -96,7 +96,7 @@ extern "C" ucn_status ucn_scp_solve_noalloc(const ucn_problem_desc* d, const dou
   // index tables (host copy of the horizons -> offsets), then the exported state
   std::vector<int> N(B);
   std::vector<long long> xoff(B), uoff(B), soff(B);
-  const int mb = obst ? max_obs : 3;
+  const int mb = obst ? max_obs : (d->model == UCN_MODEL_MARS14 ? 6 : 3);
   long long tx = 0, tu = 0, ts = 0;
   int Nmax = 0;
   for (int b = 0; b < B; ++b) {

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libucn.so")
 
 UCN_OK, UCN_EINVAL, UCN_ENOMEM, UCN_ECUDA, UCN_ENUMERIC, UCN_ENOTCONV, UCN_ETIMEOUT, UCN_EBUSY = range(8)
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENUMERIC", 5: "ENOTCONV", 6: "ETIMEOUT", 7: "EBUSY"}
-UCN_MODEL_QUAD12, UCN_MODEL_MARS7, UCN_MODEL_QUAT13 = 1, 2, 3
+UCN_MODEL_QUAD12, UCN_MODEL_MARS7, UCN_MODEL_QUAT13, UCN_MODEL_MARS14 = 1, 2, 3, 4
 UCN_PREC_FP64, UCN_PREC_FP32_REFINE = 0, 1
 
 _dp = C.POINTER(C.c_double)

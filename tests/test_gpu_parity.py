@@ -52,6 +52,7 @@ PROBLEMS = {
     "quad_uneven": lambda: W.quad_box(3, seed=5, N_range=(5, 17), obs_range=(2, 6)),
     "mars": lambda: W.mars_batch(3, seed=1, N=40),
     "quat": lambda: W.quat_study(2, seed=5, N=30, tf=3.6),
+    "mars6": lambda: W.mars6_batch(2, seed=7, N=20, tf=3.4),
 }
 
 
@@ -197,6 +198,18 @@ def test_scp_fp32_quaternion_study_matches_oracle():
 def test_scp_fp32_quaternion_converges_to_the_defect_gate():
     prob = W.quat_study(3, rho0=10.0, rho_final=1e3, scp_iters=80, admm_iters=250, settings=dict(stop=1, step_tol=1.0))
     st, sr = scp_compare(prob, ucn.UCN_PREC_FP32_REFINE, 1e-3, check_defect=True)
+
+
+def test_scp_fp64_mars6_matches_oracle():
+    # the 6-DOF landing (glide slope, gimbal, tilt and body-rate sets), fixed 40 SCP iterations
+    prob = W.mars6_batch(3, seed=7, settings=dict(scp_iters=40, stop=0))
+    scp_compare(prob, ucn.UCN_PREC_FP64, TOL64)
+
+
+def test_scp_fp32_mars6_reaches_the_defect_gate():
+    prob = W.mars6_batch(6, seed=7)
+    st, sr = scp_compare(prob, ucn.UCN_PREC_FP32_REFINE, 1e-3, check_defect=True)
+    assert (st["defect"] <= 1e-5).mean() >= 0.8
 
 
 def test_scp_fp32_quad_matches_oracle():
