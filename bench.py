@@ -289,7 +289,8 @@ def run_ours(args, rank, world):
         "data": "synthetic (seeded Mars descent dispersions)",
         "config": {"workload": WORKLOAD, "instances_per_gpu": B, "horizon": 100, "nx": 7, "nu": 3,
                    "admm_iters_per_scp": int(prob.settings["admm_iters"]), "scp_iter_cap": int(prob.settings["scp_iters"]),
-                   "rho": "1 -> 1e5 geometric", "stop": "defect <= 1e-5", "l2": "flushed (256 MB write) before each step",
+                   "rho": "%g -> %g geometric" % (prob.settings["rho_geo"], prob.settings["rho_final"]),
+                   "stop": "defect <= 1e-5", "l2": "flushed (256 MB write) before each step",
                    "parallelism": "one CTA per instance, one thread per node; ranks hold independent batches"},
         "pass_rate": passed / (B * args.steps),
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),

@@ -85,7 +85,7 @@ def test_mars_converges_and_respects_sets():
     for b in range(3):
         xb, ub = instance(prob, x, u, b)
         assert st[b, 0] <= 1e-5 and st[b, 10] == 0
-        assert st[b, 7] < 150                                                 # stopped by the test
+        assert st[b, 7] < prob.settings["scp_iters"]                          # stopped by the test
         np.testing.assert_array_equal(xb[0], prob.xinit[b])
         np.testing.assert_array_equal(xb[-1][:6], 0.0)
         Tn = np.linalg.norm(ub, axis=1)

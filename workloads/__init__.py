@@ -372,11 +372,13 @@ def mars_batch(B=1024, seed=1, N=100, tf=60.0, settings=None) -> Problem:
         us.append(ub)
     st = dict(DEFAULT_SETTINGS)
     # Paper's geometric penalty schedule (Sec. IV-A: all three rho equal, raised
-    # geometrically over the SCP iterations), here 1 -> 1e5 over a 150-iteration
-    # cap with 100 ADMM iterations each; the solve stops once the defect of an
-    # accepted candidate is <= 1e-5 (the step test is switched off: step_tol = 1).
-    st.update(dict(rho_eq=1.0, rho_dyn=1.0, rho_geo=1.0, rho_final=1e5, scp_iters=150,
-                   admm_iters=100, stop=1, step_tol=1.0))
+    # geometrically over the SCP iterations), here 1 -> 1e7 over a 60-iteration
+    # cap with 40 ADMM iterations each (the least ADMM work of an oracle sweep at
+    # which every instance passes, with the fuel of 1 -> 1e5 over 150 x 100); the
+    # solve stops once the defect of an accepted candidate is <= 1e-5 (the step
+    # test is switched off: step_tol = 1).
+    st.update(dict(rho_eq=1.0, rho_dyn=1.0, rho_geo=1.0, rho_final=1e7, scp_iters=60,
+                   admm_iters=40, stop=1, step_tol=1.0))
     st.update(settings or {})
     return Problem(
         model=MODEL_MARS7, nx=nx, nu=nu, N=np.full(B, N, np.int32), dt=np.full(B, tf / N / u["T"]),
