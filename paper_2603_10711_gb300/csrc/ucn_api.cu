@@ -61,7 +61,7 @@ Layout make_layout(int model, int nodes, int max_obs, int tsize, bool reg_mats) 
   const int mo = std::max(max_obs, 1);
   const bool m14 = model == UCN_MODEL_MARS14;
   L.MS = quad ? mo : (m14 ? M14::MS : 7);
-  L.MD = quad ? 4 * mo : (m14 ? M14::MD : 10);   // Mars: nbar, bound, nominal position, thrust (+ qyz, rates)
+  L.MD = quad ? (tsize == 4 ? 5 : 4) * mo : (m14 ? M14::MD : 10);   // ObsStride; Mars: nbar, bound, position, thrust (+ qyz, rates)
   L.MB = quad ? max_obs : (m14 ? 6 : 3);
   L.oS = fixed;
   L.oNus = fixed + L.MS;
@@ -70,7 +70,8 @@ Layout make_layout(int model, int nodes, int max_obs, int tsize, bool reg_mats) 
   if (reg_mats) {
     L.oA = L.oB = L.oH = -1;
   } else {
-    L.oA = nt; L.oB = L.oA + NX * NX; L.oH = L.oB + NX * NU;
+    const bool pad = model == UCN_MODEL_QUAD12 && tsize == 4;   // MatStride: the FP32 lane layout
+    L.oA = nt; L.oB = L.oA + NX * (pad ? (NX | 1) : NX); L.oH = L.oB + NX * (pad ? (NU | 1) : NU);
     nt = L.oH + NN * (NN + 1) / 2;
   }
   L.S = nodes;
@@ -274,6 +275,12 @@ ucn_status ucn_problem_create(const ucn_problem_desc* d, ucn_problem** out) {
   }
   int* ord = nullptr;
   COPY(ord, order.data(), B);
+  // penalty factor of each SCP iteration, (rho_final / rho_geo)^(k / (K - 1)) (1 without a schedule)
+  std::vector<double> fac(d->scp_iters, 1.0);
+  if (d->rho_final > 0.0 && d->scp_iters > 1)
+    for (int k = 0; k < d->scp_iters; ++k) fac[k] = std::pow(d->rho_final / d->rho_geo, (double)k / (double)(d->scp_iters - 1));
+  double* facd = nullptr;
+  COPY(facd, fac.data(), fac.size());
   double* sabs = nullptr;
   COPY(sabs, (const double*)nullptr, (size_t)ts);
 #undef COPY
@@ -289,6 +296,7 @@ ucn_status ucn_problem_create(const ucn_problem_desc* d, ucn_problem** out) {
   P.timeout_ns = (unsigned long long)((d->timeout_s > 0 ? d->timeout_s : 60.0) * 1e9);
   P.state_abs = sabs;
   P.order = ord;
+  P.rho_fac = facd;
   P.group = group;
   // a group is gclusters thread-block clusters of gcsize CTAs: the largest
   // cluster size <= 16 that divides it

@@ -43,6 +43,7 @@ struct ProblemDev {
   char* ws;                // per-instance node storage when it does not fit in shared memory
   const int* order;        // CTA -> instance map of the fused solve (NULL: identity)
   int group;               // scenarios per group (<= 1: independent instances)
+  const double* rho_fac;   // penalty factor of each SCP iteration (NULL: computed in the kernel)
   int gclusters;           // thread-block clusters per group (group = gclusters x cluster size)
   double* gx;              // exchange slots of the scenarios [instance][2][16]
   unsigned* gflag;         // per instance: last exchange published (+1); zeroed per launch
@@ -111,20 +112,32 @@ template <class M> struct LaneModel {
 // keep them in registers (every index below is a compile-time constant after
 // unrolling), which takes ~60% of the shared-memory traffic out of the ADMM
 // iteration; larger ones keep them in the node record.
+// Record entries per linearised obstacle (normal, bound): padded to 5 in FP32
+// so that the lanes of the lane kernel, which take every fourth obstacle, fall
+// in distinct banks.
+template <class T> struct ObsStride { static constexpr int value = sizeof(T) == 4 ? 5 : 4; };
+
+// Row strides of A and B in the record: odd (NX | 1, NU | 1) for the FP32 lane
+// layout, so that lanes reading different rows, or different columns, of their
+// node's matrix fall in distinct banks; unpadded otherwise.
+template <class M, class T> struct MatStride {
+  static constexpr bool pad = LaneModel<M>::value && sizeof(T) == 4;
+  static constexpr int A = pad ? (M::NX | 1) : M::NX, B = pad ? (M::NU | 1) : M::NU;
+};
 template <class M, class T, bool AOS>
 struct SmemMats {
   Node<T, AOS> nd;
   int oA, oB, oH;
-  __device__ __forceinline__ T& A(int k) const { return nd.at(oA, k); }
-  __device__ __forceinline__ T& B(int k) const { return nd.at(oB, k); }
+  __device__ __forceinline__ T& A(int r, int c) const { return nd.at(oA, r * MatStride<M, T>::A + c); }
+  __device__ __forceinline__ T& B(int r, int c) const { return nd.at(oB, r * MatStride<M, T>::B + c); }
   __device__ __forceinline__ T& H(int k) const { return nd.at(oH, k); }
 };
 template <class M, class T>
 struct RegMats {
   static constexpr int NN = M::NX + M::NU;
   mutable T a[M::NX * M::NX], b[M::NX * M::NU], h[NN * (NN + 1) / 2];
-  __device__ __forceinline__ T& A(int k) const { return a[k]; }
-  __device__ __forceinline__ T& B(int k) const { return b[k]; }
+  __device__ __forceinline__ T& A(int r, int c) const { return a[r * M::NX + c]; }
+  __device__ __forceinline__ T& B(int r, int c) const { return b[r * M::NU + c]; }
   __device__ __forceinline__ T& H(int k) const { return h[k]; }
 };
 template <class M> struct SmallModel {
@@ -400,8 +413,8 @@ __device__ __forceinline__ void node_jacobians(const Node<T, AOS>& nd, const MS&
     rk4_jvp<M, T>(prm, h, xt, ut, dir, col);
 #pragma unroll
     for (int r = 0; r < NX; ++r) {
-      if (dir < NX) MT.A(r * NX + dir) = col[r];
-      else MT.B(r * NU + (dir - NX)) = col[r];
+      if (dir < NX) MT.A(r, dir) = col[r];
+      else MT.B(r, dir - NX) = col[r];
     }
   }
 }
@@ -450,10 +463,10 @@ __device__ void node_setup(const Node<T, AOS>& nd, const Layout& L, const Proble
       const T inn = T(1) / nn;
       const T n0 = nv[0] * inn, n1 = nv[1] * inn, n2 = nv[2] * inn;
       const T bd = -(n0 * dp[0] + n1 * dp[1] + n2 * dp[2]) + (T)P.obs_r[(long long)b * P.max_obs + j];
-      nd.at(L.oMd, 4 * j + 0) = (T)n0;
-      nd.at(L.oMd, 4 * j + 1) = (T)n1;
-      nd.at(L.oMd, 4 * j + 2) = (T)n2;
-      nd.at(L.oMd, 4 * j + 3) = (T)bd;
+      nd.at(L.oMd, ObsStride<T>::value * j + 0) = (T)n0;
+      nd.at(L.oMd, ObsStride<T>::value * j + 1) = (T)n1;
+      nd.at(L.oMd, ObsStride<T>::value * j + 2) = (T)n2;
+      nd.at(L.oMd, ObsStride<T>::value * j + 3) = (T)bd;
     }
   } else {
     // nominal position / thrust in T, the offsets of the cone and ball projections
@@ -505,14 +518,14 @@ __device__ __forceinline__ bool node_factor(const Node<T, AOS>& nd, const MS& MT
         if (!term) {
           T acc = T(0);
           #pragma unroll
-          for (int k = 0; k < NX; ++k) acc += MT.A(k * NX + r) * MT.A(k * NX + c);
+          for (int k = 0; k < NX; ++k) acc += MT.A(k, r) * MT.A(k, c);
           h += rd * acc;
         }
         if constexpr (IsQuad<M>::value) {
           if (r < 3 && c < 3) {
             T acc = T(0);
             #pragma unroll
-            for (int j = 0; j < I.nobs; ++j) acc += nd.at(L.oMd, 4 * j + r) * nd.at(L.oMd, 4 * j + c);
+            for (int j = 0; j < I.nobs; ++j) acc += nd.at(L.oMd, ObsStride<T>::value * j + r) * nd.at(L.oMd, ObsStride<T>::value * j + c);
             h += rg * acc;
           }
         } else {
@@ -526,14 +539,14 @@ __device__ __forceinline__ bool node_factor(const Node<T, AOS>& nd, const MS& MT
       } else if (c < NX) {  // H21 = H12^T (zero at node N: no control there)
         T acc = T(0);
         #pragma unroll
-        for (int k = 0; k < NX; ++k) acc += MT.B(k * NU + (r - NX)) * MT.A(k * NX + c);
+        for (int k = 0; k < NX; ++k) acc += MT.B(k, r - NX) * MT.A(k, c);
         h = term ? T(0) : rd * acc;
       } else {  // H22 (identity at node N, decoupled from the state block)
         const int rr = r - NX, cc = c - NX;
         if (rr == cc) h = K.hd[r];
         T acc = T(0);
         #pragma unroll
-        for (int k = 0; k < NX; ++k) acc += MT.B(k * NU + rr) * MT.B(k * NU + cc);
+        for (int k = 0; k < NX; ++k) acc += MT.B(k, rr) * MT.B(k, cc);
         if (!term) h += rd * acc;
         if constexpr (!IsQuad<M>::value) {
           if (rr < 3 && cc < 3 && !term) {
@@ -627,29 +640,29 @@ __device__ __forceinline__ void apply_H(const Node<T, AOS>& nd, const MS& MT, co
     for (int r = 0; r < NX; ++r) {
       T acc = T(0);
 #pragma unroll
-      for (int c = 0; c < NX; ++c) acc += MT.A(r * NX + c) * xi[c];
+      for (int c = 0; c < NX; ++c) acc += MT.A(r, c) * xi[c];
 #pragma unroll
-      for (int c = 0; c < NU; ++c) acc += MT.B(r * NU + c) * xi[NX + c];
+      for (int c = 0; c < NU; ++c) acc += MT.B(r, c) * xi[NX + c];
       v[r] = rd * acc;
     }
 #pragma unroll
     for (int j = 0; j < NX; ++j) {
       T acc = T(0);
 #pragma unroll
-      for (int k = 0; k < NX; ++k) acc += MT.A(k * NX + j) * v[k];
+      for (int k = 0; k < NX; ++k) acc += MT.A(k, j) * v[k];
       out[j] += acc;
     }
 #pragma unroll
     for (int j = 0; j < NU; ++j) {
       T acc = T(0);
 #pragma unroll
-      for (int k = 0; k < NX; ++k) acc += MT.B(k * NU + j) * v[k];
+      for (int k = 0; k < NX; ++k) acc += MT.B(k, j) * v[k];
       out[NX + j] = K.hd[NX + j] * xi[NX + j] + acc;
     }
   }
   if constexpr (IsQuad<M>::value) {
     for (int j = 0; j < I.nobs; ++j) {
-      const T n0 = nd.at(L.oMd, 4 * j), n1 = nd.at(L.oMd, 4 * j + 1), n2 = nd.at(L.oMd, 4 * j + 2);
+      const T n0 = nd.at(L.oMd, ObsStride<T>::value * j), n1 = nd.at(L.oMd, ObsStride<T>::value * j + 1), n2 = nd.at(L.oMd, ObsStride<T>::value * j + 2);
       const T y = rg * (n0 * xi[0] + n1 * xi[1] + n2 * xi[2]);
       out[0] += n0 * y; out[1] += n1 * y; out[2] += n2 * y;
     }
@@ -695,23 +708,23 @@ __device__ __forceinline__ void node_rhs(const Node<T, AOS>& nd, const MS& MT, c
     for (int j = 0; j < NX; ++j) {
       T acc = T(0);
 #pragma unroll
-      for (int k = 0; k < NX; ++k) acc += MT.A(k * NX + j) * w[k];
+      for (int k = 0; k < NX; ++k) acc += MT.A(k, j) * w[k];
       g[j] += acc;
     }
 #pragma unroll
     for (int j = 0; j < NU; ++j) {
       T acc = T(0);
 #pragma unroll
-      for (int k = 0; k < NX; ++k) acc += MT.B(k * NU + j) * w[k];
+      for (int k = 0; k < NX; ++k) acc += MT.B(k, j) * w[k];
       g[NX + j] = -K.q[NX + j] + acc + rg * nd.at(Rec<M>::Uh, j) - nd.at(Rec<M>::Nuu, j);
     }
   }
   if constexpr (IsQuad<M>::value) {
     for (int j = 0; j < I.nobs; ++j) {
       const T a = rg * nd.at(L.oS, j) - nd.at(L.oNus, j);
-      g[0] += nd.at(L.oMd, 4 * j) * a;
-      g[1] += nd.at(L.oMd, 4 * j + 1) * a;
-      g[2] += nd.at(L.oMd, 4 * j + 2) * a;
+      g[0] += nd.at(L.oMd, ObsStride<T>::value * j) * a;
+      g[1] += nd.at(L.oMd, ObsStride<T>::value * j + 1) * a;
+      g[2] += nd.at(L.oMd, ObsStride<T>::value * j + 2) * a;
     }
   } else {
     constexpr int RC = IsMars14<M>::value ? 1 : 0;
@@ -749,8 +762,8 @@ __device__ __forceinline__ void node_mirrors(const Node<T, AOS>& nd, const Layou
   const T irg = T(1) / rg;
   if constexpr (IsQuad<M>::value) {
     for (int j = 0; j < I.nobs; ++j) {
-      const T n0 = nd.at(L.oMd, 4 * j), n1 = nd.at(L.oMd, 4 * j + 1), n2 = nd.at(L.oMd, 4 * j + 2);
-      const T bd = nd.at(L.oMd, 4 * j + 3);
+      const T n0 = nd.at(L.oMd, ObsStride<T>::value * j), n1 = nd.at(L.oMd, ObsStride<T>::value * j + 1), n2 = nd.at(L.oMd, ObsStride<T>::value * j + 2);
+      const T bd = nd.at(L.oMd, ObsStride<T>::value * j + 3);
       const T y = n0 * xi[0] + n1 * xi[1] + n2 * xi[2];
       if (reseed) { nd.at(L.oS, j) = maxv(bd, y); continue; }
       const T so = nd.at(L.oS, j);
@@ -919,9 +932,9 @@ __device__ __forceinline__ void admm_iteration(const Node<T, AOS>& nd, const MS&
         for (int r = 0; r < NX; ++r) {
           T acc = nd.at(Rec<M>::C, r);
 #pragma unroll
-          for (int c = 0; c < NX; ++c) acc += MT.A(r * NX + c) * x[c];
+          for (int c = 0; c < NX; ++c) acc += MT.A(r, c) * x[c];
 #pragma unroll
-          for (int c = 0; c < NU; ++c) acc += MT.B(r * NU + c) * x[NX + c];
+          for (int c = 0; c < NU; ++c) acc += MT.B(r, c) * x[NX + c];
           nd.at(Rec<M>::Ex1, r) = acc;
         }
       } else {
@@ -1032,14 +1045,14 @@ __device__ __forceinline__ void admm_iteration(const Node<T, AOS>& nd, const MS&
           for (int j = 0; j < NX; ++j) {
             T acc = T(0);
 #pragma unroll
-            for (int k = 0; k < NX; ++k) acc += MT.A(k * NX + j) * nd.nb(Rec<M>::Ex1, k, i + 1);
+            for (int k = 0; k < NX; ++k) acc += MT.A(k, j) * nd.nb(Rec<M>::Ex1, k, i + 1);
             sv[j] += acc;
           }
 #pragma unroll
           for (int j = 0; j < NU; ++j) {
             T acc = T(0);
 #pragma unroll
-            for (int k = 0; k < NX; ++k) acc += MT.B(k * NU + j) * nd.nb(Rec<M>::Ex1, k, i + 1);
+            for (int k = 0; k < NX; ++k) acc += MT.B(k, j) * nd.nb(Rec<M>::Ex1, k, i + 1);
             sv[NX + j] += acc;
           }
         }
@@ -1126,7 +1139,7 @@ __device__ void node_export(const Node<T, AOS>& nd, const Layout& L, const Probl
   if constexpr (IsQuad<M>::value) {
     for (int j = 0; j < P.nobs[b]; ++j) {
       double np = 0.0;
-      for (int k = 0; k < 3; ++k) np += (double)nd.at(L.oMd, 4 * j + k) * nd.dat(Rec<M>::Xbar, k);
+      for (int k = 0; k < 3; ++k) np += (double)nd.at(L.oMd, ObsStride<T>::value * j + k) * nd.dat(Rec<M>::Xbar, k);
       si[3 * j] = (double)nd.at(L.oS, j) + np;
       ni[3 * j] = (double)nd.at(L.oNus, j);
     }
@@ -1204,7 +1217,7 @@ __device__ void node_import(const Node<T, AOS>& nd, const Layout& L, const Probl
   if constexpr (IsQuad<M>::value) {
     for (int j = 0; j < P.nobs[b]; ++j) {
       double np = 0.0;
-      for (int k = 0; k < 3; ++k) np += (double)nd.at(L.oMd, 4 * j + k) * nd.dat(Rec<M>::Xbar, k);
+      for (int k = 0; k < 3; ++k) np += (double)nd.at(L.oMd, ObsStride<T>::value * j + k) * nd.dat(Rec<M>::Xbar, k);
       nd.at(L.oS, j) = (T)(si[3 * j] - np);
       nd.at(L.oNus, j) = (T)ni[3 * j];
     }
@@ -1249,7 +1262,7 @@ __device__ void node_rebase_mirrors(const Node<T, AOS>& nd, const Layout& L, con
   if constexpr (IsQuad<M>::value) {
     for (int j = 0; j < P.nobs[b]; ++j) {
       T y = T(0);
-      for (int k = 0; k < 3; ++k) y += nd.at(L.oMd, 4 * j + k) * nd.at(Rec<M>::Xh, k);
+      for (int k = 0; k < 3; ++k) y += nd.at(L.oMd, ObsStride<T>::value * j + k) * nd.at(Rec<M>::Xh, k);
       nd.at(L.oS, j) -= y;
     }
   } else {
@@ -1345,9 +1358,12 @@ __global__ void __launch_bounds__(MAX_THREADS) admm_kernel(ProblemDev P, Layout 
     // A, B in T; deviation affine term c_i = A xbar_i + B ubar_i + d_i - xbar_{i+1} in FP64
     const long long g = uo + i;
 #pragma unroll
-    for (int e = 0; e < NX * NX; ++e) MT.A(e) = (T)Ag[g * NX * NX + e];
+    for (int r = 0; r < NX; ++r) {
 #pragma unroll
-    for (int e = 0; e < NX * NU; ++e) MT.B(e) = (T)Bg[g * NX * NU + e];
+      for (int c = 0; c < NX; ++c) MT.A(r, c) = (T)Ag[g * NX * NX + r * NX + c];
+#pragma unroll
+      for (int c = 0; c < NU; ++c) MT.B(r, c) = (T)Bg[g * NX * NU + r * NU + c];
+    }
     for (int r = 0; r < NX; ++r) {
       double acc = dg[g * NX + r];
       for (int c = 0; c < NX; ++c) acc += Ag[g * NX * NX + r * NX + c] * nd.dat(Rec<M>::Xbar, c);
@@ -1485,7 +1501,8 @@ __global__ void __launch_bounds__(MAX_THREADS) scp_kernel(ProblemDev P, Layout L
   for (int k = 0; k < Kscp; ++k) {
     if (threadIdx.x == 0) {
       double f = 1.0;
-      if (P.rho_final > 0.0 && Kscp > 1) f = pow(P.rho_final / P.rho_geo, (double)k / (double)(Kscp - 1));
+      if (P.rho_fac) f = P.rho_fac[k];   // the schedule tabulated at create
+      else if (P.rho_final > 0.0 && Kscp > 1) f = pow(P.rho_final / P.rho_geo, (double)k / (double)(Kscp - 1));
       sh.fac = f;
     }
     __syncthreads();
@@ -1541,9 +1558,9 @@ __global__ void __launch_bounds__(MAX_THREADS) scp_kernel(ProblemDev P, Layout L
           dinf = fmax(dinf, fabs(fc[r]));
           T lin = nd.at(Rec<M>::C, r) - nd.nb(Rec<M>::Xh, r, i + 1);
 #pragma unroll
-          for (int c = 0; c < NX; ++c) lin += MT.A(r * NX + c) * nd.at(Rec<M>::Xh, c);
+          for (int c = 0; c < NX; ++c) lin += MT.A(r, c) * nd.at(Rec<M>::Xh, c);
 #pragma unroll
-          for (int c = 0; c < NU; ++c) lin += MT.B(r * NU + c) * nd.at(Rec<M>::Uh, c);
+          for (int c = 0; c < NU; ++c) lin += MT.B(r, c) * nd.at(Rec<M>::Uh, c);
           lin1 += absv(lin);
         }
         v[2] = (double)lin1;

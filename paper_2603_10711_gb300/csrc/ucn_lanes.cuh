@@ -114,8 +114,8 @@ __device__ __forceinline__ void lanes_jacobians(const Node<T, AOS>& nd, const MS
     rk4_jvp<M, T>(prm, h, xt, ut, dir, col);
 #pragma unroll
     for (int r = 0; r < NX; ++r) {
-      if (dir < NX) MT.A(r * NX + dir) = col[r];
-      else MT.B(r * NU + (dir - NX)) = col[r];
+      if (dir < NX) MT.A(r, dir) = col[r];
+      else MT.B(r, dir - NX) = col[r];
     }
   }
 }
@@ -181,11 +181,11 @@ __device__ __forceinline__ void admm_iteration_lanes(const Node<T, AOS>& nd, con
         if (hasU) {
           T acc = T(0);
 #pragma unroll
-          for (int k = 0; k < NX; ++k) acc += MT.A(k * NX + j) * w[k];
+          for (int k = 0; k < NX; ++k) acc += MT.A(k, j) * w[k];
           v += acc;
         }
         if (m == 0 && j < 3)
-          for (int o = 0; o < I.nobs; ++o) v += nd.at(L.oMd, 4 * o + j) * (rg * nd.at(L.oS, o) - nd.at(L.oNus, o));
+          for (int o = 0; o < I.nobs; ++o) v += nd.at(L.oMd, ObsStride<T>::value * o + j) * (rg * nd.at(L.oS, o) - nd.at(L.oNus, o));
       }
       g[m] = v;
     }
@@ -196,7 +196,7 @@ __device__ __forceinline__ void admm_iteration_lanes(const Node<T, AOS>& nd, con
       if (hasU) {
         T acc = T(0);
 #pragma unroll
-        for (int k = 0; k < NX; ++k) acc += MT.B(k * NU + j) * w[k];
+        for (int k = 0; k < NX; ++k) acc += MT.B(k, j) * w[k];
         v = -kq[RX + m] + acc + rg * nd.at(Rec<M>::Uh, j) - nd.at(Rec<M>::Nuu, j);
       }
       g[RX + m] = v;
@@ -222,9 +222,9 @@ __device__ __forceinline__ void admm_iteration_lanes(const Node<T, AOS>& nd, con
         T acc = T(0);
         if (hasU) {
 #pragma unroll
-          for (int c = 0; c < NX; ++c) acc += MT.A(k * NX + c) * xf[c];
+          for (int c = 0; c < NX; ++c) acc += MT.A(k, c) * xf[c];
 #pragma unroll
-          for (int c = 0; c < NU; ++c) acc += MT.B(k * NU + c) * xf[NX + c];
+          for (int c = 0; c < NU; ++c) acc += MT.B(k, c) * xf[NX + c];
         }
         vo[m] = rd * acc;
       }
@@ -237,12 +237,12 @@ __device__ __forceinline__ void admm_iteration_lanes(const Node<T, AOS>& nd, con
         T hx = khd[m] * xo[m];
         if (hasU) {
 #pragma unroll
-          for (int k = 0; k < NX; ++k) hx += MT.A(k * NX + j) * vf[k];
+          for (int k = 0; k < NX; ++k) hx += MT.A(k, j) * vf[k];
         }
         if (active && m == 0 && j < 3)
           for (int o = 0; o < I.nobs; ++o) {
-            const T n0 = nd.at(L.oMd, 4 * o), n1 = nd.at(L.oMd, 4 * o + 1), n2 = nd.at(L.oMd, 4 * o + 2);
-            hx += nd.at(L.oMd, 4 * o + j) * (rg * (n0 * xf[0] + n1 * xf[1] + n2 * xf[2]));
+            const T n0 = nd.at(L.oMd, ObsStride<T>::value * o), n1 = nd.at(L.oMd, ObsStride<T>::value * o + 1), n2 = nd.at(L.oMd, ObsStride<T>::value * o + 2);
+            hx += nd.at(L.oMd, ObsStride<T>::value * o + j) * (rg * (n0 * xf[0] + n1 * xf[1] + n2 * xf[2]));
           }
         res[m] = g[m] - hx;
       }
@@ -252,7 +252,7 @@ __device__ __forceinline__ void admm_iteration_lanes(const Node<T, AOS>& nd, con
         T hx = khd[RX + m] * xo[RX + m];
         if (hasU) {
 #pragma unroll
-          for (int k = 0; k < NX; ++k) hx += MT.B(k * NU + j) * vf[k];
+          for (int k = 0; k < NX; ++k) hx += MT.B(k, j) * vf[k];
         }
         res[RX + m] = g[RX + m] - hx;
       }
@@ -277,9 +277,9 @@ __device__ __forceinline__ void admm_iteration_lanes(const Node<T, AOS>& nd, con
           const int k = q + TPN * m;
           T acc = nd.at(Rec<M>::C, k);
 #pragma unroll
-          for (int c = 0; c < NX; ++c) acc += MT.A(k * NX + c) * xf[c];
+          for (int c = 0; c < NX; ++c) acc += MT.A(k, c) * xf[c];
 #pragma unroll
-          for (int c = 0; c < NU; ++c) acc += MT.B(k * NU + c) * xf[NX + c];
+          for (int c = 0; c < NU; ++c) acc += MT.B(k, c) * xf[NX + c];
           nd.at(Rec<M>::Ex1, k) = acc;
         }
       }
@@ -355,8 +355,8 @@ __device__ __forceinline__ void admm_iteration_lanes(const Node<T, AOS>& nd, con
     }
     // linearised obstacles (mirror half-spaces on the position), split over the lanes
     for (int o = q; o < I.nobs; o += TPN) {
-      const T n0 = nd.at(L.oMd, 4 * o), n1 = nd.at(L.oMd, 4 * o + 1), n2 = nd.at(L.oMd, 4 * o + 2);
-      const T bd = nd.at(L.oMd, 4 * o + 3);
+      const T n0 = nd.at(L.oMd, ObsStride<T>::value * o), n1 = nd.at(L.oMd, ObsStride<T>::value * o + 1), n2 = nd.at(L.oMd, ObsStride<T>::value * o + 2);
+      const T bd = nd.at(L.oMd, ObsStride<T>::value * o + 3);
       const T y = n0 * xf[0] + n1 * xf[1] + n2 * xf[2];
       const T so = nd.at(L.oS, o);
       const T s = maxv(bd, y + nd.at(L.oNus, o) * irg);
@@ -413,7 +413,7 @@ __device__ __forceinline__ void admm_iteration_lanes(const Node<T, AOS>& nd, con
         const int j = q + TPN * m;
         T acc = T(0);
 #pragma unroll
-        for (int k = 0; k < NX; ++k) acc += MT.A(k * NX + j) * e[k];
+        for (int k = 0; k < NX; ++k) acc += MT.A(k, j) * e[k];
         sv[m] += acc;
       }
 #pragma unroll
@@ -421,7 +421,7 @@ __device__ __forceinline__ void admm_iteration_lanes(const Node<T, AOS>& nd, con
         const int j = q + TPN * m;
         T acc = T(0);
 #pragma unroll
-        for (int k = 0; k < NX; ++k) acc += MT.B(k * NU + j) * e[k];
+        for (int k = 0; k < NX; ++k) acc += MT.B(k, j) * e[k];
         sv[RX + m] += acc;
       }
     }
@@ -541,7 +541,8 @@ __global__ void __launch_bounds__(LANES_MAX_THREADS) scp_kernel_lanes(ProblemDev
   for (int k = 0; k < Kscp; ++k) {
     if (threadIdx.x == 0) {
       double f = 1.0;
-      if (P.rho_final > 0.0 && Kscp > 1) f = pow(P.rho_final / P.rho_geo, (double)k / (double)(Kscp - 1));
+      if (P.rho_fac) f = P.rho_fac[k];   // the schedule tabulated at create
+      else if (P.rho_final > 0.0 && Kscp > 1) f = pow(P.rho_final / P.rho_geo, (double)k / (double)(Kscp - 1));
       sh.fac = f;
     }
     __syncthreads();
@@ -597,8 +598,8 @@ __global__ void __launch_bounds__(LANES_MAX_THREADS) scp_kernel_lanes(ProblemDev
           v[1] += fabs(fc[r]);
           dinf = fmax(dinf, fabs(fc[r]));
           T lin = ndd.at(Rec<M>::C, r) - ndd.nb(Rec<M>::Xh, r, id + 1);
-          for (int c = 0; c < NX; ++c) lin += MTd.A(r * NX + c) * ndd.at(Rec<M>::Xh, c);
-          for (int c = 0; c < NU; ++c) lin += MTd.B(r * NU + c) * ndd.at(Rec<M>::Uh, c);
+          for (int c = 0; c < NX; ++c) lin += MTd.A(r, c) * ndd.at(Rec<M>::Xh, c);
+          for (int c = 0; c < NU; ++c) lin += MTd.B(r, c) * ndd.at(Rec<M>::Uh, c);
           lin1 += absv(lin);
         }
         v[2] = (double)lin1;
