@@ -111,3 +111,25 @@ def test_lane_layout_is_refused_where_it_does_not_apply():
     s.scp_solve(); torch.cuda.synchronize()
     assert np.isfinite(s.stats_host()["cost"]).all()
     s.close()
+
+
+def test_full_size_uneven_batch_sampled_against_the_oracle():
+    # the 4096-instance uneven batch in the benchmark's launch (library defaults); 4 instances
+    # solved again by the oracle
+    prob = W.quad_box(4096, seed=2)
+    s = ucn.Solver(prob, precision=ucn.UCN_PREC_FP32_REFINE)
+    x, u = s.scp_solve()
+    torch.cuda.synchronize()
+    st = s.stats_host()
+    xg = x.cpu().numpy()
+    s.close()
+    assert np.isfinite(xg).all() and np.mean(st["defect"] <= 1e-5) >= 0.95
+    idx = [0, 4095, 1234, 2900]
+    sub = prob.subset(idx)
+    xr, ur, sr, _ = oracle.scp_solve(sub)
+    for k, b in enumerate(idx):
+        N = int(prob.N[b])
+        xo, so = prob.xoff[b], sub.xoff[k]
+        np.testing.assert_array_equal(xg[xo], prob.xinit[b])
+        if sr[k, 0] <= 1e-5 and st["defect"][b] <= 1e-5 and int(sr[k, 7]) == int(st["scp_iters"][b]):
+            assert rel_err(xg[xo:xo + N + 1], xr[so:so + N + 1]) <= 1e-3

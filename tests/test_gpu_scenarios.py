@@ -201,3 +201,24 @@ def test_receding_horizon_approaches_the_goal():
     # warm starts from the shifted tube converge in fewer SCP iterations than the cold start
     assert np.mean(iters[1:]) < np.mean(iters[0])
     s.close()
+
+
+def test_full_size_scenario_batch_sampled_against_the_oracle():
+    # 256 problems x 64 scenarios, the cold first step of the benchmark; one group checked
+    # against the oracle's group solve (same shared first control and iteration count)
+    prob = W.scenario_mpc(256, 64, seed=3, N=40, n_obs=8)
+    s = ucn.Solver(prob, precision=ucn.UCN_PREC_FP32_REFINE)
+    x, u = s.scp_solve()
+    torch.cuda.synchronize()
+    st = s.stats_host()
+    ug = u.cpu().numpy(); xg = x.cpu().numpy()
+    s.close()
+    check_group_invariants(prob, ug, st)
+    assert np.mean(st["defect"] <= 1e-5) >= 0.95
+    g = 37
+    sub = prob.subset(np.arange(g * 64, (g + 1) * 64))
+    xr, ur, sr, _ = oracle.scp_solve(sub)
+    if (sr[:, 0] <= 1e-5).all() and int(sr[0, 7]) == int(st["scp_iters"][g * 64]):
+        for k in range(64):
+            b = g * 64 + k
+            assert rel_err(xg[prob.xoff[b]:prob.xoff[b] + 41], xr[sub.xoff[k]:sub.xoff[k] + 41]) <= 1e-3
