@@ -327,7 +327,10 @@ def run_serving(args):
     time in FP64 (the plain per-request path)."""
     from paper_2603_10711_gb300 import serving, ucn
     stream = W.serving_stream(args.serving_requests, rate=args.serving_rate, seed=4)
-    qs, ms = W.quad_box(1).settings, W.mars_batch(1).settings
+    qs = W.quad_box(1).settings
+    # Mars requests run up to N = 200: the batch's 60 x 40 schedule converges up to N = 150,
+    # longer horizons need more ADMM iterations per SCP iteration (80 x 60 passes up to 200)
+    ms = dict(W.mars_batch(1).settings, rho_final=1e7, scp_iters=80, admm_iters=60)
 
     def servers(prec, slots):
         return {1: serving.Server(1, prec, max_slots=slots, max_horizon=120, max_obs=30, lanes=4, settings=qs),

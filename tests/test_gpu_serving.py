@@ -96,7 +96,7 @@ def test_warm_start_from_a_kept_trajectory():
 def test_mixed_stream_completes_and_matches_the_oracle():
     stream = W.serving_stream(24, rate=4000.0, seed=9)
     qs = stream[0][1].settings if stream[0][1].model == 1 else W.quad_box(1).settings
-    ms = W.mars_batch(1).settings
+    ms = dict(W.mars_batch(1).settings, rho_final=1e7, scp_iters=80, admm_iters=60)   # Mars N up to 200
     servers = {1: serving.Server(1, ucn.UCN_PREC_FP32_REFINE, max_slots=32, max_horizon=120, max_obs=30, lanes=3, settings=qs),
                2: serving.Server(2, ucn.UCN_PREC_FP32_REFINE, max_slots=32, max_horizon=200, lanes=3, settings=ms)}
     out = serving.run_stream(stream, servers)
