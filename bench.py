@@ -464,12 +464,13 @@ def run_scenarios(args):
             "fp32_cold_step_ms": step_ms[0]}
 
 
-def oracle_sample(args, seconds=None):
-    """The FP64 CPU oracle on a bounded sample of the same workload."""
+def oracle_sample(args, n=None):
+    """The FP64 CPU oracle on a bounded sample of the same workload (n instances,
+    evenly spaced; default --cpu-sample)."""
     import oracle
     prob = W.mars_batch(args.batch, seed=1)
     threads = oracle.max_threads()
-    n = max(threads, args.cpu_sample)
+    n = min(args.batch, max(threads, args.cpu_sample if n is None else n))
     sub = prob.subset(np.arange(n) * (prob.batch // n))
     t0 = time.perf_counter()
     _, _, st, _ = oracle.scp_solve(sub, nthreads=threads)
@@ -491,7 +492,7 @@ def run_reference(args, rank, world):
     for _ in range(args.warmup):
         pass   # the oracle has no warm state; warm-up steps are not needed on the CPU
     for _ in range(args.steps):
-        passed, n, dt, threads = oracle_sample(args)
+        passed, n, dt, threads = oracle_sample(args, args.ref_sample)
         times.append(dt); passed_all += passed; n_all += n
     value = passed_all / sum(times)
     return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -514,6 +515,7 @@ def main():
     ap.add_argument("--batch", type=int, default=1024)
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--cpu-sample", type=int, default=1024)
+    ap.add_argument("--ref-sample", type=int, default=128, help="instances per step of the reference (oracle) arm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=2000, help="requests of the serving stream (0: skip)")
     ap.add_argument("--serving-rate", type=float, default=2000.0, help="Poisson arrival rate of the serving stream")
