@@ -109,7 +109,7 @@ bool halloc(ucn_server* s, V** out, size_t n) {
 long long footprint(const ucn_server* s, int N) {
   const long long nodes = N + 1;
   long long b = nodes * (long long)(s->nx + s->nu) * 8 * 2;                       // guess + output
-  const int mb = s->cfg.model == UCN_MODEL_QUAD12 ? s->max_obs : 3;
+  const int mb = model_obstacles(s->cfg.model) ? s->max_obs : (s->cfg.model == UCN_MODEL_MARS14 ? 6 : 3);
   b += 8LL * (6 * nodes * s->nx + 3LL * N * s->nu + 2 * nodes * mb * 3);          // exported state
   if (!s->smem) b += (long long)s->L.bytes * nodes / (s->Nmax + 1);               // global workspace share
   return b;
@@ -133,7 +133,7 @@ ucn_status ucn_serve_create(const ucn_serve_config* c, ucn_server** out) {
   set_error_message("");
   if (!c || !out) return sfail(UCN_EINVAL, "null argument");
   *out = nullptr;
-  if (c->model != UCN_MODEL_QUAD12 && c->model != UCN_MODEL_MARS7) return sfail(UCN_EINVAL, "unknown model %d", c->model);
+  if (!model_known(c->model)) return sfail(UCN_EINVAL, "unknown model %d", c->model);
   if (c->precision != UCN_PREC_FP64 && c->precision != UCN_PREC_FP32_REFINE) return sfail(UCN_EINVAL, "unknown precision");
   if (c->max_slots < 1 || c->max_horizon < 1 || c->max_horizon + 1 > MAX_THREADS) return sfail(UCN_EINVAL, "bad slot count or horizon");
   if (c->max_obs < 0 || c->max_obs > 64) return sfail(UCN_EINVAL, "max_obs must be in [0, 64]");
@@ -144,18 +144,18 @@ ucn_status ucn_serve_create(const ucn_serve_config* c, ucn_server** out) {
   if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return sfail(UCN_ECUDA, "no CUDA device"); }
   ucn_server* s = new ucn_server();
   s->cfg = *c;
-  const bool quad = c->model == UCN_MODEL_QUAD12;
-  s->nx = quad ? 12 : 7; s->nu = quad ? 4 : 3;
+  const bool quad = model_obstacles(c->model);
+  s->nx = model_nx(c->model); s->nu = model_nu(c->model);
   s->S = c->max_slots; s->Nmax = c->max_horizon; s->max_obs = quad ? c->max_obs : 0; s->lanes = c->lanes;
   const int S = s->S, NX = s->nx, NU = s->nu, MO = std::max(s->max_obs, 1);
-  const int mb = quad ? s->max_obs : 3;
+  const int mb = quad ? s->max_obs : (c->model == UCN_MODEL_MARS14 ? 6 : 3);
   const long long Xn = (long long)(s->Nmax + 1), Un = s->Nmax;
   s->state_per_slot = 6 * Xn * NX + 3 * Un * NU + 2 * Xn * mb * 3;
   const int tsize = c->precision == UCN_PREC_FP64 ? 8 : 4;
   int optin = 0;
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   const long long static_sh = (long long)sizeof(InstShared) + 64;
-  s->L = make_layout(c->model, s->Nmax + 1, s->max_obs, tsize, !quad);
+  s->L = make_layout(c->model, s->Nmax + 1, s->max_obs, tsize, c->model == UCN_MODEL_MARS7);
   s->smem = s->L.bytes + static_sh <= optin;
   if (!s->smem) s->L = make_layout(c->model, s->Nmax + 1, s->max_obs, tsize, false);
   s->smem_bytes = s->smem ? s->L.bytes : 0;
@@ -230,9 +230,9 @@ ucn_status ucn_serve_submit(ucn_server* s, const ucn_request* r, unsigned long l
   if (!(r->dt > 0) || !r->model_params || !r->Q_diag || !r->x_ref || !r->R_diag || !r->u_ref || !r->QN_diag || !r->qN ||
       !r->x_lo || !r->x_hi || !r->u_lo || !r->u_hi || !r->x_init || !r->x_target || !r->term_mask)
     return sfail(UCN_EINVAL, "incomplete request");
-  if (s->cfg.model == UCN_MODEL_QUAD12 && (r->n_obs < 0 || r->n_obs > s->max_obs || (r->n_obs > 0 && (!r->obs_c || !r->obs_r))))
+  if (model_obstacles(s->cfg.model) && (r->n_obs < 0 || r->n_obs > s->max_obs || (r->n_obs > 0 && (!r->obs_c || !r->obs_r))))
     return sfail(UCN_EINVAL, "bad obstacle data");
-  if (s->cfg.model == UCN_MODEL_MARS7 && !r->sets) return sfail(UCN_EINVAL, "Mars requests need sets");
+  if (!model_obstacles(s->cfg.model) && !r->sets) return sfail(UCN_EINVAL, "Mars requests need sets");
   std::lock_guard<std::mutex> lk(s->mu);
   int ring = -1;
   if (!(r->x_guess && r->u_guess)) {
@@ -256,7 +256,7 @@ ucn_status ucn_serve_submit(ucn_server* s, const ucn_request* r, unsigned long l
   std::memcpy(&s->hulo[k * NU], r->u_lo, NU * 8); std::memcpy(&s->huhi[k * NU], r->u_hi, NU * 8);
   std::memcpy(&s->hxi[k * NX], r->x_init, NX * 8); std::memcpy(&s->hxt[k * NX], r->x_target, NX * 8);
   std::memcpy(&s->htm[k * NX], r->term_mask, NX);
-  s->hnobs[k] = s->cfg.model == UCN_MODEL_QUAD12 ? r->n_obs : 0;
+  s->hnobs[k] = model_obstacles(s->cfg.model) ? r->n_obs : 0;
   if (s->hnobs[k] > 0) {
     std::memcpy(&s->hoc[(size_t)k * MO * 3], r->obs_c, (size_t)r->n_obs * 3 * 8);
     std::memcpy(&s->hor[(size_t)k * MO], r->obs_r, (size_t)r->n_obs * 8);
@@ -322,8 +322,7 @@ ucn_status ucn_serve_pump(ucn_server* s, int* launched) {
   c.P = &P; c.L = &s->L; c.smem = s->smem; c.smem_bytes = s->smem_bytes;
   c.threads = s->threads; c.blocks = (int)ready.size(); c.stream = st; c.group = 1;
   c.nodes = s->cfg.max_horizon + 1; c.tpn = default_tpn(s->cfg.model, s->cfg.max_horizon + 1);
-  const bool quad = s->cfg.model == UCN_MODEL_QUAD12, f64 = s->cfg.precision == UCN_PREC_FP64;
-  auto fn = quad ? (f64 ? quad64_scp : quad32_scp) : (f64 ? mars64_scp : mars32_scp);
+  auto fn = launchers_for(s->cfg.model, s->cfg.precision).scp;
   cudaError_t e = fn(c, s->x0, s->u0, s->xo, s->uo, s->stats, s->status);
   if (e == cudaSuccess) e = cudaEventRecord(s->done[lane], st);
   if (e != cudaSuccess) return sfail(UCN_ECUDA, "serve launch: %s", cudaGetErrorString(e));

@@ -77,7 +77,8 @@ class Server:
         c.scp_iters, c.admm_iters, c.stop = int(s["scp_iters"]), int(s["admm_iters"]), int(s.get("stop", 0))
         c.tr_init, c.tr_min, c.tr_max, c.w_d = float(s["tr_init"]), float(s["tr_min"]), float(s["tr_max"]), float(s["w_d"])
         c.defect_tol, c.step_tol, c.timeout_s = float(s["defect_tol"]), float(s["step_tol"]), float(timeout_s)
-        self.model, self.nx, self.nu = model, (12 if model == 1 else 7), (4 if model == 1 else 3)
+        self.model = model
+        self.nx, self.nu = {1: (12, 4), 2: (7, 3), 3: (13, 4), 4: (14, 3)}[model]
         self.h = C.c_void_p()
         rc = self.L.ucn_serve_create(C.byref(c), C.byref(self.h))
         if rc != ucn.UCN_OK:
@@ -107,7 +108,7 @@ class Server:
         N = int(prob.N[b])
         r = Request()
         r.horizon, r.dt = N, float(prob.dt[b])
-        r.n_obs = int(prob.nobs[b]) if prob.model == 1 else 0
+        r.n_obs = int(prob.nobs[b]) if prob.model in (1, 3) else 0
         r.model_params = d(prob.params[b])
         r.Q_diag, r.x_ref, r.R_diag, r.u_ref = d(prob.Qd[b]), d(prob.xref[b]), d(prob.Rd[b]), d(prob.uref[b])
         r.QN_diag, r.qN = d(prob.QNd[b]), d(prob.qN[b])

@@ -107,8 +107,36 @@ def test_mixed_stream_completes_and_matches_the_oracle():
         srv = servers[p.model]
         rc, t = srv.submit(p); srv.pump()
         res = wait(srv, t, int(p.N[0]))
-        xr, ur, sr, _ = oracle.scp_solve(p)
+        q = p.subset(np.arange(1))
+        q.settings = dict(qs if p.model == 1 else ms)        # the server's schedule, not the request's
+        xr, ur, sr, _ = oracle.scp_solve(q)
         if sr[0, 0] <= 1e-5 and res["stats"]["defect"] <= 1e-5:
             assert np.abs(res["x"] - xr).max() <= 1e-3 * max(1.0, np.abs(xr).max())
     for s in servers.values():
         s.close()
+
+
+@pytest.mark.parametrize("kind", ["quat13", "mars14"])
+def test_paper_model_variants_serve_like_the_oracle(kind):
+    # the 13-state quaternion quadrotor and the 6-DOF Mars lander through the slot pool,
+    # two requests at once, each checked against the oracle's solve of the same problem
+    if kind == "quat13":
+        probs = [W.quat_study(1, seed=s, scp_iters=6, admm_iters=40) for s in (5, 6)]
+        srv = serving.Server(3, ucn.UCN_PREC_FP64, max_slots=4, max_horizon=60, max_obs=3, lanes=2,
+                             settings=probs[0].settings)
+    else:
+        probs = [W.mars6_batch(1, seed=s, settings=dict(scp_iters=6, admm_iters=40, stop=0)) for s in (7, 8)]
+        srv = serving.Server(4, ucn.UCN_PREC_FP64, max_slots=4, max_horizon=40, lanes=2, settings=probs[0].settings)
+    tickets = []
+    for p in probs:
+        rc, t = srv.submit(p); assert rc == ucn.UCN_OK
+        tickets.append(t)
+    srv.pump()
+    for p, t in zip(probs, tickets):
+        N = int(p.N[0])
+        res = wait(srv, t, N)
+        xr, ur, sr, _ = oracle.scp_solve(p)
+        assert np.abs(res["x"] - xr).max() <= 1e-9 * max(1.0, np.abs(xr).max())
+        assert np.abs(res["u"] - ur).max() <= 1e-9 * max(1.0, np.abs(ur).max())
+        assert res["stats"]["scp_iters"] == int(sr[0, 7])
+    srv.close()
