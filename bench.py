@@ -55,13 +55,19 @@ def mars_mirror_flops():
     return 64
 
 
+# what builds and launches the Mars FP32 fused kernel: its translation unit, the headers
+# it includes and the host code that lays out and launches it
+TRAFFIC_SOURCES = ("include/ucn.h",) + tuple("paper_2603_10711_gb300/csrc/" + f for f in (
+    "ucn_api.cu", "ucn_internal.h", "ucn_kernels.cuh", "ucn_lanes.cuh", "ucn_launch.cuh", "ucn_mars32.cu",
+    "ucn_math.cuh"))
+
+
 def kernel_sources_sha256():
-    import glob
     import hashlib
     h = hashlib.sha256()
-    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2603_10711_gb300", "csrc", "*"))):
+    for p in TRAFFIC_SOURCES:
         h.update(os.path.basename(p).encode())
-        h.update(open(p, "rb").read())
+        h.update(open(os.path.join(ROOT, p), "rb").read())
     return h.hexdigest()
 
 
@@ -72,7 +78,7 @@ def recorded_traffic():
         rec = json.load(open(os.path.join(ROOT, "profiles", "scp_kernel_traffic.json")))
     except Exception:
         return None
-    return rec["traffic_bytes_per_launch"] if rec.get("csrc_sha256") == kernel_sources_sha256() else None
+    return rec["traffic_bytes_per_launch"] if rec.get("sources_sha256") == kernel_sources_sha256() else None
 
 
 def measured_peaks():
