@@ -243,6 +243,31 @@ ucn_status ucn_scp_solve(ucn_problem* prob, const double* x0_d, const double* u0
 ucn_status ucn_mpc_shift(ucn_problem* prob, const double* x_d, const double* u_d, double* xg_d, double* ug_d,
                          void* stream);
 
+/* ---------------------------------------------------------------- double-float check
+ * The FP32 path carries its nominal trajectory and does its per-SCP-iteration
+ * rollout, defects and merits in double-float arithmetic (a value is hi + lo,
+ * two floats, ~48 significant bits) instead of FP64, whose rate on this GPU is
+ * 1/64 of FP32.  This entry point runs that arithmetic on given inputs so that
+ * it can be checked against FP64 (not in the paper; a diagnostic).
+ *   op  UCN_DF_ADD, _SUB, _MUL, _DIV: out[k] = a[k] op b[k];
+ *       UCN_DF_SQRT: out[k] = sqrt(a[k]); UCN_DF_ROUND: out[k] = a[k] through
+ *       double-float and back;
+ *       UCN_DF_RK4 + model: one RK4 step of the model (Eq. (1b)) per row,
+ *       a = x [n][nx], b = u [n][nu], prm = model_params [8], step h;
+ *       out = [n][nx].
+ * Inputs are rounded to double-float first, results returned as doubles.
+ * Device pointers, asynchronous on `stream`.  Errors: UCN_EINVAL (unknown op
+ * or model, null pointer, n < 0), UCN_ECUDA. */
+#define UCN_DF_ADD 0
+#define UCN_DF_SUB 1
+#define UCN_DF_MUL 2
+#define UCN_DF_DIV 3
+#define UCN_DF_SQRT 4
+#define UCN_DF_ROUND 5
+#define UCN_DF_RK4 100
+ucn_status ucn_df_check(int op, const double* a_d, const double* b_d, const double* prm_d, double h, long long n,
+                        double* out_d, void* stream);
+
 /* Scratch held by ucn_scp_solve_noalloc on every GPU that loads the library. */
 #define UCN_NOALLOC_SCRATCH_BYTES (64ull << 20)
 

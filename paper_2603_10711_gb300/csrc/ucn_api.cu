@@ -82,6 +82,15 @@ Layout make_layout(int model, int nodes, int max_obs, int tsize, bool reg_mats) 
   L.DS = dfixed | 1;
   L.tbytes = round_up((long long)nodes * L.NS * tsize, 16);
   L.bytes = round_up(L.tbytes + (long long)nodes * L.DS * 8, 16);
+  // FP32 path: the instance's constants in double-float (CB block) follow
+  L.oC = -1;
+  if (tsize == 4) {
+    const int cb = model == UCN_MODEL_QUAD12 ? CB<Quad12>::END
+                   : model == UCN_MODEL_QUAT13 ? CB<Quat13>::END
+                   : model == UCN_MODEL_MARS14 ? CB<Mars14>::END : CB<Mars7>::END;
+    L.oC = L.bytes;
+    L.bytes = round_up(L.bytes + 8LL * cb, 16);
+  }
   return L;
 }
 

@@ -61,8 +61,21 @@ struct Rec {
   static constexpr int Xlo = C + NX, Xhi = Xlo + NX, Ulo = Xhi + NX, Uhi = Ulo + NU;
   static constexpr int X = Uhi + NU, Z = X + NX, Lam = Z + NX, Mu = Lam + NX, Xh = Mu + NX, Nux = Xh + NX;
   static constexpr int U = Nux + NX, Uh = U + NU, Nuu = Uh + NU, Ex1 = Nuu + NU, Ex2 = Ex1 + NX, END = Ex2 + NX;
-  // FP64 record: nominal state, nominal control, candidate state (exchange)
+  // wide record (FP64, or double-float on the FP32 path): nominal state,
+  // nominal control, candidate state (exchange)
   static constexpr int Xbar = 0, Ubar = NX, Xc = NX + NU, DEND = 2 * NX + NU;
+};
+
+// Per-instance constants of the FP32 path in double-float, converted from the
+// problem's FP64 arrays once per launch, so that the per-SCP-iteration setup,
+// rollout and cost read no FP64 value: bounds, references, boundary states,
+// cost weights, model parameters and the RK4 step h, h/2, h/6.
+template <class M>
+struct CB {
+  static constexpr int NX = M::NX, NU = M::NU;
+  static constexpr int Xlo = 0, Xhi = NX, Xref = 2 * NX, Xinit = 3 * NX, Xtgt = 4 * NX, Qd = 5 * NX, QNd = 6 * NX,
+                       QN = 7 * NX, Ulo = 8 * NX, Uhi = Ulo + NU, Uref = Uhi + NU, Rd = Uref + NU, Prm = Rd + NU,
+                       Step = Prm + 8, END = Step + 3;
 };
 
 // Where the per-node records of one instance live.
@@ -76,19 +89,26 @@ struct Layout {
   int oA, oB, oH;          // matrices in the record (-1 when register-resident)
   long long tbytes;        // bytes of the T region (16-byte multiple)
   long long bytes;         // bytes per instance
+  long long oC;            // byte offset of the CB block (FP32 path; -1 without)
 };
 
-// Per-thread view of its node.
+// Per-thread view of its node.  W is the wide type of the precision (FP64,
+// or double-float for the FP32 path).
 template <class T, bool AOS>
 struct Node {
+  typedef typename WideOf<T>::type W;
   T* t;          // T region base
-  double* d;     // FP64 region base
+  W* d;          // wide region base
+  W* c;          // CB block of the instance (FP32 path)
   int S, NS, DS, i, N;
   __device__ __forceinline__ T& at(int off, int k) const { return AOS ? t[i * NS + off + k] : t[(long long)(off + k) * S + i]; }
   __device__ __forceinline__ T& nb(int off, int k, int j) const { return AOS ? t[j * NS + off + k] : t[(long long)(off + k) * S + j]; }
-  __device__ __forceinline__ double& dat(int off, int k) const { return AOS ? d[i * DS + off + k] : d[(long long)(off + k) * S + i]; }
-  __device__ __forceinline__ double& dnb(int off, int k, int j) const { return AOS ? d[j * DS + off + k] : d[(long long)(off + k) * S + j]; }
+  __device__ __forceinline__ W& dat(int off, int k) const { return AOS ? d[i * DS + off + k] : d[(long long)(off + k) * S + i]; }
+  __device__ __forceinline__ W& dnb(int off, int k, int j) const { return AOS ? d[j * DS + off + k] : d[(long long)(off + k) * S + j]; }
 };
+
+// The wide path of a compute type is double-float (FP32 path).
+template <class T> struct IsDF { static constexpr bool value = std::is_same<typename WideOf<T>::type, DF>::value; };
 
 // Models whose mirror sets are the linearised obstacles (the quadrotors); the
 // others carry the Mars sets (thrust ball and lower bound, glide-slope cone).
@@ -204,7 +224,9 @@ __device__ __forceinline__ Inst<T> make_inst(const ProblemDev& P, int b) {
 // Per-instance scalars in shared memory.
 struct InstShared {
   double red[32][6];
-  double Jn, radius, fac;
+  double Jn, radius;
+  double rho[3];            // rho_eq, rho_dyn, rho_geo of the SCP iteration
+  float rhof[3];            // the same in FP32 (no conversion per thread)
   double out[8];
   int fail;
   int accept, stop, status;
@@ -358,6 +380,9 @@ __device__ __forceinline__ GroupShared* group_slot() {
   }
 }
 
+template <class T> __device__ __forceinline__ T rho_of(const InstShared& sh, int r) { return (T)sh.rho[r]; }
+template <> __device__ __forceinline__ float rho_of<float>(const InstShared& sh, int r) { return sh.rhof[r]; }
+
 // ------------------------------------------------------------------ block reduction
 // Reduces up to 6 FP64 values: entries [0, nsum) summed, [nsum, nval) maxed.
 __device__ __forceinline__ void block_reduce(InstShared& sh, double* v, int nsum, int nval) {
@@ -378,35 +403,127 @@ __device__ __forceinline__ void block_reduce(InstShared& sh, double* v, int nsum
   __syncthreads();
 }
 
+// The same over double-float sums s[0, ns) and float maxima m[0, nm) (ns + nm
+// <= 6), with no FP64 instruction outside warp 0's final conversion; every
+// thread receives the sums then the maxima, as doubles, in out[0, ns + nm).
+// The double-float sum is commutative bit for bit (its error terms are exact),
+// so every lane of a butterfly holds the same bits.
+__device__ __forceinline__ DF df_shfl_xor(DF a, int o) {
+  return {__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
+}
+__device__ __forceinline__ void block_reduce_df(InstShared& sh, DF* s, int ns, float* m, int nm, double* out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  DF* red = reinterpret_cast<DF*>(&sh.red[0][0]);
+  float* redf = reinterpret_cast<float*>(&sh.red[0][0]);
+  for (int o = 16; o > 0; o >>= 1) {
+    for (int k = 0; k < ns; ++k) s[k] = df_add(s[k], df_shfl_xor(s[k], o));
+    for (int k = 0; k < nm; ++k) m[k] = fmaxf(m[k], __shfl_xor_sync(0xffffffffu, m[k], o));
+  }
+  if (lane == 0) {
+    for (int k = 0; k < ns; ++k) red[warp * 6 + k] = s[k];
+    for (int k = 0; k < nm; ++k) redf[2 * (warp * 6 + ns + k)] = m[k];
+  }
+  __syncthreads();
+  if (warp == 0) {
+    DF a[6];
+    float b[6];
+    for (int k = 0; k < ns; ++k) a[k] = (lane < nw) ? red[lane * 6 + k] : DF();
+    for (int k = 0; k < nm; ++k) b[k] = (lane < nw) ? redf[2 * (lane * 6 + ns + k)] : -INFINITY;
+    for (int o = 16; o > 0; o >>= 1) {
+      for (int k = 0; k < ns; ++k) a[k] = df_add(a[k], df_shfl_xor(a[k], o));
+      for (int k = 0; k < nm; ++k) b[k] = fmaxf(b[k], __shfl_xor_sync(0xffffffffu, b[k], o));
+    }
+    if (lane == 0) {
+      for (int k = 0; k < ns; ++k) sh.out[k] = df_to_double(a[k]);
+      for (int k = 0; k < nm; ++k) sh.out[ns + k] = (double)b[k];
+    }
+  }
+  __syncthreads();
+  for (int k = 0; k < ns + nm; ++k) out[k] = sh.out[k];
+  __syncthreads();
+}
+
 // ------------------------------------------------------------------ per-node pieces
+// The CB block of the instance (FP32 path): every thread of the CTA converts
+// a share of the entries; the caller synchronises before the first use.
+template <class M, class T, bool AOS>
+__device__ void stage_consts(const Node<T, AOS>& nd, const ProblemDev& P, int b) {
+  if constexpr (IsDF<T>::value) {
+    typedef CB<M> C;
+    constexpr int NX = M::NX, NU = M::NU;
+    for (int e = threadIdx.x; e < C::END; e += blockDim.x) {
+      double v;
+      if (e < C::Xhi) v = P.xlo[b * NX + e - C::Xlo];
+      else if (e < C::Xref) v = P.xhi[b * NX + e - C::Xhi];
+      else if (e < C::Xinit) v = P.xref[b * NX + e - C::Xref];
+      else if (e < C::Xtgt) v = P.xinit[b * NX + e - C::Xinit];
+      else if (e < C::Qd) v = P.xtarget[b * NX + e - C::Xtgt];
+      else if (e < C::QNd) v = P.Qd[b * NX + e - C::Qd];
+      else if (e < C::QN) v = P.QNd[b * NX + e - C::QNd];
+      else if (e < C::Ulo) v = P.qN[b * NX + e - C::QN];
+      else if (e < C::Uhi) v = P.ulo[b * NU + e - C::Ulo];
+      else if (e < C::Uref) v = P.uhi[b * NU + e - C::Uhi];
+      else if (e < C::Rd) v = P.uref[b * NU + e - C::Uref];
+      else if (e < C::Prm) v = P.Rd[b * NU + e - C::Rd];
+      else if (e < C::Step) v = P.params[b * 8 + e - C::Prm];
+      else v = P.dt[b] * (e == C::Step ? 1.0 : e == C::Step + 1 ? 0.5 : 1.0 / 6.0);
+      nd.c[e] = df_from(v);
+    }
+  }
+}
+
 // Nominal of node i from packed global trajectories.
 template <class M, class T, bool AOS>
 __device__ void load_nominal(const Node<T, AOS>& nd, const Layout& L, const double* xg, const double* ug,
                              long long xo, long long uo) {
-  for (int j = 0; j < M::NX; ++j) nd.dat(Rec<M>::Xbar, j) = xg[(xo + nd.i) * M::NX + j];
+  typedef typename Node<T, AOS>::W W;
+  for (int j = 0; j < M::NX; ++j) nd.dat(Rec<M>::Xbar, j) = wide_from_double<W>(xg[(xo + nd.i) * M::NX + j]);
   if (nd.i < nd.N)
-    for (int j = 0; j < M::NU; ++j) nd.dat(Rec<M>::Ubar, j) = ug[(uo + nd.i) * M::NU + j];
+    for (int j = 0; j < M::NU; ++j) nd.dat(Rec<M>::Ubar, j) = wide_from_double<W>(ug[(uo + nd.i) * M::NU + j]);
 }
 
 template <class M, class T, bool AOS>
-__device__ __forceinline__ void read_nominal(const Node<T, AOS>& nd, bool hasU, double* xb, double* ub) {
+__device__ __forceinline__ void read_nominal(const Node<T, AOS>& nd, bool hasU, typename Node<T, AOS>::W* xb,
+                                             typename Node<T, AOS>::W* ub) {
+  typedef typename Node<T, AOS>::W W;
 #pragma unroll
   for (int j = 0; j < M::NX; ++j) xb[j] = nd.dat(Rec<M>::Xbar, j);
 #pragma unroll
-  for (int j = 0; j < M::NU; ++j) ub[j] = hasU ? nd.dat(Rec<M>::Ubar, j) : 0.0;
+  for (int j = 0; j < M::NU; ++j) ub[j] = hasU ? nd.dat(Rec<M>::Ubar, j) : W();
 }
+
+// One RK4 step of the instance's model in the wide type: FP64 from the problem
+// arrays, or double-float from the CB block.
+template <class M, class T, bool AOS>
+__device__ __forceinline__ void rk4_wide(const Node<T, AOS>& nd, const ProblemDev& P, int b,
+                                         const typename Node<T, AOS>::W* x, const typename Node<T, AOS>::W* u,
+                                         typename Node<T, AOS>::W* xn) {
+  if constexpr (IsDF<T>::value) {
+    typedef CB<M> C;
+    rk4h<M, DF, DF, DF>(nd.c + C::Prm, nd.c[C::Step], nd.c[C::Step + 1], nd.c[C::Step + 2], x, u, xn);
+  } else {
+    rk4<M, double>(P.params + b * 8, P.dt[b], x, u, xn);
+  }
+}
+
+// |a| of a wide value, as a double for the FP64 path and rounded to float for
+// double-float (maxima and tolerance tests need no more).
+__device__ __forceinline__ double wide_abs_round(double a) { return fabs(a); }
+__device__ __forceinline__ float wide_abs_round(DF a) { return fabsf(df_to_float(a)); }
+__device__ __forceinline__ double wide_abs(double a) { return fabs(a); }
+__device__ __forceinline__ DF wide_abs(DF a) { return a.hi < 0.0f ? df_neg(a) : a; }
 
 // A_i, B_i by forward-mode differentiation of the RK4 map (Eq. (2b)), in T.
 template <class M, class T, bool AOS, class MS>
 __device__ __forceinline__ void node_jacobians(const Node<T, AOS>& nd, const MS& MT, const T* prm, double h) {
   constexpr int NX = M::NX, NU = M::NU;
-  double xb[NX], ub[NU];
+  typename Node<T, AOS>::W xb[NX], ub[NU];
   read_nominal<M, T, AOS>(nd, true, xb, ub);
   T xt[NX], ut[NU];
 #pragma unroll
-  for (int j = 0; j < NX; ++j) xt[j] = (T)xb[j];
+  for (int j = 0; j < NX; ++j) xt[j] = wide_to<T>(xb[j]);
 #pragma unroll
-  for (int j = 0; j < NU; ++j) ut[j] = (T)ub[j];
+  for (int j = 0; j < NU; ++j) ut[j] = wide_to<T>(ub[j]);
 #pragma unroll
   for (int dir = 0; dir < NX + NU; ++dir) {
     T col[NX];
@@ -427,9 +544,38 @@ __device__ void node_setup(const Node<T, AOS>& nd, const Layout& L, const Proble
                            T re, T rg, NodeConst<M, T>& K) {
   constexpr int NX = M::NX, NU = M::NU;
   const int i = nd.i, N = nd.N;
-  double xb[NX], ub[NU];
+  typename Node<T, AOS>::W xb[NX], ub[NU];
   read_nominal<M, T, AOS>(nd, i < N, xb, ub);
   const bool term = (i == N);
+  if constexpr (IsDF<T>::value) {
+    // the same quantities from the CB block in double-float, rounded to T
+    typedef CB<M> C;
+    const DF* cb = nd.c;
+    const T rad = (T)radius;
+    for (int j = 0; j < NX; ++j) {
+      const DF w = term ? cb[C::QNd + j] : cb[C::Qd + j];
+      DF gq = df_mul(df_sub(xb[j], cb[C::Xref + j]), w);
+      if (term) gq = df_add(gq, cb[C::QN + j]);
+      K.q[j] = df_to_float(gq);
+      K.hd[j] = df_to_float(w) + rg + (i > 0 ? re : T(0));
+      T lo = fmaxf(wide_diff<T>(cb[C::Xlo + j], xb[j]), -rad);
+      T hi = fminf(wide_diff<T>(cb[C::Xhi + j], xb[j]), rad);
+      if (i == 0) lo = hi = wide_diff<T>(cb[C::Xinit + j], xb[j]);
+      else if (term && P.tmask[b * NX + j]) lo = hi = wide_diff<T>(cb[C::Xtgt + j], xb[j]);
+      nd.at(Rec<M>::Xlo, j) = lo;
+      nd.at(Rec<M>::Xhi, j) = hi;
+    }
+    for (int j = 0; j < NU; ++j) { K.q[NX + j] = T(0); K.hd[NX + j] = T(1); }
+    if (!term) {
+      for (int j = 0; j < NU; ++j) {
+        const DF w = cb[C::Rd + j];
+        K.q[NX + j] = df_to_float(df_mul(df_sub(ub[j], cb[C::Uref + j]), w));
+        K.hd[NX + j] = df_to_float(w) + rg;
+        nd.at(Rec<M>::Ulo, j) = fmaxf(wide_diff<T>(cb[C::Ulo + j], ub[j]), -rad);
+        nd.at(Rec<M>::Uhi, j) = fminf(wide_diff<T>(cb[C::Uhi + j], ub[j]), rad);
+      }
+    }
+  } else {
   for (int j = 0; j < NX; ++j) {
     const double w = term ? P.QNd[b * NX + j] : P.Qd[b * NX + j];
     K.q[j] = (T)(w * (xb[j] - P.xref[b * NX + j]) + (term ? P.qN[b * NX + j] : 0.0));
@@ -450,13 +596,15 @@ __device__ void node_setup(const Node<T, AOS>& nd, const Layout& L, const Proble
       nd.at(Rec<M>::Uhi, j) = (T)(fmin(P.uhi[b * NU + j], ub[j] + radius) - ub[j]);
     }
   }
+  }
   if constexpr (IsQuad<M>::value) {
     // Obstacle j linearised about the nominal position: n = (p - c)/|p - c|,
     // keep n^T p >= n^T c + r; in deviations n^T dp >= n^T (c - pbar) + r.
     const int no = P.nobs[b];
     for (int j = 0; j < no; ++j) {
       const double* c = &P.obs_c[((long long)b * P.max_obs + j) * 3];
-      const T dp[3] = {(T)(xb[0] - c[0]), (T)(xb[1] - c[1]), (T)(xb[2] - c[2])};
+      // offset from the centre in T (|p - c| is of the order of the radius: no cancellation)
+      const T dp[3] = {wide_to<T>(xb[0]) - (T)c[0], wide_to<T>(xb[1]) - (T)c[1], wide_to<T>(xb[2]) - (T)c[2]};
       T nv[3] = {dp[0], dp[1], dp[2]};
       T nn = sqrt_(nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2]);
       if (nn < T(1e-12)) { nv[0] = 0; nv[1] = 0; nv[2] = 1; nn = 1; }
@@ -471,15 +619,15 @@ __device__ void node_setup(const Node<T, AOS>& nd, const Layout& L, const Proble
   } else {
     // nominal position / thrust in T, the offsets of the cone and ball projections
     constexpr int RC = IsMars14<M>::value ? 1 : 0;   // position's first state
-    for (int k = 0; k < 3; ++k) nd.at(L.oMd, 4 + k) = (T)xb[RC + k];
-    for (int k = 0; k < 3; ++k) nd.at(L.oMd, 7 + k) = (T)ub[k];
+    for (int k = 0; k < 3; ++k) nd.at(L.oMd, 4 + k) = wide_to<T>(xb[RC + k]);
+    for (int k = 0; k < 3; ++k) nd.at(L.oMd, 7 + k) = wide_to<T>(ub[k]);
     if constexpr (IsMars14<M>::value) {   // nominal (qy, qz) and body rates
-      for (int k = 0; k < 2; ++k) nd.at(L.oMd, M14::D_Q + k) = (T)xb[9 + k];
-      for (int k = 0; k < 3; ++k) nd.at(L.oMd, M14::D_W + k) = (T)xb[11 + k];
+      for (int k = 0; k < 2; ++k) nd.at(L.oMd, M14::D_Q + k) = wide_to<T>(xb[9 + k]);
+      for (int k = 0; k < 3; ++k) nd.at(L.oMd, M14::D_W + k) = wide_to<T>(xb[11 + k]);
     }
     // Thrust lower bound |T| >= Tmin linearised: nbar^T T >= Tmin, nbar = Tbar/|Tbar|.
     if (!term) {
-      const T ut[3] = {(T)ub[0], (T)ub[1], (T)ub[2]};
+      const T ut[3] = {wide_to<T>(ub[0]), wide_to<T>(ub[1]), wide_to<T>(ub[2])};
       T nv[3] = {ut[0], ut[1], ut[2]};
       T nn = sqrt_(nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2]);
       if (nn < T(1e-12)) { nv[0] = 1; nv[1] = 0; nv[2] = 0; nn = 1; }
@@ -757,7 +905,7 @@ __device__ __forceinline__ void node_rhs(const Node<T, AOS>& nd, const MS& MT, c
 // mode projects G xi alone and leaves the duals untouched.
 template <class M, class T, bool AOS, int n>
 __device__ __forceinline__ void node_mirrors(const Node<T, AOS>& nd, const Layout& L, const Inst<T>& I,
-                                             T rg, const T* xi, bool reseed, bool want_res, T* sv, double& rp) {
+                                             T rg, const T* xi, bool reseed, bool want_res, T* sv, T& rp) {
   constexpr int NX = M::NX;
   const T irg = T(1) / rg;
   if constexpr (IsQuad<M>::value) {
@@ -773,7 +921,7 @@ __device__ __forceinline__ void node_mirrors(const Node<T, AOS>& nd, const Layou
       if (want_res) {
         const T ds = rg * (s - so);
         sv[0] += n0 * ds; sv[1] += n1 * ds; sv[2] += n2 * ds;
-        rp += (double)(y - s) * (double)(y - s);
+        rp += (y - s) * (y - s);
       }
     }
   } else {
@@ -791,7 +939,7 @@ __device__ __forceinline__ void node_mirrors(const Node<T, AOS>& nd, const Layou
         const T so = nd.at(L.oS, k);
         nd.at(L.oS, k) = s;
         nd.at(L.oNus, k) += rg * (xi[RC + k] - s);
-        if (want_res) { sv[RC + k] += rg * (s - so); rp += (double)(xi[RC + k] - s) * (double)(xi[RC + k] - s); }
+        if (want_res) { sv[RC + k] += rg * (s - so); rp += (xi[RC + k] - s) * (xi[RC + k] - s); }
       }
     }
     if constexpr (IsMars14<M>::value) {
@@ -807,7 +955,7 @@ __device__ __forceinline__ void node_mirrors(const Node<T, AOS>& nd, const Layou
           const T so = nd.at(L.oS, M14::S_TILT + k);
           nd.at(L.oS, M14::S_TILT + k) = s;
           nd.at(L.oNus, M14::S_TILT + k) += rg * (xi[9 + k] - s);
-          if (want_res) { sv[9 + k] += rg * (s - so); rp += (double)(xi[9 + k] - s) * (double)(xi[9 + k] - s); }
+          if (want_res) { sv[9 + k] += rg * (s - so); rp += (xi[9 + k] - s) * (xi[9 + k] - s); }
         }
       }
       if (I.wball) {  // |omega| <= omega_max
@@ -821,7 +969,7 @@ __device__ __forceinline__ void node_mirrors(const Node<T, AOS>& nd, const Layou
           const T so = nd.at(L.oS, M14::S_W + k);
           nd.at(L.oS, M14::S_W + k) = s;
           nd.at(L.oNus, M14::S_W + k) += rg * (xi[11 + k] - s);
-          if (want_res) { sv[11 + k] += rg * (s - so); rp += (double)(xi[11 + k] - s) * (double)(xi[11 + k] - s); }
+          if (want_res) { sv[11 + k] += rg * (s - so); rp += (xi[11 + k] - s) * (xi[11 + k] - s); }
         }
       }
       if constexpr (n > NX) {
@@ -835,7 +983,7 @@ __device__ __forceinline__ void node_mirrors(const Node<T, AOS>& nd, const Layou
             const T so = nd.at(L.oS, M14::S_GIM + k);
             nd.at(L.oS, M14::S_GIM + k) = s;
             nd.at(L.oNus, M14::S_GIM + k) += rg * (xi[NX + k] - s);
-            if (want_res) { sv[NX + k] += rg * (s - so); rp += (double)(xi[NX + k] - s) * (double)(xi[NX + k] - s); }
+            if (want_res) { sv[NX + k] += rg * (s - so); rp += (xi[NX + k] - s) * (xi[NX + k] - s); }
           }
         }
       }
@@ -851,7 +999,7 @@ __device__ __forceinline__ void node_mirrors(const Node<T, AOS>& nd, const Layou
           const T so = nd.at(L.oS, 3 + k);
           nd.at(L.oS, 3 + k) = s;
           nd.at(L.oNus, 3 + k) += rg * (xi[NX + k] - s);
-          if (want_res) { sv[NX + k] += rg * (s - so); rp += (double)(xi[NX + k] - s) * (double)(xi[NX + k] - s); }
+          if (want_res) { sv[NX + k] += rg * (s - so); rp += (xi[NX + k] - s) * (xi[NX + k] - s); }
         }
       }
       if (I.half) {  // linearised |T| >= Tmin
@@ -867,7 +1015,7 @@ __device__ __forceinline__ void node_mirrors(const Node<T, AOS>& nd, const Layou
           if (want_res) {
             const T ds = rg * (s - so);
             sv[NX] += n0 * ds; sv[NX + 1] += n1 * ds; sv[NX + 2] += n2 * ds;
-            rp += (double)(y - s) * (double)(y - s);
+            rp += (y - s) * (y - s);
           }
         }
       }
@@ -880,7 +1028,7 @@ template <class M, class T, bool AOS>
 __device__ void node_reseed(const Node<T, AOS>& nd, const Layout& L, const Inst<T>& I) {
   constexpr int NX = M::NX, NU = M::NU;
   T xi[NX + NU], sv[NX + NU];
-  double rp = 0.0;
+  T rp = T(0);
   for (int j = 0; j < NX; ++j) xi[j] = nd.at(Rec<M>::Xh, j);
   if (nd.i < nd.N) {
     for (int j = 0; j < NU; ++j) xi[NX + j] = nd.at(Rec<M>::Uh, j);
@@ -893,8 +1041,9 @@ __device__ void node_reseed(const Node<T, AOS>& nd, const Layout& L, const Inst<
 // ------------------------------------------------------------------ the ADMM loop
 // One iteration of Steps 1-4 (Sec. III-B) over the CTA's instance; all
 // threads of the CTA call it.  The LAST instance also accumulates the primal
-// and dual residuals in FP64 (a separate instantiation, so that the hot loop
-// carries no FP64 instruction, not even a predicated-off one).
+// and dual residuals (a separate instantiation, so that the hot loop carries
+// no residual work, not even predicated off); the sums are in the compute
+// type, as they are only reported.
 //
 // GROUP: the CTA is one scenario of a group whose scenarios share the first
 // control (Sec. IV-A).  After Step 3 the node-0 thread of every CTA publishes
@@ -905,7 +1054,7 @@ __device__ void node_reseed(const Node<T, AOS>& nd, const Layout& L, const Inst<
 template <class M, class T, bool AOS, bool REFINE, bool LAST, bool GROUP, class MS>
 __device__ __forceinline__ void admm_iteration(const Node<T, AOS>& nd, const MS& MT, const Layout& L, const Inst<T>& I,
                                                const NodeConst<M, T>& K, bool active, T re, T rd, T rg,
-                                               T irg, T ired, double& rp, double& rdl, GroupShared* G,
+                                               T irg, T ired, T& rp, T& rdl, GroupShared* G,
                                                GroupX& X, const ProblemDev& P) {
   constexpr int NX = M::NX, NU = M::NU, NN = NX + NU;
   const int i = nd.i, N = nd.N;
@@ -978,7 +1127,7 @@ __device__ __forceinline__ void admm_iteration(const Node<T, AOS>& nd, const MS&
           dz[j] = z - zo;
           if (last) {
             sv[j] += re * dz[j];
-            rp += (double)(x[j] - z) * (double)(x[j] - z) + (double)(z - dd) * (double)(z - dd);
+            rp += (x[j] - z) * (x[j] - z) + (z - dd) * (z - dd);
           }
         }
       }
@@ -987,7 +1136,7 @@ __device__ __forceinline__ void admm_iteration(const Node<T, AOS>& nd, const MS&
       for (int j = 0; j < NX; ++j) {
         const T nux = nd.at(Rec<M>::Nux, j);
         const T xh = clampv(x[j] + nux * irg, nd.at(Rec<M>::Xlo, j), nd.at(Rec<M>::Xhi, j));
-        if (last) { sv[j] += rg * (xh - nd.at(Rec<M>::Xh, j)); rp += (double)(x[j] - xh) * (double)(x[j] - xh); }
+        if (last) { sv[j] += rg * (xh - nd.at(Rec<M>::Xh, j)); rp += (x[j] - xh) * (x[j] - xh); }
         nd.at(Rec<M>::Xh, j) = xh;
         nd.at(Rec<M>::Nux, j) = nux + rg * (x[j] - xh);
       }
@@ -997,7 +1146,7 @@ __device__ __forceinline__ void admm_iteration(const Node<T, AOS>& nd, const MS&
           const T nuu = nd.at(Rec<M>::Nuu, j);
           if constexpr (GROUP) {
             if (i == 0) {   // sum of arguments | max of lower bounds | max of -upper bounds
-              const double ub = nd.dat(Rec<M>::Ubar, j);
+              const double ub = wide_to_double(nd.dat(Rec<M>::Ubar, j));
               double* m = G->mine[X.epoch & 1];
               m[j] = ub + (double)(x[NX + j] + nuu * irg);
               m[NU + j] = ub + (double)nd.at(Rec<M>::Ulo, j);
@@ -1006,7 +1155,7 @@ __device__ __forceinline__ void admm_iteration(const Node<T, AOS>& nd, const MS&
             }
           }
           const T uh = clampv(x[NX + j] + nuu * irg, nd.at(Rec<M>::Ulo, j), nd.at(Rec<M>::Uhi, j));
-          if (last) { sv[NX + j] += rg * (uh - nd.at(Rec<M>::Uh, j)); rp += (double)(x[NX + j] - uh) * (double)(x[NX + j] - uh); }
+          if (last) { sv[NX + j] += rg * (uh - nd.at(Rec<M>::Uh, j)); rp += (x[NX + j] - uh) * (x[NX + j] - uh); }
           nd.at(Rec<M>::Uh, j) = uh;
           nd.at(Rec<M>::Nuu, j) = nuu + rg * (x[NX + j] - uh);
         }
@@ -1023,9 +1172,9 @@ __device__ __forceinline__ void admm_iteration(const Node<T, AOS>& nd, const MS&
         for (int j = 0; j < NU; ++j) {
           const double v = fmin(fmax(tot[j] / (double)P.group, tot[NU + j]), -tot[2 * NU + j]);
           G->u0[j] = v;
-          const T uh = (T)(v - nd.dat(Rec<M>::Ubar, j));
+          const T uh = (T)(v - wide_to_double(nd.dat(Rec<M>::Ubar, j)));
           const T nuu = nd.at(Rec<M>::Nuu, j);
-          if (last) { sv[NX + j] += rg * (uh - nd.at(Rec<M>::Uh, j)); rp += (double)(x[NX + j] - uh) * (double)(x[NX + j] - uh); }
+          if (last) { sv[NX + j] += rg * (uh - nd.at(Rec<M>::Uh, j)); rp += (x[NX + j] - uh) * (x[NX + j] - uh); }
           nd.at(Rec<M>::Uh, j) = uh;
           nd.at(Rec<M>::Nuu, j) = nuu + rg * (x[NX + j] - uh);
         }
@@ -1058,7 +1207,7 @@ __device__ __forceinline__ void admm_iteration(const Node<T, AOS>& nd, const MS&
         }
 #pragma unroll
         for (int j = 0; j < NN; ++j)
-          if (j < NX || i < N) rdl += (double)sv[j] * (double)sv[j];
+          if (j < NX || i < N) rdl += sv[j] * sv[j];
       }
     }
     if (active && i >= 1) {
@@ -1070,20 +1219,26 @@ __device__ __forceinline__ void admm_iteration(const Node<T, AOS>& nd, const MS&
 }
 
 // `iters` iterations of Steps 1-4; the primal and dual residuals of the last
-// one (FP64 sums) are returned in res[0..1].
+// one are returned, squared, in res[0..1].
 template <class M, class T, bool AOS, bool REFINE, bool GROUP = false, class MS>
 __device__ __forceinline__ void admm_iterations(const Node<T, AOS>& nd, const MS& MT, const Layout& L, const Inst<T>& I,
                                 const NodeConst<M, T>& K, bool active, T re, T rd, T rg, int iters,
                                 InstShared& sh, double* res, GroupShared* G, GroupX& X, const ProblemDev& P) {
   const T irg = T(1) / rg, ired = T(1) / (re + rd);
-  double rp = 0.0, rdl = 0.0;
+  T rp = T(0), rdl = T(0);   // residual sums in the compute type (reported only)
   for (int it = 0; it + 1 < iters; ++it)
     admm_iteration<M, T, AOS, REFINE, false, GROUP>(nd, MT, L, I, K, active, re, rd, rg, irg, ired, rp, rdl, G, X, P);
   admm_iteration<M, T, AOS, REFINE, true, GROUP>(nd, MT, L, I, K, active, re, rd, rg, irg, ired, rp, rdl, G, X, P);
-  double v[2] = {rp, rdl};
-  block_reduce(sh, v, 2, 2);
-  res[0] = sqrt(v[0]);
-  res[1] = sqrt(v[1]);
+  // squared norms (the root is taken once, when they are reported)
+  if constexpr (IsDF<T>::value) {
+    DF s2[2] = {df_from(rp), df_from(rdl)};
+    block_reduce_df(sh, s2, 2, nullptr, 0, res);
+  } else {
+    double v[2] = {(double)rp, (double)rdl};
+    block_reduce(sh, v, 2, 2);
+    res[0] = v[0];
+    res[1] = v[1];
+  }
 }
 
 // Publish mu_i + rho_dyn z_i before the first Step 1.
@@ -1118,7 +1273,7 @@ __device__ void node_export(const Node<T, AOS>& nd, const Layout& L, const Probl
   double* pnuu = pnux + nX;   double* ps = pnuu + nU;
   double* pnus = ps + (long long)(N + 1) * L.MB * 3;
   for (int j = 0; j < NX; ++j) {
-    const double xb = nd.dat(Rec<M>::Xbar, j);
+    const double xb = wide_to_double(nd.dat(Rec<M>::Xbar, j));
     px[i * NX + j] = xb + (double)nd.at(Rec<M>::X, j);
     pz[i * NX + j] = (i >= 1) ? xb + (double)nd.at(Rec<M>::Z, j) : 0.0;
     plam[i * NX + j] = (i >= 1) ? (double)nd.at(Rec<M>::Lam, j) : 0.0;
@@ -1128,7 +1283,7 @@ __device__ void node_export(const Node<T, AOS>& nd, const Layout& L, const Probl
   }
   if (i < N)
     for (int j = 0; j < NU; ++j) {
-      const double ub = nd.dat(Rec<M>::Ubar, j);
+      const double ub = wide_to_double(nd.dat(Rec<M>::Ubar, j));
       pu[i * NU + j] = ub + (double)nd.at(Rec<M>::U, j);
       puh[i * NU + j] = ub + (double)nd.at(Rec<M>::Uh, j);
       pnuu[i * NU + j] = (double)nd.at(Rec<M>::Nuu, j);
@@ -1139,7 +1294,7 @@ __device__ void node_export(const Node<T, AOS>& nd, const Layout& L, const Probl
   if constexpr (IsQuad<M>::value) {
     for (int j = 0; j < P.nobs[b]; ++j) {
       double np = 0.0;
-      for (int k = 0; k < 3; ++k) np += (double)nd.at(L.oMd, ObsStride<T>::value * j + k) * nd.dat(Rec<M>::Xbar, k);
+      for (int k = 0; k < 3; ++k) np += (double)nd.at(L.oMd, ObsStride<T>::value * j + k) * wide_to_double(nd.dat(Rec<M>::Xbar, k));
       si[3 * j] = (double)nd.at(L.oS, j) + np;
       ni[3 * j] = (double)nd.at(L.oNus, j);
     }
@@ -1147,38 +1302,38 @@ __device__ void node_export(const Node<T, AOS>& nd, const Layout& L, const Probl
     // blocks as the problem's sets: glide cone, tilt, body rate, thrust ball, thrust lower bound, gimbal
     const double* st = &P.sets[b * UCN_SET_PARAMS];
     if (st[2] > 0.0)
-      for (int k = 0; k < 3; ++k) { si[k] = (double)nd.at(L.oS, k) + nd.dat(Rec<M>::Xbar, 1 + k); ni[k] = (double)nd.at(L.oNus, k); }
+      for (int k = 0; k < 3; ++k) { si[k] = (double)nd.at(L.oS, k) + wide_to_double(nd.dat(Rec<M>::Xbar, 1 + k)); ni[k] = (double)nd.at(L.oNus, k); }
     if (st[4] > 0.0)
       for (int k = 0; k < 2; ++k) {
-        si[3 + k] = (double)nd.at(L.oS, M14::S_TILT + k) + nd.dat(Rec<M>::Xbar, 9 + k);
+        si[3 + k] = (double)nd.at(L.oS, M14::S_TILT + k) + wide_to_double(nd.dat(Rec<M>::Xbar, 9 + k));
         ni[3 + k] = (double)nd.at(L.oNus, M14::S_TILT + k);
       }
     if (st[5] > 0.0)
       for (int k = 0; k < 3; ++k) {
-        si[6 + k] = (double)nd.at(L.oS, M14::S_W + k) + nd.dat(Rec<M>::Xbar, 11 + k);
+        si[6 + k] = (double)nd.at(L.oS, M14::S_W + k) + wide_to_double(nd.dat(Rec<M>::Xbar, 11 + k));
         ni[6 + k] = (double)nd.at(L.oNus, M14::S_W + k);
       }
     if (i < N && st[1] > 0.0)
-      for (int k = 0; k < 3; ++k) { si[9 + k] = (double)nd.at(L.oS, 3 + k) + nd.dat(Rec<M>::Ubar, k); ni[9 + k] = (double)nd.at(L.oNus, 3 + k); }
+      for (int k = 0; k < 3; ++k) { si[9 + k] = (double)nd.at(L.oS, 3 + k) + wide_to_double(nd.dat(Rec<M>::Ubar, k)); ni[9 + k] = (double)nd.at(L.oNus, 3 + k); }
     if (i < N && st[0] > 0.0) {
       double np = 0.0;
-      for (int k = 0; k < 3; ++k) np += (double)nd.at(L.oMd, k) * nd.dat(Rec<M>::Ubar, k);
+      for (int k = 0; k < 3; ++k) np += (double)nd.at(L.oMd, k) * wide_to_double(nd.dat(Rec<M>::Ubar, k));
       si[12] = (double)nd.at(L.oS, 6) + np;
       ni[12] = (double)nd.at(L.oNus, 6);
     }
     if (i < N && st[3] > 0.0)
       for (int k = 0; k < 3; ++k) {
-        si[15 + k] = (double)nd.at(L.oS, M14::S_GIM + k) + nd.dat(Rec<M>::Ubar, k);
+        si[15 + k] = (double)nd.at(L.oS, M14::S_GIM + k) + wide_to_double(nd.dat(Rec<M>::Ubar, k));
         ni[15 + k] = (double)nd.at(L.oNus, M14::S_GIM + k);
       }
   } else {
     if (P.sets[b * UCN_SET_PARAMS + 2] > 0.0)
-      for (int k = 0; k < 3; ++k) { si[k] = (double)nd.at(L.oS, k) + nd.dat(Rec<M>::Xbar, k); ni[k] = (double)nd.at(L.oNus, k); }
+      for (int k = 0; k < 3; ++k) { si[k] = (double)nd.at(L.oS, k) + wide_to_double(nd.dat(Rec<M>::Xbar, k)); ni[k] = (double)nd.at(L.oNus, k); }
     if (i < N && P.sets[b * UCN_SET_PARAMS + 1] > 0.0)
-      for (int k = 0; k < 3; ++k) { si[3 + k] = (double)nd.at(L.oS, 3 + k) + nd.dat(Rec<M>::Ubar, k); ni[3 + k] = (double)nd.at(L.oNus, 3 + k); }
+      for (int k = 0; k < 3; ++k) { si[3 + k] = (double)nd.at(L.oS, 3 + k) + wide_to_double(nd.dat(Rec<M>::Ubar, k)); ni[3 + k] = (double)nd.at(L.oNus, 3 + k); }
     if (i < N && P.sets[b * UCN_SET_PARAMS + 0] > 0.0) {
       double np = 0.0;
-      for (int k = 0; k < 3; ++k) np += (double)nd.at(L.oMd, k) * nd.dat(Rec<M>::Ubar, k);
+      for (int k = 0; k < 3; ++k) np += (double)nd.at(L.oMd, k) * wide_to_double(nd.dat(Rec<M>::Ubar, k));
       si[6] = (double)nd.at(L.oS, 6) + np;
       ni[6] = (double)nd.at(L.oNus, 6);
     }
@@ -1197,7 +1352,7 @@ __device__ void node_import(const Node<T, AOS>& nd, const Layout& L, const Probl
   const double* pnuu = pnux + nX; const double* ps = pnuu + nU;
   const double* pnus = ps + (long long)(N + 1) * L.MB * 3;
   for (int j = 0; j < NX; ++j) {
-    const double xb = nd.dat(Rec<M>::Xbar, j);
+    const double xb = wide_to_double(nd.dat(Rec<M>::Xbar, j));
     nd.at(Rec<M>::X, j) = (T)(px[i * NX + j] - xb);
     nd.at(Rec<M>::Z, j) = (i >= 1) ? (T)(pz[i * NX + j] - xb) : T(0);
     nd.at(Rec<M>::Lam, j) = (T)plam[i * NX + j];
@@ -1206,7 +1361,7 @@ __device__ void node_import(const Node<T, AOS>& nd, const Layout& L, const Probl
     nd.at(Rec<M>::Nux, j) = (T)pnux[i * NX + j];
   }
   for (int j = 0; j < NU; ++j) {
-    const double ub = (i < N) ? nd.dat(Rec<M>::Ubar, j) : 0.0;
+    const double ub = (i < N) ? wide_to_double(nd.dat(Rec<M>::Ubar, j)) : 0.0;
     nd.at(Rec<M>::U, j) = (i < N) ? (T)(pu[i * NU + j] - ub) : T(0);
     nd.at(Rec<M>::Uh, j) = (i < N) ? (T)(puh[i * NU + j] - ub) : T(0);
     nd.at(Rec<M>::Nuu, j) = (i < N) ? (T)pnuu[i * NU + j] : T(0);
@@ -1217,38 +1372,38 @@ __device__ void node_import(const Node<T, AOS>& nd, const Layout& L, const Probl
   if constexpr (IsQuad<M>::value) {
     for (int j = 0; j < P.nobs[b]; ++j) {
       double np = 0.0;
-      for (int k = 0; k < 3; ++k) np += (double)nd.at(L.oMd, ObsStride<T>::value * j + k) * nd.dat(Rec<M>::Xbar, k);
+      for (int k = 0; k < 3; ++k) np += (double)nd.at(L.oMd, ObsStride<T>::value * j + k) * wide_to_double(nd.dat(Rec<M>::Xbar, k));
       nd.at(L.oS, j) = (T)(si[3 * j] - np);
       nd.at(L.oNus, j) = (T)ni[3 * j];
     }
   } else if constexpr (IsMars14<M>::value) {
     // blocks as exported: glide cone, tilt, body rate, thrust ball, thrust lower bound, gimbal
-    for (int k = 0; k < 3; ++k) { nd.at(L.oS, k) = (T)(si[k] - nd.dat(Rec<M>::Xbar, 1 + k)); nd.at(L.oNus, k) = (T)ni[k]; }
+    for (int k = 0; k < 3; ++k) { nd.at(L.oS, k) = (T)(si[k] - wide_to_double(nd.dat(Rec<M>::Xbar, 1 + k))); nd.at(L.oNus, k) = (T)ni[k]; }
     for (int k = 0; k < 2; ++k) {
-      nd.at(L.oS, M14::S_TILT + k) = (T)(si[3 + k] - nd.dat(Rec<M>::Xbar, 9 + k));
+      nd.at(L.oS, M14::S_TILT + k) = (T)(si[3 + k] - wide_to_double(nd.dat(Rec<M>::Xbar, 9 + k)));
       nd.at(L.oNus, M14::S_TILT + k) = (T)ni[3 + k];
     }
     for (int k = 0; k < 3; ++k) {
-      nd.at(L.oS, M14::S_W + k) = (T)(si[6 + k] - nd.dat(Rec<M>::Xbar, 11 + k));
+      nd.at(L.oS, M14::S_W + k) = (T)(si[6 + k] - wide_to_double(nd.dat(Rec<M>::Xbar, 11 + k)));
       nd.at(L.oNus, M14::S_W + k) = (T)ni[6 + k];
     }
     if (i < N) {
-      for (int k = 0; k < 3; ++k) { nd.at(L.oS, 3 + k) = (T)(si[9 + k] - nd.dat(Rec<M>::Ubar, k)); nd.at(L.oNus, 3 + k) = (T)ni[9 + k]; }
+      for (int k = 0; k < 3; ++k) { nd.at(L.oS, 3 + k) = (T)(si[9 + k] - wide_to_double(nd.dat(Rec<M>::Ubar, k))); nd.at(L.oNus, 3 + k) = (T)ni[9 + k]; }
       double np = 0.0;
-      for (int k = 0; k < 3; ++k) np += (double)nd.at(L.oMd, k) * nd.dat(Rec<M>::Ubar, k);
+      for (int k = 0; k < 3; ++k) np += (double)nd.at(L.oMd, k) * wide_to_double(nd.dat(Rec<M>::Ubar, k));
       nd.at(L.oS, 6) = (T)(si[12] - np);
       nd.at(L.oNus, 6) = (T)ni[12];
       for (int k = 0; k < 3; ++k) {
-        nd.at(L.oS, M14::S_GIM + k) = (T)(si[15 + k] - nd.dat(Rec<M>::Ubar, k));
+        nd.at(L.oS, M14::S_GIM + k) = (T)(si[15 + k] - wide_to_double(nd.dat(Rec<M>::Ubar, k)));
         nd.at(L.oNus, M14::S_GIM + k) = (T)ni[15 + k];
       }
     }
   } else {
-    for (int k = 0; k < 3; ++k) { nd.at(L.oS, k) = (T)(si[k] - nd.dat(Rec<M>::Xbar, k)); nd.at(L.oNus, k) = (T)ni[k]; }
+    for (int k = 0; k < 3; ++k) { nd.at(L.oS, k) = (T)(si[k] - wide_to_double(nd.dat(Rec<M>::Xbar, k))); nd.at(L.oNus, k) = (T)ni[k]; }
     if (i < N) {
-      for (int k = 0; k < 3; ++k) { nd.at(L.oS, 3 + k) = (T)(si[3 + k] - nd.dat(Rec<M>::Ubar, k)); nd.at(L.oNus, 3 + k) = (T)ni[3 + k]; }
+      for (int k = 0; k < 3; ++k) { nd.at(L.oS, 3 + k) = (T)(si[3 + k] - wide_to_double(nd.dat(Rec<M>::Ubar, k))); nd.at(L.oNus, 3 + k) = (T)ni[3 + k]; }
       double np = 0.0;
-      for (int k = 0; k < 3; ++k) np += (double)nd.at(L.oMd, k) * nd.dat(Rec<M>::Ubar, k);
+      for (int k = 0; k < 3; ++k) np += (double)nd.at(L.oMd, k) * wide_to_double(nd.dat(Rec<M>::Ubar, k));
       nd.at(L.oS, 6) = (T)(si[6] - np);
       nd.at(L.oNus, 6) = (T)ni[6];
     }
@@ -1288,7 +1443,8 @@ __device__ __forceinline__ Node<T, SMEM> make_node(const ProblemDev& P, const La
   unsigned char* base = SMEM ? smem : (unsigned char*)(P.ws + (long long)b * L.bytes);
   Node<T, SMEM> nd;
   nd.t = (T*)base;
-  nd.d = (double*)(base + L.tbytes);
+  nd.d = (typename Node<T, SMEM>::W*)(base + L.tbytes);
+  nd.c = L.oC >= 0 ? (typename Node<T, SMEM>::W*)(base + L.oC) : nullptr;
   nd.S = L.S;
   nd.NS = L.NS;
   nd.DS = L.DS;
@@ -1352,6 +1508,7 @@ __global__ void __launch_bounds__(MAX_THREADS) admm_kernel(ProblemDev P, Layout 
   const bool active = i <= N;
   const long long xo = P.xoff[b], uo = P.uoff[b];
   if (threadIdx.x == 0) sh.fail = 0;
+  stage_consts<M, T, AOS>(nd, P, b);
   if (active) load_nominal<M, T, AOS>(nd, L, xbar, ubar, xo, uo);
   __syncthreads();
   if (active && i < N) {
@@ -1366,9 +1523,9 @@ __global__ void __launch_bounds__(MAX_THREADS) admm_kernel(ProblemDev P, Layout 
     }
     for (int r = 0; r < NX; ++r) {
       double acc = dg[g * NX + r];
-      for (int c = 0; c < NX; ++c) acc += Ag[g * NX * NX + r * NX + c] * nd.dat(Rec<M>::Xbar, c);
-      for (int c = 0; c < NU; ++c) acc += Bg[g * NX * NU + r * NU + c] * nd.dat(Rec<M>::Ubar, c);
-      nd.at(Rec<M>::C, r) = (T)(acc - nd.dnb(Rec<M>::Xbar, r, i + 1));
+      for (int c = 0; c < NX; ++c) acc += Ag[g * NX * NX + r * NX + c] * wide_to_double(nd.dat(Rec<M>::Xbar, c));
+      for (int c = 0; c < NU; ++c) acc += Bg[g * NX * NU + r * NU + c] * wide_to_double(nd.dat(Rec<M>::Ubar, c));
+      nd.at(Rec<M>::C, r) = (T)(acc - wide_to_double(nd.dnb(Rec<M>::Xbar, r, i + 1)));
     }
   }
   const T re = (T)P.rho_eq, rd = (T)P.rho_dyn, rg = (T)P.rho_geo;
@@ -1393,22 +1550,51 @@ __global__ void __launch_bounds__(MAX_THREADS) admm_kernel(ProblemDev P, Layout 
   if (!sh.fail) admm_iterations<M, T, AOS, REFINE>(nd, MT, L, I, K, active, re, rd, rg, iters, sh, r2, nullptr, X, P);
   if (active) {
     node_export<M, T, AOS>(nd, L, P, b, P.state_abs + P.soff[b]);
-    for (int j = 0; j < NX; ++j) xhat[(xo + i) * NX + j] = nd.dat(Rec<M>::Xbar, j) + (double)nd.at(Rec<M>::Xh, j);
+    for (int j = 0; j < NX; ++j) xhat[(xo + i) * NX + j] = wide_to_double(nd.dat(Rec<M>::Xbar, j)) + (double)nd.at(Rec<M>::Xh, j);
     if (i < N)
-      for (int j = 0; j < NU; ++j) uhat[(uo + i) * NU + j] = nd.dat(Rec<M>::Ubar, j) + (double)nd.at(Rec<M>::Uh, j);
+      for (int j = 0; j < NU; ++j) uhat[(uo + i) * NU + j] = wide_to_double(nd.dat(Rec<M>::Ubar, j)) + (double)nd.at(Rec<M>::Uh, j);
   }
   if (threadIdx.x == 0) {
-    res[2 * b] = r2[0];
-    res[2 * b + 1] = r2[1];
+    res[2 * b] = sqrt(r2[0]);
+    res[2 * b + 1] = sqrt(r2[1]);
     status[b] = sh.fail ? ST_NUMERIC : ST_OK;
   }
 }
 
-// Nonlinear cost l(x_i,u_i) (or phi(x_N)) of node i in FP64.
-template <class M, class T>
-__device__ __forceinline__ double node_cost(const ProblemDev& P, const Inst<T>& I, int b, int i, int N,
-                                            const double* x, const double* u) {
+// Nonlinear cost l(x_i,u_i) (or phi(x_N)) of node i in the wide type (FP64
+// from the problem arrays, or double-float from the CB block).
+template <class M, class T, bool AOS>
+__device__ __forceinline__ typename Node<T, AOS>::W node_cost(const Node<T, AOS>& nd, const ProblemDev& P,
+                                                              const Inst<T>& I, int b, int i, int N,
+                                                              const typename Node<T, AOS>::W* x,
+                                                              const typename Node<T, AOS>::W* u) {
   constexpr int NX = M::NX, NU = M::NU;
+  if constexpr (IsDF<T>::value) {
+    typedef CB<M> C;
+    const DF* cb = nd.c;
+    DF c;
+    if (i == N && !I.term_quad) {
+      for (int j = 0; j < NX; ++j) c = df_add(c, df_mul(cb[C::QN + j], x[j]));
+      return c;
+    }
+    if (i < N && !I.run_cost) return c;
+    if (i < N) {
+      for (int j = 0; j < NX; ++j) {
+        const DF e = df_sub(x[j], cb[C::Xref + j]);
+        c = df_add(c, df_mul(df_mul(e, e), df_mul(cb[C::Qd + j], 0.5f)));
+      }
+      for (int j = 0; j < NU; ++j) {
+        const DF e = df_sub(u[j], cb[C::Uref + j]);
+        c = df_add(c, df_mul(df_mul(e, e), df_mul(cb[C::Rd + j], 0.5f)));
+      }
+    } else {
+      for (int j = 0; j < NX; ++j) {
+        const DF e = df_sub(x[j], cb[C::Xref + j]);
+        c = df_add(c, df_add(df_mul(df_mul(e, e), df_mul(cb[C::QNd + j], 0.5f)), df_mul(cb[C::QN + j], x[j])));
+      }
+    }
+    return c;
+  } else {
   double c = 0.0;
   if (i == N && !I.term_quad) {
     for (int j = 0; j < NX; ++j) c += P.qN[b * NX + j] * x[j];
@@ -1425,13 +1611,169 @@ __device__ __forceinline__ double node_cost(const ProblemDev& P, const Inst<T>& 
     }
   }
   return c;
+  }
+}
+
+// ------------------------------------------------------------------ per-SCP-iteration steps
+// The steps of an SCP iteration outside the ADMM loop, shared by the fused
+// kernels (one thread per node, `act` when the thread has one; every thread of
+// the CTA calls them).  Wide arithmetic: FP64, or double-float on the FP32
+// path, whose sums are reduced in double-float and handed over as doubles.
+
+// Start of a solve: c_i = RK4(xbar_i, ubar_i) - xbar_{i+1} and J(nominal) in sh.Jn.
+template <class M, class T, bool AOS>
+__device__ void scp_start(const Node<T, AOS>& nd, const ProblemDev& P, const Inst<T>& I, int b, bool act,
+                          InstShared& sh) {
+  typedef typename Node<T, AOS>::W W;
+  constexpr int NX = M::NX, NU = M::NU;
+  const int i = nd.i, N = nd.N;
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  W ac[2] = {W(), W()};
+  if (act) {
+    W xb[NX], ub[NU];
+    read_nominal<M, T, AOS>(nd, i < N, xb, ub);
+    ac[0] = node_cost<M, T, AOS>(nd, P, I, b, i, N, xb, ub);
+    if (i < N) {
+      W fn[NX];
+      rk4_wide<M, T, AOS>(nd, P, b, xb, ub, fn);
+      for (int j = 0; j < NX; ++j) {
+        const W e = fn[j] - nd.dnb(Rec<M>::Xbar, j, i + 1);
+        nd.at(Rec<M>::C, j) = wide_to<T>(e);
+        ac[1] = ac[1] + wide_abs(e);
+      }
+    }
+  }
+  if constexpr (IsDF<T>::value) {
+    block_reduce_df(sh, ac, 2, nullptr, 0, acc);
+  } else {
+    acc[0] = ac[0]; acc[1] = ac[1];
+    block_reduce(sh, acc, 2, 2);
+  }
+  if (threadIdx.x == 0) sh.Jn = acc[0] + P.w_d * acc[1];
+}
+
+// The candidate (x-hat, u-hat) of an SCP iteration: its trajectory (xc, uc),
+// defects fc_i = RK4(xc_i, uc_i) - xc_{i+1}, and CTA totals in v: cost, l1
+// defect, l1 defect of the linear model | max defect, max step.
+template <class M, class T, bool AOS, bool GROUP, class MS>
+__device__ void scp_candidate(const Node<T, AOS>& nd, const MS& MT, const ProblemDev& P, const Inst<T>& I, int b,
+                              bool act, const GroupShared* G, InstShared& sh, typename Node<T, AOS>::W* xc,
+                              typename Node<T, AOS>::W* uc, typename Node<T, AOS>::W* fc, double* v) {
+  typedef typename Node<T, AOS>::W W;
+  constexpr int NX = M::NX, NU = M::NU;
+  const int i = nd.i, N = nd.N;
+  if (act) {
+    for (int j = 0; j < NX; ++j) { xc[j] = wide_add(nd.dat(Rec<M>::Xbar, j), nd.at(Rec<M>::Xh, j)); nd.dat(Rec<M>::Xc, j) = xc[j]; }
+    for (int j = 0; j < NU; ++j) uc[j] = (i < N) ? wide_add(nd.dat(Rec<M>::Ubar, j), nd.at(Rec<M>::Uh, j)) : W();
+    if constexpr (GROUP) {
+      // the shared first control exactly (bitwise equal across the group)
+      if (i == 0)
+        for (int j = 0; j < NU; ++j) uc[j] = wide_from_double<W>(G->u0[j]);
+    }
+  }
+  __syncthreads();
+  W vs[3] = {W(), W(), W()};                    // cost, nl1, lin1
+  decltype(wide_abs_round(W())) dinf = 0;       // max |defect|
+  T st = T(0), lin1 = T(0);
+  if (act) {
+    vs[0] = node_cost<M, T, AOS>(nd, P, I, b, i, N, xc, uc);
+    for (int j = 0; j < NX; ++j) st = maxv(st, absv(nd.at(Rec<M>::Xh, j)));
+    if (i < N) {
+      for (int j = 0; j < NU; ++j) st = maxv(st, absv(nd.at(Rec<M>::Uh, j)));
+      rk4_wide<M, T, AOS>(nd, P, b, xc, uc, fc);
+#pragma unroll
+      for (int r = 0; r < NX; ++r) {
+        fc[r] = fc[r] - nd.dnb(Rec<M>::Xc, r, i + 1);
+        vs[1] = vs[1] + wide_abs(fc[r]);
+        dinf = maxv(dinf, wide_abs_round(fc[r]));
+        T lin = nd.at(Rec<M>::C, r) - nd.nb(Rec<M>::Xh, r, i + 1);
+#pragma unroll
+        for (int c = 0; c < NX; ++c) lin += MT.A(r, c) * nd.at(Rec<M>::Xh, c);
+#pragma unroll
+        for (int c = 0; c < NU; ++c) lin += MT.B(r, c) * nd.at(Rec<M>::Uh, c);
+        lin1 += absv(lin);
+      }
+    }
+  }
+  if constexpr (IsDF<T>::value) {
+    vs[2] = df_from(lin1);
+    float mx[2] = {dinf, st};
+    block_reduce_df(sh, vs, 3, mx, 2, v);
+  } else {
+    v[0] = vs[0]; v[1] = vs[1]; v[2] = (double)lin1; v[3] = dinf; v[4] = (double)st;
+    block_reduce(sh, v, 3, 5);
+  }
+}
+
+// Accepted: the candidate becomes the nominal, its defect becomes c_i, and the
+// deviations are re-based on it.
+template <class M, class T, bool AOS>
+__device__ void scp_move_nominal(const Node<T, AOS>& nd, const Layout& L, const ProblemDev& P, int b,
+                                 const typename Node<T, AOS>::W* xc, const typename Node<T, AOS>::W* uc,
+                                 const typename Node<T, AOS>::W* fc) {
+  constexpr int NX = M::NX, NU = M::NU;
+  const int i = nd.i, N = nd.N;
+  node_rebase_mirrors<M, T, AOS>(nd, L, P, b);
+  for (int j = 0; j < NX; ++j) {
+    const T xh = nd.at(Rec<M>::Xh, j);
+    nd.dat(Rec<M>::Xbar, j) = xc[j];
+    nd.at(Rec<M>::X, j) -= xh;
+    if (i >= 1) nd.at(Rec<M>::Z, j) -= xh;
+    nd.at(Rec<M>::Xh, j) = T(0);
+    if (i < N) nd.at(Rec<M>::C, j) = wide_to<T>(fc[j]);
+  }
+  if (i < N)
+    for (int j = 0; j < NU; ++j) {
+      const T uh = nd.at(Rec<M>::Uh, j);
+      nd.dat(Rec<M>::Ubar, j) = uc[j];
+      nd.at(Rec<M>::U, j) -= uh;
+      nd.at(Rec<M>::Uh, j) = T(0);
+    }
+}
+
+// End of a solve: the returned (last accepted) trajectory, its cost, l1 and
+// max defect (w[0..2], CTA totals, FP64 sums: once per launch) and the
+// exported ADMM state.
+template <class M, class T, bool AOS>
+__device__ void scp_finish(const Node<T, AOS>& nd, const Layout& L, const ProblemDev& P, const Inst<T>& I, int b,
+                           bool act, long long xo, long long uo, double* xout, double* uout, InstShared& sh,
+                           double* w) {
+  typedef typename Node<T, AOS>::W W;
+  constexpr int NX = M::NX, NU = M::NU;
+  const int i = nd.i, N = nd.N;
+  if (act) {
+    W xb[NX], ub[NU];
+    read_nominal<M, T, AOS>(nd, i < N, xb, ub);
+    w[0] = wide_to_double(node_cost<M, T, AOS>(nd, P, I, b, i, N, xb, ub));
+    if (i < N) {
+      W fn[NX];
+      rk4_wide<M, T, AOS>(nd, P, b, xb, ub, fn);
+      for (int j = 0; j < NX; ++j) {
+        const double e = fabs(wide_to_double(fn[j] - nd.dnb(Rec<M>::Xbar, j, i + 1)));
+        w[1] += e;
+        w[2] = fmax(w[2], e);
+      }
+    }
+    for (int j = 0; j < NX; ++j) {
+      double xv = wide_to_double(xb[j]);
+      // a node-0 state at the initial state (Eq. (1c)) is returned bit for bit
+      // as given, although double-float holds only ~48 of its 53 bits
+      if constexpr (IsDF<T>::value)
+        if (i == 0 && df_sub(nd.c[CB<M>::Xinit + j], xb[j]).hi == 0.0f) xv = P.xinit[b * NX + j];
+      xout[(xo + i) * NX + j] = xv;
+    }
+    if (i < N)
+      for (int j = 0; j < NU; ++j) uout[(uo + i) * NU + j] = wide_to_double(ub[j]);
+    node_export<M, T, AOS>(nd, L, P, b, P.state_abs + P.soff[b]);
+  }
+  block_reduce(sh, w, 2, 3);
 }
 
 // The whole SCP solve of one instance per CTA (Sec. III-A + III-B): per SCP
 // iteration, linearise (T), assemble + factor (T), admm_iters ADMM
-// iterations (T, FP64 residual sums), then the FP64 rollout, defects, merit
-// and trust-region acceptance, and the nominal update -- without leaving
-// the kernel.
+// iterations (T), then the rollout, defects, merit and trust-region
+// acceptance and the nominal update in the wide type (FP64, or double-float on
+// the FP32 path) -- without leaving the kernel.
 //
 // GROUP: CTA k of group g solves scenario k of problem g (instance g * group
 // + k); the group's CTAs are launched as thread-block clusters so that they are
@@ -1463,35 +1805,19 @@ __global__ void __launch_bounds__(MAX_THREADS) scp_kernel(ProblemDev P, Layout L
   Node<T, AOS> nd = make_node<T, SMEM>(P, L, smem, b);
   MatsFor<M, T, AOS> MT;
   init_mats<M, T, AOS>(MT, nd, L);
+  typedef typename Node<T, AOS>::W W;
   const int i = nd.i, N = nd.N;
   const bool active = i <= N;
   const long long xo = P.xoff[b], uo = P.uoff[b];
-  const double* prm = P.params + b * 8;
   const double h = P.dt[b];
   const unsigned long long t0 = globaltimer_ns();
   const Inst<T> I = make_inst<M, T>(P, b);
   NodeConst<M, T> K;
   if (threadIdx.x == 0) { sh.fail = 0; sh.status = ST_OK; sh.radius = P.tr_init; sh.stop = 0; }
+  stage_consts<M, T, AOS>(nd, P, b);
   if (active) load_nominal<M, T, AOS>(nd, L, x0, u0, xo, uo);
   __syncthreads();
-  // c_i = RK4(xbar_i, ubar_i) - xbar_{i+1} and J(nominal)
-  double acc[6] = {0, 0, 0, 0, 0, 0};
-  if (active) {
-    double xb[NX], ub[NU];
-    read_nominal<M, T, AOS>(nd, i < N, xb, ub);
-    acc[0] = node_cost<M, T>(P, I, b, i, N, xb, ub);
-    if (i < N) {
-      double fn[NX];
-      rk4<M, double>(prm, h, xb, ub, fn);
-      for (int j = 0; j < NX; ++j) {
-        const double e = fn[j] - nd.dnb(Rec<M>::Xbar, j, i + 1);
-        nd.at(Rec<M>::C, j) = (T)e;
-        acc[1] += fabs(e);
-      }
-    }
-  }
-  block_reduce(sh, acc, 2, 2);
-  if (threadIdx.x == 0) sh.Jn = acc[0] + P.w_d * acc[1];
+  scp_start<M, T, AOS>(nd, P, I, b, active, sh);
   if (active) node_cold_start<M, T, AOS>(nd, L);
   __syncthreads();
   int accepted = 0, iters_run = 0;
@@ -1503,11 +1829,11 @@ __global__ void __launch_bounds__(MAX_THREADS) scp_kernel(ProblemDev P, Layout L
       double f = 1.0;
       if (P.rho_fac) f = P.rho_fac[k];   // the schedule tabulated at create
       else if (P.rho_final > 0.0 && Kscp > 1) f = pow(P.rho_final / P.rho_geo, (double)k / (double)(Kscp - 1));
-      sh.fac = f;
+      sh.rho[0] = P.rho_eq * f; sh.rho[1] = P.rho_dyn * f; sh.rho[2] = P.rho_geo * f;
+      for (int r = 0; r < 3; ++r) sh.rhof[r] = (float)sh.rho[r];
     }
     __syncthreads();
-    const double fac = sh.fac;
-    const T re = (T)(P.rho_eq * fac), rd = (T)(P.rho_dyn * fac), rg = (T)(P.rho_geo * fac);
+    const T re = rho_of<T>(sh, 0), rd = rho_of<T>(sh, 1), rg = rho_of<T>(sh, 2);
     const double radius = sh.radius;
     if (active) {
       if (i < N) node_jacobians<M, T, AOS>(nd, MT, I.prm, h);
@@ -1529,46 +1855,10 @@ __global__ void __launch_bounds__(MAX_THREADS) scp_kernel(ProblemDev P, Layout L
     if (sh.fail) { if (threadIdx.x == 0) sh.status = ST_NUMERIC; iters_run++; break; }
     admm_iterations<M, T, AOS, REFINE, GROUP>(nd, MT, L, I, K, active, re, rd, rg, P.admm_iters, sh, res, G, X, P);
     ++iters_run;
-    // ---- candidate (x-hat, u-hat): FP64 rollout, defects, cost, linear model
-    double xc[NX], uc[NU], fc[NX];
-    if (active) {
-      for (int j = 0; j < NX; ++j) { xc[j] = nd.dat(Rec<M>::Xbar, j) + (double)nd.at(Rec<M>::Xh, j); nd.dat(Rec<M>::Xc, j) = xc[j]; }
-      for (int j = 0; j < NU; ++j) uc[j] = (i < N) ? nd.dat(Rec<M>::Ubar, j) + (double)nd.at(Rec<M>::Uh, j) : 0.0;
-      if constexpr (GROUP) {
-        // the shared first control exactly (bitwise equal across the group)
-        if (i == 0)
-          for (int j = 0; j < NU; ++j) uc[j] = G->u0[j];
-      }
-    }
-    __syncthreads();
+    // ---- candidate (x-hat, u-hat): wide rollout, defects, cost, linear model
+    W xc[NX], uc[NU], fc[NX];
     double v[6] = {0, 0, 0, 0, 0};   // cost, nl1, lin1 | dinf, step
-    if (active) {
-      v[0] = node_cost<M, T>(P, I, b, i, N, xc, uc);
-      T st = T(0);
-      for (int j = 0; j < NX; ++j) st = maxv(st, absv(nd.at(Rec<M>::Xh, j)));
-      if (i < N) {
-        for (int j = 0; j < NU; ++j) st = maxv(st, absv(nd.at(Rec<M>::Uh, j)));
-        rk4<M, double>(prm, h, xc, uc, fc);
-        double dinf = 0.0;
-        T lin1 = T(0);
-#pragma unroll
-        for (int r = 0; r < NX; ++r) {
-          fc[r] -= nd.dnb(Rec<M>::Xc, r, i + 1);
-          v[1] += fabs(fc[r]);
-          dinf = fmax(dinf, fabs(fc[r]));
-          T lin = nd.at(Rec<M>::C, r) - nd.nb(Rec<M>::Xh, r, i + 1);
-#pragma unroll
-          for (int c = 0; c < NX; ++c) lin += MT.A(r, c) * nd.at(Rec<M>::Xh, c);
-#pragma unroll
-          for (int c = 0; c < NU; ++c) lin += MT.B(r, c) * nd.at(Rec<M>::Uh, c);
-          lin1 += absv(lin);
-        }
-        v[2] = (double)lin1;
-        v[3] = dinf;
-      }
-      v[4] = (double)st;
-    }
-    block_reduce(sh, v, 3, 5);
+    scp_candidate<M, T, AOS, GROUP>(nd, MT, P, I, b, active, G, sh, xc, uc, fc, v);
     bool timed_out = false;
     if (threadIdx.x == 0) timed_out = globaltimer_ns() - t0 > P.timeout_ns;
     double Jn = sh.Jn, Jc = v[0] + P.w_d * v[1], Lc = v[0] + P.w_d * v[2];
@@ -1610,50 +1900,13 @@ __global__ void __launch_bounds__(MAX_THREADS) scp_kernel(ProblemDev P, Layout L
     if (sh.accept) {
       ++accepted;
       if (k < 64) mask |= (1ull << k);
-      if (active) {
-        // new nominal = candidate; its defect becomes c_i; re-base deviations
-        node_rebase_mirrors<M, T, AOS>(nd, L, P, b);
-        for (int j = 0; j < NX; ++j) {
-          const T xh = nd.at(Rec<M>::Xh, j);
-          nd.dat(Rec<M>::Xbar, j) = xc[j];
-          nd.at(Rec<M>::X, j) -= xh;
-          if (i >= 1) nd.at(Rec<M>::Z, j) -= xh;
-          nd.at(Rec<M>::Xh, j) = T(0);
-          if (i < N) nd.at(Rec<M>::C, j) = (T)fc[j];
-        }
-        if (i < N)
-          for (int j = 0; j < NU; ++j) {
-            const T uh = nd.at(Rec<M>::Uh, j);
-            nd.dat(Rec<M>::Ubar, j) = uc[j];
-            nd.at(Rec<M>::U, j) -= uh;
-            nd.at(Rec<M>::Uh, j) = T(0);
-          }
-      }
+      if (active) scp_move_nominal<M, T, AOS>(nd, L, P, b, xc, uc, fc);
     }
     __syncthreads();
     if (sh.stop) break;
   }
-  // defect, cost and merit of the returned (last accepted) trajectory, FP64
   double w[6] = {0, 0, 0, 0, 0, 0};
-  if (active) {
-    double xb[NX], ub[NU];
-    read_nominal<M, T, AOS>(nd, i < N, xb, ub);
-    w[0] = node_cost<M, T>(P, I, b, i, N, xb, ub);
-    if (i < N) {
-      double fn[NX];
-      rk4<M, double>(prm, h, xb, ub, fn);
-      for (int j = 0; j < NX; ++j) {
-        const double e = fabs(fn[j] - nd.dnb(Rec<M>::Xbar, j, i + 1));
-        w[1] += e;
-        w[2] = fmax(w[2], e);
-      }
-    }
-    for (int j = 0; j < NX; ++j) xout[(xo + i) * NX + j] = xb[j];
-    if (i < N)
-      for (int j = 0; j < NU; ++j) uout[(uo + i) * NU + j] = ub[j];
-    node_export<M, T, AOS>(nd, L, P, b, P.state_abs + P.soff[b]);
-  }
-  block_reduce(sh, w, 2, 3);
+  scp_finish<M, T, AOS>(nd, L, P, I, b, active, xo, uo, xout, uout, sh, w);
   if (threadIdx.x == 0) {
     int st = sh.status;
     if constexpr (GROUP) {
@@ -1663,7 +1916,7 @@ __global__ void __launch_bounds__(MAX_THREADS) scp_kernel(ProblemDev P, Layout L
     if (st == ST_OK && !(w[2] <= P.defect_tol)) st = ST_NOTCONV;
     ucn_scp_stats s;
     s.defect = w[2]; s.cost = w[0]; s.merit = w[0] + P.w_d * w[1];
-    s.primal_res = res[0]; s.dual_res = res[1]; s.tr_radius = sh.radius; s.step = last_step;
+    s.primal_res = sqrt(res[0]); s.dual_res = sqrt(res[1]); s.tr_radius = sh.radius; s.step = last_step;
     s.scp_iters = iters_run; s.accepted = accepted; s.accept_mask = mask; s.status = st; s.reserved = 0;
     s.t_start_ns = t0; s.t_end_ns = globaltimer_ns();
     s.pad[0] = s.pad[1] = s.pad[2] = s.pad[3] = 0.0;

@@ -102,13 +102,13 @@ struct LaneH<M, T, TPN, false> {
 template <class M, class T, bool AOS, int TPN, class MS>
 __device__ __forceinline__ void lanes_jacobians(const Node<T, AOS>& nd, const MS& MT, const T* prm, double h, int q) {
   constexpr int NX = M::NX, NU = M::NU;
-  double xb[NX], ub[NU];
+  typename Node<T, AOS>::W xb[NX], ub[NU];
   read_nominal<M, T, AOS>(nd, true, xb, ub);
   T xt[NX], ut[NU];
 #pragma unroll
-  for (int j = 0; j < NX; ++j) xt[j] = (T)xb[j];
+  for (int j = 0; j < NX; ++j) xt[j] = wide_to<T>(xb[j]);
 #pragma unroll
-  for (int j = 0; j < NU; ++j) ut[j] = (T)ub[j];
+  for (int j = 0; j < NU; ++j) ut[j] = wide_to<T>(ub[j]);
   for (int dir = q; dir < NX + NU; dir += TPN) {
     T col[NX];
     rk4_jvp<M, T>(prm, h, xt, ut, dir, col);
@@ -130,6 +130,32 @@ __device__ __forceinline__ void lanes_consts(const Node<T, AOS>& nd, const Probl
   constexpr int NX = M::NX, NU = M::NU;
   const int i = nd.i, N = nd.N;
   const bool term = (i == N);
+  if constexpr (IsDF<T>::value) {
+    typedef CB<M> C;
+    const DF* cb = nd.c;
+#pragma unroll
+    for (int m = 0; m < LR::RX; ++m) {
+      const int j = q + TPN * m;
+      const DF w = term ? cb[C::QNd + j] : cb[C::Qd + j];
+      DF gq = df_mul(df_sub(nd.dat(Rec<M>::Xbar, j), cb[C::Xref + j]), w);
+      if (term) gq = df_add(gq, cb[C::QN + j]);
+      kq[m] = df_to_float(gq);
+      khd[m] = df_to_float(w) + rg + (i > 0 ? re : T(0));
+    }
+#pragma unroll
+    for (int m = 0; m < LR::RU; ++m) {
+      const int j = q + TPN * m;
+      if (term) {
+        kq[LR::RX + m] = T(0);
+        khd[LR::RX + m] = T(1);
+      } else {
+        const DF w = cb[C::Rd + j];
+        kq[LR::RX + m] = df_to_float(df_mul(df_sub(nd.dat(Rec<M>::Ubar, j), cb[C::Uref + j]), w));
+        khd[LR::RX + m] = df_to_float(w) + rg;
+      }
+    }
+    return;
+  } else {
 #pragma unroll
   for (int m = 0; m < LR::RX; ++m) {
     const int j = q + TPN * m;
@@ -148,6 +174,7 @@ __device__ __forceinline__ void lanes_consts(const Node<T, AOS>& nd, const Probl
       khd[LR::RX + m] = (T)P.Rd[b * NU + j] + rg;
     }
   }
+  }
 }
 
 // One iteration of Steps 1-4 over the CTA's instance, lane-parallel.  Every
@@ -156,7 +183,7 @@ __device__ __forceinline__ void lanes_consts(const Node<T, AOS>& nd, const Probl
 template <class M, class T, bool AOS, bool REFINE, bool LAST, bool GROUP, int TPN, class MS, class HR>
 __device__ __forceinline__ void admm_iteration_lanes(const Node<T, AOS>& nd, const MS& MT, const HR& H, const Layout& L,
                                                      const Inst<T>& I, const T* kq, const T* khd, bool active, int q,
-                                                     T re, T rd, T rg, T irg, T ired, double& rp, double& rdl,
+                                                     T re, T rd, T rg, T irg, T ired, T& rp, T& rdl,
                                                      GroupShared* G, GroupX& X, const ProblemDev& P) {
   static_assert(IsQuad<M>::value, "the lane kernel carries the quadrotor's mirror sets");
   using LR = LaneRows<M, TPN>;
@@ -315,7 +342,7 @@ __device__ __forceinline__ void admm_iteration_lanes(const Node<T, AOS>& nd, con
         dz[m] = z - zo;
         if (LAST) {
           sv[m] += re * dz[m];
-          rp += (double)(xo[m] - z) * (double)(xo[m] - z) + (double)(z - dd) * (double)(z - dd);
+          rp += (xo[m] - z) * (xo[m] - z) + (z - dd) * (z - dd);
         }
       }
     }
@@ -325,7 +352,7 @@ __device__ __forceinline__ void admm_iteration_lanes(const Node<T, AOS>& nd, con
       const int j = q + TPN * m;
       const T nux = nd.at(Rec<M>::Nux, j);
       const T xh = clampv(xo[m] + nux * irg, nd.at(Rec<M>::Xlo, j), nd.at(Rec<M>::Xhi, j));
-      if (LAST) { sv[m] += rg * (xh - nd.at(Rec<M>::Xh, j)); rp += (double)(xo[m] - xh) * (double)(xo[m] - xh); }
+      if (LAST) { sv[m] += rg * (xh - nd.at(Rec<M>::Xh, j)); rp += (xo[m] - xh) * (xo[m] - xh); }
       nd.at(Rec<M>::Xh, j) = xh;
       nd.at(Rec<M>::Nux, j) = nux + rg * (xo[m] - xh);
     }
@@ -336,7 +363,7 @@ __device__ __forceinline__ void admm_iteration_lanes(const Node<T, AOS>& nd, con
         const T nuu = nd.at(Rec<M>::Nuu, j);
         if constexpr (GROUP) {
           if (i == 0) {   // sum of arguments | max of lower bounds | max of -upper bounds
-            const double ub = nd.dat(Rec<M>::Ubar, j);
+            const double ub = wide_to_double(nd.dat(Rec<M>::Ubar, j));
             double* mm = G->mine[X.epoch & 1];
             mm[j] = ub + (double)(xo[RX + m] + nuu * irg);
             mm[NU + j] = ub + (double)nd.at(Rec<M>::Ulo, j);
@@ -347,7 +374,7 @@ __device__ __forceinline__ void admm_iteration_lanes(const Node<T, AOS>& nd, con
         const T uh = clampv(xo[RX + m] + nuu * irg, nd.at(Rec<M>::Ulo, j), nd.at(Rec<M>::Uhi, j));
         if (LAST) {
           sv[RX + m] += rg * (uh - nd.at(Rec<M>::Uh, j));
-          rp += (double)(xo[RX + m] - uh) * (double)(xo[RX + m] - uh);
+          rp += (xo[RX + m] - uh) * (xo[RX + m] - uh);
         }
         nd.at(Rec<M>::Uh, j) = uh;
         nd.at(Rec<M>::Nuu, j) = nuu + rg * (xo[RX + m] - uh);
@@ -365,7 +392,7 @@ __device__ __forceinline__ void admm_iteration_lanes(const Node<T, AOS>& nd, con
       if (LAST) {
         const T ds = rg * (s - so);
         msv[0] += n0 * ds; msv[1] += n1 * ds; msv[2] += n2 * ds;
-        rp += (double)(y - s) * (double)(y - s);
+        rp += (y - s) * (y - s);
       }
     }
   }
@@ -382,11 +409,11 @@ __device__ __forceinline__ void admm_iteration_lanes(const Node<T, AOS>& nd, con
         const int j = q + TPN * m;
         const double v = fmin(fmax(tot[j] / (double)P.group, tot[NU + j]), -tot[2 * NU + j]);
         G->u0[j] = v;
-        const T uh = (T)(v - nd.dat(Rec<M>::Ubar, j));
+        const T uh = (T)(v - wide_to_double(nd.dat(Rec<M>::Ubar, j)));
         const T nuu = nd.at(Rec<M>::Nuu, j);
         if (LAST) {
           sv[RX + m] += rg * (uh - nd.at(Rec<M>::Uh, j));
-          rp += (double)(xo[RX + m] - uh) * (double)(xo[RX + m] - uh);
+          rp += (xo[RX + m] - uh) * (xo[RX + m] - uh);
         }
         nd.at(Rec<M>::Uh, j) = uh;
         nd.at(Rec<M>::Nuu, j) = nuu + rg * (xo[RX + m] - uh);
@@ -428,7 +455,7 @@ __device__ __forceinline__ void admm_iteration_lanes(const Node<T, AOS>& nd, con
     if (active) {
 #pragma unroll
       for (int m = 0; m < R; ++m)
-        if (m < RX || i < N) rdl += (double)sv[m] * (double)sv[m];
+        if (m < RX || i < N) rdl += sv[m] * sv[m];
     }
   }
   if (active && i >= 1) {
@@ -447,16 +474,22 @@ __device__ __forceinline__ void admm_iterations_lanes(const Node<T, AOS>& nd, co
                                                       T re, T rd, T rg, int iters, InstShared& sh, double* res,
                                                       GroupShared* G, GroupX& X, const ProblemDev& P) {
   const T irg = T(1) / rg, ired = T(1) / (re + rd);
-  double rp = 0.0, rdl = 0.0;
+  T rp = T(0), rdl = T(0);   // residual sums in the compute type (reported only)
   for (int it = 0; it + 1 < iters; ++it)
     admm_iteration_lanes<M, T, AOS, REFINE, false, GROUP, TPN>(nd, MT, H, L, I, kq, khd, active, q, re, rd, rg, irg,
                                                                ired, rp, rdl, G, X, P);
   admm_iteration_lanes<M, T, AOS, REFINE, true, GROUP, TPN>(nd, MT, H, L, I, kq, khd, active, q, re, rd, rg, irg, ired,
                                                             rp, rdl, G, X, P);
-  double v[2] = {rp, rdl};
-  block_reduce(sh, v, 2, 2);
-  res[0] = sqrt(v[0]);
-  res[1] = sqrt(v[1]);
+  // squared norms (the root is taken once, when they are reported)
+  if constexpr (IsDF<T>::value) {
+    DF s2[2] = {df_from(rp), df_from(rdl)};
+    block_reduce_df(sh, s2, 2, nullptr, 0, res);
+  } else {
+    double v[2] = {(double)rp, (double)rdl};
+    block_reduce(sh, v, 2, 2);
+    res[0] = v[0];
+    res[1] = v[1];
+  }
 }
 
 // Node view of node `i` (the lane kernel maps TPN threads to a node).
@@ -503,8 +536,8 @@ __global__ void __launch_bounds__(LANES_MAX_THREADS) scp_kernel_lanes(ProblemDev
   init_mats<M, T, AOS>(MTd, ndd, L);
   const int id = ndd.i;
   const bool dact = id <= N;
+  typedef typename Node<T, AOS>::W W;
   const long long xo = P.xoff[b], uo = P.uoff[b];
-  const double* prm = P.params + b * 8;
   const double h = P.dt[b];
   const unsigned long long t0 = globaltimer_ns();
   const Inst<T> I = make_inst<M, T>(P, b);
@@ -513,25 +546,10 @@ __global__ void __launch_bounds__(LANES_MAX_THREADS) scp_kernel_lanes(ProblemDev
 #pragma unroll
   for (int m = 0; m < R; ++m) { kq[m] = T(0); khd[m] = T(0); }
   if (threadIdx.x == 0) { sh.fail = 0; sh.status = ST_OK; sh.radius = P.tr_init; sh.stop = 0; }
+  stage_consts<M, T, AOS>(ndd, P, b);
   if (dact) load_nominal<M, T, AOS>(ndd, L, x0, u0, xo, uo);
   __syncthreads();
-  double acc[6] = {0, 0, 0, 0, 0, 0};
-  if (dact) {
-    double xb[NX], ub[NU];
-    read_nominal<M, T, AOS>(ndd, id < N, xb, ub);
-    acc[0] = node_cost<M, T>(P, I, b, id, N, xb, ub);
-    if (id < N) {
-      double fn[NX];
-      rk4<M, double>(prm, h, xb, ub, fn);
-      for (int j = 0; j < NX; ++j) {
-        const double e = fn[j] - ndd.dnb(Rec<M>::Xbar, j, id + 1);
-        ndd.at(Rec<M>::C, j) = (T)e;
-        acc[1] += fabs(e);
-      }
-    }
-  }
-  block_reduce(sh, acc, 2, 2);
-  if (threadIdx.x == 0) sh.Jn = acc[0] + P.w_d * acc[1];
+  scp_start<M, T, AOS>(ndd, P, I, b, dact, sh);
   if (dact) node_cold_start<M, T, AOS>(ndd, L);
   __syncthreads();
   int accepted = 0, iters_run = 0;
@@ -543,11 +561,11 @@ __global__ void __launch_bounds__(LANES_MAX_THREADS) scp_kernel_lanes(ProblemDev
       double f = 1.0;
       if (P.rho_fac) f = P.rho_fac[k];   // the schedule tabulated at create
       else if (P.rho_final > 0.0 && Kscp > 1) f = pow(P.rho_final / P.rho_geo, (double)k / (double)(Kscp - 1));
-      sh.fac = f;
+      sh.rho[0] = P.rho_eq * f; sh.rho[1] = P.rho_dyn * f; sh.rho[2] = P.rho_geo * f;
+      for (int r = 0; r < 3; ++r) sh.rhof[r] = (float)sh.rho[r];
     }
     __syncthreads();
-    const double fac = sh.fac;
-    const T re = (T)(P.rho_eq * fac), rd = (T)(P.rho_dyn * fac), rg = (T)(P.rho_geo * fac);
+    const T re = rho_of<T>(sh, 0), rd = rho_of<T>(sh, 1), rg = rho_of<T>(sh, 2);
     const double radius = sh.radius;
     if (active && i < N) lanes_jacobians<M, T, AOS, TPN>(nd, MT, I.prm, h, q);
     if (active) lanes_consts<M, T, AOS, TPN>(nd, P, b, q, re, rg, kq, khd);
@@ -572,42 +590,10 @@ __global__ void __launch_bounds__(LANES_MAX_THREADS) scp_kernel_lanes(ProblemDev
     admm_iterations_lanes<M, T, AOS, REFINE, GROUP, TPN>(nd, MT, H, L, I, kq, khd, active, q, re, rd, rg, P.admm_iters,
                                                          sh, res, G, X, P);
     ++iters_run;
-    // ---- candidate (x-hat, u-hat): FP64 rollout, defects, cost, linear model (lane 0)
-    double xc[NX], uc[NU], fc[NX];
-    if (dact) {
-      for (int j = 0; j < NX; ++j) { xc[j] = ndd.dat(Rec<M>::Xbar, j) + (double)ndd.at(Rec<M>::Xh, j); ndd.dat(Rec<M>::Xc, j) = xc[j]; }
-      for (int j = 0; j < NU; ++j) uc[j] = (id < N) ? ndd.dat(Rec<M>::Ubar, j) + (double)ndd.at(Rec<M>::Uh, j) : 0.0;
-      if constexpr (GROUP) {
-        if (id == 0)
-          for (int j = 0; j < NU; ++j) uc[j] = G->u0[j];
-      }
-    }
-    __syncthreads();
+    // ---- candidate (x-hat, u-hat): wide rollout, defects, cost, linear model (dense mapping)
+    W xc[NX], uc[NU], fc[NX];
     double v[6] = {0, 0, 0, 0, 0};
-    if (dact) {
-      v[0] = node_cost<M, T>(P, I, b, id, N, xc, uc);
-      T st = T(0);
-      for (int j = 0; j < NX; ++j) st = maxv(st, absv(ndd.at(Rec<M>::Xh, j)));
-      if (id < N) {
-        for (int j = 0; j < NU; ++j) st = maxv(st, absv(ndd.at(Rec<M>::Uh, j)));
-        rk4<M, double>(prm, h, xc, uc, fc);
-        double dinf = 0.0;
-        T lin1 = T(0);
-        for (int r = 0; r < NX; ++r) {
-          fc[r] -= ndd.dnb(Rec<M>::Xc, r, id + 1);
-          v[1] += fabs(fc[r]);
-          dinf = fmax(dinf, fabs(fc[r]));
-          T lin = ndd.at(Rec<M>::C, r) - ndd.nb(Rec<M>::Xh, r, id + 1);
-          for (int c = 0; c < NX; ++c) lin += MTd.A(r, c) * ndd.at(Rec<M>::Xh, c);
-          for (int c = 0; c < NU; ++c) lin += MTd.B(r, c) * ndd.at(Rec<M>::Uh, c);
-          lin1 += absv(lin);
-        }
-        v[2] = (double)lin1;
-        v[3] = dinf;
-      }
-      v[4] = (double)st;
-    }
-    block_reduce(sh, v, 3, 5);
+    scp_candidate<M, T, AOS, GROUP>(ndd, MTd, P, I, b, dact, G, sh, xc, uc, fc, v);
     bool timed_out = false;
     if (threadIdx.x == 0) timed_out = globaltimer_ns() - t0 > P.timeout_ns;
     double Jn = sh.Jn, Jc = v[0] + P.w_d * v[1], Lc = v[0] + P.w_d * v[2];
@@ -649,48 +635,13 @@ __global__ void __launch_bounds__(LANES_MAX_THREADS) scp_kernel_lanes(ProblemDev
     if (sh.accept) {
       ++accepted;
       if (k < 64) mask |= (1ull << k);
-      if (dact) {
-        node_rebase_mirrors<M, T, AOS>(ndd, L, P, b);
-        for (int j = 0; j < NX; ++j) {
-          const T xh = ndd.at(Rec<M>::Xh, j);
-          ndd.dat(Rec<M>::Xbar, j) = xc[j];
-          ndd.at(Rec<M>::X, j) -= xh;
-          if (id >= 1) ndd.at(Rec<M>::Z, j) -= xh;
-          ndd.at(Rec<M>::Xh, j) = T(0);
-          if (id < N) ndd.at(Rec<M>::C, j) = (T)fc[j];
-        }
-        if (id < N)
-          for (int j = 0; j < NU; ++j) {
-            const T uh = ndd.at(Rec<M>::Uh, j);
-            ndd.dat(Rec<M>::Ubar, j) = uc[j];
-            ndd.at(Rec<M>::U, j) -= uh;
-            ndd.at(Rec<M>::Uh, j) = T(0);
-          }
-      }
+      if (dact) scp_move_nominal<M, T, AOS>(ndd, L, P, b, xc, uc, fc);
     }
     __syncthreads();
     if (sh.stop) break;
   }
   double w[6] = {0, 0, 0, 0, 0, 0};
-  if (dact) {
-    double xb[NX], ub[NU];
-    read_nominal<M, T, AOS>(ndd, id < N, xb, ub);
-    w[0] = node_cost<M, T>(P, I, b, id, N, xb, ub);
-    if (id < N) {
-      double fn[NX];
-      rk4<M, double>(prm, h, xb, ub, fn);
-      for (int j = 0; j < NX; ++j) {
-        const double e = fabs(fn[j] - ndd.dnb(Rec<M>::Xbar, j, id + 1));
-        w[1] += e;
-        w[2] = fmax(w[2], e);
-      }
-    }
-    for (int j = 0; j < NX; ++j) xout[(xo + id) * NX + j] = xb[j];
-    if (id < N)
-      for (int j = 0; j < NU; ++j) uout[(uo + id) * NU + j] = ub[j];
-    node_export<M, T, AOS>(ndd, L, P, b, P.state_abs + P.soff[b]);
-  }
-  block_reduce(sh, w, 2, 3);
+  scp_finish<M, T, AOS>(ndd, L, P, I, b, dact, xo, uo, xout, uout, sh, w);
   if (threadIdx.x == 0) {
     int st = sh.status;
     if constexpr (GROUP) {
@@ -700,7 +651,7 @@ __global__ void __launch_bounds__(LANES_MAX_THREADS) scp_kernel_lanes(ProblemDev
     if (st == ST_OK && !(w[2] <= P.defect_tol)) st = ST_NOTCONV;
     ucn_scp_stats s;
     s.defect = w[2]; s.cost = w[0]; s.merit = w[0] + P.w_d * w[1];
-    s.primal_res = res[0]; s.dual_res = res[1]; s.tr_radius = sh.radius; s.step = last_step;
+    s.primal_res = sqrt(res[0]); s.dual_res = sqrt(res[1]); s.tr_radius = sh.radius; s.step = last_step;
     s.scp_iters = iters_run; s.accepted = accepted; s.accept_mask = mask; s.status = st; s.reserved = 0;
     s.t_start_ns = t0; s.t_end_ns = globaltimer_ns();
     s.pad[0] = s.pad[1] = s.pad[2] = s.pad[3] = 0.0;

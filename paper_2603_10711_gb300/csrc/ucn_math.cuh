@@ -8,6 +8,8 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include "ucn_df.cuh"
+
 namespace ucn {
 
 // ------------------------------------------------------------------ dual numbers
@@ -45,6 +47,11 @@ __device__ __forceinline__ float sqrt_(float a) { return sqrtf(a); }
 __device__ __forceinline__ double sin_(double a) { return sin(a); }
 __device__ __forceinline__ double cos_(double a) { return cos(a); }
 __device__ __forceinline__ double sqrt_(double a) { return sqrt(a); }
+// Double-float: the root by one corrected step; sine and cosine (the 12-state
+// quadrotor's Euler angles only) through FP64.
+__device__ __forceinline__ DF sqrt_(DF a) { return df_sqrt(a); }
+__device__ __forceinline__ DF sin_(DF a) { return df_from(sin(df_to_double(a))); }
+__device__ __forceinline__ DF cos_(DF a) { return df_from(cos(df_to_double(a))); }
 template <class T> __device__ __forceinline__ Dual<T> sin_(Dual<T> a) { return {sin_(a.v), cos_(a.v) * a.d}; }
 template <class T> __device__ __forceinline__ Dual<T> cos_(Dual<T> a) { return {cos_(a.v), -sin_(a.v) * a.d}; }
 template <class T> __device__ __forceinline__ Dual<T> sqrt_(Dual<T> a) {
@@ -185,12 +192,11 @@ struct Mars14 {
   }
 };
 
-// Classical fourth-order Runge-Kutta step (Eq. (1b)).
-template <class M, class S, class P>
-__device__ __forceinline__ void rk4(const P* prm, double h_, const S* x, const S* u, S* xn) {
-  typedef typename BaseOf<S>::type R;
+// Classical fourth-order Runge-Kutta step (Eq. (1b)) with the step h and its
+// multiples h/2, h/6 given in the base type R of S.
+template <class M, class S, class P, class R>
+__device__ __forceinline__ void rk4h(const P* prm, R h, R hh, R h6, const S* x, const S* u, S* xn) {
   constexpr int NX = M::NX;
-  const R h = (R)h_, hh = (R)(0.5 * h_), h6 = (R)(h_ / 6.0);
   S k[NX], t[NX], acc[NX];
   M::f(prm, x, u, k);
 #pragma unroll
@@ -204,6 +210,12 @@ __device__ __forceinline__ void rk4(const P* prm, double h_, const S* x, const S
   M::f(prm, t, u, k);
 #pragma unroll
   for (int j = 0; j < NX; ++j) xn[j] = x[j] + h6 * (acc[j] + k[j]);
+}
+
+template <class M, class S, class P>
+__device__ __forceinline__ void rk4(const P* prm, double h_, const S* x, const S* u, S* xn) {
+  typedef typename BaseOf<S>::type R;
+  rk4h<M, S, P, R>(prm, (R)h_, (R)(0.5 * h_), (R)(h_ / 6.0), x, u, xn);
 }
 
 // Column `dir` of [A B] = d RK4 / d(x, u) at (x, u), by one forward-mode pass.

@@ -98,6 +98,8 @@ def lib():
             L.ucn_mpc_shift.restype = C.c_int
             L.ucn_scp_solve_noalloc.argtypes = [C.POINTER(ProblemDesc), vp, vp, vp, vp, vp, vp, vp]
             L.ucn_scp_solve_noalloc.restype = C.c_int
+            L.ucn_df_check.argtypes = [C.c_int, vp, vp, vp, C.c_double, C.c_longlong, vp, vp]
+            L.ucn_df_check.restype = C.c_int
             _lib = L
         return _lib
 
@@ -262,6 +264,20 @@ def ucn_mpc_shift(h, x, u, xg, ug, stream=None):
     f = torch.float64
     _check(lib().ucn_mpc_shift(h, _ptr(x, f, name="x"), _ptr(u, f, name="u"), _ptr(xg, f, name="xg"),
                                _ptr(ug, f, name="ug"), _stream(stream)))
+
+
+UCN_DF_ADD, UCN_DF_SUB, UCN_DF_MUL, UCN_DF_DIV, UCN_DF_SQRT, UCN_DF_ROUND, UCN_DF_RK4 = 0, 1, 2, 3, 4, 5, 100
+
+
+def ucn_df_check(op, a, b, prm, h, out, stream=None):
+    """The FP32 path's double-float arithmetic on device FP64 tensors (see
+    include/ucn.h): elementwise ops on a, b, or one RK4 step per row."""
+    import torch
+    f = torch.float64
+    n = out.numel() if op < UCN_DF_RK4 else out.shape[0]
+    _check(lib().ucn_df_check(int(op), _ptr(a, f, name="a"), None if b is None else _ptr(b, f, name="b"),
+                              None if prm is None else _ptr(prm, f, name="prm"), float(h), int(n),
+                              _ptr(out, f, name="out"), _stream(stream)))
 
 
 def ucn_scp_solve_noalloc(desc: ProblemDesc, x0, u0, x_out, u_out, stats, status, stream=None):
