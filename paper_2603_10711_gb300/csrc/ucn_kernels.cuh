@@ -905,9 +905,8 @@ __device__ __forceinline__ void node_rhs(const Node<T, AOS>& nd, const MS& MT, c
 // mode projects G xi alone and leaves the duals untouched.
 template <class M, class T, bool AOS, int n>
 __device__ __forceinline__ void node_mirrors(const Node<T, AOS>& nd, const Layout& L, const Inst<T>& I,
-                                             T rg, const T* xi, bool reseed, bool want_res, T* sv, T& rp) {
+                                             T rg, T irg, const T* xi, bool reseed, bool want_res, T* sv, T& rp) {
   constexpr int NX = M::NX;
-  const T irg = T(1) / rg;
   if constexpr (IsQuad<M>::value) {
     for (int j = 0; j < I.nobs; ++j) {
       const T n0 = nd.at(L.oMd, ObsStride<T>::value * j), n1 = nd.at(L.oMd, ObsStride<T>::value * j + 1), n2 = nd.at(L.oMd, ObsStride<T>::value * j + 2);
@@ -1032,9 +1031,9 @@ __device__ void node_reseed(const Node<T, AOS>& nd, const Layout& L, const Inst<
   for (int j = 0; j < NX; ++j) xi[j] = nd.at(Rec<M>::Xh, j);
   if (nd.i < nd.N) {
     for (int j = 0; j < NU; ++j) xi[NX + j] = nd.at(Rec<M>::Uh, j);
-    node_mirrors<M, T, AOS, NX + NU>(nd, L, I, T(1), xi, true, false, sv, rp);
+    node_mirrors<M, T, AOS, NX + NU>(nd, L, I, T(1), T(1), xi, true, false, sv, rp);
   } else {
-    node_mirrors<M, T, AOS, NX>(nd, L, I, T(1), xi, true, false, sv, rp);
+    node_mirrors<M, T, AOS, NX>(nd, L, I, T(1), T(1), xi, true, false, sv, rp);
   }
 }
 
@@ -1159,9 +1158,9 @@ __device__ __forceinline__ void admm_iteration(const Node<T, AOS>& nd, const MS&
           nd.at(Rec<M>::Uh, j) = uh;
           nd.at(Rec<M>::Nuu, j) = nuu + rg * (x[NX + j] - uh);
         }
-        node_mirrors<M, T, AOS, NN>(nd, L, I, rg, x, false, last, sv, rp);
+        node_mirrors<M, T, AOS, NN>(nd, L, I, rg, irg, x, false, last, sv, rp);
       } else {
-        node_mirrors<M, T, AOS, NX>(nd, L, I, rg, x, false, last, sv, rp);
+        node_mirrors<M, T, AOS, NX>(nd, L, I, rg, irg, x, false, last, sv, rp);
       }
     }
     if constexpr (GROUP) {

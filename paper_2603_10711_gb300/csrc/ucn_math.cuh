@@ -8,6 +8,8 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <type_traits>
+
 #include "ucn_df.cuh"
 
 namespace ucn {
@@ -25,6 +27,16 @@ template <class T> __device__ __forceinline__ Dual<T> operator+(Dual<T> a, Dual<
 template <class T> __device__ __forceinline__ Dual<T> operator-(Dual<T> a, Dual<T> b) { return {a.v - b.v, a.d - b.d}; }
 template <class T> __device__ __forceinline__ Dual<T> operator-(Dual<T> a) { return {-a.v, -a.d}; }
 template <class T> __device__ __forceinline__ Dual<T> operator*(Dual<T> a, Dual<T> b) { return {a.v * b.v, a.d * b.v + a.v * b.d}; }
+// FP32 duals divide through one correctly rounded reciprocal (the Jacobian
+// passes' latency is the chain of divisions); FP64 keeps the IEEE quotient.
+__device__ __forceinline__ Dual<float> operator/(Dual<float> a, Dual<float> b) {
+  const float r = __frcp_rn(b.v), q = a.v * r;
+  return {q, (a.d - q * b.d) * r};
+}
+__device__ __forceinline__ Dual<float> operator/(float a, Dual<float> b) {
+  const float r = __frcp_rn(b.v), q = a * r;
+  return {q, -q * b.d * r};
+}
 template <class T> __device__ __forceinline__ Dual<T> operator/(Dual<T> a, Dual<T> b) {
   T q = a.v / b.v;
   return {q, (a.d - q * b.d) / b.v};
@@ -233,13 +245,22 @@ __device__ __forceinline__ void rk4_jvp(const P* prm, double h, const X* x, cons
 }
 
 // ------------------------------------------------------------------ projections
-// Ball {|y| <= R}: vector scaling.
+// Ball {|y| <= R}: vector scaling.  FP32: the test on squares and the scale
+// from one reciprocal square root (no square root, no division).
 template <class T>
 __device__ __forceinline__ void proj_ball3(T* y, T R) {
-  const T n = sqrt_(y[0] * y[0] + y[1] * y[1] + y[2] * y[2]);
-  if (n > R) {
-    const T s = R / n;
-    y[0] *= s; y[1] *= s; y[2] *= s;
+  if constexpr (std::is_same<T, float>::value) {
+    const float n2 = y[0] * y[0] + y[1] * y[1] + y[2] * y[2];
+    if (n2 > R * R) {
+      const float s = R * rsqrtf(n2);
+      y[0] *= s; y[1] *= s; y[2] *= s;
+    }
+  } else {
+    const T n = sqrt_(y[0] * y[0] + y[1] * y[1] + y[2] * y[2]);
+    if (n > R) {
+      const T s = R / n;
+      y[0] *= s; y[1] *= s; y[2] *= s;
+    }
   }
 }
 
@@ -260,8 +281,21 @@ __device__ __forceinline__ void proj_cone3(T* v, T tau) {
 }
 
 // The same cone projection with cos / sin of the half-angle precomputed.
+// FP32: the two tests on squares (tau >= 0) and one reciprocal square root.
 template <class T>
 __device__ __forceinline__ void proj_cone3c(T* v, T tau, T ca, T sa) {
+  if constexpr (std::is_same<T, float>::value) {
+    const float t = v[0], s2 = v[1] * v[1] + v[2] * v[2], t2 = t * t, tau2 = tau * tau;
+    if (t >= 0.0f && s2 <= tau2 * t2) return;                              // inside
+    if (t <= 0.0f && tau2 * s2 <= t2) { v[0] = v[1] = v[2] = 0.0f; return; }   // polar cone
+    const float rs = rsqrtf(s2), s = s2 * rs;                               // s2 > 0 here
+    const float c = t * ca + s * sa;
+    v[0] = c * ca;
+    const float r = c * sa * rs;
+    v[1] *= r;
+    v[2] *= r;
+    return;
+  }
   const T t = v[0];
   const T s = sqrt_(v[1] * v[1] + v[2] * v[2]);
   if (s <= tau * t) return;
