@@ -652,7 +652,7 @@ __host__ __device__ constexpr int pk(int r, int c) { return r * (r + 1) / 2 + c;
 template <class M, class T, bool AOS, int n, class MS>
 __device__ __forceinline__ bool node_factor(const Node<T, AOS>& nd, const MS& MT, const Layout& L, const Inst<T>& I,
                                             const NodeConst<M, T>& K, T rd, T rg) {
-  constexpr int NX = M::NX, NU = M::NU;
+  constexpr int NX = M::NX;
   const int i = nd.i, N = nd.N;
   const bool hasU = (n > NX);
   const bool term = (i == N);
@@ -782,7 +782,12 @@ __device__ __forceinline__ void apply_H(const Node<T, AOS>& nd, const MS& MT, co
   constexpr int NX = M::NX, NU = M::NU;
 #pragma unroll
   for (int j = 0; j < NX; ++j) out[j] = K.hd[j] * xi[j];
+  const bool coupled = nd.i < nd.N;   // node N: identity control block, no coupling
   if constexpr (n > NX) {
+   if (!coupled) {
+#pragma unroll
+    for (int j = 0; j < NU; ++j) out[NX + j] = K.hd[NX + j] * xi[NX + j];
+   } else {
     T v[NX];
 #pragma unroll
     for (int r = 0; r < NX; ++r) {
@@ -807,6 +812,7 @@ __device__ __forceinline__ void apply_H(const Node<T, AOS>& nd, const MS& MT, co
       for (int k = 0; k < NX; ++k) acc += MT.B(k, j) * v[k];
       out[NX + j] = K.hd[NX + j] * xi[NX + j] + acc;
     }
+   }
   }
   if constexpr (IsQuad<M>::value) {
     for (int j = 0; j < I.nobs; ++j) {
@@ -821,7 +827,7 @@ __device__ __forceinline__ void apply_H(const Node<T, AOS>& nd, const MS& MT, co
       if (I.tilt) { out[9] += rg * xi[9]; out[10] += rg * xi[10]; }
       if (I.wball) { out[11] += rg * xi[11]; out[12] += rg * xi[12]; out[13] += rg * xi[13]; }
     }
-    if constexpr (n > NX) {
+    if (n > NX && coupled) {
       if (I.ball) { out[NX] += rg * xi[NX]; out[NX + 1] += rg * xi[NX + 1]; out[NX + 2] += rg * xi[NX + 2]; }
       if constexpr (IsMars14<M>::value) {
         if (I.gim) { out[NX] += rg * xi[NX]; out[NX + 1] += rg * xi[NX + 1]; out[NX + 2] += rg * xi[NX + 2]; }
@@ -848,6 +854,7 @@ __device__ __forceinline__ void node_rhs(const Node<T, AOS>& nd, const MS& MT, c
     g[j] = v;
   }
   if constexpr (n > NX) {
+   if (i < nd.N) {
     // w_i = mu_{i+1} + rho_dyn (z_{i+1} - c_i); node i+1 publishes mu + rho_dyn z
     T w[NX];
 #pragma unroll
@@ -866,6 +873,10 @@ __device__ __forceinline__ void node_rhs(const Node<T, AOS>& nd, const MS& MT, c
       for (int k = 0; k < NX; ++k) acc += MT.B(k, j) * w[k];
       g[NX + j] = -K.q[NX + j] + acc + rg * nd.at(Rec<M>::Uh, j) - nd.at(Rec<M>::Nuu, j);
     }
+   } else {
+#pragma unroll
+    for (int j = 0; j < NU; ++j) g[NX + j] = T(0);   // node N: no control
+   }
   }
   if constexpr (IsQuad<M>::value) {
     for (int j = 0; j < I.nobs; ++j) {
@@ -884,7 +895,7 @@ __device__ __forceinline__ void node_rhs(const Node<T, AOS>& nd, const MS& MT, c
       if (I.wball)
         for (int k = 0; k < 3; ++k) g[11 + k] += rg * nd.at(L.oS, M14::S_W + k) - nd.at(L.oNus, M14::S_W + k);
     }
-    if constexpr (n > NX) {
+    if (n > NX && i < nd.N) {
       if constexpr (IsMars14<M>::value) {
         if (I.gim)
           for (int k = 0; k < 3; ++k) g[NX + k] += rg * nd.at(L.oS, M14::S_GIM + k) - nd.at(L.oNus, M14::S_GIM + k);
@@ -971,7 +982,7 @@ __device__ __forceinline__ void node_mirrors(const Node<T, AOS>& nd, const Layou
           if (want_res) { sv[11 + k] += rg * (s - so); rp += (xi[11 + k] - s) * (xi[11 + k] - s); }
         }
       }
-      if constexpr (n > NX) {
+      if (n > NX && nd.i < nd.N) {
         if (I.gim) {  // gimbal: |(T_y, T_z)| <= tan(delta_max) T_x (t = body x)
           T v[3];
           for (int k = 0; k < 3; ++k) v[k] = ub[k] + xi[NX + k] + (reseed ? T(0) : nd.at(L.oNus, M14::S_GIM + k) * irg);
@@ -987,7 +998,7 @@ __device__ __forceinline__ void node_mirrors(const Node<T, AOS>& nd, const Layou
         }
       }
     }
-    if constexpr (n > NX) {
+    if (n > NX && nd.i < nd.N) {   // control sets (node N has no control)
       if (I.ball) {  // |T| <= Tmax
         T v[3];
         for (int k = 0; k < 3; ++k) v[k] = ub[k] + xi[NX + k] + (reseed ? T(0) : nd.at(L.oNus, 3 + k) * irg);
@@ -1060,21 +1071,25 @@ __device__ __forceinline__ void admm_iteration(const Node<T, AOS>& nd, const MS&
   constexpr bool last = LAST;
   {
     T x[NN];
-    // ---- Step 1: H_i xi_i = g_i with the cached factor (+ one refinement step)
+    // ---- Step 1: H_i xi_i = g_i with the cached factor (+ one refinement step).
+    // Node N takes the same path: its factor carries an identity control block
+    // with no coupling and its control rows of g are zero, so its control part
+    // stays exactly zero and its state part is the state-only solve, while the
+    // warp that holds it runs one code path instead of two.
     if (active) {
       T g[NN];
+      node_rhs<M, T, AOS, NN>(nd, MT, L, I, K, re, rd, rg, g);
+      sym_solve<T, NN>(MT, g, x);
+      if constexpr (REFINE) {
+        T hx[NN], dx[NN];
+        apply_H<M, T, AOS, NN>(nd, MT, L, I, K, rd, rg, x, hx);
+#pragma unroll
+        for (int j = 0; j < NN; ++j) hx[j] = g[j] - hx[j];
+        sym_solve<T, NN>(MT, hx, dx);
+#pragma unroll
+        for (int j = 0; j < NN; ++j) x[j] += dx[j];
+      }
       if (i < N) {
-        node_rhs<M, T, AOS, NN>(nd, MT, L, I, K, re, rd, rg, g);
-        sym_solve<T, NN>(MT, g, x);
-        if constexpr (REFINE) {
-          T hx[NN], dx[NN];
-          apply_H<M, T, AOS, NN>(nd, MT, L, I, K, rd, rg, x, hx);
-#pragma unroll
-          for (int j = 0; j < NN; ++j) hx[j] = g[j] - hx[j];
-          sym_solve<T, NN>(MT, hx, dx);
-#pragma unroll
-          for (int j = 0; j < NN; ++j) x[j] += dx[j];
-        }
         // linearised propagation d_dyn,i = A x + B u + c_i, published to node i+1
 #pragma unroll
         for (int r = 0; r < NX; ++r) {
@@ -1084,18 +1099,6 @@ __device__ __forceinline__ void admm_iteration(const Node<T, AOS>& nd, const MS&
 #pragma unroll
           for (int c = 0; c < NU; ++c) acc += MT.B(r, c) * x[NX + c];
           nd.at(Rec<M>::Ex1, r) = acc;
-        }
-      } else {
-        node_rhs<M, T, AOS, NX>(nd, MT, L, I, K, re, rd, rg, g);
-        sym_solve<T, NX>(MT, g, x);
-        if constexpr (REFINE) {
-          T hx[NX], dx[NX];
-          apply_H<M, T, AOS, NX>(nd, MT, L, I, K, rd, rg, x, hx);
-#pragma unroll
-          for (int j = 0; j < NX; ++j) hx[j] = g[j] - hx[j];
-          sym_solve<T, NX>(MT, hx, dx);
-#pragma unroll
-          for (int j = 0; j < NX; ++j) x[j] += dx[j];
         }
       }
 #pragma unroll
@@ -1158,10 +1161,8 @@ __device__ __forceinline__ void admm_iteration(const Node<T, AOS>& nd, const MS&
           nd.at(Rec<M>::Uh, j) = uh;
           nd.at(Rec<M>::Nuu, j) = nuu + rg * (x[NX + j] - uh);
         }
-        node_mirrors<M, T, AOS, NN>(nd, L, I, rg, irg, x, false, last, sv, rp);
-      } else {
-        node_mirrors<M, T, AOS, NX>(nd, L, I, rg, irg, x, false, last, sv, rp);
       }
+      node_mirrors<M, T, AOS, NN>(nd, L, I, rg, irg, x, false, last, sv, rp);   // control sets: i < N only
     }
     if constexpr (GROUP) {
       double tot[3 * NU];
