@@ -47,6 +47,13 @@ int default_tpn(int model, int nodes) {
   return (model == UCN_MODEL_QUAD12 && 4 * nodes <= LANES_MAX_THREADS) ? 4 : 1;
 }
 
+std::vector<double> rho_schedule(double rho_final, double rho_geo, int K) {
+  std::vector<double> fac(std::max(K, 1), 1.0);
+  if (rho_final > 0.0 && K > 1)
+    for (int k = 0; k < K; ++k) fac[k] = std::pow(rho_final / rho_geo, (double)k / (double)(K - 1));
+  return fac;
+}
+
 Layout make_layout(int model, int nodes, int max_obs, int tsize, bool reg_mats) {
   const bool quad = model_obstacles(model);
   const int NX = model_nx(model), NU = model_nu(model), NN = NX + NU;
@@ -284,10 +291,7 @@ ucn_status ucn_problem_create(const ucn_problem_desc* d, ucn_problem** out) {
   }
   int* ord = nullptr;
   COPY(ord, order.data(), B);
-  // penalty factor of each SCP iteration, (rho_final / rho_geo)^(k / (K - 1)) (1 without a schedule)
-  std::vector<double> fac(d->scp_iters, 1.0);
-  if (d->rho_final > 0.0 && d->scp_iters > 1)
-    for (int k = 0; k < d->scp_iters; ++k) fac[k] = std::pow(d->rho_final / d->rho_geo, (double)k / (double)(d->scp_iters - 1));
+  const std::vector<double> fac = rho_schedule(d->rho_final, d->rho_geo, d->scp_iters);
   double* facd = nullptr;
   COPY(facd, fac.data(), fac.size());
   double* sabs = nullptr;

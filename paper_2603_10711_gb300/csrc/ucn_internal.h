@@ -3,6 +3,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "ucn.h"
 
 namespace ucn {
@@ -63,6 +65,11 @@ inline int model_nx(int m) {
 inline int model_nu(int m) { return (m == UCN_MODEL_MARS7 || m == UCN_MODEL_MARS14) ? 3 : 4; }
 // quadrotors: obstacle mirrors; Mars models: their thrust / attitude / glide-slope sets
 inline bool model_obstacles(int m) { return m == UCN_MODEL_QUAD12 || m == UCN_MODEL_QUAT13; }
+
+// Penalty factor of each SCP iteration, (rho_final / rho_geo)^(k / (K - 1))
+// (1 without a schedule), tabulated on the host so that no kernel evaluates
+// pow per iteration.
+std::vector<double> rho_schedule(double rho_final, double rho_geo, int K);
 
 // The launchers of one model and precision.
 struct Launchers {

@@ -11,7 +11,8 @@
 // (per-instance index tables and the final ADMM state the kernel writes out)
 // in one file-scope __device__ array instead of allocated memory.
 //
-// Limits and sharing.  The array holds UCN_NOALLOC_SCRATCH_BYTES (64 MiB) on
+// Limits and sharing.  The array (index tables, the penalty schedule, the
+// exported state) holds UCN_NOALLOC_SCRATCH_BYTES (64 MiB) on
 // every GPU that loads the library, until the process exits.  All calls share
 // it and it keeps the last call's contents; two calls whose kernels overlap on
 // the GPU (different streams, or different host threads on one device) race
@@ -107,8 +108,9 @@ extern "C" ucn_status ucn_scp_solve_noalloc(const ucn_problem_desc* d, const dou
     ts += 6LL * (n + 1) * NX + 3LL * n * NU + 2LL * (n + 1) * mb * 3;
     Nmax = std::max(Nmax, n);
   }
+  const std::vector<double> fac = rho_schedule(d->rho_final, d->rho_geo, d->scp_iters);
   const long long oN = 0, oX = up256(4LL * B), oU = oX + up256(8LL * B), oS = oU + up256(8LL * B);
-  const long long oState = oS + up256(8LL * B);
+  const long long oF = oS + up256(8LL * B), oState = oF + up256(8LL * (long long)fac.size());
   const long long need = oState + 8LL * ts;
   if (need > (long long)UCN_NOALLOC_SCRATCH_BYTES)
     return nfail(UCN_EINVAL, "batch needs %lld bytes of scratch; the no-allocation entry point holds %llu",
@@ -129,7 +131,8 @@ extern "C" ucn_status ucn_scp_solve_noalloc(const ucn_problem_desc* d, const dou
   if ((e = cudaMemcpyAsync(scr + oN, N.data(), 4LL * B, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
       (e = cudaMemcpyAsync(scr + oX, xoff.data(), 8LL * B, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
       (e = cudaMemcpyAsync(scr + oU, uoff.data(), 8LL * B, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
-      (e = cudaMemcpyAsync(scr + oS, soff.data(), 8LL * B, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+      (e = cudaMemcpyAsync(scr + oS, soff.data(), 8LL * B, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(scr + oF, fac.data(), 8LL * fac.size(), cudaMemcpyHostToDevice, st)) != cudaSuccess)
     return nfail(UCN_ECUDA, "table copy: %s", cudaGetErrorString(e));
   ProblemDev P;
   std::memset(&P, 0, sizeof(P));
@@ -146,6 +149,7 @@ extern "C" ucn_status ucn_scp_solve_noalloc(const ucn_problem_desc* d, const dou
   P.defect_tol = d->defect_tol; P.step_tol = d->step_tol;
   P.timeout_ns = (unsigned long long)((d->timeout_s > 0 ? d->timeout_s : 60.0) * 1e9);
   P.state_abs = (double*)(scr + oState);
+  P.rho_fac = (const double*)(scr + oF);
   P.ws = nullptr;
   LaunchCfg c;
   c.P = &P; c.L = &L; c.smem = true; c.smem_bytes = L.bytes;

@@ -181,8 +181,10 @@ ucn_status ucn_serve_create(const ucn_serve_config* c, ucn_server** out) {
   ok = ok && dalloc(s, &s->stats, (size_t)S) && dalloc(s, &s->status, (size_t)S);
   ok = ok && dalloc(s, &s->ring_x, (size_t)s->R * Xn * NX) && dalloc(s, &s->ring_u, (size_t)s->R * Un * NU);
   long long *dxoff = nullptr, *duoff = nullptr, *dsoff = nullptr;
-  double* sabs = nullptr;
+  double *sabs = nullptr, *dfac = nullptr;
   ok = ok && dalloc(s, &dxoff, S) && dalloc(s, &duoff, S) && dalloc(s, &dsoff, S) && dalloc(s, &sabs, (size_t)S * s->state_per_slot);
+  const std::vector<double> fac = rho_schedule(c->rho_final, c->rho_geo, c->scp_iters);
+  ok = ok && dalloc(s, &dfac, fac.size());
   char* ws = nullptr;
   if (ok && !s->smem) ok = dalloc(s, &ws, (size_t)s->L.bytes * S);
   if (ok) {
@@ -191,6 +193,7 @@ ucn_status ucn_serve_create(const ucn_serve_config* c, ucn_server** out) {
     cudaMemcpy(dxoff, xo.data(), sizeof(long long) * S, cudaMemcpyHostToDevice);
     cudaMemcpy(duoff, uo.data(), sizeof(long long) * S, cudaMemcpyHostToDevice);
     cudaMemcpy(dsoff, so.data(), sizeof(long long) * S, cudaMemcpyHostToDevice);
+    cudaMemcpy(dfac, fac.data(), sizeof(double) * fac.size(), cudaMemcpyHostToDevice);
     for (int l = 0; l < s->lanes && ok; ++l) {
       cudaStream_t st; cudaEvent_t ev; int *od, *oh;
       ok = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess &&
@@ -212,7 +215,7 @@ ucn_status ucn_serve_create(const ucn_serve_config* c, ucn_server** out) {
   P.tr_init = c->tr_init; P.tr_min = c->tr_min; P.tr_max = c->tr_max; P.w_d = c->w_d;
   P.defect_tol = c->defect_tol; P.step_tol = c->step_tol;
   P.timeout_ns = (unsigned long long)((c->timeout_s > 0 ? c->timeout_s : 60.0) * 1e9);
-  P.state_abs = sabs; P.ws = ws; P.order = nullptr;
+  P.state_abs = sabs; P.ws = ws; P.order = nullptr; P.rho_fac = dfac;
   s->slot_state.assign(S, SLOT_FREE); s->slot_lane.assign(S, -1); s->slot_warm_ring.assign(S, -1);
   s->slot_ticket.assign(S, 0); s->slot_bytes.assign(S, 0);
   s->ring_ticket.assign(s->R, 0); s->ring_N.assign(s->R, 0); s->ring_next = 0;
