@@ -223,6 +223,7 @@ __device__ __forceinline__ Inst<T> make_inst(const ProblemDev& P, int b) {
 
 // Per-instance scalars in shared memory.
 struct InstShared {
+  unsigned long long xbar[2];   // split barrier of the ADMM exchange + failure flag
   double red[32][6];
   double Jn, radius;
   double rho[3];            // rho_eq, rho_dyn, rho_geo of the SCP iteration
@@ -243,7 +244,35 @@ struct GroupShared {
 struct GroupX {
   unsigned epoch;       // exchanges done
   int g, k;             // group index, scenario index within the group
+  unsigned long long* bar;   // the CTA's split barrier (mbarrier) and its failure flag
+  unsigned ph;               // completed phases of the split barrier
 };
+
+// Split CTA barrier on an mbarrier object in shared memory: every thread
+// arrives once per phase (release), may do independent work, then waits for
+// the phase to complete (acquire).  The wait is bounded; a wait that gives up
+// sets bar[1] (reported as a numerical failure) and returns.
+__device__ __forceinline__ void split_barrier_init(unsigned long long* bar, unsigned count) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(bar);
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
+  bar[1] = 0ull;
+}
+__device__ __forceinline__ void split_barrier_arrive(unsigned long long* bar) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(bar);
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}" ::"r"(a) : "memory");
+}
+__device__ __forceinline__ void split_barrier_wait(unsigned long long* bar, unsigned& ph) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(bar);
+  const unsigned parity = ph & 1u;
+  ++ph;
+  for (int it = 0; it < (1 << 20); ++it) {
+    unsigned done;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(done) : "r"(a), "r"(parity) : "memory");
+    if (done) return;
+  }
+  bar[1] = 1ull;
+}
 
 __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
   unsigned v;
@@ -1108,31 +1137,17 @@ __device__ __forceinline__ void admm_iteration(const Node<T, AOS>& nd, const MS&
         for (int j = 0; j < NU; ++j) nd.at(Rec<M>::U, j) = x[NX + j];
       }
     }
-    __syncthreads();
+    // Steps 2 and 3 use disjoint variables (z, lambda, mu | x-hat, u-hat, nu,
+    // mirrors) and both read only this iteration's xi, so Step 3 runs first,
+    // between the arrival on the split barrier (Ex1 published) and the wait
+    // for the left neighbour's Ex1 that Step 2 needs: a warp that is ahead
+    // projects instead of idling at a barrier.
+    split_barrier_arrive(X.bar);
     T dz[NX];
     T sv[NN];
+#pragma unroll
+    for (int j = 0; j < NN; ++j) sv[j] = T(0);
     if (active) {
-#pragma unroll
-      for (int j = 0; j < NN; ++j) sv[j] = T(0);
-      // ---- Step 2: dynamic consensus, Eq. (5), then its duals (Step 4)
-      if (i >= 1) {
-#pragma unroll
-        for (int j = 0; j < NX; ++j) {
-          const T dd = nd.nb(Rec<M>::Ex1, j, i - 1);
-          const T zo = nd.at(Rec<M>::Z, j);
-          const T lam = nd.at(Rec<M>::Lam, j), mu = nd.at(Rec<M>::Mu, j);
-          const T z = (re * x[j] + lam + rd * dd - mu) * ired;
-          nd.at(Rec<M>::Z, j) = z;
-          nd.at(Rec<M>::Lam, j) = lam + re * (x[j] - z);
-          const T mun = mu + rd * (z - dd);
-          nd.at(Rec<M>::Mu, j) = mun;
-          dz[j] = z - zo;
-          if (last) {
-            sv[j] += re * dz[j];
-            rp += (x[j] - z) * (x[j] - z) + (z - dd) * (z - dd);
-          }
-        }
-      }
       // ---- Step 3: projections onto the boxes (Eq. (7)) and Step 4 for nu_x, nu_u
 #pragma unroll
       for (int j = 0; j < NX; ++j) {
@@ -1177,6 +1192,28 @@ __device__ __forceinline__ void admm_iteration(const Node<T, AOS>& nd, const MS&
           if (last) { sv[NX + j] += rg * (uh - nd.at(Rec<M>::Uh, j)); rp += (x[NX + j] - uh) * (x[NX + j] - uh); }
           nd.at(Rec<M>::Uh, j) = uh;
           nd.at(Rec<M>::Nuu, j) = nuu + rg * (x[NX + j] - uh);
+        }
+      }
+    }
+    split_barrier_wait(X.bar, X.ph);
+    if (active) {
+      // ---- Step 2: dynamic consensus, Eq. (5), then its duals (Step 4)
+      if (i >= 1) {
+#pragma unroll
+        for (int j = 0; j < NX; ++j) {
+          const T dd = nd.nb(Rec<M>::Ex1, j, i - 1);
+          const T zo = nd.at(Rec<M>::Z, j);
+          const T lam = nd.at(Rec<M>::Lam, j), mu = nd.at(Rec<M>::Mu, j);
+          const T z = (re * x[j] + lam + rd * dd - mu) * ired;
+          nd.at(Rec<M>::Z, j) = z;
+          nd.at(Rec<M>::Lam, j) = lam + re * (x[j] - z);
+          const T mun = mu + rd * (z - dd);
+          nd.at(Rec<M>::Mu, j) = mun;
+          dz[j] = z - zo;
+          if (last) {
+            sv[j] += re * dz[j];
+            rp += (x[j] - z) * (x[j] - z) + (z - dd) * (z - dd);
+          }
         }
       }
     }
@@ -1507,7 +1544,7 @@ __global__ void __launch_bounds__(MAX_THREADS) admm_kernel(ProblemDev P, Layout 
   const int i = nd.i, N = nd.N;
   const bool active = i <= N;
   const long long xo = P.xoff[b], uo = P.uoff[b];
-  if (threadIdx.x == 0) sh.fail = 0;
+  if (threadIdx.x == 0) { sh.fail = 0; split_barrier_init(sh.xbar, blockDim.x); }
   stage_consts<M, T, AOS>(nd, P, b);
   if (active) load_nominal<M, T, AOS>(nd, L, xbar, ubar, xo, uo);
   __syncthreads();
@@ -1546,7 +1583,7 @@ __global__ void __launch_bounds__(MAX_THREADS) admm_kernel(ProblemDev P, Layout 
   }
   __syncthreads();
   double r2[2] = {0.0, 0.0};
-  GroupX X{0u, 0, 0};
+  GroupX X{0u, 0, 0, sh.xbar, 0u};
   if (!sh.fail) admm_iterations<M, T, AOS, REFINE>(nd, MT, L, I, K, active, re, rd, rg, iters, sh, r2, nullptr, X, P);
   if (active) {
     node_export<M, T, AOS>(nd, L, P, b, P.state_abs + P.soff[b]);
@@ -1557,7 +1594,7 @@ __global__ void __launch_bounds__(MAX_THREADS) admm_kernel(ProblemDev P, Layout 
   if (threadIdx.x == 0) {
     res[2 * b] = sqrt(r2[0]);
     res[2 * b + 1] = sqrt(r2[1]);
-    status[b] = sh.fail ? ST_NUMERIC : ST_OK;
+    status[b] = (sh.fail || sh.xbar[1]) ? ST_NUMERIC : ST_OK;
   }
 }
 
@@ -1813,7 +1850,11 @@ __global__ void __launch_bounds__(MAX_THREADS) scp_kernel(ProblemDev P, Layout L
   const unsigned long long t0 = globaltimer_ns();
   const Inst<T> I = make_inst<M, T>(P, b);
   NodeConst<M, T> K;
-  if (threadIdx.x == 0) { sh.fail = 0; sh.status = ST_OK; sh.radius = P.tr_init; sh.stop = 0; }
+  if (threadIdx.x == 0) {
+    sh.fail = 0; sh.status = ST_OK; sh.radius = P.tr_init; sh.stop = 0;
+    split_barrier_init(sh.xbar, blockDim.x);
+  }
+  X.bar = sh.xbar;
   stage_consts<M, T, AOS>(nd, P, b);
   if (active) load_nominal<M, T, AOS>(nd, L, x0, u0, xo, uo);
   __syncthreads();
@@ -1912,7 +1953,7 @@ __global__ void __launch_bounds__(MAX_THREADS) scp_kernel(ProblemDev P, Layout L
     if constexpr (GROUP) {
       if (G->gfail && st != ST_NUMERIC) st = ST_TIMEOUT;   // the group lost its consensus partner
     }
-    if (!isfinite(w[2])) st = ST_NUMERIC;
+    if (!isfinite(w[2]) || sh.xbar[1]) st = ST_NUMERIC;
     if (st == ST_OK && !(w[2] <= P.defect_tol)) st = ST_NOTCONV;
     ucn_scp_stats s;
     s.defect = w[2]; s.cost = w[0]; s.merit = w[0] + P.w_d * w[1];
