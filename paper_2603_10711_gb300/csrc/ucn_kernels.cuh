@@ -1142,7 +1142,8 @@ __device__ __forceinline__ void admm_iteration(const Node<T, AOS>& nd, const MS&
     // between the arrival on the split barrier (Ex1 published) and the wait
     // for the left neighbour's Ex1 that Step 2 needs: a warp that is ahead
     // projects instead of idling at a barrier.
-    split_barrier_arrive(X.bar);
+    if constexpr (GROUP) __syncthreads();   // groups: their exchange follows Step 2 on a plain barrier
+    else split_barrier_arrive(X.bar);
     T dz[NX];
     T sv[NN];
 #pragma unroll
@@ -1179,23 +1180,7 @@ __device__ __forceinline__ void admm_iteration(const Node<T, AOS>& nd, const MS&
       }
       node_mirrors<M, T, AOS, NN>(nd, L, I, rg, irg, x, false, last, sv, rp);   // control sets: i < N only
     }
-    if constexpr (GROUP) {
-      double tot[3 * NU];
-      group_allreduce<3 * NU>(P, G, X, NU, tot);
-      if (active && i == 0 && i < N) {
-#pragma unroll
-        for (int j = 0; j < NU; ++j) {
-          const double v = fmin(fmax(tot[j] / (double)P.group, tot[NU + j]), -tot[2 * NU + j]);
-          G->u0[j] = v;
-          const T uh = (T)(v - wide_to_double(nd.dat(Rec<M>::Ubar, j)));
-          const T nuu = nd.at(Rec<M>::Nuu, j);
-          if (last) { sv[NX + j] += rg * (uh - nd.at(Rec<M>::Uh, j)); rp += (x[NX + j] - uh) * (x[NX + j] - uh); }
-          nd.at(Rec<M>::Uh, j) = uh;
-          nd.at(Rec<M>::Nuu, j) = nuu + rg * (x[NX + j] - uh);
-        }
-      }
-    }
-    split_barrier_wait(X.bar, X.ph);
+    if constexpr (!GROUP) split_barrier_wait(X.bar, X.ph);
     if (active) {
       // ---- Step 2: dynamic consensus, Eq. (5), then its duals (Step 4)
       if (i >= 1) {
@@ -1214,6 +1199,22 @@ __device__ __forceinline__ void admm_iteration(const Node<T, AOS>& nd, const MS&
             sv[j] += re * dz[j];
             rp += (x[j] - z) * (x[j] - z) + (z - dd) * (z - dd);
           }
+        }
+      }
+    }
+    if constexpr (GROUP) {
+      double tot[3 * NU];
+      group_allreduce<3 * NU>(P, G, X, NU, tot);
+      if (active && i == 0 && i < N) {
+#pragma unroll
+        for (int j = 0; j < NU; ++j) {
+          const double v = fmin(fmax(tot[j] / (double)P.group, tot[NU + j]), -tot[2 * NU + j]);
+          G->u0[j] = v;
+          const T uh = (T)(v - wide_to_double(nd.dat(Rec<M>::Ubar, j)));
+          const T nuu = nd.at(Rec<M>::Nuu, j);
+          if (last) { sv[NX + j] += rg * (uh - nd.at(Rec<M>::Uh, j)); rp += (x[NX + j] - uh) * (x[NX + j] - uh); }
+          nd.at(Rec<M>::Uh, j) = uh;
+          nd.at(Rec<M>::Nuu, j) = nuu + rg * (x[NX + j] - uh);
         }
       }
     }

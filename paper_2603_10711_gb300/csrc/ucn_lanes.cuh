@@ -318,7 +318,11 @@ __device__ __forceinline__ void admm_iteration_lanes(const Node<T, AOS>& nd, con
       }
     }
   }
-  __syncthreads();
+  // Step 3 before Step 2 (disjoint variables, both read only this iteration's
+  // xi): between the arrival on the split barrier and the wait for the left
+  // neighbour's Ex1
+  if constexpr (GROUP) __syncthreads();   // groups: their exchange follows Step 2 on a plain barrier
+  else split_barrier_arrive(X.bar);
   T dz[RX];
   T sv[R];
 #pragma unroll
@@ -327,25 +331,6 @@ __device__ __forceinline__ void admm_iteration_lanes(const Node<T, AOS>& nd, con
   for (int m = 0; m < RX; ++m) dz[m] = T(0);
   T msv[3] = {T(0), T(0), T(0)};
   if (active) {
-    // ---- Step 2: dynamic consensus, Eq. (5), then its duals (Step 4)
-    if (i >= 1) {
-#pragma unroll
-      for (int m = 0; m < RX; ++m) {
-        const int j = q + TPN * m;
-        const T dd = nd.nb(Rec<M>::Ex1, j, i - 1);
-        const T zo = nd.at(Rec<M>::Z, j);
-        const T lam = nd.at(Rec<M>::Lam, j), mu = nd.at(Rec<M>::Mu, j);
-        const T z = (re * xo[m] + lam + rd * dd - mu) * ired;
-        nd.at(Rec<M>::Z, j) = z;
-        nd.at(Rec<M>::Lam, j) = lam + re * (xo[m] - z);
-        nd.at(Rec<M>::Mu, j) = mu + rd * (z - dd);
-        dz[m] = z - zo;
-        if (LAST) {
-          sv[m] += re * dz[m];
-          rp += (xo[m] - z) * (xo[m] - z) + (z - dd) * (z - dd);
-        }
-      }
-    }
     // ---- Step 3: projections onto the boxes (Eq. (7)) and Step 4 for nu_x, nu_u
 #pragma unroll
     for (int m = 0; m < RX; ++m) {
@@ -393,6 +378,28 @@ __device__ __forceinline__ void admm_iteration_lanes(const Node<T, AOS>& nd, con
         const T ds = rg * (s - so);
         msv[0] += n0 * ds; msv[1] += n1 * ds; msv[2] += n2 * ds;
         rp += (y - s) * (y - s);
+      }
+    }
+  }
+  if constexpr (!GROUP) split_barrier_wait(X.bar, X.ph);
+  if (active) {
+    // ---- Step 2: dynamic consensus, Eq. (5), then its duals (Step 4)
+    if (i >= 1) {
+#pragma unroll
+      for (int m = 0; m < RX; ++m) {
+        const int j = q + TPN * m;
+        const T dd = nd.nb(Rec<M>::Ex1, j, i - 1);
+        const T zo = nd.at(Rec<M>::Z, j);
+        const T lam = nd.at(Rec<M>::Lam, j), mu = nd.at(Rec<M>::Mu, j);
+        const T z = (re * xo[m] + lam + rd * dd - mu) * ired;
+        nd.at(Rec<M>::Z, j) = z;
+        nd.at(Rec<M>::Lam, j) = lam + re * (xo[m] - z);
+        nd.at(Rec<M>::Mu, j) = mu + rd * (z - dd);
+        dz[m] = z - zo;
+        if (LAST) {
+          sv[m] += re * dz[m];
+          rp += (xo[m] - z) * (xo[m] - z) + (z - dd) * (z - dd);
+        }
       }
     }
   }
@@ -545,7 +552,11 @@ __global__ void __launch_bounds__(LANES_MAX_THREADS) scp_kernel_lanes(ProblemDev
   T kq[R], khd[R];
 #pragma unroll
   for (int m = 0; m < R; ++m) { kq[m] = T(0); khd[m] = T(0); }
-  if (threadIdx.x == 0) { sh.fail = 0; sh.status = ST_OK; sh.radius = P.tr_init; sh.stop = 0; }
+  if (threadIdx.x == 0) {
+    sh.fail = 0; sh.status = ST_OK; sh.radius = P.tr_init; sh.stop = 0;
+    split_barrier_init(sh.xbar, blockDim.x);
+  }
+  X.bar = sh.xbar;
   stage_consts<M, T, AOS>(ndd, P, b);
   if (dact) load_nominal<M, T, AOS>(ndd, L, x0, u0, xo, uo);
   __syncthreads();
@@ -647,7 +658,7 @@ __global__ void __launch_bounds__(LANES_MAX_THREADS) scp_kernel_lanes(ProblemDev
     if constexpr (GROUP) {
       if (G->gfail && st != ST_NUMERIC) st = ST_TIMEOUT;
     }
-    if (!isfinite(w[2])) st = ST_NUMERIC;
+    if (!isfinite(w[2]) || sh.xbar[1]) st = ST_NUMERIC;
     if (st == ST_OK && !(w[2] <= P.defect_tol)) st = ST_NOTCONV;
     ucn_scp_stats s;
     s.defect = w[2]; s.cost = w[0]; s.merit = w[0] + P.w_d * w[1];
