@@ -88,8 +88,10 @@ typedef enum { UCN_PREC_FP64 = 0, UCN_PREC_FP32_REFINE = 1 } ucn_precision;
  *  vc_weight     virtual control weight; must be 0 (virtual control is off)
  *  precision     UCN_PREC_FP64: every step in FP64.  UCN_PREC_FP32_REFINE:
  *                Jacobians, factorisation and ADMM in FP32 with one
- *                iterative-refinement step per KKT solve; the RK4 rollout,
- *                defects, costs and residual sums in FP64
+ *                iterative-refinement step per KKT solve; the nominal
+ *                trajectory, RK4 rollout, defects, costs and merits in
+ *                double-float (float pairs, ~48 bits; see ucn_df_check),
+ *                the acceptance test and the results in FP64
  *  timeout_s     device time budget per ucn_scp_solve launch (0: 60 s)
  *  group         scenarios per group for robust MPC (Sec. IV-A); 0 or 1:
  *                independent instances.  With group = K in [2, UCN_MAX_GROUP] the
@@ -219,7 +221,7 @@ ucn_status ucn_state_export(ucn_problem* prob, double* state_d, void* stream);
 /* Full SCP solve (Sec. III-A with the ADMM of Sec. III-B) of every
  * instance in ONE persistent kernel launch: per SCP iteration the RK4
  * linearisation, assembly + factorisation, admm_iters ADMM iterations, and
- * the FP64 rollout / defect / trust-region acceptance test, all on the
+ * the rollout / defect / trust-region acceptance test, all on the
  * device.  In: initial guesses x0_d, u0_d.  Out: x_out_d, u_out_d (the last
  * accepted trajectory), stats_d [batch], status_d [batch] (== stats.status). */
 ucn_status ucn_scp_solve(ucn_problem* prob, const double* x0_d, const double* u0_d,

@@ -1550,7 +1550,7 @@ __global__ void __launch_bounds__(MAX_THREADS) admm_kernel(ProblemDev P, Layout 
   if (active) load_nominal<M, T, AOS>(nd, L, xbar, ubar, xo, uo);
   __syncthreads();
   if (active && i < N) {
-    // A, B in T; deviation affine term c_i = A xbar_i + B ubar_i + d_i - xbar_{i+1} in FP64
+    // A, B in T; deviation affine term c_i = A xbar_i + B ubar_i + d_i - xbar_{i+1} in FP64 (once per call)
     const long long g = uo + i;
 #pragma unroll
     for (int r = 0; r < NX; ++r) {

@@ -6,7 +6,7 @@
 // the dependent chain of the per-node mat-vecs by TPN and multiplies the
 // resident warps by TPN -- the one-thread kernel of a 16-row node runs 1-2
 // warps per scheduler and is latency-bound.  The per-SCP-iteration work
-// (assembly and factorisation, the FP64 rollout, acceptance) maps one thread
+// (assembly and factorisation, the wide rollout, acceptance) maps one thread
 // to one node again; the Jacobian directions are split over the lanes.
 #pragma once
 #include "ucn_kernels.cuh"
@@ -534,10 +534,10 @@ __global__ void __launch_bounds__(LANES_MAX_THREADS) scp_kernel_lanes(ProblemDev
   LaneH<M, T, TPN, std::is_same<T, float>::value> H;
   const int i = nd.i, N = nd.N;
   const bool active = i <= N;
-  // The per-SCP-iteration work (nominal, assembly and factorisation, the FP64
+  // The per-SCP-iteration work (nominal, assembly and factorisation, the wide
   // rollout and acceptance, the nominal update) maps one thread to one node, so
-  // that its warps run full -- the FP64 pipe charges a warp instruction whatever
-  // its active lanes.
+  // that its warps run full -- the FP64 plain path's FP64 pipe charges a warp
+  // instruction whatever its active lanes.
   Node<T, AOS> ndd = make_node<T, SMEM>(P, L, smem, b);
   SmemMats<M, T, AOS> MTd;
   init_mats<M, T, AOS>(MTd, ndd, L);

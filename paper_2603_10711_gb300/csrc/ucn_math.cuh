@@ -315,7 +315,7 @@ __device__ __forceinline__ float absv(float a) { return fabsf(a); }
 __device__ __forceinline__ double absv(double a) { return fabs(a); }
 __device__ __forceinline__ float clampv(float v, float lo, float hi) { return fminf(fmaxf(v, lo), hi); }
 
-// ------------------------------------------------------------------ block reductions (FP64)
+// ------------------------------------------------------------------ warp reductions (FP64)
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
