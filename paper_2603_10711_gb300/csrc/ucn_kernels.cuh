@@ -553,14 +553,33 @@ __device__ __forceinline__ void node_jacobians(const Node<T, AOS>& nd, const MS&
   for (int j = 0; j < NX; ++j) xt[j] = wide_to<T>(xb[j]);
 #pragma unroll
   for (int j = 0; j < NU; ++j) ut[j] = wide_to<T>(ub[j]);
+  if constexpr (std::is_same<T, float>::value) {
+    // FP32: two columns per pass (the value of the RK4 map is computed once for both)
 #pragma unroll
-  for (int dir = 0; dir < NX + NU; ++dir) {
-    T col[NX];
-    rk4_jvp<M, T>(prm, h, xt, ut, dir, col);
+    for (int dir = 0; dir < NX + NU; dir += 2) {
+      T col[NX], col1[NX];
+      if (dir + 1 < NX + NU) rk4_jvp2<M, T>(prm, h, xt, ut, dir, dir + 1, col, col1);
+      else rk4_jvp<M, T>(prm, h, xt, ut, dir, col);
 #pragma unroll
-    for (int r = 0; r < NX; ++r) {
-      if (dir < NX) MT.A(r, dir) = col[r];
-      else MT.B(r, dir - NX) = col[r];
+      for (int r = 0; r < NX; ++r) {
+        if (dir < NX) MT.A(r, dir) = col[r];
+        else MT.B(r, dir - NX) = col[r];
+        if (dir + 1 < NX + NU) {
+          if (dir + 1 < NX) MT.A(r, dir + 1) = col1[r];
+          else MT.B(r, dir + 1 - NX) = col1[r];
+        }
+      }
+    }
+  } else {
+#pragma unroll
+    for (int dir = 0; dir < NX + NU; ++dir) {
+      T col[NX];
+      rk4_jvp<M, T>(prm, h, xt, ut, dir, col);
+#pragma unroll
+      for (int r = 0; r < NX; ++r) {
+        if (dir < NX) MT.A(r, dir) = col[r];
+        else MT.B(r, dir - NX) = col[r];
+      }
     }
   }
 }

@@ -53,6 +53,28 @@ template <class T> __device__ __forceinline__ Dual<T> operator/(T a, Dual<T> b) 
   return {q, -q * b.d / b.v};
 }
 
+// Two tangent directions on one value (the Jacobian passes of the FP32 path):
+// the value is computed once for both; each tangent takes exactly the
+// operations of Dual<T>, so the columns are those of two Dual passes.
+template <class T>
+struct Dual2 {
+  T v, d0, d1;
+};
+template <class T> struct BaseOf<Dual2<T>> { typedef T type; };
+template <class T> __device__ __forceinline__ Dual2<T> operator+(Dual2<T> a, Dual2<T> b) { return {a.v + b.v, a.d0 + b.d0, a.d1 + b.d1}; }
+template <class T> __device__ __forceinline__ Dual2<T> operator-(Dual2<T> a, Dual2<T> b) { return {a.v - b.v, a.d0 - b.d0, a.d1 - b.d1}; }
+template <class T> __device__ __forceinline__ Dual2<T> operator-(Dual2<T> a) { return {-a.v, -a.d0, -a.d1}; }
+template <class T> __device__ __forceinline__ Dual2<T> operator*(Dual2<T> a, Dual2<T> b) {
+  return {a.v * b.v, a.d0 * b.v + a.v * b.d0, a.d1 * b.v + a.v * b.d1};
+}
+template <class T> __device__ __forceinline__ Dual2<T> operator+(Dual2<T> a, T b) { return {a.v + b, a.d0, a.d1}; }
+template <class T> __device__ __forceinline__ Dual2<T> operator+(T b, Dual2<T> a) { return {a.v + b, a.d0, a.d1}; }
+template <class T> __device__ __forceinline__ Dual2<T> operator-(Dual2<T> a, T b) { return {a.v - b, a.d0, a.d1}; }
+template <class T> __device__ __forceinline__ Dual2<T> operator-(T b, Dual2<T> a) { return {b - a.v, -a.d0, -a.d1}; }
+template <class T> __device__ __forceinline__ Dual2<T> operator*(Dual2<T> a, T b) { return {a.v * b, a.d0 * b, a.d1 * b}; }
+template <class T> __device__ __forceinline__ Dual2<T> operator*(T b, Dual2<T> a) { return {a.v * b, a.d0 * b, a.d1 * b}; }
+template <class T> __device__ __forceinline__ Dual2<T> operator/(Dual2<T> a, T b) { return {a.v / b, a.d0 / b, a.d1 / b}; }
+
 __device__ __forceinline__ float sin_(float a) { return sinf(a); }
 __device__ __forceinline__ float cos_(float a) { return cosf(a); }
 __device__ __forceinline__ float sqrt_(float a) { return sqrtf(a); }
@@ -69,6 +91,27 @@ template <class T> __device__ __forceinline__ Dual<T> cos_(Dual<T> a) { return {
 template <class T> __device__ __forceinline__ Dual<T> sqrt_(Dual<T> a) {
   T s = sqrt_(a.v);
   return {s, s > T(0) ? a.d / (T(2) * s) : T(0)};
+}
+// Dual2<float> as Dual<float> per tangent (one reciprocal per division)
+__device__ __forceinline__ Dual2<float> operator/(Dual2<float> a, Dual2<float> b) {
+  const float r = __frcp_rn(b.v), q = a.v * r;
+  return {q, (a.d0 - q * b.d0) * r, (a.d1 - q * b.d1) * r};
+}
+__device__ __forceinline__ Dual2<float> operator/(float a, Dual2<float> b) {
+  const float r = __frcp_rn(b.v), q = a * r;
+  return {q, -q * b.d0 * r, -q * b.d1 * r};
+}
+template <class T> __device__ __forceinline__ Dual2<T> sin_(Dual2<T> a) {
+  const T c = cos_(a.v);
+  return {sin_(a.v), c * a.d0, c * a.d1};
+}
+template <class T> __device__ __forceinline__ Dual2<T> cos_(Dual2<T> a) {
+  const T sn = sin_(a.v);
+  return {cos_(a.v), -sn * a.d0, -sn * a.d1};
+}
+template <class T> __device__ __forceinline__ Dual2<T> sqrt_(Dual2<T> a) {
+  T s = sqrt_(a.v);
+  return {s, s > T(0) ? a.d0 / (T(2) * s) : T(0), s > T(0) ? a.d1 / (T(2) * s) : T(0)};
 }
 
 // ------------------------------------------------------------------ models
@@ -242,6 +285,21 @@ __device__ __forceinline__ void rk4_jvp(const P* prm, double h, const X* x, cons
   rk4<M, Dual<T>, P>(prm, h, xd, ud, out);
 #pragma unroll
   for (int j = 0; j < NX; ++j) col[j] = out[j].d;
+}
+
+// Columns `dir0` and `dir1` of [A B] in one forward-mode pass (two tangents).
+template <class M, class T, class X, class P>
+__device__ __forceinline__ void rk4_jvp2(const P* prm, double h, const X* x, const X* u, int dir0, int dir1, T* col0,
+                                         T* col1) {
+  constexpr int NX = M::NX, NU = M::NU;
+  Dual2<T> xd[NX], ud[NU], out[NX];
+#pragma unroll
+  for (int j = 0; j < NX; ++j) xd[j] = {(T)x[j], (T)(dir0 == j ? 1 : 0), (T)(dir1 == j ? 1 : 0)};
+#pragma unroll
+  for (int j = 0; j < NU; ++j) ud[j] = {(T)u[j], (T)(dir0 == NX + j ? 1 : 0), (T)(dir1 == NX + j ? 1 : 0)};
+  rk4<M, Dual2<T>, P>(prm, h, xd, ud, out);
+#pragma unroll
+  for (int j = 0; j < NX; ++j) { col0[j] = out[j].d0; col1[j] = out[j].d1; }
 }
 
 // ------------------------------------------------------------------ projections
