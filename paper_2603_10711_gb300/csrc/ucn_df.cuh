@@ -82,6 +82,17 @@ __device__ __forceinline__ DF df_mul(DF a, float b) {
   p.lo = __fmaf_rn(a.lo, b, p.lo);
   return df_quick_two_sum(p.hi, p.lo);
 }
+// a + b c: the product exact in its high parts plus the cross terms, then one
+// sum of the pair (Dekker's add without the separate low-part sum); the error
+// is a few units of 2^-48 relative to |a| + |b c| -- what an RK4 update
+// x + h k needs -- at about half the instructions of a product and a sum.
+__device__ __forceinline__ DF df_fma(DF a, DF b, DF c) {
+  DF p = df_two_prod(b.hi, c.hi);
+  p.lo = __fmaf_rn(b.hi, c.lo, __fmaf_rn(b.lo, c.hi, p.lo));
+  DF s = df_two_sum(a.hi, p.hi);
+  s.lo = __fadd_rn(s.lo, __fadd_rn(a.lo, p.lo));
+  return df_quick_two_sum(s.hi, s.lo);
+}
 __device__ __forceinline__ DF df_div(DF a, DF b) {
   const float q1 = __fdiv_rn(a.hi, b.hi);
   const DF r = df_sub(a, df_mul(b, q1));   // exact-enough residual a - q1 b

@@ -247,6 +247,10 @@ struct Mars14 {
   }
 };
 
+// a + b c in the type of a and c (one fused pass for double-float).
+template <class S, class R> __device__ __forceinline__ S fma_(S a, R b, S c) { return a + b * c; }
+__device__ __forceinline__ DF fma_(DF a, DF b, DF c) { return df_fma(a, b, c); }
+
 // Classical fourth-order Runge-Kutta step (Eq. (1b)) with the step h and its
 // multiples h/2, h/6 given in the base type R of S.
 template <class M, class S, class P, class R>
@@ -255,16 +259,16 @@ __device__ __forceinline__ void rk4h(const P* prm, R h, R hh, R h6, const S* x, 
   S k[NX], t[NX], acc[NX];
   M::f(prm, x, u, k);
 #pragma unroll
-  for (int j = 0; j < NX; ++j) { acc[j] = k[j]; t[j] = x[j] + hh * k[j]; }
+  for (int j = 0; j < NX; ++j) { acc[j] = k[j]; t[j] = fma_(x[j], hh, k[j]); }
   M::f(prm, t, u, k);
 #pragma unroll
-  for (int j = 0; j < NX; ++j) { acc[j] = acc[j] + R(2) * k[j]; t[j] = x[j] + hh * k[j]; }
+  for (int j = 0; j < NX; ++j) { acc[j] = fma_(acc[j], R(2), k[j]); t[j] = fma_(x[j], hh, k[j]); }
   M::f(prm, t, u, k);
 #pragma unroll
-  for (int j = 0; j < NX; ++j) { acc[j] = acc[j] + R(2) * k[j]; t[j] = x[j] + h * k[j]; }
+  for (int j = 0; j < NX; ++j) { acc[j] = fma_(acc[j], R(2), k[j]); t[j] = fma_(x[j], h, k[j]); }
   M::f(prm, t, u, k);
 #pragma unroll
-  for (int j = 0; j < NX; ++j) xn[j] = x[j] + h6 * (acc[j] + k[j]);
+  for (int j = 0; j < NX; ++j) xn[j] = fma_(x[j], h6, acc[j] + k[j]);
 }
 
 template <class M, class S, class P>
