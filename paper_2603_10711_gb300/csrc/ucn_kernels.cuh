@@ -588,8 +588,8 @@ __device__ __forceinline__ void node_jacobians(const Node<T, AOS>& nd, const MS&
 // trust-region boxes of Eq. (2c) (with the boundary conditions of Eq. (1c)
 // as degenerate boxes at nodes 0 and N), and the mirror-set data.
 template <class M, class T, bool AOS>
-__device__ void node_setup(const Node<T, AOS>& nd, const Layout& L, const ProblemDev& P, int b, double radius,
-                           T re, T rg, NodeConst<M, T>& K) {
+__device__ void node_setup(const Node<T, AOS>& nd, const Layout& L, const ProblemDev& P, const Inst<T>& I, int b,
+                           double radius, T re, T rg, NodeConst<M, T>& K) {
   constexpr int NX = M::NX, NU = M::NU;
   const int i = nd.i, N = nd.N;
   typename Node<T, AOS>::W xb[NX], ub[NU];
@@ -600,11 +600,18 @@ __device__ void node_setup(const Node<T, AOS>& nd, const Layout& L, const Proble
     typedef CB<M> C;
     const DF* cb = nd.c;
     const T rad = (T)radius;
+    // running nodes of a problem without running state cost (the Mars batch):
+    // zero gradient and weight without the double-float product
+    const bool cost = term || I.run_cost;
     for (int j = 0; j < NX; ++j) {
       const DF w = term ? cb[C::QNd + j] : cb[C::Qd + j];
-      DF gq = df_mul(df_sub(xb[j], cb[C::Xref + j]), w);
-      if (term) gq = df_add(gq, cb[C::QN + j]);
-      K.q[j] = df_to_float(gq);
+      if (cost) {
+        DF gq = df_mul(df_sub(xb[j], cb[C::Xref + j]), w);
+        if (term) gq = df_add(gq, cb[C::QN + j]);
+        K.q[j] = df_to_float(gq);
+      } else {
+        K.q[j] = T(0);
+      }
       K.hd[j] = df_to_float(w) + rg + (i > 0 ? re : T(0));
       T lo = fmaxf(wide_diff<T>(cb[C::Xlo + j], xb[j]), -rad);
       T hi = fminf(wide_diff<T>(cb[C::Xhi + j], xb[j]), rad);
@@ -617,7 +624,7 @@ __device__ void node_setup(const Node<T, AOS>& nd, const Layout& L, const Proble
     if (!term) {
       for (int j = 0; j < NU; ++j) {
         const DF w = cb[C::Rd + j];
-        K.q[NX + j] = df_to_float(df_mul(df_sub(ub[j], cb[C::Uref + j]), w));
+        K.q[NX + j] = I.run_cost ? df_to_float(df_mul(df_sub(ub[j], cb[C::Uref + j]), w)) : T(0);
         K.hd[NX + j] = df_to_float(w) + rg;
         nd.at(Rec<M>::Ulo, j) = fmaxf(wide_diff<T>(cb[C::Ulo + j], ub[j]), -rad);
         nd.at(Rec<M>::Uhi, j) = fminf(wide_diff<T>(cb[C::Uhi + j], ub[j]), rad);
@@ -1589,7 +1596,7 @@ __global__ void __launch_bounds__(MAX_THREADS) admm_kernel(ProblemDev P, Layout 
   const Inst<T> I = make_inst<M, T>(P, b);
   NodeConst<M, T> K;
   if (active) {
-    node_setup<M, T, AOS>(nd, L, P, b, radius[b], re, rg, K);
+    node_setup<M, T, AOS>(nd, L, P, I, b, radius[b], re, rg, K);
     const bool ok = node_factor<M, T, AOS, NX + NU>(nd, MT, L, I, K, rd, rg);
     if (!ok) atomicOr(&sh.fail, 1);
     const double* sa = P.state_abs + P.soff[b];
@@ -1898,7 +1905,7 @@ __global__ void __launch_bounds__(MAX_THREADS) scp_kernel(ProblemDev P, Layout L
     const double radius = sh.radius;
     if (active) {
       if (i < N) node_jacobians<M, T, AOS>(nd, MT, I.prm, h);
-      node_setup<M, T, AOS>(nd, L, P, b, radius, re, rg, K);
+      node_setup<M, T, AOS>(nd, L, P, I, b, radius, re, rg, K);
       const bool ok = node_factor<M, T, AOS, NN>(nd, MT, L, I, K, rd, rg);
       if (!ok) atomicOr(&sh.fail, 1);
       node_reseed<M, T, AOS>(nd, L, I);

@@ -582,7 +582,7 @@ __global__ void __launch_bounds__(LANES_MAX_THREADS) scp_kernel_lanes(ProblemDev
     if (active) lanes_consts<M, T, AOS, TPN>(nd, P, b, q, re, rg, kq, khd);
     __syncthreads();
     if (dact) {
-      node_setup<M, T, AOS>(ndd, L, P, b, radius, re, rg, K);
+      node_setup<M, T, AOS>(ndd, L, P, I, b, radius, re, rg, K);
       const bool ok = node_factor<M, T, AOS, NN>(ndd, MTd, L, I, K, rd, rg);
       if (!ok) atomicOr(&sh.fail, 1);
       node_reseed<M, T, AOS>(ndd, L, I);
