@@ -109,13 +109,32 @@ __device__ __forceinline__ void lanes_jacobians(const Node<T, AOS>& nd, const MS
   for (int j = 0; j < NX; ++j) xt[j] = wide_to<T>(xb[j]);
 #pragma unroll
   for (int j = 0; j < NU; ++j) ut[j] = wide_to<T>(ub[j]);
-  for (int dir = q; dir < NX + NU; dir += TPN) {
-    T col[NX];
-    rk4_jvp<M, T>(prm, h, xt, ut, dir, col);
+  if constexpr (std::is_same<T, float>::value) {
+    // FP32: the lane's directions two per pass (q, q + TPN), (q + 2 TPN, q + 3 TPN), ...
+    for (int dir = q; dir < NX + NU; dir += 2 * TPN) {
+      const int dir1 = dir + TPN;
+      T col[NX], col1[NX];
+      if (dir1 < NX + NU) rk4_jvp2<M, T>(prm, h, xt, ut, dir, dir1, col, col1);
+      else rk4_jvp<M, T>(prm, h, xt, ut, dir, col);
 #pragma unroll
-    for (int r = 0; r < NX; ++r) {
-      if (dir < NX) MT.A(r, dir) = col[r];
-      else MT.B(r, dir - NX) = col[r];
+      for (int r = 0; r < NX; ++r) {
+        if (dir < NX) MT.A(r, dir) = col[r];
+        else MT.B(r, dir - NX) = col[r];
+        if (dir1 < NX + NU) {
+          if (dir1 < NX) MT.A(r, dir1) = col1[r];
+          else MT.B(r, dir1 - NX) = col1[r];
+        }
+      }
+    }
+  } else {
+    for (int dir = q; dir < NX + NU; dir += TPN) {
+      T col[NX];
+      rk4_jvp<M, T>(prm, h, xt, ut, dir, col);
+#pragma unroll
+      for (int r = 0; r < NX; ++r) {
+        if (dir < NX) MT.A(r, dir) = col[r];
+        else MT.B(r, dir - NX) = col[r];
+      }
     }
   }
 }
