@@ -101,3 +101,15 @@ def test_null_arguments_are_rejected(ucn):
     assert lib.ucn_linearize(None, None, None, None, None, None, None) == ucn.UCN_EINVAL
     assert lib.ucn_state_export(None, None, None) == ucn.UCN_EINVAL
     assert lib.ucn_total_x(None) == -1
+
+
+def test_double_float_check_validates_before_any_launch(ucn):
+    # argument errors return before the library touches a device
+    lib = ucn.lib()
+    fake = C.c_void_p(16)   # never dereferenced on these paths
+    assert lib.ucn_df_check(ucn.UCN_DF_ADD, None, None, None, 0.0, 4, fake, None) == ucn.UCN_EINVAL
+    assert lib.ucn_df_check(ucn.UCN_DF_ADD, fake, fake, None, 0.0, -1, fake, None) == ucn.UCN_EINVAL
+    assert lib.ucn_df_check(ucn.UCN_DF_ADD, fake, fake, None, 0.0, 4, None, None) == ucn.UCN_EINVAL
+    assert lib.ucn_df_check(ucn.UCN_DF_ADD, fake, fake, None, 0.0, 0, fake, None) == ucn.UCN_OK   # nothing to do
+    assert lib.ucn_df_check(7, fake, fake, None, 0.0, 4, fake, None) == ucn.UCN_EINVAL          # unknown op
+    assert lib.ucn_df_check(ucn.UCN_DF_RK4 + 9, fake, fake, fake, 0.1, 4, fake, None) == ucn.UCN_EINVAL
