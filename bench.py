@@ -339,8 +339,8 @@ def run_serving(args):
     ms = dict(W.mars_batch(1).settings, rho_final=1e7, scp_iters=80, admm_iters=60)
 
     def servers(prec, slots):
-        return {1: serving.Server(1, prec, max_slots=slots, max_horizon=120, max_obs=30, lanes=4, settings=qs),
-                2: serving.Server(2, prec, max_slots=slots, max_horizon=200, lanes=4, settings=ms)}
+        return {1: serving.Server(1, prec, max_slots=slots, max_horizon=120, max_obs=30, lanes=16, settings=qs),
+                2: serving.Server(2, prec, max_slots=slots, max_horizon=200, lanes=16, settings=ms)}
 
     sv = servers(ucn.UCN_PREC_FP32_REFINE, 512)
     serving.run_stream(stream[:32], sv)                # warm-up
