@@ -554,19 +554,31 @@ __device__ __forceinline__ void node_jacobians(const Node<T, AOS>& nd, const MS&
 #pragma unroll
   for (int j = 0; j < NU; ++j) ut[j] = wide_to<T>(ub[j]);
   if constexpr (std::is_same<T, float>::value) {
-    // FP32: two columns per pass (the value of the RK4 map is computed once for both)
+    // FP32: five columns per pass (the value of the RK4 map once for the five),
+    // the remainder one column per pass
+    constexpr int KD = 5;
 #pragma unroll
-    for (int dir = 0; dir < NX + NU; dir += 2) {
-      T col[NX], col1[NX];
-      if (dir + 1 < NX + NU) rk4_jvp2<M, T>(prm, h, xt, ut, dir, dir + 1, col, col1);
-      else rk4_jvp<M, T>(prm, h, xt, ut, dir, col);
+    for (int dir = 0; dir < NX + NU; dir += KD) {
+      if (dir + KD <= NX + NU) {
+        T cols[KD][NX];
+        rk4_jvpn<M, T, KD>(prm, h, xt, ut, dir, 1, cols);
 #pragma unroll
-      for (int r = 0; r < NX; ++r) {
-        if (dir < NX) MT.A(r, dir) = col[r];
-        else MT.B(r, dir - NX) = col[r];
-        if (dir + 1 < NX + NU) {
-          if (dir + 1 < NX) MT.A(r, dir + 1) = col1[r];
-          else MT.B(r, dir + 1 - NX) = col1[r];
+        for (int q = 0; q < KD; ++q)
+#pragma unroll
+          for (int r = 0; r < NX; ++r) {
+            if (dir + q < NX) MT.A(r, dir + q) = cols[q][r];
+            else MT.B(r, dir + q - NX) = cols[q][r];
+          }
+      } else {
+#pragma unroll
+        for (int d1 = dir; d1 < NX + NU; ++d1) {
+          T col[NX];
+          rk4_jvp<M, T>(prm, h, xt, ut, d1, col);
+#pragma unroll
+          for (int r = 0; r < NX; ++r) {
+            if (d1 < NX) MT.A(r, d1) = col[r];
+            else MT.B(r, d1 - NX) = col[r];
+          }
         }
       }
     }

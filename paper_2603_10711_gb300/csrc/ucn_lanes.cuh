@@ -113,16 +113,16 @@ __device__ __forceinline__ void lanes_jacobians(const Node<T, AOS>& nd, const MS
     // FP32: the lane's directions two per pass (q, q + TPN), (q + 2 TPN, q + 3 TPN), ...
     for (int dir = q; dir < NX + NU; dir += 2 * TPN) {
       const int dir1 = dir + TPN;
-      T col[NX], col1[NX];
-      if (dir1 < NX + NU) rk4_jvp2<M, T>(prm, h, xt, ut, dir, dir1, col, col1);
-      else rk4_jvp<M, T>(prm, h, xt, ut, dir, col);
+      T cols[2][NX];
+      if (dir1 < NX + NU) rk4_jvpn<M, T, 2>(prm, h, xt, ut, dir, TPN, cols);
+      else rk4_jvp<M, T>(prm, h, xt, ut, dir, cols[0]);
 #pragma unroll
       for (int r = 0; r < NX; ++r) {
-        if (dir < NX) MT.A(r, dir) = col[r];
-        else MT.B(r, dir - NX) = col[r];
+        if (dir < NX) MT.A(r, dir) = cols[0][r];
+        else MT.B(r, dir - NX) = cols[0][r];
         if (dir1 < NX + NU) {
-          if (dir1 < NX) MT.A(r, dir1) = col1[r];
-          else MT.B(r, dir1 - NX) = col1[r];
+          if (dir1 < NX) MT.A(r, dir1) = cols[1][r];
+          else MT.B(r, dir1 - NX) = cols[1][r];
         }
       }
     }

@@ -53,27 +53,67 @@ template <class T> __device__ __forceinline__ Dual<T> operator/(T a, Dual<T> b) 
   return {q, -q * b.d / b.v};
 }
 
-// Two tangent directions on one value (the Jacobian passes of the FP32 path):
-// the value is computed once for both; each tangent takes exactly the
-// operations of Dual<T>, so the columns are those of two Dual passes.
-template <class T>
-struct Dual2 {
-  T v, d0, d1;
+// K tangent directions on one value (the Jacobian passes of the FP32 path): the
+// value is computed once for all K; each tangent takes exactly the operations
+// of Dual<T>, so the columns are those of K single-tangent passes.
+template <class T, int K>
+struct DualN {
+  T v, d[K];
 };
-template <class T> struct BaseOf<Dual2<T>> { typedef T type; };
-template <class T> __device__ __forceinline__ Dual2<T> operator+(Dual2<T> a, Dual2<T> b) { return {a.v + b.v, a.d0 + b.d0, a.d1 + b.d1}; }
-template <class T> __device__ __forceinline__ Dual2<T> operator-(Dual2<T> a, Dual2<T> b) { return {a.v - b.v, a.d0 - b.d0, a.d1 - b.d1}; }
-template <class T> __device__ __forceinline__ Dual2<T> operator-(Dual2<T> a) { return {-a.v, -a.d0, -a.d1}; }
-template <class T> __device__ __forceinline__ Dual2<T> operator*(Dual2<T> a, Dual2<T> b) {
-  return {a.v * b.v, a.d0 * b.v + a.v * b.d0, a.d1 * b.v + a.v * b.d1};
+template <class T, int K> struct BaseOf<DualN<T, K>> { typedef T type; };
+template <class T, int K> __device__ __forceinline__ DualN<T, K> operator+(DualN<T, K> a, DualN<T, K> b) {
+  DualN<T, K> r;
+  r.v = a.v + b.v;
+#pragma unroll
+  for (int q = 0; q < K; ++q) r.d[q] = a.d[q] + b.d[q];
+  return r;
 }
-template <class T> __device__ __forceinline__ Dual2<T> operator+(Dual2<T> a, T b) { return {a.v + b, a.d0, a.d1}; }
-template <class T> __device__ __forceinline__ Dual2<T> operator+(T b, Dual2<T> a) { return {a.v + b, a.d0, a.d1}; }
-template <class T> __device__ __forceinline__ Dual2<T> operator-(Dual2<T> a, T b) { return {a.v - b, a.d0, a.d1}; }
-template <class T> __device__ __forceinline__ Dual2<T> operator-(T b, Dual2<T> a) { return {b - a.v, -a.d0, -a.d1}; }
-template <class T> __device__ __forceinline__ Dual2<T> operator*(Dual2<T> a, T b) { return {a.v * b, a.d0 * b, a.d1 * b}; }
-template <class T> __device__ __forceinline__ Dual2<T> operator*(T b, Dual2<T> a) { return {a.v * b, a.d0 * b, a.d1 * b}; }
-template <class T> __device__ __forceinline__ Dual2<T> operator/(Dual2<T> a, T b) { return {a.v / b, a.d0 / b, a.d1 / b}; }
+template <class T, int K> __device__ __forceinline__ DualN<T, K> operator-(DualN<T, K> a, DualN<T, K> b) {
+  DualN<T, K> r;
+  r.v = a.v - b.v;
+#pragma unroll
+  for (int q = 0; q < K; ++q) r.d[q] = a.d[q] - b.d[q];
+  return r;
+}
+template <class T, int K> __device__ __forceinline__ DualN<T, K> operator-(DualN<T, K> a) {
+  DualN<T, K> r;
+  r.v = -a.v;
+#pragma unroll
+  for (int q = 0; q < K; ++q) r.d[q] = -a.d[q];
+  return r;
+}
+template <class T, int K> __device__ __forceinline__ DualN<T, K> operator*(DualN<T, K> a, DualN<T, K> b) {
+  DualN<T, K> r;
+  r.v = a.v * b.v;
+#pragma unroll
+  for (int q = 0; q < K; ++q) r.d[q] = a.d[q] * b.v + a.v * b.d[q];
+  return r;
+}
+template <class T, int K> __device__ __forceinline__ DualN<T, K> operator+(DualN<T, K> a, T b) { a.v = a.v + b; return a; }
+template <class T, int K> __device__ __forceinline__ DualN<T, K> operator+(T b, DualN<T, K> a) { a.v = a.v + b; return a; }
+template <class T, int K> __device__ __forceinline__ DualN<T, K> operator-(DualN<T, K> a, T b) { a.v = a.v - b; return a; }
+template <class T, int K> __device__ __forceinline__ DualN<T, K> operator-(T b, DualN<T, K> a) {
+  DualN<T, K> r;
+  r.v = b - a.v;
+#pragma unroll
+  for (int q = 0; q < K; ++q) r.d[q] = -a.d[q];
+  return r;
+}
+template <class T, int K> __device__ __forceinline__ DualN<T, K> operator*(DualN<T, K> a, T b) {
+  DualN<T, K> r;
+  r.v = a.v * b;
+#pragma unroll
+  for (int q = 0; q < K; ++q) r.d[q] = a.d[q] * b;
+  return r;
+}
+template <class T, int K> __device__ __forceinline__ DualN<T, K> operator*(T b, DualN<T, K> a) { return a * b; }
+template <class T, int K> __device__ __forceinline__ DualN<T, K> operator/(DualN<T, K> a, T b) {
+  DualN<T, K> r;
+  r.v = a.v / b;
+#pragma unroll
+  for (int q = 0; q < K; ++q) r.d[q] = a.d[q] / b;
+  return r;
+}
 
 __device__ __forceinline__ float sin_(float a) { return sinf(a); }
 __device__ __forceinline__ float cos_(float a) { return cosf(a); }
@@ -92,26 +132,45 @@ template <class T> __device__ __forceinline__ Dual<T> sqrt_(Dual<T> a) {
   T s = sqrt_(a.v);
   return {s, s > T(0) ? a.d / (T(2) * s) : T(0)};
 }
-// Dual2<float> as Dual<float> per tangent (one reciprocal per division)
-__device__ __forceinline__ Dual2<float> operator/(Dual2<float> a, Dual2<float> b) {
-  const float r = __frcp_rn(b.v), q = a.v * r;
-  return {q, (a.d0 - q * b.d0) * r, (a.d1 - q * b.d1) * r};
+// DualN<float> as Dual<float> per tangent (one reciprocal per division)
+template <int K> __device__ __forceinline__ DualN<float, K> operator/(DualN<float, K> a, DualN<float, K> b) {
+  const float rr = __frcp_rn(b.v);
+  DualN<float, K> r;
+  r.v = a.v * rr;
+#pragma unroll
+  for (int q = 0; q < K; ++q) r.d[q] = (a.d[q] - r.v * b.d[q]) * rr;
+  return r;
 }
-__device__ __forceinline__ Dual2<float> operator/(float a, Dual2<float> b) {
-  const float r = __frcp_rn(b.v), q = a * r;
-  return {q, -q * b.d0 * r, -q * b.d1 * r};
+template <int K> __device__ __forceinline__ DualN<float, K> operator/(float a, DualN<float, K> b) {
+  const float rr = __frcp_rn(b.v);
+  DualN<float, K> r;
+  r.v = a * rr;
+#pragma unroll
+  for (int q = 0; q < K; ++q) r.d[q] = -r.v * b.d[q] * rr;
+  return r;
 }
-template <class T> __device__ __forceinline__ Dual2<T> sin_(Dual2<T> a) {
+template <class T, int K> __device__ __forceinline__ DualN<T, K> sin_(DualN<T, K> a) {
   const T c = cos_(a.v);
-  return {sin_(a.v), c * a.d0, c * a.d1};
+  DualN<T, K> r;
+  r.v = sin_(a.v);
+#pragma unroll
+  for (int q = 0; q < K; ++q) r.d[q] = c * a.d[q];
+  return r;
 }
-template <class T> __device__ __forceinline__ Dual2<T> cos_(Dual2<T> a) {
+template <class T, int K> __device__ __forceinline__ DualN<T, K> cos_(DualN<T, K> a) {
   const T sn = sin_(a.v);
-  return {cos_(a.v), -sn * a.d0, -sn * a.d1};
+  DualN<T, K> r;
+  r.v = cos_(a.v);
+#pragma unroll
+  for (int q = 0; q < K; ++q) r.d[q] = -sn * a.d[q];
+  return r;
 }
-template <class T> __device__ __forceinline__ Dual2<T> sqrt_(Dual2<T> a) {
-  T s = sqrt_(a.v);
-  return {s, s > T(0) ? a.d0 / (T(2) * s) : T(0), s > T(0) ? a.d1 / (T(2) * s) : T(0)};
+template <class T, int K> __device__ __forceinline__ DualN<T, K> sqrt_(DualN<T, K> a) {
+  DualN<T, K> r;
+  r.v = sqrt_(a.v);
+#pragma unroll
+  for (int q = 0; q < K; ++q) r.d[q] = r.v > T(0) ? a.d[q] / (T(2) * r.v) : T(0);
+  return r;
 }
 
 // ------------------------------------------------------------------ models
@@ -291,19 +350,30 @@ __device__ __forceinline__ void rk4_jvp(const P* prm, double h, const X* x, cons
   for (int j = 0; j < NX; ++j) col[j] = out[j].d;
 }
 
-// Columns `dir0` and `dir1` of [A B] in one forward-mode pass (two tangents).
-template <class M, class T, class X, class P>
-__device__ __forceinline__ void rk4_jvp2(const P* prm, double h, const X* x, const X* u, int dir0, int dir1, T* col0,
-                                         T* col1) {
+// Columns dir0, dir0 + stride, ..., dir0 + (K - 1) stride of [A B] in one
+// forward-mode pass (K tangents); cols[q] receives column dir0 + q stride.
+template <class M, class T, int K, class X, class P>
+__device__ __forceinline__ void rk4_jvpn(const P* prm, double h, const X* x, const X* u, int dir0, int stride,
+                                         T (*cols)[M::NX]) {
   constexpr int NX = M::NX, NU = M::NU;
-  Dual2<T> xd[NX], ud[NU], out[NX];
+  DualN<T, K> xd[NX], ud[NU], out[NX];
 #pragma unroll
-  for (int j = 0; j < NX; ++j) xd[j] = {(T)x[j], (T)(dir0 == j ? 1 : 0), (T)(dir1 == j ? 1 : 0)};
+  for (int j = 0; j < NX; ++j) {
+    xd[j].v = (T)x[j];
 #pragma unroll
-  for (int j = 0; j < NU; ++j) ud[j] = {(T)u[j], (T)(dir0 == NX + j ? 1 : 0), (T)(dir1 == NX + j ? 1 : 0)};
-  rk4<M, Dual2<T>, P>(prm, h, xd, ud, out);
+    for (int q = 0; q < K; ++q) xd[j].d[q] = (T)(dir0 + q * stride == j ? 1 : 0);
+  }
 #pragma unroll
-  for (int j = 0; j < NX; ++j) { col0[j] = out[j].d0; col1[j] = out[j].d1; }
+  for (int j = 0; j < NU; ++j) {
+    ud[j].v = (T)u[j];
+#pragma unroll
+    for (int q = 0; q < K; ++q) ud[j].d[q] = (T)(dir0 + q * stride == NX + j ? 1 : 0);
+  }
+  rk4<M, DualN<T, K>, P>(prm, h, xd, ud, out);
+#pragma unroll
+  for (int j = 0; j < NX; ++j)
+#pragma unroll
+    for (int q = 0; q < K; ++q) cols[q][j] = out[j].d[q];
 }
 
 // ------------------------------------------------------------------ projections
