@@ -291,7 +291,7 @@ def run_ours(args, rank, world):
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (ADMM) + f64 (rollout, defect, acceptance)",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (ADMM) + f32-pair double-float (nominal, rollout, defects, merits) + f64 (acceptance test, results)",
         "data": "synthetic (seeded Mars descent dispersions)",
         "config": {"workload": WORKLOAD, "instances_per_gpu": B, "horizon": 100, "nx": 7, "nu": 3,
                    "admm_iters_per_scp": int(prob.settings["admm_iters"]), "scp_iter_cap": int(prob.settings["scp_iters"]),
