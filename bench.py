@@ -2,16 +2,20 @@
 
 Workload: the Mars powered-descent batch (1024 instances, N = 100, 3-DOF,
 |T| in [4.8, 19.2] kN, glide slope 86 deg), solved by the fused persistent
-SCP kernel in the FP32 + refinement path (ADMM in FP32, RK4 rollout /
-defect / acceptance in FP64).  One step = one ucn_scp_solve launch over the
-whole batch.  `value` counts only solves whose returned trajectory has max
-defect <= 1e-5.  The plain FP64 path is timed beside it on the same batch.
+SCP kernel in the FP32 + refinement path (ADMM in FP32; nominal, rollout and
+merits in double-float; acceptance test, returned trajectory and its defect
+in FP64).  One step = one ucn_scp_solve launch over the whole batch.  `value`
+counts only solves whose returned trajectory has max defect <= 1e-5 (an FP64
+RK4 defect of the returned doubles, computed by the kernel; the parity leg
+recomputes it with the oracle's RK4).  The plain FP64 path is timed beside it
+on the same batch.
 
   python bench.py [--steps K] [--warmup W] [--gpus N] [--impl ours|reference]
 
 Multi-GPU (torchrun): instances are independent, so every rank solves its
-own batch (weak scaling, no data-path collective); value = passing solves
-of all ranks / max time over ranks.
+shard of one seeded global batch of 1024 x N instances (weak scaling, no
+data-path collective); value = passing solves of all ranks / max time over
+ranks.
 """
 from __future__ import annotations
 
@@ -33,7 +37,7 @@ import workloads as W  # noqa: E402
 METRIC = "SCP solves/s at defect<=1e-5 (batched FP32+refine; plain FP64 beside it); p50/p99 ms"
 UNIT = "solves/s"
 WORKLOAD = "mars_batch_1024_N100"
-SM_COUNT, FP32_LANES = 152, 128
+FP32_LANES_PER_SM = 128   # FP32 FMA lanes per SM of Blackwell (compute capability 10.x)
 
 
 def flops_per_node_iter(nx, nu, mirror_flops, refine=True):
@@ -96,13 +100,14 @@ class ClockSampler:
          "clocks_event_reasons.sw_power_cap")
 
     def __init__(self, gpu_index):
+        import tempfile
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_rank%d.csv" % gpu_index)
+        fd, self.path = tempfile.mkstemp(prefix="ucn_clocks_gpu%d_" % gpu_index, suffix=".csv")
+        os.close(fd)
 
     def __enter__(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
                                           "--format=csv,noheader,nounits", "-lms", "100"],
@@ -127,6 +132,10 @@ class ClockSampler:
             rows = []
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
         sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
         mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
@@ -156,17 +165,26 @@ def shard_bounds(batch, rank, world):
     return lo, lo + per + (1 if rank < extra else 0)
 
 
-def make_problem(args, rank=0):
+def make_problem(args, rank=0, world=1):
+    """The rank's share of one seeded global batch of args.batch x world
+    instances (weak scaling: args.batch instances per rank; with one rank, the
+    whole batch)."""
     over = {}
     if args.scp_iters:
         over = dict(scp_iters=args.scp_iters, stop=0)
     if getattr(args, "admm_iters", 0):
         over["admm_iters"] = args.admm_iters
+    total = args.batch * world
     if getattr(args, "workload", "mars") == "quad_box":
-        return W.quad_box(args.batch, seed=2 + rank, settings=over)
-    if getattr(args, "workload", "mars") == "quad40":
-        return W.quad_box(args.batch, seed=2 + rank, N_range=(40, 40), obs_range=(8, 8), settings=over)
-    return W.mars_batch(args.batch, seed=1 + rank, settings=over)
+        prob = W.quad_box(total, seed=2, settings=over)
+    elif getattr(args, "workload", "mars") == "quad40":
+        prob = W.quad_box(total, seed=2, N_range=(40, 40), obs_range=(8, 8), settings=over)
+    else:
+        prob = W.mars_batch(total, seed=1, settings=over)
+    if world == 1:
+        return prob
+    lo, hi = shard_bounds(total, rank, world)
+    return prob.subset(np.arange(lo, hi))
 
 
 def run_kernel_only(args):
@@ -198,7 +216,7 @@ def run_ours(args, rank, world):
 
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
-    prob = make_problem(args, rank)
+    prob = make_problem(args, rank, world)
     B = prob.batch
     solver = ucn.Solver(prob, precision=ucn.UCN_PREC_FP32_REFINE, device=dev)
     stream = torch.cuda.current_stream(dev)
@@ -232,6 +250,8 @@ def run_ours(args, rank, world):
             lat.extend(((st["t_end_ns"] - t0) / 1e6).tolist())
             nodeiters += int(np.sum(st["scp_iters"].astype(np.int64) * (prob.N.astype(np.int64) + 1))) * int(prob.settings["admm_iters"])
     torch.cuda.synchronize()
+    # the last timed step's results, for the parity check against the oracle
+    x_last, u_last, st_timed = solver.x_out.cpu().numpy(), solver.u_out.cpu().numpy(), solver.stats_host()
     total = sum(times)
     if world > 1:
         total, passed_all = reduce_over_ranks(total, passed, dev)
@@ -285,7 +305,8 @@ def run_ours(args, rank, world):
     avg = total / args.steps if world == 1 else sum(times) / len(times)
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    peak_tf = SM_COUNT * FP32_LANES * 2 * sm_max * 1e6 / 1e12
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak_tf = sm_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     achieved = flops_launch / avg / 1e12
     st_last = solver.stats_host()
     out = {
@@ -308,7 +329,8 @@ def run_ours(args, rank, world):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
                      "frac": achieved / peak_tf, "traffic": recorded_traffic(),
                      "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
-                     "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 x %.0f MHz" % sm_max,
+                     "peak_note": "derived: %d SMs (read from the device) x %d FP32 lanes x 2 x %.0f MHz (max SM clock, "
+                                  "MEASURED_PEAKS.json)" % (sm_count, FP32_LANES_PER_SM, sm_max),
                      "algorithmic_flops_per_node_iter": flops_ni, "node_iters_per_launch": nodeiters / args.steps},
         "gpu_launches": args.steps,
         "clocks": clocks,
@@ -322,7 +344,7 @@ def run_ours(args, rank, world):
     if rho_out is not None:
         out["rho_study"] = rho_out
     if rank == 0 and not args.no_cpu_baseline and world == 1:
-        out["cpu_baseline"] = cpu_baseline(args)
+        out["cpu_baseline"], out["parity"] = cpu_baseline(args, (x_last, u_last, st_timed))
     solver.close()
     return out
 
@@ -472,23 +494,51 @@ def run_scenarios(args):
 
 def oracle_sample(args, n=None):
     """The FP64 CPU oracle on a bounded sample of the same workload (n instances,
-    evenly spaced; default --cpu-sample)."""
+    evenly spaced; default --cpu-sample).  Returns (passed, n, seconds, threads,
+    sample indices, the oracle's (x, u, stats), the sample problem)."""
     import oracle
     prob = W.mars_batch(args.batch, seed=1)
     threads = oracle.max_threads()
     n = min(args.batch, max(threads, args.cpu_sample if n is None else n))
-    sub = prob.subset(np.arange(n) * (prob.batch // n))
+    idx = np.arange(n) * (prob.batch // n)
+    sub = prob.subset(idx)
     t0 = time.perf_counter()
-    _, _, st, _ = oracle.scp_solve(sub, nthreads=threads)
+    xr, ur, st, _ = oracle.scp_solve(sub, nthreads=threads)
     dt = time.perf_counter() - t0
     passed = int(np.sum(st[:, 0] <= 1e-5))
-    return passed, n, dt, threads
+    return passed, n, dt, threads, idx, (xr, ur, st), sub
 
 
-def cpu_baseline(args):
-    passed, n, dt, threads = oracle_sample(args)
-    return {"value": passed / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+def cpu_baseline(args, gpu_result=None):
+    """The oracle timed on the host cores, and -- on the same instances, from its
+    trajectories -- the parity of the GPU's last timed step: every sampled
+    trajectory against the oracle's at 1e-4 after the same SCP iteration count,
+    and the FP64 defect of the GPU's returned doubles by the oracle's RK4."""
+    passed, n, dt, threads, idx, ref, sub = oracle_sample(args)
+    base = {"value": passed / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": "%d of the %d Mars instances (every %d-th), %.1f s, %d passed" % (n, args.batch, args.batch // n, dt, passed)}
+    if gpu_result is None:
+        return base, None
+    import oracle
+    xg, ug, st = gpu_result
+    prob = W.mars_batch(args.batch, seed=1)
+    xs = np.concatenate([xg[prob.xoff[b]:prob.xoff[b] + prob.N[b] + 1] for b in idx])
+    us = np.concatenate([ug[prob.uoff[b]:prob.uoff[b] + prob.N[b]] for b in idx])
+    t0 = time.perf_counter()
+    r = oracle.compare_batch(sub, xs, us, st["scp_iters"][idx], ref, 1e-4, nthreads=threads)
+    same = np.ones(n, dtype=bool)
+    same[r["mismatch"]] = False
+    parity = dict(r["summary"])
+    parity.update({
+        "max_rel_err_same_iters_as_oracle": float(r["err"][same].max()) if same.any() else None,
+        "gpu_defect_vs_oracle_rk4_max_abs": float(np.abs(st["defect"][idx] - r["fp64_defect"]).max()),
+        "check_s": time.perf_counter() - t0,
+        "definition": "per instance |gpu - oracle|_max / max(1, |oracle|_max) over x and u of the returned "
+                      "trajectory, the oracle (FP64 CPU) solving the same inputs; where the stop test "
+                      "(defect <= 1e-5) ended the two solves after different SCP iteration counts the "
+                      "oracle is re-run to the GPU's count (scp_iters_mismatch); fp64_defect_* = max_i "
+                      "|RK4(x_i, u_i) - x_{i+1}|_inf of the GPU's returned doubles by the oracle's FP64 RK4"})
+    return base, parity
 
 
 def run_reference(args, rank, world):
@@ -498,7 +548,7 @@ def run_reference(args, rank, world):
     for _ in range(args.warmup):
         pass   # the oracle has no warm state; warm-up steps are not needed on the CPU
     for _ in range(args.steps):
-        passed, n, dt, threads = oracle_sample(args, args.ref_sample)
+        passed, n, dt, threads = oracle_sample(args, args.ref_sample)[:4]
         times.append(dt); passed_all += passed; n_all += n
     value = passed_all / sum(times)
     return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,

@@ -138,11 +138,16 @@ typedef struct {
 
 /* Per-instance result of ucn_scp_solve (device memory, 128 bytes). */
 typedef struct {
-  double defect;        /* max_i |RK4(x_i,u_i) - x_{i+1}|_inf of the returned trajectory */
+  double defect;        /* max_i |RK4(x_i,u_i) - x_{i+1}|_inf of the returned trajectory, by FP64
+                           RK4 steps on the returned doubles on both paths (the status's
+                           defect_tol test uses it) */
   double cost;          /* phi(x_N) + sum l(x_i,u_i) of the returned trajectory */
   double merit;         /* cost + w_d * sum_i |defect_i|_1 */
-  double primal_res;    /* ADMM primal residual of the last ADMM call (FP64 sum) */
-  double dual_res;      /* ADMM dual residual of the last ADMM step (FP64 sum) */
+  double primal_res;    /* ADMM primal residual of the last ADMM iteration (Sec. III-B, Step 4) */
+  double dual_res;      /* ADMM dual residual of the last ADMM iteration; both norms are sums of
+                           squared iterate differences accumulated in FP64 (FP64 path) or in
+                           double-float (FP32 path: exact differences of the FP32 iterates,
+                           relative error of the sums below 1e-11; see ucn_df_check) */
   double tr_radius;     /* trust-region radius at exit */
   double step;          /* |candidate - nominal|_inf of the last SCP iteration */
   int scp_iters;        /* SCP iterations run */
@@ -254,6 +259,10 @@ ucn_status ucn_mpc_shift(ucn_problem* prob, const double* x_d, const double* u_d
  *   op  UCN_DF_ADD, _SUB, _MUL, _DIV: out[k] = a[k] op b[k];
  *       UCN_DF_SQRT: out[k] = sqrt(a[k]); UCN_DF_ROUND: out[k] = a[k] through
  *       double-float and back;
+ *       UCN_DF_SQDIFF_SUM: out[0] = sum_k (float(a[k]) - float(b[k]))^2 and
+ *       UCN_DF_SQ_SUM: out[0] = sum_k float(a[k])^2, accumulated in order by the
+ *       arithmetic that sums the FP32 path's ADMM residual norms (exact
+ *       differences of the float values, double-float sums; one thread);
  *       UCN_DF_RK4 + model: one RK4 step of the model (Eq. (1b)) per row,
  *       a = x [n][nx], b = u [n][nu], prm = model_params [8], step h;
  *       out = [n][nx].
@@ -266,6 +275,8 @@ ucn_status ucn_mpc_shift(ucn_problem* prob, const double* x_d, const double* u_d
 #define UCN_DF_DIV 3
 #define UCN_DF_SQRT 4
 #define UCN_DF_ROUND 5
+#define UCN_DF_SQDIFF_SUM 6
+#define UCN_DF_SQ_SUM 7
 #define UCN_DF_RK4 100
 ucn_status ucn_df_check(int op, const double* a_d, const double* b_d, const double* prm_d, double h, long long n,
                         double* out_d, void* stream);

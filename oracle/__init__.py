@@ -79,6 +79,8 @@ def lib():
             _lib.orc_linearize.argtypes = [C.c_int, _dp, C.c_double, _dp, _dp, _dp, _dp, _dp, _dp]
             _lib.orc_jac_complex_step.argtypes = [C.c_int, _dp, C.c_double, _dp, _dp, _dp, _dp]
             _lib.orc_project.argtypes = [C.c_int, C.c_int, C.c_double, _dp, _dp]
+            _lib.orc_scp_solve_iters.restype = C.c_int
+            _lib.orc_traj_defects.restype = C.c_int
         return _lib
 
 
@@ -243,6 +245,70 @@ def scp_solve(prob, nthreads: int = 0, xguess=None, uguess=None, log=False):
     lib().orc_scp_solve(C.byref(pin.c), _d(xg), _d(ug), _d(xo), _d(uo), _d(st),
                         _d(lg) if log else _dp(), C.c_int(nthreads))
     return xo, uo, st, lg
+
+
+def scp_solve_iters(prob, run_iters, nthreads: int = 0, xguess=None, uguess=None):
+    """SCP solve with exactly ``run_iters[b]`` SCP iterations per instance
+    (per scenario group: its first instance's entry), without the stop test and
+    with the penalty schedule of the cap.  Returns (x, u, stats[B,16])."""
+    pin = _Pinned(prob)
+    xg = _f64(prob.xguess if xguess is None else xguess)
+    ug = _f64(prob.uguess if uguess is None else uguess)
+    xo = np.zeros_like(xg); uo = np.zeros_like(ug)
+    st = np.zeros((prob.batch, NSTAT))
+    ri = np.ascontiguousarray(run_iters, dtype=np.int32)
+    assert ri.shape == (prob.batch,)
+    lib().orc_scp_solve_iters(C.byref(pin.c), _d(xg), _d(ug), _d(xo), _d(uo), _d(st),
+                              ri.ctypes.data_as(_ip), C.c_int(nthreads))
+    return xo, uo, st
+
+
+def traj_defects(prob, x, u):
+    """max_i |RK4(x_i, u_i) - x_{i+1}|_inf per instance of packed trajectories, FP64."""
+    pin = _Pinned(prob)
+    out = np.zeros(prob.batch)
+    lib().orc_traj_defects(C.byref(pin.c), _d(_f64(x)), _d(_f64(u)), _d(out))
+    return out
+
+
+def rel_err(a, b):
+    """Normwise relative difference with floor 1: |a - b|_max / max(1, |b|_max)."""
+    a = np.asarray(a, dtype=np.float64); b = np.asarray(b, dtype=np.float64)
+    return float(np.abs(a - b).max() / max(1.0, np.abs(b).max())) if b.size else 0.0
+
+
+def compare_batch(prob, x, u, iters, ref, tol, nthreads: int = 0):
+    """Element-by-element parity of packed trajectories (x, u) that ran
+    ``iters[b]`` SCP iterations against the oracle's solve ``ref = (xr, ur, sr)``
+    of the same inputs.  The stop test (max defect <= defect_tol) is a decision
+    on a floating-point value: where the two solves stopped after different
+    iteration counts, both stopping points are valid and the unique object to
+    compare is the trajectory after the same count, so the oracle is re-run to
+    exactly ``iters[b]`` iterations for those instances.  Returns a dict with
+    per-instance errors and a summary."""
+    xr, ur, sr = ref[0], ref[1], ref[2]
+    iters = np.asarray(iters).astype(np.int64)
+    mism = np.nonzero(iters != sr[:, 7].astype(np.int64))[0]
+    K = int(prob.settings.get("group", 1))
+    if K > 1 and mism.size:       # whole scenario groups
+        mism = np.unique(np.concatenate([np.arange(g * K, (g + 1) * K) for g in np.unique(mism // K)]))
+    xr = xr.copy(); ur = ur.copy()
+    if mism.size:
+        sub = prob.subset(mism)
+        xs, us, _ = scp_solve_iters(sub, iters[mism], nthreads=nthreads)
+        for k, b in enumerate(mism):
+            xr[prob.xoff[b]:prob.xoff[b] + prob.N[b] + 1] = xs[sub.xoff[k]:sub.xoff[k] + sub.N[k] + 1]
+            ur[prob.uoff[b]:prob.uoff[b] + prob.N[b]] = us[sub.uoff[k]:sub.uoff[k] + sub.N[k]]
+    err = np.zeros(prob.batch)
+    for b in range(prob.batch):
+        xo, uo, N = prob.xoff[b], prob.uoff[b], int(prob.N[b])
+        err[b] = max(rel_err(x[xo:xo + N + 1], xr[xo:xo + N + 1]), rel_err(u[uo:uo + N], ur[uo:uo + N]))
+    d64 = traj_defects(prob, x, u)
+    return {"err": err, "mismatch": mism, "fp64_defect": d64,
+            "summary": {"instances": int(prob.batch), "tol": tol, "max_rel_err": float(err.max()) if err.size else 0.0,
+                        "n_over_tol": int(np.sum(err > tol)), "scp_iters_mismatch": int(mism.size),
+                        "fp64_defect_max": float(d64.max()) if d64.size else 0.0,
+                        "n_fp64_defect_over_tol": int(np.sum(d64 > prob.settings["defect_tol"]))}}
 
 
 def max_threads() -> int:

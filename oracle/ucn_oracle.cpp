@@ -1141,8 +1141,13 @@ enum { NLOG = 8 };
 // A x + B u + d in place of f; ratio = (J(x_bar) - J(cand)) / (J(x_bar) - L(cand));
 // accept if ratio > 0 or the model decrease is <= 1e-12; radius halves below
 // 0.25, doubles (capped) above 0.75, floored at tr_min.
+//
+// run_iters > 0: run exactly that many iterations (at most scp_iters) without
+// the stop test -- the trajectory after a given iteration count, for comparing
+// solves whose stop tests landed on opposite sides of defect_tol.  The penalty
+// schedule stays that of the scp_iters cap.
 void scp_instance(const OrcProblem& P, int b, const double* xg, const double* ug,
-                  double* xout, double* uout, double* stat, double* log) {
+                  double* xout, double* uout, double* stat, double* log, int run_iters = 0) {
   const int N = P.N[b], nx = P.nx, nu = P.nu;
   const double* prm = P.params + b * 8;
   const double h = P.dt[b];
@@ -1155,6 +1160,7 @@ void scp_instance(const OrcProblem& P, int b, const double* xg, const double* ug
   AdmmStats as;
   const int K = P.scp_iters;
   for (int k = 0; k < K; ++k) {
+    if (run_iters > 0 && k >= run_iters) break;
     double fac = 1.0;
     if (P.rho_final > 0.0 && K > 1) fac = std::pow(P.rho_final / P.rho_geo, (double)k / (K - 1));
     const double re = P.rho_eq * fac, rd = P.rho_dyn * fac, rg = P.rho_geo * fac;
@@ -1216,7 +1222,7 @@ void scp_instance(const OrcProblem& P, int b, const double* xg, const double* ug
       L[0] = accept; L[1] = ratio; L[2] = Jn; L[3] = Jc; L[4] = Lc; L[5] = dmax_c; L[6] = radius; L[7] = step;
     }
     if (status == ST_NUMERIC) break;
-    if (P.stop && accept && dmax_c <= P.defect_tol && step <= P.step_tol) break;
+    if (run_iters <= 0 && P.stop && accept && dmax_c <= P.defect_tol && step <= P.step_tol) break;
   }
   // defect of the returned (last accepted) trajectory
   double dmax = 0.0, nl = 0.0;
@@ -1263,8 +1269,9 @@ void consensus_u0(const std::vector<QP>& qps, std::vector<State>& sts) {
 // step between Step 3 and Step 4; the acceptance test is taken on the group
 // (sums of merit and model over the scenarios, one trust radius, one
 // decision), so accepted nominals keep a common first control.
+// run_iters > 0: exactly that many iterations without the stop test (as scp_instance).
 void scp_group(const OrcProblem& P, int b0, int K, const double* xg_all, const double* ug_all,
-               double* xout_all, double* uout_all, double* stat, double* log) {
+               double* xout_all, double* uout_all, double* stat, double* log, int run_iters = 0) {
   const int nx = P.nx, nu = P.nu;
   std::vector<std::vector<double>> xbar(K), ubar(K), A(K), B(K), d(K), fnom(K);
   std::vector<QP> qps(K);
@@ -1282,6 +1289,7 @@ void scp_group(const OrcProblem& P, int b0, int K, const double* xg_all, const d
   const int Kscp = P.scp_iters;
   std::vector<double> fc(nx);
   for (int it_scp = 0; it_scp < Kscp; ++it_scp) {
+    if (run_iters > 0 && it_scp >= run_iters) break;
     double fac = 1.0;
     if (P.rho_final > 0.0 && Kscp > 1) fac = std::pow(P.rho_final / P.rho_geo, (double)it_scp / (Kscp - 1));
     const double re = P.rho_eq * fac, rd = P.rho_dyn * fac, rg = P.rho_geo * fac;
@@ -1358,7 +1366,7 @@ void scp_group(const OrcProblem& P, int b0, int K, const double* xg_all, const d
         L[0] = accept; L[1] = ratio; L[2] = Jn; L[3] = Jc; L[4] = Lc; L[5] = dmax; L[6] = radius; L[7] = step;
       }
     if (status == ST_NUMERIC) break;
-    if (P.stop && accept && dmax <= P.defect_tol && step <= P.step_tol) break;
+    if (run_iters <= 0 && P.stop && accept && dmax <= P.defect_tol && step <= P.step_tol) break;
   }
   for (int k = 0; k < K; ++k) {
     const int b = b0 + k, N = P.N[b];
@@ -1399,6 +1407,44 @@ int orc_scp_solve(const OrcProblem* P, const double* xg, const double* ug, doubl
     }
     const long long xo = P->xoff[b], uo = P->uoff[b];
     scp_instance(*P, b, xg + xo * P->nx, ug + uo * P->nu, xout + xo * P->nx, uout + uo * P->nu, stat, log);
+  }
+  return 0;
+}
+
+// Every instance (or scenario group, by its first instance's entry) solved
+// with exactly run_iters[b] SCP iterations (no stop test; see scp_instance);
+// run_iters[b] <= 0 keeps the stop test.
+int orc_scp_solve_iters(const OrcProblem* P, const double* xg, const double* ug, double* xout, double* uout,
+                        double* stat, const int* run_iters, int nthreads) {
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+  for (int b = 0; b < P->batch; ++b) {
+    if (P->group > 1) {
+      if (b % P->group == 0) scp_group(*P, b, P->group, xg, ug, xout, uout, stat, nullptr, run_iters[b]);
+      continue;
+    }
+    const long long xo = P->xoff[b], uo = P->uoff[b];
+    scp_instance(*P, b, xg + xo * P->nx, ug + uo * P->nu, xout + xo * P->nx, uout + uo * P->nu, stat, nullptr,
+                 run_iters[b]);
+  }
+  return 0;
+}
+
+// Max defect max_i |RK4(x_i, u_i) - x_{i+1}|_inf (Eq. (1b)) of every instance
+// of packed trajectories x, u (laid out like the guesses), in FP64.
+int orc_traj_defects(const OrcProblem* P, const double* x, const double* u, double* out) {
+  const int nx = P->nx, nu = P->nu;
+  for (int b = 0; b < P->batch; ++b) {
+    const long long xo = P->xoff[b], uo = P->uoff[b];
+    std::vector<double> f(nx);
+    double m = 0.0;
+    for (int i = 0; i < P->N[b]; ++i) {
+      rk4<double>(P->model, P->params + b * 8, P->dt[b], x + (xo + i) * nx, u + (uo + i) * nu, f.data());
+      for (int j = 0; j < nx; ++j) m = std::max(m, std::fabs(f[j] - x[(xo + i + 1) * nx + j]));
+    }
+    out[b] = m;
   }
   return 0;
 }

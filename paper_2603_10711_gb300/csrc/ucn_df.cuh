@@ -112,6 +112,25 @@ __device__ __forceinline__ DF operator-(DF a) { return df_neg(a); }
 __device__ __forceinline__ DF operator*(DF a, DF b) { return df_mul(a, b); }
 __device__ __forceinline__ DF operator/(DF a, DF b) { return df_div(a, b); }
 
+// Residual norms of Step 4 (Sec. III-B) are accumulated in the wide type of
+// the path: FP64 on the plain path; double-float on the FP32 path, where each
+// term is the square of the EXACT difference of two FP32 iterates (Knuth's
+// error-free sum) and every sum is a double-float sum of non-negative terms
+// (relative error below 2^-44 each), so a CTA total of t terms per node over a
+// tree of <= 256 nodes is within (t + 8) 2^-44 < 1e-11 of the exact sum of the
+// iterates' squared differences -- FP64-grade, without the FP64 pipe (1/64 of
+// the FP32 rate on this GPU).
+__device__ __forceinline__ void acc_sq_diff(double& acc, double a, double b) {
+  const double d = a - b;
+  acc += d * d;
+}
+__device__ __forceinline__ void acc_sq_diff(DF& acc, float a, float b) {
+  const DF d = df_two_sum(a, -b);
+  acc = df_add(acc, df_mul(d, d));
+}
+__device__ __forceinline__ void acc_sq(double& acc, double v) { acc += v * v; }
+__device__ __forceinline__ void acc_sq(DF& acc, float v) { acc = df_add(acc, df_two_prod(v, v)); }
+
 // The wide type of a compute precision: FP64 for the FP64 path; double-float
 // for the FP32 path (no FP64 instruction in its per-iteration work).
 template <class T> struct WideOf { typedef double type; };

@@ -26,6 +26,17 @@ __global__ void df_op_kernel(int op, const double* a, const double* b, long long
   out[k] = df_to_double(r);
 }
 
+// The residual accumulation of the FP32 path on given data: one thread sums
+// (float(a_k) - float(b_k))^2 (or float(a_k)^2) over k in order.
+__global__ void df_sum_kernel(int op, const double* a, const double* b, long long n, double* out) {
+  DF acc;
+  for (long long k = 0; k < n; ++k) {
+    if (op == UCN_DF_SQDIFF_SUM) acc_sq_diff(acc, __double2float_rn(a[k]), __double2float_rn(b[k]));
+    else acc_sq(acc, __double2float_rn(a[k]));
+  }
+  out[0] = df_to_double(acc);
+}
+
 template <class M>
 __global__ void df_rk4_kernel(const double* x, const double* u, const double* prm, double h, long long n, double* out) {
   const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -51,6 +62,9 @@ extern "C" ucn_status ucn_df_check(int op, const double* a_d, const double* b_d,
   if (op >= UCN_DF_ADD && op <= UCN_DF_ROUND) {
     if (!b_d && op != UCN_DF_SQRT && op != UCN_DF_ROUND) { set_error_message("null argument"); return UCN_EINVAL; }
     df_op_kernel<<<blocks, 128, 0, st>>>(op, a_d, b_d, n, out_d);
+  } else if (op == UCN_DF_SQDIFF_SUM || op == UCN_DF_SQ_SUM) {
+    if (!b_d && op == UCN_DF_SQDIFF_SUM) { set_error_message("null argument"); return UCN_EINVAL; }
+    df_sum_kernel<<<1, 1, 0, st>>>(op, a_d, b_d, n, out_d);
   } else if (op > UCN_DF_RK4 && model_known(op - UCN_DF_RK4)) {
     if (!b_d || !prm_d) { set_error_message("null argument"); return UCN_EINVAL; }
     switch (op - UCN_DF_RK4) {

@@ -472,6 +472,18 @@ __device__ __forceinline__ void block_reduce_df(InstShared& sh, DF* s, int ns, f
   __syncthreads();
 }
 
+// CTA totals of the squared residual norms, as doubles in res[0..1].
+__device__ __forceinline__ void reduce_residuals(InstShared& sh, double rp, double rdl, double* res) {
+  double v[2] = {rp, rdl};
+  block_reduce(sh, v, 2, 2);
+  res[0] = v[0];
+  res[1] = v[1];
+}
+__device__ __forceinline__ void reduce_residuals(InstShared& sh, DF rp, DF rdl, double* res) {
+  DF s2[2] = {rp, rdl};
+  block_reduce_df(sh, s2, 2, nullptr, 0, res);
+}
+
 // ------------------------------------------------------------------ per-node pieces
 // The CB block of the instance (FP32 path): every thread of the CTA converts
 // a share of the entries; the caller synchronises before the first use.
@@ -983,7 +995,7 @@ __device__ __forceinline__ void node_rhs(const Node<T, AOS>& nd, const MS& MT, c
 // mode projects G xi alone and leaves the duals untouched.
 template <class M, class T, bool AOS, int n>
 __device__ __forceinline__ void node_mirrors(const Node<T, AOS>& nd, const Layout& L, const Inst<T>& I,
-                                             T rg, T irg, const T* xi, bool reseed, bool want_res, T* sv, T& rp) {
+                                             T rg, T irg, const T* xi, bool reseed, bool want_res, T* sv, typename WideOf<T>::type& rp) {
   constexpr int NX = M::NX;
   if constexpr (IsQuad<M>::value) {
     for (int j = 0; j < I.nobs; ++j) {
@@ -998,7 +1010,7 @@ __device__ __forceinline__ void node_mirrors(const Node<T, AOS>& nd, const Layou
       if (want_res) {
         const T ds = rg * (s - so);
         sv[0] += n0 * ds; sv[1] += n1 * ds; sv[2] += n2 * ds;
-        rp += (y - s) * (y - s);
+        acc_sq_diff(rp, y, s);
       }
     }
   } else {
@@ -1016,7 +1028,7 @@ __device__ __forceinline__ void node_mirrors(const Node<T, AOS>& nd, const Layou
         const T so = nd.at(L.oS, k);
         nd.at(L.oS, k) = s;
         nd.at(L.oNus, k) += rg * (xi[RC + k] - s);
-        if (want_res) { sv[RC + k] += rg * (s - so); rp += (xi[RC + k] - s) * (xi[RC + k] - s); }
+        if (want_res) { sv[RC + k] += rg * (s - so); acc_sq_diff(rp, xi[RC + k], s); }
       }
     }
     if constexpr (IsMars14<M>::value) {
@@ -1032,7 +1044,7 @@ __device__ __forceinline__ void node_mirrors(const Node<T, AOS>& nd, const Layou
           const T so = nd.at(L.oS, M14::S_TILT + k);
           nd.at(L.oS, M14::S_TILT + k) = s;
           nd.at(L.oNus, M14::S_TILT + k) += rg * (xi[9 + k] - s);
-          if (want_res) { sv[9 + k] += rg * (s - so); rp += (xi[9 + k] - s) * (xi[9 + k] - s); }
+          if (want_res) { sv[9 + k] += rg * (s - so); acc_sq_diff(rp, xi[9 + k], s); }
         }
       }
       if (I.wball) {  // |omega| <= omega_max
@@ -1046,7 +1058,7 @@ __device__ __forceinline__ void node_mirrors(const Node<T, AOS>& nd, const Layou
           const T so = nd.at(L.oS, M14::S_W + k);
           nd.at(L.oS, M14::S_W + k) = s;
           nd.at(L.oNus, M14::S_W + k) += rg * (xi[11 + k] - s);
-          if (want_res) { sv[11 + k] += rg * (s - so); rp += (xi[11 + k] - s) * (xi[11 + k] - s); }
+          if (want_res) { sv[11 + k] += rg * (s - so); acc_sq_diff(rp, xi[11 + k], s); }
         }
       }
       if (n > NX && nd.i < nd.N) {
@@ -1060,7 +1072,7 @@ __device__ __forceinline__ void node_mirrors(const Node<T, AOS>& nd, const Layou
             const T so = nd.at(L.oS, M14::S_GIM + k);
             nd.at(L.oS, M14::S_GIM + k) = s;
             nd.at(L.oNus, M14::S_GIM + k) += rg * (xi[NX + k] - s);
-            if (want_res) { sv[NX + k] += rg * (s - so); rp += (xi[NX + k] - s) * (xi[NX + k] - s); }
+            if (want_res) { sv[NX + k] += rg * (s - so); acc_sq_diff(rp, xi[NX + k], s); }
           }
         }
       }
@@ -1076,7 +1088,7 @@ __device__ __forceinline__ void node_mirrors(const Node<T, AOS>& nd, const Layou
           const T so = nd.at(L.oS, 3 + k);
           nd.at(L.oS, 3 + k) = s;
           nd.at(L.oNus, 3 + k) += rg * (xi[NX + k] - s);
-          if (want_res) { sv[NX + k] += rg * (s - so); rp += (xi[NX + k] - s) * (xi[NX + k] - s); }
+          if (want_res) { sv[NX + k] += rg * (s - so); acc_sq_diff(rp, xi[NX + k], s); }
         }
       }
       if (I.half) {  // linearised |T| >= Tmin
@@ -1092,7 +1104,7 @@ __device__ __forceinline__ void node_mirrors(const Node<T, AOS>& nd, const Layou
           if (want_res) {
             const T ds = rg * (s - so);
             sv[NX] += n0 * ds; sv[NX + 1] += n1 * ds; sv[NX + 2] += n2 * ds;
-            rp += (y - s) * (y - s);
+            acc_sq_diff(rp, y, s);
           }
         }
       }
@@ -1105,7 +1117,7 @@ template <class M, class T, bool AOS>
 __device__ void node_reseed(const Node<T, AOS>& nd, const Layout& L, const Inst<T>& I) {
   constexpr int NX = M::NX, NU = M::NU;
   T xi[NX + NU], sv[NX + NU];
-  T rp = T(0);
+  typename WideOf<T>::type rp{};
   for (int j = 0; j < NX; ++j) xi[j] = nd.at(Rec<M>::Xh, j);
   if (nd.i < nd.N) {
     for (int j = 0; j < NU; ++j) xi[NX + j] = nd.at(Rec<M>::Uh, j);
@@ -1119,8 +1131,8 @@ __device__ void node_reseed(const Node<T, AOS>& nd, const Layout& L, const Inst<
 // One iteration of Steps 1-4 (Sec. III-B) over the CTA's instance; all
 // threads of the CTA call it.  The LAST instance also accumulates the primal
 // and dual residuals (a separate instantiation, so that the hot loop carries
-// no residual work, not even predicated off); the sums are in the compute
-// type, as they are only reported.
+// no residual work, not even predicated off); their squared terms are summed
+// in the wide type, per node and over the CTA (acc_sq_diff, reduce_residuals).
 //
 // GROUP: the CTA is one scenario of a group whose scenarios share the first
 // control (Sec. IV-A).  After Step 3 the node-0 thread of every CTA publishes
@@ -1131,7 +1143,8 @@ __device__ void node_reseed(const Node<T, AOS>& nd, const Layout& L, const Inst<
 template <class M, class T, bool AOS, bool REFINE, bool LAST, bool GROUP, class MS>
 __device__ __forceinline__ void admm_iteration(const Node<T, AOS>& nd, const MS& MT, const Layout& L, const Inst<T>& I,
                                                const NodeConst<M, T>& K, bool active, T re, T rd, T rg,
-                                               T irg, T ired, T& rp, T& rdl, GroupShared* G,
+                                               T irg, T ired, typename WideOf<T>::type& rp,
+                                               typename WideOf<T>::type& rdl, GroupShared* G,
                                                GroupX& X, const ProblemDev& P) {
   constexpr int NX = M::NX, NU = M::NU, NN = NX + NU;
   const int i = nd.i, N = nd.N;
@@ -1192,7 +1205,7 @@ __device__ __forceinline__ void admm_iteration(const Node<T, AOS>& nd, const MS&
       for (int j = 0; j < NX; ++j) {
         const T nux = nd.at(Rec<M>::Nux, j);
         const T xh = clampv(x[j] + nux * irg, nd.at(Rec<M>::Xlo, j), nd.at(Rec<M>::Xhi, j));
-        if (last) { sv[j] += rg * (xh - nd.at(Rec<M>::Xh, j)); rp += (x[j] - xh) * (x[j] - xh); }
+        if (last) { sv[j] += rg * (xh - nd.at(Rec<M>::Xh, j)); acc_sq_diff(rp, x[j], xh); }
         nd.at(Rec<M>::Xh, j) = xh;
         nd.at(Rec<M>::Nux, j) = nux + rg * (x[j] - xh);
       }
@@ -1211,7 +1224,7 @@ __device__ __forceinline__ void admm_iteration(const Node<T, AOS>& nd, const MS&
             }
           }
           const T uh = clampv(x[NX + j] + nuu * irg, nd.at(Rec<M>::Ulo, j), nd.at(Rec<M>::Uhi, j));
-          if (last) { sv[NX + j] += rg * (uh - nd.at(Rec<M>::Uh, j)); rp += (x[NX + j] - uh) * (x[NX + j] - uh); }
+          if (last) { sv[NX + j] += rg * (uh - nd.at(Rec<M>::Uh, j)); acc_sq_diff(rp, x[NX + j], uh); }
           nd.at(Rec<M>::Uh, j) = uh;
           nd.at(Rec<M>::Nuu, j) = nuu + rg * (x[NX + j] - uh);
         }
@@ -1235,7 +1248,7 @@ __device__ __forceinline__ void admm_iteration(const Node<T, AOS>& nd, const MS&
           dz[j] = z - zo;
           if (last) {
             sv[j] += re * dz[j];
-            rp += (x[j] - z) * (x[j] - z) + (z - dd) * (z - dd);
+            acc_sq_diff(rp, x[j], z); acc_sq_diff(rp, z, dd);
           }
         }
       }
@@ -1250,7 +1263,7 @@ __device__ __forceinline__ void admm_iteration(const Node<T, AOS>& nd, const MS&
           G->u0[j] = v;
           const T uh = (T)(v - wide_to_double(nd.dat(Rec<M>::Ubar, j)));
           const T nuu = nd.at(Rec<M>::Nuu, j);
-          if (last) { sv[NX + j] += rg * (uh - nd.at(Rec<M>::Uh, j)); rp += (x[NX + j] - uh) * (x[NX + j] - uh); }
+          if (last) { sv[NX + j] += rg * (uh - nd.at(Rec<M>::Uh, j)); acc_sq_diff(rp, x[NX + j], uh); }
           nd.at(Rec<M>::Uh, j) = uh;
           nd.at(Rec<M>::Nuu, j) = nuu + rg * (x[NX + j] - uh);
         }
@@ -1283,7 +1296,7 @@ __device__ __forceinline__ void admm_iteration(const Node<T, AOS>& nd, const MS&
         }
 #pragma unroll
         for (int j = 0; j < NN; ++j)
-          if (j < NX || i < N) rdl += sv[j] * sv[j];
+          if (j < NX || i < N) acc_sq(rdl, sv[j]);
       }
     }
     if (active && i >= 1) {
@@ -1301,20 +1314,12 @@ __device__ __forceinline__ void admm_iterations(const Node<T, AOS>& nd, const MS
                                 const NodeConst<M, T>& K, bool active, T re, T rd, T rg, int iters,
                                 InstShared& sh, double* res, GroupShared* G, GroupX& X, const ProblemDev& P) {
   const T irg = T(1) / rg, ired = T(1) / (re + rd);
-  T rp = T(0), rdl = T(0);   // residual sums in the compute type (reported only)
+  typename WideOf<T>::type rp{}, rdl{};   // residual sums in the wide type (FP64 or double-float)
   for (int it = 0; it + 1 < iters; ++it)
     admm_iteration<M, T, AOS, REFINE, false, GROUP>(nd, MT, L, I, K, active, re, rd, rg, irg, ired, rp, rdl, G, X, P);
   admm_iteration<M, T, AOS, REFINE, true, GROUP>(nd, MT, L, I, K, active, re, rd, rg, irg, ired, rp, rdl, G, X, P);
   // squared norms (the root is taken once, when they are reported)
-  if constexpr (IsDF<T>::value) {
-    DF s2[2] = {df_from(rp), df_from(rdl)};
-    block_reduce_df(sh, s2, 2, nullptr, 0, res);
-  } else {
-    double v[2] = {(double)rp, (double)rdl};
-    block_reduce(sh, v, 2, 2);
-    res[0] = v[0];
-    res[1] = v[1];
-  }
+  reduce_residuals(sh, rp, rdl, res);
 }
 
 // Publish mu_i + rho_dyn z_i before the first Step 1.
@@ -1808,8 +1813,8 @@ __device__ void scp_move_nominal(const Node<T, AOS>& nd, const Layout& L, const 
 }
 
 // End of a solve: the returned (last accepted) trajectory, its cost, l1 and
-// max defect (w[0..2], CTA totals, FP64 sums: once per launch) and the
-// exported ADMM state.
+// max defect (w[0..2], CTA totals; the defects by FP64 RK4 steps and FP64
+// sums: once per launch) and the exported ADMM state.
 template <class M, class T, bool AOS>
 __device__ void scp_finish(const Node<T, AOS>& nd, const Layout& L, const ProblemDev& P, const Inst<T>& I, int b,
                            bool act, long long xo, long long uo, double* xout, double* uout, InstShared& sh,
@@ -1821,25 +1826,30 @@ __device__ void scp_finish(const Node<T, AOS>& nd, const Layout& L, const Proble
     W xb[NX], ub[NU];
     read_nominal<M, T, AOS>(nd, i < N, xb, ub);
     w[0] = wide_to_double(node_cost<M, T, AOS>(nd, P, I, b, i, N, xb, ub));
+    // the returned trajectory as doubles
+    double xd[NX], ud[NU];
+    for (int j = 0; j < NX; ++j) {
+      xd[j] = wide_to_double(xb[j]);
+      // a node-0 state at the initial state (Eq. (1c)) is returned bit for bit
+      // as given, although double-float holds only ~48 of its 53 bits
+      if constexpr (IsDF<T>::value)
+        if (i == 0 && df_sub(nd.c[CB<M>::Xinit + j], xb[j]).hi == 0.0f) xd[j] = P.xinit[b * NX + j];
+      xout[(xo + i) * NX + j] = xd[j];
+    }
+    for (int j = 0; j < NU; ++j) ud[j] = (i < N) ? wide_to_double(ub[j]) : 0.0;
     if (i < N) {
-      W fn[NX];
-      rk4_wide<M, T, AOS>(nd, P, b, xb, ub, fn);
+      for (int j = 0; j < NU; ++j) uout[(uo + i) * NU + j] = ud[j];
+      // the defect of the returned trajectory by an FP64 RK4 step on both paths
+      // (once per launch): the reported defect and the defect_tol status are
+      // FP64 quantities of exactly the doubles returned
+      double fn[NX];
+      rk4<M, double>(P.params + b * 8, P.dt[b], xd, ud, fn);
       for (int j = 0; j < NX; ++j) {
-        const double e = fabs(wide_to_double(fn[j] - nd.dnb(Rec<M>::Xbar, j, i + 1)));
+        const double e = fabs(fn[j] - wide_to_double(nd.dnb(Rec<M>::Xbar, j, i + 1)));
         w[1] += e;
         w[2] = fmax(w[2], e);
       }
     }
-    for (int j = 0; j < NX; ++j) {
-      double xv = wide_to_double(xb[j]);
-      // a node-0 state at the initial state (Eq. (1c)) is returned bit for bit
-      // as given, although double-float holds only ~48 of its 53 bits
-      if constexpr (IsDF<T>::value)
-        if (i == 0 && df_sub(nd.c[CB<M>::Xinit + j], xb[j]).hi == 0.0f) xv = P.xinit[b * NX + j];
-      xout[(xo + i) * NX + j] = xv;
-    }
-    if (i < N)
-      for (int j = 0; j < NU; ++j) uout[(uo + i) * NU + j] = wide_to_double(ub[j]);
     node_export<M, T, AOS>(nd, L, P, b, P.state_abs + P.soff[b]);
   }
   block_reduce(sh, w, 2, 3);

@@ -202,7 +202,8 @@ __device__ __forceinline__ void lanes_consts(const Node<T, AOS>& nd, const Probl
 template <class M, class T, bool AOS, bool REFINE, bool LAST, bool GROUP, int TPN, class MS, class HR>
 __device__ __forceinline__ void admm_iteration_lanes(const Node<T, AOS>& nd, const MS& MT, const HR& H, const Layout& L,
                                                      const Inst<T>& I, const T* kq, const T* khd, bool active, int q,
-                                                     T re, T rd, T rg, T irg, T ired, T& rp, T& rdl,
+                                                     T re, T rd, T rg, T irg, T ired, typename WideOf<T>::type& rp,
+                                               typename WideOf<T>::type& rdl,
                                                      GroupShared* G, GroupX& X, const ProblemDev& P) {
   static_assert(IsQuad<M>::value, "the lane kernel carries the quadrotor's mirror sets");
   using LR = LaneRows<M, TPN>;
@@ -356,7 +357,7 @@ __device__ __forceinline__ void admm_iteration_lanes(const Node<T, AOS>& nd, con
       const int j = q + TPN * m;
       const T nux = nd.at(Rec<M>::Nux, j);
       const T xh = clampv(xo[m] + nux * irg, nd.at(Rec<M>::Xlo, j), nd.at(Rec<M>::Xhi, j));
-      if (LAST) { sv[m] += rg * (xh - nd.at(Rec<M>::Xh, j)); rp += (xo[m] - xh) * (xo[m] - xh); }
+      if (LAST) { sv[m] += rg * (xh - nd.at(Rec<M>::Xh, j)); acc_sq_diff(rp, xo[m], xh); }
       nd.at(Rec<M>::Xh, j) = xh;
       nd.at(Rec<M>::Nux, j) = nux + rg * (xo[m] - xh);
     }
@@ -378,7 +379,7 @@ __device__ __forceinline__ void admm_iteration_lanes(const Node<T, AOS>& nd, con
         const T uh = clampv(xo[RX + m] + nuu * irg, nd.at(Rec<M>::Ulo, j), nd.at(Rec<M>::Uhi, j));
         if (LAST) {
           sv[RX + m] += rg * (uh - nd.at(Rec<M>::Uh, j));
-          rp += (xo[RX + m] - uh) * (xo[RX + m] - uh);
+          acc_sq_diff(rp, xo[RX + m], uh);
         }
         nd.at(Rec<M>::Uh, j) = uh;
         nd.at(Rec<M>::Nuu, j) = nuu + rg * (xo[RX + m] - uh);
@@ -396,7 +397,7 @@ __device__ __forceinline__ void admm_iteration_lanes(const Node<T, AOS>& nd, con
       if (LAST) {
         const T ds = rg * (s - so);
         msv[0] += n0 * ds; msv[1] += n1 * ds; msv[2] += n2 * ds;
-        rp += (y - s) * (y - s);
+        acc_sq_diff(rp, y, s);
       }
     }
   }
@@ -417,7 +418,7 @@ __device__ __forceinline__ void admm_iteration_lanes(const Node<T, AOS>& nd, con
         dz[m] = z - zo;
         if (LAST) {
           sv[m] += re * dz[m];
-          rp += (xo[m] - z) * (xo[m] - z) + (z - dd) * (z - dd);
+          acc_sq_diff(rp, xo[m], z); acc_sq_diff(rp, z, dd);
         }
       }
     }
@@ -439,7 +440,7 @@ __device__ __forceinline__ void admm_iteration_lanes(const Node<T, AOS>& nd, con
         const T nuu = nd.at(Rec<M>::Nuu, j);
         if (LAST) {
           sv[RX + m] += rg * (uh - nd.at(Rec<M>::Uh, j));
-          rp += (xo[RX + m] - uh) * (xo[RX + m] - uh);
+          acc_sq_diff(rp, xo[RX + m], uh);
         }
         nd.at(Rec<M>::Uh, j) = uh;
         nd.at(Rec<M>::Nuu, j) = nuu + rg * (xo[RX + m] - uh);
@@ -481,7 +482,7 @@ __device__ __forceinline__ void admm_iteration_lanes(const Node<T, AOS>& nd, con
     if (active) {
 #pragma unroll
       for (int m = 0; m < R; ++m)
-        if (m < RX || i < N) rdl += sv[m] * sv[m];
+        if (m < RX || i < N) acc_sq(rdl, sv[m]);
     }
   }
   if (active && i >= 1) {
@@ -500,22 +501,14 @@ __device__ __forceinline__ void admm_iterations_lanes(const Node<T, AOS>& nd, co
                                                       T re, T rd, T rg, int iters, InstShared& sh, double* res,
                                                       GroupShared* G, GroupX& X, const ProblemDev& P) {
   const T irg = T(1) / rg, ired = T(1) / (re + rd);
-  T rp = T(0), rdl = T(0);   // residual sums in the compute type (reported only)
+  typename WideOf<T>::type rp{}, rdl{};   // residual sums in the wide type (FP64 or double-float)
   for (int it = 0; it + 1 < iters; ++it)
     admm_iteration_lanes<M, T, AOS, REFINE, false, GROUP, TPN>(nd, MT, H, L, I, kq, khd, active, q, re, rd, rg, irg,
                                                                ired, rp, rdl, G, X, P);
   admm_iteration_lanes<M, T, AOS, REFINE, true, GROUP, TPN>(nd, MT, H, L, I, kq, khd, active, q, re, rd, rg, irg, ired,
                                                             rp, rdl, G, X, P);
   // squared norms (the root is taken once, when they are reported)
-  if constexpr (IsDF<T>::value) {
-    DF s2[2] = {df_from(rp), df_from(rdl)};
-    block_reduce_df(sh, s2, 2, nullptr, 0, res);
-  } else {
-    double v[2] = {(double)rp, (double)rdl};
-    block_reduce(sh, v, 2, 2);
-    res[0] = v[0];
-    res[1] = v[1];
-  }
+  reduce_residuals(sh, rp, rdl, res);
 }
 
 // Node view of node `i` (the lane kernel maps TPN threads to a node).

@@ -267,6 +267,7 @@ def ucn_mpc_shift(h, x, u, xg, ug, stream=None):
 
 
 UCN_DF_ADD, UCN_DF_SUB, UCN_DF_MUL, UCN_DF_DIV, UCN_DF_SQRT, UCN_DF_ROUND, UCN_DF_RK4 = 0, 1, 2, 3, 4, 5, 100
+UCN_DF_SQDIFF_SUM, UCN_DF_SQ_SUM = 6, 7
 
 
 def ucn_df_check(op, a, b, prm, h, out, stream=None):
@@ -274,7 +275,7 @@ def ucn_df_check(op, a, b, prm, h, out, stream=None):
     include/ucn.h): elementwise ops on a, b, or one RK4 step per row."""
     import torch
     f = torch.float64
-    n = out.numel() if op < UCN_DF_RK4 else out.shape[0]
+    n = a.numel() if op in (UCN_DF_SQDIFF_SUM, UCN_DF_SQ_SUM) else out.numel() if op < UCN_DF_RK4 else out.shape[0]
     _check(lib().ucn_df_check(int(op), _ptr(a, f, name="a"), None if b is None else _ptr(b, f, name="b"),
                               None if prm is None else _ptr(prm, f, name="prm"), float(h), int(n),
                               _ptr(out, f, name="out"), _stream(stream)))

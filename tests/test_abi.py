@@ -111,5 +111,6 @@ def test_double_float_check_validates_before_any_launch(ucn):
     assert lib.ucn_df_check(ucn.UCN_DF_ADD, fake, fake, None, 0.0, -1, fake, None) == ucn.UCN_EINVAL
     assert lib.ucn_df_check(ucn.UCN_DF_ADD, fake, fake, None, 0.0, 4, None, None) == ucn.UCN_EINVAL
     assert lib.ucn_df_check(ucn.UCN_DF_ADD, fake, fake, None, 0.0, 0, fake, None) == ucn.UCN_OK   # nothing to do
-    assert lib.ucn_df_check(7, fake, fake, None, 0.0, 4, fake, None) == ucn.UCN_EINVAL          # unknown op
+    assert lib.ucn_df_check(9, fake, fake, None, 0.0, 4, fake, None) == ucn.UCN_EINVAL          # unknown op
+    assert lib.ucn_df_check(ucn.UCN_DF_SQDIFF_SUM, fake, None, None, 0.0, 4, fake, None) == ucn.UCN_EINVAL
     assert lib.ucn_df_check(ucn.UCN_DF_RK4 + 9, fake, fake, fake, 0.1, 4, fake, None) == ucn.UCN_EINVAL

@@ -114,22 +114,27 @@ def test_lane_layout_is_refused_where_it_does_not_apply():
 
 
 def test_full_size_uneven_batch_sampled_against_the_oracle():
-    # the 4096-instance uneven batch in the benchmark's launch (library defaults); 4 instances
-    # solved again by the oracle
+    # the 4096-instance uneven batch in the benchmark's launch (library defaults); 32
+    # evenly spaced instances solved again by the oracle and compared at 1e-4 after the
+    # GPU's SCP iteration count; the FP64 defect of every returned trajectory passes
+    # wherever the oracle's does
     prob = W.quad_box(4096, seed=2)
     s = ucn.Solver(prob, precision=ucn.UCN_PREC_FP32_REFINE)
     x, u = s.scp_solve()
     torch.cuda.synchronize()
     st = s.stats_host()
-    xg = x.cpu().numpy()
+    xg, ug = x.cpu().numpy(), u.cpu().numpy()
     s.close()
-    assert np.isfinite(xg).all() and np.mean(st["defect"] <= 1e-5) >= 0.95
-    idx = [0, 4095, 1234, 2900]
+    assert np.isfinite(xg).all()
+    idx = np.arange(32) * 128 + 5
     sub = prob.subset(idx)
-    xr, ur, sr, _ = oracle.scp_solve(sub)
+    xs = np.concatenate([xg[prob.xoff[b]:prob.xoff[b] + prob.N[b] + 1] for b in idx])
+    us = np.concatenate([ug[prob.uoff[b]:prob.uoff[b] + prob.N[b]] for b in idx])
+    ref = oracle.scp_solve(sub)[:3]
+    r = oracle.compare_batch(sub, xs, us, st["scp_iters"][idx], ref, 1e-4)
+    assert r["summary"]["n_over_tol"] == 0, (r["summary"], r["err"])
+    conv = ref[2][:, 0] <= 1e-5
+    assert (r["fp64_defect"][conv] <= 1e-5).all()
+    assert np.mean(st["defect"] <= 1e-5) >= 0.98
     for k, b in enumerate(idx):
-        N = int(prob.N[b])
-        xo, so = prob.xoff[b], sub.xoff[k]
-        np.testing.assert_array_equal(xg[xo], prob.xinit[b])
-        if sr[k, 0] <= 1e-5 and st["defect"][b] <= 1e-5 and int(sr[k, 7]) == int(st["scp_iters"][b]):
-            assert rel_err(xg[xo:xo + N + 1], xr[so:so + N + 1]) <= 1e-3
+        np.testing.assert_array_equal(xg[prob.xoff[b]], prob.xinit[b])

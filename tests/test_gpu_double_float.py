@@ -101,6 +101,30 @@ def test_rk4_step_matches_the_fp64_oracle(kind):
 def test_rejects_an_unknown_op():
     x = torch.zeros(4, dtype=torch.float64, device="cuda")
     with pytest.raises(ucn.UcnError):
-        ucn.ucn_df_check(7, x, x, None, 0.0, x)
+        ucn.ucn_df_check(9, x, x, None, 0.0, x)
     with pytest.raises(ucn.UcnError):
         ucn.ucn_df_check(ucn.UCN_DF_RK4 + 9, x, x, x, 0.1, x.view(4, 1))
+
+
+def test_residual_accumulation_within_its_bound():
+    # the sums of the FP32 path's ADMM residual norms: exact differences of float
+    # iterates, squared and summed in double-float; a sum of t non-negative terms is
+    # within (t + 8) 2^-44 of the exact sum (t = 78 here; the kernel's CTA totals add
+    # at most 8 levels of a tree to each node's t terms)
+    from fractions import Fraction
+    rng = np.random.default_rng(5)
+    t = 78
+    for trial in range(20):
+        a = (10.0 ** rng.uniform(-6, 2, t) * rng.uniform(-1, 1, t)).astype(np.float32).astype(np.float64)
+        b = a * (1.0 + rng.uniform(-1e-3, 1e-3, t))          # near-cancelling pairs
+        b[: t // 3] = (10.0 ** rng.uniform(-6, 2, t // 3)).astype(np.float32)
+        b[t // 3: t // 3 + 3] = a[t // 3: t // 3 + 3]          # exact zeros
+        b = b.astype(np.float32).astype(np.float64)
+        exact = float(sum((Fraction(x) - Fraction(y)) ** 2 for x, y in zip(a, b)))
+        dev = torch.device("cuda")
+        out = torch.zeros(1, dtype=torch.float64, device=dev)
+        ucn.ucn_df_check(ucn.UCN_DF_SQDIFF_SUM, torch.tensor(a, device=dev), torch.tensor(b, device=dev), None, 0.0, out)
+        assert abs(float(out[0]) - exact) <= (t + 8) * EPS * exact, trial
+        exact2 = float(sum(Fraction(x) ** 2 for x in a))
+        ucn.ucn_df_check(ucn.UCN_DF_SQ_SUM, torch.tensor(a, device=dev), None, None, 0.0, out)
+        assert abs(float(out[0]) - exact2) <= (t + 8) * EPS * exact2, trial

@@ -2,8 +2,9 @@
 
 Tolerances (normwise, floor 1):  |gpu - oracle|_max <= tol * max(1, |oracle|_max)
   * FP64 plain path:          tol = 1e-9
-  * FP32 path with refinement: tol = 1e-4, and the GPU result's own max
-    nonlinear defect <= 1e-5 where the oracle reaches it.
+  * FP32 path with refinement: tol = 1e-4 after the same number of SCP
+    iterations, and the FP64 defect of the returned trajectory <= 1e-5 where
+    the oracle reaches it.
 """
 import numpy as np
 import pytest
@@ -113,37 +114,88 @@ def test_admm_fp64_matches_oracle(name):
         assert rel_err(got, ref) <= TOL64, (b, what, rel_err(got, ref))
 
 
+def residual_bound(prob, b, e):
+    """Bound on |r_gpu - r_oracle| for the primal and dual residual norms of one
+    instance, given e = the largest deviation of any ADMM iterate between the two
+    paths.  |r_gpu - r_oracle| <= |v_gpu - v_oracle|_2 for the residual vectors v,
+    whose m components are differences of iterates: primal ones (x - x-hat, x - z,
+    z - (A x + B u + c), G xi - s) within (2 + |[A B]|_inf) e, dual ones
+    (rho (new - old) of x-hat, z and the mirrors, and A^T of the neighbour's
+    rho dz) within 2 rho (2 + |A|_1 + n_mirror) e."""
+    N, nx, nu = int(prob.N[b]), prob.nx, prob.nu
+    mb = oracle.maxblk(prob)
+    x, u = perturbed_nominal(prob, seed=3, scale=0.02)
+    A, B, _ = oracle_linearize(prob, x, u)
+    uo = prob.uoff[b]
+    Ab, Bb = A[uo:uo + N], B[uo:uo + N]
+    ninf = max(np.abs(np.concatenate([Ab, Bb], axis=2)).sum(axis=2).max(), 0.0)
+    n1 = np.abs(Ab).sum(axis=1).max()
+    rho = max(prob.settings["rho_eq"], prob.settings["rho_dyn"], prob.settings["rho_geo"])
+    m = (N + 1) * (nx + nu + 3 * mb)
+    return (np.sqrt(m) * (2.0 + ninf) * e, np.sqrt(m) * 2.0 * rho * (2.0 + n1 + mb) * e)
+
+
 @pytest.mark.parametrize("name", list(PROBLEMS))
 def test_admm_fp32_matches_oracle(name):
-    for b, what, got, ref in admm_case(PROBLEMS[name](), ucn.UCN_PREC_FP32_REFINE, 150, 60):
-        if what.endswith("res"):
-            continue   # residual norms are differences of iterates: not compared at FP32
-        assert rel_err(got, ref) <= TOL32, (b, what, rel_err(got, ref))
+    prob = PROBLEMS[name]()
+    rows = list(admm_case(prob, ucn.UCN_PREC_FP32_REFINE, 150, 60))
+    for b, what, got, ref in rows:
+        if not what.endswith("res"):
+            assert rel_err(got, ref) <= TOL32, (b, what, rel_err(got, ref))
+    # the residual norms (summed in double-float from the FP32 iterates) differ from the
+    # oracle's only through the iterates themselves
+    for b in range(prob.batch):
+        e = max(np.abs(np.asarray(g) - np.asarray(r)).max() for bb, w, g, r in rows if bb == b and w == "warm-state")
+        bp, bd = residual_bound(prob, b, e)
+        for bb, what, got, ref in rows:
+            if bb == b and what.endswith("res"):
+                assert abs(got[0] - ref[0]) <= bp, (b, what, got, ref, bp)
+                assert abs(got[1] - ref[1]) <= bd, (b, what, got, ref, bd)
 
 
 # ------------------------------------------------------------------ full SCP solve
+def check_fp64_defects(prob, st, xg, ug):
+    """The kernel's reported defect is an FP64 RK4 defect of exactly the doubles it
+    returned: the oracle's RK4 on those doubles gives it to FP64 rounding."""
+    d64 = oracle.traj_defects(prob, xg, ug)
+    scale = np.array([max(1.0, np.abs(xg[prob.xoff[b]:prob.xoff[b] + prob.N[b] + 1]).max()) for b in range(prob.batch)])
+    assert (np.abs(st["defect"] - d64) <= 1e-13 * scale).all(), np.abs(st["defect"] - d64).max()
+    return d64
+
+
 def scp_compare(prob, prec, tol, check_defect=False):
+    """Every instance against the oracle's solve of the same inputs.  FP64: the
+    same iterates (trajectories at 1e-9, identical accept flags and counts).
+    FP32: trajectories at 1e-4 after the same number of SCP iterations (where the
+    stop test landed on the other side of defect_tol the oracle is re-run to the
+    GPU's count), and with check_defect every instance the oracle brings to the
+    defect gate also passes it by the FP64 defect of the returned doubles."""
     s = ucn.Solver(prob, precision=prec)
     x, u = s.scp_solve()
     torch.cuda.synchronize()
     st = s.stats_host()
     xg, ug = x.cpu().numpy(), u.cpu().numpy()
+    s.close()
     xr, ur, sr, _ = oracle.scp_solve(prob)
-    for b in range(prob.batch):
-        xo, uo, N = prob.xoff[b], prob.uoff[b], int(prob.N[b])
-        assert rel_err(xg[xo:xo + N + 1], xr[xo:xo + N + 1]) <= tol, (b, rel_err(xg[xo:xo + N + 1], xr[xo:xo + N + 1]))
-        assert rel_err(ug[uo:uo + N], ur[uo:uo + N]) <= tol, b
-        if prec == ucn.UCN_PREC_FP64:
+    d64 = check_fp64_defects(prob, st, xg, ug)
+    if prec == ucn.UCN_PREC_FP64:
+        for b in range(prob.batch):
+            xo, uo, N = prob.xoff[b], prob.uoff[b], int(prob.N[b])
+            assert rel_err(xg[xo:xo + N + 1], xr[xo:xo + N + 1]) <= tol, (b, rel_err(xg[xo:xo + N + 1], xr[xo:xo + N + 1]))
+            assert rel_err(ug[uo:uo + N], ur[uo:uo + N]) <= tol, b
             assert int(st["scp_iters"][b]) == int(sr[b, 7])
             assert int(st["accepted"][b]) == int(sr[b, 8])
             assert int(st["accept_mask"][b]) == int(sr[b, 9])
             assert int(st["status"][b]) == int(sr[b, 10])
             assert abs(st["defect"][b] - sr[b, 0]) <= 1e-9 * max(1e-3, sr[b, 0])
             assert abs(st["cost"][b] - sr[b, 1]) <= 1e-9 * max(1.0, abs(sr[b, 1]))
-        if check_defect and sr[b, 0] <= 1e-5:
-            assert st["defect"][b] <= 1e-5, (b, st["defect"][b])
-            assert int(st["status"][b]) == 0
-    s.close()
+    else:
+        r = oracle.compare_batch(prob, xg, ug, st["scp_iters"], (xr, ur, sr), tol)
+        assert r["summary"]["n_over_tol"] == 0, (r["summary"], r["err"])
+    if check_defect:
+        conv = sr[:, 0] <= 1e-5
+        assert (d64[conv] <= 1e-5).all(), d64[conv].max()
+        assert (st["status"][conv] == 0).all()
     return st, sr
 
 
@@ -197,7 +249,8 @@ def test_scp_fp32_quaternion_study_matches_oracle():
 
 def test_scp_fp32_quaternion_converges_to_the_defect_gate():
     prob = W.quat_study(3, rho0=10.0, rho_final=1e3, scp_iters=80, admm_iters=250, settings=dict(stop=1, step_tol=1.0))
-    st, sr = scp_compare(prob, ucn.UCN_PREC_FP32_REFINE, 1e-3, check_defect=True)
+    st, sr = scp_compare(prob, ucn.UCN_PREC_FP32_REFINE, TOL32, check_defect=True)
+    assert (sr[:, 0] <= 1e-5).all()
 
 
 def test_scp_fp64_mars6_matches_oracle():
@@ -208,8 +261,8 @@ def test_scp_fp64_mars6_matches_oracle():
 
 def test_scp_fp32_mars6_reaches_the_defect_gate():
     prob = W.mars6_batch(6, seed=7)
-    st, sr = scp_compare(prob, ucn.UCN_PREC_FP32_REFINE, 1e-3, check_defect=True)
-    assert (st["defect"] <= 1e-5).mean() >= 0.8
+    st, sr = scp_compare(prob, ucn.UCN_PREC_FP32_REFINE, TOL32, check_defect=True)
+    assert (sr[:, 0] <= 1e-5).all() and (st["defect"] <= 1e-5).all()
 
 
 def test_scp_fp32_quad_matches_oracle():
@@ -230,7 +283,9 @@ def test_longest_horizon():
 
 
 def test_full_size_mars_batch_sampled_against_oracle():
-    # the Mars batch of 1024 instances in the benchmark's launch; 4 instances checked against the oracle
+    # the Mars batch of 1024 instances in the benchmark's launch: every instance passes
+    # the defect gate by the FP64 defect of its returned doubles (the kernel's own and the
+    # oracle's RK4), and 64 evenly spaced instances match the oracle at 1e-4
     prob = W.mars_batch(1024, seed=1)
     s = ucn.Solver(prob, precision=ucn.UCN_PREC_FP32_REFINE)
     x, u = s.scp_solve()
@@ -239,16 +294,17 @@ def test_full_size_mars_batch_sampled_against_oracle():
     xg, ug = x.cpu().numpy(), u.cpu().numpy()
     s.close()
     assert np.isfinite(xg).all() and np.isfinite(ug).all()
-    assert (st["status"] == np.where(st["defect"] <= 1e-5, 0, st["status"])).all()
-    assert np.mean(st["defect"] <= 1e-5) >= 0.95
-    idx = [0, 1023, 377, 640]
+    assert (st["status"] == 0).all() and (st["defect"] <= 1e-5).all()
+    d64 = check_fp64_defects(prob, st, xg, ug)
+    assert (d64 <= 1e-5).all()
+    idx = np.arange(64) * 16 + 7
     sub = prob.subset(idx)
-    xr, ur, sr, _ = oracle.scp_solve(sub)
-    for k, b in enumerate(idx):
-        xo, uo = prob.xoff[b], prob.uoff[b]
-        so, su = sub.xoff[k], sub.uoff[k]
-        if sr[k, 0] <= 1e-5 and st["defect"][b] <= 1e-5:
-            assert rel_err(xg[xo:xo + 101], xr[so:so + 101]) <= TOL32 * 10
+    xs = np.concatenate([xg[prob.xoff[b]:prob.xoff[b] + 101] for b in idx])
+    us = np.concatenate([ug[prob.uoff[b]:prob.uoff[b] + 100] for b in idx])
+    ref = oracle.scp_solve(sub)[:3]
+    r = oracle.compare_batch(sub, xs, us, st["scp_iters"][idx], ref, TOL32)
+    assert r["summary"]["n_over_tol"] == 0, (r["summary"], r["err"])
+    for b in idx:
         # every returned trajectory satisfies the boundary conditions exactly
-        np.testing.assert_array_equal(xg[xo], prob.xinit[b])
-        np.testing.assert_array_equal(xg[xo + 100][:6], 0.0)
+        np.testing.assert_array_equal(xg[prob.xoff[b]], prob.xinit[b])
+        np.testing.assert_array_equal(xg[prob.xoff[b] + 100][:6], 0.0)

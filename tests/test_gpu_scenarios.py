@@ -204,8 +204,8 @@ def test_receding_horizon_approaches_the_goal():
 
 
 def test_full_size_scenario_batch_sampled_against_the_oracle():
-    # 256 problems x 64 scenarios, the cold first step of the benchmark; one group checked
-    # against the oracle's group solve (same shared first control and iteration count)
+    # 256 problems x 64 scenarios, the cold first step of the benchmark; two groups checked
+    # against the oracle's group solves at 1e-4 after the same SCP iteration count
     prob = W.scenario_mpc(256, 64, seed=3, N=40, n_obs=8)
     s = ucn.Solver(prob, precision=ucn.UCN_PREC_FP32_REFINE)
     x, u = s.scp_solve()
@@ -215,10 +215,10 @@ def test_full_size_scenario_batch_sampled_against_the_oracle():
     s.close()
     check_group_invariants(prob, ug, st)
     assert np.mean(st["defect"] <= 1e-5) >= 0.95
-    g = 37
-    sub = prob.subset(np.arange(g * 64, (g + 1) * 64))
-    xr, ur, sr, _ = oracle.scp_solve(sub)
-    if (sr[:, 0] <= 1e-5).all() and int(sr[0, 7]) == int(st["scp_iters"][g * 64]):
-        for k in range(64):
-            b = g * 64 + k
-            assert rel_err(xg[prob.xoff[b]:prob.xoff[b] + 41], xr[sub.xoff[k]:sub.xoff[k] + 41]) <= 1e-3
+    idx = np.concatenate([np.arange(g * 64, (g + 1) * 64) for g in (37, 200)])
+    sub = prob.subset(idx)
+    xs = np.concatenate([xg[prob.xoff[b]:prob.xoff[b] + 41] for b in idx])
+    us = np.concatenate([ug[prob.uoff[b]:prob.uoff[b] + 40] for b in idx])
+    ref = oracle.scp_solve(sub)[:3]
+    r = oracle.compare_batch(sub, xs, us, st["scp_iters"][idx], ref, 1e-4)
+    assert r["summary"]["n_over_tol"] == 0, (r["summary"], r["err"])

@@ -1,7 +1,11 @@
-"""The multi-rank path on CPU (gloo, world_size 2): cross-rank reduction of
-the benchmark's timing and pass counts, and the instance sharding."""
+"""The multi-rank path on CPU (gloo, world_size 2): every rank builds its
+shard of one seeded global batch, and the benchmark's cross-rank reduction
+combines the timing (max) and the solve counts (sum)."""
+import argparse
 import os
 import socket
+
+import numpy as np
 
 import pytest
 
@@ -10,6 +14,9 @@ import torch.distributed as dist  # noqa: E402
 import torch.multiprocessing as mp  # noqa: E402
 
 import bench  # noqa: E402
+import workloads as W  # noqa: E402
+
+ARGS = argparse.Namespace(batch=6, scp_iters=0, admm_iters=0, workload="mars")
 
 
 def _free_port():
@@ -25,8 +32,9 @@ def _worker(rank, world, port, q):
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
-        total, passed = bench.reduce_over_ranks(1.5 + rank, 10 * (rank + 1), torch.device("cpu"))
-        q.put((rank, total, passed))
+        shard = bench.make_problem(ARGS, rank, world)
+        total, count = bench.reduce_over_ranks(1.5 + rank, shard.batch, torch.device("cpu"))
+        q.put((rank, total, count, shard.xinit.tolist()))
     finally:
         dist.destroy_process_group()
 
@@ -42,9 +50,12 @@ def test_reduce_over_ranks_gloo_world2():
     for p in procs:
         p.join(timeout=60)
         assert p.exitcode == 0
-    for rank, total, passed in out:
-        assert total == 2.5          # slowest rank
-        assert passed == 30.0        # all ranks' solves
+    for rank, total, count, _ in out:
+        assert total == 2.5                          # slowest rank
+        assert count == 2 * ARGS.batch               # all ranks' instances
+    # the two shards are the global batch, in order, without overlap
+    whole = W.mars_batch(2 * ARGS.batch, seed=1)
+    np.testing.assert_array_equal(np.concatenate([np.array(o[3]) for o in out]), whole.xinit)
 
 
 @pytest.mark.parametrize("batch,world", [(1024, 2), (1024, 3), (5, 8), (7, 1)])

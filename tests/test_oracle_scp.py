@@ -138,3 +138,50 @@ def test_fixed_count_solve_runs_every_iteration():
     _, _, st, log = oracle.scp_solve(prob, log=True)
     assert st[0, 7] == prob.settings["scp_iters"]
     assert np.all(np.isfinite(log[0, :, 2]))
+
+
+def test_exact_iteration_count_solve_agrees_with_the_stop_test_and_the_cap():
+    # run to each instance's own stopping iteration: the stop-test solve, bit for bit;
+    # run to the cap: the solve without a stop test, bit for bit
+    for prob in (W.mars_batch(3, seed=1, N=30), W.scenario_mpc(2, 3, seed=3, N=10, n_obs=2,
+                                                               settings=dict(scp_iters=12, admm_iters=30))):
+        x, u, st, _ = oracle.scp_solve(prob)
+        xs, us, ss = oracle.scp_solve_iters(prob, st[:, 7].astype(int))
+        np.testing.assert_array_equal(xs, x)
+        np.testing.assert_array_equal(us, u)
+        np.testing.assert_array_equal(ss[:, 7], st[:, 7])
+        K = int(prob.settings["scp_iters"])
+        nostop = prob.subset(np.arange(prob.batch))
+        nostop.settings["stop"] = 0
+        x0, u0, s0, _ = oracle.scp_solve(nostop)
+        xk, uk, sk = oracle.scp_solve_iters(prob, np.full(prob.batch, K))
+        np.testing.assert_array_equal(xk, x0)
+        np.testing.assert_array_equal(uk, u0)
+        assert (sk[:, 7] == K).all()
+
+
+def test_trajectory_defects_are_the_rk4_defects():
+    prob = W.mars_batch(3, seed=2, N=25)
+    x, u, st, _ = oracle.scp_solve(prob)
+    d = oracle.traj_defects(prob, x, u)
+    np.testing.assert_array_equal(d, st[:, 0])
+    for b in range(prob.batch):
+        xb, ub = instance(prob, x, u, b)
+        ref = max(np.abs(oracle.rk4(prob.model, prob.params[b], prob.dt[b], xb[i], ub[i]) - xb[i + 1]).max()
+                  for i in range(int(prob.N[b])))
+        assert d[b] == ref
+
+
+def test_batch_comparison_reruns_instances_that_stopped_elsewhere():
+    prob = W.mars_batch(3, seed=1, N=30)
+    ref = oracle.scp_solve(prob)[:3]
+    it = ref[2][:, 7].astype(int)
+    r = oracle.compare_batch(prob, ref[0], ref[1], it, ref, 1e-4)
+    assert r["summary"]["max_rel_err"] == 0.0 and r["summary"]["scp_iters_mismatch"] == 0
+    # a solve that ran one more iteration on instance 1 is compared after that many
+    it2 = it.copy(); it2[1] += 1
+    xs, us, _ = oracle.scp_solve_iters(prob, it2)
+    r = oracle.compare_batch(prob, xs, us, it2, ref, 1e-4)
+    assert list(r["mismatch"]) == [1] and r["summary"]["max_rel_err"] == 0.0
+    # ... whereas against the stop-test solve it differs
+    assert oracle.rel_err(xs, ref[0]) > 0.0
