@@ -13,6 +13,7 @@
 #include "ucn_internal.h"
 #include "ucn_kernels.cuh"
 #include "ucn_lanes.cuh"
+#include "ucn_pair.cuh"
 
 using namespace ucn;
 
@@ -43,8 +44,18 @@ namespace ucn {
 
 void set_error_message(const char* msg) { snprintf(g_err, sizeof(g_err), "%s", msg); }
 
-int default_tpn(int model, int nodes) {
-  return (model == UCN_MODEL_QUAD12 && 4 * nodes <= LANES_MAX_THREADS) ? 4 : 1;
+bool tpn_allowed(int tpn, int model, int nodes, int precision, bool smem) {
+  if (tpn == 1) return true;
+  if (tpn == 4) return model == UCN_MODEL_QUAD12 && 4 * nodes <= LANES_MAX_THREADS;
+  if (tpn == 2)
+    return model == UCN_MODEL_MARS7 && precision == UCN_PREC_FP32_REFINE && smem &&
+           (2 * nodes + 31) / 32 * 32 <= PAIR_MAX_THREADS;
+  return false;
+}
+
+int default_tpn(int model, int nodes, int precision) {
+  if (tpn_allowed(4, model, nodes, precision, true)) return 4;
+  return 1;
 }
 
 std::vector<double> rho_schedule(double rho_final, double rho_geo, int K) {
@@ -54,7 +65,7 @@ std::vector<double> rho_schedule(double rho_final, double rho_geo, int K) {
   return fac;
 }
 
-Layout make_layout(int model, int nodes, int max_obs, int tsize, bool reg_mats) {
+Layout make_layout(int model, int nodes, int max_obs, int tsize, bool reg_mats, int tpn) {
   const bool quad = model_obstacles(model);
   const int NX = model_nx(model), NU = model_nu(model), NN = NX + NU;
   const int fixed = model == UCN_MODEL_QUAD12 ? Rec<Quad12>::END                 // fixed part of a node record
@@ -84,8 +95,9 @@ Layout make_layout(int model, int nodes, int max_obs, int tsize, bool reg_mats) 
   L.S = nodes;
   // Record stride: odd for one thread per node (consecutive nodes fall in
   // distinct banks); 4 mod 32 for the lane kernel, whose warps read 8 nodes x
-  // 4 consecutive row elements -- 32 distinct banks.
-  L.NS = default_tpn(model, nodes) == 4 ? nt + ((4 - nt) % 32 + 32) % 32 : (nt | 1);
+  // 4 consecutive row elements, and twice an odd number for the pair kernel,
+  // whose warps read 16 nodes x 2 consecutive row elements -- 32 distinct banks.
+  L.NS = tpn == 4 ? nt + ((4 - nt) % 32 + 32) % 32 : tpn == 2 ? nt + ((2 - nt) % 4 + 4) % 4 : (nt | 1);
   L.DS = dfixed | 1;
   L.tbytes = round_up((long long)nodes * L.NS * tsize, 16);
   L.bytes = round_up(L.tbytes + (long long)nodes * L.DS * 8, 16);
@@ -97,6 +109,12 @@ Layout make_layout(int model, int nodes, int max_obs, int tsize, bool reg_mats) 
                    : model == UCN_MODEL_MARS14 ? CB<Mars14>::END : CB<Mars7>::END;
     L.oC = L.bytes;
     L.bytes = round_up(L.bytes + 8LL * cb, 16);
+  }
+  // pair kernel: one H^-1 record per thread (two per node)
+  L.oPH = -1;
+  if (tpn == 2) {
+    L.oPH = L.bytes;
+    L.bytes += (long long)((2 * nodes + 31) / 32 * 32) * PAIR_HREC * 4;
   }
   return L;
 }
@@ -116,6 +134,7 @@ struct ucn_problem {
   int* order_d;
   int group, gcsize;     // scenarios per group, CTAs per thread-block cluster
   int tpn;               // threads per node of the fused solve
+  int optin;             // shared memory per CTA the device allows
 };
 
 namespace {
@@ -233,7 +252,7 @@ ucn_status ucn_problem_create(const ucn_problem_desc* d, ucn_problem** out) {
   ucn_problem* p = new ucn_problem();
   p->model = d->model; p->nx = NX; p->nu = NU; p->batch = d->batch; p->max_obs = obst ? d->max_obs : 0;
   p->Nmax = Nmax; p->precision = d->precision; p->group = group;
-  p->tpn = default_tpn(d->model, Nmax + 1);
+  p->tpn = default_tpn(d->model, Nmax + 1, d->precision);
   const int B = d->batch;
   std::vector<long long> xoff(B), uoff(B), soff(B);
   std::vector<int> node_inst;
@@ -330,9 +349,13 @@ ucn_status ucn_problem_create(const ucn_problem_desc* d, ucn_problem** out) {
   int optin = 0;
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   const long long static_sh = (long long)sizeof(InstShared) + (group > 1 ? (long long)sizeof(GroupShared) : 0) + 64;
-  p->L = make_layout(d->model, Nmax + 1, p->max_obs, tsize, small);
+  p->L = make_layout(d->model, Nmax + 1, p->max_obs, tsize, small, p->tpn);
   p->smem = p->L.bytes + static_sh <= optin;
-  if (!p->smem) p->L = make_layout(d->model, Nmax + 1, p->max_obs, tsize, false);
+  if (!p->smem) {
+    if (!tpn_allowed(p->tpn, d->model, Nmax + 1, d->precision, false)) p->tpn = 1;
+    p->L = make_layout(d->model, Nmax + 1, p->max_obs, tsize, false, p->tpn);
+  }
+  p->optin = optin;
   p->threads = (int)round_up(Nmax + 1, 32);
   p->smem_bytes = p->smem ? p->L.bytes : 0;
   if (group > 1 && !p->smem) {
@@ -401,10 +424,21 @@ ucn_status ucn_problem_set_order(ucn_problem* p, const int* order) {
 ucn_status ucn_problem_set_lanes(ucn_problem* p, int lanes_per_node) {
   g_err[0] = 0;
   if (!p) return fail(UCN_EINVAL, "null problem");
-  if (lanes_per_node == 1) { p->tpn = 1; return UCN_OK; }
-  if (lanes_per_node == 4 && default_tpn(p->model, p->Nmax + 1) == 4) { p->tpn = 4; return UCN_OK; }
-  return fail(UCN_EINVAL, "%d threads per node: 1, or 4 for quadrotor problems of at most %d nodes", lanes_per_node,
-              LANES_MAX_THREADS / 4);
+  if (!tpn_allowed(lanes_per_node, p->model, p->Nmax + 1, p->precision, p->smem))
+    return fail(UCN_EINVAL, "%d threads per node: 1; 2 for 3-DOF Mars problems of at most %d nodes on the FP32 path; "
+                "4 for quadrotor problems of at most %d nodes", lanes_per_node, PAIR_MAX_THREADS / 2,
+                LANES_MAX_THREADS / 4);
+  if (p->smem && lanes_per_node != p->tpn) {
+    // the record stride follows the threads per node (bank-conflict-free reads)
+    const Layout L = make_layout(p->model, p->Nmax + 1, p->max_obs, p->precision == UCN_PREC_FP64 ? 8 : 4,
+                                 p->model == UCN_MODEL_MARS7, lanes_per_node);
+    const long long static_sh = (long long)sizeof(InstShared) + (p->group > 1 ? (long long)sizeof(GroupShared) : 0) + 64;
+    if (L.bytes + static_sh > p->optin) return fail(UCN_EINVAL, "the %d-thread layout does not fit in shared memory", lanes_per_node);
+    p->L = L;
+    p->smem_bytes = L.bytes;
+  }
+  p->tpn = lanes_per_node;
+  return UCN_OK;
 }
 
 int ucn_problem_lanes(const ucn_problem* p) { return p ? p->tpn : -1; }

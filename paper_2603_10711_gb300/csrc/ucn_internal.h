@@ -15,8 +15,9 @@ struct Layout;
 // Sets the thread-local message returned by ucn_last_error (ucn_api.cu).
 void set_error_message(const char* msg);
 
-// Node-record layout of one instance (defined in ucn_api.cu).
-Layout make_layout(int model, int nodes, int max_obs, int tsize, bool reg_mats);
+// Node-record layout of one instance for a kernel with `tpn` threads per node
+// (defined in ucn_api.cu).
+Layout make_layout(int model, int nodes, int max_obs, int tsize, bool reg_mats, int tpn);
 
 // Everything one kernel launch needs besides its buffers.
 struct LaunchCfg {
@@ -29,11 +30,16 @@ struct LaunchCfg {
   cudaStream_t stream;
   int group;            // CTAs per thread-block cluster (scenario groups only)
   int nodes;            // nodes of the longest instance (N_max + 1)
-  int tpn;              // threads per node of the fused solve: 1, or 4 (lane kernel, quadrotor)
+  int tpn;              // threads per node of the fused solve: 1; 2 (pair kernel: 3-DOF Mars, FP32,
+                        // records in shared memory); 4 (lane kernel, quadrotor)
 };
 
-// Threads per node the fused solve uses by default for a model and node count.
-int default_tpn(int model, int nodes);
+// Threads per node the fused solve uses by default for a model, node count and
+// precision (records in shared memory; 1 otherwise for the 3-DOF Mars model).
+int default_tpn(int model, int nodes, int precision);
+// Whether `tpn` threads per node can run a model, node count and precision
+// (with the node records in shared memory when smem).
+bool tpn_allowed(int tpn, int model, int nodes, int precision, bool smem);
 
 // Launchers, one translation unit per (model, precision) so that the four
 // compile in parallel.

@@ -90,6 +90,7 @@ struct Layout {
   long long tbytes;        // bytes of the T region (16-byte multiple)
   long long bytes;         // bytes per instance
   long long oC;            // byte offset of the CB block (FP32 path; -1 without)
+  long long oPH;           // byte offset of the pair kernel's per-lane H^-1 records (-1 without)
 };
 
 // Per-thread view of its node.  W is the wide type of the precision (FP64,
@@ -144,8 +145,24 @@ template <class M, class T> struct MatStride {
   static constexpr bool pad = LaneModel<M>::value && sizeof(T) == 4;
   static constexpr int A = pad ? (M::NX | 1) : M::NX, B = pad ? (M::NU | 1) : M::NU;
 };
+// Which entries of A_i = dRK4/dx are exactly zero (0) or exactly one (1) at
+// every nominal, else 2.  Forward-mode differentiation gives an exact 0 where
+// the dynamics do not couple two states and an exact 1 where a state enters
+// its own update only additively.  3-DOF Mars (x = r, v, m; r' = v,
+// v' = T/m + g, m' = -alpha |T|): r_{k+1} depends on r (identity), on v along
+// the same axis and on m; v_{k+1} on v (identity) and m; m_{k+1} on m alone.
+template <class M> struct APattern {
+  __host__ __device__ static constexpr int kind(int, int) { return 2; }
+};
+template <> struct APattern<Mars7> {
+  __host__ __device__ static constexpr int kind(int r, int c) {
+    return r == c ? 1 : (r < 3 && c == r + 3) ? 2 : (r < 6 && c == 6) ? 2 : 0;
+  }
+};
+
 template <class M, class T, bool AOS>
 struct SmemMats {
+  __host__ __device__ static constexpr int akind(int, int) { return 2; }
   Node<T, AOS> nd;
   int oA, oB, oH;
   __device__ __forceinline__ T& A(int r, int c) const { return nd.at(oA, r * MatStride<M, T>::A + c); }
@@ -154,6 +171,7 @@ struct SmemMats {
 };
 template <class M, class T>
 struct RegMats {
+  __host__ __device__ static constexpr int akind(int, int) { return 2; }
   static constexpr int NN = M::NX + M::NU;
   mutable T a[M::NX * M::NX], b[M::NX * M::NU], h[NN * (NN + 1) / 2];
   __device__ __forceinline__ T& A(int r, int c) const { return a[r * M::NX + c]; }
@@ -164,8 +182,39 @@ template <class M> struct SmallModel {
   static constexpr int NN = M::NX + M::NU;
   static constexpr bool value = M::NX * M::NX + M::NX * M::NU + NN * (NN + 1) / 2 <= 128;
 };
-template <class M, class T, bool AOS>
-using MatsFor = typename std::conditional<AOS && SmallModel<M>::value, RegMats<M, T>, SmemMats<M, T, AOS>>::type;
+// Register-resident matrices of the kernel's own Jacobians: the products skip
+// the structural zeros of A_i and add its exact ones (APattern) -- the same
+// sums up to rounding (an exact one's term is added without a multiply, which
+// the compiler may fuse with that term's own product: bitwise equal in FP64,
+// within a few float ulps in FP32), fewer instructions, and no registers for
+// those entries.  The 3-DOF Mars model keeps 9 of its 49 entries.
+template <class M, class T>
+struct RegMatsS : RegMats<M, T> {
+  __host__ __device__ static constexpr int akind(int r, int c) { return APattern<M>::kind(r, c); }
+};
+// OWNJ: the matrices are the kernel's own Jacobians (their structure holds);
+// a caller's A (ucn_admm_solve) is taken as dense.
+template <class M, class T, bool AOS, bool OWNJ = false>
+using MatsFor = typename std::conditional<AOS && SmallModel<M>::value,
+                                          typename std::conditional<OWNJ, RegMatsS<M, T>, RegMats<M, T>>::type,
+                                          SmemMats<M, T, AOS>>::type;
+
+// acc += A(r, c) v, and acc += A(k, r) A(k, c), with the storage's structure of
+// A: exact zeros skipped, exact ones added without the product.
+template <class MS, class T>
+__device__ __forceinline__ void acc_A(T& acc, const MS& MT, int r, int c, T v) {
+  if (MS::akind(r, c) == 1) acc += v;
+  else if (MS::akind(r, c) == 2) acc += MT.A(r, c) * v;
+}
+template <class MS, class T>
+__device__ __forceinline__ void acc_AA(T& acc, const MS& MT, int k, int r, int c) {
+  const int kr = MS::akind(k, r), kc = MS::akind(k, c);
+  if (kr == 0 || kc == 0) return;
+  if (kr == 1 && kc == 1) acc += T(1);
+  else if (kr == 1) acc += MT.A(k, c);
+  else if (kc == 1) acc += MT.A(k, r);
+  else acc += MT.A(k, r) * MT.A(k, c);
+}
 
 template <class M, class T, bool AOS>
 __device__ __forceinline__ void init_mats(SmemMats<M, T, AOS>& m, const Node<T, AOS>& nd, const Layout& L) {
@@ -723,6 +772,9 @@ __device__ void node_setup(const Node<T, AOS>& nd, const Layout& L, const Proble
 // Packed lower-triangular index (row r, column c <= r).
 __host__ __device__ constexpr int pk(int r, int c) { return r * (r + 1) / 2 + c; }
 
+template <class T, int n, class MS>
+__device__ __forceinline__ bool factor_invert_packed(const MS& MT);
+
 // H_i of Eq. (4) plus rho_geo G_j^T G_j for each mirror set, assembled in
 // packed form and factored H = L L^T in place (unpivoted Cholesky; the
 // diagonal holds 1/L_jj).  Returns false on a non-positive pivot.  Node N,
@@ -745,7 +797,7 @@ __device__ __forceinline__ bool node_factor(const Node<T, AOS>& nd, const MS& MT
         if (!term) {
           T acc = T(0);
           #pragma unroll
-          for (int k = 0; k < NX; ++k) acc += MT.A(k, r) * MT.A(k, c);
+          for (int k = 0; k < NX; ++k) acc_AA(acc, MT, k, r, c);
           h += rd * acc;
         }
         if constexpr (IsQuad<M>::value) {
@@ -766,7 +818,7 @@ __device__ __forceinline__ bool node_factor(const Node<T, AOS>& nd, const MS& MT
       } else if (c < NX) {  // H21 = H12^T (zero at node N: no control there)
         T acc = T(0);
         #pragma unroll
-        for (int k = 0; k < NX; ++k) acc += MT.B(k, r - NX) * MT.A(k, c);
+        for (int k = 0; k < NX; ++k) acc_A(acc, MT, k, c, MT.B(k, r - NX));
         h = term ? T(0) : rd * acc;
       } else {  // H22 (identity at node N, decoupled from the state block)
         const int rr = r - NX, cc = c - NX;
@@ -789,6 +841,14 @@ __device__ __forceinline__ bool node_factor(const Node<T, AOS>& nd, const MS& MT
     }
   }
   (void)hasU;
+  return factor_invert_packed<T, n>(MT);
+}
+
+// Packed H (lower triangle) -> packed H^-1 in place: unpivoted Cholesky
+// H = L L^T, then L^-1 and H^-1 = L^-T L^-1.  Returns false on a non-positive
+// pivot (replaced by 1 so that the arithmetic stays finite).
+template <class T, int n, class MS>
+__device__ __forceinline__ bool factor_invert_packed(const MS& MT) {
   bool ok = true;
   #pragma unroll
   for (int j = 0; j < n; ++j) {
@@ -872,7 +932,7 @@ __device__ __forceinline__ void apply_H(const Node<T, AOS>& nd, const MS& MT, co
     for (int r = 0; r < NX; ++r) {
       T acc = T(0);
 #pragma unroll
-      for (int c = 0; c < NX; ++c) acc += MT.A(r, c) * xi[c];
+      for (int c = 0; c < NX; ++c) acc_A(acc, MT, r, c, xi[c]);
 #pragma unroll
       for (int c = 0; c < NU; ++c) acc += MT.B(r, c) * xi[NX + c];
       v[r] = rd * acc;
@@ -881,7 +941,7 @@ __device__ __forceinline__ void apply_H(const Node<T, AOS>& nd, const MS& MT, co
     for (int j = 0; j < NX; ++j) {
       T acc = T(0);
 #pragma unroll
-      for (int k = 0; k < NX; ++k) acc += MT.A(k, j) * v[k];
+      for (int k = 0; k < NX; ++k) acc_A(acc, MT, k, j, v[k]);
       out[j] += acc;
     }
 #pragma unroll
@@ -942,7 +1002,7 @@ __device__ __forceinline__ void node_rhs(const Node<T, AOS>& nd, const MS& MT, c
     for (int j = 0; j < NX; ++j) {
       T acc = T(0);
 #pragma unroll
-      for (int k = 0; k < NX; ++k) acc += MT.A(k, j) * w[k];
+      for (int k = 0; k < NX; ++k) acc_A(acc, MT, k, j, w[k]);
       g[j] += acc;
     }
 #pragma unroll
@@ -1175,7 +1235,7 @@ __device__ __forceinline__ void admm_iteration(const Node<T, AOS>& nd, const MS&
         for (int r = 0; r < NX; ++r) {
           T acc = nd.at(Rec<M>::C, r);
 #pragma unroll
-          for (int c = 0; c < NX; ++c) acc += MT.A(r, c) * x[c];
+          for (int c = 0; c < NX; ++c) acc_A(acc, MT, r, c, x[c]);
 #pragma unroll
           for (int c = 0; c < NU; ++c) acc += MT.B(r, c) * x[NX + c];
           nd.at(Rec<M>::Ex1, r) = acc;
@@ -1283,7 +1343,8 @@ __device__ __forceinline__ void admm_iteration(const Node<T, AOS>& nd, const MS&
           for (int j = 0; j < NX; ++j) {
             T acc = T(0);
 #pragma unroll
-            for (int k = 0; k < NX; ++k) acc += MT.A(k, j) * nd.nb(Rec<M>::Ex1, k, i + 1);
+            for (int k = 0; k < NX; ++k)
+              if (MS::akind(k, j)) acc_A(acc, MT, k, j, nd.nb(Rec<M>::Ex1, k, i + 1));
             sv[j] += acc;
           }
 #pragma unroll
@@ -1769,7 +1830,8 @@ __device__ void scp_candidate(const Node<T, AOS>& nd, const MS& MT, const Proble
         dinf = maxv(dinf, wide_abs_round(fc[r]));
         T lin = nd.at(Rec<M>::C, r) - nd.nb(Rec<M>::Xh, r, i + 1);
 #pragma unroll
-        for (int c = 0; c < NX; ++c) lin += MT.A(r, c) * nd.at(Rec<M>::Xh, c);
+        for (int c = 0; c < NX; ++c)
+          if (MS::akind(r, c)) acc_A(lin, MT, r, c, nd.at(Rec<M>::Xh, c));
 #pragma unroll
         for (int c = 0; c < NU; ++c) lin += MT.B(r, c) * nd.at(Rec<M>::Uh, c);
         lin1 += absv(lin);
@@ -1855,6 +1917,55 @@ __device__ void scp_finish(const Node<T, AOS>& nd, const Layout& L, const Proble
   block_reduce(sh, w, 2, 3);
 }
 
+// The acceptance test and trust-region update of one SCP iteration (the paper
+// omits them, Sec. III-A; ratio test on an l1 merit), by one thread: J(nominal)
+// Jn, J(candidate) Jc, the linear model L(candidate) Lc (sums over a scenario
+// group where there is one, Jc_own this CTA's own J(candidate)), the
+// candidate's max defect and step; sets sh.accept, sh.radius, sh.Jn, sh.stop
+// and sh.status.
+__device__ __forceinline__ void scp_decide(InstShared& sh, const ProblemDev& P, double Jn, double Jc, double Lc,
+                                           double Jc_own, double dinf, double step, bool timed_out, int k, int Kscp) {
+  const double den = Jn - Lc, num = Jn - Jc;
+  double radius2 = sh.radius;
+  bool acc_ = true;
+  if (!(den <= 1e-12)) {
+    const double ratio = num / den;
+    acc_ = ratio > 0.0;
+    if (ratio < 0.25) radius2 *= 0.5;
+    else if (ratio > 0.75) radius2 = fmin(2.0 * radius2, P.tr_max);
+  }
+  radius2 = fmax(radius2, P.tr_min);
+  if (!isfinite(Jc)) { acc_ = false; sh.status = ST_NUMERIC; }
+  if (acc_) sh.Jn = Jc_own;
+  sh.radius = radius2;
+  sh.accept = acc_;
+  int stop = (sh.status == ST_NUMERIC);
+  if (P.stop && acc_ && dinf <= P.defect_tol && step <= P.step_tol) stop = 1;
+  if (timed_out && !stop && k + 1 < Kscp) { sh.status = ST_TIMEOUT; stop = 1; }
+  sh.stop = stop;
+}
+
+// The per-instance result record and status of a solve, by one thread; w: the
+// returned trajectory's cost, l1 and max defect (scp_finish); group_failed: a
+// scenario group lost its consensus partner.
+__device__ __forceinline__ void scp_report(const InstShared& sh, const ProblemDev& P, int b, const double* w,
+                                           const double* res, double last_step, int iters_run, int accepted,
+                                           unsigned long long mask, unsigned long long t0, bool group_failed,
+                                           ucn_scp_stats* stats, int* status_out) {
+  int st = sh.status;
+  if (group_failed && st != ST_NUMERIC) st = ST_TIMEOUT;
+  if (!isfinite(w[2]) || sh.xbar[1]) st = ST_NUMERIC;
+  if (st == ST_OK && !(w[2] <= P.defect_tol)) st = ST_NOTCONV;
+  ucn_scp_stats s;
+  s.defect = w[2]; s.cost = w[0]; s.merit = w[0] + P.w_d * w[1];
+  s.primal_res = sqrt(res[0]); s.dual_res = sqrt(res[1]); s.tr_radius = sh.radius; s.step = last_step;
+  s.scp_iters = iters_run; s.accepted = accepted; s.accept_mask = mask; s.status = st; s.reserved = 0;
+  s.t_start_ns = t0; s.t_end_ns = globaltimer_ns();
+  s.pad[0] = s.pad[1] = s.pad[2] = s.pad[3] = 0.0;
+  stats[b] = s;
+  status_out[b] = st;
+}
+
 // The whole SCP solve of one instance per CTA (Sec. III-A + III-B): per SCP
 // iteration, linearise (T), assemble + factor (T), admm_iters ADMM
 // iterations (T), then the rollout, defects, merit and trust-region
@@ -1889,7 +2000,7 @@ __global__ void __launch_bounds__(MAX_THREADS) scp_kernel(ProblemDev P, Layout L
   const int b = (GROUP || !P.order) ? (int)blockIdx.x : P.order[blockIdx.x];
   constexpr bool AOS = SMEM;
   Node<T, AOS> nd = make_node<T, SMEM>(P, L, smem, b);
-  MatsFor<M, T, AOS> MT;
+  MatsFor<M, T, AOS, true> MT;
   init_mats<M, T, AOS>(MT, nd, L);
   typedef typename Node<T, AOS>::W W;
   const int i = nd.i, N = nd.N;
@@ -1964,27 +2075,7 @@ __global__ void __launch_bounds__(MAX_THREADS) scp_kernel(ProblemDev P, Layout L
         Jn = a[0]; Jc = a[1]; Lc = a[2]; v[3] = a[3]; v[4] = a[4]; timed_out = a[5] != 0.0;
       }
     }
-    if (threadIdx.x == 0) {
-      // acceptance (the paper omits it; ratio test on an l1 merit)
-      const double den = Jn - Lc, num = Jn - Jc;
-      double radius2 = sh.radius;
-      bool acc_ = true;
-      if (!(den <= 1e-12)) {
-        const double ratio = num / den;
-        acc_ = ratio > 0.0;
-        if (ratio < 0.25) radius2 *= 0.5;
-        else if (ratio > 0.75) radius2 = fmin(2.0 * radius2, P.tr_max);
-      }
-      radius2 = fmax(radius2, P.tr_min);
-      if (!isfinite(Jc)) { acc_ = false; sh.status = ST_NUMERIC; }
-      if (acc_) sh.Jn = Jc_own;
-      sh.radius = radius2;
-      sh.accept = acc_;
-      int stop = (sh.status == ST_NUMERIC);
-      if (P.stop && acc_ && v[3] <= P.defect_tol && v[4] <= P.step_tol) stop = 1;
-      if (timed_out && !stop && k + 1 < Kscp) { sh.status = ST_TIMEOUT; stop = 1; }
-      sh.stop = stop;
-    }
+    if (threadIdx.x == 0) scp_decide(sh, P, Jn, Jc, Lc, Jc_own, v[3], v[4], timed_out, k, Kscp);
     __syncthreads();
     last_step = v[4];
     if (sh.accept) {
@@ -1998,20 +2089,9 @@ __global__ void __launch_bounds__(MAX_THREADS) scp_kernel(ProblemDev P, Layout L
   double w[6] = {0, 0, 0, 0, 0, 0};
   scp_finish<M, T, AOS>(nd, L, P, I, b, active, xo, uo, xout, uout, sh, w);
   if (threadIdx.x == 0) {
-    int st = sh.status;
-    if constexpr (GROUP) {
-      if (G->gfail && st != ST_NUMERIC) st = ST_TIMEOUT;   // the group lost its consensus partner
-    }
-    if (!isfinite(w[2]) || sh.xbar[1]) st = ST_NUMERIC;
-    if (st == ST_OK && !(w[2] <= P.defect_tol)) st = ST_NOTCONV;
-    ucn_scp_stats s;
-    s.defect = w[2]; s.cost = w[0]; s.merit = w[0] + P.w_d * w[1];
-    s.primal_res = sqrt(res[0]); s.dual_res = sqrt(res[1]); s.tr_radius = sh.radius; s.step = last_step;
-    s.scp_iters = iters_run; s.accepted = accepted; s.accept_mask = mask; s.status = st; s.reserved = 0;
-    s.t_start_ns = t0; s.t_end_ns = globaltimer_ns();
-    s.pad[0] = s.pad[1] = s.pad[2] = s.pad[3] = 0.0;
-    stats[b] = s;
-    status_out[b] = st;
+    bool gfail = false;
+    if constexpr (GROUP) gfail = G->gfail;   // the group lost its consensus partner
+    scp_report(sh, P, b, w, res, last_step, iters_run, accepted, mask, t0, gfail, stats, status_out);
   }
   if constexpr (GROUP) group_finish(P);
 }

@@ -632,27 +632,7 @@ __global__ void __launch_bounds__(LANES_MAX_THREADS) scp_kernel_lanes(ProblemDev
         Jn = a[0]; Jc = a[1]; Lc = a[2]; v[3] = a[3]; v[4] = a[4]; timed_out = a[5] != 0.0;
       }
     }
-    if (threadIdx.x == 0) {
-      // acceptance (the paper omits it; ratio test on an l1 merit)
-      const double den = Jn - Lc, num = Jn - Jc;
-      double radius2 = sh.radius;
-      bool acc_ = true;
-      if (!(den <= 1e-12)) {
-        const double ratio = num / den;
-        acc_ = ratio > 0.0;
-        if (ratio < 0.25) radius2 *= 0.5;
-        else if (ratio > 0.75) radius2 = fmin(2.0 * radius2, P.tr_max);
-      }
-      radius2 = fmax(radius2, P.tr_min);
-      if (!isfinite(Jc)) { acc_ = false; sh.status = ST_NUMERIC; }
-      if (acc_) sh.Jn = Jc_own;
-      sh.radius = radius2;
-      sh.accept = acc_;
-      int stop = (sh.status == ST_NUMERIC);
-      if (P.stop && acc_ && v[3] <= P.defect_tol && v[4] <= P.step_tol) stop = 1;
-      if (timed_out && !stop && k + 1 < Kscp) { sh.status = ST_TIMEOUT; stop = 1; }
-      sh.stop = stop;
-    }
+    if (threadIdx.x == 0) scp_decide(sh, P, Jn, Jc, Lc, Jc_own, v[3], v[4], timed_out, k, Kscp);
     __syncthreads();
     last_step = v[4];
     if (sh.accept) {
@@ -666,20 +646,9 @@ __global__ void __launch_bounds__(LANES_MAX_THREADS) scp_kernel_lanes(ProblemDev
   double w[6] = {0, 0, 0, 0, 0, 0};
   scp_finish<M, T, AOS>(ndd, L, P, I, b, dact, xo, uo, xout, uout, sh, w);
   if (threadIdx.x == 0) {
-    int st = sh.status;
-    if constexpr (GROUP) {
-      if (G->gfail && st != ST_NUMERIC) st = ST_TIMEOUT;
-    }
-    if (!isfinite(w[2]) || sh.xbar[1]) st = ST_NUMERIC;
-    if (st == ST_OK && !(w[2] <= P.defect_tol)) st = ST_NOTCONV;
-    ucn_scp_stats s;
-    s.defect = w[2]; s.cost = w[0]; s.merit = w[0] + P.w_d * w[1];
-    s.primal_res = sqrt(res[0]); s.dual_res = sqrt(res[1]); s.tr_radius = sh.radius; s.step = last_step;
-    s.scp_iters = iters_run; s.accepted = accepted; s.accept_mask = mask; s.status = st; s.reserved = 0;
-    s.t_start_ns = t0; s.t_end_ns = globaltimer_ns();
-    s.pad[0] = s.pad[1] = s.pad[2] = s.pad[3] = 0.0;
-    stats[b] = s;
-    status_out[b] = st;
+    bool gfail = false;
+    if constexpr (GROUP) gfail = G->gfail;   // the group lost its consensus partner
+    scp_report(sh, P, b, w, res, last_step, iters_run, accepted, mask, t0, gfail, stats, status_out);
   }
   if constexpr (GROUP) group_finish(P);
 }

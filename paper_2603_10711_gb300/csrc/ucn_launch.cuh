@@ -3,6 +3,7 @@
 #include "ucn_internal.h"
 #include "ucn_kernels.cuh"
 #include "ucn_lanes.cuh"
+#include "ucn_pair.cuh"
 
 namespace ucn {
 
@@ -39,9 +40,30 @@ cudaError_t launch_scpl_v(const LaunchCfg& c, const double* x0, const double* u0
   return cudaGetLastError();
 }
 
+// The pair kernel (2 threads per node; 3-DOF Mars, FP32, records in shared memory).
+template <class M, bool R>
+cudaError_t launch_scpp_v(const LaunchCfg& c, const double* x0, const double* u0, double* xo, double* uo,
+                          ucn_scp_stats* st, int* status) {
+  const ProblemDev& P = *(const ProblemDev*)c.P;
+  const Layout& L = *(const Layout*)c.L;
+  auto k = scp_kernel_pair<M, R>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem_bytes);
+  if (e != cudaSuccess) return e;
+  // the whole unified L1 / shared memory as shared memory: two ~105 KB CTAs per SM
+  e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  if (e != cudaSuccess) return e;
+  const int threads = (2 * c.nodes + 31) / 32 * 32;
+  if (!c.smem || threads > PAIR_MAX_THREADS) return cudaErrorInvalidConfiguration;
+  k<<<c.blocks, threads, c.smem_bytes, c.stream>>>(P, L, x0, u0, xo, uo, st, status);
+  return cudaGetLastError();
+}
+
 template <class M, class T, bool R>
 cudaError_t launch_scp_t(const LaunchCfg& c, const double* x0, const double* u0, double* xo, double* uo,
                          ucn_scp_stats* st, int* status) {
+  if constexpr (std::is_same<M, Mars7>::value && std::is_same<T, float>::value && R) {
+    if (c.tpn == 2) return launch_scpp_v<M, R>(c, x0, u0, xo, uo, st, status);
+  }
   if constexpr (LaneModel<M>::value) {
     if (c.tpn == 4)
       return c.smem ? launch_scpl_v<M, T, true, R>(c, x0, u0, xo, uo, st, status)
@@ -189,3 +211,10 @@ cudaError_t launch_linearize_t(const void* Pv, const int* node_inst, long long t
     return scp_kernel_lanes<MODEL, T, true, REFINE, true, 4>;                                              \
   }                                                                                                        \
   }
+
+// Pair-kernel variant in its own translation unit.
+#define UCN_SCPP_V(MODEL, REFINE)                                                                          \
+  cudaError_t ucn::launch_scpp_v<ucn::MODEL, REFINE>(const ucn::LaunchCfg&, const double*, const double*, \
+                                                     double*, double*, ucn_scp_stats*, int*)
+#define UCN_INSTANTIATE_SCPP(MODEL, REFINE) template UCN_SCPP_V(MODEL, REFINE);
+#define UCN_EXTERN_SCPP(MODEL, REFINE) extern template UCN_SCPP_V(MODEL, REFINE);

@@ -116,7 +116,8 @@ extern "C" ucn_status ucn_scp_solve_noalloc(const ucn_problem_desc* d, const dou
     return nfail(UCN_EINVAL, "batch needs %lld bytes of scratch; the no-allocation entry point holds %llu",
                  need, (unsigned long long)UCN_NOALLOC_SCRATCH_BYTES);
   const int tsize = d->precision == UCN_PREC_FP64 ? 8 : 4;
-  const Layout L = make_layout(d->model, Nmax + 1, max_obs, tsize, d->model == UCN_MODEL_MARS7);
+  const int tpn = default_tpn(d->model, Nmax + 1, d->precision);
+  const Layout L = make_layout(d->model, Nmax + 1, max_obs, tsize, d->model == UCN_MODEL_MARS7, tpn);
   int dev = 0, optin = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return nfail(UCN_ECUDA, "no CUDA device"); }
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -154,7 +155,7 @@ extern "C" ucn_status ucn_scp_solve_noalloc(const ucn_problem_desc* d, const dou
   LaunchCfg c;
   c.P = &P; c.L = &L; c.smem = true; c.smem_bytes = L.bytes;
   c.threads = (int)((Nmax + 1 + 31) / 32 * 32); c.blocks = B; c.stream = st; c.group = 1;
-  c.nodes = Nmax + 1; c.tpn = default_tpn(d->model, Nmax + 1);
+  c.nodes = Nmax + 1; c.tpn = tpn;
   auto fn = launchers_for(d->model, d->precision).scp;
   e = fn(c, x0_d, u0_d, x_out_d, u_out_d, stats_d, status_d);
   if (e != cudaSuccess) return nfail(UCN_ECUDA, "scp launch: %s", cudaGetErrorString(e));

@@ -51,6 +51,7 @@ struct ucn_server {
   bool smem;
   long long smem_bytes;
   int threads;
+  int tpn;               // threads per node of the fused solve
   std::vector<void*> dev_allocs, host_allocs;
   // pinned host mirrors of the per-slot problem arrays (same layout as on the device)
   int *hN, *hnobs;
@@ -155,9 +156,13 @@ ucn_status ucn_serve_create(const ucn_serve_config* c, ucn_server** out) {
   int optin = 0;
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   const long long static_sh = (long long)sizeof(InstShared) + 64;
-  s->L = make_layout(c->model, s->Nmax + 1, s->max_obs, tsize, c->model == UCN_MODEL_MARS7);
+  s->tpn = default_tpn(c->model, s->Nmax + 1, c->precision);
+  s->L = make_layout(c->model, s->Nmax + 1, s->max_obs, tsize, c->model == UCN_MODEL_MARS7, s->tpn);
   s->smem = s->L.bytes + static_sh <= optin;
-  if (!s->smem) s->L = make_layout(c->model, s->Nmax + 1, s->max_obs, tsize, false);
+  if (!s->smem) {
+    if (!tpn_allowed(s->tpn, c->model, s->Nmax + 1, c->precision, false)) s->tpn = 1;
+    s->L = make_layout(c->model, s->Nmax + 1, s->max_obs, tsize, false, s->tpn);
+  }
   s->smem_bytes = s->smem ? s->L.bytes : 0;
   s->threads = (s->Nmax + 1 + 31) / 32 * 32;
   s->R = c->kept > 0 ? c->kept : 2 * S;
@@ -324,7 +329,7 @@ ucn_status ucn_serve_pump(ucn_server* s, int* launched) {
   LaunchCfg c;
   c.P = &P; c.L = &s->L; c.smem = s->smem; c.smem_bytes = s->smem_bytes;
   c.threads = s->threads; c.blocks = (int)ready.size(); c.stream = st; c.group = 1;
-  c.nodes = s->cfg.max_horizon + 1; c.tpn = default_tpn(s->cfg.model, s->cfg.max_horizon + 1);
+  c.nodes = s->cfg.max_horizon + 1; c.tpn = s->tpn;
   auto fn = launchers_for(s->cfg.model, s->cfg.precision).scp;
   cudaError_t e = fn(c, s->x0, s->u0, s->xo, s->uo, s->stats, s->status);
   if (e == cudaSuccess) e = cudaEventRecord(s->done[lane], st);

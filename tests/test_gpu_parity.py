@@ -308,3 +308,70 @@ def test_full_size_mars_batch_sampled_against_oracle():
         # every returned trajectory satisfies the boundary conditions exactly
         np.testing.assert_array_equal(xg[prob.xoff[b]], prob.xinit[b])
         np.testing.assert_array_equal(xg[prob.xoff[b] + 100][:6], 0.0)
+
+
+# ------------------------------------------------------------------ two threads per node (3-DOF Mars, FP32)
+def solve_with_lanes(prob, lanes, prec=ucn.UCN_PREC_FP32_REFINE):
+    s = ucn.Solver(prob, precision=prec)
+    ucn.ucn_problem_set_lanes(s.handle, lanes)
+    assert ucn.ucn_problem_lanes(s.handle) == lanes
+    x, u = s.scp_solve()
+    torch.cuda.synchronize()
+    st = s.stats_host()
+    out = x.cpu().numpy(), u.cpu().numpy(), st
+    s.close()
+    return out
+
+
+@pytest.mark.parametrize("case", ["batch", "uneven", "shortest", "longest"])
+def test_pair_kernel_matches_oracle(case):
+    # the pair kernel (2 threads per node) against the oracle at 1e-4 after the same
+    # SCP iteration count, and against the one-thread kernel
+    if case == "batch":
+        prob = W.mars_batch(48, seed=1)
+    elif case == "uneven":
+        # horizons 5..111 in one launch: inactive pairs and partly filled warps
+        base = W.mars_batch(1, seed=2, N=111)
+        probs = [W.mars_batch(1, seed=20 + k, N=n) for k, n in enumerate((5, 37, 64, 111, 90, 17))]
+        prob = probs[0]
+        for p in probs[1:]:
+            prob = concat(prob, p)
+    elif case == "shortest":
+        prob = W.mars_batch(3, seed=4, N=1, settings=dict(scp_iters=4, admm_iters=30, stop=0))
+    else:
+        prob = W.mars_batch(4, seed=5, N=111)
+    xg, ug, st = solve_with_lanes(prob, 2)
+    ref = oracle.scp_solve(prob)[:3]
+    r = oracle.compare_batch(prob, xg, ug, st["scp_iters"], ref, TOL32)
+    assert r["summary"]["n_over_tol"] == 0, (r["summary"], r["err"])
+    d64 = check_fp64_defects(prob, st, xg, ug)
+    conv = ref[2][:, 0] <= 1e-5
+    assert (d64[conv] <= 1e-5).all() and (st["status"][conv] == 0).all()
+    x1, u1, st1 = solve_with_lanes(prob, 1)
+    same = st1["scp_iters"] == st["scp_iters"]
+    for b in np.nonzero(same)[0]:
+        xo, N = prob.xoff[b], int(prob.N[b])
+        assert rel_err(xg[xo:xo + N + 1], x1[xo:xo + N + 1]) <= TOL32
+
+
+def concat(a, b):
+    import dataclasses
+    f = {}
+    for fld in dataclasses.fields(a):
+        va, vb = getattr(a, fld.name), getattr(b, fld.name)
+        if fld.name in ("model", "nx", "nu"):
+            f[fld.name] = va
+        elif fld.name == "settings":
+            f[fld.name] = dict(va)
+        else:
+            f[fld.name] = np.concatenate([va, vb])
+    return W.Problem(**f)
+
+
+def test_pair_layout_is_refused_where_it_does_not_apply():
+    with pytest.raises(ucn.UcnError):
+        solve_with_lanes(W.mars_batch(1, seed=1, N=20), 2, prec=ucn.UCN_PREC_FP64)
+    with pytest.raises(ucn.UcnError):
+        solve_with_lanes(W.mars_batch(1, seed=1, N=112), 2)      # 113 nodes: beyond the pair kernel's CTA
+    with pytest.raises(ucn.UcnError):
+        solve_with_lanes(W.quad_path(1, seed=0, N=20), 2)
