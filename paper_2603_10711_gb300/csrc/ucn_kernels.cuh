@@ -980,16 +980,64 @@ __device__ __forceinline__ void apply_H(const Node<T, AOS>& nd, const MS& MT, co
   }
 }
 
+// The node's own ADMM variables z, lambda, mu, nu_x, nu_u (no other node reads
+// them).  REG: held in registers for the length of an ADMM call, loaded from
+// the node record before it and written back after it (the register-resident
+// FP32 kernels of small models, where the structure of A leaves room);
+// otherwise references into the record.
+template <class M, class T, bool AOS, bool REG>
+struct NodeState;
+template <class M, class T, bool AOS>
+struct NodeState<M, T, AOS, true> {
+  mutable T zv[M::NX], lamv[M::NX], muv[M::NX], nuxv[M::NX], nuuv[M::NU];
+  __device__ __forceinline__ T& z(int j) const { return zv[j]; }
+  __device__ __forceinline__ T& lam(int j) const { return lamv[j]; }
+  __device__ __forceinline__ T& mu(int j) const { return muv[j]; }
+  __device__ __forceinline__ T& nux(int j) const { return nuxv[j]; }
+  __device__ __forceinline__ T& nuu(int j) const { return nuuv[j]; }
+  __device__ __forceinline__ void load(const Node<T, AOS>& nd) {
+#pragma unroll
+    for (int j = 0; j < M::NX; ++j) {
+      zv[j] = nd.at(Rec<M>::Z, j); lamv[j] = nd.at(Rec<M>::Lam, j); muv[j] = nd.at(Rec<M>::Mu, j);
+      nuxv[j] = nd.at(Rec<M>::Nux, j);
+    }
+#pragma unroll
+    for (int j = 0; j < M::NU; ++j) nuuv[j] = nd.at(Rec<M>::Nuu, j);
+  }
+  __device__ __forceinline__ void store(const Node<T, AOS>& nd) const {
+#pragma unroll
+    for (int j = 0; j < M::NX; ++j) {
+      nd.at(Rec<M>::Z, j) = zv[j]; nd.at(Rec<M>::Lam, j) = lamv[j]; nd.at(Rec<M>::Mu, j) = muv[j];
+      nd.at(Rec<M>::Nux, j) = nuxv[j];
+    }
+#pragma unroll
+    for (int j = 0; j < M::NU; ++j) nd.at(Rec<M>::Nuu, j) = nuuv[j];
+  }
+};
+template <class M, class T, bool AOS>
+struct NodeState<M, T, AOS, false> {
+  Node<T, AOS> nd;
+  __device__ __forceinline__ T& z(int j) const { return nd.at(Rec<M>::Z, j); }
+  __device__ __forceinline__ T& lam(int j) const { return nd.at(Rec<M>::Lam, j); }
+  __device__ __forceinline__ T& mu(int j) const { return nd.at(Rec<M>::Mu, j); }
+  __device__ __forceinline__ T& nux(int j) const { return nd.at(Rec<M>::Nux, j); }
+  __device__ __forceinline__ T& nuu(int j) const { return nd.at(Rec<M>::Nuu, j); }
+  __device__ __forceinline__ void load(const Node<T, AOS>& n) { nd = n; }
+  __device__ __forceinline__ void store(const Node<T, AOS>&) const {}
+};
+template <class M, class T, bool AOS>
+using NodeStateFor = NodeState<M, T, AOS, AOS && SmallModel<M>::value && std::is_same<T, float>::value>;
+
 // Right-hand side g_i of Step 1 (stationarity of Eq. (3) in (x_i, u_i)).
 template <class M, class T, bool AOS, int n, class MS>
 __device__ __forceinline__ void node_rhs(const Node<T, AOS>& nd, const MS& MT, const Layout& L, const Inst<T>& I,
-                                         const NodeConst<M, T>& K, T re, T rd, T rg, T* g) {
+                                         const NodeConst<M, T>& K, const NodeStateFor<M, T, AOS>& S, T re, T rd, T rg, T* g) {
   constexpr int NX = M::NX, NU = M::NU;
   const int i = nd.i;
 #pragma unroll
   for (int j = 0; j < NX; ++j) {
-    T v = -K.q[j] + rg * nd.at(Rec<M>::Xh, j) - nd.at(Rec<M>::Nux, j);
-    if (i > 0) v += re * nd.at(Rec<M>::Z, j) - nd.at(Rec<M>::Lam, j);
+    T v = -K.q[j] + rg * nd.at(Rec<M>::Xh, j) - S.nux(j);
+    if (i > 0) v += re * S.z(j) - S.lam(j);
     g[j] = v;
   }
   if constexpr (n > NX) {
@@ -1010,7 +1058,7 @@ __device__ __forceinline__ void node_rhs(const Node<T, AOS>& nd, const MS& MT, c
       T acc = T(0);
 #pragma unroll
       for (int k = 0; k < NX; ++k) acc += MT.B(k, j) * w[k];
-      g[NX + j] = -K.q[NX + j] + acc + rg * nd.at(Rec<M>::Uh, j) - nd.at(Rec<M>::Nuu, j);
+      g[NX + j] = -K.q[NX + j] + acc + rg * nd.at(Rec<M>::Uh, j) - S.nuu(j);
     }
    } else {
 #pragma unroll
@@ -1205,7 +1253,7 @@ __device__ __forceinline__ void admm_iteration(const Node<T, AOS>& nd, const MS&
                                                const NodeConst<M, T>& K, bool active, T re, T rd, T rg,
                                                T irg, T ired, typename WideOf<T>::type& rp,
                                                typename WideOf<T>::type& rdl, GroupShared* G,
-                                               GroupX& X, const ProblemDev& P) {
+                                               GroupX& X, const ProblemDev& P, const NodeStateFor<M, T, AOS>& S) {
   constexpr int NX = M::NX, NU = M::NU, NN = NX + NU;
   const int i = nd.i, N = nd.N;
   constexpr bool last = LAST;
@@ -1218,7 +1266,7 @@ __device__ __forceinline__ void admm_iteration(const Node<T, AOS>& nd, const MS&
     // warp that holds it runs one code path instead of two.
     if (active) {
       T g[NN];
-      node_rhs<M, T, AOS, NN>(nd, MT, L, I, K, re, rd, rg, g);
+      node_rhs<M, T, AOS, NN>(nd, MT, L, I, K, S, re, rd, rg, g);
       sym_solve<T, NN>(MT, g, x);
       if constexpr (REFINE) {
         T hx[NN], dx[NN];
@@ -1263,16 +1311,16 @@ __device__ __forceinline__ void admm_iteration(const Node<T, AOS>& nd, const MS&
       // ---- Step 3: projections onto the boxes (Eq. (7)) and Step 4 for nu_x, nu_u
 #pragma unroll
       for (int j = 0; j < NX; ++j) {
-        const T nux = nd.at(Rec<M>::Nux, j);
+        const T nux = S.nux(j);
         const T xh = clampv(x[j] + nux * irg, nd.at(Rec<M>::Xlo, j), nd.at(Rec<M>::Xhi, j));
         if (last) { sv[j] += rg * (xh - nd.at(Rec<M>::Xh, j)); acc_sq_diff(rp, x[j], xh); }
         nd.at(Rec<M>::Xh, j) = xh;
-        nd.at(Rec<M>::Nux, j) = nux + rg * (x[j] - xh);
+        S.nux(j) = nux + rg * (x[j] - xh);
       }
       if (i < N) {
 #pragma unroll
         for (int j = 0; j < NU; ++j) {
-          const T nuu = nd.at(Rec<M>::Nuu, j);
+          const T nuu = S.nuu(j);
           if constexpr (GROUP) {
             if (i == 0) {   // sum of arguments | max of lower bounds | max of -upper bounds
               const double ub = wide_to_double(nd.dat(Rec<M>::Ubar, j));
@@ -1286,7 +1334,7 @@ __device__ __forceinline__ void admm_iteration(const Node<T, AOS>& nd, const MS&
           const T uh = clampv(x[NX + j] + nuu * irg, nd.at(Rec<M>::Ulo, j), nd.at(Rec<M>::Uhi, j));
           if (last) { sv[NX + j] += rg * (uh - nd.at(Rec<M>::Uh, j)); acc_sq_diff(rp, x[NX + j], uh); }
           nd.at(Rec<M>::Uh, j) = uh;
-          nd.at(Rec<M>::Nuu, j) = nuu + rg * (x[NX + j] - uh);
+          S.nuu(j) = nuu + rg * (x[NX + j] - uh);
         }
       }
       node_mirrors<M, T, AOS, NN>(nd, L, I, rg, irg, x, false, last, sv, rp);   // control sets: i < N only
@@ -1298,13 +1346,13 @@ __device__ __forceinline__ void admm_iteration(const Node<T, AOS>& nd, const MS&
 #pragma unroll
         for (int j = 0; j < NX; ++j) {
           const T dd = nd.nb(Rec<M>::Ex1, j, i - 1);
-          const T zo = nd.at(Rec<M>::Z, j);
-          const T lam = nd.at(Rec<M>::Lam, j), mu = nd.at(Rec<M>::Mu, j);
+          const T zo = S.z(j);
+          const T lam = S.lam(j), mu = S.mu(j);
           const T z = (re * x[j] + lam + rd * dd - mu) * ired;
-          nd.at(Rec<M>::Z, j) = z;
-          nd.at(Rec<M>::Lam, j) = lam + re * (x[j] - z);
+          S.z(j) = z;
+          S.lam(j) = lam + re * (x[j] - z);
           const T mun = mu + rd * (z - dd);
-          nd.at(Rec<M>::Mu, j) = mun;
+          S.mu(j) = mun;
           dz[j] = z - zo;
           if (last) {
             sv[j] += re * dz[j];
@@ -1322,10 +1370,10 @@ __device__ __forceinline__ void admm_iteration(const Node<T, AOS>& nd, const MS&
           const double v = fmin(fmax(tot[j] / (double)P.group, tot[NU + j]), -tot[2 * NU + j]);
           G->u0[j] = v;
           const T uh = (T)(v - wide_to_double(nd.dat(Rec<M>::Ubar, j)));
-          const T nuu = nd.at(Rec<M>::Nuu, j);
+          const T nuu = S.nuu(j);
           if (last) { sv[NX + j] += rg * (uh - nd.at(Rec<M>::Uh, j)); acc_sq_diff(rp, x[NX + j], uh); }
           nd.at(Rec<M>::Uh, j) = uh;
-          nd.at(Rec<M>::Nuu, j) = nuu + rg * (x[NX + j] - uh);
+          S.nuu(j) = nuu + rg * (x[NX + j] - uh);
         }
       }
     }
@@ -1362,7 +1410,7 @@ __device__ __forceinline__ void admm_iteration(const Node<T, AOS>& nd, const MS&
     }
     if (active && i >= 1) {
 #pragma unroll
-      for (int j = 0; j < NX; ++j) nd.at(Rec<M>::Ex2, j) = nd.at(Rec<M>::Mu, j) + rd * nd.at(Rec<M>::Z, j);
+      for (int j = 0; j < NX; ++j) nd.at(Rec<M>::Ex2, j) = S.mu(j) + rd * S.z(j);
     }
     __syncthreads();
   }
@@ -1376,9 +1424,12 @@ __device__ __forceinline__ void admm_iterations(const Node<T, AOS>& nd, const MS
                                 InstShared& sh, double* res, GroupShared* G, GroupX& X, const ProblemDev& P) {
   const T irg = T(1) / rg, ired = T(1) / (re + rd);
   typename WideOf<T>::type rp{}, rdl{};   // residual sums in the wide type (FP64 or double-float)
+  NodeStateFor<M, T, AOS> S;
+  if (active) S.load(nd);
   for (int it = 0; it + 1 < iters; ++it)
-    admm_iteration<M, T, AOS, REFINE, false, GROUP>(nd, MT, L, I, K, active, re, rd, rg, irg, ired, rp, rdl, G, X, P);
-  admm_iteration<M, T, AOS, REFINE, true, GROUP>(nd, MT, L, I, K, active, re, rd, rg, irg, ired, rp, rdl, G, X, P);
+    admm_iteration<M, T, AOS, REFINE, false, GROUP>(nd, MT, L, I, K, active, re, rd, rg, irg, ired, rp, rdl, G, X, P, S);
+  admm_iteration<M, T, AOS, REFINE, true, GROUP>(nd, MT, L, I, K, active, re, rd, rg, irg, ired, rp, rdl, G, X, P, S);
+  if (active) S.store(nd);
   // squared norms (the root is taken once, when they are reported)
   reduce_residuals(sh, rp, rdl, res);
 }
