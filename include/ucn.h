@@ -285,19 +285,24 @@ ucn_status ucn_df_check(int op, const double* a_d, const double* b_d, const doub
 #define UCN_NOALLOC_SCRATCH_BYTES (64ull << 20)
 
 /* ucn_scp_solve without any device allocation, for callers that cannot call
- * cudaMalloc (a real-time loop that must not allocate or synchronise, an
- * application whose memory pool owns the GPU, a runtime that only hands out
+ * cudaMalloc (a real-time loop that must not allocate or wait on the device,
+ * an application whose memory pool owns the GPU, a runtime that only hands out
  * pre-registered buffers).  The paper has no counterpart; this is a
  * deployment variant of the same fused kernel.
  *
  * desc: a host struct as for ucn_problem_create, except that `horizon` is a
  *   HOST array and every other array field is a DEVICE pointer (same layouts;
  *   owned by the caller, read during the kernel).  Device-side contents are
- *   not validated: n_obs[b] must lie in [0, max_obs] and dt[b] > 0.
- *   Quadrotor problems need n_obs even when max_obs = 0.
+ *   not validated: dt[b] must be > 0; obstacle counts n_obs[b] are clamped to
+ *   [0, max_obs] where the kernel reads them.  Quadrotor problems need n_obs
+ *   even when max_obs = 0.
  * Buffers: as ucn_scp_solve.  The kernel's scratch -- per-instance index
- *   tables and the final ADMM state -- lives in one static device array of
- *   UCN_NOALLOC_SCRATCH_BYTES (64 MiB) per GPU, held until the process exits.
+ *   tables, the penalty schedule and the final ADMM state -- lives in one
+ *   static device array of UCN_NOALLOC_SCRATCH_BYTES (64 MiB) per GPU, held
+ *   until the process exits.  The tables reach the device as by-value
+ *   parameters of small set-up kernels on `stream`: the call copies nothing
+ *   from host memory, allocates nothing (device or host) and does not wait for
+ *   the stream.
  * Errors: UCN_EINVAL when the batch needs more scratch than that, or when
  *   an instance does not fit in shared memory (there is no global workspace
  *   here), plus the descriptor checks of ucn_problem_create; UCN_ECUDA.
@@ -305,7 +310,8 @@ ucn_status ucn_df_check(int op, const double* a_d, const double* b_d, const doub
  *   that device current); make that first call before any stream capture.
  * Every call shares the array: calls whose kernels overlap on the GPU race,
  *   so serialise them (one stream, or events).  The array keeps the last
- *   call's contents; nothing in it needs to start at zero. */
+ *   call's contents; nothing in it needs to start at zero (each call writes
+ *   every table entry and exported state entry its kernels read). */
 ucn_status ucn_scp_solve_noalloc(const ucn_problem_desc* desc, const double* x0_d, const double* u0_d,
                                  double* x_out_d, double* u_out_d, ucn_scp_stats* stats_d,
                                  int* status_d, void* stream);

@@ -58,10 +58,13 @@ int default_tpn(int model, int nodes, int precision) {
   return 1;
 }
 
+double rho_factor(double rho_final, double rho_geo, int K, int k) {
+  return (rho_final > 0.0 && K > 1) ? std::pow(rho_final / rho_geo, (double)k / (double)(K - 1)) : 1.0;
+}
+
 std::vector<double> rho_schedule(double rho_final, double rho_geo, int K) {
   std::vector<double> fac(std::max(K, 1), 1.0);
-  if (rho_final > 0.0 && K > 1)
-    for (int k = 0; k < K; ++k) fac[k] = std::pow(rho_final / rho_geo, (double)k / (double)(K - 1));
+  for (int k = 0; k < (int)fac.size(); ++k) fac[k] = rho_factor(rho_final, rho_geo, K, k);
   return fac;
 }
 

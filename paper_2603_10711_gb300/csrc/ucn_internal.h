@@ -76,6 +76,8 @@ inline bool model_obstacles(int m) { return m == UCN_MODEL_QUAD12 || m == UCN_MO
 // (1 without a schedule), tabulated on the host so that no kernel evaluates
 // pow per iteration.
 std::vector<double> rho_schedule(double rho_final, double rho_geo, int K);
+// Entry k of that schedule.
+double rho_factor(double rho_final, double rho_geo, int K, int k);
 
 // The launchers of one model and precision.
 struct Launchers {

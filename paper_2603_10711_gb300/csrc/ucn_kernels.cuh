@@ -245,10 +245,19 @@ struct Inst {
   T prm[8];                 // model constants in T (Jacobian passes)
 };
 
+// Obstacles of instance b, clamped to [0, max_obs]: ucn_problem_create checks
+// the counts on the host, but the no-allocation entry point reads them from a
+// caller's device array it cannot check, and a count beyond max_obs would
+// index past the instance's obstacle and mirror slots.
+__device__ __forceinline__ int nobs_of(const ProblemDev& P, int b) {
+  const int v = P.nobs[b];
+  return v < 0 ? 0 : (v > P.max_obs ? P.max_obs : v);
+}
+
 template <class M, class T>
 __device__ __forceinline__ Inst<T> make_inst(const ProblemDev& P, int b) {
   Inst<T> I;
-  I.nobs = IsQuad<M>::value ? P.nobs[b] : 0;
+  I.nobs = IsQuad<M>::value ? nobs_of(P, b) : 0;
   const double tmin = IsQuad<M>::value ? 0.0 : P.sets[b * UCN_SET_PARAMS + 0];
   const double tmax = IsQuad<M>::value ? 0.0 : P.sets[b * UCN_SET_PARAMS + 1];
   const double tau = IsQuad<M>::value ? 0.0 : P.sets[b * UCN_SET_PARAMS + 2];
@@ -605,7 +614,7 @@ __device__ __forceinline__ DF wide_abs(DF a) { return a.hi < 0.0f ? df_neg(a) : 
 
 // A_i, B_i by forward-mode differentiation of the RK4 map (Eq. (2b)), in T.
 template <class M, class T, bool AOS, class MS>
-__device__ __forceinline__ void node_jacobians(const Node<T, AOS>& nd, const MS& MT, const T* prm, double h) {
+__device__ __forceinline__ void node_jacobians(const Node<T, AOS>& nd, const MS& MT, const T* prm, const Step3<T>& hs) {
   constexpr int NX = M::NX, NU = M::NU;
   typename Node<T, AOS>::W xb[NX], ub[NU];
   read_nominal<M, T, AOS>(nd, true, xb, ub);
@@ -614,7 +623,29 @@ __device__ __forceinline__ void node_jacobians(const Node<T, AOS>& nd, const MS&
   for (int j = 0; j < NX; ++j) xt[j] = wide_to<T>(xb[j]);
 #pragma unroll
   for (int j = 0; j < NU; ++j) ut[j] = wide_to<T>(ub[j]);
-  if constexpr (std::is_same<T, float>::value) {
+  if constexpr (std::is_same<M, Mars7>::value && std::is_same<MS, RegMatsS<M, T>>::value) {
+    // The structure of A (APattern<Mars7>), whose products read nothing else: the r
+    // columns are unit vectors, and a v_i column holds besides its unit entry
+    // d r_i / d v_i, which the RK4 weights of r' = v make h/6 (1 + 2 + 2 + 1) for every
+    // axis and nominal (the value a forward-mode pass along v_i computes, bit for bit).
+    // One pass along m and the thrust gives the rest: the m column of A, and B.
+    T cols[4][NX];
+    if constexpr (std::is_same<T, float>::value) {
+      rk4_jvpn<M, T, 4>(prm, hs, xt, ut, NX - 1, 1, cols);
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) rk4_jvp<M, T>(prm, hs, xt, ut, NX - 1 + q, cols[q]);
+    }
+    const T dh = hs.h6 * T(6);
+#pragma unroll
+    for (int r = 0; r < 3; ++r) MT.A(r, 3 + r) = dh;
+#pragma unroll
+    for (int r = 0; r < NX; ++r) {
+      MT.A(r, NX - 1) = cols[0][r];
+#pragma unroll
+      for (int c = 0; c < NU; ++c) MT.B(r, c) = cols[1 + c][r];
+    }
+  } else if constexpr (std::is_same<T, float>::value) {
     // FP32: five columns per pass (the value of the RK4 map once for the five),
     // the remainder one column per pass
     constexpr int KD = 5;
@@ -622,7 +653,7 @@ __device__ __forceinline__ void node_jacobians(const Node<T, AOS>& nd, const MS&
     for (int dir = 0; dir < NX + NU; dir += KD) {
       if (dir + KD <= NX + NU) {
         T cols[KD][NX];
-        rk4_jvpn<M, T, KD>(prm, h, xt, ut, dir, 1, cols);
+        rk4_jvpn<M, T, KD>(prm, hs, xt, ut, dir, 1, cols);
 #pragma unroll
         for (int q = 0; q < KD; ++q)
 #pragma unroll
@@ -634,7 +665,7 @@ __device__ __forceinline__ void node_jacobians(const Node<T, AOS>& nd, const MS&
 #pragma unroll
         for (int d1 = dir; d1 < NX + NU; ++d1) {
           T col[NX];
-          rk4_jvp<M, T>(prm, h, xt, ut, d1, col);
+          rk4_jvp<M, T>(prm, hs, xt, ut, d1, col);
 #pragma unroll
           for (int r = 0; r < NX; ++r) {
             if (d1 < NX) MT.A(r, d1) = col[r];
@@ -647,7 +678,7 @@ __device__ __forceinline__ void node_jacobians(const Node<T, AOS>& nd, const MS&
 #pragma unroll
     for (int dir = 0; dir < NX + NU; ++dir) {
       T col[NX];
-      rk4_jvp<M, T>(prm, h, xt, ut, dir, col);
+      rk4_jvp<M, T>(prm, hs, xt, ut, dir, col);
 #pragma unroll
       for (int r = 0; r < NX; ++r) {
         if (dir < NX) MT.A(r, dir) = col[r];
@@ -728,7 +759,7 @@ __device__ void node_setup(const Node<T, AOS>& nd, const Layout& L, const Proble
   if constexpr (IsQuad<M>::value) {
     // Obstacle j linearised about the nominal position: n = (p - c)/|p - c|,
     // keep n^T p >= n^T c + r; in deviations n^T dp >= n^T (c - pbar) + r.
-    const int no = P.nobs[b];
+    const int no = nobs_of(P, b);
     for (int j = 0; j < no; ++j) {
       const double* c = &P.obs_c[((long long)b * P.max_obs + j) * 3];
       // offset from the centre in T (|p - c| is of the order of the radius: no cancellation)
@@ -1485,7 +1516,7 @@ __device__ void node_export(const Node<T, AOS>& nd, const Layout& L, const Probl
   double* ni = pnus + (long long)i * L.MB * 3;
   for (int k = 0; k < L.MB * 3; ++k) { si[k] = 0.0; ni[k] = 0.0; }
   if constexpr (IsQuad<M>::value) {
-    for (int j = 0; j < P.nobs[b]; ++j) {
+    for (int j = 0; j < nobs_of(P, b); ++j) {
       double np = 0.0;
       for (int k = 0; k < 3; ++k) np += (double)nd.at(L.oMd, ObsStride<T>::value * j + k) * wide_to_double(nd.dat(Rec<M>::Xbar, k));
       si[3 * j] = (double)nd.at(L.oS, j) + np;
@@ -1563,7 +1594,7 @@ __device__ void node_import(const Node<T, AOS>& nd, const Layout& L, const Probl
   const double* si = ps + (long long)i * L.MB * 3;
   const double* ni = pnus + (long long)i * L.MB * 3;
   if constexpr (IsQuad<M>::value) {
-    for (int j = 0; j < P.nobs[b]; ++j) {
+    for (int j = 0; j < nobs_of(P, b); ++j) {
       double np = 0.0;
       for (int k = 0; k < 3; ++k) np += (double)nd.at(L.oMd, ObsStride<T>::value * j + k) * wide_to_double(nd.dat(Rec<M>::Xbar, k));
       nd.at(L.oS, j) = (T)(si[3 * j] - np);
@@ -1608,7 +1639,7 @@ __device__ void node_import(const Node<T, AOS>& nd, const Layout& L, const Probl
 template <class M, class T, bool AOS>
 __device__ void node_rebase_mirrors(const Node<T, AOS>& nd, const Layout& L, const ProblemDev& P, int b) {
   if constexpr (IsQuad<M>::value) {
-    for (int j = 0; j < P.nobs[b]; ++j) {
+    for (int j = 0; j < nobs_of(P, b); ++j) {
       T y = T(0);
       for (int k = 0; k < 3; ++k) y += nd.at(L.oMd, ObsStride<T>::value * j + k) * nd.at(Rec<M>::Xh, k);
       nd.at(L.oS, j) -= y;
@@ -1665,7 +1696,7 @@ __global__ void __launch_bounds__(128) linearize_kernel(ProblemDev P, const int*
   double Ad[NX * NX], Bd[NX * NU];
   for (int dir = 0; dir < NX + NU; ++dir) {
     T col[NX];
-    rk4_jvp<M, T>(prm, h, x, u, dir, col);
+    rk4_jvp<M, T>(prm, step_of<T>(h), x, u, dir, col);
     for (int r = 0; r < NX; ++r) {
       if (dir < NX) Ad[r * NX + dir] = (double)col[r];
       else Bd[r * NU + dir - NX] = (double)col[r];
@@ -2057,7 +2088,7 @@ __global__ void __launch_bounds__(MAX_THREADS) scp_kernel(ProblemDev P, Layout L
   const int i = nd.i, N = nd.N;
   const bool active = i <= N;
   const long long xo = P.xoff[b], uo = P.uoff[b];
-  const double h = P.dt[b];
+  const Step3<T> hs = step_of<T>(P.dt[b]);   // the RK4 step in T, once per launch
   const unsigned long long t0 = globaltimer_ns();
   const Inst<T> I = make_inst<M, T>(P, b);
   NodeConst<M, T> K;
@@ -2088,7 +2119,7 @@ __global__ void __launch_bounds__(MAX_THREADS) scp_kernel(ProblemDev P, Layout L
     const T re = rho_of<T>(sh, 0), rd = rho_of<T>(sh, 1), rg = rho_of<T>(sh, 2);
     const double radius = sh.radius;
     if (active) {
-      if (i < N) node_jacobians<M, T, AOS>(nd, MT, I.prm, h);
+      if (i < N) node_jacobians<M, T, AOS>(nd, MT, I.prm, hs);
       node_setup<M, T, AOS>(nd, L, P, I, b, radius, re, rg, K);
       const bool ok = node_factor<M, T, AOS, NN>(nd, MT, L, I, K, rd, rg);
       if (!ok) atomicOr(&sh.fail, 1);

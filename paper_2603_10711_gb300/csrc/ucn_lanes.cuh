@@ -100,7 +100,8 @@ struct LaneH<M, T, TPN, false> {
 
 // A_i, B_i (Eq. (2b)): the NN forward-mode directions split over the lanes.
 template <class M, class T, bool AOS, int TPN, class MS>
-__device__ __forceinline__ void lanes_jacobians(const Node<T, AOS>& nd, const MS& MT, const T* prm, double h, int q) {
+__device__ __forceinline__ void lanes_jacobians(const Node<T, AOS>& nd, const MS& MT, const T* prm, const Step3<T>& hs,
+                                                int q) {
   constexpr int NX = M::NX, NU = M::NU;
   typename Node<T, AOS>::W xb[NX], ub[NU];
   read_nominal<M, T, AOS>(nd, true, xb, ub);
@@ -114,8 +115,8 @@ __device__ __forceinline__ void lanes_jacobians(const Node<T, AOS>& nd, const MS
     for (int dir = q; dir < NX + NU; dir += 2 * TPN) {
       const int dir1 = dir + TPN;
       T cols[2][NX];
-      if (dir1 < NX + NU) rk4_jvpn<M, T, 2>(prm, h, xt, ut, dir, TPN, cols);
-      else rk4_jvp<M, T>(prm, h, xt, ut, dir, cols[0]);
+      if (dir1 < NX + NU) rk4_jvpn<M, T, 2>(prm, hs, xt, ut, dir, TPN, cols);
+      else rk4_jvp<M, T>(prm, hs, xt, ut, dir, cols[0]);
 #pragma unroll
       for (int r = 0; r < NX; ++r) {
         if (dir < NX) MT.A(r, dir) = cols[0][r];
@@ -129,7 +130,7 @@ __device__ __forceinline__ void lanes_jacobians(const Node<T, AOS>& nd, const MS
   } else {
     for (int dir = q; dir < NX + NU; dir += TPN) {
       T col[NX];
-      rk4_jvp<M, T>(prm, h, xt, ut, dir, col);
+      rk4_jvp<M, T>(prm, hs, xt, ut, dir, col);
 #pragma unroll
       for (int r = 0; r < NX; ++r) {
         if (dir < NX) MT.A(r, dir) = col[r];
@@ -557,7 +558,7 @@ __global__ void __launch_bounds__(LANES_MAX_THREADS) scp_kernel_lanes(ProblemDev
   const bool dact = id <= N;
   typedef typename Node<T, AOS>::W W;
   const long long xo = P.xoff[b], uo = P.uoff[b];
-  const double h = P.dt[b];
+  const Step3<T> hs = step_of<T>(P.dt[b]);   // the RK4 step in T, once per launch
   const unsigned long long t0 = globaltimer_ns();
   const Inst<T> I = make_inst<M, T>(P, b);
   NodeConst<M, T> K;
@@ -590,7 +591,7 @@ __global__ void __launch_bounds__(LANES_MAX_THREADS) scp_kernel_lanes(ProblemDev
     __syncthreads();
     const T re = rho_of<T>(sh, 0), rd = rho_of<T>(sh, 1), rg = rho_of<T>(sh, 2);
     const double radius = sh.radius;
-    if (active && i < N) lanes_jacobians<M, T, AOS, TPN>(nd, MT, I.prm, h, q);
+    if (active && i < N) lanes_jacobians<M, T, AOS, TPN>(nd, MT, I.prm, hs, q);
     if (active) lanes_consts<M, T, AOS, TPN>(nd, P, b, q, re, rg, kq, khd);
     __syncthreads();
     if (dact) {

@@ -336,16 +336,27 @@ __device__ __forceinline__ void rk4(const P* prm, double h_, const S* x, const S
   rk4h<M, S, P, R>(prm, (R)h_, (R)(0.5 * h_), (R)(h_ / 6.0), x, u, xn);
 }
 
+// The RK4 step h and its multiples h/2, h/6 in the arithmetic type R, rounded
+// once from the FP64 step (the values rk4 forms on every call).
+template <class R>
+struct Step3 {
+  R h, hh, h6;
+};
+template <class R>
+__device__ __forceinline__ Step3<R> step_of(double h) {
+  return {(R)h, (R)(0.5 * h), (R)(h / 6.0)};
+}
+
 // Column `dir` of [A B] = d RK4 / d(x, u) at (x, u), by one forward-mode pass.
 template <class M, class T, class X, class P>
-__device__ __forceinline__ void rk4_jvp(const P* prm, double h, const X* x, const X* u, int dir, T* col) {
+__device__ __forceinline__ void rk4_jvp(const P* prm, const Step3<T>& hs, const X* x, const X* u, int dir, T* col) {
   constexpr int NX = M::NX, NU = M::NU;
   Dual<T> xd[NX], ud[NU], out[NX];
 #pragma unroll
   for (int j = 0; j < NX; ++j) xd[j] = {(T)x[j], (T)(dir == j ? 1 : 0)};
 #pragma unroll
   for (int j = 0; j < NU; ++j) ud[j] = {(T)u[j], (T)(dir == NX + j ? 1 : 0)};
-  rk4<M, Dual<T>, P>(prm, h, xd, ud, out);
+  rk4h<M, Dual<T>, P, T>(prm, hs.h, hs.hh, hs.h6, xd, ud, out);
 #pragma unroll
   for (int j = 0; j < NX; ++j) col[j] = out[j].d;
 }
@@ -353,7 +364,7 @@ __device__ __forceinline__ void rk4_jvp(const P* prm, double h, const X* x, cons
 // Columns dir0, dir0 + stride, ..., dir0 + (K - 1) stride of [A B] in one
 // forward-mode pass (K tangents); cols[q] receives column dir0 + q stride.
 template <class M, class T, int K, class X, class P>
-__device__ __forceinline__ void rk4_jvpn(const P* prm, double h, const X* x, const X* u, int dir0, int stride,
+__device__ __forceinline__ void rk4_jvpn(const P* prm, const Step3<T>& hs, const X* x, const X* u, int dir0, int stride,
                                          T (*cols)[M::NX]) {
   constexpr int NX = M::NX, NU = M::NU;
   DualN<T, K> xd[NX], ud[NU], out[NX];
@@ -369,7 +380,7 @@ __device__ __forceinline__ void rk4_jvpn(const P* prm, double h, const X* x, con
 #pragma unroll
     for (int q = 0; q < K; ++q) ud[j].d[q] = (T)(dir0 + q * stride == NX + j ? 1 : 0);
   }
-  rk4<M, DualN<T, K>, P>(prm, h, xd, ud, out);
+  rk4h<M, DualN<T, K>, P, T>(prm, hs.h, hs.hh, hs.h6, xd, ud, out);
 #pragma unroll
   for (int j = 0; j < NX; ++j)
 #pragma unroll

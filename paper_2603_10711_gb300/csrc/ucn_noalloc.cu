@@ -13,7 +13,9 @@
 //
 // Limits and sharing.  The array (index tables, the penalty schedule, the
 // exported state) holds UCN_NOALLOC_SCRATCH_BYTES (64 MiB) on
-// every GPU that loads the library, until the process exits.  All calls share
+// every GPU that loads the library, until the process exits.  The tables reach
+// it through small set-up kernels that take them as by-value parameters, so
+// the call copies nothing from host memory and does not wait for the stream.  All calls share
 // it and it keeps the last call's contents; two calls whose kernels overlap on
 // the GPU (different streams, or different host threads on one device) race
 // on it.  Nothing in it has to start at zero: each call writes every table
@@ -25,7 +27,6 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
-#include <vector>
 
 #include "ucn_internal.h"
 #include "ucn_kernels.cuh"
@@ -67,6 +68,54 @@ cudaError_t scratch_address(int dev, void** out) {
   return cudaSuccess;
 }
 
+// The index tables and the penalty schedule reach the device as kernel
+// parameters (copied into the launch by value, 4 KB or less each), not by a
+// copy from host memory: a copy from pageable memory would make the call wait
+// for the stream.  Chunks of horizons, then one block turns them into the
+// per-instance offsets.
+constexpr int NA_HCHUNK = 960, NA_FCHUNK = 500;
+struct HorizonChunk { int n, off; int N[NA_HCHUNK]; };
+struct ScheduleChunk { int n, off; double f[NA_FCHUNK]; };
+
+__global__ void na_horizons_kernel(HorizonChunk c, int* N) {
+  for (int k = threadIdx.x; k < c.n; k += blockDim.x) N[c.off + k] = c.N[k];
+}
+__global__ void na_schedule_kernel(ScheduleChunk c, double* f) {
+  for (int k = threadIdx.x; k < c.n; k += blockDim.x) f[c.off + k] = c.f[k];
+}
+
+// xoff, uoff, soff of every instance (exclusive prefix sums of N + 1, N and
+// the exported-state size) by one block of NA_SCAN threads: each thread sums a
+// contiguous run of instances, the block scans the run totals, and each thread
+// writes its run's offsets.
+constexpr int NA_SCAN = 1024;
+__global__ void __launch_bounds__(NA_SCAN) na_offsets_kernel(int B, int nx, int nu, int mb, const int* N,
+                                                             long long* xoff, long long* uoff, long long* soff) {
+  __shared__ long long sx[NA_SCAN], su[NA_SCAN], ss[NA_SCAN];
+  const int t = threadIdx.x, per = (B + NA_SCAN - 1) / NA_SCAN;
+  const int lo = min(B, t * per), hi = min(B, lo + per);
+  long long ax = 0, au = 0, as = 0;
+  for (int b = lo; b < hi; ++b) {
+    const long long n = N[b];
+    ax += n + 1; au += n; as += 6 * (n + 1) * nx + 3 * n * nu + 2 * (n + 1) * mb * 3;
+  }
+  sx[t] = ax; su[t] = au; ss[t] = as;
+  __syncthreads();
+  for (int o = 1; o < NA_SCAN; o <<= 1) {   // inclusive Hillis-Steele scan
+    long long vx = 0, vu = 0, vs = 0;
+    if (t >= o) { vx = sx[t - o]; vu = su[t - o]; vs = ss[t - o]; }
+    __syncthreads();
+    sx[t] += vx; su[t] += vu; ss[t] += vs;
+    __syncthreads();
+  }
+  long long px = sx[t] - ax, pu = su[t] - au, ps = ss[t] - as;   // exclusive
+  for (int b = lo; b < hi; ++b) {
+    const long long n = N[b];
+    xoff[b] = px; uoff[b] = pu; soff[b] = ps;
+    px += n + 1; pu += n; ps += 6 * (n + 1) * nx + 3 * n * nu + 2 * (n + 1) * mb * 3;
+  }
+}
+
 }  // namespace
 
 extern "C" ucn_status ucn_scp_solve_noalloc(const ucn_problem_desc* d, const double* x0_d, const double* u0_d,
@@ -94,23 +143,18 @@ extern "C" ucn_status ucn_scp_solve_noalloc(const ucn_problem_desc* d, const dou
   if (d->scp_iters < 1 || d->admm_iters < 1) return nfail(UCN_EINVAL, "iteration counts must be >= 1");
   if (!(d->tr_init > 0 && d->tr_min > 0 && d->tr_max >= d->tr_min)) return nfail(UCN_EINVAL, "bad trust-region bounds");
   const int B = d->batch;
-  // index tables (host copy of the horizons -> offsets), then the exported state
-  std::vector<int> N(B);
-  std::vector<long long> xoff(B), uoff(B), soff(B);
   const int mb = obst ? max_obs : (d->model == UCN_MODEL_MARS14 ? 6 : 3);
-  long long tx = 0, tu = 0, ts = 0;
+  long long ts = 0;
   int Nmax = 0;
   for (int b = 0; b < B; ++b) {
-    const int n = d->horizon[b];
-    if (n < 1 || n + 1 > MAX_THREADS) return nfail(UCN_EINVAL, "horizon[%d] = %d outside [1, %d]", b, n, MAX_THREADS - 1);
-    N[b] = n; xoff[b] = tx; uoff[b] = tu; soff[b] = ts;
-    tx += n + 1; tu += n;
-    ts += 6LL * (n + 1) * NX + 3LL * n * NU + 2LL * (n + 1) * mb * 3;
-    Nmax = std::max(Nmax, n);
+    const long long n = d->horizon[b];
+    if (n < 1 || n + 1 > MAX_THREADS) return nfail(UCN_EINVAL, "horizon[%d] = %lld outside [1, %d]", b, n, MAX_THREADS - 1);
+    ts += 6 * (n + 1) * NX + 3 * n * NU + 2 * (n + 1) * mb * 3;
+    Nmax = std::max(Nmax, (int)n);
   }
-  const std::vector<double> fac = rho_schedule(d->rho_final, d->rho_geo, d->scp_iters);
+  const int K = d->scp_iters;
   const long long oN = 0, oX = up256(4LL * B), oU = oX + up256(8LL * B), oS = oU + up256(8LL * B);
-  const long long oF = oS + up256(8LL * B), oState = oF + up256(8LL * (long long)fac.size());
+  const long long oF = oS + up256(8LL * B), oState = oF + up256(8LL * K);
   const long long need = oState + 8LL * ts;
   if (need > (long long)UCN_NOALLOC_SCRATCH_BYTES)
     return nfail(UCN_EINVAL, "batch needs %lld bytes of scratch; the no-allocation entry point holds %llu",
@@ -128,13 +172,24 @@ extern "C" ucn_status ucn_scp_solve_noalloc(const ucn_problem_desc* d, const dou
   cudaError_t e = scratch_address(dev, (void**)&scr);
   if (e != cudaSuccess) return nfail(UCN_ECUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
   cudaStream_t st = (cudaStream_t)stream;
-  // the tables go in with stream-ordered copies from host memory (no allocation)
-  if ((e = cudaMemcpyAsync(scr + oN, N.data(), 4LL * B, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
-      (e = cudaMemcpyAsync(scr + oX, xoff.data(), 8LL * B, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
-      (e = cudaMemcpyAsync(scr + oU, uoff.data(), 8LL * B, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
-      (e = cudaMemcpyAsync(scr + oS, soff.data(), 8LL * B, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
-      (e = cudaMemcpyAsync(scr + oF, fac.data(), 8LL * fac.size(), cudaMemcpyHostToDevice, st)) != cudaSuccess)
-    return nfail(UCN_ECUDA, "table copy: %s", cudaGetErrorString(e));
+  // tables and schedule in by value (see na_horizons_kernel), offsets on the device
+  {
+    HorizonChunk hc;
+    for (int off = 0; off < B; off += NA_HCHUNK) {
+      hc.off = off; hc.n = std::min(NA_HCHUNK, B - off);
+      for (int k = 0; k < hc.n; ++k) hc.N[k] = d->horizon[off + k];
+      na_horizons_kernel<<<1, 256, 0, st>>>(hc, (int*)(scr + oN));
+    }
+    ScheduleChunk fc;
+    for (int off = 0; off < K; off += NA_FCHUNK) {
+      fc.off = off; fc.n = std::min(NA_FCHUNK, K - off);
+      for (int k = 0; k < fc.n; ++k) fc.f[k] = rho_factor(d->rho_final, d->rho_geo, K, off + k);
+      na_schedule_kernel<<<1, 256, 0, st>>>(fc, (double*)(scr + oF));
+    }
+    na_offsets_kernel<<<1, NA_SCAN, 0, st>>>(B, NX, NU, mb, (const int*)(scr + oN), (long long*)(scr + oX),
+                                            (long long*)(scr + oU), (long long*)(scr + oS));
+    if ((e = cudaGetLastError()) != cudaSuccess) return nfail(UCN_ECUDA, "table set-up launch: %s", cudaGetErrorString(e));
+  }
   ProblemDev P;
   std::memset(&P, 0, sizeof(P));
   P.model = d->model; P.nx = NX; P.nu = NU; P.batch = B; P.max_obs = max_obs;

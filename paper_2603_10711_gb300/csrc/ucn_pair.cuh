@@ -104,7 +104,7 @@ __device__ __forceinline__ float own_of(const float* v, int m, int q) {
 // the node has a control (else its rows are zero).
 template <class M>
 __device__ __forceinline__ void pair_jacobians(const Node<float, true>& nd, PairMats<M>& PM, const float* prm,
-                                               double h, int q, bool has_u) {
+                                               const Step3<float>& hs, int q, bool has_u) {
   constexpr int NX = M::NX, NU = M::NU, NN = NX + NU, RA = PairRows<M>::RA, KD = (NN + 1) / 2;
   float xt[NX], ut[NU];
 #pragma unroll
@@ -112,7 +112,7 @@ __device__ __forceinline__ void pair_jacobians(const Node<float, true>& nd, Pair
 #pragma unroll
   for (int j = 0; j < NU; ++j) ut[j] = has_u ? wide_to<float>(nd.dat(Rec<M>::Ubar, j)) : 1.0f;
   float cols[KD][NX];
-  rk4_jvpn<M, float, KD>(prm, h, xt, ut, q * KD, 1, cols);
+  rk4_jvpn<M, float, KD>(prm, hs, xt, ut, q * KD, 1, cols);
 #pragma unroll
   for (int m = 0; m < RA; ++m) {
 #pragma unroll
@@ -609,7 +609,7 @@ __global__ void __launch_bounds__(PAIR_MAX_THREADS, 2) scp_kernel_pair(ProblemDe
   const bool active = i <= N, has_u = active && i < N;
   const bool dact = ndd.i <= N;
   const long long xo = P.xoff[b], uo = P.uoff[b];
-  const double h = P.dt[b];
+  const Step3<float> hs = step_of<float>(P.dt[b]);   // the RK4 step in FP32, once per launch
   const unsigned long long t0 = globaltimer_ns();
   const Inst<float> I = make_inst<M, float>(P, b);
   NodeConst<M, float> Kd;   // node_setup's constants on the dense mapping (not used there)
@@ -644,7 +644,7 @@ __global__ void __launch_bounds__(PAIR_MAX_THREADS, 2) scp_kernel_pair(ProblemDe
     __syncthreads();
     const float re = sh.rhof[0], rd = sh.rhof[1], rg = sh.rhof[2];
     const double radius = sh.radius;
-    pair_jacobians<M>(nd, PM, I.prm, h, q, has_u);
+    pair_jacobians<M>(nd, PM, I.prm, hs, q, has_u);
     if (dact) {
       node_setup<M, float, true>(ndd, L, P, I, b, radius, re, rg, Kd);
       node_reseed<M, float, true>(ndd, L, I);

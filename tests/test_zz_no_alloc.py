@@ -83,3 +83,44 @@ def test_noalloc_rejects_batches_beyond_its_scratch():
     with pytest.raises(ucn.UcnError) as ei:
         ucn.ucn_scp_solve_noalloc(desc, x0, u0, x0.clone(), u0.clone(), stats, status)
     assert ei.value.status == ucn.UCN_EINVAL and "scratch" in str(ei.value)
+
+
+def noalloc_solve(prob, precision, desc=None, held=None):
+    if desc is None:
+        desc, held = device_desc(prob, precision)
+    x0 = torch.as_tensor(prob.xguess, device="cuda"); u0 = torch.as_tensor(prob.uguess, device="cuda")
+    xo = torch.full_like(x0, np.nan); uo = torch.full_like(u0, np.nan)
+    stats = torch.zeros(prob.batch * 128, dtype=torch.uint8, device="cuda")
+    status = torch.full((prob.batch,), -1, dtype=torch.int32, device="cuda")
+    ucn.ucn_scp_solve_noalloc(desc, x0, u0, xo, uo, stats, status)
+    torch.cuda.synchronize()
+    return xo.cpu().numpy(), uo.cpu().numpy(), np.frombuffer(stats.cpu().numpy().tobytes(), dtype=ucn.STATS_DTYPE)
+
+
+def test_noalloc_uneven_batch_over_several_table_chunks():
+    # 1000 uneven horizons: the horizons reach the device in two by-value chunks and the
+    # offsets come from the device-side scan with several instances per thread
+    prob = W.quad_box(1000, seed=8, N_range=(3, 24), obs_range=(0, 3), settings=dict(scp_iters=2, admm_iters=15, stop=0))
+    ref = ucn.Solver(prob, precision=ucn.UCN_PREC_FP64)
+    xr, ur = ref.scp_solve()
+    torch.cuda.synchronize()
+    xr, ur, sr = xr.cpu().numpy(), ur.cpu().numpy(), ref.stats_host()
+    ref.close()
+    xo, uo, st = noalloc_solve(prob, ucn.UCN_PREC_FP64)
+    assert rel_err(xo, xr) <= 1e-9 and rel_err(uo, ur) <= 1e-9
+    np.testing.assert_array_equal(st["scp_iters"], sr["scp_iters"])
+
+
+def test_noalloc_clamps_obstacle_counts_beyond_max_obs():
+    # a device n_obs above max_obs (which only the host-side create can reject) is read as
+    # max_obs: the solve ends and matches the same problem with n_obs = max_obs
+    prob = W.quad_path(2, seed=0, n_obs=5, settings=dict(scp_iters=4, admm_iters=40))
+    x5, u5, s5 = noalloc_solve(prob, ucn.UCN_PREC_FP64)
+    desc, held = device_desc(prob, ucn.UCN_PREC_FP64)
+    bad = torch.tensor([9, 64], dtype=torch.int32, device="cuda")
+    held.append(bad)
+    desc.n_obs = C.cast(C.c_void_p(bad.data_ptr()), C.POINTER(C.c_int))
+    x9, u9, s9 = noalloc_solve(prob, ucn.UCN_PREC_FP64, desc, held)
+    np.testing.assert_array_equal(x9, x5)
+    np.testing.assert_array_equal(u9, u5)
+    np.testing.assert_array_equal(s9["status"], s5["status"])
