@@ -351,10 +351,12 @@ def run_ours(args, rank, world):
 
 def run_serving(args):
     """Continuous batching of a mixed Poisson request stream (70% quadrotor,
-    30% Mars descent) in FP32, and the same stream's head solved one request at a
-    time in FP64 (the plain per-request path)."""
+    30% Mars descent) in FP32 at each arrival rate of --serving-rates (the
+    configuration's 2k-20k req/s), and the stream's head solved one request at
+    a time in FP64 (the plain per-request path).  Capacity = the largest
+    completed-solve rate; knee = the first rate at which the completed rate
+    falls below 90% of the arrival rate (the server saturates)."""
     from paper_2603_10711_gb300 import serving, ucn
-    stream = W.serving_stream(args.serving_requests, rate=args.serving_rate, seed=4)
     qs = W.quad_box(1).settings
     # Mars requests run up to N = 200: the batch's 60 x 40 schedule converges up to N = 150,
     # longer horizons need more ADMM iterations per SCP iteration (80 x 60 passes up to 200)
@@ -364,18 +366,26 @@ def run_serving(args):
         return {1: serving.Server(1, prec, max_slots=slots, max_horizon=120, max_obs=30, lanes=16, settings=qs),
                 2: serving.Server(2, prec, max_slots=slots, max_horizon=200, lanes=16, settings=ms)}
 
+    rates = [float(r) for r in args.serving_rates.split(",")]
     sv = servers(ucn.UCN_PREC_FP32_REFINE, 512)
-    serving.run_stream(stream[:32], sv)                # warm-up
-    fp32 = serving.run_stream(stream, sv)
+    serving.run_stream(W.serving_stream(32, rate=rates[0], seed=4), sv)                # warm-up
+    sweep = []
+    for rate in rates:
+        stream = W.serving_stream(args.serving_requests, rate=rate, seed=4)
+        r = serving.run_stream(stream, sv)
+        sweep.append(dict(r, arrival_rate_per_s=rate, requests=len(stream)))
     for s in sv.values():
         s.close()
+    knee = next((r["arrival_rate_per_s"] for r in sweep if r["solves_per_s"] < 0.9 * r["arrival_rate_per_s"]), None)
+    stream = W.serving_stream(args.serving_requests, rate=rates[0], seed=4)
     sv = servers(ucn.UCN_PREC_FP64, 4)
     n64 = min(len(stream), args.serving_fp64_requests)
     fp64 = serving.run_stream([(0.0, p) for _, p in stream[:n64]], sv, max_inflight=1)
     for s in sv.values():
         s.close()
-    return {"arrival_rate_per_s": args.serving_rate, "requests": len(stream), "mix": "70% quad N 30-120 / 30% Mars N 50-200",
-            "fp32_continuous": fp32, "fp64_per_request": dict(fp64, requests=n64),
+    return {"mix": "70% quad N 30-120, 5-30 obstacles / 30% Mars N 50-200", "fp32_continuous": sweep,
+            "capacity_solves_per_s": max(r["solves_per_s"] for r in sweep), "knee_arrival_rate_per_s": knee,
+            "fp64_per_request": dict(fp64, requests=n64),
             "latency": "arrival -> result collected (host clock)"}
 
 
@@ -574,7 +584,7 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=128, help="instances per step of the reference (oracle) arm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=2000, help="requests of the serving stream (0: skip)")
-    ap.add_argument("--serving-rate", type=float, default=2000.0, help="Poisson arrival rate of the serving stream")
+    ap.add_argument("--serving-rates", default="2000,5000,10000,20000", help="Poisson arrival rates of the serving sweep")
     ap.add_argument("--serving-fp64-requests", type=int, default=16)
     ap.add_argument("--batching-batch", type=int, default=4096, help="uneven quadrotor batch (0: skip the section)")
     ap.add_argument("--rho-study-batch", type=int, default=256, help="quaternion study tasks per setting (0: skip)")
@@ -582,7 +592,7 @@ def main():
     ap.add_argument("--scenario-count", type=int, default=64, help="scenarios per problem (group size)")
     ap.add_argument("--scenario-steps", type=int, default=3, help="receding-horizon steps (0: skip the section)")
     ap.add_argument("--scenario-fp64-problems", type=int, default=64)
-    ap.add_argument("--mode", default="full", choices=["full", "kernel", "scenario", "batching", "rho_study"],
+    ap.add_argument("--mode", default="full", choices=["full", "kernel", "scenario", "batching", "rho_study", "serving"],
                     help="kernel: time only the fused kernel (profiler captures)")
     ap.add_argument("--scp-iters", type=int, default=0, help="fixed SCP iteration count (0: the workload's cap + stop test)")
     ap.add_argument("--admm-iters", type=int, default=0, help="kernel mode: ADMM iterations per SCP iteration (0: the workload's)")
@@ -605,6 +615,8 @@ def main():
         out = run_batching(args)
     elif args.mode == "rho_study":
         out = run_rho_study(args)
+    elif args.mode == "serving":
+        out = run_serving(args)
     elif args.impl == "reference":
         out = run_reference(args, rank, world)
     else:

@@ -233,6 +233,22 @@ ucn_status ucn_scp_solve(ucn_problem* prob, const double* x0_d, const double* u0
                          double* x_out_d, double* u_out_d, ucn_scp_stats* stats_d,
                          int* status_d, void* stream);
 
+/* ucn_scp_solve started from a kept ADMM state instead of the cold start
+ * (Sec. III-B: the inner ADMM solves are warm-started; here across solves, as
+ * a server or a receding-horizon loop keeps the state of a finished solve).
+ * state_d [ucn_state_size]: the absolute FP64 layout of ucn_state_export (for
+ * instance b, the state of a solve of the same horizon -- typically exported
+ * by an earlier solve of this or a nearby problem); each instance's variables
+ * are taken relative to its guess (x0_d, u0_d), its mirror sets are
+ * re-projected with the first SCP iteration's sets, as every later iteration
+ * does, and with a penalty schedule (rho_final > 0) every SCP iteration uses
+ * the schedule's final penalties, at which the kept state was computed.  Asynchronous on `stream`: state_d is copied into the problem's state
+ * buffer first (it may be that buffer, as after ucn_state_export into it).
+ * Errors: UCN_EINVAL (null pointer, scenario groups), UCN_ECUDA. */
+ucn_status ucn_scp_solve_warm(ucn_problem* prob, const double* x0_d, const double* u0_d, const double* state_d,
+                              double* x_out_d, double* u_out_d, ucn_scp_stats* stats_d, int* status_d,
+                              void* stream);
+
 /* Receding-horizon step for MPC (Sec. IV-A: the common first control is
  * executed after each solve and the next solve starts from the previous tube
  * moved one step ahead).
@@ -321,14 +337,17 @@ ucn_status ucn_scp_solve_noalloc(const ucn_problem_desc* desc, const double* x0_
  * paper; the serving layer around the method).  ucn_serve_create allocates
  * everything for `max_slots` instances of up to `max_horizon` nodes of one
  * model and precision, plus `lanes` CUDA streams and a ring of `kept`
- * finished trajectories (0: 2 * max_slots) for warm starts.  A request is
- * admitted into a free slot while the sum of admitted footprints stays within
- * hbm_budget_bytes (0: no budget beyond the slots); each pump launches the
- * fused SCP kernel (one CTA per instance) over the slots admitted since the
- * last pump on the next free lane, while earlier launches keep running; a
- * non-blocking poll returns a finished result and frees its slot.  Every slot
- * has the same CTA size and layout, so a result does not depend on what it was
- * batched with.  Solver settings have the meaning they have in ucn_problem_desc. */
+ * finished results (0: 2 * max_slots) -- trajectory and final ADMM state --
+ * for warm starts.  A request is admitted into a free slot while the sum of
+ * admitted footprints stays within hbm_budget_bytes (0: no budget beyond the
+ * slots); each pump launches the fused SCP kernel (one CTA per instance) over
+ * the slots admitted since the last pump (at most 128) on the next free lane,
+ * while earlier launches keep running: the requests' data go up in one copy
+ * and a scatter kernel places them.  Each CTA writes its request's result into
+ * mapped host memory the moment its solve ends, so a result is ready when its
+ * own solve is done, and polls read host memory only.  Every slot has the same
+ * CTA size and layout, so a result does not depend on what it was batched with.
+ * Solver settings have the meaning they have in ucn_problem_desc. */
 typedef struct {
   int model, precision, max_slots, max_horizon, max_obs, lanes, kept;
   double hbm_budget_bytes;
@@ -340,8 +359,10 @@ typedef struct {
 /* One solve request (host memory, copied at submit).  Arrays as one instance
  * of ucn_problem_desc (model_params [8], sets [UCN_SET_PARAMS], obs_c [n_obs][3]).  The
  * initial guess is x_guess [(horizon+1)][nx], u_guess [horizon][nu]; if either
- * is NULL the guess is the kept trajectory of the finished request
- * `warm_ticket` (same horizon), copied on the device. */
+ * is NULL the request starts from the kept result of the request `warm_ticket`
+ * (same horizon; launched, finished or not): its trajectory as the guess and its
+ * final ADMM state as the start of the inner solves, as ucn_scp_solve_warm does
+ * (copied on the device; the launch waits for that request's launch). */
 typedef struct {
   int horizon, n_obs;
   double dt;
@@ -375,10 +396,17 @@ ucn_status ucn_serve_submit(ucn_server* srv, const ucn_request* req, unsigned lo
 /* Launches every admitted slot on a free lane (stream); *launched = their
  * count (0 when nothing was admitted).  UCN_EBUSY when every lane is busy. */
 ucn_status ucn_serve_pump(ucn_server* srv, int* launched);
-/* Non-blocking: UCN_OK and the result (the slot is freed and the trajectory
- * kept for warm starts), UCN_EBUSY while the request is queued or running,
- * UCN_EINVAL for an unknown ticket, UCN_ECUDA if its launch failed. */
+/* Non-blocking (reads host memory; no CUDA call unless the request is still
+ * running): UCN_OK and the result (the slot is freed, for reuse once its
+ * launch has ended; the result stays kept for warm starts until the ring
+ * reuses its entry), UCN_EBUSY while the request
+ * is queued or running, UCN_EINVAL for an unknown ticket, UCN_ECUDA if its
+ * launch failed. */
 ucn_status ucn_serve_poll(ucn_server* srv, unsigned long long ticket, ucn_result* res);
+/* Non-blocking: UCN_OK and the result of some finished request (res->ticket
+ * says which; res->x, res->u, when not NULL, must hold max_horizon nodes),
+ * UCN_EBUSY when none has finished, UCN_ECUDA if a launch failed. */
+ucn_status ucn_serve_poll_any(ucn_server* srv, ucn_result* res);
 /* Free slots right now (-1 for a NULL server). */
 int ucn_serve_free_slots(ucn_server* srv);
 

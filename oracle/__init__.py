@@ -81,6 +81,7 @@ def lib():
             _lib.orc_project.argtypes = [C.c_int, C.c_int, C.c_double, _dp, _dp]
             _lib.orc_scp_solve_iters.restype = C.c_int
             _lib.orc_traj_defects.restype = C.c_int
+            _lib.orc_scp_solve_warm.restype = C.c_int
         return _lib
 
 
@@ -260,6 +261,21 @@ def scp_solve_iters(prob, run_iters, nthreads: int = 0, xguess=None, uguess=None
     assert ri.shape == (prob.batch,)
     lib().orc_scp_solve_iters(C.byref(pin.c), _d(xg), _d(ug), _d(xo), _d(uo), _d(st),
                               ri.ctypes.data_as(_ip), C.c_int(nthreads))
+    return xo, uo, st
+
+
+def scp_solve_warm(prob, state, nthreads: int = 0, xguess=None, uguess=None):
+    """SCP solve of independent instances started from the ADMM ``state`` (the
+    instances' flat absolute states, one after the other) instead of the cold
+    start.  Returns (x, u, stats[B,16])."""
+    pin = _Pinned(prob)
+    xg = _f64(prob.xguess if xguess is None else xguess)
+    ug = _f64(prob.uguess if uguess is None else uguess)
+    xo = np.zeros_like(xg); uo = np.zeros_like(ug)
+    st = np.zeros((prob.batch, NSTAT))
+    if lib().orc_scp_solve_warm(C.byref(pin.c), _d(xg), _d(ug), _d(_f64(state)), _d(xo), _d(uo), _d(st),
+                                C.c_int(nthreads)) != 0:
+        raise ValueError("scenario groups start cold")
     return xo, uo, st
 
 

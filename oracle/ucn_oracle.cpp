@@ -1146,8 +1146,16 @@ enum { NLOG = 8 };
 // the stop test -- the trajectory after a given iteration count, for comparing
 // solves whose stop tests landed on opposite sides of defect_tol.  The penalty
 // schedule stays that of the scp_iters cap.
+//
+// state0 (not NULL): the solve starts from that ADMM state (the flat absolute
+// layout of orc_state_size) instead of the cold start -- a warm start from kept
+// ADMM state (Sec. III-B warm-starts the inner solves); its mirrors are
+// re-projected with the first QP's sets, as every later iteration does, and
+// the penalties stay at the schedule's final value, at which a kept state was
+// computed (the schedule of Sec. IV-A rises over a solve from a cold start).
 void scp_instance(const OrcProblem& P, int b, const double* xg, const double* ug,
-                  double* xout, double* uout, double* stat, double* log, int run_iters = 0) {
+                  double* xout, double* uout, double* stat, double* log, int run_iters = 0,
+                  const double* state0 = nullptr) {
   const int N = P.N[b], nx = P.nx, nu = P.nu;
   const double* prm = P.params + b * 8;
   const double h = P.dt[b];
@@ -1161,16 +1169,22 @@ void scp_instance(const OrcProblem& P, int b, const double* xg, const double* ug
   const int K = P.scp_iters;
   for (int k = 0; k < K; ++k) {
     if (run_iters > 0 && k >= run_iters) break;
+    // a warm start continues at the schedule's final penalty (its state was computed there)
+    const int ks = state0 ? K - 1 : k;
     double fac = 1.0;
-    if (P.rho_final > 0.0 && K > 1) fac = std::pow(P.rho_final / P.rho_geo, (double)k / (K - 1));
+    if (P.rho_final > 0.0 && K > 1) fac = std::pow(P.rho_final / P.rho_geo, (double)ks / (K - 1));
     const double re = P.rho_eq * fac, rd = P.rho_dyn * fac, rg = P.rho_geo * fac;
     for (int i = 0; i < N; ++i)
       orc_linearize(P.model, prm, h, &xbar[i * nx], &ubar[i * nu], &A[i * nx * nx], &B[i * nx * nu],
                     &d[i * nx], &fnom[i * nx]);
     QP qp;
     build_qp(P, b, xbar.data(), ubar.data(), A.data(), B.data(), d.data(), radius, re, rd, rg, qp);
-    if (k == 0) init_state(qp, xbar.data(), ubar.data(), st);
-    else reseed_mirrors(qp, st);
+    if (k == 0 && !state0) {
+      init_state(qp, xbar.data(), ubar.data(), st);
+    } else {
+      if (k == 0) { st.alloc(qp.N, qp.nx, qp.nu, qp.maxblk); st.from_flat(state0); }
+      reseed_mirrors(qp, st);
+    }
     as = admm_run(qp, st, P.admm_iters);
     ++iters_run;
     if (!as.ok) { status = ST_NUMERIC; break; }
@@ -1428,6 +1442,26 @@ int orc_scp_solve_iters(const OrcProblem* P, const double* xg, const double* ug,
     const long long xo = P->xoff[b], uo = P->uoff[b];
     scp_instance(*P, b, xg + xo * P->nx, ug + uo * P->nu, xout + xo * P->nx, uout + uo * P->nu, stat, nullptr,
                  run_iters[b]);
+  }
+  return 0;
+}
+
+// Independent instances solved from given ADMM states (state_all: each
+// instance's flat state, instances one after the other in batch order).
+int orc_scp_solve_warm(const OrcProblem* P, const double* xg, const double* ug, const double* state_all,
+                       double* xout, double* uout, double* stat, int nthreads) {
+  if (P->group > 1) return 1;
+  std::vector<long long> so(P->batch + 1, 0);
+  const int mb = P->model == 1 || P->model == 3 ? P->max_obs : (P->model == 4 ? 6 : 3);
+  for (int b = 0; b < P->batch; ++b) so[b + 1] = so[b] + orc_state_size(P->N[b], P->nx, P->nu, mb);
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+  for (int b = 0; b < P->batch; ++b) {
+    const long long xo = P->xoff[b], uo = P->uoff[b];
+    scp_instance(*P, b, xg + xo * P->nx, ug + uo * P->nu, xout + xo * P->nx, uout + uo * P->nu, stat, nullptr, 0,
+                 state_all + so[b]);
   }
   return 0;
 }

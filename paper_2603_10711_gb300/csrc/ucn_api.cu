@@ -138,6 +138,7 @@ struct ucn_problem {
   int group, gcsize;     // scenarios per group, CTAs per thread-block cluster
   int tpn;               // threads per node of the fused solve
   int optin;             // shared memory per CTA the device allows
+  unsigned char* warm_ones;   // batch flags, all 1: every instance starts from the given state
 };
 
 namespace {
@@ -318,6 +319,9 @@ ucn_status ucn_problem_create(const ucn_problem_desc* d, ucn_problem** out) {
   COPY(facd, fac.data(), fac.size());
   double* sabs = nullptr;
   COPY(sabs, (const double*)nullptr, (size_t)ts);
+  const std::vector<unsigned char> ones(B, 1);
+  unsigned char* wones = nullptr;
+  COPY(wones, ones.data(), B);
 #undef COPY
   if (s != UCN_OK) { ucn_problem_destroy(p); return s; }
   P.N = Ndev; P.xoff = xo; P.uoff = uo; P.soff = so; P.dt = dtd; P.params = prm;
@@ -331,6 +335,7 @@ ucn_status ucn_problem_create(const ucn_problem_desc* d, ucn_problem** out) {
   P.timeout_ns = (unsigned long long)((d->timeout_s > 0 ? d->timeout_s : 60.0) * 1e9);
   P.state_abs = sabs;
   P.order = ord;
+  p->warm_ones = wones;
   P.rho_fac = facd;
   P.group = group;
   // a group is gclusters thread-block clusters of gcsize CTAs: the largest
@@ -510,6 +515,27 @@ ucn_status ucn_scp_solve(ucn_problem* p, const double* x0_d, const double* u0_d,
     if (e != cudaSuccess) return fail(UCN_ECUDA, "scp group launch: %s", cudaGetErrorString(e));
     return UCN_OK;
   }
+  auto fn = launchers_for(p->model, p->precision).scp;
+  const cudaError_t e = fn(c, x0_d, u0_d, x_out_d, u_out_d, stats_d, status_d);
+  if (e != cudaSuccess) return fail(UCN_ECUDA, "scp launch: %s", cudaGetErrorString(e));
+  return UCN_OK;
+}
+
+ucn_status ucn_scp_solve_warm(ucn_problem* p, const double* x0_d, const double* u0_d, const double* state_d,
+                              double* x_out_d, double* u_out_d, ucn_scp_stats* stats_d, int* status_d, void* stream) {
+  g_err[0] = 0;
+  if (!p || !x0_d || !u0_d || !state_d || !x_out_d || !u_out_d || !stats_d || !status_d)
+    return fail(UCN_EINVAL, "null argument");
+  if (p->group > 1) return fail(UCN_EINVAL, "scenario groups start cold (warm-start them through their guesses)");
+  if (state_d != p->dev.state_abs) {
+    const cudaError_t e = cudaMemcpyAsync(p->dev.state_abs, state_d, (size_t)p->state_size * sizeof(double),
+                                          cudaMemcpyDeviceToDevice, as_stream(stream));
+    if (e != cudaSuccess) return fail(UCN_ECUDA, "state copy: %s", cudaGetErrorString(e));
+  }
+  ProblemDev Pw = p->dev;
+  Pw.warm = p->warm_ones;
+  LaunchCfg c = cfg_of(p, stream);
+  c.P = &Pw;
   auto fn = launchers_for(p->model, p->precision).scp;
   const cudaError_t e = fn(c, x0_d, u0_d, x_out_d, u_out_d, stats_d, status_d);
   if (e != cudaSuccess) return fail(UCN_ECUDA, "scp launch: %s", cudaGetErrorString(e));

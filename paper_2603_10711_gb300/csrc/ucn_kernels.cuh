@@ -48,7 +48,38 @@ struct ProblemDev {
   double* gx;              // exchange slots of the scenarios [instance][2][16]
   unsigned* gflag;         // per instance: last exchange published (+1); zeroed per launch
   unsigned long long gwait_ns;   // bound on a wait for another scenario of the group
+  const unsigned char* warm;     // per instance: 1 = start from the ADMM state in state_abs (NULL: all cold)
+  // Result delivery to mapped host memory (serving; NULL: none): at its end each
+  // CTA copies its instance's stats (16 doubles), x and u into res_host[b]
+  // (res_stride doubles per instance), then sets res_flag[b] = res_tag[b].
+  double* res_host;
+  unsigned long long* res_flag;
+  const unsigned long long* res_tag;
+  long long res_stride;
 };
+
+// The end of a fused solve with result delivery: every thread copies its share
+// of the instance's x and u (just written to xout, uout by this CTA) into the
+// mapped host record and fences them system-wide, then one thread copies the
+// stats record, fences, and publishes the instance's tag in its flag -- the
+// host sees the flag only after the record.  No thread waits on the host.
+__device__ __forceinline__ void deliver_result(const ProblemDev& P, int b, const double* xout, const double* uout,
+                                               const ucn_scp_stats* stats) {
+  if (!P.res_host) return;
+  const int N = P.N[b], nx = P.nx, nu = P.nu;
+  const long long xo = P.xoff[b], uo = P.uoff[b];
+  double* r = P.res_host + (long long)b * P.res_stride;
+  for (int e = threadIdx.x; e < (N + 1) * nx; e += blockDim.x) r[16 + e] = xout[xo * nx + e];
+  for (int e = threadIdx.x; e < N * nu; e += blockDim.x) r[16 + (N + 1) * nx + e] = uout[uo * nu + e];
+  __threadfence_system();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const double* sd = reinterpret_cast<const double*>(stats + b);
+    for (int e = 0; e < 16; ++e) r[e] = sd[e];
+    __threadfence_system();
+    *(volatile unsigned long long*)(P.res_flag + b) = P.res_tag[b];
+  }
+}
 
 // Fixed part of a node record: compile-time element offsets of every per-node
 // array.  The mirror arrays (whose length depends on the obstacle count) follow
@@ -1483,6 +1514,17 @@ __device__ void node_cold_start(const Node<T, AOS>& nd, const Layout& L) {
   for (int j = 0; j < L.MS; ++j) { nd.at(L.oS, j) = T(0); nd.at(L.oNus, j) = T(0); }
 }
 
+// The ADMM state a solve starts from: cold (x = x-hat = z = nominal, zero
+// duals), or -- warm[b] -- the absolute state in state_abs (a kept state of an
+// earlier solve), taken relative to this solve's nominal.
+template <class M, class T, bool AOS>
+__device__ void node_import(const Node<T, AOS>& nd, const Layout& L, const ProblemDev& P, int b, const double* in);
+template <class M, class T, bool AOS>
+__device__ __forceinline__ void node_start(const Node<T, AOS>& nd, const Layout& L, const ProblemDev& P, int b) {
+  if (P.warm && P.warm[b]) node_import<M, T, AOS>(nd, L, P, b, P.state_abs + P.soff[b]);
+  else node_cold_start<M, T, AOS>(nd, L);
+}
+
 // ------------------------------------------------------------------ absolute state in/out
 // Flat per-instance order: x, u, z, lam, mu, xh, uh, nux, nuu, s[(N+1)][MB][3], nus[...].
 template <class M, class T, bool AOS>
@@ -2101,7 +2143,7 @@ __global__ void __launch_bounds__(MAX_THREADS) scp_kernel(ProblemDev P, Layout L
   if (active) load_nominal<M, T, AOS>(nd, L, x0, u0, xo, uo);
   __syncthreads();
   scp_start<M, T, AOS>(nd, P, I, b, active, sh);
-  if (active) node_cold_start<M, T, AOS>(nd, L);
+  if (active) node_start<M, T, AOS>(nd, L, P, b);
   __syncthreads();
   int accepted = 0, iters_run = 0;
   unsigned long long mask = 0ull;
@@ -2110,8 +2152,11 @@ __global__ void __launch_bounds__(MAX_THREADS) scp_kernel(ProblemDev P, Layout L
   for (int k = 0; k < Kscp; ++k) {
     if (threadIdx.x == 0) {
       double f = 1.0;
-      if (P.rho_fac) f = P.rho_fac[k];   // the schedule tabulated at create
-      else if (P.rho_final > 0.0 && Kscp > 1) f = pow(P.rho_final / P.rho_geo, (double)k / (double)(Kscp - 1));
+      // the schedule tabulated at create; a warm start continues at its final penalty,
+      // the one its kept ADMM state was computed at
+      const int ks = (P.warm && P.warm[b]) ? Kscp - 1 : k;
+      if (P.rho_fac) f = P.rho_fac[ks];
+      else if (P.rho_final > 0.0 && Kscp > 1) f = pow(P.rho_final / P.rho_geo, (double)ks / (double)(Kscp - 1));
       sh.rho[0] = P.rho_eq * f; sh.rho[1] = P.rho_dyn * f; sh.rho[2] = P.rho_geo * f;
       for (int r = 0; r < 3; ++r) sh.rhof[r] = (float)sh.rho[r];
     }
@@ -2175,6 +2220,8 @@ __global__ void __launch_bounds__(MAX_THREADS) scp_kernel(ProblemDev P, Layout L
     if constexpr (GROUP) gfail = G->gfail;   // the group lost its consensus partner
     scp_report(sh, P, b, w, res, last_step, iters_run, accepted, mask, t0, gfail, stats, status_out);
   }
+  __syncthreads();
+  deliver_result(P, b, xout, uout, stats);
   if constexpr (GROUP) group_finish(P);
 }
 

@@ -574,7 +574,7 @@ __global__ void __launch_bounds__(LANES_MAX_THREADS) scp_kernel_lanes(ProblemDev
   if (dact) load_nominal<M, T, AOS>(ndd, L, x0, u0, xo, uo);
   __syncthreads();
   scp_start<M, T, AOS>(ndd, P, I, b, dact, sh);
-  if (dact) node_cold_start<M, T, AOS>(ndd, L);
+  if (dact) node_start<M, T, AOS>(ndd, L, P, b);
   __syncthreads();
   int accepted = 0, iters_run = 0;
   unsigned long long mask = 0ull;
@@ -583,8 +583,11 @@ __global__ void __launch_bounds__(LANES_MAX_THREADS) scp_kernel_lanes(ProblemDev
   for (int k = 0; k < Kscp; ++k) {
     if (threadIdx.x == 0) {
       double f = 1.0;
-      if (P.rho_fac) f = P.rho_fac[k];   // the schedule tabulated at create
-      else if (P.rho_final > 0.0 && Kscp > 1) f = pow(P.rho_final / P.rho_geo, (double)k / (double)(Kscp - 1));
+      // the schedule tabulated at create; a warm start continues at its final penalty,
+      // the one its kept ADMM state was computed at
+      const int ks = (P.warm && P.warm[b]) ? Kscp - 1 : k;
+      if (P.rho_fac) f = P.rho_fac[ks];
+      else if (P.rho_final > 0.0 && Kscp > 1) f = pow(P.rho_final / P.rho_geo, (double)ks / (double)(Kscp - 1));
       sh.rho[0] = P.rho_eq * f; sh.rho[1] = P.rho_dyn * f; sh.rho[2] = P.rho_geo * f;
       for (int r = 0; r < 3; ++r) sh.rhof[r] = (float)sh.rho[r];
     }
@@ -651,6 +654,8 @@ __global__ void __launch_bounds__(LANES_MAX_THREADS) scp_kernel_lanes(ProblemDev
     if constexpr (GROUP) gfail = G->gfail;   // the group lost its consensus partner
     scp_report(sh, P, b, w, res, last_step, iters_run, accepted, mask, t0, gfail, stats, status_out);
   }
+  __syncthreads();
+  deliver_result(P, b, xout, uout, stats);
   if constexpr (GROUP) group_finish(P);
 }
 

@@ -2,18 +2,29 @@
 //
 // All device memory is allocated once by ucn_serve_create, for `max_slots`
 // instances of up to `max_horizon` nodes (problem data, guesses, outputs,
-// exported state, workspace) plus a ring of kept trajectories for warm
-// starts.  Requests are admitted into free slots while their HBM footprint
-// fits the budget; every pump launches the fused SCP kernel over the slots
-// admitted since the last pump, on the next free lane (a CUDA stream), while
-// earlier launches keep running on the other lanes.  A finished request is
-// collected by a non-blocking poll, which frees its slot for the next arrival.
-// Each instance's solve is independent of the others in its launch (one CTA
-// per instance, same CTA size and layout for every slot), so a result does
-// not depend on what it was batched with.
+// exported ADMM state, workspace) plus a ring of kept results -- trajectory
+// and final ADMM state -- for warm starts.  Requests are admitted into free
+// slots while their HBM footprint fits the budget; every pump launches the
+// fused SCP kernel over the slots admitted since the last pump, on the next
+// free lane (a CUDA stream), while earlier launches keep running on the other
+// lanes.  Each instance's solve is independent of the others in its launch
+// (one CTA per instance, same CTA size and layout for every slot), so a result
+// does not depend on what it was batched with.
+//
+// Data movement of a launch, all on its lane's stream: the admitted requests'
+// records (problem data and guesses) go up in ONE copy from a pinned staging
+// buffer and a scatter kernel writes them into the slot arrays (a warm request
+// instead takes its guess and ADMM state from the ring entry of the request it
+// names).  Each CTA of the solve writes its own result (stats, x, u) into its
+// slot's record in mapped host memory the moment its instance is done and then
+// raises the slot's flag (deliver_result), so a request's result is available
+// when ITS solve ends, not when the launch's slowest one does; after the solve
+// a keep kernel copies the launch's trajectories and final ADMM states into the
+// ring.  ucn_serve_poll and ucn_serve_poll_any read host memory only.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -38,50 +49,156 @@ ucn_status sfail(ucn_status s, const char* fmt, ...) {
   return s;
 }
 
-enum { SLOT_FREE = 0, SLOT_ADMITTED = 1, SLOT_RUNNING = 2 };
+// A slot is FREE, ADMITTED (waiting for a pump), RUNNING (launched), or
+// DRAINING: its result was taken but its launch's keep kernel may still read
+// its device arrays, so it is not reused before that launch ends.
+enum { SLOT_FREE = 0, SLOT_ADMITTED = 1, SLOT_RUNNING = 2, SLOT_DRAINING = 3 };
+
+// Requests per launch (bounds the pinned staging of a lane).
+constexpr int LAUNCH_CAP = 128;
+
+// Offsets (in doubles) of one request record: slot, ring entry to read (warm
+// start; -1: none), ring entry to fill (-1: none), the request's ticket (its
+// delivery tag), horizon, obstacle count, the problem data of one instance,
+// then the guesses.  Integers and bytes are stored as doubles (exact; tickets
+// below 2^53).
+struct RecLayout {
+  int K, RING, RINGW, TAG, N, NOBS, DT, PRM, QD, XR, RD, UR, QND, QN, XLO, XHI, ULO, UHI, XI, XT, TM, OC, OR, SETS, XG, UG,
+      END;
+};
+RecLayout rec_layout(int NX, int NU, int MO, int Xn, int Un) {
+  RecLayout r;
+  int o = 0;
+  r.K = o++; r.RING = o++; r.RINGW = o++; r.TAG = o++; r.N = o++; r.NOBS = o++; r.DT = o++;
+  r.PRM = o; o += 8;
+  r.QD = o; o += NX; r.XR = o; o += NX; r.RD = o; o += NU; r.UR = o; o += NU;
+  r.QND = o; o += NX; r.QN = o; o += NX; r.XLO = o; o += NX; r.XHI = o; o += NX;
+  r.ULO = o; o += NU; r.UHI = o; o += NU; r.XI = o; o += NX; r.XT = o; o += NX; r.TM = o; o += NX;
+  r.OC = o; o += 3 * MO; r.OR = o; o += MO; r.SETS = o; o += UCN_SET_PARAMS;
+  r.XG = o; o += Xn * NX; r.UG = o; o += Un * NU;
+  r.END = (o + 1) / 2 * 2;   // 16-byte records
+  return r;
+}
+
+// What the scatter and keep kernels need (by value).
+struct ServeDev {
+  int NX, NU, MO, Xn, Un, REC, RES;
+  long long state_per_slot;
+  RecLayout rl;
+  int *N, *nobs;
+  double *dt, *prm, *Qd, *xr, *Rd, *ur, *QNd, *qN, *xlo, *xhi, *ulo, *uhi, *xi, *xt, *oc, *orr, *sets;
+  unsigned char *tm, *warm;
+  unsigned long long* tag;
+  double *x0, *u0, *xo, *uo, *state;
+  ucn_scp_stats* stats;
+  double *ring_x, *ring_u, *ring_state;
+};
+
+// One CTA per launched request j: its record rec[j] into the slot arrays (or
+// the guess and ADMM state from a ring entry for a warm start), and the CTA ->
+// slot order of the launch.
+__global__ void serve_scatter_kernel(ServeDev D, const double* rec, int* order) {
+  const int j = blockIdx.x, t = threadIdx.x, nt = blockDim.x;
+  const double* r = rec + (long long)j * D.REC;
+  const RecLayout& L = D.rl;
+  const int k = (int)r[L.K], ring = (int)r[L.RING], N = (int)r[L.N];
+  const int NX = D.NX, NU = D.NU, MO = D.MO;
+  if (t == 0) {
+    order[j] = k;
+    D.tag[k] = (unsigned long long)r[L.TAG];
+    D.N[k] = N;
+    D.nobs[k] = (int)r[L.NOBS];
+    D.dt[k] = r[L.DT];
+    D.warm[k] = ring >= 0 ? 1 : 0;
+  }
+  for (int e = t; e < 8; e += nt) { D.prm[k * 8 + e] = r[L.PRM + e]; D.sets[k * UCN_SET_PARAMS + e] = r[L.SETS + e]; }
+  for (int e = t; e < NX; e += nt) {
+    D.Qd[k * NX + e] = r[L.QD + e]; D.xr[k * NX + e] = r[L.XR + e]; D.QNd[k * NX + e] = r[L.QND + e];
+    D.qN[k * NX + e] = r[L.QN + e]; D.xlo[k * NX + e] = r[L.XLO + e]; D.xhi[k * NX + e] = r[L.XHI + e];
+    D.xi[k * NX + e] = r[L.XI + e]; D.xt[k * NX + e] = r[L.XT + e]; D.tm[k * NX + e] = (unsigned char)r[L.TM + e];
+  }
+  for (int e = t; e < NU; e += nt) {
+    D.Rd[k * NU + e] = r[L.RD + e]; D.ur[k * NU + e] = r[L.UR + e];
+    D.ulo[k * NU + e] = r[L.ULO + e]; D.uhi[k * NU + e] = r[L.UHI + e];
+  }
+  for (int e = t; e < 3 * MO; e += nt) D.oc[(long long)k * 3 * MO + e] = r[L.OC + e];
+  for (int e = t; e < MO; e += nt) D.orr[(long long)k * MO + e] = r[L.OR + e];
+  double* x0 = D.x0 + (long long)k * D.Xn * NX;
+  double* u0 = D.u0 + (long long)k * D.Un * NU;
+  if (ring >= 0) {
+    const double* rx = D.ring_x + (long long)ring * D.Xn * NX;
+    const double* ru = D.ring_u + (long long)ring * D.Un * NU;
+    const double* rs = D.ring_state + (long long)ring * D.state_per_slot;
+    double* st = D.state + (long long)k * D.state_per_slot;
+    for (int e = t; e < (N + 1) * NX; e += nt) x0[e] = rx[e];
+    for (int e = t; e < N * NU; e += nt) u0[e] = ru[e];
+    for (long long e = t; e < D.state_per_slot; e += nt) st[e] = rs[e];
+  } else {
+    for (int e = t; e < (N + 1) * NX; e += nt) x0[e] = r[L.XG + e];
+    for (int e = t; e < N * NU; e += nt) u0[e] = r[L.UG + e];
+  }
+}
+
+// One CTA per launched request j that keeps its result: its trajectory and
+// final ADMM state into the ring entry the launch assigned it (warm starts).
+__global__ void serve_keep_kernel(ServeDev D, const double* rec) {
+  const int j = blockIdx.x, t = threadIdx.x, nt = blockDim.x;
+  const double* r = rec + (long long)j * D.REC;
+  const RecLayout& L = D.rl;
+  const int k = (int)r[L.K], ringw = (int)r[L.RINGW], N = (int)r[L.N];
+  if (ringw < 0) return;
+  const int NX = D.NX, NU = D.NU;
+  const double* xo = D.xo + (long long)k * D.Xn * NX;
+  const double* uo = D.uo + (long long)k * D.Un * NU;
+  double* rx = D.ring_x + (long long)ringw * D.Xn * NX;
+  double* ru = D.ring_u + (long long)ringw * D.Un * NU;
+  double* rs = D.ring_state + (long long)ringw * D.state_per_slot;
+  const double* st = D.state + (long long)k * D.state_per_slot;
+  for (int e = t; e < (N + 1) * NX; e += nt) rx[e] = xo[e];
+  for (int e = t; e < N * NU; e += nt) ru[e] = uo[e];
+  for (long long e = t; e < D.state_per_slot; e += nt) rs[e] = st[e];
+}
 
 }  // namespace
 
 struct ucn_server {
   ucn_serve_config cfg;
-  int nx, nu, S, Nmax, max_obs, lanes;
+  int nx, nu, S, Nmax, max_obs, lanes, MO;
   long long state_per_slot, budget, used;
   ProblemDev P;
+  ServeDev D;
+  RecLayout rl;
   Layout L;
   bool smem;
   long long smem_bytes;
   int threads;
   int tpn;               // threads per node of the fused solve
+  int* status_d;         // per-slot status of the fused solve
   std::vector<void*> dev_allocs, host_allocs;
-  // pinned host mirrors of the per-slot problem arrays (same layout as on the device)
-  int *hN, *hnobs;
-  double *hdt, *hprm, *hQd, *hxr, *hRd, *hur, *hQNd, *hqN, *hxlo, *hxhi, *hulo, *huhi, *hxi, *hxt, *hoc, *hor, *hsets;
-  unsigned char* htm;
-  double *hxg, *hug;
-  // device
-  int *dN, *dnobs;
-  double *ddt, *dprm, *dQd, *dxr, *dRd, *dur, *dQNd, *dqN, *dxlo, *dxhi, *dulo, *duhi, *dxi, *dxt, *doc, *dor, *dsets;
-  unsigned char* dtm;
-  double *x0, *u0, *xo, *uo;
-  ucn_scp_stats* stats;
-  int* status;
+  std::vector<double> hrec;          // admitted requests' records, [S][REC] (host)
   // slots
-  std::vector<int> slot_state, slot_lane, slot_warm_ring;
+  std::vector<int> slot_state, slot_lane, slot_pos, slot_ring_read, slot_ring_write;
   std::vector<unsigned long long> slot_ticket;
   std::vector<long long> slot_bytes;
   std::map<unsigned long long, int> ticket_slot;
   unsigned long long next_ticket;
-  // lanes
+  // results: per-slot records and flags in mapped host memory (host and device views)
+  double *res_h, *res_dv;
+  unsigned long long *flag_h, *flag_dv;
+  // lanes: stream, completion event, staging (pinned host, device), the ring
+  // entries its running launch fills, a launch failure
   std::vector<cudaStream_t> streams;
   std::vector<cudaEvent_t> done;
+  std::vector<double*> stage_h, stage_d;
   std::vector<int*> order_d;
-  std::vector<int*> order_h;
   std::vector<int> lane_busy;
-  // kept trajectories (warm starts)
+  std::vector<cudaError_t> lane_error;
+  std::vector<std::vector<int>> lane_rings;
+  // ring of kept results: ticket, horizon, kept (its launch has finished),
+  // being written (by lane ring_lane), admitted requests reading it
   int R, ring_next;
-  double *ring_x, *ring_u;
   std::vector<unsigned long long> ring_ticket;
-  std::vector<int> ring_N;
+  std::vector<int> ring_N, ring_done, ring_writing, ring_lane, ring_readers;
   std::mutex mu;
 };
 
@@ -107,6 +224,21 @@ bool halloc(ucn_server* s, V** out, size_t n) {
   return true;
 }
 
+// Pinned host memory the device writes directly (mapped): host and device views.
+template <class V>
+bool mapped(ucn_server* s, V** host, V** dev, size_t n) {
+  void* p = nullptr;
+  const size_t bytes = std::max<size_t>(n * sizeof(V), 16);
+  if (cudaHostAlloc(&p, bytes, cudaHostAllocMapped) != cudaSuccess) { cudaGetLastError(); return false; }
+  std::memset(p, 0, bytes);
+  s->host_allocs.push_back(p);
+  void* d = nullptr;
+  if (cudaHostGetDevicePointer(&d, p, 0) != cudaSuccess) { cudaGetLastError(); return false; }
+  *host = (V*)p;
+  *dev = (V*)d;
+  return true;
+}
+
 long long footprint(const ucn_server* s, int N) {
   const long long nodes = N + 1;
   long long b = nodes * (long long)(s->nx + s->nu) * 8 * 2;                       // guess + output
@@ -114,6 +246,51 @@ long long footprint(const ucn_server* s, int N) {
   b += 8LL * (6 * nodes * s->nx + 3LL * N * s->nu + 2 * nodes * mb * 3);          // exported state
   if (!s->smem) b += (long long)s->L.bytes * nodes / (s->Nmax + 1);               // global workspace share
   return b;
+}
+
+void release_slot(ucn_server* s, int k) {
+  s->slot_state[k] = SLOT_FREE;
+  s->used -= s->slot_bytes[k];
+  s->slot_bytes[k] = 0;
+}
+
+// A lane whose launch has finished: the ring entries it filled become kept and
+// its drained slots free.
+void retire_lane(ucn_server* s, int l) {
+  for (int r : s->lane_rings[l]) { s->ring_writing[r] = 0; s->ring_done[r] = 1; }
+  s->lane_rings[l].clear();
+  s->lane_busy[l] = 0;
+  for (int k = 0; k < s->S; ++k)
+    if (s->slot_state[k] == SLOT_DRAINING && s->slot_lane[k] == l) release_slot(s, k);
+}
+
+
+// Whether lane l's launch has ended (finished, or failed: lane_error).
+bool lane_ended(ucn_server* s, int l) {
+  if (!s->lane_busy[l]) return true;
+  const cudaError_t q = cudaEventQuery(s->done[l]);
+  if (q == cudaErrorNotReady) return false;
+  if (q != cudaSuccess) s->lane_error[l] = q;
+  retire_lane(s, l);
+  return true;
+}
+
+// Retires every lane whose launch has ended.
+void retire_ended(ucn_server* s) {
+  for (int l = 0; l < s->lanes; ++l) lane_ended(s, l);
+}
+
+// A ring entry that no launch is writing and no admitted request reads, the
+// oldest first (round robin); -1 when every entry is held.
+int take_ring_entry(ucn_server* s) {
+  for (int t = 0; t < s->R; ++t) {
+    const int r = (s->ring_next + t) % s->R;
+    if (!s->ring_writing[r] && s->ring_readers[r] == 0) {
+      s->ring_next = (r + 1) % s->R;
+      return r;
+    }
+  }
+  return -1;
 }
 
 }  // namespace
@@ -149,6 +326,7 @@ ucn_status ucn_serve_create(const ucn_serve_config* c, ucn_server** out) {
   s->nx = model_nx(c->model); s->nu = model_nu(c->model);
   s->S = c->max_slots; s->Nmax = c->max_horizon; s->max_obs = quad ? c->max_obs : 0; s->lanes = c->lanes;
   const int S = s->S, NX = s->nx, NU = s->nu, MO = std::max(s->max_obs, 1);
+  s->MO = MO;
   const int mb = quad ? s->max_obs : (c->model == UCN_MODEL_MARS14 ? 6 : 3);
   const long long Xn = (long long)(s->Nmax + 1), Un = s->Nmax;
   s->state_per_slot = 6 * Xn * NX + 3 * Un * NU + 2 * Xn * mb * 3;
@@ -166,28 +344,33 @@ ucn_status ucn_serve_create(const ucn_serve_config* c, ucn_server** out) {
   s->smem_bytes = s->smem ? s->L.bytes : 0;
   s->threads = (s->Nmax + 1 + 31) / 32 * 32;
   s->R = c->kept > 0 ? c->kept : 2 * S;
+  s->rl = rec_layout(NX, NU, MO, (int)Xn, (int)Un);
+  const int REC = s->rl.END, RES = (int)((16 + Xn * NX + Un * NU + 1) / 2 * 2);
+  const int cap = std::min(S, LAUNCH_CAP);
+  ServeDev& D = s->D;
+  std::memset(&D, 0, sizeof(D));
+  D.NX = NX; D.NU = NU; D.MO = MO; D.Xn = (int)Xn; D.Un = (int)Un; D.REC = REC; D.RES = RES;
+  D.state_per_slot = s->state_per_slot; D.rl = s->rl;
   bool ok = true;
-  ok = ok && halloc(s, &s->hN, S) && halloc(s, &s->hnobs, S) && halloc(s, &s->hdt, S) && halloc(s, &s->hprm, (size_t)S * 8);
-  ok = ok && halloc(s, &s->hQd, (size_t)S * NX) && halloc(s, &s->hxr, (size_t)S * NX) && halloc(s, &s->hRd, (size_t)S * NU);
-  ok = ok && halloc(s, &s->hur, (size_t)S * NU) && halloc(s, &s->hQNd, (size_t)S * NX) && halloc(s, &s->hqN, (size_t)S * NX);
-  ok = ok && halloc(s, &s->hxlo, (size_t)S * NX) && halloc(s, &s->hxhi, (size_t)S * NX) && halloc(s, &s->hulo, (size_t)S * NU);
-  ok = ok && halloc(s, &s->huhi, (size_t)S * NU) && halloc(s, &s->hxi, (size_t)S * NX) && halloc(s, &s->hxt, (size_t)S * NX);
-  ok = ok && halloc(s, &s->htm, (size_t)S * NX) && halloc(s, &s->hoc, (size_t)S * MO * 3) && halloc(s, &s->hor, (size_t)S * MO);
-  ok = ok && halloc(s, &s->hsets, (size_t)S * UCN_SET_PARAMS) && halloc(s, &s->hxg, (size_t)S * Xn * NX) && halloc(s, &s->hug, (size_t)S * Un * NU);
-  ok = ok && dalloc(s, &s->dN, S) && dalloc(s, &s->dnobs, S) && dalloc(s, &s->ddt, S) && dalloc(s, &s->dprm, (size_t)S * 8);
-  ok = ok && dalloc(s, &s->dQd, (size_t)S * NX) && dalloc(s, &s->dxr, (size_t)S * NX) && dalloc(s, &s->dRd, (size_t)S * NU);
-  ok = ok && dalloc(s, &s->dur, (size_t)S * NU) && dalloc(s, &s->dQNd, (size_t)S * NX) && dalloc(s, &s->dqN, (size_t)S * NX);
-  ok = ok && dalloc(s, &s->dxlo, (size_t)S * NX) && dalloc(s, &s->dxhi, (size_t)S * NX) && dalloc(s, &s->dulo, (size_t)S * NU);
-  ok = ok && dalloc(s, &s->duhi, (size_t)S * NU) && dalloc(s, &s->dxi, (size_t)S * NX) && dalloc(s, &s->dxt, (size_t)S * NX);
-  ok = ok && dalloc(s, &s->dtm, (size_t)S * NX) && dalloc(s, &s->doc, (size_t)S * MO * 3) && dalloc(s, &s->dor, (size_t)S * MO);
-  ok = ok && dalloc(s, &s->dsets, (size_t)S * UCN_SET_PARAMS);
-  ok = ok && dalloc(s, &s->x0, (size_t)S * Xn * NX) && dalloc(s, &s->u0, (size_t)S * Un * NU);
-  ok = ok && dalloc(s, &s->xo, (size_t)S * Xn * NX) && dalloc(s, &s->uo, (size_t)S * Un * NU);
-  ok = ok && dalloc(s, &s->stats, (size_t)S) && dalloc(s, &s->status, (size_t)S);
-  ok = ok && dalloc(s, &s->ring_x, (size_t)s->R * Xn * NX) && dalloc(s, &s->ring_u, (size_t)s->R * Un * NU);
+  ok = ok && dalloc(s, &D.N, S) && dalloc(s, &D.nobs, S) && dalloc(s, &D.dt, S) && dalloc(s, &D.prm, (size_t)S * 8);
+  ok = ok && dalloc(s, &D.Qd, (size_t)S * NX) && dalloc(s, &D.xr, (size_t)S * NX) && dalloc(s, &D.Rd, (size_t)S * NU);
+  ok = ok && dalloc(s, &D.ur, (size_t)S * NU) && dalloc(s, &D.QNd, (size_t)S * NX) && dalloc(s, &D.qN, (size_t)S * NX);
+  ok = ok && dalloc(s, &D.xlo, (size_t)S * NX) && dalloc(s, &D.xhi, (size_t)S * NX) && dalloc(s, &D.ulo, (size_t)S * NU);
+  ok = ok && dalloc(s, &D.uhi, (size_t)S * NU) && dalloc(s, &D.xi, (size_t)S * NX) && dalloc(s, &D.xt, (size_t)S * NX);
+  ok = ok && dalloc(s, &D.tm, (size_t)S * NX) && dalloc(s, &D.oc, (size_t)S * MO * 3) && dalloc(s, &D.orr, (size_t)S * MO);
+  ok = ok && dalloc(s, &D.sets, (size_t)S * UCN_SET_PARAMS) && dalloc(s, &D.warm, (size_t)S) && dalloc(s, &D.tag, (size_t)S);
+  ok = ok && dalloc(s, &D.x0, (size_t)S * Xn * NX) && dalloc(s, &D.u0, (size_t)S * Un * NU);
+  ok = ok && dalloc(s, &D.xo, (size_t)S * Xn * NX) && dalloc(s, &D.uo, (size_t)S * Un * NU);
+  ok = ok && dalloc(s, &D.stats, (size_t)S);
+  ok = ok && dalloc(s, &D.state, (size_t)S * s->state_per_slot);
+  ok = ok && dalloc(s, &D.ring_x, (size_t)s->R * Xn * NX) && dalloc(s, &D.ring_u, (size_t)s->R * Un * NU);
+  ok = ok && dalloc(s, &D.ring_state, (size_t)s->R * s->state_per_slot);
+  ok = ok && dalloc(s, &s->status_d, (size_t)S);
+  // result records and flags in mapped host memory, written by the solve's CTAs
+  ok = ok && mapped(s, &s->res_h, &s->res_dv, (size_t)S * RES) && mapped(s, &s->flag_h, &s->flag_dv, (size_t)S);
   long long *dxoff = nullptr, *duoff = nullptr, *dsoff = nullptr;
-  double *sabs = nullptr, *dfac = nullptr;
-  ok = ok && dalloc(s, &dxoff, S) && dalloc(s, &duoff, S) && dalloc(s, &dsoff, S) && dalloc(s, &sabs, (size_t)S * s->state_per_slot);
+  double* dfac = nullptr;
+  ok = ok && dalloc(s, &dxoff, S) && dalloc(s, &duoff, S) && dalloc(s, &dsoff, S);
   const std::vector<double> fac = rho_schedule(c->rho_final, c->rho_geo, c->scp_iters);
   ok = ok && dalloc(s, &dfac, fac.size());
   char* ws = nullptr;
@@ -200,30 +383,38 @@ ucn_status ucn_serve_create(const ucn_serve_config* c, ucn_server** out) {
     cudaMemcpy(dsoff, so.data(), sizeof(long long) * S, cudaMemcpyHostToDevice);
     cudaMemcpy(dfac, fac.data(), sizeof(double) * fac.size(), cudaMemcpyHostToDevice);
     for (int l = 0; l < s->lanes && ok; ++l) {
-      cudaStream_t st; cudaEvent_t ev; int *od, *oh;
+      cudaStream_t st; cudaEvent_t ev; int* od; double *sh, *sd;
       ok = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess &&
-           cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess &&
-           dalloc(s, &od, S) && halloc(s, &oh, S);
-      if (ok) { s->streams.push_back(st); s->done.push_back(ev); s->order_d.push_back(od); s->order_h.push_back(oh); s->lane_busy.push_back(0); }
+           cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess && dalloc(s, &od, cap) &&
+           halloc(s, &sh, (size_t)cap * REC) && dalloc(s, &sd, (size_t)cap * REC);
+      if (ok) {
+        s->streams.push_back(st); s->done.push_back(ev); s->order_d.push_back(od);
+        s->stage_h.push_back(sh); s->stage_d.push_back(sd);
+        s->lane_busy.push_back(0); s->lane_error.push_back(cudaSuccess); s->lane_rings.emplace_back();
+      }
     }
   }
   if (!ok) { ucn_serve_destroy(s); return sfail(UCN_ENOMEM, "server allocation failed"); }
+  s->hrec.assign((size_t)S * REC, 0.0);
   ProblemDev& P = s->P;
   std::memset(&P, 0, sizeof(P));
   P.model = c->model; P.nx = NX; P.nu = NU; P.batch = S; P.max_obs = s->max_obs;
-  P.N = s->dN; P.xoff = dxoff; P.uoff = duoff; P.soff = dsoff; P.dt = s->ddt; P.params = s->dprm;
-  P.Qd = s->dQd; P.xref = s->dxr; P.Rd = s->dRd; P.uref = s->dur; P.QNd = s->dQNd; P.qN = s->dqN;
-  P.xlo = s->dxlo; P.xhi = s->dxhi; P.ulo = s->dulo; P.uhi = s->duhi; P.xinit = s->dxi; P.xtarget = s->dxt;
-  P.tmask = s->dtm; P.nobs = s->dnobs; P.obs_c = s->doc; P.obs_r = s->dor; P.sets = s->dsets;
+  P.N = D.N; P.xoff = dxoff; P.uoff = duoff; P.soff = dsoff; P.dt = D.dt; P.params = D.prm;
+  P.Qd = D.Qd; P.xref = D.xr; P.Rd = D.Rd; P.uref = D.ur; P.QNd = D.QNd; P.qN = D.qN;
+  P.xlo = D.xlo; P.xhi = D.xhi; P.ulo = D.ulo; P.uhi = D.uhi; P.xinit = D.xi; P.xtarget = D.xt;
+  P.tmask = D.tm; P.nobs = D.nobs; P.obs_c = D.oc; P.obs_r = D.orr; P.sets = D.sets;
   P.rho_eq = c->rho_eq; P.rho_dyn = c->rho_dyn; P.rho_geo = c->rho_geo; P.rho_final = c->rho_final;
   P.scp_iters = c->scp_iters; P.admm_iters = c->admm_iters; P.stop = c->stop;
   P.tr_init = c->tr_init; P.tr_min = c->tr_min; P.tr_max = c->tr_max; P.w_d = c->w_d;
   P.defect_tol = c->defect_tol; P.step_tol = c->step_tol;
   P.timeout_ns = (unsigned long long)((c->timeout_s > 0 ? c->timeout_s : 60.0) * 1e9);
-  P.state_abs = sabs; P.ws = ws; P.order = nullptr; P.rho_fac = dfac;
-  s->slot_state.assign(S, SLOT_FREE); s->slot_lane.assign(S, -1); s->slot_warm_ring.assign(S, -1);
+  P.state_abs = D.state; P.ws = ws; P.order = nullptr; P.rho_fac = dfac; P.warm = D.warm;
+  P.res_host = s->res_dv; P.res_flag = s->flag_dv; P.res_tag = D.tag; P.res_stride = RES;
+  s->slot_state.assign(S, SLOT_FREE); s->slot_lane.assign(S, -1); s->slot_pos.assign(S, -1);
+  s->slot_ring_read.assign(S, -1); s->slot_ring_write.assign(S, -1);
   s->slot_ticket.assign(S, 0); s->slot_bytes.assign(S, 0);
-  s->ring_ticket.assign(s->R, 0); s->ring_N.assign(s->R, 0); s->ring_next = 0;
+  s->ring_ticket.assign(s->R, 0); s->ring_N.assign(s->R, 0); s->ring_done.assign(s->R, 0);
+  s->ring_writing.assign(s->R, 0); s->ring_lane.assign(s->R, -1); s->ring_readers.assign(s->R, 0); s->ring_next = 0;
   s->next_ticket = 1; s->used = 0;
   s->budget = c->hbm_budget_bytes > 0 ? (long long)c->hbm_budget_bytes : (long long)1 << 62;
   *out = s;
@@ -245,38 +436,47 @@ ucn_status ucn_serve_submit(ucn_server* s, const ucn_request* r, unsigned long l
   int ring = -1;
   if (!(r->x_guess && r->u_guess)) {
     for (int k = 0; k < s->R; ++k)
-      if (s->ring_ticket[k] == r->warm_ticket && r->warm_ticket != 0 && s->ring_N[k] == N) ring = k;
-    if (ring < 0) return sfail(UCN_EINVAL, "no guess and no kept trajectory of horizon %d for ticket %llu", N, r->warm_ticket);
+      if (r->warm_ticket != 0 && s->ring_ticket[k] == r->warm_ticket && (s->ring_done[k] || s->ring_writing[k]) &&
+          s->ring_N[k] == N)
+        ring = k;
+    if (ring < 0) return sfail(UCN_EINVAL, "no guess and no kept result of horizon %d for ticket %llu", N, r->warm_ticket);
   }
   const long long fp = footprint(s, N);
   int slot = -1;
-  for (int k = 0; k < s->S; ++k)
-    if (s->slot_state[k] == SLOT_FREE) { slot = k; break; }
+  for (int pass = 0; pass < 2 && slot < 0; ++pass) {
+    if (pass == 1 || s->used + fp > s->budget) retire_ended(s);   // frees drained slots
+    for (int k = 0; k < s->S; ++k)
+      if (s->slot_state[k] == SLOT_FREE) { slot = k; break; }
+  }
   if (slot < 0) return sfail(UCN_EBUSY, "no free slot");
   if (s->used + fp > s->budget) return sfail(UCN_EBUSY, "HBM budget: %lld of %lld bytes in use, request needs %lld", s->used, s->budget, fp);
-  const int k = slot, MO = std::max(s->max_obs, 1);
-  s->hN[k] = N; s->hdt[k] = r->dt;
-  std::memcpy(&s->hprm[k * 8], r->model_params, 8 * sizeof(double));
-  std::memcpy(&s->hQd[k * NX], r->Q_diag, NX * 8); std::memcpy(&s->hxr[k * NX], r->x_ref, NX * 8);
-  std::memcpy(&s->hRd[k * NU], r->R_diag, NU * 8); std::memcpy(&s->hur[k * NU], r->u_ref, NU * 8);
-  std::memcpy(&s->hQNd[k * NX], r->QN_diag, NX * 8); std::memcpy(&s->hqN[k * NX], r->qN, NX * 8);
-  std::memcpy(&s->hxlo[k * NX], r->x_lo, NX * 8); std::memcpy(&s->hxhi[k * NX], r->x_hi, NX * 8);
-  std::memcpy(&s->hulo[k * NU], r->u_lo, NU * 8); std::memcpy(&s->huhi[k * NU], r->u_hi, NU * 8);
-  std::memcpy(&s->hxi[k * NX], r->x_init, NX * 8); std::memcpy(&s->hxt[k * NX], r->x_target, NX * 8);
-  std::memcpy(&s->htm[k * NX], r->term_mask, NX);
-  s->hnobs[k] = model_obstacles(s->cfg.model) ? r->n_obs : 0;
-  if (s->hnobs[k] > 0) {
-    std::memcpy(&s->hoc[(size_t)k * MO * 3], r->obs_c, (size_t)r->n_obs * 3 * 8);
-    std::memcpy(&s->hor[(size_t)k * MO], r->obs_r, (size_t)r->n_obs * 8);
+  const int k = slot;
+  const RecLayout& L = s->rl;
+  double* rec = &s->hrec[(size_t)k * L.END];
+  std::fill(rec, rec + L.END, 0.0);
+  rec[L.K] = k; rec[L.RING] = ring; rec[L.RINGW] = -1; rec[L.N] = N; rec[L.DT] = r->dt;
+  rec[L.TAG] = (double)s->next_ticket;
+  rec[L.NOBS] = model_obstacles(s->cfg.model) ? r->n_obs : 0;
+  std::memcpy(&rec[L.PRM], r->model_params, 8 * sizeof(double));
+  std::memcpy(&rec[L.QD], r->Q_diag, NX * 8); std::memcpy(&rec[L.XR], r->x_ref, NX * 8);
+  std::memcpy(&rec[L.RD], r->R_diag, NU * 8); std::memcpy(&rec[L.UR], r->u_ref, NU * 8);
+  std::memcpy(&rec[L.QND], r->QN_diag, NX * 8); std::memcpy(&rec[L.QN], r->qN, NX * 8);
+  std::memcpy(&rec[L.XLO], r->x_lo, NX * 8); std::memcpy(&rec[L.XHI], r->x_hi, NX * 8);
+  std::memcpy(&rec[L.ULO], r->u_lo, NU * 8); std::memcpy(&rec[L.UHI], r->u_hi, NU * 8);
+  std::memcpy(&rec[L.XI], r->x_init, NX * 8); std::memcpy(&rec[L.XT], r->x_target, NX * 8);
+  for (int j = 0; j < NX; ++j) rec[L.TM + j] = r->term_mask[j];
+  if (rec[L.NOBS] > 0) {
+    std::memcpy(&rec[L.OC], r->obs_c, (size_t)r->n_obs * 3 * 8);
+    std::memcpy(&rec[L.OR], r->obs_r, (size_t)r->n_obs * 8);
   }
-  if (r->sets) std::memcpy(&s->hsets[k * UCN_SET_PARAMS], r->sets, UCN_SET_PARAMS * 8);
-  else std::memset(&s->hsets[k * UCN_SET_PARAMS], 0, UCN_SET_PARAMS * 8);
-  const long long Xn = s->Nmax + 1, Un = s->Nmax;
+  if (r->sets) std::memcpy(&rec[L.SETS], r->sets, UCN_SET_PARAMS * 8);
   if (ring < 0) {
-    std::memcpy(&s->hxg[k * Xn * NX], r->x_guess, (size_t)(N + 1) * NX * 8);
-    std::memcpy(&s->hug[k * Un * NU], r->u_guess, (size_t)N * NU * 8);
+    std::memcpy(&rec[L.XG], r->x_guess, (size_t)(N + 1) * NX * 8);
+    std::memcpy(&rec[L.UG], r->u_guess, (size_t)N * NU * 8);
+  } else {
+    s->ring_readers[ring]++;   // held until this request's result is collected
   }
-  s->slot_warm_ring[k] = ring;
+  s->slot_ring_read[k] = ring;
   s->slot_state[k] = SLOT_ADMITTED;
   s->slot_bytes[k] = fp;
   s->used += fp;
@@ -292,53 +492,109 @@ ucn_status ucn_serve_pump(ucn_server* s, int* launched) {
   if (launched) *launched = 0;
   std::lock_guard<std::mutex> lk(s->mu);
   std::vector<int> ready;
-  for (int k = 0; k < s->S; ++k)
+  const int cap = std::min(s->S, LAUNCH_CAP);
+  for (int k = 0; k < s->S && (int)ready.size() < cap; ++k)
     if (s->slot_state[k] == SLOT_ADMITTED) ready.push_back(k);
   if (ready.empty()) return UCN_OK;
+  // a free lane: its last launch has ended
   int lane = -1;
-  for (int l = 0; l < s->lanes; ++l) {
-    if (s->lane_busy[l] && cudaEventQuery(s->done[l]) == cudaSuccess) s->lane_busy[l] = 0;
-    if (!s->lane_busy[l] && lane < 0) lane = l;
-  }
+  for (int l = 0; l < s->lanes; ++l)
+    if (lane_ended(s, l) && lane < 0) lane = l;
   if (lane < 0) return sfail(UCN_EBUSY, "every lane is running a launch");
+  s->lane_error[lane] = cudaSuccess;
   cudaStream_t st = s->streams[lane];
-  const int S = s->S, NX = s->nx, NU = s->nu, MO = std::max(s->max_obs, 1);
-  const long long Xn = s->Nmax + 1, Un = s->Nmax;
-  // whole per-slot arrays from the pinned mirrors (running slots get their own, unchanged, bytes)
-#define H2D(d, h, n) cudaMemcpyAsync(d, h, (size_t)(n) * sizeof(*(h)), cudaMemcpyHostToDevice, st)
-  H2D(s->dN, s->hN, S); H2D(s->dnobs, s->hnobs, S); H2D(s->ddt, s->hdt, S); H2D(s->dprm, s->hprm, S * 8);
-  H2D(s->dQd, s->hQd, S * NX); H2D(s->dxr, s->hxr, S * NX); H2D(s->dRd, s->hRd, S * NU); H2D(s->dur, s->hur, S * NU);
-  H2D(s->dQNd, s->hQNd, S * NX); H2D(s->dqN, s->hqN, S * NX); H2D(s->dxlo, s->hxlo, S * NX); H2D(s->dxhi, s->hxhi, S * NX);
-  H2D(s->dulo, s->hulo, S * NU); H2D(s->duhi, s->huhi, S * NU); H2D(s->dxi, s->hxi, S * NX); H2D(s->dxt, s->hxt, S * NX);
-  H2D(s->dtm, s->htm, S * NX); H2D(s->doc, s->hoc, (size_t)S * MO * 3); H2D(s->dor, s->hor, (size_t)S * MO); H2D(s->dsets, s->hsets, S * UCN_SET_PARAMS);
-  for (size_t j = 0; j < ready.size(); ++j) {
-    const int k = ready[j], N = s->hN[k], ring = s->slot_warm_ring[k];
-    if (ring >= 0) {
-      cudaMemcpyAsync(&s->x0[k * Xn * NX], &s->ring_x[ring * Xn * NX], (size_t)(N + 1) * NX * 8, cudaMemcpyDeviceToDevice, st);
-      cudaMemcpyAsync(&s->u0[k * Un * NU], &s->ring_u[ring * Un * NU], (size_t)N * NU * 8, cudaMemcpyDeviceToDevice, st);
-    } else {
-      H2D(&s->x0[k * Xn * NX], &s->hxg[k * Xn * NX], (N + 1) * NX);
-      H2D(&s->u0[k * Un * NU], &s->hug[k * Un * NU], N * NU);
+  const RecLayout& L = s->rl;
+  const int n = (int)ready.size();
+  double* stage = s->stage_h[lane];
+  for (int j = 0; j < n; ++j) {
+    const int k = ready[j];
+    double* rec = &s->hrec[(size_t)k * L.END];
+    const int rw = take_ring_entry(s);   // where this request's result is kept for warm starts
+    rec[L.RINGW] = rw;
+    s->slot_ring_write[k] = rw;
+    if (rw >= 0) {
+      s->ring_writing[rw] = 1; s->ring_done[rw] = 0; s->ring_lane[rw] = lane;
+      s->ring_ticket[rw] = s->slot_ticket[k]; s->ring_N[rw] = (int)rec[L.N];
+      s->lane_rings[lane].push_back(rw);
     }
-    s->order_h[lane][j] = k;
+    std::memcpy(stage + (size_t)j * L.END, rec, (size_t)L.END * sizeof(double));
   }
-  H2D(s->order_d[lane], s->order_h[lane], ready.size());
-#undef H2D
-  ProblemDev P = s->P;
-  P.order = s->order_d[lane];
-  LaunchCfg c;
-  c.P = &P; c.L = &s->L; c.smem = s->smem; c.smem_bytes = s->smem_bytes;
-  c.threads = s->threads; c.blocks = (int)ready.size(); c.stream = st; c.group = 1;
-  c.nodes = s->cfg.max_horizon + 1; c.tpn = s->tpn;
-  auto fn = launchers_for(s->cfg.model, s->cfg.precision).scp;
-  cudaError_t e = fn(c, s->x0, s->u0, s->xo, s->uo, s->stats, s->status);
+  cudaError_t e = cudaSuccess;
+  // a warm request whose ring entry another lane is still filling reads it after that lane's launch
+  for (int k : ready) {
+    const int rr = s->slot_ring_read[k];
+    if (rr >= 0 && s->ring_writing[rr] && s->ring_lane[rr] != lane && e == cudaSuccess)
+      e = cudaStreamWaitEvent(st, s->done[s->ring_lane[rr]], 0);
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(s->stage_d[lane], stage, (size_t)n * L.END * sizeof(double), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) {
+    serve_scatter_kernel<<<n, 128, 0, st>>>(s->D, s->stage_d[lane], s->order_d[lane]);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
+    ProblemDev P = s->P;
+    P.order = s->order_d[lane];
+    LaunchCfg c;
+    c.P = &P; c.L = &s->L; c.smem = s->smem; c.smem_bytes = s->smem_bytes;
+    c.threads = s->threads; c.blocks = n; c.stream = st; c.group = 1;
+    c.nodes = s->cfg.max_horizon + 1; c.tpn = s->tpn;
+    auto fn = launchers_for(s->cfg.model, s->cfg.precision).scp;
+    e = fn(c, s->D.x0, s->D.u0, s->D.xo, s->D.uo, s->D.stats, s->status_d);
+  }
+  if (e == cudaSuccess) {
+    serve_keep_kernel<<<n, 128, 0, st>>>(s->D, s->stage_d[lane]);
+    e = cudaGetLastError();
+  }
   if (e == cudaSuccess) e = cudaEventRecord(s->done[lane], st);
-  if (e != cudaSuccess) return sfail(UCN_ECUDA, "serve launch: %s", cudaGetErrorString(e));
+  if (e != cudaSuccess) {
+    for (int k : ready)
+      if (s->slot_ring_write[k] >= 0) { s->ring_writing[s->slot_ring_write[k]] = 0; s->slot_ring_write[k] = -1; }
+    s->lane_rings[lane].clear();
+    return sfail(UCN_ECUDA, "serve launch: %s", cudaGetErrorString(e));
+  }
   s->lane_busy[lane] = 1;
-  for (int k : ready) { s->slot_state[k] = SLOT_RUNNING; s->slot_lane[k] = lane; }
-  if (launched) *launched = (int)ready.size();
+  for (int j = 0; j < n; ++j) {
+    const int k = ready[j];
+    s->slot_state[k] = SLOT_RUNNING; s->slot_lane[k] = lane; s->slot_pos[k] = j;
+  }
+  if (launched) *launched = n;
   return UCN_OK;
 }
+
+}  // extern "C"
+
+namespace {
+
+// The finished request in slot k (its flag carries its ticket) into res; frees
+// the slot.  Host memory only.
+void take_result(ucn_server* s, int k, ucn_result* res) {
+  const int NX = s->nx, NU = s->nu, N = (int)s->hrec[(size_t)k * s->rl.END + s->rl.N];
+  const double* o = s->res_h + (size_t)k * s->D.RES;
+  std::memcpy(&res->stats, o, sizeof(ucn_scp_stats));
+  if (res->x) std::memcpy(res->x, o + 16, (size_t)(N + 1) * NX * sizeof(double));
+  if (res->u) std::memcpy(res->u, o + 16 + (N + 1) * NX, (size_t)N * NU * sizeof(double));
+  const int rr = s->slot_ring_read[k];
+  if (rr >= 0) s->ring_readers[rr]--;   // its launch read the entry before the solve began
+  s->slot_ring_write[k] = s->slot_ring_read[k] = -1;
+  res->ticket = s->slot_ticket[k];
+  res->horizon = N;
+  s->ticket_slot.erase(s->slot_ticket[k]);
+  if (s->lane_busy[s->slot_lane[k]]) s->slot_state[k] = SLOT_DRAINING;   // freed when its lane retires
+  else release_slot(s, k);
+}
+
+// Slot k's request has been delivered (its CTA raised the flag with its ticket).
+bool delivered(const ucn_server* s, int k) {
+  if (s->slot_state[k] != SLOT_RUNNING || *(volatile const unsigned long long*)(s->flag_h + k) != s->slot_ticket[k])
+    return false;
+  std::atomic_thread_fence(std::memory_order_acquire);   // the record was written before the flag
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
 
 ucn_status ucn_serve_poll(ucn_server* s, unsigned long long ticket, ucn_result* res) {
   set_error_message("");
@@ -347,35 +603,39 @@ ucn_status ucn_serve_poll(ucn_server* s, unsigned long long ticket, ucn_result* 
   auto it = s->ticket_slot.find(ticket);
   if (it == s->ticket_slot.end()) return sfail(UCN_EINVAL, "unknown ticket %llu", ticket);
   const int k = it->second;
-  if (s->slot_state[k] != SLOT_RUNNING) return UCN_EBUSY;                 // admitted, not launched yet
-  const int lane = s->slot_lane[k];
-  const cudaError_t q = cudaEventQuery(s->done[lane]);
-  if (q == cudaErrorNotReady) return UCN_EBUSY;
-  if (q != cudaSuccess) return sfail(UCN_ECUDA, "serve launch failed: %s", cudaGetErrorString(q));
-  const int NX = s->nx, NU = s->nu, N = s->hN[k];
-  const long long Xn = s->Nmax + 1, Un = s->Nmax;
-  cudaError_t e = cudaMemcpy(&res->stats, &s->stats[k], sizeof(ucn_scp_stats), cudaMemcpyDeviceToHost);
-  if (e == cudaSuccess && res->x) e = cudaMemcpy(res->x, &s->xo[k * Xn * NX], (size_t)(N + 1) * NX * 8, cudaMemcpyDeviceToHost);
-  if (e == cudaSuccess && res->u) e = cudaMemcpy(res->u, &s->uo[k * Un * NU], (size_t)N * NU * 8, cudaMemcpyDeviceToHost);
-  // keep the trajectory on the device for warm starts of later requests
-  const int ring = s->ring_next;
-  s->ring_next = (s->ring_next + 1) % s->R;
-  if (e == cudaSuccess) e = cudaMemcpy(&s->ring_x[ring * Xn * NX], &s->xo[k * Xn * NX], (size_t)(N + 1) * NX * 8, cudaMemcpyDeviceToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(&s->ring_u[ring * Un * NU], &s->uo[k * Un * NU], (size_t)N * NU * 8, cudaMemcpyDeviceToDevice);
-  if (e != cudaSuccess) return sfail(UCN_ECUDA, "result copy: %s", cudaGetErrorString(e));
-  s->ring_ticket[ring] = ticket;
-  s->ring_N[ring] = N;
-  res->ticket = ticket;
-  res->horizon = N;
-  s->slot_state[k] = SLOT_FREE;
-  s->used -= s->slot_bytes[k];
-  s->ticket_slot.erase(it);
+  if (!delivered(s, k)) {
+    if (s->slot_state[k] == SLOT_RUNNING) {
+      const int l = s->slot_lane[k];
+      if (lane_ended(s, l) && !delivered(s, k) && s->lane_error[l] != cudaSuccess)
+        return sfail(UCN_ECUDA, "serve launch failed: %s", cudaGetErrorString(s->lane_error[l]));
+    }
+    return UCN_EBUSY;                 // admitted and not launched yet, or still solving
+  }
+  take_result(s, k, res);
   return UCN_OK;
+}
+
+ucn_status ucn_serve_poll_any(ucn_server* s, ucn_result* res) {
+  set_error_message("");
+  if (!s || !res) return sfail(UCN_EINVAL, "null argument");
+  std::lock_guard<std::mutex> lk(s->mu);
+  for (int k = 0; k < s->S; ++k)
+    if (delivered(s, k)) {
+      take_result(s, k, res);
+      return UCN_OK;
+    }
+  // nothing delivered: retire the lanes whose launches ended (their ring entries
+  // become kept) and report a failed launch
+  for (int l = 0; l < s->lanes; ++l)
+    if (lane_ended(s, l) && s->lane_error[l] != cudaSuccess)
+      return sfail(UCN_ECUDA, "serve launch failed: %s", cudaGetErrorString(s->lane_error[l]));
+  return UCN_EBUSY;
 }
 
 int ucn_serve_free_slots(ucn_server* s) {
   if (!s) return -1;
   std::lock_guard<std::mutex> lk(s->mu);
+  retire_ended(s);
   int n = 0;
   for (int v : s->slot_state) n += (v == SLOT_FREE);
   return n;

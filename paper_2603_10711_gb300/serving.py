@@ -56,6 +56,8 @@ def _setup(L):
     L.ucn_serve_pump.restype = C.c_int
     L.ucn_serve_poll.argtypes = [vp, C.c_ulonglong, C.POINTER(Result)]
     L.ucn_serve_poll.restype = C.c_int
+    L.ucn_serve_poll_any.argtypes = [vp, C.POINTER(Result)]
+    L.ucn_serve_poll_any.restype = C.c_int
     L.ucn_serve_free_slots.argtypes = [vp]
     L.ucn_serve_free_slots.restype = C.c_int
     L._serve_ready = True
@@ -77,7 +79,7 @@ class Server:
         c.scp_iters, c.admm_iters, c.stop = int(s["scp_iters"]), int(s["admm_iters"]), int(s.get("stop", 0))
         c.tr_init, c.tr_min, c.tr_max, c.w_d = float(s["tr_init"]), float(s["tr_min"]), float(s["tr_max"]), float(s["w_d"])
         c.defect_tol, c.step_tol, c.timeout_s = float(s["defect_tol"]), float(s["step_tol"]), float(timeout_s)
-        self.model = model
+        self.model, self.max_horizon = model, max_horizon
         self.nx, self.nu = {1: (12, 4), 2: (7, 3), 3: (13, 4), 4: (14, 3)}[model]
         self.h = C.c_void_p()
         rc = self.L.ucn_serve_create(C.byref(c), C.byref(self.h))
@@ -154,6 +156,26 @@ class Server:
         st = np.frombuffer(bytes(res.stats), dtype=ucn.STATS_DTYPE)[0]
         return rc, {"ticket": int(res.ticket), "horizon": int(res.horizon), "stats": st, "x": x, "u": u}
 
+    def poll_any(self, trajectories=False):
+        """(status, ticket, result dict) of some finished request; status
+        UCN_EBUSY (and None, None) when none has finished.  The dict holds
+        "stats", and "x", "u" when `trajectories`."""
+        res = Result()
+        x = u = None
+        if trajectories:
+            x = np.zeros((self.max_horizon + 1, self.nx)); u = np.zeros((self.max_horizon, self.nu))
+            res.x, res.u = x.ctypes.data_as(_dp), u.ctypes.data_as(_dp)
+        rc = self.L.ucn_serve_poll_any(self.h, C.byref(res))
+        if rc == ucn.UCN_EBUSY:
+            return rc, None, None
+        if rc != ucn.UCN_OK:
+            raise ucn.UcnError(rc, ucn.ucn_last_error())
+        out = {"stats": np.frombuffer(bytes(res.stats), dtype=ucn.STATS_DTYPE)[0]}
+        if trajectories:
+            N = int(res.horizon)
+            out["x"], out["u"] = x[:N + 1].copy(), u[:N].copy()
+        return rc, int(res.ticket), out
+
     def free_slots(self):
         return int(self.L.ucn_serve_free_slots(self.h))
 
@@ -163,35 +185,46 @@ def run_stream(stream, servers, max_inflight=None, time_scale=1.0):
     (dict model -> Server) in real time.  max_inflight=1 gives the one-at-a-time
     (per-request) path.  Returns latencies and throughput."""
     pending = deque(sorted(stream, key=lambda r: r[0]))
-    waiting = deque()
+    waiting = {m: deque() for m in servers}     # arrived, not yet admitted, per server (FIFO)
     inflight = {}
-    lat, defects = [], []
+    lat, defects, models = [], [], []
     n = len(pending)
     t0 = time.perf_counter()
     while len(lat) < n:
         now = (time.perf_counter() - t0) / time_scale
         while pending and pending[0][0] <= now:
-            waiting.append(pending.popleft())
-        while waiting and (max_inflight is None or len(inflight) < max_inflight):
-            arr, p = waiting[0]
-            srv = servers[p.model]
-            rc, ticket = srv.submit(p)
-            if rc == ucn.UCN_EBUSY:
-                break
-            waiting.popleft()
-            inflight[(p.model, ticket)] = (arr, int(p.N[0]))
+            arr, p = pending.popleft()
+            waiting[p.model].append((arr, p))
+        for m, q in waiting.items():
+            # admit in arrival order per server; a full server does not hold up the others
+            while q and (max_inflight is None or len(inflight) < max_inflight):
+                arr, p = q[0]
+                rc, ticket = servers[m].submit(p)
+                if rc == ucn.UCN_EBUSY:
+                    break
+                q.popleft()
+                inflight[(p.model, ticket)] = (arr, int(p.N[0]))
         for srv in servers.values():
             srv.pump()
-        for key in list(inflight):
-            model, ticket = key
-            rc, res = servers[model].poll(ticket, trajectories=False)
-            if rc == ucn.UCN_OK:
-                arr, N = inflight.pop(key)
+        for model, srv in servers.items():
+            # every request finished since the last pass (one call each)
+            while True:
+                rc, ticket, res = srv.poll_any()
+                if rc != ucn.UCN_OK:
+                    break
+                arr, N = inflight.pop((model, ticket))
                 lat.append((time.perf_counter() - t0) / time_scale - arr)
                 defects.append(float(res["stats"]["defect"]))
+                models.append(model)
     elapsed = time.perf_counter() - t0
     lat = np.array(lat)
     d = np.array(defects)
-    return {"completed": n, "elapsed_s": elapsed, "solves_per_s": float(np.sum(d <= 1e-5)) / elapsed,
-            "requests_per_s": n / elapsed, "pass_rate": float(np.mean(d <= 1e-5)),
-            "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99))}
+    models = np.array(models)
+    out = {"completed": n, "elapsed_s": elapsed, "solves_per_s": float(np.sum(d <= 1e-5)) / elapsed,
+           "requests_per_s": n / elapsed, "pass_rate": float(np.mean(d <= 1e-5)),
+           "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99))}
+    for m in np.unique(models):
+        lm = lat[models == m]
+        out["model%d" % m] = {"requests": int(lm.size), "p50_ms": 1e3 * float(np.percentile(lm, 50)),
+                              "p99_ms": 1e3 * float(np.percentile(lm, 99))}
+    return out

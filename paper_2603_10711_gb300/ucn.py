@@ -94,6 +94,8 @@ def lib():
             L.ucn_state_export.restype = C.c_int
             L.ucn_scp_solve.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
             L.ucn_scp_solve.restype = C.c_int
+            L.ucn_scp_solve_warm.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp]
+            L.ucn_scp_solve_warm.restype = C.c_int
             L.ucn_mpc_shift.argtypes = [vp, vp, vp, vp, vp, vp]
             L.ucn_mpc_shift.restype = C.c_int
             L.ucn_scp_solve_noalloc.argtypes = [C.POINTER(ProblemDesc), vp, vp, vp, vp, vp, vp, vp]
@@ -257,6 +259,17 @@ def ucn_scp_solve(h, x0, u0, x_out, u_out, stats, status, stream=None):
                                _ptr(status, torch.int32, name="status"), _stream(stream)))
 
 
+def ucn_scp_solve_warm(h, x0, u0, state, x_out, u_out, stats, status, stream=None):
+    """ucn_scp_solve started from an exported ADMM state (``state``: float64,
+    ucn_state_size elements)."""
+    import torch
+    f = torch.float64
+    _check(lib().ucn_scp_solve_warm(h, _ptr(x0, f, name="x0"), _ptr(u0, f, name="u0"),
+                                    _ptr(state, f, ucn_state_size(h), "state"), _ptr(x_out, f, name="x_out"),
+                                    _ptr(u_out, f, name="u_out"), _ptr(stats, torch.uint8, name="stats"),
+                                    _ptr(status, torch.int32, name="status"), _stream(stream)))
+
+
 def ucn_mpc_shift(h, x, u, xg, ug, stream=None):
     """Apply the (shared) first control to the plant and shift the solution
     into the next warm start; updates the problem's initial states."""
@@ -327,11 +340,15 @@ class Solver:
         import torch
         return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype or torch.float64, device=self.device)
 
-    def scp_solve(self, x0=None, u0=None, stream=None):
-        """Launch the fused SCP kernel; returns the output tensors (not synchronised)."""
+    def scp_solve(self, x0=None, u0=None, stream=None, state=None):
+        """Launch the fused SCP kernel (from the ADMM ``state`` when given: a
+        warm start); returns the output tensors (not synchronised)."""
         x0 = self.tensor(self.prob.xguess) if x0 is None else x0
         u0 = self.tensor(self.prob.uguess) if u0 is None else u0
-        ucn_scp_solve(self.handle, x0, u0, self.x_out, self.u_out, self.stats, self.status, stream)
+        if state is None:
+            ucn_scp_solve(self.handle, x0, u0, self.x_out, self.u_out, self.stats, self.status, stream)
+        else:
+            ucn_scp_solve_warm(self.handle, x0, u0, state, self.x_out, self.u_out, self.stats, self.status, stream)
         return self.x_out, self.u_out
 
     def mpc_shift(self, x=None, u=None, stream=None):

@@ -375,3 +375,52 @@ def test_pair_layout_is_refused_where_it_does_not_apply():
         solve_with_lanes(W.mars_batch(1, seed=1, N=112), 2)      # 113 nodes: beyond the pair kernel's CTA
     with pytest.raises(ucn.UcnError):
         solve_with_lanes(W.quad_path(1, seed=0, N=20), 2)
+
+
+# ------------------------------------------------------------------ warm start from a kept ADMM state
+def shifted(prob, dr):
+    """The same instances with the initial position moved by dr (non-dimensional)."""
+    q = prob.subset(np.arange(prob.batch))
+    q.xinit = q.xinit.copy()
+    q.xinit[:, 0:3] += dr
+    return q
+
+
+@pytest.mark.parametrize("prec,tol", [(ucn.UCN_PREC_FP64, TOL64), (ucn.UCN_PREC_FP32_REFINE, TOL32)])
+def test_warm_start_from_kept_state_matches_oracle(prec, tol):
+    # solve, keep the final ADMM state and trajectory, then solve from that state (at
+    # the schedule's final penalties): (1) the problem with its initial position moved
+    # (the next request of a stream, or the next MPC step) against the oracle started
+    # from the same state and guess; (2) the same problem again, which stops at once,
+    # in fewer SCP iterations than a start from the kept trajectory alone
+    prob = W.mars_batch(4, seed=11, N=60)
+    s = ucn.Solver(prob, precision=prec)
+    x1, u1 = s.scp_solve()
+    state = s.state_export()
+    torch.cuda.synchronize()
+    x1h, u1h = x1.cpu().numpy().copy(), u1.cpu().numpy().copy()
+    s.close()
+    p2 = shifted(prob, np.array([0.005, -0.003, 0.002]))
+    s2 = ucn.Solver(p2, precision=prec)
+    xg, ug = s2.tensor(x1h), s2.tensor(u1h)
+    xw, uw = s2.scp_solve(xg, ug, state=state)
+    torch.cuda.synchronize()
+    xw, uw, stw = xw.cpu().numpy(), uw.cpu().numpy(), s2.stats_host()
+    s2.close()
+    xr, ur, sr = oracle.scp_solve_warm(p2, state.cpu().numpy(), xguess=x1h, uguess=u1h)
+    np.testing.assert_array_equal(stw["scp_iters"], sr[:, 7].astype(int))
+    for b in range(p2.batch):
+        xo, uo, N = p2.xoff[b], p2.uoff[b], int(p2.N[b])
+        assert rel_err(xw[xo:xo + N + 1], xr[xo:xo + N + 1]) <= tol, (b, rel_err(xw[xo:xo + N + 1], xr[xo:xo + N + 1]))
+        assert rel_err(uw[uo:uo + N], ur[uo:uo + N]) <= tol, b
+    s3 = ucn.Solver(prob, precision=prec)
+    xg, ug = s3.tensor(x1h), s3.tensor(u1h)
+    s3.scp_solve(xg, ug, state=state)
+    torch.cuda.synchronize()
+    st_state = s3.stats_host()
+    s3.scp_solve(xg, ug)                  # the kept trajectory alone (cold ADMM state)
+    torch.cuda.synchronize()
+    st_traj = s3.stats_host()
+    s3.close()
+    assert (st_state["defect"] <= 1e-5).all() and (st_state["status"] == 0).all()
+    assert st_state["scp_iters"].mean() < st_traj["scp_iters"].mean(), (st_state["scp_iters"], st_traj["scp_iters"])

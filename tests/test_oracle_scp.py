@@ -185,3 +185,36 @@ def test_batch_comparison_reruns_instances_that_stopped_elsewhere():
     assert list(r["mismatch"]) == [1] and r["summary"]["max_rel_err"] == 0.0
     # ... whereas against the stop-test solve it differs
     assert oracle.rel_err(xs, ref[0]) > 0.0
+
+
+def cold_state(prob):
+    """The flat ADMM state of the cold start: x = x-hat = z = the guess, u = u-hat,
+    zero duals and mirrors (the mirrors are re-projected at the first iteration)."""
+    mb = oracle.maxblk(prob)
+    parts = []
+    for b in range(prob.batch):
+        N = int(prob.N[b])
+        xb, ub = instance(prob, prob.xguess, prob.uguess, b)
+        st = np.zeros(oracle.state_size(N, prob.nx, prob.nu, mb))
+        S = oracle.unpack_state(st, N, prob.nx, prob.nu, mb)
+        S["x"][:] = xb; S["xh"][:] = xb; S["z"][1:] = xb[1:]; S["u"][:] = ub; S["uh"][:] = ub
+        parts.append(st)
+    return np.concatenate(parts)
+
+
+def test_warm_start_from_the_cold_state_is_the_cold_solve():
+    # the state plumbing: starting from the state the cold start builds gives the cold
+    # solve bit for bit (variables in the flat layout's order, mirrors re-projected); a
+    # warm start keeps the schedule's final penalties, so a scheduled problem is compared
+    # with its cold solve at those penalties throughout
+    for prob in (W.mars_batch(2, seed=3, N=30), W.quad_path(1, seed=1, N=15, settings=dict(scp_iters=5, admm_iters=60))):
+        const = prob.subset(np.arange(prob.batch))
+        st_ = const.settings
+        if st_.get("rho_final", 0.0) > 0:
+            f = st_["rho_final"] / st_["rho_geo"]
+            st_.update(rho_eq=st_["rho_eq"] * f, rho_dyn=st_["rho_dyn"] * f, rho_geo=st_["rho_geo"] * f, rho_final=0.0)
+        x, u, st, _ = oracle.scp_solve(const)
+        xw, uw, sw = oracle.scp_solve_warm(prob, cold_state(prob))
+        np.testing.assert_array_equal(xw, x)
+        np.testing.assert_array_equal(uw, u)
+        np.testing.assert_array_equal(sw[:, 7], st[:, 7])
