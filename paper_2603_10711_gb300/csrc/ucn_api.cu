@@ -29,13 +29,6 @@ ucn_status fail(ucn_status s, const char* fmt, ...) {
   return s;
 }
 
-// Host-side fault injection: UCN_FAULT_ALLOC=n makes the n-th device
-// allocation of a ucn_problem_create call fail (1-based).
-int fault_alloc_at() {
-  const char* e = std::getenv("UCN_FAULT_ALLOC");
-  return e ? std::atoi(e) : 0;
-}
-
 long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
 
 }  // namespace
@@ -43,6 +36,11 @@ long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
 namespace ucn {
 
 void set_error_message(const char* msg) { snprintf(g_err, sizeof(g_err), "%s", msg); }
+
+int fault_alloc_at() {
+  const char* e = std::getenv("UCN_FAULT_ALLOC");
+  return e ? std::atoi(e) : 0;
+}
 
 bool tpn_allowed(int tpn, int model, int nodes, int precision, bool smem) {
   if (tpn == 1) return true;

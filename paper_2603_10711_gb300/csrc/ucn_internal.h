@@ -15,6 +15,11 @@ struct Layout;
 // Sets the thread-local message returned by ucn_last_error (ucn_api.cu).
 void set_error_message(const char* msg);
 
+// Host-side fault injection: with UCN_FAULT_ALLOC=n in the environment the
+// n-th device or pinned allocation (1-based) of a ucn_problem_create or
+// ucn_serve_create call fails as if the memory were exhausted; 0 when unset.
+int fault_alloc_at();
+
 // Node-record layout of one instance for a kernel with `tpn` threads per node
 // (defined in ucn_api.cu).
 Layout make_layout(int model, int nodes, int max_obs, int tsize, bool reg_mats, int tpn);

@@ -58,6 +58,8 @@ struct ProblemDev {
   long long res_stride;
 };
 
+static_assert(sizeof(ucn_scp_stats) == 16 * sizeof(double), "a result record starts with 16 doubles of stats");
+
 // The end of a fused solve with result delivery: every thread copies its share
 // of the instance's x and u (just written to xout, uout by this CTA) into the
 // mapped host record and fences them system-wide, then one thread copies the
@@ -1887,6 +1889,36 @@ __device__ __forceinline__ typename Node<T, AOS>::W node_cost(const Node<T, AOS>
 // path, whose sums are reduced in double-float and handed over as doubles.
 
 // Start of a solve: c_i = RK4(xbar_i, ubar_i) - xbar_{i+1} and J(nominal) in sh.Jn.
+// Input check of one instance, by all threads of its CTA (after sh.fail is
+// cleared, before the first factorisation): a NaN anywhere in its data or
+// guesses, or an infinity where only finite values have a meaning (everything
+// but the state and control bounds and the set parameters, where +-inf means
+// "no bound"), sets sh.fail, so the solve stops after its first factorisation
+// with UCN_ENUMERIC instead of iterating on garbage.  Other instances of the
+// launch are not touched.
+template <class M>
+__device__ void flag_bad_inputs(const ProblemDev& P, int b, const double* x0, const double* u0, long long xo,
+                                long long uo, InstShared& sh) {
+  const int nx = P.nx, nu = P.nu, N = P.N[b];
+  const int no = IsQuad<M>::value ? nobs_of(P, b) : 0;
+  struct Span { const double* p; int n; bool finite; };
+  const Span sp[] = {
+      {P.dt + b, 1, true}, {P.params + 8 * b, 8, true}, {P.Qd + b * nx, nx, true}, {P.xref + b * nx, nx, true},
+      {P.Rd + b * nu, nu, true}, {P.uref + b * nu, nu, true}, {P.QNd + b * nx, nx, true}, {P.qN + b * nx, nx, true},
+      {P.xinit + b * nx, nx, true}, {P.xtarget + b * nx, nx, true}, {P.xlo + b * nx, nx, false},
+      {P.xhi + b * nx, nx, false}, {P.ulo + b * nu, nu, false}, {P.uhi + b * nu, nu, false},
+      {P.sets + b * UCN_SET_PARAMS, UCN_SET_PARAMS, false}, {x0 + xo * nx, (N + 1) * nx, true},
+      {u0 + uo * nu, N * nu, true}, {P.obs_c + (long long)b * P.max_obs * 3, 3 * no, true},
+      {P.obs_r + (long long)b * P.max_obs, no, true}};
+  bool bad = false;
+  for (const Span& q : sp)
+    for (int e = threadIdx.x; e < q.n; e += blockDim.x) {
+      const double v = q.p[e];
+      bad |= q.finite ? !isfinite(v) : isnan(v);
+    }
+  if (bad) atomicOr(&sh.fail, 1);
+}
+
 template <class M, class T, bool AOS>
 __device__ void scp_start(const Node<T, AOS>& nd, const ProblemDev& P, const Inst<T>& I, int b, bool act,
                           InstShared& sh) {
@@ -2142,6 +2174,7 @@ __global__ void __launch_bounds__(MAX_THREADS) scp_kernel(ProblemDev P, Layout L
   stage_consts<M, T, AOS>(nd, P, b);
   if (active) load_nominal<M, T, AOS>(nd, L, x0, u0, xo, uo);
   __syncthreads();
+  flag_bad_inputs<M>(P, b, x0, u0, xo, uo, sh);
   scp_start<M, T, AOS>(nd, P, I, b, active, sh);
   if (active) node_start<M, T, AOS>(nd, L, P, b);
   __syncthreads();

@@ -14,6 +14,11 @@
 namespace ucn {
 
 constexpr int LANES_MAX_THREADS = 512;   // CTA size cap of the lane kernel
+// CTA size cap of its wide-register variant: __launch_bounds__(384, 1) lets a
+// thread hold 168 registers (65,536 / 384, allocation granularity), which the
+// 16-row node state needs to stay out of local memory; the launcher takes it
+// whenever it keeps as many CTAs per SM resident as the other variant.
+constexpr int LANES_WIDE_THREADS = 384;
 constexpr unsigned WARP_ALL = 0xffffffffu;
 
 template <class M, int TPN>
@@ -521,11 +526,12 @@ __device__ __forceinline__ Node<T, SMEM> make_node_at(const ProblemDev& P, const
   return nd;
 }
 
-// The fused SCP solve (as scp_kernel) with TPN lanes per node.
+// The fused SCP solve (as scp_kernel) with TPN lanes per node: the body of the
+// two kernels below.
 template <class M, class T, bool SMEM, bool REFINE, bool GROUP, int TPN>
-__global__ void __launch_bounds__(LANES_MAX_THREADS) scp_kernel_lanes(ProblemDev P, Layout L, const double* x0,
-                                                                      const double* u0, double* xout, double* uout,
-                                                                      ucn_scp_stats* stats, int* status_out) {
+__device__ __forceinline__ void scp_lanes_body(const ProblemDev& P, const Layout& L, const double* x0,
+                                               const double* u0, double* xout, double* uout, ucn_scp_stats* stats,
+                                               int* status_out) {
   using LR = LaneRows<M, TPN>;
   constexpr int NX = M::NX, NU = M::NU, NN = NX + NU, R = LR::R;
   static_assert(!GROUP || NU <= 4, "GroupShared holds nu <= 4");
@@ -573,6 +579,7 @@ __global__ void __launch_bounds__(LANES_MAX_THREADS) scp_kernel_lanes(ProblemDev
   stage_consts<M, T, AOS>(ndd, P, b);
   if (dact) load_nominal<M, T, AOS>(ndd, L, x0, u0, xo, uo);
   __syncthreads();
+  flag_bad_inputs<M>(P, b, x0, u0, xo, uo, sh);
   scp_start<M, T, AOS>(ndd, P, I, b, dact, sh);
   if (dact) node_start<M, T, AOS>(ndd, L, P, b);
   __syncthreads();
@@ -657,6 +664,30 @@ __global__ void __launch_bounds__(LANES_MAX_THREADS) scp_kernel_lanes(ProblemDev
   __syncthreads();
   deliver_result(P, b, xout, uout, stats);
   if constexpr (GROUP) group_finish(P);
+}
+
+// CTAs of up to 512 threads; the compiler chooses the registers (128 at most).
+template <class M, class T, bool SMEM, bool REFINE, bool GROUP, int TPN>
+__global__ void __launch_bounds__(LANES_MAX_THREADS) scp_kernel_lanes(ProblemDev P, Layout L, const double* x0,
+                                                                      const double* u0, double* xout, double* uout,
+                                                                      ucn_scp_stats* stats, int* status_out) {
+  scp_lanes_body<M, T, SMEM, REFINE, GROUP, TPN>(P, L, x0, u0, xout, uout, stats, status_out);
+}
+
+// CTAs of up to 384 threads, one resident per SM guaranteed its registers (168).
+template <class M, class T, bool SMEM, bool REFINE, bool GROUP, int TPN>
+__global__ void __launch_bounds__(LANES_WIDE_THREADS, 1) scp_kernel_lanes_wide(ProblemDev P, Layout L,
+                                                                               const double* x0, const double* u0,
+                                                                               double* xout, double* uout,
+                                                                               ucn_scp_stats* stats, int* status_out) {
+  scp_lanes_body<M, T, SMEM, REFINE, GROUP, TPN>(P, L, x0, u0, xout, uout, stats, status_out);
+}
+
+// The kernel of register class MAXT (LANES_WIDE_THREADS or LANES_MAX_THREADS).
+template <class M, class T, bool SMEM, bool REFINE, bool GROUP, int TPN, int MAXT>
+constexpr auto lanes_kernel() {
+  if constexpr (MAXT == LANES_WIDE_THREADS) return scp_kernel_lanes_wide<M, T, SMEM, REFINE, GROUP, TPN>;
+  else return scp_kernel_lanes<M, T, SMEM, REFINE, GROUP, TPN>;
 }
 
 }  // namespace ucn

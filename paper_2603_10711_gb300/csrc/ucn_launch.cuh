@@ -23,21 +23,64 @@ cudaError_t launch_scp_v(const LaunchCfg& c, const double* x0, const double* u0,
   return cudaGetLastError();
 }
 
-// The lane kernel (4 threads per node; quadrotor).
+// The lane kernel (4 threads per node; quadrotor), one register class per
+// variant (MAXT: LANES_WIDE_THREADS or LANES_MAX_THREADS): set-up, occupancy
+// and launch, explicitly instantiated in one translation unit per variant.
+template <class M, class T, bool SMEM, bool R, int MAXT>
+struct LanesVariant {
+  static auto kernel() { return lanes_kernel<M, T, SMEM, R, false, 4, MAXT>(); }
+  // CTAs of `threads` threads and the layout's shared memory resident per SM (0: none)
+  static cudaError_t occupancy(const LaunchCfg& c, int threads, int* blocks) {
+    *blocks = 0;
+    if (threads > MAXT) return cudaSuccess;
+    auto k = kernel();
+    if (SMEM) {
+      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem_bytes);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k, threads, SMEM ? c.smem_bytes : 0);
+  }
+  static cudaError_t launch(const LaunchCfg& c, int threads, const double* x0, const double* u0, double* xo,
+                            double* uo, ucn_scp_stats* st, int* status) {
+    const ProblemDev& P = *(const ProblemDev*)c.P;
+    const Layout& L = *(const Layout*)c.L;
+    if (threads > MAXT) return cudaErrorInvalidConfiguration;
+    auto k = kernel();
+    if (SMEM) {
+      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem_bytes);
+      if (e != cudaSuccess) return e;
+    }
+    k<<<c.blocks, threads, SMEM ? c.smem_bytes : 0, c.stream>>>(P, L, x0, u0, xo, uo, st, status);
+    return cudaGetLastError();
+  }
+};
+
+// Whether the wide-register variant keeps at least as many CTAs of this launch
+// resident per SM as the 128-register one (then it runs without the spills).
+template <class Wide, class Narrow>
+cudaError_t lanes_prefer_wide(const LaunchCfg& c, int threads, bool* wide) {
+  *wide = false;
+  if (threads > LANES_WIDE_THREADS) return cudaSuccess;
+  int bw = 0, bn = 0;
+  cudaError_t e = Wide::occupancy(c, threads, &bw);
+  if (e == cudaSuccess) e = Narrow::occupancy(c, threads, &bn);
+  if (e != cudaSuccess) return e;
+  *wide = bw > 0 && bw >= bn;
+  return cudaSuccess;
+}
+
 template <class M, class T, bool SMEM, bool R>
 cudaError_t launch_scpl_v(const LaunchCfg& c, const double* x0, const double* u0, double* xo, double* uo,
                           ucn_scp_stats* st, int* status) {
-  const ProblemDev& P = *(const ProblemDev*)c.P;
-  const Layout& L = *(const Layout*)c.L;
-  auto k = scp_kernel_lanes<M, T, SMEM, R, false, 4>;
-  if (SMEM) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem_bytes);
-    if (e != cudaSuccess) return e;
-  }
+  using Wide = LanesVariant<M, T, SMEM, R, LANES_WIDE_THREADS>;
+  using Narrow = LanesVariant<M, T, SMEM, R, LANES_MAX_THREADS>;
   const int threads = (4 * c.nodes + 31) / 32 * 32;
   if (threads > LANES_MAX_THREADS) return cudaErrorInvalidConfiguration;
-  k<<<c.blocks, threads, SMEM ? c.smem_bytes : 0, c.stream>>>(P, L, x0, u0, xo, uo, st, status);
-  return cudaGetLastError();
+  bool wide = false;
+  cudaError_t e = lanes_prefer_wide<Wide, Narrow>(c, threads, &wide);
+  if (e != cudaSuccess) return e;
+  return wide ? Wide::launch(c, threads, x0, u0, xo, uo, st, status)
+              : Narrow::launch(c, threads, x0, u0, xo, uo, st, status);
 }
 
 // The pair kernel (2 threads per node; 3-DOF Mars, FP32, records in shared memory).
@@ -73,11 +116,32 @@ cudaError_t launch_scp_t(const LaunchCfg& c, const double* x0, const double* u0,
                 : launch_scp_v<M, T, false, R>(c, x0, u0, xo, uo, st, status);
 }
 
-// The group kernel of the lane layout (its own translation unit: defined there).
+// The group kernels of the lane layout, one per register class (each in its
+// own translation unit: defined there).
 template <class M, class T, bool R>
 using ScpKernelPtr = void (*)(ProblemDev, Layout, const double*, const double*, double*, double*, ucn_scp_stats*, int*);
-template <class M, class T, bool R>
+template <class M, class T, bool R, int MAXT>
 ScpKernelPtr<M, T, R> scp_group_lanes();
+
+// The group lane kernel for CTAs of `threads` threads: the wide-register
+// variant when it keeps as many CTAs resident per SM.
+template <class M, class T, bool R>
+cudaError_t pick_group_lanes(const LaunchCfg& c, int threads, ScpKernelPtr<M, T, R>* out) {
+  auto kw = scp_group_lanes<M, T, R, LANES_WIDE_THREADS>();
+  auto kn = scp_group_lanes<M, T, R, LANES_MAX_THREADS>();
+  *out = kn;
+  if (threads > LANES_WIDE_THREADS) return cudaSuccess;
+  int bw = 0, bn = 0;
+  for (auto k : {kw, kn}) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem_bytes);
+    if (e != cudaSuccess) return e;
+  }
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bw, kw, threads, c.smem_bytes);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bn, kn, threads, c.smem_bytes);
+  if (e != cudaSuccess) return e;
+  if (bw > 0 && bw >= bn) *out = kw;
+  return cudaSuccess;
+}
 
 // Scenario groups: thread-block clusters of c.group CTAs (records in shared
 // memory only), P.gclusters clusters per group.  cudaErrorInvalidClusterSize
@@ -89,10 +153,15 @@ cudaError_t launch_scp_group_t(const LaunchCfg& c, const double* x0, const doubl
   const ProblemDev& P = *(const ProblemDev*)c.P;
   const Layout& L = *(const Layout*)c.L;
   if (!c.smem || c.group < 1 || c.group > 16 || c.blocks % c.group) return cudaErrorInvalidClusterSize;
-  auto k = c.tpn == 4 ? scp_group_lanes<M, T, R>() : scp_kernel<M, T, true, R, true>;
   const int threads = c.tpn == 4 ? (4 * c.nodes + 31) / 32 * 32 : c.threads;
   if (threads > LANES_MAX_THREADS) return cudaErrorInvalidConfiguration;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem_bytes);
+  ScpKernelPtr<M, T, R> k = scp_kernel<M, T, true, R, true>;
+  cudaError_t e = cudaSuccess;
+  if (c.tpn == 4) {
+    e = pick_group_lanes<M, T, R>(c, threads, &k);
+    if (e != cudaSuccess) return e;
+  }
+  e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem_bytes);
   if (e != cudaSuccess) return e;
   if (c.group > 8) {
     e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
@@ -197,18 +266,15 @@ cudaError_t launch_linearize_t(const void* Pv, const int* node_inst, long long t
 #define UCN_EXTERN_SCP(MODEL, T, SMEM, REFINE) extern template UCN_SCP_V(MODEL, T, SMEM, REFINE);
 #define UCN_EXTERN_ADMM(MODEL, T, SMEM, REFINE) extern template UCN_ADMM_V(MODEL, T, SMEM, REFINE);
 
-// Lane-kernel variants, each in its own translation unit.
-#define UCN_SCPL_V(MODEL, T, SMEM, REFINE)                                                                 \
-  cudaError_t ucn::launch_scpl_v<ucn::MODEL, T, SMEM, REFINE>(const ucn::LaunchCfg&, const double*,      \
-                                                              const double*, double*, double*,           \
-                                                              ucn_scp_stats*, int*)
-#define UCN_INSTANTIATE_SCPL(MODEL, T, SMEM, REFINE) template UCN_SCPL_V(MODEL, T, SMEM, REFINE);
-#define UCN_EXTERN_SCPL(MODEL, T, SMEM, REFINE) extern template UCN_SCPL_V(MODEL, T, SMEM, REFINE);
-#define UCN_DEFINE_GROUP_LANES(MODEL, T, REFINE)                                                           \
+// Lane-kernel variants (records in shared or global memory, register class
+// MAXT), each in its own translation unit.
+#define UCN_INSTANTIATE_SCPL(MODEL, T, SMEM, REFINE, MAXT) template struct ucn::LanesVariant<ucn::MODEL, T, SMEM, REFINE, MAXT>;
+#define UCN_EXTERN_SCPL(MODEL, T, SMEM, REFINE, MAXT) extern template struct ucn::LanesVariant<ucn::MODEL, T, SMEM, REFINE, MAXT>;
+#define UCN_DEFINE_GROUP_LANES(MODEL, T, REFINE, MAXT)                                                     \
   namespace ucn {                                                                                          \
   template <>                                                                                              \
-  ScpKernelPtr<MODEL, T, REFINE> scp_group_lanes<MODEL, T, REFINE>() {                                     \
-    return scp_kernel_lanes<MODEL, T, true, REFINE, true, 4>;                                              \
+  ScpKernelPtr<MODEL, T, REFINE> scp_group_lanes<MODEL, T, REFINE, MAXT>() {                               \
+    return lanes_kernel<MODEL, T, true, REFINE, true, 4, MAXT>();                                          \
   }                                                                                                        \
   }
 

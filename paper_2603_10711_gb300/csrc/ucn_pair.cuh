@@ -626,6 +626,7 @@ __global__ void __launch_bounds__(PAIR_MAX_THREADS, 2) scp_kernel_pair(ProblemDe
   stage_consts<M, float, true>(ndd, P, b);
   if (dact) load_nominal<M, float, true>(ndd, L, x0, u0, xo, uo);
   __syncthreads();
+  flag_bad_inputs<M>(P, b, x0, u0, xo, uo, sh);
   scp_start<M, float, true>(ndd, P, I, b, dact, sh);
   if (dact) node_start<M, float, true>(ndd, L, P, b);
   __syncthreads();

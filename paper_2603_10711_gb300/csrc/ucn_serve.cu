@@ -165,6 +165,7 @@ struct ucn_server {
   ucn_serve_config cfg;
   int nx, nu, S, Nmax, max_obs, lanes, MO;
   long long state_per_slot, budget, used;
+  int nalloc = 0, fault_at = 0;   // allocations made by create; UCN_FAULT_ALLOC
   ProblemDev P;
   ServeDev D;
   RecLayout rl;
@@ -206,6 +207,7 @@ namespace {
 
 template <class V>
 bool dalloc(ucn_server* s, V** out, size_t n) {
+  if (++s->nalloc == s->fault_at) return false;
   void* p = nullptr;
   if (cudaMalloc(&p, std::max<size_t>(n * sizeof(V), 16)) != cudaSuccess) { cudaGetLastError(); return false; }
   cudaMemset(p, 0, std::max<size_t>(n * sizeof(V), 16));
@@ -216,6 +218,7 @@ bool dalloc(ucn_server* s, V** out, size_t n) {
 
 template <class V>
 bool halloc(ucn_server* s, V** out, size_t n) {
+  if (++s->nalloc == s->fault_at) return false;
   void* p = nullptr;
   if (cudaMallocHost(&p, std::max<size_t>(n * sizeof(V), 16)) != cudaSuccess) { cudaGetLastError(); return false; }
   std::memset(p, 0, std::max<size_t>(n * sizeof(V), 16));
@@ -227,6 +230,7 @@ bool halloc(ucn_server* s, V** out, size_t n) {
 // Pinned host memory the device writes directly (mapped): host and device views.
 template <class V>
 bool mapped(ucn_server* s, V** host, V** dev, size_t n) {
+  if (++s->nalloc == s->fault_at) return false;
   void* p = nullptr;
   const size_t bytes = std::max<size_t>(n * sizeof(V), 16);
   if (cudaHostAlloc(&p, bytes, cudaHostAllocMapped) != cudaSuccess) { cudaGetLastError(); return false; }
@@ -322,6 +326,7 @@ ucn_status ucn_serve_create(const ucn_serve_config* c, ucn_server** out) {
   if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return sfail(UCN_ECUDA, "no CUDA device"); }
   ucn_server* s = new ucn_server();
   s->cfg = *c;
+  s->fault_at = fault_alloc_at();
   const bool quad = model_obstacles(c->model);
   s->nx = model_nx(c->model); s->nu = model_nu(c->model);
   s->S = c->max_slots; s->Nmax = c->max_horizon; s->max_obs = quad ? c->max_obs : 0; s->lanes = c->lanes;
@@ -383,18 +388,27 @@ ucn_status ucn_serve_create(const ucn_serve_config* c, ucn_server** out) {
     cudaMemcpy(dsoff, so.data(), sizeof(long long) * S, cudaMemcpyHostToDevice);
     cudaMemcpy(dfac, fac.data(), sizeof(double) * fac.size(), cudaMemcpyHostToDevice);
     for (int l = 0; l < s->lanes && ok; ++l) {
+      // each resource is owned by the server as soon as it exists, so a failure
+      // part way leaves nothing for destroy to miss
       cudaStream_t st; cudaEvent_t ev; int* od; double *sh, *sd;
-      ok = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess &&
-           cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess && dalloc(s, &od, cap) &&
-           halloc(s, &sh, (size_t)cap * REC) && dalloc(s, &sd, (size_t)cap * REC);
+      ok = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess;
+      if (ok) s->streams.push_back(st);
+      ok = ok && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess;
+      if (ok) s->done.push_back(ev);
+      ok = ok && dalloc(s, &od, cap) && halloc(s, &sh, (size_t)cap * REC) && dalloc(s, &sd, (size_t)cap * REC);
       if (ok) {
-        s->streams.push_back(st); s->done.push_back(ev); s->order_d.push_back(od);
-        s->stage_h.push_back(sh); s->stage_d.push_back(sd);
+        s->order_d.push_back(od); s->stage_h.push_back(sh); s->stage_d.push_back(sd);
         s->lane_busy.push_back(0); s->lane_error.push_back(cudaSuccess); s->lane_rings.emplace_back();
       }
     }
   }
-  if (!ok) { ucn_serve_destroy(s); return sfail(UCN_ENOMEM, "server allocation failed"); }
+  if (!ok) {
+    const int fa = s->fault_at;
+    const bool injected = fa > 0 && s->nalloc >= fa;
+    ucn_serve_destroy(s);
+    return injected ? sfail(UCN_ENOMEM, "injected allocation failure (UCN_FAULT_ALLOC=%d)", fa)
+                    : sfail(UCN_ENOMEM, "server allocation failed");
+  }
   s->hrec.assign((size_t)S * REC, 0.0);
   ProblemDev& P = s->P;
   std::memset(&P, 0, sizeof(P));
