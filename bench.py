@@ -62,8 +62,8 @@ def mars_mirror_flops():
 # what builds and launches the Mars FP32 fused kernel: its translation unit, the headers
 # it includes and the host code that lays out and launches it
 TRAFFIC_SOURCES = ("include/ucn.h",) + tuple("paper_2603_10711_gb300/csrc/" + f for f in (
-    "ucn_api.cu", "ucn_internal.h", "ucn_kernels.cuh", "ucn_lanes.cuh", "ucn_launch.cuh", "ucn_mars32.cu",
-    "ucn_math.cuh"))
+    "ucn_api.cu", "ucn_df.cuh", "ucn_internal.h", "ucn_kernels.cuh", "ucn_lanes.cuh", "ucn_launch.cuh",
+    "ucn_mars32.cu", "ucn_math.cuh", "ucn_pair.cuh"))
 
 
 def kernel_sources_sha256():
@@ -299,6 +299,7 @@ def run_ours(args, rank, world):
     batching_out = run_batching(args) if (args.batching_batch > 0 and world == 1) else None
     rho_out = run_rho_study(args) if (args.rho_study_batch > 0 and world == 1) else None
     scenario_out = run_scenarios(args) if (args.scenario_steps > 0 and world == 1) else None
+    single_out = run_single_quad(args) if (args.single_solves > 0 and world == 1) else None
 
     flops_ni = flops_per_node_iter(prob.nx, prob.nu, mars_mirror_flops())
     flops_launch = nodeiters / args.steps * flops_ni
@@ -335,6 +336,8 @@ def run_ours(args, rank, world):
         "gpu_launches": args.steps,
         "clocks": clocks,
     }
+    if single_out is not None:
+        out["single_quad"] = single_out
     if serving_out is not None:
         out["serving"] = serving_out
     if scenario_out is not None:
@@ -389,13 +392,42 @@ def run_serving(args):
             "latency": "arrival -> result collected (host clock)"}
 
 
+def run_single_quad(args):
+    """The single quadrotor (12 states, N = 50, 5 obstacles, goal drawn with seed
+    0) in the plain FP64 path with the fixed 15 SCP x 200 ADMM schedule, one
+    instance per launch, timed per solve (CUDA events, after warm-up); the FP32
+    path with refinement on the same problem beside it."""
+    import torch
+    from paper_2603_10711_gb300 import ucn
+    prob = W.quad_path(1, seed=0)
+    out = {"workload": "quad_path_1_N50_obs5", "scp_iters": int(prob.settings["scp_iters"]),
+           "admm_iters": int(prob.settings["admm_iters"]), "solves": args.single_solves}
+    for name, prec in (("fp64_plain", ucn.UCN_PREC_FP64), ("fp32_refine", ucn.UCN_PREC_FP32_REFINE)):
+        s = ucn.Solver(prob, precision=prec)
+        x0, u0 = s.tensor(prob.xguess), s.tensor(prob.uguess)
+        for _ in range(3):
+            s.scp_solve(x0, u0)
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(args.single_solves):
+            e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(); s.scp_solve(x0, u0); e1.record(); e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        st = s.stats_host()
+        s.close()
+        out[name] = {"ms_p50": float(np.percentile(ms, 50)), "ms_p99": float(np.percentile(ms, 99)),
+                     "solves_per_s": 1e3 / float(np.mean(ms)), "defect": float(st["defect"][0]),
+                     "status": int(st["status"][0])}
+    return out
+
+
 def run_batching(args):
     """Uneven-horizon batching: 4096 quadrotors, N ~ U{40..120}, 10-30 obstacles,
     FP32 + refinement.  The autotuner picks the size-class split and threads per
     node on a 608-instance sample; the batch is then solved as one plain launch
     (library defaults) and as the tuned classes replayed from a CUDA graph."""
     import torch
-    from paper_2603_10711_gb300 import batching
+    from paper_2603_10711_gb300 import batching, ucn
     prob = W.quad_box(args.batching_batch, seed=2)
     t0 = time.perf_counter()
     cfg, timings = batching.autotune(prob, cache_path=None)
@@ -417,6 +449,18 @@ def run_batching(args):
         out[name] = {"ms": min(ms), "solves_per_s": passed / (min(ms) / 1e3), "pass_rate": passed / prob.batch,
                      "scp_iters_mean": float(st["scp_iters"].mean())}
         cs.close()
+    # the plain FP64 path on the same batch, one launch (library defaults)
+    s64 = ucn.Solver(prob, precision=ucn.UCN_PREC_FP64)
+    x0, u0 = s64.tensor(prob.xguess), s64.tensor(prob.uguess)
+    s64.scp_solve(x0, u0); torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(); s64.scp_solve(x0, u0); e1.record(); e1.synchronize()
+    ms64 = e0.elapsed_time(e1)
+    st = s64.stats_host()
+    s64.close()
+    passed = int(np.sum(st["defect"] <= 1e-5))
+    out["fp64_plain_single_launch"] = {"ms": ms64, "solves_per_s": passed / (ms64 / 1e3), "pass_rate": passed / prob.batch,
+                                       "scp_iters_mean": float(st["scp_iters"].mean())}
     return out
 
 
@@ -590,9 +634,10 @@ def main():
     ap.add_argument("--rho-study-batch", type=int, default=256, help="quaternion study tasks per setting (0: skip)")
     ap.add_argument("--scenario-problems", type=int, default=256)
     ap.add_argument("--scenario-count", type=int, default=64, help="scenarios per problem (group size)")
-    ap.add_argument("--scenario-steps", type=int, default=3, help="receding-horizon steps (0: skip the section)")
+    ap.add_argument("--scenario-steps", type=int, default=50, help="receding-horizon steps (0: skip the section)")
+    ap.add_argument("--single-solves", type=int, default=20, help="timed solves of the single quadrotor (0: skip)")
     ap.add_argument("--scenario-fp64-problems", type=int, default=64)
-    ap.add_argument("--mode", default="full", choices=["full", "kernel", "scenario", "batching", "rho_study", "serving"],
+    ap.add_argument("--mode", default="full", choices=["full", "kernel", "scenario", "batching", "rho_study", "serving", "single"],
                     help="kernel: time only the fused kernel (profiler captures)")
     ap.add_argument("--scp-iters", type=int, default=0, help="fixed SCP iteration count (0: the workload's cap + stop test)")
     ap.add_argument("--admm-iters", type=int, default=0, help="kernel mode: ADMM iterations per SCP iteration (0: the workload's)")
@@ -617,6 +662,8 @@ def main():
         out = run_rho_study(args)
     elif args.mode == "serving":
         out = run_serving(args)
+    elif args.mode == "single":
+        out = run_single_quad(args)
     elif args.impl == "reference":
         out = run_reference(args, rank, world)
     else:

@@ -1089,13 +1089,15 @@ struct NodeState<M, T, AOS, false> {
   __device__ __forceinline__ void load(const Node<T, AOS>& n) { nd = n; }
   __device__ __forceinline__ void store(const Node<T, AOS>&) const {}
 };
-template <class M, class T, bool AOS>
-using NodeStateFor = NodeState<M, T, AOS, AOS && SmallModel<M>::value && std::is_same<T, float>::value>;
+// REGS: the kernel variant leaves registers for the state (the 3-CTAs-per-SM
+// variant of the one-thread kernel does not).
+template <class M, class T, bool AOS, bool REGS = true>
+using NodeStateFor = NodeState<M, T, AOS, REGS && AOS && SmallModel<M>::value && std::is_same<T, float>::value>;
 
 // Right-hand side g_i of Step 1 (stationarity of Eq. (3) in (x_i, u_i)).
-template <class M, class T, bool AOS, int n, class MS>
+template <class M, class T, bool AOS, int n, class MS, class NS>
 __device__ __forceinline__ void node_rhs(const Node<T, AOS>& nd, const MS& MT, const Layout& L, const Inst<T>& I,
-                                         const NodeConst<M, T>& K, const NodeStateFor<M, T, AOS>& S, T re, T rd, T rg, T* g) {
+                                         const NodeConst<M, T>& K, const NS& S, T re, T rd, T rg, T* g) {
   constexpr int NX = M::NX, NU = M::NU;
   const int i = nd.i;
 #pragma unroll
@@ -1312,12 +1314,12 @@ __device__ void node_reseed(const Node<T, AOS>& nd, const Layout& L, const Inst<
 // group all-reduce combines them, and each CTA sets u-hat_0 to the projection
 // onto {equal u_0} intersected with every box, i.e. the average clamped to the
 // common box, before its Step 4.
-template <class M, class T, bool AOS, bool REFINE, bool LAST, bool GROUP, class MS>
+template <class M, class T, bool AOS, bool REFINE, bool LAST, bool GROUP, class MS, class NS>
 __device__ __forceinline__ void admm_iteration(const Node<T, AOS>& nd, const MS& MT, const Layout& L, const Inst<T>& I,
                                                const NodeConst<M, T>& K, bool active, T re, T rd, T rg,
                                                T irg, T ired, typename WideOf<T>::type& rp,
                                                typename WideOf<T>::type& rdl, GroupShared* G,
-                                               GroupX& X, const ProblemDev& P, const NodeStateFor<M, T, AOS>& S) {
+                                               GroupX& X, const ProblemDev& P, const NS& S) {
   constexpr int NX = M::NX, NU = M::NU, NN = NX + NU;
   const int i = nd.i, N = nd.N;
   constexpr bool last = LAST;
@@ -1482,13 +1484,13 @@ __device__ __forceinline__ void admm_iteration(const Node<T, AOS>& nd, const MS&
 
 // `iters` iterations of Steps 1-4; the primal and dual residuals of the last
 // one are returned, squared, in res[0..1].
-template <class M, class T, bool AOS, bool REFINE, bool GROUP = false, class MS>
+template <class M, class T, bool AOS, bool REFINE, bool GROUP = false, bool REGS = true, class MS>
 __device__ __forceinline__ void admm_iterations(const Node<T, AOS>& nd, const MS& MT, const Layout& L, const Inst<T>& I,
                                 const NodeConst<M, T>& K, bool active, T re, T rd, T rg, int iters,
                                 InstShared& sh, double* res, GroupShared* G, GroupX& X, const ProblemDev& P) {
   const T irg = T(1) / rg, ired = T(1) / (re + rd);
   typename WideOf<T>::type rp{}, rdl{};   // residual sums in the wide type (FP64 or double-float)
-  NodeStateFor<M, T, AOS> S;
+  NodeStateFor<M, T, AOS, REGS> S;
   if (active) S.load(nd);
   for (int it = 0; it + 1 < iters; ++it)
     admm_iteration<M, T, AOS, REFINE, false, GROUP>(nd, MT, L, I, K, active, re, rd, rg, irg, ired, rp, rdl, G, X, P, S);
@@ -2136,9 +2138,12 @@ __device__ __forceinline__ void scp_report(const InstShared& sh, const ProblemDe
 // radius, stopping and the time budget are decided on the group's sums
 // (merits) and maxima (defect, step), so that accepted nominals keep one first
 // control.
-template <class M, class T, bool SMEM, bool REFINE, bool GROUP = false>
-__global__ void __launch_bounds__(MAX_THREADS) scp_kernel(ProblemDev P, Layout L, const double* x0, const double* u0,
-                                                          double* xout, double* uout, ucn_scp_stats* stats, int* status_out) {
+//
+// REGS = false: the ADMM state stays in the node records (the variant that runs
+// three CTAs per SM has no registers for it).
+template <class M, class T, bool SMEM, bool REFINE, bool GROUP, bool REGS>
+__device__ __forceinline__ void scp_body(const ProblemDev& P, const Layout& L, const double* x0, const double* u0,
+                                         double* xout, double* uout, ucn_scp_stats* stats, int* status_out) {
   constexpr int NX = M::NX, NU = M::NU, NN = NX + NU;
   static_assert(!GROUP || NU <= 4, "GroupShared holds nu <= 4");
   extern __shared__ __align__(16) unsigned char smem[];
@@ -2214,7 +2219,7 @@ __global__ void __launch_bounds__(MAX_THREADS) scp_kernel(ProblemDev P, Layout L
       __syncthreads();
     }
     if (sh.fail) { if (threadIdx.x == 0) sh.status = ST_NUMERIC; iters_run++; break; }
-    admm_iterations<M, T, AOS, REFINE, GROUP>(nd, MT, L, I, K, active, re, rd, rg, P.admm_iters, sh, res, G, X, P);
+    admm_iterations<M, T, AOS, REFINE, GROUP, REGS>(nd, MT, L, I, K, active, re, rd, rg, P.admm_iters, sh, res, G, X, P);
     ++iters_run;
     // ---- candidate (x-hat, u-hat): wide rollout, defects, cost, linear model
     W xc[NX], uc[NU], fc[NX];
@@ -2256,6 +2261,26 @@ __global__ void __launch_bounds__(MAX_THREADS) scp_kernel(ProblemDev P, Layout L
   __syncthreads();
   deliver_result(P, b, xout, uout, stats);
   if constexpr (GROUP) group_finish(P);
+}
+
+// The fused solve for CTAs of up to MAX_THREADS threads; the compiler chooses
+// the registers (up to 255: two 4-warp CTAs per SM).
+template <class M, class T, bool SMEM, bool REFINE, bool GROUP = false>
+__global__ void __launch_bounds__(MAX_THREADS) scp_kernel(ProblemDev P, Layout L, const double* x0, const double* u0,
+                                                          double* xout, double* uout, ucn_scp_stats* stats, int* status_out) {
+  scp_body<M, T, SMEM, REFINE, GROUP, true>(P, L, x0, u0, xout, uout, stats, status_out);
+}
+
+// The same solve for CTAs of up to 128 threads, three resident per SM (168
+// registers; the ADMM state in the node records).  Each CTA runs ~1.4x longer
+// than in scp_kernel, so three per SM solve ~7% more instances per unit time;
+// the launcher uses it for the first round of a batch (see launch_scp_v).
+constexpr int SCP3_MAX_THREADS = 128;
+template <class M, class T, bool SMEM, bool REFINE>
+__global__ void __launch_bounds__(SCP3_MAX_THREADS, 3) scp_kernel_3(ProblemDev P, Layout L, const double* x0,
+                                                                  const double* u0, double* xout, double* uout,
+                                                                  ucn_scp_stats* stats, int* status_out) {
+  scp_body<M, T, SMEM, REFINE, false, false>(P, L, x0, u0, xout, uout, stats, status_out);
 }
 
 }  // namespace ucn

@@ -7,6 +7,75 @@
 
 namespace ucn {
 
+// The 3-CTAs-per-SM variant of the one-thread kernel (scp_kernel_3): set-up,
+// occupancy and launch, explicitly instantiated in its own translation unit
+// for the configurations listed in has_scp3.
+template <class M, class T, bool SMEM, bool R>
+constexpr bool has_scp3 = false;
+template <>
+constexpr bool has_scp3<Mars7, float, true, true> = true;
+
+template <class M, class T, bool SMEM, bool R>
+struct Scp3Variant {
+  static cudaError_t occupancy(const LaunchCfg& c, int* blocks);
+  static cudaError_t launch(const LaunchCfg& c, const ProblemDev& P, int blocks, const double* x0, const double* u0,
+                            double* xo, double* uo, ucn_scp_stats* st, int* status);
+};
+// (defined out of the class, so that an extern template declaration keeps the
+// kernel out of the translation units that only launch it)
+template <class M, class T, bool SMEM, bool R>
+cudaError_t Scp3Variant<M, T, SMEM, R>::occupancy(const LaunchCfg& c, int* blocks) {
+  *blocks = 0;
+  if (c.threads > SCP3_MAX_THREADS) return cudaSuccess;
+  auto k = scp_kernel_3<M, T, SMEM, R>;
+  if (SMEM) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem_bytes);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k, c.threads, SMEM ? c.smem_bytes : 0);
+}
+template <class M, class T, bool SMEM, bool R>
+cudaError_t Scp3Variant<M, T, SMEM, R>::launch(const LaunchCfg& c, const ProblemDev& P, int blocks, const double* x0,
+                                               const double* u0, double* xo, double* uo, ucn_scp_stats* st,
+                                               int* status) {
+  const Layout& L = *(const Layout*)c.L;
+  auto k = scp_kernel_3<M, T, SMEM, R>;
+  if (SMEM) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem_bytes);
+    if (e != cudaSuccess) return e;
+  }
+  k<<<blocks, c.threads, SMEM ? c.smem_bytes : 0, c.stream>>>(P, L, x0, u0, xo, uo, st, status);
+  return cudaGetLastError();
+}
+
+// Time of one CTA of scp_kernel_3 (three per SM) over one of scp_kernel (two
+// per SM), measured on the Mars batch (7.2 vs 5.1 ms per instance, GB300).
+constexpr double SCP3_TIME_RATIO = 1.41;
+
+// How many of a launch's CTAs (taken in the launch's order) run as
+// scp_kernel_3 before the rest run as scp_kernel: the split with the shortest
+// modelled time, rounds(k3 on b3 per SM) x SCP3_TIME_RATIO + rounds(rest on b2
+// per SM).  Whole CTAs are resident in rounds, so a batch that is not a whole
+// number of rounds leaves SMs idle in its last one; one round of three CTAs per
+// SM followed by rounds of two fills 1024 CTAs on 152 SMs in 3.4 round-times
+// instead of 4.  0 when the variant keeps no more CTAs resident.
+inline int scp3_split(int B, int sms, int b2, int b3) {
+  if (b3 <= b2 || b2 < 1 || sms < 1) return 0;
+  const long long r2 = (long long)sms * b2, r3 = (long long)sms * b3;
+  auto cost = [&](long long k3) {
+    return (double)((k3 + r3 - 1) / r3) * SCP3_TIME_RATIO + (double)((B - k3 + r2 - 1) / r2);
+  };
+  long long best = 0;
+  double bc = cost(0);
+  for (long long k3 = r3;; k3 += r3) {
+    const long long k = k3 < B ? k3 : B;
+    const double v = cost(k);
+    if (v < bc - 1e-9) { bc = v; best = k; }
+    if (k3 >= B) break;
+  }
+  return (int)best;
+}
+
 // One kernel variant per function, so that a translation unit can leave a
 // variant to another one (extern template) and the slow ones compile in parallel.
 template <class M, class T, bool SMEM, bool R>
@@ -19,7 +88,28 @@ cudaError_t launch_scp_v(const LaunchCfg& c, const double* x0, const double* u0,
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem_bytes);
     if (e != cudaSuccess) return e;
   }
-  k<<<c.blocks, c.threads, SMEM ? c.smem_bytes : 0, c.stream>>>(P, L, x0, u0, xo, uo, st, status);
+  int k3 = 0;
+  if constexpr (has_scp3<M, T, SMEM, R>) {
+    // the first k3 CTAs of the order on the 3-per-SM variant, the rest after them
+    if (P.order && c.threads <= SCP3_MAX_THREADS && c.blocks > 0) {
+      int dev = 0, sms = 0, b2 = 0, b3 = 0;
+      cudaError_t e = cudaGetDevice(&dev);
+      if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, k, c.threads, SMEM ? c.smem_bytes : 0);
+      if (e == cudaSuccess) e = Scp3Variant<M, T, SMEM, R>::occupancy(c, &b3);
+      if (e != cudaSuccess) return e;
+      k3 = scp3_split(c.blocks, sms, b2, b3);
+      if (k3 > 0) {
+        e = Scp3Variant<M, T, SMEM, R>::launch(c, P, k3, x0, u0, xo, uo, st, status);
+        if (e != cudaSuccess) return e;
+      }
+    }
+  }
+  if (k3 >= c.blocks) return cudaSuccess;
+  ProblemDev Pr = P;
+  if (k3 > 0) Pr.order = P.order + k3;
+  k<<<c.blocks - k3, c.threads, SMEM ? c.smem_bytes : 0, c.stream>>>(Pr, L, x0, u0, xo, uo, st, status);
   return cudaGetLastError();
 }
 
@@ -28,32 +118,39 @@ cudaError_t launch_scp_v(const LaunchCfg& c, const double* x0, const double* u0,
 // and launch, explicitly instantiated in one translation unit per variant.
 template <class M, class T, bool SMEM, bool R, int MAXT>
 struct LanesVariant {
-  static auto kernel() { return lanes_kernel<M, T, SMEM, R, false, 4, MAXT>(); }
   // CTAs of `threads` threads and the layout's shared memory resident per SM (0: none)
-  static cudaError_t occupancy(const LaunchCfg& c, int threads, int* blocks) {
-    *blocks = 0;
-    if (threads > MAXT) return cudaSuccess;
-    auto k = kernel();
-    if (SMEM) {
-      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem_bytes);
-      if (e != cudaSuccess) return e;
-    }
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k, threads, SMEM ? c.smem_bytes : 0);
-  }
+  static cudaError_t occupancy(const LaunchCfg& c, int threads, int* blocks);
   static cudaError_t launch(const LaunchCfg& c, int threads, const double* x0, const double* u0, double* xo,
-                            double* uo, ucn_scp_stats* st, int* status) {
-    const ProblemDev& P = *(const ProblemDev*)c.P;
-    const Layout& L = *(const Layout*)c.L;
-    if (threads > MAXT) return cudaErrorInvalidConfiguration;
-    auto k = kernel();
-    if (SMEM) {
-      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem_bytes);
-      if (e != cudaSuccess) return e;
-    }
-    k<<<c.blocks, threads, SMEM ? c.smem_bytes : 0, c.stream>>>(P, L, x0, u0, xo, uo, st, status);
-    return cudaGetLastError();
-  }
+                            double* uo, ucn_scp_stats* st, int* status);
 };
+// (defined out of the class, so that an extern template declaration keeps the
+// kernel out of the translation units that only launch it)
+template <class M, class T, bool SMEM, bool R, int MAXT>
+cudaError_t LanesVariant<M, T, SMEM, R, MAXT>::occupancy(const LaunchCfg& c, int threads, int* blocks) {
+  *blocks = 0;
+  if (threads > MAXT) return cudaSuccess;
+  auto k = lanes_kernel<M, T, SMEM, R, false, 4, MAXT>();
+  if (SMEM) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem_bytes);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k, threads, SMEM ? c.smem_bytes : 0);
+}
+template <class M, class T, bool SMEM, bool R, int MAXT>
+cudaError_t LanesVariant<M, T, SMEM, R, MAXT>::launch(const LaunchCfg& c, int threads, const double* x0,
+                                                      const double* u0, double* xo, double* uo, ucn_scp_stats* st,
+                                                      int* status) {
+  const ProblemDev& P = *(const ProblemDev*)c.P;
+  const Layout& L = *(const Layout*)c.L;
+  if (threads > MAXT) return cudaErrorInvalidConfiguration;
+  auto k = lanes_kernel<M, T, SMEM, R, false, 4, MAXT>();
+  if (SMEM) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem_bytes);
+    if (e != cudaSuccess) return e;
+  }
+  k<<<c.blocks, threads, SMEM ? c.smem_bytes : 0, c.stream>>>(P, L, x0, u0, xo, uo, st, status);
+  return cudaGetLastError();
+}
 
 // Whether the wide-register variant keeps at least as many CTAs of this launch
 // resident per SM as the 128-register one (then it runs without the spills).
@@ -277,6 +374,10 @@ cudaError_t launch_linearize_t(const void* Pv, const int* node_inst, long long t
     return lanes_kernel<MODEL, T, true, REFINE, true, 4, MAXT>();                                          \
   }                                                                                                        \
   }
+
+// The 3-CTAs-per-SM variant of the one-thread kernel in its own translation unit.
+#define UCN_INSTANTIATE_SCP3(MODEL, T, SMEM, REFINE) template struct ucn::Scp3Variant<ucn::MODEL, T, SMEM, REFINE>;
+#define UCN_EXTERN_SCP3(MODEL, T, SMEM, REFINE) extern template struct ucn::Scp3Variant<ucn::MODEL, T, SMEM, REFINE>;
 
 // Pair-kernel variant in its own translation unit.
 #define UCN_SCPP_V(MODEL, REFINE)                                                                          \

@@ -310,6 +310,29 @@ def test_full_size_mars_batch_sampled_against_oracle():
         np.testing.assert_array_equal(xg[prob.xoff[b] + 100][:6], 0.0)
 
 
+def test_three_per_sm_first_round_gives_the_bits_of_a_solo_solve():
+    # a 1024-instance Mars launch runs its first round (456 CTAs on 152 SMs) in the
+    # three-CTAs-per-SM variant and the rest in the two-per-SM kernel; an instance
+    # from each part gives the same bits as when it is solved alone (one CTA, the
+    # two-per-SM kernel)
+    prob = W.mars_batch(1024, seed=1, settings=dict(scp_iters=8, stop=0))
+    s = ucn.Solver(prob, precision=ucn.UCN_PREC_FP32_REFINE)
+    x, u = s.scp_solve()
+    torch.cuda.synchronize()
+    xg, ug, st = x.cpu().numpy(), u.cpu().numpy(), s.stats_host()
+    s.close()
+    for b in (0, 455, 456, 1023):
+        one = prob.subset(np.array([b]))
+        s1 = ucn.Solver(one, precision=ucn.UCN_PREC_FP32_REFINE)
+        x1, u1 = s1.scp_solve()
+        torch.cuda.synchronize()
+        x1, u1, st1 = x1.cpu().numpy(), u1.cpu().numpy(), s1.stats_host()
+        s1.close()
+        np.testing.assert_array_equal(x1, xg[prob.xoff[b]:prob.xoff[b] + 101])
+        np.testing.assert_array_equal(u1, ug[prob.uoff[b]:prob.uoff[b] + 100])
+        assert st1["accept_mask"][0] == st["accept_mask"][b] and st1["defect"][0] == st["defect"][b]
+
+
 # ------------------------------------------------------------------ two threads per node (3-DOF Mars, FP32)
 def solve_with_lanes(prob, lanes, prec=ucn.UCN_PREC_FP32_REFINE):
     s = ucn.Solver(prob, precision=prec)
