@@ -287,6 +287,16 @@ __device__ __forceinline__ int nobs_of(const ProblemDev& P, int b) {
   return v < 0 ? 0 : (v > P.max_obs ? P.max_obs : v);
 }
 
+// A value the compiler cannot trace back to how it was computed.  The set
+// flags below come from FP64 comparisons; left traceable, the compiler may
+// recompute such a flag by its FP64 comparison at every branch on it instead
+// of keeping it (measured on GB300: ten FP64-pipe instructions per ADMM
+// iteration, on a pipe that runs at 1/64 of the FP32 rate there).
+__device__ __forceinline__ unsigned opaque_u32(unsigned v) {
+  asm volatile("mov.b32 %0, %0;" : "+r"(v));
+  return v;
+}
+
 template <class M, class T>
 __device__ __forceinline__ Inst<T> make_inst(const ProblemDev& P, int b) {
   Inst<T> I;
@@ -294,20 +304,23 @@ __device__ __forceinline__ Inst<T> make_inst(const ProblemDev& P, int b) {
   const double tmin = IsQuad<M>::value ? 0.0 : P.sets[b * UCN_SET_PARAMS + 0];
   const double tmax = IsQuad<M>::value ? 0.0 : P.sets[b * UCN_SET_PARAMS + 1];
   const double tau = IsQuad<M>::value ? 0.0 : P.sets[b * UCN_SET_PARAMS + 2];
-  I.half = tmin > 0.0; I.ball = tmax > 0.0; I.cone = tau > 0.0;
   I.tau = (T)tau; I.tmax = (T)tmax;
   const double ca = 1.0 / sqrt(1.0 + tau * tau);
   I.ca = (T)ca; I.sa = (T)(tau * ca);
   const double tg = IsMars14<M>::value ? P.sets[b * UCN_SET_PARAMS + 3] : 0.0;
   const double rt = IsMars14<M>::value ? P.sets[b * UCN_SET_PARAMS + 4] : 0.0;
   const double wm = IsMars14<M>::value ? P.sets[b * UCN_SET_PARAMS + 5] : 0.0;
-  I.gim = tg > 0.0; I.tilt = rt > 0.0; I.wball = wm > 0.0;
   const double cg = 1.0 / sqrt(1.0 + tg * tg);
   I.tg = (T)tg; I.cg = (T)cg; I.sg = (T)(tg * cg); I.rtilt = (T)rt; I.wmax = (T)wm;
   bool rc = false, tq = false;
   for (int j = 0; j < M::NX; ++j) { rc = rc || P.Qd[b * M::NX + j] != 0.0; tq = tq || P.QNd[b * M::NX + j] != 0.0; }
   for (int j = 0; j < M::NU; ++j) rc = rc || P.Rd[b * M::NU + j] != 0.0;
-  I.run_cost = rc; I.term_quad = tq;
+  const unsigned f = opaque_u32((tmin > 0.0 ? 1u : 0u) | (tmax > 0.0 ? 2u : 0u) | (tau > 0.0 ? 4u : 0u) |
+                                (tg > 0.0 ? 8u : 0u) | (rt > 0.0 ? 16u : 0u) | (wm > 0.0 ? 32u : 0u) |
+                                (rc ? 64u : 0u) | (tq ? 128u : 0u));
+  I.half = f & 1u; I.ball = f & 2u; I.cone = f & 4u;
+  I.gim = f & 8u; I.tilt = f & 16u; I.wball = f & 32u;
+  I.run_cost = f & 64u; I.term_quad = f & 128u;
   for (int k = 0; k < 8; ++k) I.prm[k] = (T)P.params[b * 8 + k];
   return I;
 }
@@ -1890,7 +1903,6 @@ __device__ __forceinline__ typename Node<T, AOS>::W node_cost(const Node<T, AOS>
 // the CTA calls them).  Wide arithmetic: FP64, or double-float on the FP32
 // path, whose sums are reduced in double-float and handed over as doubles.
 
-// Start of a solve: c_i = RK4(xbar_i, ubar_i) - xbar_{i+1} and J(nominal) in sh.Jn.
 // Input check of one instance, by all threads of its CTA (after sh.fail is
 // cleared, before the first factorisation): a NaN anywhere in its data or
 // guesses, or an infinity where only finite values have a meaning (everything
@@ -1921,6 +1933,7 @@ __device__ void flag_bad_inputs(const ProblemDev& P, int b, const double* x0, co
   if (bad) atomicOr(&sh.fail, 1);
 }
 
+// Start of a solve: c_i = RK4(xbar_i, ubar_i) - xbar_{i+1} and J(nominal) in sh.Jn.
 template <class M, class T, bool AOS>
 __device__ void scp_start(const Node<T, AOS>& nd, const ProblemDev& P, const Inst<T>& I, int b, bool act,
                           InstShared& sh) {
@@ -2272,8 +2285,8 @@ __global__ void __launch_bounds__(MAX_THREADS) scp_kernel(ProblemDev P, Layout L
 }
 
 // The same solve for CTAs of up to 128 threads, three resident per SM (168
-// registers; the ADMM state in the node records).  Each CTA runs ~1.4x longer
-// than in scp_kernel, so three per SM solve ~7% more instances per unit time;
+// registers; the ADMM state in the node records).  Each CTA runs ~1.45x longer
+// than in scp_kernel, so three per SM solve ~3% more instances per unit time;
 // the launcher uses it for the first round of a batch (see launch_scp_v).
 constexpr int SCP3_MAX_THREADS = 128;
 template <class M, class T, bool SMEM, bool REFINE>

@@ -49,8 +49,8 @@ cudaError_t Scp3Variant<M, T, SMEM, R>::launch(const LaunchCfg& c, const Problem
 }
 
 // Time of one CTA of scp_kernel_3 (three per SM) over one of scp_kernel (two
-// per SM), measured on the Mars batch (7.2 vs 5.1 ms per instance, GB300).
-constexpr double SCP3_TIME_RATIO = 1.41;
+// per SM), measured on the Mars batch (6.78 vs 4.66 ms per instance, GB300).
+constexpr double SCP3_TIME_RATIO = 1.45;
 
 // How many of a launch's CTAs (taken in the launch's order) run as
 // scp_kernel_3 before the rest run as scp_kernel: the split with the shortest
