@@ -933,7 +933,7 @@ __device__ __forceinline__ bool factor_invert_packed(const MS& MT) {
     #pragma unroll
     for (int k = 0; k < j; ++k) { const T l = MT.H(pk(j, k)); s -= l * l; }
     if (!(s > T(0))) { ok = false; s = T(1); }
-    const T inv = T(1) / sqrt_(s);
+    const T inv = inv_sqrt_(s);
     MT.H(pk(j, j)) = inv;
     #pragma unroll
     for (int r = j + 1; r < n; ++r) {

@@ -121,6 +121,15 @@ __device__ __forceinline__ float sqrt_(float a) { return sqrtf(a); }
 __device__ __forceinline__ double sin_(double a) { return sin(a); }
 __device__ __forceinline__ double cos_(double a) { return cos(a); }
 __device__ __forceinline__ double sqrt_(double a) { return sqrt(a); }
+// 1 / sqrt(a) of a Cholesky pivot: FP64 correctly rounded; FP32 by the hardware
+// reciprocal square root and one Newton-Raphson step y (3 - a y^2) / 2 (within
+// about one ulp; the factor feeds a refined solve), which replaces a rounded
+// square root followed by a rounded divide on the factorisation's serial chain.
+__device__ __forceinline__ double inv_sqrt_(double a) { return 1.0 / sqrt(a); }
+__device__ __forceinline__ float inv_sqrt_(float a) {
+  const float y = rsqrtf(a);
+  return y * fmaf(-0.5f * a * y, y, 1.5f);
+}
 // Double-float: the root by one corrected step; sine and cosine (the 12-state
 // quadrotor's Euler angles only) through FP64.
 __device__ __forceinline__ DF sqrt_(DF a) { return df_sqrt(a); }
@@ -253,11 +262,19 @@ struct Quat13 {
 // unit thrust), non-dimensional units.
 struct Mars7 {
   static constexpr int NX = 7, NU = 3;
+  // The mass rate -alpha |T|, which depends on the control alone: constant over
+  // an RK4 step (the control is held), so rk4h forms it once per step.
   template <class S, class P>
-  __device__ static void f(const P* prm, const S* x, const S* u, S* xd) {
+  __device__ static S mass_rate(const P* prm, const S* u) {
     typedef typename BaseOf<S>::type R;
-    const R g = (R)prm[0], alpha = (R)prm[1];
+    const R alpha = (R)prm[1];
     const S Tn = sqrt_(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    return -(alpha * Tn);
+  }
+  template <class S, class P>
+  __device__ static void f_held(const P* prm, const S* x, const S* u, const S& mdot, S* xd) {
+    typedef typename BaseOf<S>::type R;
+    const R g = (R)prm[0];
     const S im = R(1) / x[6];   // one division per evaluation (GB300's FP64 divide is costly)
     xd[0] = x[3];
     xd[1] = x[4];
@@ -265,7 +282,11 @@ struct Mars7 {
     xd[3] = u[0] * im - g;
     xd[4] = u[1] * im;
     xd[5] = u[2] * im;
-    xd[6] = -(alpha * Tn);
+    xd[6] = mdot;
+  }
+  template <class S, class P>
+  __device__ static void f(const P* prm, const S* x, const S* u, S* xd) {
+    f_held(prm, x, u, mass_rate(prm, u), xd);
   }
 };
 
@@ -310,22 +331,42 @@ struct Mars14 {
 template <class S, class R> __device__ __forceinline__ S fma_(S a, R b, S c) { return a + b * c; }
 __device__ __forceinline__ DF fma_(DF a, DF b, DF c) { return df_fma(a, b, c); }
 
+// f with the control held over an RK4 step, as a callable x -> x-dot.  For
+// the 3-DOF Mars model the control-only part (the mass rate) is formed once,
+// at construction, instead of at each of the four stages: the same numbers.
+template <class M, class S, class P>
+struct HeldControl {
+  const P* prm;
+  const S* u;
+  __device__ __forceinline__ HeldControl(const P* p, const S* uu) : prm(p), u(uu) {}
+  __device__ __forceinline__ void operator()(const S* x, S* xd) const { M::f(prm, x, u, xd); }
+};
+template <class S, class P>
+struct HeldControl<Mars7, S, P> {
+  const P* prm;
+  const S* u;
+  S mdot;
+  __device__ __forceinline__ HeldControl(const P* p, const S* uu) : prm(p), u(uu), mdot(Mars7::mass_rate(p, uu)) {}
+  __device__ __forceinline__ void operator()(const S* x, S* xd) const { Mars7::f_held(prm, x, u, mdot, xd); }
+};
+
 // Classical fourth-order Runge-Kutta step (Eq. (1b)) with the step h and its
 // multiples h/2, h/6 given in the base type R of S.
 template <class M, class S, class P, class R>
 __device__ __forceinline__ void rk4h(const P* prm, R h, R hh, R h6, const S* x, const S* u, S* xn) {
   constexpr int NX = M::NX;
   S k[NX], t[NX], acc[NX];
-  M::f(prm, x, u, k);
+  const HeldControl<M, S, P> F(prm, u);
+  F(x, k);
 #pragma unroll
   for (int j = 0; j < NX; ++j) { acc[j] = k[j]; t[j] = fma_(x[j], hh, k[j]); }
-  M::f(prm, t, u, k);
+  F(t, k);
 #pragma unroll
   for (int j = 0; j < NX; ++j) { acc[j] = fma_(acc[j], R(2), k[j]); t[j] = fma_(x[j], hh, k[j]); }
-  M::f(prm, t, u, k);
+  F(t, k);
 #pragma unroll
   for (int j = 0; j < NX; ++j) { acc[j] = fma_(acc[j], R(2), k[j]); t[j] = fma_(x[j], h, k[j]); }
-  M::f(prm, t, u, k);
+  F(t, k);
 #pragma unroll
   for (int j = 0; j < NX; ++j) xn[j] = fma_(x[j], h6, acc[j] + k[j]);
 }
