@@ -224,11 +224,17 @@ ucn_status ucn_admm_solve(ucn_problem* prob, const double* xbar_d, const double*
 ucn_status ucn_state_export(ucn_problem* prob, double* state_d, void* stream);
 
 /* Full SCP solve (Sec. III-A with the ADMM of Sec. III-B) of every
- * instance in ONE persistent kernel launch: per SCP iteration the RK4
- * linearisation, assembly + factorisation, admm_iters ADMM iterations, and
- * the rollout / defect / trust-region acceptance test, all on the
- * device.  In: initial guesses x0_d, u0_d.  Out: x_out_d, u_out_d (the last
- * accepted trajectory), stats_d [batch], status_d [batch] (== stats.status). */
+ * instance by persistent kernel launches that each run whole solves: per SCP
+ * iteration the RK4 linearisation, assembly + factorisation, admm_iters ADMM
+ * iterations, and the rollout / defect / trust-region acceptance test, all on
+ * the device, one CTA per instance.  One launch; for batches of the 3-DOF Mars
+ * model in FP32 that are not a whole number of resident rounds, a first launch
+ * runs one round on a three-CTAs-per-SM variant of the same kernel and a second
+ * the rest (same results per instance).  In: initial guesses x0_d, u0_d.  Out:
+ * x_out_d, u_out_d (the last accepted trajectory), stats_d [batch], status_d
+ * [batch] (== stats.status).  An instance whose data or guesses hold a NaN (or an
+ * infinity outside the bounds and set parameters) ends UCN_ENUMERIC after its
+ * first factorisation; the other instances are not affected. */
 ucn_status ucn_scp_solve(ucn_problem* prob, const double* x0_d, const double* u0_d,
                          double* x_out_d, double* u_out_d, ucn_scp_stats* stats_d,
                          int* status_d, void* stream);
@@ -242,8 +248,9 @@ ucn_status ucn_scp_solve(ucn_problem* prob, const double* x0_d, const double* u0
  * are taken relative to its guess (x0_d, u0_d), its mirror sets are
  * re-projected with the first SCP iteration's sets, as every later iteration
  * does, and with a penalty schedule (rho_final > 0) every SCP iteration uses
- * the schedule's final penalties, at which the kept state was computed.  Asynchronous on `stream`: state_d is copied into the problem's state
- * buffer first (it may be that buffer, as after ucn_state_export into it).
+ * the schedule's final penalties, at which the kept state was computed.
+ * Asynchronous on `stream`: state_d is copied into the problem's state buffer
+ * first (it may be that buffer, as after ucn_state_export into it).
  * Errors: UCN_EINVAL (null pointer, scenario groups), UCN_ECUDA. */
 ucn_status ucn_scp_solve_warm(ucn_problem* prob, const double* x0_d, const double* u0_d, const double* state_d,
                               double* x_out_d, double* u_out_d, ucn_scp_stats* stats_d, int* status_d,
