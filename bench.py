@@ -63,7 +63,7 @@ def mars_mirror_flops():
 # it includes and the host code that lays out and launches it
 TRAFFIC_SOURCES = ("include/ucn.h",) + tuple("paper_2603_10711_gb300/csrc/" + f for f in (
     "ucn_api.cu", "ucn_df.cuh", "ucn_internal.h", "ucn_kernels.cuh", "ucn_lanes.cuh", "ucn_launch.cuh",
-    "ucn_mars32.cu", "ucn_math.cuh", "ucn_pair.cuh"))
+    "ucn_mars32.cu", "ucn_mars32_3.cu", "ucn_math.cuh", "ucn_pair.cuh"))
 
 
 def kernel_sources_sha256():
@@ -76,13 +76,14 @@ def kernel_sources_sha256():
 
 
 def recorded_traffic():
-    """DRAM bytes per launch of the fused kernel from the committed ncu capture,
-    or None when the kernel sources changed since that capture."""
+    """DRAM bytes of one batch solve (the fused kernel's launches of one
+    ucn_scp_solve) from the committed ncu capture, or None when the kernel
+    sources changed since that capture."""
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "scp_kernel_traffic.json")))
     except Exception:
         return None
-    return rec["traffic_bytes_per_launch"] if rec.get("sources_sha256") == kernel_sources_sha256() else None
+    return rec["traffic_bytes_per_solve"] if rec.get("sources_sha256") == kernel_sources_sha256() else None
 
 
 def measured_peaks():
@@ -329,11 +330,12 @@ def run_ours(args, rank, world):
         "e2e": {"value": e2e_pass / sum(e2e_times), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
                      "frac": achieved / peak_tf, "traffic": recorded_traffic(),
-                     "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
+                     "traffic_unit": "bytes per batch solve: the fused kernel's launches of one ucn_scp_solve "
+                                     "(ncu dram__bytes_read.sum + dram__bytes_write.sum)",
                      "peak_note": "derived: %d SMs (read from the device) x %d FP32 lanes x 2 x %.0f MHz (max SM clock, "
                                   "MEASURED_PEAKS.json)" % (sm_count, FP32_LANES_PER_SM, sm_max),
                      "algorithmic_flops_per_node_iter": flops_ni, "node_iters_per_launch": nodeiters / args.steps},
-        "gpu_launches": args.steps,
+        "gpu_launches": args.steps * ucn.ucn_problem_last_launches(solver.handle),
         "clocks": clocks,
     }
     if single_out is not None:

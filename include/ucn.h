@@ -186,6 +186,13 @@ ucn_status ucn_problem_set_order(ucn_problem* prob, const int* order);
 ucn_status ucn_problem_set_lanes(ucn_problem* prob, int lanes_per_node);
 int ucn_problem_lanes(const ucn_problem* prob);
 
+/* Kernel launches made by the last ucn_scp_solve / ucn_scp_solve_warm /
+ * ucn_admm_solve call on this problem: 1, or 2 when the fused
+ * solve ran a first round on its three-CTAs-per-SM variant (see
+ * ucn_scp_solve); 0 before the first call, -1 for NULL.  (Not in the paper;
+ * for launch accounting.) */
+int ucn_problem_last_launches(const ucn_problem* prob);
+
 /* Number of elements of the packed state / trajectory buffers. */
 long long ucn_total_x(const ucn_problem* prob);
 long long ucn_total_u(const ucn_problem* prob);

@@ -135,6 +135,7 @@ struct ucn_problem {
   int* order_d;
   int group, gcsize;     // scenarios per group, CTAs per thread-block cluster
   int tpn;               // threads per node of the fused solve
+  int last_launches = 0; // kernel launches of the last fused solve
   int optin;             // shared memory per CTA the device allows
   unsigned char* warm_ones;   // batch flags, all 1: every instance starts from the given state
 };
@@ -449,6 +450,8 @@ ucn_status ucn_problem_set_lanes(ucn_problem* p, int lanes_per_node) {
 
 int ucn_problem_lanes(const ucn_problem* p) { return p ? p->tpn : -1; }
 
+int ucn_problem_last_launches(const ucn_problem* p) { return p ? p->last_launches : -1; }
+
 long long ucn_total_x(const ucn_problem* p) { return p ? p->total_x : -1; }
 long long ucn_total_u(const ucn_problem* p) { return p ? p->total_u : -1; }
 long long ucn_state_size(const ucn_problem* p) { return p ? p->state_size : -1; }
@@ -458,6 +461,8 @@ static LaunchCfg cfg_of(ucn_problem* p, void* stream) {
   c.P = &p->dev; c.L = &p->L; c.smem = p->smem; c.smem_bytes = p->smem_bytes;
   c.threads = p->threads; c.blocks = p->batch; c.stream = as_stream(stream); c.group = p->gcsize;
   c.nodes = p->Nmax + 1; c.tpn = p->tpn;
+  c.launched = &p->last_launches;
+  p->last_launches = 1;   // one launch unless the launcher splits the batch
   return c;
 }
 

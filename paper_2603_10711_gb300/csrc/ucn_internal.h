@@ -37,6 +37,7 @@ struct LaunchCfg {
   int nodes;            // nodes of the longest instance (N_max + 1)
   int tpn;              // threads per node of the fused solve: 1; 2 (pair kernel: 3-DOF Mars, FP32,
                         // records in shared memory); 4 (lane kernel, quadrotor)
+  int* launched = nullptr;   // out (when not NULL): kernel launches the fused solve made
 };
 
 // Threads per node the fused solve uses by default for a model, node count and

@@ -106,6 +106,7 @@ cudaError_t launch_scp_v(const LaunchCfg& c, const double* x0, const double* u0,
       }
     }
   }
+  if (c.launched) *c.launched = (k3 > 0) + (k3 < c.blocks);
   if (k3 >= c.blocks) return cudaSuccess;
   ProblemDev Pr = P;
   if (k3 > 0) Pr.order = P.order + k3;

@@ -86,6 +86,8 @@ def lib():
             L.ucn_problem_set_lanes.restype = C.c_int
             L.ucn_problem_lanes.argtypes = [vp]
             L.ucn_problem_lanes.restype = C.c_int
+            L.ucn_problem_last_launches.argtypes = [vp]
+            L.ucn_problem_last_launches.restype = C.c_int
             L.ucn_linearize.argtypes = [vp, vp, vp, vp, vp, vp, vp]
             L.ucn_linearize.restype = C.c_int
             L.ucn_admm_solve.argtypes = [vp, vp, vp, vp, vp, vp, vp, C.c_int, C.c_int, vp, vp, vp, vp, vp]
@@ -208,6 +210,10 @@ def ucn_problem_set_lanes(h, lanes_per_node):
 
 def ucn_problem_lanes(h):
     return int(lib().ucn_problem_lanes(h))
+
+
+def ucn_problem_last_launches(h):
+    return int(lib().ucn_problem_last_launches(h))
 
 
 def ucn_problem_set_order(h, order=None):

@@ -101,6 +101,7 @@ def test_null_arguments_are_rejected(ucn):
     assert lib.ucn_linearize(None, None, None, None, None, None, None) == ucn.UCN_EINVAL
     assert lib.ucn_state_export(None, None, None) == ucn.UCN_EINVAL
     assert lib.ucn_total_x(None) == -1
+    assert lib.ucn_problem_last_launches(None) == -1
 
 
 def test_double_float_check_validates_before_any_launch(ucn):

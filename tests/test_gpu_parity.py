@@ -320,6 +320,7 @@ def test_three_per_sm_first_round_gives_the_bits_of_a_solo_solve():
     x, u = s.scp_solve()
     torch.cuda.synchronize()
     xg, ug, st = x.cpu().numpy(), u.cpu().numpy(), s.stats_host()
+    assert ucn.ucn_problem_last_launches(s.handle) == 2
     s.close()
     for b in (0, 455, 456, 1023):
         one = prob.subset(np.array([b]))
@@ -327,6 +328,7 @@ def test_three_per_sm_first_round_gives_the_bits_of_a_solo_solve():
         x1, u1 = s1.scp_solve()
         torch.cuda.synchronize()
         x1, u1, st1 = x1.cpu().numpy(), u1.cpu().numpy(), s1.stats_host()
+        assert ucn.ucn_problem_last_launches(s1.handle) == 1
         s1.close()
         np.testing.assert_array_equal(x1, xg[prob.xoff[b]:prob.xoff[b] + 101])
         np.testing.assert_array_equal(u1, ug[prob.uoff[b]:prob.uoff[b] + 100])
