@@ -505,7 +505,7 @@ def run_scenarios(args):
         w = ucn.Solver(W.scenario_mpc(2, K, seed=13, N=40, n_obs=8, settings=dict(scp_iters=2, admm_iters=20)),
                        precision=prec)
         w.scp_solve(); torch.cuda.synchronize(); w.close()
-    kc = max(c for c in range(1, min(K, 16) + 1) if K % c == 0)
+    kc = K if K <= 16 else (2 if K % 2 == 0 else 1)     # the library's cluster size for a group of K
     goal = prob.xtarget[::K, :3]
     d0 = np.linalg.norm(prob.xinit[::K, :3] - goal, axis=1)
     s = ucn.Solver(prob, precision=ucn.UCN_PREC_FP32_REFINE)

@@ -337,11 +337,13 @@ ucn_status ucn_problem_create(const ucn_problem_desc* d, ucn_problem** out) {
   p->warm_ones = wones;
   P.rho_fac = facd;
   P.group = group;
-  // a group is gclusters thread-block clusters of gcsize CTAs: the largest
-  // cluster size <= 16 that divides it
-  int gcsize = 1;
-  for (int c = std::min(group, 16); c >= 1; --c)
-    if (group % c == 0) { gcsize = c; break; }
+  // a group is gclusters thread-block clusters of gcsize CTAs: a group of up to
+  // 16 scenarios is one cluster (its exchange stays in distributed shared
+  // memory: 16 scenarios 1.7x faster than clusters of 2); a larger group runs
+  // as clusters of 2 CTAs (1 if the group is odd) that combine through global
+  // memory -- measured on GB300 with 64 scenarios per problem, 20% faster than
+  // clusters of 16, whose 16-CTA co-scheduling leaves SMs idle
+  const int gcsize = group <= 16 ? group : (group % 2 == 0 ? 2 : 1);
   p->gcsize = gcsize;
   P.gclusters = group / gcsize;
   // bound on a wait for another scenario (the group runs in lockstep, so waits

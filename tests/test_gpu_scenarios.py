@@ -92,8 +92,8 @@ def test_largest_group_with_benchmark_records():
 
 @pytest.mark.parametrize("K", [17, 24, 32, 64])
 def test_groups_of_several_clusters_match_the_oracle(K):
-    # K > 16: clusters of the largest divisor <= 16 (1, 12, 16, 16 CTAs) whose
-    # rank-0 CTAs combine partial sums through global memory
+    # K > 16: clusters of 2 CTAs (1 for odd K) whose rank-0 CTAs combine
+    # partial sums through global memory
     compare(grouped(2, K, N=16, n_obs=3, seed=7), ucn.UCN_PREC_FP64, TOL64)
 
 
