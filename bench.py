@@ -367,28 +367,43 @@ def run_serving(args):
     # longer horizons need more ADMM iterations per SCP iteration (80 x 60 passes up to 200)
     ms = dict(W.mars_batch(1).settings, rho_final=1e7, scp_iters=80, admm_iters=60)
 
+    # one server per model and horizon bucket: a server's CTA size and node layout follow
+    # its longest horizon, so short requests run in small CTAs with their records in
+    # shared memory (a quadrotor node with 30 obstacle mirrors takes ~3 KB: up to 72
+    # nodes fit one CTA's shared memory)
+    buckets = {1: (40, 72, 120), 2: (100, 200)}
+    route = serving.horizon_route(buckets)
+
     def servers(prec, slots):
-        return {1: serving.Server(1, prec, max_slots=slots, max_horizon=120, max_obs=30, lanes=16, settings=qs),
-                2: serving.Server(2, prec, max_slots=slots, max_horizon=200, lanes=16, settings=ms)}
+        sv = {}
+        for h in buckets[1]:
+            sv[(1, h)] = serving.Server(1, prec, max_slots=slots, max_horizon=h, max_obs=30, lanes=8, settings=qs)
+        for h in buckets[2]:
+            sv[(2, h)] = serving.Server(2, prec, max_slots=slots, max_horizon=h, lanes=8, settings=ms)
+        return sv
 
     rates = [float(r) for r in args.serving_rates.split(",")]
     sv = servers(ucn.UCN_PREC_FP32_REFINE, 512)
-    serving.run_stream(W.serving_stream(32, rate=rates[0], seed=4), sv)                # warm-up
+    serving.run_stream(W.serving_stream(32, rate=rates[0], seed=4), sv, route=route)    # warm-up
+    # one set of requests; the arrival gaps are Exp(rate) = Exp(1) / rate of the same draws
+    base = W.serving_stream(args.serving_requests, rate=1.0, seed=4)
     sweep = []
     for rate in rates:
-        stream = W.serving_stream(args.serving_requests, rate=rate, seed=4)
-        r = serving.run_stream(stream, sv)
+        stream = [(t / rate, p) for t, p in base]
+        r = serving.run_stream(stream, sv, route=route)
         sweep.append(dict(r, arrival_rate_per_s=rate, requests=len(stream)))
     for s in sv.values():
         s.close()
     knee = next((r["arrival_rate_per_s"] for r in sweep if r["solves_per_s"] < 0.9 * r["arrival_rate_per_s"]), None)
-    stream = W.serving_stream(args.serving_requests, rate=rates[0], seed=4)
+    stream = base
     sv = servers(ucn.UCN_PREC_FP64, 4)
     n64 = min(len(stream), args.serving_fp64_requests)
-    fp64 = serving.run_stream([(0.0, p) for _, p in stream[:n64]], sv, max_inflight=1)
+    fp64 = serving.run_stream([(0.0, p) for _, p in stream[:n64]], sv, max_inflight=1, route=route)
     for s in sv.values():
         s.close()
-    return {"mix": "70% quad N 30-120, 5-30 obstacles / 30% Mars N 50-200", "fp32_continuous": sweep,
+    return {"mix": "70% quad N 30-120, 5-30 obstacles / 30% Mars N 50-200",
+            "servers": "one per model and horizon bucket: quadrotor N <= 40 / 72 / 120, Mars N <= 100 / 200",
+            "fp32_continuous": sweep,
             "capacity_solves_per_s": max(r["solves_per_s"] for r in sweep), "knee_arrival_rate_per_s": knee,
             "fp64_per_request": dict(fp64, requests=n64),
             "latency": "arrival -> result collected (host clock)"}
@@ -629,7 +644,9 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=1024)
     ap.add_argument("--ref-sample", type=int, default=128, help="instances per step of the reference (oracle) arm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--serving-requests", type=int, default=2000, help="requests of the serving stream (0: skip)")
+    ap.add_argument("--serving-requests", type=int, default=8000,
+                    help="requests of each serving stream (0: skip); long enough that the drain after the last "
+                         "arrival weighs little in the completed rate")
     ap.add_argument("--serving-rates", default="2000,5000,10000,20000", help="Poisson arrival rates of the serving sweep")
     ap.add_argument("--serving-fp64-requests", type=int, default=16)
     ap.add_argument("--batching-batch", type=int, default=4096, help="uneven quadrotor batch (0: skip the section)")

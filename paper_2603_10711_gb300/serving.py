@@ -180,10 +180,23 @@ class Server:
         return int(self.L.ucn_serve_free_slots(self.h))
 
 
-def run_stream(stream, servers, max_inflight=None, time_scale=1.0):
-    """Replay a request stream [(arrival_s, Problem)] against `servers`
-    (dict model -> Server) in real time.  max_inflight=1 gives the one-at-a-time
-    (per-request) path.  Returns latencies and throughput."""
+def horizon_route(buckets):
+    """A route for run_stream over servers keyed (model, max_horizon): each
+    request to its model's server with the smallest max_horizon that holds it
+    (a server's CTA size and node layout follow its max_horizon, so short
+    requests run in small CTAs with their records in shared memory)."""
+    def route(p):
+        N = int(p.N[0])
+        return (p.model, min(h for h in buckets[p.model] if h >= N))
+    return route
+
+
+def run_stream(stream, servers, max_inflight=None, time_scale=1.0, route=None):
+    """Replay a request stream [(arrival_s, Problem)] against `servers` in real
+    time: a dict key -> Server, each request going to servers[route(request)]
+    (default key: the request's model).  max_inflight=1 gives the one-at-a-time
+    (per-request) path.  Returns latencies and throughput (also per model)."""
+    route = route or (lambda p: p.model)
     pending = deque(sorted(stream, key=lambda r: r[0]))
     waiting = {m: deque() for m in servers}     # arrived, not yet admitted, per server (FIFO)
     inflight = {}
@@ -194,7 +207,7 @@ def run_stream(stream, servers, max_inflight=None, time_scale=1.0):
         now = (time.perf_counter() - t0) / time_scale
         while pending and pending[0][0] <= now:
             arr, p = pending.popleft()
-            waiting[p.model].append((arr, p))
+            waiting[route(p)].append((arr, p))
         for m, q in waiting.items():
             # admit in arrival order per server; a full server does not hold up the others
             while q and (max_inflight is None or len(inflight) < max_inflight):
@@ -203,16 +216,16 @@ def run_stream(stream, servers, max_inflight=None, time_scale=1.0):
                 if rc == ucn.UCN_EBUSY:
                     break
                 q.popleft()
-                inflight[(p.model, ticket)] = (arr, int(p.N[0]))
+                inflight[(m, ticket)] = (arr, p.model)
         for srv in servers.values():
             srv.pump()
-        for model, srv in servers.items():
+        for key, srv in servers.items():
             # every request finished since the last pass (one call each)
             while True:
                 rc, ticket, res = srv.poll_any()
                 if rc != ucn.UCN_OK:
                     break
-                arr, N = inflight.pop((model, ticket))
+                arr, model = inflight.pop((key, ticket))
                 lat.append((time.perf_counter() - t0) / time_scale - arr)
                 defects.append(float(res["stats"]["defect"]))
                 models.append(model)
