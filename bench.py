@@ -4,7 +4,8 @@ Workload: the Mars powered-descent batch (1024 instances, N = 100, 3-DOF,
 |T| in [4.8, 19.2] kN, glide slope 86 deg), solved by the fused persistent
 SCP kernel in the FP32 + refinement path (ADMM in FP32; nominal, rollout and
 merits in double-float; acceptance test, returned trajectory and its defect
-in FP64).  One step = one ucn_scp_solve launch over the whole batch.  `value`
+in FP64).  One step = one ucn_scp_solve over the whole batch (two launches of
+the fused kernel: a first round of three CTAs per SM, then the rest).  `value`
 counts only solves whose returned trajectory has max defect <= 1e-5 (an FP64
 RK4 defect of the returned doubles, computed by the kernel; the parity leg
 recomputes it with the oracle's RK4).  The plain FP64 path is timed beside it
