@@ -358,8 +358,9 @@ def run_ours(args, rank, world):
 def run_serving(args):
     """Continuous batching of a mixed Poisson request stream (70% quadrotor,
     30% Mars descent) in FP32 at each arrival rate of --serving-rates (the
-    configuration's 2k-20k req/s), and the stream's head solved one request at
-    a time in FP64 (the plain per-request path).  Capacity = the largest
+    configuration's 2k-20k req/s), by pump launches and by the device-resident
+    request loop, and the stream's head solved one request at a time in FP64
+    (the plain per-request path).  Capacity = the largest
     completed-solve rate; knee = the first rate at which the completed rate
     falls below 90% of the arrival rate (the server saturates)."""
     from paper_2603_10711_gb300 import serving, ucn
@@ -396,6 +397,37 @@ def run_serving(args):
     for s in sv.values():
         s.close()
     knee = next((r["arrival_rate_per_s"] for r in sweep if r["solves_per_s"] < 0.9 * r["arrival_rate_per_s"]), None)
+
+    # the same streams through the device-resident request loop: one persistent kernel
+    # per server whose CTAs claim each request as it is submitted (no pump launches).
+    # The loops run at the same time, so each holds a share of the device: server i
+    # needs c_i = rate_i x t_i CTAs to keep up (t_i: its mean device time per solve,
+    # measured in the pump sweep's first stream) and c_i / cap_i of the device (cap_i:
+    # its CTAs that fit at once), so c_i = cap_i x s_i with s_i proportional to
+    # n_i t_i / cap_i, 90% of the device in all
+    sv = servers(ucn.UCN_PREC_FP32_REFINE, 512)
+    busy = sweep[0]["solve_ms_by_server"]
+    caps = {k: srv.loop_capacity() for k, srv in sv.items()}
+    name = serving.server_name
+    need = {k: (busy[name(k)][0] * busy[name(k)][1] / caps[k] if name(k) in busy else 0.0) for k in sv}
+    total = sum(need.values())
+    loop_ctas = {}
+    for k, srv in sv.items():
+        loop_ctas[k] = max(1, int(0.9 * caps[k] * need[k] / total))
+        srv.loop_start(ctas=loop_ctas[k], idle_s=2.0)
+    serving.run_stream(W.serving_stream(32, rate=rates[0], seed=4), sv, route=route)    # warm-up
+    loop_sweep = []
+    for rate in rates:
+        stream = [(t / rate, p) for t, p in base]
+        r = serving.run_stream(stream, sv, route=route)
+        loop_sweep.append(dict(r, arrival_rate_per_s=rate, requests=len(stream)))
+    loop_launches = 0
+    for s in sv.values():
+        s.loop_stop()
+        loop_launches += s.loop_launches()
+        s.close()
+    loop_knee = next((r["arrival_rate_per_s"] for r in loop_sweep if r["solves_per_s"] < 0.9 * r["arrival_rate_per_s"]),
+                     None)
     stream = base
     sv = servers(ucn.UCN_PREC_FP64, 4)
     n64 = min(len(stream), args.serving_fp64_requests)
@@ -406,6 +438,11 @@ def run_serving(args):
             "servers": "one per model and horizon bucket: quadrotor N <= 40 / 72 / 120, Mars N <= 100 / 200",
             "fp32_continuous": sweep,
             "capacity_solves_per_s": max(r["solves_per_s"] for r in sweep), "knee_arrival_rate_per_s": knee,
+            "fp32_device_loop": loop_sweep,
+            "device_loop_capacity_solves_per_s": max(r["solves_per_s"] for r in loop_sweep),
+            "device_loop_knee_arrival_rate_per_s": loop_knee,
+            "device_loop_ctas": {name(k): [v, caps[k]] for k, v in loop_ctas.items()},
+            "device_loop_launches": loop_launches,
             "fp64_per_request": dict(fp64, requests=n64),
             "latency": "arrival -> result collected (host clock)"}
 

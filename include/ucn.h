@@ -402,7 +402,7 @@ typedef struct ucn_server ucn_server;
 
 /* Allocates the server.  Errors: UCN_EINVAL, UCN_ENOMEM, UCN_ECUDA. */
 ucn_status ucn_serve_create(const ucn_serve_config* cfg, ucn_server** out);
-/* Synchronises the device and frees everything. */
+/* Ends a running request loop, synchronises the device and frees everything. */
 void ucn_serve_destroy(ucn_server* srv);
 /* Admits a request into a free slot: UCN_OK and a ticket; UCN_EBUSY when no
  * slot is free or its footprint exceeds the HBM budget; UCN_EINVAL. */
@@ -423,6 +423,38 @@ ucn_status ucn_serve_poll(ucn_server* srv, unsigned long long ticket, ucn_result
 ucn_status ucn_serve_poll_any(ucn_server* srv, ucn_result* res);
 /* Free slots right now (-1 for a NULL server). */
 int ucn_serve_free_slots(ucn_server* srv);
+
+/* Device-resident request loop (not in the paper; the serving layer around the
+ * method, 12-state quadrotor and 3-DOF Mars servers).  ucn_serve_loop_start
+ * launches one persistent kernel of `ctas` CTAs (0: as many as can be
+ * resident at once) on the server's own stream.  From then on ucn_serve_submit
+ * publishes each admitted request at once -- its record into mapped host
+ * memory, the slot into a queue, then the queue head -- and a CTA of the
+ * running kernel that is free claims it (in submission order), copies its data
+ * into the slot, runs the same fused SCP solve as a pump launch (Secs. III-A,
+ * III-B: the same kernel body on the same slot layout), keeps its result in the
+ * ring and delivers it to host memory; there is no pump and no launch per
+ * request.  Requests admitted and not pumped when the loop starts go to it
+ * first.  Every wait of the kernel is bounded: a CTA that has found no request
+ * for `idle_s` seconds (0 < idle_s <= 60) ends, and the next submit, pump,
+ * poll or poll_any relaunches the loop if requests wait.  While the loop is on,
+ * ucn_serve_pump only does that relaunch (*launched = 0), and a warm start must
+ * name a result that has been delivered (UCN_EBUSY until then).  Errors:
+ * UCN_EINVAL (other models, bad arguments, loop already on), UCN_ECUDA. */
+ucn_status ucn_serve_loop_start(ucn_server* srv, int ctas, double idle_s);
+/* Serves every published request, ends the loop kernel (blocks until it has)
+ * and returns the server to pump launches; UCN_OK when no loop is on.
+ * Results stay in their slots until polled.  UCN_ECUDA if the loop failed. */
+ucn_status ucn_serve_loop_stop(ucn_server* srv);
+/* Launches of the loop kernel so far (the first one and every relaunch after
+ * an idle end); -1 for a NULL server. */
+int ucn_serve_loop_launches(ucn_server* srv);
+/* How many CTAs of this server's loop kernel can be resident at once on the
+ * current device (the `ctas` that 0 stands for); -1 for a NULL server or a
+ * model without a loop.  Several servers whose loops run at the same time
+ * share the device: CTAs beyond what fits start only when others end, so give
+ * each loop a share of its capacity. */
+int ucn_serve_loop_capacity(ucn_server* srv);
 
 /* Thread-local description of the last error on this thread ("" if none). */
 const char* ucn_last_error(void);

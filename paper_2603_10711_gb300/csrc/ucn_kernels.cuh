@@ -2156,7 +2156,8 @@ __device__ __forceinline__ void scp_report(const InstShared& sh, const ProblemDe
 // three CTAs per SM has no registers for it).
 template <class M, class T, bool SMEM, bool REFINE, bool GROUP, bool REGS>
 __device__ __forceinline__ void scp_body(const ProblemDev& P, const Layout& L, const double* x0, const double* u0,
-                                         double* xout, double* uout, ucn_scp_stats* stats, int* status_out) {
+                                         double* xout, double* uout, ucn_scp_stats* stats, int* status_out,
+                                         const int b) {
   constexpr int NX = M::NX, NU = M::NU, NN = NX + NU;
   static_assert(!GROUP || NU <= 4, "GroupShared holds nu <= 4");
   extern __shared__ __align__(16) unsigned char smem[];
@@ -2168,10 +2169,6 @@ __device__ __forceinline__ void scp_body(const ProblemDev& P, const Layout& L, c
     X.k = (int)blockIdx.x % P.group;
     if (threadIdx.x == 0) G->gfail = 0;
   }
-  // instances are taken in the order given (largest first by default), so that
-  // the long solves of an uneven batch start in the first wave; a scenario group
-  // keeps its cluster's consecutive instances
-  const int b = (GROUP || !P.order) ? (int)blockIdx.x : P.order[blockIdx.x];
   constexpr bool AOS = SMEM;
   Node<T, AOS> nd = make_node<T, SMEM>(P, L, smem, b);
   MatsFor<M, T, AOS, true> MT;
@@ -2276,12 +2273,20 @@ __device__ __forceinline__ void scp_body(const ProblemDev& P, const Layout& L, c
   if constexpr (GROUP) group_finish(P);
 }
 
+// Instance of a launch's CTA: instances are taken in the order given (largest
+// first by default), so that the long solves of an uneven batch start in the
+// first wave; a scenario group keeps its cluster's consecutive instances.
+template <bool GROUP>
+__device__ __forceinline__ int cta_instance(const ProblemDev& P) {
+  return (GROUP || !P.order) ? (int)blockIdx.x : P.order[blockIdx.x];
+}
+
 // The fused solve for CTAs of up to MAX_THREADS threads; the compiler chooses
 // the registers (up to 255: two 4-warp CTAs per SM).
 template <class M, class T, bool SMEM, bool REFINE, bool GROUP = false>
 __global__ void __launch_bounds__(MAX_THREADS) scp_kernel(ProblemDev P, Layout L, const double* x0, const double* u0,
                                                           double* xout, double* uout, ucn_scp_stats* stats, int* status_out) {
-  scp_body<M, T, SMEM, REFINE, GROUP, true>(P, L, x0, u0, xout, uout, stats, status_out);
+  scp_body<M, T, SMEM, REFINE, GROUP, true>(P, L, x0, u0, xout, uout, stats, status_out, cta_instance<GROUP>(P));
 }
 
 // The same solve for CTAs of up to 128 threads, three resident per SM (168
@@ -2293,7 +2298,7 @@ template <class M, class T, bool SMEM, bool REFINE>
 __global__ void __launch_bounds__(SCP3_MAX_THREADS, 3) scp_kernel_3(ProblemDev P, Layout L, const double* x0,
                                                                   const double* u0, double* xout, double* uout,
                                                                   ucn_scp_stats* stats, int* status_out) {
-  scp_body<M, T, SMEM, REFINE, false, false>(P, L, x0, u0, xout, uout, stats, status_out);
+  scp_body<M, T, SMEM, REFINE, false, false>(P, L, x0, u0, xout, uout, stats, status_out, cta_instance<false>(P));
 }
 
 }  // namespace ucn

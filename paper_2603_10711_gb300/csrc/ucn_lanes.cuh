@@ -531,7 +531,7 @@ __device__ __forceinline__ Node<T, SMEM> make_node_at(const ProblemDev& P, const
 template <class M, class T, bool SMEM, bool REFINE, bool GROUP, int TPN>
 __device__ __forceinline__ void scp_lanes_body(const ProblemDev& P, const Layout& L, const double* x0,
                                                const double* u0, double* xout, double* uout, ucn_scp_stats* stats,
-                                               int* status_out) {
+                                               int* status_out, const int b) {
   using LR = LaneRows<M, TPN>;
   constexpr int NX = M::NX, NU = M::NU, NN = NX + NU, R = LR::R;
   static_assert(!GROUP || NU <= 4, "GroupShared holds nu <= 4");
@@ -544,7 +544,6 @@ __device__ __forceinline__ void scp_lanes_body(const ProblemDev& P, const Layout
     X.k = (int)blockIdx.x % P.group;
     if (threadIdx.x == 0) G->gfail = 0;
   }
-  const int b = (GROUP || !P.order) ? (int)blockIdx.x : P.order[blockIdx.x];
   constexpr bool AOS = SMEM;
   const int q = (int)threadIdx.x % TPN;
   Node<T, AOS> nd = make_node_at<T, SMEM>(P, L, smem, b, (int)threadIdx.x / TPN);
@@ -671,7 +670,7 @@ template <class M, class T, bool SMEM, bool REFINE, bool GROUP, int TPN>
 __global__ void __launch_bounds__(LANES_MAX_THREADS) scp_kernel_lanes(ProblemDev P, Layout L, const double* x0,
                                                                       const double* u0, double* xout, double* uout,
                                                                       ucn_scp_stats* stats, int* status_out) {
-  scp_lanes_body<M, T, SMEM, REFINE, GROUP, TPN>(P, L, x0, u0, xout, uout, stats, status_out);
+  scp_lanes_body<M, T, SMEM, REFINE, GROUP, TPN>(P, L, x0, u0, xout, uout, stats, status_out, cta_instance<GROUP>(P));
 }
 
 // CTAs of up to 384 threads, one resident per SM guaranteed its registers (168).
@@ -680,7 +679,7 @@ __global__ void __launch_bounds__(LANES_WIDE_THREADS, 1) scp_kernel_lanes_wide(P
                                                                                const double* x0, const double* u0,
                                                                                double* xout, double* uout,
                                                                                ucn_scp_stats* stats, int* status_out) {
-  scp_lanes_body<M, T, SMEM, REFINE, GROUP, TPN>(P, L, x0, u0, xout, uout, stats, status_out);
+  scp_lanes_body<M, T, SMEM, REFINE, GROUP, TPN>(P, L, x0, u0, xout, uout, stats, status_out, cta_instance<GROUP>(P));
 }
 
 // The kernel of register class MAXT (LANES_WIDE_THREADS or LANES_MAX_THREADS).

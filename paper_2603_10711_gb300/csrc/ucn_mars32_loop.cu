@@ -1,0 +1,8 @@
+// Device-resident request loop of a server: 3-DOF Mars descent, FP32 path with refinement; one thread
+// per node, node records in shared memory here, the other variants in their own units (compiled in
+// parallel).
+#include "ucn_launch.cuh"
+#include "ucn_serve.cuh"
+UCN_EXTERN_LOOP(Mars7, float, false, true, 1)
+UCN_INSTANTIATE_LOOP(Mars7, float, true, true, 1)
+UCN_DEFINE_LOOP_LAUNCHER(mars32, Mars7, float, true)

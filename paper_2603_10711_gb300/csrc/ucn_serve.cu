@@ -33,7 +33,7 @@
 #include <vector>
 
 #include "ucn_internal.h"
-#include "ucn_kernels.cuh"
+#include "ucn_serve.cuh"
 
 using namespace ucn;
 
@@ -53,110 +53,24 @@ ucn_status sfail(ucn_status s, const char* fmt, ...) {
 // DRAINING: its result was taken but its launch's keep kernel may still read
 // its device arrays, so it is not reused before that launch ends.
 enum { SLOT_FREE = 0, SLOT_ADMITTED = 1, SLOT_RUNNING = 2, SLOT_DRAINING = 3 };
+// slot_lane / ring_lane of a request published to the device-resident loop
+constexpr int LOOP_LANE = -2;
 
 // Requests per launch (bounds the pinned staging of a lane).
 constexpr int LAUNCH_CAP = 128;
-
-// Offsets (in doubles) of one request record: slot, ring entry to read (warm
-// start; -1: none), ring entry to fill (-1: none), the request's ticket (its
-// delivery tag), horizon, obstacle count, the problem data of one instance,
-// then the guesses.  Integers and bytes are stored as doubles (exact; tickets
-// below 2^53).
-struct RecLayout {
-  int K, RING, RINGW, TAG, N, NOBS, DT, PRM, QD, XR, RD, UR, QND, QN, XLO, XHI, ULO, UHI, XI, XT, TM, OC, OR, SETS, XG, UG,
-      END;
-};
-RecLayout rec_layout(int NX, int NU, int MO, int Xn, int Un) {
-  RecLayout r;
-  int o = 0;
-  r.K = o++; r.RING = o++; r.RINGW = o++; r.TAG = o++; r.N = o++; r.NOBS = o++; r.DT = o++;
-  r.PRM = o; o += 8;
-  r.QD = o; o += NX; r.XR = o; o += NX; r.RD = o; o += NU; r.UR = o; o += NU;
-  r.QND = o; o += NX; r.QN = o; o += NX; r.XLO = o; o += NX; r.XHI = o; o += NX;
-  r.ULO = o; o += NU; r.UHI = o; o += NU; r.XI = o; o += NX; r.XT = o; o += NX; r.TM = o; o += NX;
-  r.OC = o; o += 3 * MO; r.OR = o; o += MO; r.SETS = o; o += UCN_SET_PARAMS;
-  r.XG = o; o += Xn * NX; r.UG = o; o += Un * NU;
-  r.END = (o + 1) / 2 * 2;   // 16-byte records
-  return r;
-}
-
-// What the scatter and keep kernels need (by value).
-struct ServeDev {
-  int NX, NU, MO, Xn, Un, REC, RES;
-  long long state_per_slot;
-  RecLayout rl;
-  int *N, *nobs;
-  double *dt, *prm, *Qd, *xr, *Rd, *ur, *QNd, *qN, *xlo, *xhi, *ulo, *uhi, *xi, *xt, *oc, *orr, *sets;
-  unsigned char *tm, *warm;
-  unsigned long long* tag;
-  double *x0, *u0, *xo, *uo, *state;
-  ucn_scp_stats* stats;
-  double *ring_x, *ring_u, *ring_state;
-};
 
 // One CTA per launched request j: its record rec[j] into the slot arrays (or
 // the guess and ADMM state from a ring entry for a warm start), and the CTA ->
 // slot order of the launch.
 __global__ void serve_scatter_kernel(ServeDev D, const double* rec, int* order) {
-  const int j = blockIdx.x, t = threadIdx.x, nt = blockDim.x;
-  const double* r = rec + (long long)j * D.REC;
-  const RecLayout& L = D.rl;
-  const int k = (int)r[L.K], ring = (int)r[L.RING], N = (int)r[L.N];
-  const int NX = D.NX, NU = D.NU, MO = D.MO;
-  if (t == 0) {
-    order[j] = k;
-    D.tag[k] = (unsigned long long)r[L.TAG];
-    D.N[k] = N;
-    D.nobs[k] = (int)r[L.NOBS];
-    D.dt[k] = r[L.DT];
-    D.warm[k] = ring >= 0 ? 1 : 0;
-  }
-  for (int e = t; e < 8; e += nt) { D.prm[k * 8 + e] = r[L.PRM + e]; D.sets[k * UCN_SET_PARAMS + e] = r[L.SETS + e]; }
-  for (int e = t; e < NX; e += nt) {
-    D.Qd[k * NX + e] = r[L.QD + e]; D.xr[k * NX + e] = r[L.XR + e]; D.QNd[k * NX + e] = r[L.QND + e];
-    D.qN[k * NX + e] = r[L.QN + e]; D.xlo[k * NX + e] = r[L.XLO + e]; D.xhi[k * NX + e] = r[L.XHI + e];
-    D.xi[k * NX + e] = r[L.XI + e]; D.xt[k * NX + e] = r[L.XT + e]; D.tm[k * NX + e] = (unsigned char)r[L.TM + e];
-  }
-  for (int e = t; e < NU; e += nt) {
-    D.Rd[k * NU + e] = r[L.RD + e]; D.ur[k * NU + e] = r[L.UR + e];
-    D.ulo[k * NU + e] = r[L.ULO + e]; D.uhi[k * NU + e] = r[L.UHI + e];
-  }
-  for (int e = t; e < 3 * MO; e += nt) D.oc[(long long)k * 3 * MO + e] = r[L.OC + e];
-  for (int e = t; e < MO; e += nt) D.orr[(long long)k * MO + e] = r[L.OR + e];
-  double* x0 = D.x0 + (long long)k * D.Xn * NX;
-  double* u0 = D.u0 + (long long)k * D.Un * NU;
-  if (ring >= 0) {
-    const double* rx = D.ring_x + (long long)ring * D.Xn * NX;
-    const double* ru = D.ring_u + (long long)ring * D.Un * NU;
-    const double* rs = D.ring_state + (long long)ring * D.state_per_slot;
-    double* st = D.state + (long long)k * D.state_per_slot;
-    for (int e = t; e < (N + 1) * NX; e += nt) x0[e] = rx[e];
-    for (int e = t; e < N * NU; e += nt) u0[e] = ru[e];
-    for (long long e = t; e < D.state_per_slot; e += nt) st[e] = rs[e];
-  } else {
-    for (int e = t; e < (N + 1) * NX; e += nt) x0[e] = r[L.XG + e];
-    for (int e = t; e < N * NU; e += nt) u0[e] = r[L.UG + e];
-  }
+  const int k = serve_scatter_one<false>(D, rec + (long long)blockIdx.x * D.REC);
+  if (threadIdx.x == 0) order[blockIdx.x] = k;
 }
 
 // One CTA per launched request j that keeps its result: its trajectory and
 // final ADMM state into the ring entry the launch assigned it (warm starts).
 __global__ void serve_keep_kernel(ServeDev D, const double* rec) {
-  const int j = blockIdx.x, t = threadIdx.x, nt = blockDim.x;
-  const double* r = rec + (long long)j * D.REC;
-  const RecLayout& L = D.rl;
-  const int k = (int)r[L.K], ringw = (int)r[L.RINGW], N = (int)r[L.N];
-  if (ringw < 0) return;
-  const int NX = D.NX, NU = D.NU;
-  const double* xo = D.xo + (long long)k * D.Xn * NX;
-  const double* uo = D.uo + (long long)k * D.Un * NU;
-  double* rx = D.ring_x + (long long)ringw * D.Xn * NX;
-  double* ru = D.ring_u + (long long)ringw * D.Un * NU;
-  double* rs = D.ring_state + (long long)ringw * D.state_per_slot;
-  const double* st = D.state + (long long)k * D.state_per_slot;
-  for (int e = t; e < (N + 1) * NX; e += nt) rx[e] = xo[e];
-  for (int e = t; e < N * NU; e += nt) ru[e] = uo[e];
-  for (long long e = t; e < D.state_per_slot; e += nt) rs[e] = st[e];
+  serve_keep_one<false>(D, rec + (long long)blockIdx.x * D.REC);
 }
 
 }  // namespace
@@ -200,6 +114,24 @@ struct ucn_server {
   int R, ring_next;
   std::vector<unsigned long long> ring_ticket;
   std::vector<int> ring_N, ring_done, ring_writing, ring_lane, ring_readers;
+  // the device-resident request loop: per-slot request records, the queue of
+  // published slots and its head, the stop flag (mapped host memory; host and
+  // device views), the claim counter (device memory), its stream and the event
+  // recorded after its launch
+  double *lrec_h = nullptr, *lrec_dv = nullptr;
+  long long *lq_h = nullptr, *lq_dv = nullptr;
+  unsigned long long *lhead_h = nullptr, *lhead_dv = nullptr;
+  unsigned *lstop_h = nullptr, *lstop_dv = nullptr;
+  unsigned long long* lnext_d = nullptr;
+  cudaStream_t loop_stream = nullptr;
+  cudaEvent_t loop_done = nullptr;
+  bool loop_on = false;         // submit publishes to the loop (ucn_serve_loop_start .. _stop)
+  bool loop_live = false;       // a loop launch has been made and not seen to end
+  int loop_ctas = 0;            // CTAs asked for (0: every CTA that can be resident)
+  unsigned long long loop_idle_ns = 0;
+  unsigned long long published = 0;
+  cudaError_t loop_error = cudaSuccess;
+  int loop_launches = 0, loop_ctas_launched = 0;
   std::mutex mu;
 };
 
@@ -297,13 +229,103 @@ int take_ring_entry(ucn_server* s) {
   return -1;
 }
 
+bool delivered(const ucn_server* s, int k);
+
+// Publishes admitted slot k to the device-resident loop: the ring entry that
+// keeps its result, its record into mapped memory, its queue entry, then the
+// head (a release store: the GPU's acquire load of the head sees the rest).
+void publish(ucn_server* s, int k) {
+  const RecLayout& L = s->rl;
+  double* rec = &s->hrec[(size_t)k * L.END];
+  const int rw = take_ring_entry(s);
+  rec[L.RINGW] = rw;
+  s->slot_ring_write[k] = rw;
+  if (rw >= 0) {
+    s->ring_writing[rw] = 1; s->ring_done[rw] = 0; s->ring_lane[rw] = LOOP_LANE;
+    s->ring_ticket[rw] = s->slot_ticket[k]; s->ring_N[rw] = (int)rec[L.N];
+  }
+  std::memcpy(s->lrec_h + (size_t)k * L.END, rec, (size_t)L.END * sizeof(double));
+  s->lq_h[s->published % (unsigned long long)s->S] = k;
+  ++s->published;
+  __atomic_store_n(s->lhead_h, s->published, __ATOMIC_RELEASE);
+  s->slot_state[k] = SLOT_RUNNING; s->slot_lane[k] = LOOP_LANE; s->slot_pos[k] = -1;
+}
+
+// Whether the loop launch has ended (recording a failure); false while it runs.
+bool loop_ended(ucn_server* s) {
+  if (!s->loop_live) return true;
+  const cudaError_t q = cudaEventQuery(s->loop_done);
+  if (q == cudaErrorNotReady) return false;
+  if (q != cudaSuccess) s->loop_error = q;
+  s->loop_live = false;
+  return true;
+}
+
+// One launch of the loop kernel on the loop's stream (query: only the number
+// of its CTAs that can be resident at once, into *cap).
+cudaError_t loop_launch(ucn_server* s, bool query = false, int* cap = nullptr) {
+  auto fn = loop_launcher_for(s->cfg.model, s->cfg.precision);
+  if (!fn) return cudaErrorNotSupported;
+  LoopDev Q;
+  Q.rec = s->lrec_dv; Q.queue = s->lq_dv; Q.head = s->lhead_dv; Q.stop = s->lstop_dv; Q.next = s->lnext_d;
+  Q.idle_ns = s->loop_idle_ns; Q.S = s->S;
+  LoopCfg c;
+  c.Q = &Q; c.D = &s->D; c.P = &s->P; c.L = &s->L; c.status = s->status_d;
+  c.smem = s->smem; c.smem_bytes = s->smem_bytes;
+  c.threads = s->tpn == 4 ? (4 * (s->Nmax + 1) + 31) / 32 * 32 : s->threads;
+  c.tpn = s->tpn; c.ctas = s->loop_ctas; c.stream = s->loop_stream;
+  int n = 0;
+  c.launched_ctas = &n;
+  c.query = query;
+  cudaError_t e = fn(c);
+  if (query) {
+    if (cap) *cap = e == cudaSuccess ? n : 0;
+    return e;
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(s->loop_done, s->loop_stream);
+  if (e != cudaSuccess) { s->loop_error = e; return e; }
+  s->loop_live = true;
+  ++s->loop_launches;
+  s->loop_ctas_launched = n;
+  return cudaSuccess;
+}
+
+// A new loop launch when the last one has ended (its CTAs found no request for
+// the idle time) while published requests wait; the loop's failure, if any.
+cudaError_t loop_kick(ucn_server* s) {
+  if (!s->loop_on || s->loop_error != cudaSuccess || !loop_ended(s) || s->loop_error != cudaSuccess)
+    return s->loop_error;
+  bool pending = false;
+  for (int k = 0; k < s->S && !pending; ++k)
+    pending = s->slot_state[k] == SLOT_RUNNING && s->slot_lane[k] == LOOP_LANE && !delivered(s, k);
+  return pending ? loop_launch(s) : cudaSuccess;
+}
+
+// Whether ring entry r holds a complete result that a request published to the
+// loop may read (the loop orders nothing by streams): its writer's launch has
+// ended, or its writer is a loop request whose result has been delivered (the
+// loop writes the ring entry before it delivers).
+bool ring_complete(ucn_server* s, int r) {
+  if (s->ring_done[r]) return true;
+  if (!s->ring_writing[r]) return false;
+  if (s->ring_lane[r] == LOOP_LANE) {
+    auto it = s->ticket_slot.find(s->ring_ticket[r]);
+    return it != s->ticket_slot.end() && delivered(s, it->second);
+  }
+  lane_ended(s, s->ring_lane[r]);   // retires the lane: its entries become kept
+  return s->ring_done[r] != 0;
+}
+
 }  // namespace
 
 extern "C" {
 
 void ucn_serve_destroy(ucn_server* s) {
   if (!s) return;
+  if (s->lstop_h) __atomic_store_n(s->lstop_h, 1u, __ATOMIC_RELEASE);   // a running loop ends
   cudaDeviceSynchronize();
+  if (s->loop_stream) cudaStreamDestroy(s->loop_stream);
+  if (s->loop_done) cudaEventDestroy(s->loop_done);
   for (cudaStream_t st : s->streams) cudaStreamDestroy(st);
   for (cudaEvent_t e : s->done) cudaEventDestroy(e);
   for (void* p : s->dev_allocs) cudaFree(p);
@@ -373,6 +395,18 @@ ucn_status ucn_serve_create(const ucn_serve_config* c, ucn_server** out) {
   ok = ok && dalloc(s, &s->status_d, (size_t)S);
   // result records and flags in mapped host memory, written by the solve's CTAs
   ok = ok && mapped(s, &s->res_h, &s->res_dv, (size_t)S * RES) && mapped(s, &s->flag_h, &s->flag_dv, (size_t)S);
+  // the request loop's records, queue, head and stop flag, claim counter
+  ok = ok && mapped(s, &s->lrec_h, &s->lrec_dv, (size_t)S * REC) && mapped(s, &s->lq_h, &s->lq_dv, (size_t)S);
+  ok = ok && mapped(s, &s->lhead_h, &s->lhead_dv, 1) && mapped(s, &s->lstop_h, &s->lstop_dv, 1);
+  ok = ok && dalloc(s, &s->lnext_d, 1);
+  if (ok) {
+    ok = cudaStreamCreateWithFlags(&s->loop_stream, cudaStreamNonBlocking) == cudaSuccess;
+    if (!ok) s->loop_stream = nullptr;
+  }
+  if (ok) {
+    ok = cudaEventCreateWithFlags(&s->loop_done, cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) s->loop_done = nullptr;
+  }
   long long *dxoff = nullptr, *duoff = nullptr, *dsoff = nullptr;
   double* dfac = nullptr;
   ok = ok && dalloc(s, &dxoff, S) && dalloc(s, &duoff, S) && dalloc(s, &dsoff, S);
@@ -454,6 +488,8 @@ ucn_status ucn_serve_submit(ucn_server* s, const ucn_request* r, unsigned long l
           s->ring_N[k] == N)
         ring = k;
     if (ring < 0) return sfail(UCN_EINVAL, "no guess and no kept result of horizon %d for ticket %llu", N, r->warm_ticket);
+    if (s->loop_on && !ring_complete(s, ring))
+      return sfail(UCN_EBUSY, "the kept result of ticket %llu is not complete yet", r->warm_ticket);
   }
   const long long fp = footprint(s, N);
   int slot = -1;
@@ -497,6 +533,11 @@ ucn_status ucn_serve_submit(ucn_server* s, const ucn_request* r, unsigned long l
   s->slot_ticket[k] = s->next_ticket++;
   s->ticket_slot[s->slot_ticket[k]] = k;
   *ticket = s->slot_ticket[k];
+  if (s->loop_on) {
+    publish(s, k);
+    const cudaError_t e = loop_kick(s);
+    if (e != cudaSuccess) return sfail(UCN_ECUDA, "request loop: %s", cudaGetErrorString(e));
+  }
   return UCN_OK;
 }
 
@@ -505,6 +546,10 @@ ucn_status ucn_serve_pump(ucn_server* s, int* launched) {
   if (!s) return sfail(UCN_EINVAL, "null server");
   if (launched) *launched = 0;
   std::lock_guard<std::mutex> lk(s->mu);
+  if (s->loop_on) {   // requests go to the loop at submit; relaunch it if it ended idle
+    const cudaError_t e = loop_kick(s);
+    return e == cudaSuccess ? UCN_OK : sfail(UCN_ECUDA, "request loop: %s", cudaGetErrorString(e));
+  }
   std::vector<int> ready;
   const int cap = std::min(s->S, LAUNCH_CAP);
   for (int k = 0; k < s->S && (int)ready.size() < cap; ++k)
@@ -588,14 +633,21 @@ void take_result(ucn_server* s, int k, ucn_result* res) {
   std::memcpy(&res->stats, o, sizeof(ucn_scp_stats));
   if (res->x) std::memcpy(res->x, o + 16, (size_t)(N + 1) * NX * sizeof(double));
   if (res->u) std::memcpy(res->u, o + 16 + (N + 1) * NX, (size_t)N * NU * sizeof(double));
-  const int rr = s->slot_ring_read[k];
+  const int rr = s->slot_ring_read[k], rw = s->slot_ring_write[k];
   if (rr >= 0) s->ring_readers[rr]--;   // its launch read the entry before the solve began
   s->slot_ring_write[k] = s->slot_ring_read[k] = -1;
   res->ticket = s->slot_ticket[k];
   res->horizon = N;
   s->ticket_slot.erase(s->slot_ticket[k]);
-  if (s->lane_busy[s->slot_lane[k]]) s->slot_state[k] = SLOT_DRAINING;   // freed when its lane retires
-  else release_slot(s, k);
+  if (s->slot_lane[k] == LOOP_LANE) {
+    // the loop's CTA kept the result and left the slot before it delivered
+    if (rw >= 0) { s->ring_writing[rw] = 0; s->ring_done[rw] = 1; }
+    release_slot(s, k);
+  } else if (s->lane_busy[s->slot_lane[k]]) {
+    s->slot_state[k] = SLOT_DRAINING;   // freed when its lane retires
+  } else {
+    release_slot(s, k);
+  }
 }
 
 // Slot k's request has been delivered (its CTA raised the flag with its ticket).
@@ -620,10 +672,15 @@ ucn_status ucn_serve_poll(ucn_server* s, unsigned long long ticket, ucn_result* 
   if (!delivered(s, k)) {
     if (s->slot_state[k] == SLOT_RUNNING) {
       const int l = s->slot_lane[k];
-      if (lane_ended(s, l) && !delivered(s, k) && s->lane_error[l] != cudaSuccess)
+      if (l == LOOP_LANE) {
+        const cudaError_t e = loop_kick(s);
+        if (e != cudaSuccess && !delivered(s, k))
+          return sfail(UCN_ECUDA, "request loop failed: %s", cudaGetErrorString(e));
+      } else if (lane_ended(s, l) && !delivered(s, k) && s->lane_error[l] != cudaSuccess) {
         return sfail(UCN_ECUDA, "serve launch failed: %s", cudaGetErrorString(s->lane_error[l]));
+      }
     }
-    return UCN_EBUSY;                 // admitted and not launched yet, or still solving
+    if (!delivered(s, k)) return UCN_EBUSY;   // admitted and not launched yet, or still solving
   }
   take_result(s, k, res);
   return UCN_OK;
@@ -643,7 +700,72 @@ ucn_status ucn_serve_poll_any(ucn_server* s, ucn_result* res) {
   for (int l = 0; l < s->lanes; ++l)
     if (lane_ended(s, l) && s->lane_error[l] != cudaSuccess)
       return sfail(UCN_ECUDA, "serve launch failed: %s", cudaGetErrorString(s->lane_error[l]));
+  const cudaError_t e = loop_kick(s);
+  if (e != cudaSuccess) return sfail(UCN_ECUDA, "request loop failed: %s", cudaGetErrorString(e));
   return UCN_EBUSY;
+}
+
+ucn_status ucn_serve_loop_start(ucn_server* s, int ctas, double idle_s) {
+  set_error_message("");
+  if (!s) return sfail(UCN_EINVAL, "null server");
+  if (!loop_launcher_for(s->cfg.model, s->cfg.precision))
+    return sfail(UCN_EINVAL, "the request loop serves the 12-state quadrotor and the 3-DOF Mars model");
+  if (ctas < 0 || !(idle_s > 0.0 && idle_s <= 60.0)) return sfail(UCN_EINVAL, "ctas must be >= 0 and idle_s in (0, 60]");
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (s->loop_on) return sfail(UCN_EINVAL, "the request loop is already on");
+  s->loop_ctas = ctas;
+  s->loop_idle_ns = (unsigned long long)(idle_s * 1e9);
+  s->loop_error = cudaSuccess;
+  __atomic_store_n(s->lstop_h, 0u, __ATOMIC_RELEASE);
+  s->loop_on = true;
+  // requests admitted and not pumped go to the loop, oldest first
+  std::vector<std::pair<unsigned long long, int>> adm;
+  for (int k = 0; k < s->S; ++k)
+    if (s->slot_state[k] == SLOT_ADMITTED) adm.emplace_back(s->slot_ticket[k], k);
+  std::sort(adm.begin(), adm.end());
+  for (auto& a : adm) publish(s, a.second);
+  const cudaError_t e = loop_launch(s);
+  if (e != cudaSuccess) return sfail(UCN_ECUDA, "request loop launch: %s", cudaGetErrorString(e));
+  return UCN_OK;
+}
+
+ucn_status ucn_serve_loop_stop(ucn_server* s) {
+  set_error_message("");
+  if (!s) return sfail(UCN_EINVAL, "null server");
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (!s->loop_on) return UCN_OK;
+  cudaError_t e = loop_kick(s);   // requests that wait get a launch to serve them
+  __atomic_store_n(s->lstop_h, 1u, __ATOMIC_RELEASE);
+  const cudaError_t w = cudaStreamSynchronize(s->loop_stream);   // the loop ends once the queue is empty
+  if (e == cudaSuccess) e = w;
+  loop_ended(s);
+  if (e == cudaSuccess) e = s->loop_error;
+  __atomic_store_n(s->lstop_h, 0u, __ATOMIC_RELEASE);
+  s->loop_on = false;
+  if (e != cudaSuccess) return sfail(UCN_ECUDA, "request loop failed: %s", cudaGetErrorString(e));
+  // every published request has been delivered: the ring entries it wrote are complete
+  for (int r = 0; r < s->R; ++r)
+    if (s->ring_writing[r] && s->ring_lane[r] == LOOP_LANE) { s->ring_writing[r] = 0; s->ring_done[r] = 1; }
+  return UCN_OK;
+}
+
+int ucn_serve_loop_capacity(ucn_server* s) {
+  set_error_message("");
+  if (!s) return -1;
+  std::lock_guard<std::mutex> lk(s->mu);
+  int cap = 0;
+  const cudaError_t e = loop_launch(s, true, &cap);
+  if (e != cudaSuccess) {
+    sfail(UCN_EINVAL, "request loop: %s", cudaGetErrorString(e));
+    return -1;
+  }
+  return cap;
+}
+
+int ucn_serve_loop_launches(ucn_server* s) {
+  if (!s) return -1;
+  std::lock_guard<std::mutex> lk(s->mu);
+  return s->loop_launches;
 }
 
 int ucn_serve_free_slots(ucn_server* s) {

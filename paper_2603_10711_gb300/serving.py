@@ -4,7 +4,10 @@ and a host scheduling loop for request streams).
 Requests are admitted into the server's slots as they arrive (while slots and
 the HBM budget allow), every pump launches the admitted ones on a free lane
 (stream) while earlier launches are still running, and finished results are
-collected by non-blocking polls.  Latency is arrival -> result collected.
+collected by non-blocking polls.  With the device-resident loop on
+(Server.loop_start) a persistent kernel claims each request as it is submitted
+instead, and pump only relaunches that kernel after an idle end.  Latency is
+arrival -> result collected.
 """
 from __future__ import annotations
 
@@ -60,6 +63,14 @@ def _setup(L):
     L.ucn_serve_poll_any.restype = C.c_int
     L.ucn_serve_free_slots.argtypes = [vp]
     L.ucn_serve_free_slots.restype = C.c_int
+    L.ucn_serve_loop_start.argtypes = [vp, C.c_int, C.c_double]
+    L.ucn_serve_loop_start.restype = C.c_int
+    L.ucn_serve_loop_stop.argtypes = [vp]
+    L.ucn_serve_loop_stop.restype = C.c_int
+    L.ucn_serve_loop_launches.argtypes = [vp]
+    L.ucn_serve_loop_launches.restype = C.c_int
+    L.ucn_serve_loop_capacity.argtypes = [vp]
+    L.ucn_serve_loop_capacity.restype = C.c_int
     L._serve_ready = True
     return L
 
@@ -179,6 +190,31 @@ class Server:
     def free_slots(self):
         return int(self.L.ucn_serve_free_slots(self.h))
 
+    def loop_start(self, ctas=0, idle_s=1.0):
+        """Switch to the device-resident request loop (ucn_serve_loop_start):
+        from here on every submit is published to a persistent kernel whose
+        CTAs claim and solve requests as they free up; pump only relaunches the
+        loop after an idle end."""
+        rc = self.L.ucn_serve_loop_start(self.h, int(ctas), float(idle_s))
+        if rc != ucn.UCN_OK:
+            raise ucn.UcnError(rc, ucn.ucn_last_error())
+
+    def loop_stop(self):
+        """Serve what is queued, end the loop kernel, back to pump launches."""
+        rc = self.L.ucn_serve_loop_stop(self.h)
+        if rc != ucn.UCN_OK:
+            raise ucn.UcnError(rc, ucn.ucn_last_error())
+
+    def loop_launches(self):
+        return int(self.L.ucn_serve_loop_launches(self.h))
+
+    def loop_capacity(self):
+        """CTAs of this server's loop kernel that can be resident at once."""
+        n = int(self.L.ucn_serve_loop_capacity(self.h))
+        if n < 0:
+            raise ucn.UcnError(ucn.UCN_EINVAL, ucn.ucn_last_error())
+        return n
+
 
 def horizon_route(buckets):
     """A route for run_stream over servers keyed (model, max_horizon): each
@@ -191,16 +227,24 @@ def horizon_route(buckets):
     return route
 
 
+def server_name(key):
+    """A server key as text: "1" for a model, "1/40" for (model, max_horizon)."""
+    return "/".join(str(v) for v in key) if isinstance(key, tuple) else str(key)
+
+
 def run_stream(stream, servers, max_inflight=None, time_scale=1.0, route=None):
     """Replay a request stream [(arrival_s, Problem)] against `servers` in real
     time: a dict key -> Server, each request going to servers[route(request)]
     (default key: the request's model).  max_inflight=1 gives the one-at-a-time
-    (per-request) path.  Returns latencies and throughput (also per model)."""
+    (per-request) path.  Returns latencies and throughput (also per model), and
+    per server the number of solves and their mean device time (start to end of
+    the solve's CTA) in solve_ms_by_server."""
     route = route or (lambda p: p.model)
     pending = deque(sorted(stream, key=lambda r: r[0]))
     waiting = {m: deque() for m in servers}     # arrived, not yet admitted, per server (FIFO)
     inflight = {}
     lat, defects, models = [], [], []
+    busy = {m: [] for m in servers}     # device time of each solve (its CTA's start to end), per server
     n = len(pending)
     t0 = time.perf_counter()
     while len(lat) < n:
@@ -227,8 +271,10 @@ def run_stream(stream, servers, max_inflight=None, time_scale=1.0, route=None):
                     break
                 arr, model = inflight.pop((key, ticket))
                 lat.append((time.perf_counter() - t0) / time_scale - arr)
-                defects.append(float(res["stats"]["defect"]))
+                st = res["stats"]
+                defects.append(float(st["defect"]))
                 models.append(model)
+                busy[key].append(1e-6 * (int(st["t_end_ns"]) - int(st["t_start_ns"])))
     elapsed = time.perf_counter() - t0
     lat = np.array(lat)
     d = np.array(defects)
@@ -240,4 +286,5 @@ def run_stream(stream, servers, max_inflight=None, time_scale=1.0, route=None):
         lm = lat[models == m]
         out["model%d" % m] = {"requests": int(lm.size), "p50_ms": 1e3 * float(np.percentile(lm, 50)),
                               "p99_ms": 1e3 * float(np.percentile(lm, 99))}
+    out["solve_ms_by_server"] = {server_name(k): [len(v), float(np.mean(v))] for k, v in busy.items() if v}
     return out

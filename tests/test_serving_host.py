@@ -1,5 +1,6 @@
 """Host-side serving logic without a GPU: the horizon route sends each request
-to its model's server with the smallest horizon that holds it."""
+to its model's server with the smallest horizon that holds it; the request-loop
+entry points reject a missing server before touching the device."""
 import pytest
 
 import workloads as W
@@ -14,3 +15,14 @@ def test_horizon_route_picks_the_smallest_bucket_that_holds_the_request():
         assert route(W.mars_batch(1, seed=1, N=N)) == key
     with pytest.raises(ValueError):                       # no bucket holds it
         route(W.mars_batch(1, seed=1, N=201))
+
+
+def test_loop_entry_points_reject_a_null_server():
+    from paper_2603_10711_gb300 import build, ucn
+    build.build()
+    L = serving._setup(ucn.lib())
+    assert L.ucn_serve_loop_start(None, 0, 1.0) == ucn.UCN_EINVAL
+    assert "null server" in ucn.ucn_last_error()
+    assert L.ucn_serve_loop_stop(None) == ucn.UCN_EINVAL
+    assert L.ucn_serve_loop_launches(None) == -1
+    assert L.ucn_serve_loop_capacity(None) == -1
