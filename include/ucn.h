@@ -435,8 +435,10 @@ int ucn_serve_free_slots(ucn_server* srv);
  * III-B: the same kernel body on the same slot layout), keeps its result in the
  * ring and delivers it to host memory; there is no pump and no launch per
  * request.  Requests admitted and not pumped when the loop starts go to it
- * first.  Every wait of the kernel is bounded: a CTA that has found no request
- * for `idle_s` seconds (0 < idle_s <= 60) ends, and the next submit, pump,
+ * first.  Every wait of the kernel is bounded: once no request has been
+ * published to the server for `idle_s` seconds (0 < idle_s <= 60) its CTAs
+ * end (each CTA's idle clock restarts whenever a request is published, so the
+ * loop keeps all its CTAs while requests arrive), and the next submit, pump,
  * poll or poll_any relaunches the loop if requests wait.  While the loop is on,
  * ucn_serve_pump only does that relaunch (*launched = 0), and a warm start must
  * name a result that has been delivered (UCN_EBUSY until then).  Errors:

@@ -144,7 +144,7 @@ struct LoopDev {
   const unsigned long long* head;  // requests published (mapped; written by the host)
   const unsigned* stop;            // nonzero: end once every published request is claimed (mapped)
   unsigned long long* next;        // requests claimed so far (device memory; never reset)
-  unsigned long long idle_ns;      // a CTA that has found no request for this long ends
+  unsigned long long idle_ns;      // the loop ends once no request has been published for this long
   int S;
 };
 
@@ -155,12 +155,20 @@ __device__ __forceinline__ unsigned long long ld_acquire_sys_u64(const unsigned 
 }
 
 // Thread 0: the slot of the next request, or -1 when the loop should end (stop
-// requested and nothing left to claim, or no request for Q.idle_ns).  Every
-// wait is a bounded sleep.
-__device__ __forceinline__ long long loop_claim(const LoopDev& Q, unsigned long long& idle_t0) {
+// requested and nothing left to claim, or no request published to the server
+// for Q.idle_ns).  The idle clock restarts whenever the head moves, whichever
+// CTA claims the request, so that every CTA of the loop stays while requests
+// keep arriving and all of them end together once the server has been quiet
+// for the idle time.  Every wait is a bounded sleep.
+__device__ __forceinline__ long long loop_claim(const LoopDev& Q, unsigned long long& idle_t0,
+                                                unsigned long long& seen_head) {
   unsigned sleep_ns = 32;
   for (;;) {
     const unsigned long long h = ld_acquire_sys_u64(Q.head);
+    if (h != seen_head) {
+      seen_head = h;
+      idle_t0 = globaltimer_ns();
+    }
     unsigned long long n = *(volatile unsigned long long*)Q.next;
     while (n < h) {
       const long long k = *(volatile const long long*)(Q.queue + n % (unsigned long long)Q.S);
@@ -184,11 +192,11 @@ template <class M, class T, bool SMEM, bool REFINE, int TPN>
 __device__ __forceinline__ void serve_loop_body(const LoopDev& Q, const ServeDev& D, const ProblemDev& P,
                                                 const Layout& L, int* status) {
   __shared__ long long slot;
-  unsigned long long idle_t0 = globaltimer_ns();
+  unsigned long long idle_t0 = globaltimer_ns(), seen_head = ~0ull;
   ProblemDev Ps = P;
   Ps.res_host = nullptr;   // the solve delivers nothing itself: the ring entry is written first
   for (;;) {
-    if (threadIdx.x == 0) slot = loop_claim(Q, idle_t0);
+    if (threadIdx.x == 0) slot = loop_claim(Q, idle_t0, seen_head);
     __syncthreads();
     const long long k = slot;
     __syncthreads();
@@ -205,7 +213,6 @@ __device__ __forceinline__ void serve_loop_body(const LoopDev& Q, const ServeDev
     __threadfence();
     __syncthreads();
     deliver_result(P, (int)k, D.xo, D.uo, D.stats);
-    if (threadIdx.x == 0) idle_t0 = globaltimer_ns();
   }
 }
 

@@ -238,7 +238,8 @@ def run_stream(stream, servers, max_inflight=None, time_scale=1.0, route=None):
     (default key: the request's model).  max_inflight=1 gives the one-at-a-time
     (per-request) path.  Returns latencies and throughput (also per model), and
     per server the number of solves and their mean device time (start to end of
-    the solve's CTA) in solve_ms_by_server."""
+    the solve's CTA) in solve_ms_by_server, and how many ran at once
+    (device_by_server)."""
     route = route or (lambda p: p.model)
     pending = deque(sorted(stream, key=lambda r: r[0]))
     waiting = {m: deque() for m in servers}     # arrived, not yet admitted, per server (FIFO)
@@ -274,7 +275,7 @@ def run_stream(stream, servers, max_inflight=None, time_scale=1.0, route=None):
                 st = res["stats"]
                 defects.append(float(st["defect"]))
                 models.append(model)
-                busy[key].append(1e-6 * (int(st["t_end_ns"]) - int(st["t_start_ns"])))
+                busy[key].append((int(st["t_start_ns"]), int(st["t_end_ns"])))
     elapsed = time.perf_counter() - t0
     lat = np.array(lat)
     d = np.array(defects)
@@ -286,5 +287,21 @@ def run_stream(stream, servers, max_inflight=None, time_scale=1.0, route=None):
         lm = lat[models == m]
         out["model%d" % m] = {"requests": int(lm.size), "p50_ms": 1e3 * float(np.percentile(lm, 50)),
                               "p99_ms": 1e3 * float(np.percentile(lm, 99))}
-    out["solve_ms_by_server"] = {server_name(k): [len(v), float(np.mean(v))] for k, v in busy.items() if v}
+    out["solve_ms_by_server"] = {server_name(k): [len(v), 1e-6 * float(np.mean([e - b for b, e in v]))]
+                                 for k, v in busy.items() if v}
+    out["device_by_server"] = {server_name(k): device_use(v) for k, v in busy.items() if v}
     return out
+
+
+def device_use(spans):
+    """Solves of one server on the device, from their (start, end) timestamps in
+    ns: the most that ran at once, and the device time they took in all over the
+    span from the first start to the last end (mean solves running at once)."""
+    ev = sorted([(b, 1) for b, _ in spans] + [(e, -1) for _, e in spans])
+    run = most = 0
+    for _, d in ev:
+        run += d
+        most = max(most, run)
+    first, last = min(b for b, _ in spans), max(e for _, e in spans)
+    total = float(sum(e - b for b, e in spans))
+    return {"max_running": most, "span_s": 1e-9 * (last - first), "mean_running": total / max(last - first, 1)}
