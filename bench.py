@@ -668,7 +668,17 @@ def cpu_baseline(args, gpu_result=None):
     same = np.ones(n, dtype=bool)
     same[r["mismatch"]] = False
     parity = dict(r["summary"])
+    def spread(v):
+        # per-instance values: percentiles and a histogram by decade (upper edges)
+        v = np.asarray(v, dtype=np.float64)
+        edges = [1e-12, 1e-11, 1e-10, 1e-9, 1e-8, 1e-7, 1e-6, 1e-5, 1e-4, 1e-3, np.inf]
+        counts = np.histogram(v, bins=[0.0] + edges)[0]
+        return {"p50": float(np.percentile(v, 50)), "p90": float(np.percentile(v, 90)),
+                "p99": float(np.percentile(v, 99)), "max": float(v.max()),
+                "count_below": {("%.0e" % e if np.isfinite(e) else "inf"): int(c) for e, c in zip(edges, counts)}}
     parity.update({
+        "per_instance_rel_err": spread(r["err"]),
+        "per_instance_fp64_defect": spread(r["fp64_defect"]),
         "max_rel_err_same_iters_as_oracle": float(r["err"][same].max()) if same.any() else None,
         "gpu_defect_vs_oracle_rk4_max_abs": float(np.abs(st["defect"][idx] - r["fp64_defect"]).max()),
         "check_s": time.perf_counter() - t0,
