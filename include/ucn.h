@@ -446,7 +446,9 @@ int ucn_serve_free_slots(ucn_server* srv);
 ucn_status ucn_serve_loop_start(ucn_server* srv, int ctas, double idle_s);
 /* Serves every published request, ends the loop kernel (blocks until it has)
  * and returns the server to pump launches; UCN_OK when no loop is on.
- * Results stay in their slots until polled.  UCN_ECUDA if the loop failed. */
+ * Results stay in their slots until polled.  UCN_ECUDA if the loop failed (a
+ * launch error or a device fault): requests it had not delivered cannot
+ * complete, so destroy the server. */
 ucn_status ucn_serve_loop_stop(ucn_server* srv);
 /* Launches of the loop kernel so far (the first one and every relaunch after
  * an idle end); -1 for a NULL server. */
