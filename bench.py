@@ -90,11 +90,18 @@ TRAFFIC_SOURCES = ("include/ucn.h",) + tuple("paper_2603_10711_gb300/csrc/" + f 
 
 
 def kernel_sources_sha256():
+    """Hash of TRAFFIC_SOURCES with their comments and blank lines removed, so
+    that a change of documentation alone keeps the recorded traffic valid."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for p in TRAFFIC_SOURCES:
+        text = open(os.path.join(ROOT, p), encoding="utf-8").read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        text = "\n".join(line.rstrip() for line in text.splitlines() if line.strip())
         h.update(os.path.basename(p).encode())
-        h.update(open(os.path.join(ROOT, p), "rb").read())
+        h.update(text.encode())
     return h.hexdigest()
 
 
