@@ -425,7 +425,7 @@ ucn_status ucn_serve_poll_any(ucn_server* srv, ucn_result* res);
 int ucn_serve_free_slots(ucn_server* srv);
 
 /* Device-resident request loop (not in the paper; the serving layer around the
- * method, 12-state quadrotor and 3-DOF Mars servers).  ucn_serve_loop_start
+ * method).  ucn_serve_loop_start
  * launches one persistent kernel of `ctas` CTAs (0: as many as can be
  * resident at once) on the server's own stream.  From then on ucn_serve_submit
  * publishes each admitted request at once -- its record into mapped host
@@ -442,7 +442,7 @@ int ucn_serve_free_slots(ucn_server* srv);
  * poll or poll_any relaunches the loop if requests wait.  While the loop is on,
  * ucn_serve_pump only does that relaunch (*launched = 0), and a warm start must
  * name a result that has been delivered (UCN_EBUSY until then).  Errors:
- * UCN_EINVAL (other models, bad arguments, loop already on), UCN_ECUDA. */
+ * UCN_EINVAL (bad arguments, loop already on), UCN_ECUDA. */
 ucn_status ucn_serve_loop_start(ucn_server* srv, int ctas, double idle_s);
 /* Serves every published request, ends the loop kernel (blocks until it has)
  * and returns the server to pump launches; UCN_OK when no loop is on.
@@ -454,8 +454,7 @@ ucn_status ucn_serve_loop_stop(ucn_server* srv);
  * an idle end); -1 for a NULL server. */
 int ucn_serve_loop_launches(ucn_server* srv);
 /* How many CTAs of this server's loop kernel can be resident at once on the
- * current device (the `ctas` that 0 stands for); -1 for a NULL server or a
- * model without a loop.  Several servers whose loops run at the same time
+ * current device (the `ctas` that 0 stands for); -1 for a NULL server.  Several servers whose loops run at the same time
  * share the device: CTAs beyond what fits start only when others end, so give
  * each loop a share of its capacity. */
 int ucn_serve_loop_capacity(ucn_server* srv);

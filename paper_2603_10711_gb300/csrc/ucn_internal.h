@@ -104,17 +104,23 @@ inline Launchers launchers_for(int model, int precision) {
   return f64 ? Launchers{mars64_scp, mars64_admm, mars64_linearize} : Launchers{mars32_scp, mars32_admm, mars32_linearize};
 }
 
-// The device-resident request loop of a server (ucn_serve.cuh), for the
-// 12-state quadrotor and the 3-DOF Mars model; NULL for other models.
+// The device-resident request loop of a server (ucn_serve.cuh), one launcher
+// per model and precision; NULL for an unknown model.
 struct LoopCfg;
 cudaError_t quad64_loop(const LoopCfg& c);
 cudaError_t quad32_loop(const LoopCfg& c);
 cudaError_t mars64_loop(const LoopCfg& c);
 cudaError_t mars32_loop(const LoopCfg& c);
+cudaError_t quat64_loop(const LoopCfg& c);
+cudaError_t quat32_loop(const LoopCfg& c);
+cudaError_t m6dof64_loop(const LoopCfg& c);
+cudaError_t m6dof32_loop(const LoopCfg& c);
 inline cudaError_t (*loop_launcher_for(int model, int precision))(const LoopCfg&) {
   const bool f64 = precision == UCN_PREC_FP64;
   if (model == UCN_MODEL_QUAD12) return f64 ? quad64_loop : quad32_loop;
   if (model == UCN_MODEL_MARS7) return f64 ? mars64_loop : mars32_loop;
+  if (model == UCN_MODEL_QUAT13) return f64 ? quat64_loop : quat32_loop;
+  if (model == UCN_MODEL_MARS14) return f64 ? m6dof64_loop : m6dof32_loop;
   return nullptr;
 }
 

@@ -1,0 +1,8 @@
+// Device-resident request loop of a server: 6-DOF Mars lander, FP32 path with refinement; one thread
+// per node, node records in shared memory here, the other variant in its own unit (compiled in
+// parallel).
+#include "ucn_launch.cuh"
+#include "ucn_serve.cuh"
+UCN_EXTERN_LOOP(Mars14, float, false, true, 1)
+UCN_INSTANTIATE_LOOP(Mars14, float, true, true, 1)
+UCN_DEFINE_LOOP_LAUNCHER(m6dof32, Mars14, float, true)

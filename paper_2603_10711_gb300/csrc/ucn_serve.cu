@@ -708,8 +708,7 @@ ucn_status ucn_serve_poll_any(ucn_server* s, ucn_result* res) {
 ucn_status ucn_serve_loop_start(ucn_server* s, int ctas, double idle_s) {
   set_error_message("");
   if (!s) return sfail(UCN_EINVAL, "null server");
-  if (!loop_launcher_for(s->cfg.model, s->cfg.precision))
-    return sfail(UCN_EINVAL, "the request loop serves the 12-state quadrotor and the 3-DOF Mars model");
+  if (!loop_launcher_for(s->cfg.model, s->cfg.precision)) return sfail(UCN_EINVAL, "no request loop for this model");
   if (ctas < 0 || !(idle_s > 0.0 && idle_s <= 60.0)) return sfail(UCN_EINVAL, "ctas must be >= 0 and idle_s in (0, 60]");
   std::lock_guard<std::mutex> lk(s->mu);
   if (s->loop_on) return sfail(UCN_EINVAL, "the request loop is already on");

@@ -157,16 +157,37 @@ def test_idle_loop_ends_and_the_next_request_relaunches_it():
     srv.close()
 
 
-def test_loop_rejects_models_it_does_not_serve_and_a_second_start():
-    probs = W.quat_study(1, seed=5, scp_iters=6, admm_iters=40)
-    srv = serving.Server(3, ucn.UCN_PREC_FP64, max_slots=2, max_horizon=60, max_obs=3, lanes=1, settings=probs.settings)
+@pytest.mark.parametrize("kind", ["quat13", "mars14"])
+def test_paper_model_variants_through_the_loop_match_the_oracle(kind):
+    # the 13-state quaternion quadrotor and the 6-DOF Mars lander through the loop
+    # (one thread per node), two requests in flight, each against the oracle in FP64
+    if kind == "quat13":
+        probs = [W.quat_study(1, seed=s, scp_iters=6, admm_iters=40) for s in (5, 6)]
+        srv = serving.Server(3, ucn.UCN_PREC_FP64, max_slots=4, max_horizon=60, max_obs=3, lanes=1,
+                             settings=probs[0].settings)
+    else:
+        probs = [W.mars6_batch(1, seed=s, settings=dict(scp_iters=6, admm_iters=40, stop=0)) for s in (7, 8)]
+        srv = serving.Server(4, ucn.UCN_PREC_FP64, max_slots=4, max_horizon=40, lanes=1, settings=probs[0].settings)
+    srv.loop_start(idle_s=5.0)
+    tickets = []
+    for p in probs:
+        rc, t = srv.submit(p)
+        assert rc == ucn.UCN_OK
+        tickets.append(t)
+    res = [wait(srv, t, int(p.N[0])) for p, t in zip(probs, tickets)]
+    srv.loop_stop()
+    srv.close()
+    for p, r in zip(probs, res):
+        xr, ur, sr, _ = oracle.scp_solve(p)
+        assert rel(r["x"], xr) <= 1e-9 and rel(r["u"], ur) <= 1e-9
+        assert r["stats"]["scp_iters"] == int(sr[0, 7])
+
+
+def test_a_second_loop_start_is_rejected():
+    srv = serving.Server(1, ucn.UCN_PREC_FP64, max_slots=2, max_horizon=40, max_obs=4, lanes=1, settings=QSET)
+    srv.loop_start(idle_s=0.5)
     with pytest.raises(ucn.UcnError) as e:
         srv.loop_start()
     assert e.value.status == ucn.UCN_EINVAL
-    srv.close()
-    srv = serving.Server(1, ucn.UCN_PREC_FP64, max_slots=2, max_horizon=40, max_obs=4, lanes=1, settings=QSET)
-    srv.loop_start(idle_s=0.5)
-    with pytest.raises(ucn.UcnError):
-        srv.loop_start()
     srv.loop_stop()
     srv.close()
