@@ -185,6 +185,7 @@ def test_paper_model_variants_through_the_loop_match_the_oracle(kind):
 
 def test_a_second_loop_start_is_rejected():
     srv = serving.Server(1, ucn.UCN_PREC_FP64, max_slots=2, max_horizon=40, max_obs=4, lanes=1, settings=QSET)
+    assert srv.loop_capacity() >= torch.cuda.get_device_properties(0).multi_processor_count
     srv.loop_start(idle_s=0.5)
     with pytest.raises(ucn.UcnError) as e:
         srv.loop_start()
