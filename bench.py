@@ -663,9 +663,16 @@ def cpu_baseline(args, gpu_result=None):
     passed, n, dt, threads, idx, ref, sub = oracle_sample(args)
     base = {"value": passed / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": "%d of the %d Mars instances (every %d-th), %.1f s, %d passed" % (n, args.batch, args.batch // n, dt, passed)}
+    import oracle
+    # the same oracle on one host core, on the first 16 instances of that sample
+    one = sub.subset(np.arange(min(16, n)))
+    t0 = time.perf_counter()
+    st1 = oracle.scp_solve(one, nthreads=1)[2]
+    dt1 = time.perf_counter() - t0
+    base["single_core"] = {"value": float(np.sum(st1[:, 0] <= 1e-5)) / dt1, "unit": UNIT, "cores": 1,
+                           "sample": "the first %d instances of the sample, %.2f s" % (one.batch, dt1)}
     if gpu_result is None:
         return base, None
-    import oracle
     xg, ug, st = gpu_result
     prob = W.mars_batch(args.batch, seed=1)
     xs = np.concatenate([xg[prob.xoff[b]:prob.xoff[b] + prob.N[b] + 1] for b in idx])
