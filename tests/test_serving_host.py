@@ -26,3 +26,18 @@ def test_loop_entry_points_reject_a_null_server():
     assert L.ucn_serve_loop_stop(None) == ucn.UCN_EINVAL
     assert L.ucn_serve_loop_launches(None) == -1
     assert L.ucn_serve_loop_capacity(None) == -1
+
+
+def test_device_use_counts_the_solves_running_at_once():
+    # spans in ns: two overlap, a third starts when the first has ended (an end at the
+    # same instant as a start does not count as overlap)
+    d = serving.device_use([(0, 10), (5, 15), (10, 20)])
+    assert d["max_running"] == 2
+    assert abs(d["span_s"] - 20e-9) < 1e-15
+    assert abs(d["mean_running"] - 30.0 / 20.0) < 1e-12
+    assert serving.device_use([(3, 4)])["max_running"] == 1
+
+
+def test_server_names_of_stream_keys():
+    assert serving.server_name((1, 40)) == "1/40"
+    assert serving.server_name(2) == "2"
